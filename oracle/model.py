@@ -1,0 +1,503 @@
+"""Whole-lattice FP64 oracle of one thermocapillary phase-field LBM time step.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Every array is
+float64; PDF arrays are shaped (Q, nz, ny, nx), scalar fields (nz, ny, nx),
+vector fields (3, nz, ny, nx); x is the fastest axis.
+
+Time stepping (Sec. 2.5 / Sec. 4.1, Alg. 1 and Alg. 2; pull "one step, two
+grid" scheme): the stored PDFs are post-collision values.  One step
+
+  a1  pulls every PDF, p*_i(x) = p_i(x - c_i)   (half-way bounce-back for
+      h, g and anti-bounce-back for f at z walls),
+  a2  takes the zeroth moments phi = sum h*, p* = sum g*, T = sum f*,
+  a3  forms grad phi, lap phi, grad T with the isotropic D3Q27 operators,
+  a4  forms n, F^phi, sigma(T), mu_phi,
+  a5  forms F = F_s + F_b (+ F_p),
+  a6  forms u = sum c_i g*_i + F/(2 rho),
+  a7  collides h (single rate, Guo source),
+  a8  collides g in central-moment space (Guo forcing in moment space),
+  a9  collides f (single rate, + w_i q_T)   or a9' advances T by RK2/RK4,
+and all macroscopic quantities used in the collisions are those computed
+from the pulled PDFs of this step.  The first step pulls the initial
+equilibrium PDFs.
+
+Readings of passages that the paper leaves open or prints garbled (the CUDA
+path implements the same readings):
+  * relaxation rates of Eq. pflbm-tau / thlbm-tau are read as rates with the
+    diffusivity divided by c_s^2: omega = 1 / (1/2 + M / c_s^2);
+  * nu = c_s^2 (tau - 1/2) (the paper prints nu = tau c_s^2);
+  * the interface force of Eq. phasefieldforce enters as the Guo source
+    S_i = (1 - omega_phi/2) w_i (c_i . F^phi), whose first moment
+    c_s^2 (1 - omega_phi/2) F^phi recovers the flux M 4 phi (1-phi)/xi n;
+  * |grad phi^2| in F_s is read as |grad phi|^2;
+  * the chemical potential (not printed) is the double-well form
+    mu_phi = 4 beta phi (phi - 1)(phi - 1/2) - kappa lap phi,
+    beta = 12 sigma / xi, kappa = 3 sigma xi / 2, with the local sigma(T);
+  * Guo forcing "in collision space" for g: the force's central moments are
+    those of S_i = w_i [(c_i - u)/c_s^2 + (c_i . u) c_i / c_s^4] . a,
+    a = F / rho; second-order central moments relax with 1/tau(phi), all
+    moments of order >= 3 with ``omega_high`` (1 by default);
+  * walls: half-way bounce-back (h, g), anti-bounce-back f_i = -f_opp +
+    2 w_i T_w (f), mirror ghost for phi (neutral wetting), ghost
+    T_g = 2 T_w - T for temperature stencils;
+  * heat source Eq. HeatSource is non-zero for r^2 <= d_s^2 (printed >=);
+  * RK2 (Eq. rk2) is the midpoint rule T + R(T + K1/2);
+  * the imposed background gradient G enters as T_total = T + G.(x - x_0);
+    the evolved T is the periodic remainder, with source -u.G.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from math import comb
+from typing import Dict, Iterable, Optional, Sequence
+
+import numpy as np
+
+from .stencils import stencil
+
+CS2 = 1.0 / 3.0
+
+# Central-moment exponents (a, b, c) in {0,1,2}^3 for the D3Q27 moment space.
+MOMENT_EXPONENTS = np.array(list(itertools.product(range(3), repeat=3)),
+                            dtype=np.int64)
+
+
+def raw_moment_matrix(c: np.ndarray) -> np.ndarray:
+    """M[k, i] = c_ix^a c_iy^b c_iz^c for the exponents (a, b, c) of moment k."""
+    E = MOMENT_EXPONENTS
+    M = np.ones((len(E), len(c)))
+    for k, e in enumerate(E):
+        for i, ci in enumerate(c):
+            M[k, i] = float(ci[0] ** e[0] * ci[1] ** e[1] * ci[2] ** e[2])
+    return M
+
+
+def central_moments(pdf: np.ndarray, u: np.ndarray, c: np.ndarray) -> np.ndarray:
+    """kappa_abc = sum_i pdf_i (c_ix-u_x)^a (c_iy-u_y)^b (c_iz-u_z)^c, by definition.
+
+    (Central moments in the sense of the cascaded/central-moment LBM the
+    paper builds on, Sec. 2.2.)  The sum over i runs as one array reduction."""
+    shp = (len(c),) + (1,) * (pdf.ndim - 1)
+    # powers[a][e][i] = (c_ia - u_a)^e, e = 0, 1, 2
+    powers = []
+    for a in range(3):
+        d = c[:, a].astype(float).reshape(shp) - u[a][None]
+        powers.append((np.ones_like(d), d, d * d))
+    out = np.zeros((len(MOMENT_EXPONENTS),) + pdf.shape[1:])
+    for k, e in enumerate(MOMENT_EXPONENTS):
+        out[k] = (pdf * powers[0][e[0]] * powers[1][e[1]] * powers[2][e[2]]).sum(axis=0)
+    return out
+
+
+def _shift_terms():
+    """(k, k', binomial product, exponent difference) for all e' <= e."""
+    E = MOMENT_EXPONENTS
+    out = []
+    for k, e in enumerate(E):
+        for k2, e2 in enumerate(E):
+            if np.all(e2 <= e):
+                b = 1
+                for a in range(3):
+                    b *= comb(int(e[a]), int(e2[a]))
+                out.append((k, k2, float(b), tuple(int(v) for v in (e - e2))))
+    return out
+
+
+_SHIFT_TERMS = _shift_terms()
+
+
+def raw_from_central(kappa: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """Binomial shift back to raw moments:
+    m_e = sum_{e' <= e} prod_a C(e_a, e'_a) u_a^(e_a - e'_a) kappa_e'."""
+    upow = [(np.ones_like(u[a]), u[a], u[a] * u[a]) for a in range(3)]
+    m = np.zeros_like(kappa)
+    for k, k2, b, d in _SHIFT_TERMS:
+        m[k] += b * upow[0][d[0]] * upow[1][d[1]] * upow[2][d[2]] * kappa[k2]
+    return m
+
+
+def central_from_raw(m: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """N(u): raw -> central moments (binomial shift with -u)."""
+    return raw_from_central(m, -u)
+
+
+def eq_scalar(psi, u, S):
+    """h^eq / f^eq of Sec. 2.2 (Eq. for h_i^eq; same form for f^eq, Sec. 2.3):
+    psi w_i [1 + c.u/c_s^2 + (c.u)^2/(2 c_s^4) - u.u/(2 c_s^2)]."""
+    uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2]
+    out = np.empty((S.Q,) + psi.shape)
+    for i in range(S.Q):
+        cu = S.c[i, 0] * u[0] + S.c[i, 1] * u[1] + S.c[i, 2] * u[2]
+        out[i] = S.w[i] * psi * (1.0 + cu / CS2 + cu * cu / (2 * CS2 * CS2) - uu / (2 * CS2))
+    return out
+
+
+def eq_hydro(p, u, S):
+    """Incompressible (velocity-based) g^eq of Sec. 2.2:
+    w_i (p* + [c.u/c_s^2 + (c.u)^2/(2 c_s^4) - u.u/(2 c_s^2)])."""
+    uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2]
+    out = np.empty((S.Q,) + p.shape)
+    for i in range(S.Q):
+        cu = S.c[i, 0] * u[0] + S.c[i, 1] * u[1] + S.c[i, 2] * u[2]
+        out[i] = S.w[i] * (p + cu / CS2 + cu * cu / (2 * CS2 * CS2) - uu / (2 * CS2))
+    return out
+
+
+def guo_source(u, a, S):
+    """Guo source S_i = w_i [(c_i - u)/c_s^2 + (c_i.u) c_i / c_s^4] . a."""
+    out = np.empty((S.Q,) + u.shape[1:])
+    for i in range(S.Q):
+        cu = S.c[i, 0] * u[0] + S.c[i, 1] * u[1] + S.c[i, 2] * u[2]
+        acc = 0.0
+        for k in range(3):
+            acc = acc + ((S.c[i, k] - u[k]) / CS2 + cu * S.c[i, k] / (CS2 * CS2)) * a[k]
+        out[i] = S.w[i] * acc
+    return out
+
+
+def cm_collide(gs, geq, src, u, omega2, omega_high=1.0, omega_all=None):
+    """Central-moment collision of Sec. 2.2 (relaxation of K(u) g):
+    kappa' = kappa - W (kappa - kappa^eq) + (I - W/2) kappa^F,  g' = K(u)^-1 kappa'.
+    W = diag: omega2 (per cell) for second-order moments, omega_high for the
+    others (orders 0 and 1 are conserved up to the force term whatever their
+    rate).  ``omega_all`` forces one rate for every moment (single-rate test)."""
+    S27 = stencil(27)
+    k = central_moments(gs, u, S27.c)
+    keq = central_moments(geq, u, S27.c)
+    kF = central_moments(src, u, S27.c)
+    post = np.empty_like(k)
+    for m, e in enumerate(MOMENT_EXPONENTS):
+        order = int(e.sum())
+        if omega_all is not None:
+            w = omega_all
+        elif order == 2:
+            w = omega2
+        else:
+            w = omega_high
+        post[m] = k[m] - w * (k[m] - keq[m]) + (1.0 - 0.5 * w) * kF[m]
+    raw = raw_from_central(post, u)
+    return np.tensordot(_minv27(), raw, axes=(1, 0))
+
+
+_MINV27 = []
+
+
+def _minv27():
+    """M^-1 of the D3Q27 raw-moment matrix (inverted once)."""
+    if not _MINV27:
+        _MINV27.append(np.linalg.inv(raw_moment_matrix(stencil(27).c)))
+    return _MINV27[0]
+
+
+class OracleLBM:
+    """Literal FP64 implementation on a (nx, ny, nz) box.
+
+    ``origin``/``global_shape`` place the box inside a larger periodic lattice
+    (used to check sampled cells of a large run: the box is then treated as
+    periodic and only cells at least 2 x steps away from its x/y edges are
+    meaningful).  Walls, when enabled, are at the box's z faces.
+    """
+
+    def __init__(self, nx, ny, nz, params, q_phase=15, thermal="D3Q7",
+                 sources: Sequence = (), patches=None, origin=(0, 0, 0),
+                 global_shape=None):
+        if params.rho_L != params.rho_H:
+            raise NotImplementedError("density ratio != 1 (F_p, F_mu) not supported")
+        if params.alpha_L != params.alpha_H:
+            raise NotImplementedError("conductivity ratio != 1 not supported")
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.p = params
+        self.Sh = stencil(q_phase)
+        self.S27 = stencil(27)
+        self.thermal = thermal
+        self.lb_thermal = thermal.startswith("D3Q")
+        self.Sf = stencil(int(thermal[3:])) if self.lb_thermal else None
+        self.walls = bool(params.walls_z)
+        self.NX, self.NY, self.NZ = global_shape if global_shape else (nx, ny, nz)
+        ox, oy, oz = origin
+        Z, Y, X = np.meshgrid(np.arange(nz, dtype=float) + oz,
+                              np.arange(ny, dtype=float) + oy,
+                              np.arange(nx, dtype=float) + ox, indexing="ij")
+        self.X, self.Y, self.Z = X, Y, Z
+        self.q = self._heat_source(sources, patches)
+        self.time = 0
+        self.h = self.g = self.f = self.T = None
+
+    # ------------------------------------------------------------ inputs
+    def _heat_source(self, sources, patches):
+        """Eq. HeatSource summed over the sources (+ heater patches)."""
+        q = np.zeros((self.nz, self.ny, self.nx))
+        for s in sources:
+            r2 = (self.X - s.x) ** 2 + (self.Y - s.y) ** 2 + (self.Z - s.z) ** 2
+            val = s.Q * np.exp(-2.0 * r2 / (s.w * s.w))
+            if math.isfinite(s.d):
+                val = np.where(r2 <= s.d * s.d, val, 0.0)
+            q = q + val
+        if patches is not None:
+            for k, I in enumerate(patches.intensity):
+                m = ((self.Z == patches.z)
+                     & (self.X >= patches.x0[k]) & (self.X < patches.x0[k] + patches.sx)
+                     & (self.Y >= patches.y0[k]) & (self.Y < patches.y0[k] + patches.sy))
+                q = q + np.where(m, I, 0.0)
+        return q
+
+    def init_droplets(self, droplets: Iterable):
+        """Initial state: phi = max_k tanh profiles (Sec. 3.1 initial profile,
+        phi0 + (phiH - phiL)/2 tanh(r/(xi/2))), u = sum_k phi_k v_k,
+        h = h^eq(phi, u), g = g^eq(0, u), f = f^eq(T0, u); T0 is the conduction
+        profile between the walls, else 0."""
+        p = self.p
+        phi = np.zeros((self.nz, self.ny, self.nx))
+        u = np.zeros((3, self.nz, self.ny, self.nx))
+        for d in droplets:
+            dx = self.X - d.cx
+            dx = dx - self.NX * np.round(dx / self.NX)
+            dy = self.Y - d.cy
+            dy = dy - self.NY * np.round(dy / self.NY)
+            dz = self.Z - d.cz
+            if not self.walls:
+                dz = dz - self.NZ * np.round(dz / self.NZ)
+            r = np.sqrt(dx * dx + dy * dy + dz * dz)
+            pk = 0.5 * (1.0 + np.tanh(2.0 * (d.R - r) / p.xi))
+            phi = np.maximum(phi, pk)
+            u[0] += pk * d.ux
+            u[1] += pk * d.uy
+            u[2] += pk * d.uz
+        if self.walls:
+            T0 = p.T_bottom + (p.T_top - p.T_bottom) * (self.Z + 0.5) / self.NZ
+        else:
+            T0 = np.zeros_like(phi)
+        self.h = eq_scalar(phi, u, self.Sh)
+        self.g = eq_hydro(np.zeros_like(phi), u, self.S27)
+        if self.lb_thermal:
+            self.f = eq_scalar(T0, u, self.Sf)
+        else:
+            self.T = T0.copy()
+        self.time = 0
+
+    # ------------------------------------------------------------ a1 stream
+    def _pull(self, pdf, S, rule=None, Tb=0.0, Tt=0.0):
+        """Pull streaming p*_i(x) = p_i(x - c_i) (periodic by np.roll); at z
+        walls the half-way bounce-back p*_i = p_opp(i) (rule None) or the
+        anti-bounce-back p*_i = -p_opp(i) + 2 w_i T_w (rule 'abb')."""
+        out = np.empty_like(pdf)
+        for i in range(S.Q):
+            cx, cy, cz = (int(v) for v in S.c[i])
+            out[i] = np.roll(pdf[i], shift=(cz, cy, cx), axis=(0, 1, 2))
+            if self.walls and cz != 0:
+                zl = 0 if cz == 1 else -1
+                Tw = Tb if cz == 1 else Tt
+                back = pdf[S.opp[i]][zl]
+                if rule == "abb":
+                    out[i][zl] = -back + 2.0 * S.w[i] * Tw
+                else:
+                    out[i][zl] = back
+        return out
+
+    # ------------------------------------------------------------ a3 stencils
+    def _pad(self, psi, kind):
+        """One ghost layer: periodic wrap in x, y (and z without walls); at
+        walls a mirror (phi) or the Dirichlet ghost 2 T_w - T (T)."""
+        q = np.pad(psi, 1, mode="wrap")
+        if self.walls:
+            if kind == "mirror":
+                q[0] = q[1]
+                q[-1] = q[-2]
+            else:
+                q[0] = 2.0 * self.p.T_bottom - q[1]
+                q[-1] = 2.0 * self.p.T_top - q[-2]
+        return q
+
+    def _at(self, q, c):
+        """Value of a padded field at x + c for every interior x."""
+        cx, cy, cz = (int(v) for v in c)
+        return q[1 + cz:1 + cz + self.nz, 1 + cy:1 + cy + self.ny, 1 + cx:1 + cx + self.nx]
+
+    def grad_iso(self, q):
+        """Isotropic gradient (1/c_s^2) sum_i w_i c_i psi(x + c_i), D3Q27."""
+        S = self.S27
+        gx = np.zeros((self.nz, self.ny, self.nx))
+        gy = np.zeros_like(gx)
+        gz = np.zeros_like(gx)
+        for i in range(S.Q):
+            v = self._at(q, S.c[i])
+            gx = gx + S.w[i] * S.c[i, 0] * v
+            gy = gy + S.w[i] * S.c[i, 1] * v
+            gz = gz + S.w[i] * S.c[i, 2] * v
+        return np.stack([gx, gy, gz]) / CS2
+
+    def lap_iso(self, q):
+        """Isotropic Laplacian (2/c_s^2) sum_i w_i [psi(x + c_i) - psi(x)], D3Q27."""
+        S = self.S27
+        centre = self._at(q, (0, 0, 0))
+        acc = np.zeros_like(centre)
+        for i in range(S.Q):
+            acc = acc + S.w[i] * (self._at(q, S.c[i]) - centre)
+        return 2.0 * acc / CS2
+
+    def grad_std(self, q):
+        """Second-order central difference (psi(x+e) - psi(x-e)) / 2."""
+        out = []
+        for a in range(3):
+            e = [0, 0, 0]
+            e[a] = 1
+            m = [0, 0, 0]
+            m[a] = -1
+            out.append(0.5 * (self._at(q, e) - self._at(q, m)))
+        return np.stack(out)
+
+    def lap_std(self, q):
+        """7-point Laplacian sum_faces psi(x + e) - 6 psi(x)."""
+        centre = self._at(q, (0, 0, 0))
+        acc = np.zeros_like(centre)
+        for e in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+            acc = acc + self._at(q, e)
+        return acc - 6.0 * centre
+
+    # ------------------------------------------------------------ a2-a6
+    def _background(self):
+        G = self.p.grad_T
+        o = self.p.grad_T_origin
+        return G[0] * (self.X - o[0]) + G[1] * (self.Y - o[1]) + G[2] * (self.Z - o[2])
+
+    def _macro_from_pulled(self, hs, gs, fs):
+        p = self.p
+        phi = hs.sum(axis=0)                       # Eq. zeroth_moment_phase
+        pstar = gs.sum(axis=0)                     # Eq. zeroth_moment_hydro
+        T = fs.sum(axis=0) if self.lb_thermal else self.T   # Eq. zeroth_moment_thermal
+        qphi = self._pad(phi, "mirror")
+        qT = self._pad(T, "dirichlet")
+        gphi = self.grad_iso(qphi)
+        lphi = self.lap_iso(qphi)
+        G = np.array(p.grad_T).reshape(3, 1, 1, 1)
+        gT = self.grad_iso(qT) + G
+        Ttot = T + self._background()
+        sigma = p.sigma_ref + p.sigma_T * (Ttot - p.T_ref)          # Eq. sigma(T)
+        beta = 12.0 * sigma / p.xi
+        kap = 1.5 * sigma * p.xi
+        mu = 4.0 * beta * phi * (phi - 1.0) * (phi - 0.5) - kap * lphi
+        g2 = gphi[0] ** 2 + gphi[1] ** 2 + gphi[2] ** 2
+        gTgphi = gT[0] * gphi[0] + gT[1] * gphi[1] + gT[2] * gphi[2]
+        Fs = mu * gphi + 1.5 * p.xi * p.sigma_T * (g2 * gT - gTgphi * gphi)  # Eq. F_s
+        rho = p.rho_L + phi * (p.rho_H - p.rho_L)
+        Fb = rho * np.array(p.gravity).reshape(3, 1, 1, 1)
+        F = Fs + Fb
+        a = F / rho
+        jg = np.einsum("iq,i...->q...", self.S27.c.astype(float), gs)
+        u = jg + 0.5 * a
+        return dict(phi=phi, p=pstar, T=T, u=u, a=a, F=F, rho=rho, gphi=gphi,
+                    lphi=lphi, gT=gT, g2=g2)
+
+    # ------------------------------------------------------------ RK (a9')
+    def rk_rhs(self, psi, u):
+        """R(T) = -u.grad T - u.G + alpha lap T + q_T (Eq. temperature with
+        uniform kappa, rho c_p; standard 7-point / central operators)."""
+        p = self.p
+        q = self._pad(psi, "dirichlet")
+        if p.rk_isotropic_fd:
+            gr, lp = self.grad_iso(q), self.lap_iso(q)
+        else:
+            gr, lp = self.grad_std(q), self.lap_std(q)
+        G = p.grad_T
+        adv = u[0] * (gr[0] + G[0]) + u[1] * (gr[1] + G[1]) + u[2] * (gr[2] + G[2])
+        return -adv + p.alpha_L * lp + self.q
+
+    # ------------------------------------------------------------ step
+    def macro(self):
+        """Macroscopic fields of the current time level (what the next step
+        computes from its pulled PDFs), without advancing."""
+        hs = self._pull(self.h, self.Sh)
+        gs = self._pull(self.g, self.S27)
+        fs = (self._pull(self.f, self.Sf, "abb", self.p.T_bottom, self.p.T_top)
+              if self.lb_thermal else None)
+        return self._macro_from_pulled(hs, gs, fs)
+
+    def step(self, n: int = 1):
+        for _ in range(n):
+            self._step1()
+
+    def _step1(self):
+        p = self.p
+        hs = self._pull(self.h, self.Sh)
+        gs = self._pull(self.g, self.S27)
+        fs = (self._pull(self.f, self.Sf, "abb", p.T_bottom, p.T_top)
+              if self.lb_thermal else None)
+        m = self._macro_from_pulled(hs, gs, fs)
+        phi, u, a = m["phi"], m["u"], m["a"]
+
+        # a7: phase field, Eq. lb_interface with Eq. phasefieldforce as Guo source
+        w_phi = 1.0 / (0.5 + p.mobility / CS2)
+        gphi = m["gphi"]
+        nrm = np.sqrt(m["g2"]) + p.eps_n
+        Fphi = 4.0 * phi * (1.0 - phi) / p.xi * gphi / nrm
+        heq = eq_scalar(phi, u, self.Sh)
+        h_new = np.empty_like(hs)
+        for i in range(self.Sh.Q):
+            cF = self.Sh.c[i, 0] * Fphi[0] + self.Sh.c[i, 1] * Fphi[1] + self.Sh.c[i, 2] * Fphi[2]
+            h_new[i] = hs[i] - w_phi * (hs[i] - heq[i]) + (1.0 - 0.5 * w_phi) * self.Sh.w[i] * cF
+
+        # a8: hydrodynamics, central-moment collision with tau(phi)
+        tau_L = p.nu_L / CS2 + 0.5
+        tau_H = p.nu_H / CS2 + 0.5
+        tau = tau_L + phi * (tau_H - tau_L)
+        geq = eq_hydro(m["p"], u, self.S27)
+        src = guo_source(u, a, self.S27)
+        g_new = cm_collide(gs, geq, src, u, 1.0 / tau, p.omega_high)
+
+        # a9 / a9': temperature
+        G = p.grad_T
+        uG = u[0] * G[0] + u[1] * G[1] + u[2] * G[2]
+        if self.lb_thermal:
+            w_T = 1.0 / (0.5 + p.alpha_L / CS2)
+            feq = eq_scalar(m["T"], u, self.Sf)
+            f_new = np.empty_like(fs)
+            for i in range(self.Sf.Q):
+                f_new[i] = fs[i] - w_T * (fs[i] - feq[i]) + self.Sf.w[i] * (self.q - uG)
+            self.f = f_new
+        else:
+            T = self.T
+            if self.thermal == "RK2":
+                K1 = self.rk_rhs(T, u)
+                self.T = T + self.rk_rhs(T + 0.5 * K1, u)
+            else:
+                K1 = self.rk_rhs(T, u)
+                K2 = self.rk_rhs(T + 0.5 * K1, u)
+                K3 = self.rk_rhs(T + 0.5 * K2, u)
+                K4 = self.rk_rhs(T + K3, u)
+                self.T = T + K1 / 6.0 + K2 / 3.0 + K3 / 3.0 + K4 / 6.0
+        self.h, self.g = h_new, g_new
+        self.time += 1
+        return m
+
+    # ------------------------------------------------------------ a10
+    def diagnostics(self) -> Dict[str, float]:
+        """phi mass, sum T, kinetic energy 1/2 sum rho |u|^2, phi-weighted
+        first moments and the centroid sum(phi x)/sum(phi) of the current level."""
+        m = self.macro()
+        phi, u, rho, T = m["phi"], m["u"], m["rho"], m["T"]
+        mass = float(phi.sum())
+        out = dict(mass=mass, heat=float(T.sum()),
+                   kinetic=float(0.5 * (rho * (u[0] ** 2 + u[1] ** 2 + u[2] ** 2)).sum()),
+                   mx=float((phi * self.X).sum()), my=float((phi * self.Y).sum()),
+                   mz=float((phi * self.Z).sum()))
+        out["centroid"] = (out["mx"] / mass, out["my"] / mass, out["mz"] / mass) if mass else (0, 0, 0)
+        return out
+
+    def state(self):
+        s = dict(h=self.h.copy(), g=self.g.copy())
+        if self.lb_thermal:
+            s["f"] = self.f.copy()
+        else:
+            s["T"] = self.T.copy()
+        return s
+
+
+def build(workload, origin=(0, 0, 0), shape=None) -> OracleLBM:
+    """Oracle instance for a ``workloads.Workload`` (optionally a sub-box)."""
+    nx, ny, nz = shape if shape else (workload.nx, workload.ny, workload.nz)
+    o = OracleLBM(nx, ny, nz, workload.params, workload.q_phase, workload.thermal,
+                  workload.sources, workload.patches, origin=origin,
+                  global_shape=(workload.nx, workload.ny, workload.nz))
+    o.init_droplets(workload.droplets)
+    return o

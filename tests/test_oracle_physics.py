@@ -1,0 +1,366 @@
+"""Physics pins of the FP64 oracle: what the paper's model must reproduce
+whatever the implementation (closed forms, conservation laws, stationary
+solutions, exact discrete amplification factors).  Small boxes only, so the
+whole file runs in about a minute."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import model as om
+from oracle.model import OracleLBM
+
+
+def make(nx, ny, nz, thermal="D3Q7", q_phase=15, **kw):
+    p = W.Params(**kw)
+    return OracleLBM(nx, ny, nz, p, q_phase, thermal)
+
+
+def set_fields(o, phi, u=None, T=None, p=None):
+    """Equilibrium state for given fields (the oracle's own init formulas)."""
+    shape = (o.nz, o.ny, o.nx)
+    phi = np.broadcast_to(phi, shape).astype(float)
+    u = np.zeros((3,) + shape) if u is None else np.broadcast_to(u, (3,) + shape).astype(float)
+    T = np.zeros(shape) if T is None else np.broadcast_to(T, shape).astype(float)
+    p = np.zeros(shape) if p is None else p
+    o.h = om.eq_scalar(phi, u, o.Sh)
+    o.g = om.eq_hydro(p, u, o.S27)
+    if o.lb_thermal:
+        o.f = om.eq_scalar(T, u, o.Sf)
+    else:
+        o.T = T.copy()
+
+
+# ------------------------------------------------------------ streaming
+@pytest.mark.parametrize("walls", [False, True])
+def test_pull_moves_populations_along_c(walls):
+    o = make(4, 5, 6, walls_z=walls)
+    S = o.S27
+    src = np.zeros((27, 6, 5, 4))
+    x0 = (2, 1, 3)  # (z, y, x)
+    for i in range(27):
+        src[i][x0] = i + 1.0
+    out = o._pull(src, S)
+    for i in range(27):
+        cx, cy, cz = S.c[i]
+        z = x0[0] + cz
+        dest = (z % 6, (x0[1] + cy) % 5, (x0[2] + cx) % 4)
+        assert out[i][dest] == i + 1.0
+    # bounce-back: population leaving z = 0 downward returns reversed in place
+    if walls:
+        src = np.zeros((27, 6, 5, 4))
+        down = [i for i in range(27) if S.c[i, 2] == -1]
+        for i in down:
+            src[i][0, 2, 1] = 10.0 + i
+        out = o._pull(src, S)
+        for i in down:
+            assert out[S.opp[i]][0, 2, 1] == 10.0 + i
+        fo = o._pull(src, S, "abb", 0.25, 0.0)
+        for i in down:
+            j = S.opp[i]
+            assert fo[j][0, 2, 1] == -(10.0 + i) + 2 * S.w[j] * 0.25
+
+
+# ------------------------------------------------------------ conservation
+@pytest.mark.parametrize("walls", [False, True])
+def test_phi_mass_conserved(walls):
+    w = W.config1()
+    p = W.Params(**{**w.params.__dict__, "walls_z": walls, "T_bottom": -0.1, "T_top": 0.2})
+    o = OracleLBM(16, 16, 16, p, 15, "D3Q7")
+    o.init_droplets([W.Droplet(8.0, 7.5, 8.2, 5.0, 1e-3, -2e-3, 1e-3)])
+    m0 = o.macro()["phi"].sum()
+    o.step(30)
+    m1 = o.macro()["phi"].sum()
+    assert abs(m1 - m0) / m0 < 1e-13
+
+
+def test_uniform_body_force_momentum_growth():
+    """Guo forcing: with a uniform force the level-n velocity is (n + 1/2) a
+    and the total first moment grows by a per cell per step."""
+    g = (1e-5, -2e-5, 3e-5)
+    o = make(4, 4, 4, gravity=g)
+    set_fields(o, 0.0)
+    for n in range(1, 6):
+        o.step(1)
+        u = o.macro()["u"]
+        for a in range(3):
+            assert np.abs(u[a] - (n + 0.5) * g[a]).max() < 1e-18
+        j = np.einsum("iq,i...->q...", o.S27.c.astype(float), o.g)
+        for a in range(3):
+            assert abs(j[a].sum() - n * g[a] * 64) < 1e-16
+
+
+@pytest.mark.parametrize("thermal", ["D3Q7", "D3Q19", "RK2", "RK4"])
+def test_uniform_heat_source(thermal):
+    o = make(4, 3, 5, thermal=thermal)
+    set_fields(o, 0.0, T=0.0)
+    o.q = np.full((5, 3, 4), 2.5e-3)
+    o.step(4)
+    T = o.macro()["T"]
+    assert np.abs(T - 4 * 2.5e-3).max() < 1e-17
+
+
+# ------------------------------------------------------------ transport coefficients
+def _amp(field, coord, k):
+    return 2.0 * np.mean(field * np.sin(k * coord))
+
+
+def test_shear_wave_viscosity():
+    """u_x = U sin(k z) decays as exp(-nu k^2 t), nu = c_s^2 (tau - 1/2)."""
+    nu = 0.1
+    o = make(1, 1, 32, nu_L=nu, nu_H=nu)
+    k = 2 * math.pi / 32
+    z = o.Z
+    u = np.zeros((3, 32, 1, 1))
+    u[0] = 1e-4 * np.sin(k * z)
+    set_fields(o, 0.0, u=u)
+    o.step(20)
+    a0 = _amp(o.macro()["u"][0], z, k)
+    o.step(100)
+    a1 = _amp(o.macro()["u"][0], z, k)
+    rate = -math.log(a1 / a0) / 100
+    assert abs(rate / (nu * k * k) - 1) < 0.01
+
+
+@pytest.mark.parametrize("thermal", ["D3Q7", "D3Q15", "D3Q19", "D3Q27"])
+def test_lb_heat_diffusion_rate(thermal):
+    alpha = 0.05
+    o = make(32, 1, 1, thermal=thermal, alpha_L=alpha, alpha_H=alpha)
+    k = 2 * math.pi / 32
+    x = o.X
+    set_fields(o, 0.0, T=1e-2 * np.sin(k * x))
+    o.step(10)
+    a0 = _amp(o.macro()["T"], x, k)
+    o.step(200)
+    a1 = _amp(o.macro()["T"], x, k)
+    rate = -math.log(a1 / a0) / 200
+    assert abs(rate / (alpha * k * k) - 1) < 0.01
+
+
+@pytest.mark.parametrize("scheme", ["RK2", "RK4"])
+def test_rk_amplification_exact(scheme):
+    """RK on the 7-point Laplacian: T^{n+1} = P(z) T^n with z = alpha(2cos k - 2),
+    P = 1 + z + z^2/2 (RK2, midpoint) or the quartic Taylor polynomial (RK4)."""
+    alpha = 0.1
+    o = make(16, 1, 1, thermal=scheme, alpha_L=alpha, alpha_H=alpha)
+    k = 2 * math.pi * 3 / 16
+    T0 = 0.3 * np.sin(k * o.X)
+    set_fields(o, 0.0, T=T0)
+    z = alpha * (2 * math.cos(k) - 2)
+    P = 1 + z + z * z / 2 + ((z ** 3 / 6 + z ** 4 / 24) if scheme == "RK4" else 0)
+    o.step(5)
+    assert np.abs(o.T - P ** 5 * T0).max() < 1e-15
+
+
+@pytest.mark.parametrize("thermal", ["D3Q7", "D3Q27", "RK2", "RK4"])
+def test_wall_conduction_linear_profile_exact(thermal):
+    """Between walls at T_b, T_t the conduction profile is linear in the
+    wall-normal coordinate with the walls half a cell outside the first and
+    last cell; anti-bounce-back (LB) and the ghost 2T_w - T (RK) keep it exactly."""
+    o = make(2, 2, 12, thermal=thermal, walls_z=True, T_bottom=-0.5, T_top=0.5)
+    o.init_droplets([])
+    T_lin = -0.5 + (o.Z + 0.5) / 12.0
+    o.step(40)
+    assert np.abs(o.macro()["T"] - T_lin).max() < 1e-14
+
+
+# ------------------------------------------------------------ interface
+def _slab(z, z1, z2, xi):
+    return 0.5 * (np.tanh(2 * (z - z1) / xi) - np.tanh(2 * (z - z2) / xi))
+
+
+def test_tanh_profile_is_stationary():
+    """phi = 1/2 (1 + tanh(2 x / xi)) solves the conservative Allen-Cahn
+    equation at rest; a wrong source scale changes the width by a factor 3.
+    On the lattice the stationary profile differs from the continuous tanh by
+    O(1/xi^2) (width +0.9%, 4e-3 at xi = 5); it must be stationary."""
+    from scipy.optimize import curve_fit
+    xi = 5.0
+    o = make(1, 1, 64, xi=xi, sigma_T=0.0, mobility=0.02)
+    z = o.Z
+    phi0 = _slab(z, 16.0, 48.0, xi)
+    set_fields(o, phi0)
+    o.step(1000)
+    phi_a = o.macro()["phi"]
+    o.step(1000)
+    phi = o.macro()["phi"]
+    assert np.abs(phi - phi_a).max() < 2e-4
+    assert np.abs(phi - phi0).max() < 5e-3
+    zz = z[:, 0, 0]
+    popt, _ = curve_fit(lambda zz, a, b, w: _slab(zz, a, b, w), zz, phi[:, 0, 0],
+                        p0=(15.0, 47.0, 4.0))
+    assert abs(popt[2] / xi - 1) < 0.02
+    assert abs(popt[0] - 16.0) < 0.05 and abs(popt[1] - 48.0) < 0.05
+
+
+def test_planar_interface_advected_with_flow():
+    """A uniform velocity carries a planar interface: after N steps the
+    profile is the initial one shifted by U N (Galilean invariance of the
+    phase-field equation, Eq. phasefield)."""
+    from scipy.optimize import curve_fit
+    xi, U = 5.0, 0.02
+    o = make(1, 1, 64, xi=xi, sigma_T=0.0)
+    z = o.Z
+    u = np.zeros((3, 64, 1, 1))
+    u[2] = U
+    set_fields(o, _slab(z, 16.0, 40.0, xi), u=u)
+    o.step(300)
+    phi = o.macro()["phi"][:, 0, 0]
+    popt, _ = curve_fit(lambda zz, a, b: _slab(zz, a, b, xi), z[:, 0, 0], phi, p0=(20.0, 44.0))
+    shift = U * 300.5   # the level-300 fields follow 300 collisions + 1 streaming
+    assert abs(popt[0] - 16.0 - shift) < 0.1 and abs(popt[1] - 40.0 - shift) < 0.1
+
+
+def test_laplace_pressure_cylinder():
+    """Static cylinder: Delta p = sigma / R (Young-Laplace in 2D), with
+    p = rho c_s^2 p* (p* the zeroth moment of g, Sec. 2.2)."""
+    R, sigma, xi = 8.0, 5e-3, 5.0
+    o = make(32, 32, 1, sigma_ref=sigma, sigma_T=0.0, xi=xi, nu_L=0.1, nu_H=0.1,
+             mobility=0.02)
+    r = np.sqrt((o.X - 16.0) ** 2 + (o.Y - 16.0) ** 2)
+    set_fields(o, 0.5 * (1 + np.tanh(2 * (R - r) / xi)))
+    o.step(1000)
+    m = o.macro()
+    pin = m["p"][r < 3].mean()
+    pout = m["p"][r > 14].mean()
+    dp = (pin - pout) / 3.0
+    assert abs(dp / (sigma / R) - 1) < 0.05
+
+
+def test_marangoni_shear_between_walls():
+    """Planar interface between no-slip walls under a tangential gradient G.
+    The Marangoni part of Eq. F_s, f_x = (3/2) xi sigma_T |d phi/dz|^2 G
+    (integral sigma_T G across the interface), drives the steady Stokes flow
+    mu u'' = -f_x with u = 0 on the half-way walls; compare with that exact
+    solution (Green's-function quadrature on the continuous tanh profile)."""
+    H, nu, G, sT, xi = 32, 0.5, 1e-2, -5e-4, 5.0
+    o = make(1, 1, H, nu_L=nu, nu_H=nu, sigma_T=sT, grad_T=(G, 0.0, 0.0),
+             walls_z=True, alpha_L=0.05, alpha_H=0.05, xi=xi)
+    zi = H / 2 - 0.5
+    set_fields(o, 0.5 * (1 + np.tanh(2 * (o.Z - zi) / xi)))
+    o.step(1500)
+    ux = o.macro()["u"][0][:, 0, 0]
+    lo, hi = -0.5, H - 0.5
+    s = np.linspace(lo, hi, 200001)
+    dphi = (1.0 / xi) / np.cosh(2 * (s - zi) / xi) ** 2
+    f = 1.5 * xi * sT * G * dphi ** 2
+    z = np.arange(H, dtype=float)
+    exact = np.empty(H)
+    for j, zz in enumerate(z):
+        gr = np.where(zz <= s, (zz - lo) * (hi - s), (s - lo) * (hi - zz)) / (hi - lo)
+        exact[j] = np.trapezoid(gr * f, s) / nu
+    ui_sharp = sT * G / (nu * (2.0 / (H / 2)))
+    assert abs(np.trapezoid(f, s) / (sT * G) - 1) < 1e-6
+    # On the lattice the force integral falls short of sigma_T G by O(1/xi^2)
+    # (the central difference underestimates the tanh slope: 0.95 at xi = 5).
+    ratio = o.macro()["F"][0].sum() / (sT * G)
+    assert 0.93 < ratio < 1.0
+    # the flow is the Stokes response to that force
+    assert np.abs(ux - ratio * exact).max() < 0.015 * abs(ui_sharp)
+
+
+def test_centred_droplet_does_not_move():
+    o = make(16, 16, 16, sigma_T=-5e-4, grad_T=(0.0, 0.0, 0.0))
+    # centre between cells so that the lattice is mirror-symmetric about it
+    o.init_droplets([W.Droplet(7.5, 7.5, 7.5, 5.0)])
+    c0 = np.array(o.diagnostics()["centroid"])
+    o.step(40)
+    c1 = np.array(o.diagnostics()["centroid"])
+    assert np.abs(c1 - c0).max() < 1e-12
+
+
+def test_mobility_sets_interface_relaxation_rate():
+    """A tanh profile of width xi' != xi relaxes at the rate given by the
+    conservative Allen-Cahn flux J = M (grad phi - 4 phi (1-phi)/xi n):
+    d phi/dt = M (1/xi' - 1/xi) 4 (1 - 2 phi) phi'  (Eq. phasefield), which
+    fixes the relaxation rate omega_phi = 1/(1/2 + M/c_s^2)."""
+    M, xi, xip = 0.02, 5.0, 10.0
+    o = make(1, 1, 96, xi=xi, mobility=M, sigma_ref=0.0, sigma_T=0.0)
+    z = o.Z[:, 0, 0]
+    set_fields(o, _slab(o.Z, 24.0, 72.0, xip))
+    o.step(10)
+    p0 = o.macro()["phi"][:, 0, 0]
+    o.step(10)
+    p1 = o.macro()["phi"][:, 0, 0]
+    rate = (p1 - p0) / 10.0
+    ph = _slab(z, 24.0, 72.0, xip)           # profile at the midpoint, to O(dt)
+    sgn = np.where(z < 48, 1.0, -1.0)        # n points into the slab
+    dph = sgn * 4 * ph * (1 - ph) / xip
+    want = M * (1 / xip - 1 / xi) * 4 * (1 - 2 * ph) * dph * sgn
+    assert np.abs(rate - want).max() < 0.05 * np.abs(want).max()
+
+
+def test_heat_source_integral_and_cutoff():
+    """Eq. HeatSource: sum over the lattice of Q exp(-2 r^2/w^2) equals the
+    Gaussian integral Q (pi w^2/2)^(3/2) (w = 6 >> 1); with the cut-off
+    r <= d (read: the printed >= would heat everything but the spot) the
+    total is Q (pi w^2/2)^(3/2) [erf(s) - 2 s exp(-s^2)/sqrt(pi)], s = sqrt2 d/w."""
+    from math import erf, exp, pi, sqrt
+    Q, w = 0.2, 6.0
+    o = OracleLBM(48, 48, 48, W.Params(), 15, "D3Q7",
+                  sources=[W.HeatSource(24.0, 24.3, 23.6, Q, w)])
+    full = Q * (pi * w * w / 2) ** 1.5
+    assert abs(o.q.sum() / full - 1) < 1e-9
+    d = 8.0
+    o2 = OracleLBM(48, 48, 48, W.Params(), 15, "D3Q7",
+                   sources=[W.HeatSource(24.0, 24.0, 24.0, Q, w, d)])
+    s = sqrt(2) * d / w
+    cut = full * (erf(s) - 2 * s * exp(-s * s) / sqrt(pi))
+    # lattice sum of a truncated Gaussian: discretisation of the sharp edge
+    assert abs(o2.q.sum() / cut - 1) < 0.01
+    assert o2.q[24, 24, 24] == Q
+
+
+@pytest.mark.parametrize("thermal", ["D3Q7", "RK2", "RK4"])
+def test_background_gradient_advection_source(thermal):
+    """T_total = T + G.(x - x0): a uniform flow U across the imposed gradient
+    changes T at the rate -U.G (Eq. temperature, advection term)."""
+    U, G = 2e-3, 3e-3
+    o = make(4, 4, 4, thermal=thermal, grad_T=(G, 0.0, 0.0))
+    u = np.zeros((3, 4, 4, 4))
+    u[0] = U
+    set_fields(o, 0.0, u=u)
+    o.step(6)
+    T = o.macro()["T"]
+    assert np.abs(T + 6 * U * G).max() < 1e-15
+
+
+@pytest.mark.parametrize("scheme", ["RK2", "RK4"])
+def test_rk_advection_diffusion_amplification(scheme):
+    """Uniform u: the central-difference / 7-point operator has symbol
+    z = -i U sin k + alpha (2 cos k - 2); T^n = Im(P(z)^n e^{ikx}) exactly."""
+    U, alpha = 0.05, 0.08
+    o = make(16, 1, 1, thermal=scheme, alpha_L=alpha, alpha_H=alpha)
+    k = 2 * math.pi * 2 / 16
+    u = np.zeros((3, 1, 1, 16))
+    u[0] = U
+    set_fields(o, 0.0, u=u, T=np.sin(k * o.X))
+    z = -1j * U * math.sin(k) + alpha * (2 * math.cos(k) - 2)
+    P = 1 + z + z * z / 2 + ((z ** 3 / 6 + z ** 4 / 24) if scheme == "RK4" else 0)
+    o.step(4)
+    want = np.imag(P ** 4 * np.exp(1j * k * o.X))
+    assert np.abs(o.T - want).max() < 1e-14
+
+
+def test_wall_ghost_gives_exact_temperature_gradient():
+    o = make(2, 2, 10, walls_z=True, T_bottom=-0.3, T_top=0.7)
+    o.init_droplets([])
+    gT = o.macro()["gT"]
+    assert np.abs(gT[2] - 1.0 / 10).max() < 1e-15
+    assert np.abs(gT[0]).max() < 1e-16 and np.abs(gT[1]).max() < 1e-16
+
+
+def test_initial_droplet_profile_properties():
+    """Initial phi: 1/2 exactly at distance R from the centre, tanh profile
+    (Sec. 3.1 initialisation), periodic minimum-image distances."""
+    p = W.Params()
+    o = OracleLBM(32, 32, 32, p, 15, "D3Q7")
+    o.init_droplets([W.Droplet(16.0, 16.0, 16.0, 8.0), W.Droplet(1.0, 5.0, 16.0, 5.0)])
+    phi = o.h.sum(axis=0)
+    assert abs(phi[16, 16, 24] - 0.5) < 1e-15 and abs(phi[16, 24, 16] - 0.5) < 1e-15
+    assert phi[16, 16, 16] > 0.99
+    # second droplet wraps around x = 0: mirror images about x = 1
+    for d in range(1, 6):
+        assert phi[16, 5, (1 + d) % 32] == phi[16, 5, (1 - d) % 32]
+    assert phi[16, 5, 31] > 0.9
