@@ -1,0 +1,218 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) thermocapillary phase-field lattice
+ * Boltzmann library.
+ *
+ * The method is that of Holzer, Mitchell, Leonardi and Ruede, "Development of
+ * a central-moment phase-field lattice Boltzmann model for thermocapillary
+ * flows" (arXiv 2401.03041):
+ *   - conservative Allen-Cahn phase-field LB for phi            (Sec. 2.2, Eq. lb_interface,
+ *                                                                Eq. phasefieldforce)
+ *   - D3Q27 central-moment hydrodynamic LB, velocity-based      (Sec. 2.2, Eq. for g^eq,
+ *     formulation, surface-tension and Marangoni forcing          Eq. F_s, Eq. sigma(T))
+ *   - energy equation as a D3Q7/15/19/27 passive-scalar LB      (Sec. 2.3, Eq. lb_thermal)
+ *     or as RK2 / RK4 finite differences                        (Sec. 2.3, Eq. rk2, Eq. rk4)
+ *   - pull "one step, two grid" stream-collide, sweep order     (Sec. 4.1, Alg. 1, Alg. 2)
+ *
+ * Conventions for every entry point:
+ *   - Lattice units (dx = dt = 1).  Cell (x, y, z) sits at integer
+ *     coordinates; x and y are periodic; z is periodic or bounded by two
+ *     walls at z = -1/2 and z = nz - 1/2 (lbm_params.walls_z).
+ *   - Field layout: [z][y][x], x fastest; multi-component fields are stored
+ *     component-major ([comp][z][y][x]).  N = nx * ny * nz.
+ *   - The library owns its state (PDF double buffers and auxiliary fields),
+ *     either in a caller-provided device workspace or, if none is given, in
+ *     memory it allocates itself.  The caller owns every other pointer.
+ *   - Work is enqueued asynchronously on the CUDA stream given at creation;
+ *     only calls that return host data (lbm_get_fields to host memory,
+ *     lbm_get_pdfs, lbm_get_diagnostics, lbm_step_diagnostics) synchronise
+ *     that stream.
+ *   - Every call validates its arguments and returns an lbm_status; no call
+ *     aborts the process.  A CUDA error is sticky on its domain: further
+ *     calls on it return LBM_ERR_CUDA.  lbm_last_error() returns a message
+ *     for the calling thread's most recent failure.
+ *   - Not thread-safe per domain: one host thread at a time per domain.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_domain lbm_domain;   /* opaque, library-owned */
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = -1,          /* invalid argument (message in lbm_last_error) */
+  LBM_ERR_CUDA = -2,         /* CUDA runtime error (sticky on the domain)   */
+  LBM_ERR_OOM = -3,          /* device allocation failed / workspace too small */
+  LBM_ERR_STATE = -4,        /* call out of order (e.g. step before init)   */
+  LBM_ERR_NONFINITE = -5,    /* diagnostics found NaN/Inf in the state      */
+  LBM_ERR_TIMEOUT = -6,      /* a bounded wait ran out                      */
+  LBM_ERR_UNSUPPORTED = -7   /* valid request this build does not implement */
+} lbm_status;
+
+/* PDF storage precision.  FP64: stored and computed in double.  FP32: stored
+ * and computed in float.  FP16_STORE: stored in IEEE half, computed in float.
+ * FP32 and FP16 store the shifted values p_i - w_i * s (s = 1/2 for h, 0 for
+ * g, T_ref for f).  Macroscopic reductions are always accumulated in FP64. */
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16_STORE = 2 } lbm_precision;
+
+/* Energy-equation solver (Sec. 2.3). */
+typedef enum {
+  LBM_TH_D3Q7 = 0, LBM_TH_D3Q15 = 1, LBM_TH_D3Q19 = 2, LBM_TH_D3Q27 = 3,
+  LBM_TH_RK2 = 4, LBM_TH_RK4 = 5
+} lbm_thermal;
+
+/* Model parameters (Sec. 2.1-2.3).  lbm_default_params() fills defaults. */
+typedef struct {
+  double nu_L, nu_H;       /* kinematic viscosity of the light (phi=0) / heavy (phi=1) phase;
+                              tau(phi) = tau_L + phi (tau_H - tau_L), tau = nu / c_s^2 + 1/2 */
+  double rho_L, rho_H;     /* densities; this build requires rho_L == rho_H */
+  double mobility;         /* Allen-Cahn mobility M; omega_phi = 1 / (1/2 + M / c_s^2) */
+  double xi;               /* interface width */
+  double sigma_ref, sigma_T, T_ref;  /* sigma(T) = sigma_ref + sigma_T (T - T_ref) */
+  double alpha_L, alpha_H; /* thermal diffusivity kappa / (rho c_p); requires alpha_L == alpha_H;
+                              omega_T = 1 / (1/2 + alpha / c_s^2) */
+  double gravity[3];       /* body-force acceleration g (F_b = rho g) */
+  int32_t walls_z;         /* 1: no-slip walls at both z faces, else periodic in z */
+  double T_bottom, T_top;  /* wall temperatures (walls_z == 1) */
+  double grad_T[3];        /* imposed background gradient G: T_total = T + G.(x - x0) */
+  double grad_T_origin[3]; /* x0 */
+  double eps_n;            /* n = grad phi / (|grad phi| + eps_n) */
+  double omega_high;       /* rate of central moments of order >= 3; this build requires 1 */
+  int32_t rk_isotropic_fd; /* RK solvers: 0 = 7-point Laplacian and central gradient,
+                              1 = isotropic D3Q27 operators */
+} lbm_params;
+
+/* Gaussian laser heat source, Eq. HeatSource: q = Q exp(-2 r^2 / w^2) where
+ * r^2 <= d^2 (d <= 0 or infinite: no cut-off). */
+typedef struct { double x, y, z, Q, w, d; } lbm_heat_source;
+
+/* Spherical droplet for initialisation: phi = 1/2 (1 + tanh(2 (R - r) / xi)),
+ * velocity (ux, uy, uz) weighted by the droplet's own phi. */
+typedef struct { double cx, cy, cz, R, ux, uy, uz; } lbm_droplet;
+
+/* FP64 diagnostics of one time level (Sec. 3.4 centroid tracking). */
+typedef struct {
+  double mass;      /* sum phi */
+  double heat;      /* sum T (the evolved field, without the background G term) */
+  double kinetic;   /* 1/2 sum rho |u|^2 */
+  double mx, my, mz;/* sum phi x, sum phi y, sum phi z (no periodic unwrapping) */
+  int64_t level;    /* time level the values describe */
+  int32_t nonfinite;/* 1 if any summand was NaN/Inf */
+  int32_t pad_;
+} lbm_diag;
+
+#define LBM_FIELD_PHI 1u   /* phi              (1 component)  */
+#define LBM_FIELD_U   2u   /* velocity u       (3 components) */
+#define LBM_FIELD_P   4u   /* normalised pressure p* (1)      */
+#define LBM_FIELD_T   8u   /* temperature T    (1)            */
+
+#define LBM_MAX_SOURCES  64
+#define LBM_MAX_PATCHES  64
+#define LBM_MAX_DROPLETS 4096
+
+/* Fill *p with the defaults (the 32^3 periodic droplet workload's values). */
+void lbm_default_params(lbm_params* p);
+
+/* Device workspace bytes a domain needs (PDF double buffers for h (q_phase),
+ * g (27) and f, RK stage fields, reduction scratch).  0 for invalid input. */
+size_t lbm_workspace_bytes(int nx, int ny, int nz, lbm_precision prec,
+                           lbm_thermal thermal, int q_phase);
+
+/* Create a domain of nx * ny * nz cells (each >= 1; N < 2^40).
+ *   q_phase:   15 (D3Q15) or 27 (D3Q27) for the phase-field PDFs h.
+ *   stream:    a cudaStream_t (NULL = legacy default stream).
+ *   workspace: device pointer of at least lbm_workspace_bytes(...) bytes,
+ *              256-byte aligned, owned by the caller and kept alive until
+ *              lbm_destroy_domain; NULL makes the library allocate it.
+ * Errors: LBM_ERR_ARG (sizes, enums), LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_create_domain(int nx, int ny, int nz, lbm_precision prec,
+                             lbm_thermal thermal, int q_phase, void* stream,
+                             void* workspace, size_t workspace_bytes,
+                             lbm_domain** out);
+
+/* Synchronise the domain's stream and release everything the library owns. */
+lbm_status lbm_destroy_domain(lbm_domain* dom);
+
+/* Set the model parameters (Sec. 2.1-2.3).  Copied; takes effect for the
+ * next launch.  LBM_ERR_ARG for non-physical values (nu <= 0, M <= 0,
+ * xi <= 0, alpha <= 0, non-finite); LBM_ERR_UNSUPPORTED for rho_L != rho_H,
+ * alpha_L != alpha_H or omega_high != 1. */
+lbm_status lbm_set_params(lbm_domain* dom, const lbm_params* p);
+
+/* Replace the Gaussian heat sources (0 <= n <= LBM_MAX_SOURCES; Eq. HeatSource,
+ * read as non-zero inside r <= d).  src is host memory, copied. */
+lbm_status lbm_set_heat_sources(lbm_domain* dom, int n, const lbm_heat_source* src);
+
+/* Replace the rectangular heater patches on layer z (0 <= n <= LBM_MAX_PATCHES):
+ * patch k adds heat source density intensity[k] on the cells
+ * x0[k] <= x < x0[k] + sx, y0[k] <= y < y0[k] + sy of layer z.  Host arrays, copied. */
+lbm_status lbm_set_heater_patches(lbm_domain* dom, int z, int sx, int sy, int n,
+                                  const int32_t* x0, const int32_t* y0,
+                                  const double* intensity);
+
+/* Initialise the state from n droplets (0 <= n <= LBM_MAX_DROPLETS, host
+ * array): phi = max_k phi_k (periodic minimum-image distances), u = sum_k phi_k v_k,
+ * T = linear conduction profile between the walls (walls_z) else 0;
+ * h = h^eq(phi, u), g = g^eq(0, u), f = f^eq(T, u) (Sec. 2.2 equilibria).
+ * These PDFs are treated as the post-collision values of level 0: the first
+ * step streams them.  Resets the level counter to 0. */
+lbm_status lbm_init_droplets(lbm_domain* dom, int n, const lbm_droplet* d);
+
+/* Advance nsteps >= 0 time steps (Alg. 1 / Alg. 2 order: h, g, then f or the
+ * RK stages), asynchronously on the domain's stream. */
+lbm_status lbm_step(lbm_domain* dom, int nsteps);
+
+/* Advance nsteps >= 1 steps and return the FP64 diagnostics of the time level
+ * the last step consumed (accumulated inside that step's kernel, no extra
+ * pass).  Synchronises.  LBM_ERR_NONFINITE if a NaN/Inf was met (the step is
+ * still taken and *out still written). */
+lbm_status lbm_step_diagnostics(lbm_domain* dom, int nsteps, lbm_diag* out);
+
+/* Diagnostics of the current time level (one extra read-only pass).  Synchronises. */
+lbm_status lbm_get_diagnostics(lbm_domain* dom, lbm_diag* out);
+
+/* Macroscopic fields of the current time level (what the next step computes
+ * from its pulled PDFs): the fields selected by mask (LBM_FIELD_*) are written
+ * in the order phi, u (3), p*, T, each N values, as double (dtype 0) or float
+ * (dtype 1).  dst is a device pointer if dst_on_device, else host memory
+ * (then the call synchronises).  dst must hold count * N values. */
+lbm_status lbm_get_fields(lbm_domain* dom, unsigned mask, void* dst,
+                          int dst_on_device, int dtype);
+
+/* Copy one PDF set of the current state to host memory as FP64, un-shifted:
+ * which = 0 (h, q_phase values), 1 (g, 27), 2 (f, thermal Q; LB thermal only)
+ * or 3 (T field, 1 value; RK thermal only).  dst holds Q * N doubles.  Synchronises. */
+lbm_status lbm_get_pdfs(lbm_domain* dom, int which, double* dst_host);
+
+/* Overwrite one PDF set of the current state from FP64 host values (layout as
+ * lbm_get_pdfs; shifted and rounded to the storage precision). */
+lbm_status lbm_set_pdfs(lbm_domain* dom, int which, const double* src_host);
+
+/* Current time level (number of steps since lbm_init_droplets). */
+lbm_status lbm_get_level(lbm_domain* dom, int64_t* level);
+
+/* Wait for the domain's stream with a bounded host-side wait (event polling);
+ * LBM_ERR_TIMEOUT if the work has not finished after timeout_ms. */
+lbm_status lbm_synchronize(lbm_domain* dom, int timeout_ms);
+
+/* Message of the calling thread's most recent failed call ("" if none). */
+const char* lbm_last_error(void);
+
+/* Velocity set of stencil Q (7, 15, 19 or 27) in the library's direction order
+ * (rest; +x,-x,+y,-y,+z,-z; twelve edges; eight corners; App. B classes):
+ * c_out[3*i + a] = component a of c_i, w_out[i] = w_i.  Either pointer may be NULL. */
+lbm_status lbm_stencil(int Q, int32_t* c_out, double* w_out);
+
+/* Library version string. */
+const char* lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,38 @@
+// inst_step.cuh - explicit instantiations of the step-kernel launchers for one
+// storage type LBM_S and one phase-field stencil LBM_QH (set by the including
+// translation unit), for every energy solver (QF = 0: RK; 7/15/19/27: LB).
+#pragma once
+
+#include "launchers.h"
+#include "lbm_aux.cuh"
+
+namespace lbm {
+
+template <class S, int QH, int QF>
+void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A, dim3 grid,
+                 int zchunk, int mode, cudaStream_t st) {
+  step_kernel<S, QH, QF><<<grid, dim3(TX, TY), 0, st>>>(P, A, zchunk, mode);
+}
+
+template <class S, int QH, int QF>
+void launch_init(const DevParams& P, const double* drops, int nd, S* h, S* g, S* f,
+                 typename Store<S>::R* T, cudaStream_t st) {
+  const long long blocks = (P.N + 255) / 256;
+  const int grid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
+  init_kernel<S, QH, QF><<<grid, 256, 0, st>>>(P, drops, nd, h, g, f, T);
+}
+
+#define LBM_INST(QF)                                                                          \
+  template void launch_step<LBM_S, LBM_QH, QF>(const DevParams&,                              \
+                                               const StepPtrs<LBM_S, Store<LBM_S>::R>&, dim3, \
+                                               int, int, cudaStream_t);                       \
+  template void launch_init<LBM_S, LBM_QH, QF>(const DevParams&, const double*, int, LBM_S*,  \
+                                               LBM_S*, LBM_S*, Store<LBM_S>::R*, cudaStream_t);
+LBM_INST(0)
+LBM_INST(7)
+LBM_INST(15)
+LBM_INST(19)
+LBM_INST(27)
+#undef LBM_INST
+
+}  // namespace lbm

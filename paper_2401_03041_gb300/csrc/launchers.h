@@ -1,0 +1,31 @@
+// launchers.h - host-side launch entry points of the device kernels.  The
+// kernel templates are instantiated in the inst_*.cu translation units (one
+// per storage precision) so that they compile in parallel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+template <class S, int QH, int QF>
+void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A, dim3 grid,
+                 int zchunk, int mode, cudaStream_t st);
+
+template <class S, int QH, int QF>
+void launch_init(const DevParams& P, const double* drops, int nd, S* h, S* g, S* f,
+                 typename Store<S>::R* T, cudaStream_t st);
+
+template <class S>
+void launch_rk_stage(const DevParams& P, const typename Store<S>::R* psi, typename Store<S>::R* T,
+                     const typename Store<S>::R* u, typename Store<S>::R* acc,
+                     typename Store<S>::R* out, int kind, cudaStream_t st);
+
+template <class S>
+void launch_pdf_convert(int Q, bool to_f64, void* pdf, double* f64, long long N, double shift,
+                        cudaStream_t st);
+
+void launch_diag_finalize(const double* partials, int nblocks, double* out, cudaStream_t st);
+
+}  // namespace lbm

@@ -1,0 +1,673 @@
+// lbm_api.cu - host implementation of the C ABI declared in include/lbm.h.
+//
+// A domain owns one device workspace holding, 256-byte aligned:
+//   h[2][q_phase][N], g[2][27][N], f[2][Q_f][N]     PDF double buffers (storage type)
+//   T[N], u[3][N], S_a[N], S_b[N], acc[N]           RK thermal fields (compute type)
+//   diagnostics partials [grid][7], result [8]      FP64 reduction scratch
+//   droplet table [LBM_MAX_DROPLETS][7]             FP64 init input
+// Each step reads buffer `cur` and writes `cur ^ 1`, then flips `cur`.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "launchers.h"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+lbm_status fail(lbm_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+int thermal_q(lbm_thermal th) {
+  switch (th) {
+    case LBM_TH_D3Q7: return 7;
+    case LBM_TH_D3Q15: return 15;
+    case LBM_TH_D3Q19: return 19;
+    case LBM_TH_D3Q27: return 27;
+    default: return 0;
+  }
+}
+
+size_t store_bytes(lbm_precision p) { return p == LBM_FP64 ? 8 : (p == LBM_FP32 ? 4 : 2); }
+size_t field_bytes(lbm_precision p) { return p == LBM_FP64 ? 8 : 4; }
+
+struct Layout {
+  size_t h[2], g[2], f[2], T, u, sa, sb, acc, partials, diag, drops, total;
+};
+
+// Launch geometry of the step kernel: TX x TY columns, z split into chunks.
+struct Geometry {
+  dim3 grid;
+  int zchunk;
+  int nblocks;
+};
+
+Geometry geometry(int nx, int ny, int nz) {
+  Geometry g;
+  const int bx = (nx + TX - 1) / TX, by = (ny + TY - 1) / TY;
+  const long long cols = (long long)bx * by;
+  int nchunks = 1;
+  const char* env = std::getenv("LBM_ZCHUNK");
+  int zc = env ? std::atoi(env) : 0;
+  if (zc <= 0) {
+    // aim for about 8 CTAs per SM over the 152 SMs, chunks of >= 8 planes
+    const long long want = 152LL * 8;
+    nchunks = (int)((want + cols - 1) / cols);
+    if (nchunks > nz / 8) nchunks = nz / 8;
+    if (nchunks < 1) nchunks = 1;
+    zc = (nz + nchunks - 1) / nchunks;
+  }
+  nchunks = (nz + zc - 1) / zc;
+  g.grid = dim3(bx, by, nchunks);
+  g.zchunk = zc;
+  g.nblocks = (int)(cols * nchunks);
+  return g;
+}
+
+bool layout(int nx, int ny, int nz, lbm_precision prec, lbm_thermal th, int qh, Layout* L) {
+  if (nx < 1 || ny < 1 || nz < 1) return false;
+  if (qh != 15 && qh != 27) return false;
+  if (prec < LBM_FP64 || prec > LBM_FP16_STORE) return false;
+  if (th < LBM_TH_D3Q7 || th > LBM_TH_RK4) return false;
+  const size_t N = (size_t)nx * ny * nz;
+  if (N >= (size_t(1) << 40)) return false;
+  const size_t sb = store_bytes(prec), fb = field_bytes(prec);
+  const int qf = thermal_q(th);
+  size_t off = 0;
+  for (int k = 0; k < 2; ++k) { L->h[k] = off; off = align256(off + qh * N * sb); }
+  for (int k = 0; k < 2; ++k) { L->g[k] = off; off = align256(off + 27 * N * sb); }
+  for (int k = 0; k < 2; ++k) { L->f[k] = off; off = align256(off + (size_t)qf * N * sb); }
+  const bool rk = qf == 0;
+  const bool rk4 = th == LBM_TH_RK4;
+  L->T = off; off = align256(off + (rk ? N * fb : 0));
+  L->u = off; off = align256(off + (rk ? 3 * N * fb : 0));
+  L->sa = off; off = align256(off + (rk ? N * fb : 0));
+  L->sb = off; off = align256(off + (rk4 ? N * fb : 0));
+  L->acc = off; off = align256(off + (rk4 ? N * fb : 0));
+  // room for the largest grid any z-chunk choice can produce
+  const size_t max_blocks = (size_t)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * nz;
+  L->partials = off; off = align256(off + max_blocks * kDiagVals * 8);
+  L->diag = off; off = align256(off + 8 * 8);
+  L->drops = off; off = align256(off + (size_t)LBM_MAX_DROPLETS * 7 * 8);
+  L->total = off;
+  return true;
+}
+
+}  // namespace
+
+struct lbm_domain {
+  int nx, ny, nz;
+  long long N;
+  lbm_precision prec;
+  lbm_thermal th;
+  int qh, qf;
+  cudaStream_t stream;
+  char* ws;
+  size_t ws_bytes;
+  bool owns_ws;
+  Layout L;
+  Geometry geo;
+  int cur;
+  bool params_set, inited;
+  long long level;
+  lbm_params params;
+  DevParams dp;
+  void* staging;  // device buffer for host-bound field copies (lazy)
+  size_t staging_bytes;
+  lbm_status sticky;
+  std::string sticky_msg;
+};
+
+namespace {
+
+lbm_status check_cuda(lbm_domain* d, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return LBM_OK;
+  const std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+  if (d) {
+    d->sticky = LBM_ERR_CUDA;
+    d->sticky_msg = msg;
+  }
+  return fail(LBM_ERR_CUDA, msg);
+}
+
+lbm_status check_launch(lbm_domain* d, const char* what) {
+  return check_cuda(d, cudaGetLastError(), what);
+}
+
+lbm_status usable(lbm_domain* d) {
+  if (!d) return fail(LBM_ERR_ARG, "null domain");
+  if (d->sticky != LBM_OK) return fail(d->sticky, "domain has a sticky error: " + d->sticky_msg);
+  return LBM_OK;
+}
+
+void* at(lbm_domain* d, size_t off) { return d->ws + off; }
+
+// ----------------------------------------------------------------- dispatch
+template <class S>
+StepPtrs<S, typename Store<S>::R> ptrs(lbm_domain* d) {
+  using R = typename Store<S>::R;
+  StepPtrs<S, R> A{};
+  const int c = d->cur;
+  A.h_src = (const S*)at(d, d->L.h[c]);
+  A.h_dst = (S*)at(d, d->L.h[c ^ 1]);
+  A.g_src = (const S*)at(d, d->L.g[c]);
+  A.g_dst = (S*)at(d, d->L.g[c ^ 1]);
+  A.f_src = (const S*)at(d, d->L.f[c]);
+  A.f_dst = (S*)at(d, d->L.f[c ^ 1]);
+  A.T = (const R*)at(d, d->L.T);
+  A.u_out = (R*)at(d, d->L.u);
+  A.s1_out = (R*)at(d, d->L.sa);
+  A.acc_out = (R*)at(d, d->L.acc);
+  A.rk_acc = d->th == LBM_TH_RK4;
+  A.diag_partials = (double*)at(d, d->L.partials);
+  return A;
+}
+
+template <class S, int QH>
+void step_qf(lbm_domain* d, const StepPtrs<S, typename Store<S>::R>& A, int mode) {
+  switch (d->qf) {
+    case 0: launch_step<S, QH, 0>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
+    case 7: launch_step<S, QH, 7>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
+    case 15: launch_step<S, QH, 15>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
+    case 19: launch_step<S, QH, 19>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
+    default: launch_step<S, QH, 27>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
+  }
+}
+
+template <class S>
+void step_launch(lbm_domain* d, const StepPtrs<S, typename Store<S>::R>& A, int mode) {
+  if (d->qh == 15) step_qf<S, 15>(d, A, mode);
+  else step_qf<S, 27>(d, A, mode);
+}
+
+template <class S>
+void rk_tail(lbm_domain* d) {
+  using R = typename Store<S>::R;
+  R* T = (R*)at(d, d->L.T);
+  R* u = (R*)at(d, d->L.u);
+  R* sa = (R*)at(d, d->L.sa);
+  R* sb = (R*)at(d, d->L.sb);
+  R* acc = (R*)at(d, d->L.acc);
+  if (d->th == LBM_TH_RK2) {
+    launch_rk_stage<S>(d->dp, sa, T, u, nullptr, nullptr, 0, d->stream);
+  } else {
+    launch_rk_stage<S>(d->dp, sa, T, u, acc, sb, 1, d->stream);   // S2 -> sb
+    launch_rk_stage<S>(d->dp, sb, T, u, acc, sa, 2, d->stream);   // S3 -> sa
+    launch_rk_stage<S>(d->dp, sa, T, u, acc, nullptr, 3, d->stream);
+  }
+}
+
+// One step (mode: MODE_COLLIDE [| MODE_DIAG]), or a read-only pass.
+lbm_status run_pass(lbm_domain* d, int mode, void* macro_out = nullptr, int macro_dtype = 0,
+                    unsigned mask = 0) {
+  auto go = [&](auto tag) {
+    using S = decltype(tag);
+    auto A = ptrs<S>(d);
+    A.macro_out = macro_out;
+    A.macro_dtype = macro_dtype;
+    A.macro_mask = mask;
+    step_launch<S>(d, A, mode);
+    if ((mode & MODE_COLLIDE) && d->qf == 0) rk_tail<S>(d);
+  };
+  if (d->prec == LBM_FP64) go(double{});
+  else if (d->prec == LBM_FP32) go(float{});
+  else go(__half{});
+  lbm_status s = check_launch(d, "step kernel launch");
+  if (s != LBM_OK) return s;
+  if (mode & MODE_COLLIDE) {
+    d->cur ^= 1;
+    d->level += 1;
+  }
+  return LBM_OK;
+}
+
+lbm_status finish_diag(lbm_domain* d, long long level, lbm_diag* out) {
+  launch_diag_finalize((const double*)at(d, d->L.partials), d->geo.nblocks,
+                       (double*)at(d, d->L.diag), d->stream);
+  lbm_status s = check_launch(d, "diagnostics reduction");
+  if (s != LBM_OK) return s;
+  double v[kDiagVals];
+  s = check_cuda(d, cudaMemcpyAsync(v, at(d, d->L.diag), sizeof(v), cudaMemcpyDeviceToHost, d->stream),
+                 "diagnostics copy");
+  if (s != LBM_OK) return s;
+  s = check_cuda(d, cudaStreamSynchronize(d->stream), "diagnostics sync");
+  if (s != LBM_OK) return s;
+  out->mass = v[0];
+  out->heat = v[1];
+  out->kinetic = v[2];
+  out->mx = v[3];
+  out->my = v[4];
+  out->mz = v[5];
+  out->level = level;
+  out->nonfinite = v[6] != 0.0 || !std::isfinite(v[0]) || !std::isfinite(v[1]) || !std::isfinite(v[2]);
+  out->pad_ = 0;
+  if (out->nonfinite) return fail(LBM_ERR_NONFINITE, "non-finite value in the state");
+  return LBM_OK;
+}
+
+bool finite_all(const double* v, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+void refresh_devparams(lbm_domain* d) {
+  DevParams& q = d->dp;
+  const lbm_params& p = d->params;
+  const double cs2 = 1.0 / 3.0;
+  q.nx = d->nx; q.ny = d->ny; q.nz = d->nz; q.N = d->N;
+  q.walls = p.walls_z ? 1 : 0;
+  q.omega_phi = 1.0 / (0.5 + p.mobility / cs2);
+  q.omega_T = 1.0 / (0.5 + p.alpha_L / cs2);
+  q.tau_L = p.nu_L / cs2 + 0.5;
+  q.tau_H = p.nu_H / cs2 + 0.5;
+  q.rho_L = p.rho_L; q.rho_H = p.rho_H; q.xi = p.xi;
+  q.sigma_ref = p.sigma_ref; q.sigma_T = p.sigma_T; q.T_ref = p.T_ref; q.alpha = p.alpha_L;
+  for (int k = 0; k < 3; ++k) {
+    q.gravity[k] = p.gravity[k];
+    q.grad[k] = p.grad_T[k];
+    q.origin[k] = p.grad_T_origin[k];
+  }
+  q.T_bottom = p.T_bottom; q.T_top = p.T_top;
+  q.eps_n = p.eps_n;
+  q.shift_h = d->prec == LBM_FP64 ? 0.0 : 0.5;
+  q.shift_f = d->prec == LBM_FP64 ? 0.0 : p.T_ref;
+  q.rk_iso = p.rk_isotropic_fd ? 1 : 0;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+extern "C" {
+
+void lbm_default_params(lbm_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->nu_L = p->nu_H = 0.1;
+  p->rho_L = p->rho_H = 1.0;
+  p->mobility = 0.02;
+  p->xi = 5.0;
+  p->sigma_ref = 5e-3;
+  p->sigma_T = -5e-4;
+  p->T_ref = 0.0;
+  p->alpha_L = p->alpha_H = 0.05;
+  p->eps_n = 1e-12;
+  p->omega_high = 1.0;
+}
+
+size_t lbm_workspace_bytes(int nx, int ny, int nz, lbm_precision prec, lbm_thermal thermal,
+                           int q_phase) {
+  Layout L;
+  if (!layout(nx, ny, nz, prec, thermal, q_phase, &L)) return 0;
+  return L.total;
+}
+
+lbm_status lbm_create_domain(int nx, int ny, int nz, lbm_precision prec, lbm_thermal thermal,
+                             int q_phase, void* stream, void* workspace, size_t workspace_bytes,
+                             lbm_domain** out) {
+  g_last_error.clear();
+  if (!out) return fail(LBM_ERR_ARG, "out is null");
+  *out = nullptr;
+  Layout L;
+  if (!layout(nx, ny, nz, prec, thermal, q_phase, &L))
+    return fail(LBM_ERR_ARG, "invalid lattice size, precision, thermal scheme or q_phase");
+  if (workspace && workspace_bytes < L.total)
+    return fail(LBM_ERR_OOM, "workspace smaller than lbm_workspace_bytes()");
+  if (workspace && ((uintptr_t)workspace & 255))
+    return fail(LBM_ERR_ARG, "workspace must be 256-byte aligned");
+  lbm_domain* d = new (std::nothrow) lbm_domain();
+  if (!d) return fail(LBM_ERR_OOM, "host allocation failed");
+  d->nx = nx; d->ny = ny; d->nz = nz;
+  d->N = (long long)nx * ny * nz;
+  d->prec = prec; d->th = thermal; d->qh = q_phase; d->qf = thermal_q(thermal);
+  d->stream = (cudaStream_t)stream;
+  d->L = L;
+  d->geo = geometry(nx, ny, nz);
+  d->sticky = LBM_OK;
+  lbm_default_params(&d->params);
+  if (workspace) {
+    d->ws = (char*)workspace;
+    d->ws_bytes = workspace_bytes;
+    d->owns_ws = false;
+  } else {
+    void* p = nullptr;
+    const cudaError_t e = cudaMalloc(&p, L.total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete d;
+      return fail(LBM_ERR_OOM, std::string("cudaMalloc of the workspace failed: ") + cudaGetErrorString(e));
+    }
+    d->ws = (char*)p;
+    d->ws_bytes = L.total;
+    d->owns_ws = true;
+  }
+  refresh_devparams(d);
+  *out = d;
+  return LBM_OK;
+}
+
+lbm_status lbm_destroy_domain(lbm_domain* d) {
+  if (!d) return fail(LBM_ERR_ARG, "null domain");
+  cudaStreamSynchronize(d->stream);
+  if (d->owns_ws) cudaFree(d->ws);
+  if (d->staging) cudaFree(d->staging);
+  delete d;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_params(lbm_domain* d, const lbm_params* p) {
+  lbm_status s = usable(d);
+  if (s != LBM_OK) return s;
+  if (!p) return fail(LBM_ERR_ARG, "params is null");
+  const double vals[] = {p->nu_L, p->nu_H, p->rho_L, p->rho_H, p->mobility, p->xi, p->sigma_ref,
+                         p->sigma_T, p->T_ref, p->alpha_L, p->alpha_H, p->gravity[0], p->gravity[1],
+                         p->gravity[2], p->T_bottom, p->T_top, p->grad_T[0], p->grad_T[1],
+                         p->grad_T[2], p->grad_T_origin[0], p->grad_T_origin[1],
+                         p->grad_T_origin[2], p->eps_n, p->omega_high};
+  if (!finite_all(vals, (int)(sizeof(vals) / sizeof(vals[0]))))
+    return fail(LBM_ERR_ARG, "non-finite parameter");
+  if (p->nu_L <= 0 || p->nu_H <= 0) return fail(LBM_ERR_ARG, "viscosity must be > 0");
+  if (p->mobility <= 0) return fail(LBM_ERR_ARG, "mobility must be > 0");
+  if (p->xi <= 0) return fail(LBM_ERR_ARG, "interface width must be > 0");
+  if (p->alpha_L <= 0 || p->alpha_H <= 0) return fail(LBM_ERR_ARG, "diffusivity must be > 0");
+  if (p->rho_L <= 0 || p->rho_H <= 0) return fail(LBM_ERR_ARG, "density must be > 0");
+  if (p->eps_n < 0) return fail(LBM_ERR_ARG, "eps_n must be >= 0");
+  if (p->rho_L != p->rho_H)
+    return fail(LBM_ERR_UNSUPPORTED, "density ratio != 1 (pressure/viscous correction forces) not built");
+  if (p->alpha_L != p->alpha_H)
+    return fail(LBM_ERR_UNSUPPORTED, "conductivity ratio != 1 not built");
+  if (p->omega_high != 1.0)
+    return fail(LBM_ERR_UNSUPPORTED, "higher-order central-moment rate != 1 not built");
+  d->params = *p;
+  d->params_set = true;
+  refresh_devparams(d);
+  return LBM_OK;
+}
+
+lbm_status lbm_set_heat_sources(lbm_domain* d, int n, const lbm_heat_source* src) {
+  lbm_status s = usable(d);
+  if (s != LBM_OK) return s;
+  if (n < 0 || n > LBM_MAX_SOURCES) return fail(LBM_ERR_ARG, "number of heat sources out of range");
+  if (n > 0 && !src) return fail(LBM_ERR_ARG, "sources is null");
+  for (int k = 0; k < n; ++k) {
+    const double v[5] = {src[k].x, src[k].y, src[k].z, src[k].Q, src[k].w};
+    if (!finite_all(v, 5) || src[k].w <= 0) return fail(LBM_ERR_ARG, "invalid heat source");
+    if (std::isnan(src[k].d)) return fail(LBM_ERR_ARG, "invalid heat source cut-off");
+  }
+  d->dp.nsrc = n;
+  for (int k = 0; k < n; ++k) {
+    d->dp.src[k][0] = src[k].x; d->dp.src[k][1] = src[k].y; d->dp.src[k][2] = src[k].z;
+    d->dp.src[k][3] = src[k].Q; d->dp.src[k][4] = src[k].w;
+    d->dp.src[k][5] = (src[k].d > 0 && std::isfinite(src[k].d)) ? src[k].d * src[k].d : -1.0;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_set_heater_patches(lbm_domain* d, int z, int sx, int sy, int n, const int32_t* x0,
+                                  const int32_t* y0, const double* intensity) {
+  lbm_status s = usable(d);
+  if (s != LBM_OK) return s;
+  if (n < 0 || n > LBM_MAX_PATCHES) return fail(LBM_ERR_ARG, "number of patches out of range");
+  if (n > 0 && (!x0 || !y0 || !intensity)) return fail(LBM_ERR_ARG, "patch arrays are null");
+  if (n > 0 && (sx < 1 || sy < 1 || z < 0 || z >= d->nz)) return fail(LBM_ERR_ARG, "invalid patch geometry");
+  if (n > 0 && !finite_all(intensity, n)) return fail(LBM_ERR_ARG, "non-finite patch intensity");
+  d->dp.npatch = n;
+  d->dp.patch_z = z;
+  d->dp.patch_sx = sx;
+  d->dp.patch_sy = sy;
+  for (int k = 0; k < n; ++k) {
+    d->dp.px0[k] = x0[k];
+    d->dp.py0[k] = y0[k];
+    d->dp.pI[k] = intensity[k];
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_init_droplets(lbm_domain* d, int n, const lbm_droplet* drops) {
+  lbm_status s = usable(d);
+  if (s != LBM_OK) return s;
+  if (n < 0 || n > LBM_MAX_DROPLETS) return fail(LBM_ERR_ARG, "number of droplets out of range");
+  if (n > 0 && !drops) return fail(LBM_ERR_ARG, "droplets is null");
+  std::vector<double> tab((size_t)n * 7);
+  for (int k = 0; k < n; ++k) {
+    const double v[7] = {drops[k].cx, drops[k].cy, drops[k].cz, drops[k].R,
+                         drops[k].ux, drops[k].uy, drops[k].uz};
+    if (!finite_all(v, 7) || drops[k].R < 0) return fail(LBM_ERR_ARG, "invalid droplet");
+    std::memcpy(&tab[(size_t)k * 7], v, sizeof(v));
+  }
+  double* dev = (double*)at(d, d->L.drops);
+  if (n > 0) {
+    s = check_cuda(d, cudaMemcpyAsync(dev, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, d->stream),
+                   "droplet upload");
+    if (s != LBM_OK) return s;
+  }
+  d->cur = 0;
+  auto go = [&](auto tag) {
+    using S = decltype(tag);
+    using R = typename Store<S>::R;
+    S* h = (S*)at(d, d->L.h[0]);
+    S* g = (S*)at(d, d->L.g[0]);
+    S* f = (S*)at(d, d->L.f[0]);
+    R* T = (R*)at(d, d->L.T);
+    auto qf = [&](auto qh_tag) {
+      constexpr int QH = decltype(qh_tag)::value;
+      switch (d->qf) {
+        case 0: launch_init<S, QH, 0>(d->dp, dev, n, h, g, f, T, d->stream); break;
+        case 7: launch_init<S, QH, 7>(d->dp, dev, n, h, g, f, T, d->stream); break;
+        case 15: launch_init<S, QH, 15>(d->dp, dev, n, h, g, f, T, d->stream); break;
+        case 19: launch_init<S, QH, 19>(d->dp, dev, n, h, g, f, T, d->stream); break;
+        default: launch_init<S, QH, 27>(d->dp, dev, n, h, g, f, T, d->stream); break;
+      }
+    };
+    if (d->qh == 15) qf(std::integral_constant<int, 15>{});
+    else qf(std::integral_constant<int, 27>{});
+  };
+  if (d->prec == LBM_FP64) go(double{});
+  else if (d->prec == LBM_FP32) go(float{});
+  else go(__half{});
+  s = check_launch(d, "init kernel launch");
+  if (s != LBM_OK) return s;
+  if (n > 0) {
+    // the pageable upload above must complete before `tab` goes out of scope
+    s = check_cuda(d, cudaStreamSynchronize(d->stream), "init sync");
+    if (s != LBM_OK) return s;
+  }
+  d->inited = true;
+  d->level = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_domain* d, int nsteps) {
+  lbm_status s = usable(d);
+  if (s != LBM_OK) return s;
+  if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps must be >= 0");
+  if (!d->inited) return fail(LBM_ERR_STATE, "lbm_init_droplets (or lbm_set_pdfs) has not been called");
+  for (int k = 0; k < nsteps; ++k) {
+    s = run_pass(d, MODE_COLLIDE);
+    if (s != LBM_OK) return s;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_step_diagnostics(lbm_domain* d, int nsteps, lbm_diag* out) {
+  lbm_status s = usable(d);
+  if (s != LBM_OK) return s;
+  if (nsteps < 1 || !out) return fail(LBM_ERR_ARG, "nsteps must be >= 1 and out non-null");
+  if (!d->inited) return fail(LBM_ERR_STATE, "domain not initialised");
+  s = lbm_step(d, nsteps - 1);
+  if (s != LBM_OK) return s;
+  const long long level = d->level;
+  s = run_pass(d, MODE_COLLIDE | MODE_DIAG);
+  if (s != LBM_OK) return s;
+  return finish_diag(d, level, out);
+}
+
+lbm_status lbm_get_diagnostics(lbm_domain* d, lbm_diag* out) {
+  lbm_status s = usable(d);
+  if (s != LBM_OK) return s;
+  if (!out) return fail(LBM_ERR_ARG, "out is null");
+  if (!d->inited) return fail(LBM_ERR_STATE, "domain not initialised");
+  s = run_pass(d, MODE_DIAG);
+  if (s != LBM_OK) return s;
+  return finish_diag(d, d->level, out);
+}
+
+lbm_status lbm_get_fields(lbm_domain* d, unsigned mask, void* dst, int dst_on_device, int dtype) {
+  lbm_status s = usable(d);
+  if (s != LBM_OK) return s;
+  if (!dst) return fail(LBM_ERR_ARG, "dst is null");
+  if (mask == 0 || (mask & ~15u)) return fail(LBM_ERR_ARG, "invalid field mask");
+  if (dtype != 0 && dtype != 1) return fail(LBM_ERR_ARG, "dtype must be 0 (f64) or 1 (f32)");
+  if (!d->inited) return fail(LBM_ERR_STATE, "domain not initialised");
+  const int comps = ((mask & 1u) ? 1 : 0) + ((mask & 2u) ? 3 : 0) + ((mask & 4u) ? 1 : 0) + ((mask & 8u) ? 1 : 0);
+  const size_t bytes = (size_t)comps * d->N * (dtype == 0 ? 8 : 4);
+  void* target = dst;
+  if (!dst_on_device) {
+    if (d->staging_bytes < bytes) {
+      if (d->staging) cudaFree(d->staging);
+      d->staging = nullptr;
+      d->staging_bytes = 0;
+      if (cudaMalloc(&d->staging, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ERR_OOM, "staging allocation failed");
+      }
+      d->staging_bytes = bytes;
+    }
+    target = d->staging;
+  }
+  s = run_pass(d, MODE_MACRO, target, dtype, mask);
+  if (s != LBM_OK) return s;
+  if (!dst_on_device) {
+    s = check_cuda(d, cudaMemcpyAsync(dst, target, bytes, cudaMemcpyDeviceToHost, d->stream), "field copy");
+    if (s != LBM_OK) return s;
+    s = check_cuda(d, cudaStreamSynchronize(d->stream), "field sync");
+  }
+  return s;
+}
+
+static lbm_status pdf_io(lbm_domain* d, int which, double* host, bool to_host) {
+  lbm_status s = usable(d);
+  if (s != LBM_OK) return s;
+  if (!host) return fail(LBM_ERR_ARG, "host buffer is null");
+  if (which < 0 || which > 3) return fail(LBM_ERR_ARG, "which must be 0..3");
+  if (which == 2 && d->qf == 0) return fail(LBM_ERR_ARG, "no thermal PDFs with an RK solver");
+  if (which == 3 && d->qf != 0) return fail(LBM_ERR_ARG, "no T field with an LB thermal solver");
+  int Q = which == 0 ? d->qh : (which == 1 ? 27 : (which == 2 ? d->qf : 1));
+  double shift = which == 0 ? d->dp.shift_h : (which == 2 ? d->dp.shift_f : 0.0);
+  void* buf = which == 0 ? at(d, d->L.h[d->cur])
+            : which == 1 ? at(d, d->L.g[d->cur])
+            : which == 2 ? at(d, d->L.f[d->cur]) : at(d, d->L.T);
+  const size_t bytes = (size_t)Q * d->N * 8;
+  double* tmp = nullptr;
+  s = check_cuda(d, cudaMalloc(&tmp, bytes), "conversion buffer");
+  if (s != LBM_OK) return s;
+  if (which == 3) {
+    // T field is stored in the compute type, not shifted
+    if (to_host) {
+      if (d->prec == LBM_FP64) s = check_cuda(d, cudaMemcpyAsync(tmp, buf, bytes, cudaMemcpyDeviceToDevice, d->stream), "copy");
+      else launch_pdf_convert<float>(1, true, buf, tmp, d->N, 0.0, d->stream);
+    } else {
+      s = check_cuda(d, cudaMemcpyAsync(tmp, host, bytes, cudaMemcpyHostToDevice, d->stream), "upload");
+      if (d->prec == LBM_FP64) s = check_cuda(d, cudaMemcpyAsync(buf, tmp, bytes, cudaMemcpyDeviceToDevice, d->stream), "copy");
+      else launch_pdf_convert<float>(1, false, buf, tmp, d->N, 0.0, d->stream);
+    }
+  } else {
+    auto conv = [&](auto tag, bool dir) {
+      using S = decltype(tag);
+      launch_pdf_convert<S>(Q, dir, buf, tmp, d->N, shift, d->stream);
+    };
+    if (!to_host) s = check_cuda(d, cudaMemcpyAsync(tmp, host, bytes, cudaMemcpyHostToDevice, d->stream), "upload");
+    if (d->prec == LBM_FP64) conv(double{}, to_host);
+    else if (d->prec == LBM_FP32) conv(float{}, to_host);
+    else conv(__half{}, to_host);
+  }
+  if (s == LBM_OK) s = check_launch(d, "conversion kernel");
+  if (s == LBM_OK && to_host)
+    s = check_cuda(d, cudaMemcpyAsync(host, tmp, bytes, cudaMemcpyDeviceToHost, d->stream), "download");
+  if (s == LBM_OK) s = check_cuda(d, cudaStreamSynchronize(d->stream), "conversion sync");
+  cudaFree(tmp);
+  return s;
+}
+
+lbm_status lbm_get_pdfs(lbm_domain* d, int which, double* dst_host) {
+  return pdf_io(d, which, dst_host, true);
+}
+
+lbm_status lbm_set_pdfs(lbm_domain* d, int which, const double* src_host) {
+  lbm_status s = pdf_io(d, which, const_cast<double*>(src_host), false);
+  if (s == LBM_OK) d->inited = true;
+  return s;
+}
+
+lbm_status lbm_get_level(lbm_domain* d, int64_t* level) {
+  if (!d || !level) return fail(LBM_ERR_ARG, "null argument");
+  *level = d->level;
+  return LBM_OK;
+}
+
+lbm_status lbm_synchronize(lbm_domain* d, int timeout_ms) {
+  lbm_status s = usable(d);
+  if (s != LBM_OK) return s;
+  cudaEvent_t ev;
+  s = check_cuda(d, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event create");
+  if (s != LBM_OK) return s;
+  s = check_cuda(d, cudaEventRecord(ev, d->stream), "event record");
+  const auto t0 = std::chrono::steady_clock::now();
+  while (s == LBM_OK) {
+    const cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) {
+      s = check_cuda(d, e, "event query");
+      break;
+    }
+    const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
+                        std::chrono::steady_clock::now() - t0).count();
+    if (timeout_ms >= 0 && ms > timeout_ms) {
+      s = fail(LBM_ERR_TIMEOUT, "stream did not finish within the timeout");
+      break;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(200));
+  }
+  cudaEventDestroy(ev);
+  return s;
+}
+
+lbm_status lbm_stencil(int Q, int32_t* c_out, double* w_out) {
+  if (Q != 7 && Q != 15 && Q != 19 && Q != 27) return fail(LBM_ERR_ARG, "Q must be 7, 15, 19 or 27");
+  for (int i = 0; i < Q; ++i) {
+    int c[3];
+    double w;
+    switch (Q) {
+      case 7: c[0] = cx<7>(i); c[1] = cy<7>(i); c[2] = cz<7>(i); w = weight<7>(i); break;
+      case 15: c[0] = cx<15>(i); c[1] = cy<15>(i); c[2] = cz<15>(i); w = weight<15>(i); break;
+      case 19: c[0] = cx<19>(i); c[1] = cy<19>(i); c[2] = cz<19>(i); w = weight<19>(i); break;
+      default: c[0] = cx<27>(i); c[1] = cy<27>(i); c[2] = cz<27>(i); w = weight<27>(i); break;
+    }
+    if (c_out)
+      for (int a = 0; a < 3; ++a) c_out[3 * i + a] = c[a];
+    if (w_out) w_out[i] = w;
+  }
+  return LBM_OK;
+}
+
+const char* lbm_last_error(void) { return g_last_error.c_str(); }
+
+const char* lbm_version(void) { return "thermocap-lbm-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+// lbm_device.cuh - device-side building blocks of the GB300 thermocapillary
+// phase-field LBM: lattice tables, storage traits, launch parameter structs.
+//
+// Lattices (App. B): velocity classes rest / 6 faces / 12 edges / 8 corners,
+// in the order rest; +x,-x,+y,-y,+z,-z; the twelve edges; the eight corners.
+// D3Q7 = rest + faces (w_0 = 0, w_face = 1/6), D3Q15 = rest + faces + corners,
+// D3Q19 = rest + faces + edges, D3Q27 = all.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// ----------------------------------------------------------------- lattices
+// Direction k of D3Q27 (the superset).  Other stencils index into it.
+__host__ __device__ constexpr int q27_cx(int k) {
+  constexpr int t[27] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0,
+                         1, -1, 1, -1, 1, -1, -1, 1};
+  return t[k];
+}
+__host__ __device__ constexpr int q27_cy(int k) {
+  constexpr int t[27] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1,
+                         1, -1, 1, -1, -1, 1, 1, -1};
+  return t[k];
+}
+__host__ __device__ constexpr int q27_cz(int k) {
+  constexpr int t[27] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1,
+                         1, -1, -1, 1, 1, -1, 1, -1};
+  return t[k];
+}
+
+// Map direction i of stencil Q to its D3Q27 index.
+template <int Q>
+__host__ __device__ constexpr int to27(int i) {
+  return (Q == 15 && i >= 7) ? i + 12 : i;
+}
+template <int Q> __host__ __device__ constexpr int cx(int i) { return q27_cx(to27<Q>(i)); }
+template <int Q> __host__ __device__ constexpr int cy(int i) { return q27_cy(to27<Q>(i)); }
+template <int Q> __host__ __device__ constexpr int cz(int i) { return q27_cz(to27<Q>(i)); }
+
+// Opposite direction: same stencil, negated velocity.
+template <int Q>
+__host__ __device__ constexpr int opp(int i) {
+  int r = 0;
+  for (int j = 0; j < Q; ++j)
+    if (cx<Q>(j) == -cx<Q>(i) && cy<Q>(j) == -cy<Q>(i) && cz<Q>(j) == -cz<Q>(i)) r = j;
+  return r;
+}
+
+// Weights per velocity class, App. B.
+template <int Q>
+__host__ __device__ constexpr double weight(int i) {
+  const int n = (cx<Q>(i) != 0) + (cy<Q>(i) != 0) + (cz<Q>(i) != 0);
+  if (Q == 7) return n == 0 ? 0.0 : 1.0 / 6.0;
+  if (Q == 15) return n == 0 ? 16.0 / 72.0 : (n == 1 ? 8.0 / 72.0 : 1.0 / 72.0);
+  if (Q == 19) return n == 0 ? 12.0 / 36.0 : (n == 1 ? 2.0 / 36.0 : 1.0 / 36.0);
+  return n == 0 ? 64.0 / 216.0 : (n == 1 ? 16.0 / 216.0 : (n == 2 ? 4.0 / 216.0 : 1.0 / 216.0));
+}
+
+// ----------------------------------------------------------------- storage
+template <class S> struct Store;
+template <> struct Store<double> {
+  using R = double;
+  __device__ __forceinline__ static R ld(const double* p) { return __ldg(p); }
+  __device__ __forceinline__ static void st(double* p, R v) { *p = v; }
+};
+template <> struct Store<float> {
+  using R = float;
+  __device__ __forceinline__ static R ld(const float* p) { return __ldg(p); }
+  __device__ __forceinline__ static void st(float* p, R v) { *p = v; }
+};
+template <> struct Store<__half> {
+  using R = float;
+  __device__ __forceinline__ static R ld(const __half* p) { return __half2float(__ldg(p)); }
+  __device__ __forceinline__ static void st(__half* p, R v) { *p = __float2half_rn(v); }
+};
+
+// Step-kernel tile: a CTA of TX x TY threads owns a TX x TY column of cells.
+constexpr int TX = 32;
+constexpr int TY = 8;
+
+// ----------------------------------------------------------------- params
+constexpr int kMaxSources = 64;
+constexpr int kMaxPatches = 64;
+
+// Everything a kernel needs, passed by value (lives in the constant bank).
+struct DevParams {
+  int nx, ny, nz, walls;
+  long long N;
+  double omega_phi, omega_T, tau_L, tau_H;
+  double rho_L, rho_H, xi, sigma_ref, sigma_T, T_ref, alpha;
+  double gravity[3];
+  double T_bottom, T_top;
+  double grad[3], origin[3];
+  double eps_n;
+  double shift_h, shift_f;        // storage shifts (w_i * shift) for h and f
+  int rk_iso;
+  int nsrc;
+  double src[kMaxSources][6];     // x, y, z, Q, w, d^2 (d^2 < 0: no cut-off)
+  int npatch, patch_z, patch_sx, patch_sy;
+  int px0[kMaxPatches], py0[kMaxPatches];
+  double pI[kMaxPatches];
+};
+
+// Kernel modes (bit set).
+enum : int { MODE_COLLIDE = 1, MODE_DIAG = 2, MODE_MACRO = 4 };
+
+constexpr int kDiagVals = 7;  // mass, heat, kinetic, mx, my, mz, nonfinite count
+
+template <class S, class RF>
+struct StepPtrs {
+  const S* h_src; S* h_dst;
+  const S* g_src; S* g_dst;
+  const S* f_src; S* f_dst;
+  // RK thermal fields (RF = double in FP64 mode, float otherwise)
+  const RF* T; RF* u_out; RF* s1_out; RF* acc_out;
+  int rk_acc;                     // RK4: write acc = K1/6
+  // macroscopic output (MODE_MACRO): order phi, u(3), p, T, selected by mask
+  void* macro_out; int macro_dtype; unsigned macro_mask;
+  double* diag_partials;          // [grid blocks][kDiagVals] (MODE_DIAG)
+};
+
+}  // namespace lbm

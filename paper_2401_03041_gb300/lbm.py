@@ -1,0 +1,294 @@
+"""ctypes binding of ``liblbm.so`` (declared in ``include/lbm.h``).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch supplies the device workspace and the CUDA stream.
+If the library is missing the import fails loudly; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Iterable, Optional, Sequence
+
+from . import build as _build
+
+LBM_OK = 0
+STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_OOM",
+          -4: "LBM_ERR_STATE", -5: "LBM_ERR_NONFINITE", -6: "LBM_ERR_TIMEOUT",
+          -7: "LBM_ERR_UNSUPPORTED"}
+PRECISION = {"fp64": 0, "fp32": 1, "fp16": 2}
+THERMAL = {"D3Q7": 0, "D3Q15": 1, "D3Q19": 2, "D3Q27": 3, "RK2": 4, "RK4": 5}
+FIELD_PHI, FIELD_U, FIELD_P, FIELD_T = 1, 2, 4, 8
+
+# Every symbol include/lbm.h declares.
+SYMBOLS = ("lbm_default_params", "lbm_workspace_bytes", "lbm_create_domain",
+           "lbm_destroy_domain", "lbm_set_params", "lbm_set_heat_sources",
+           "lbm_set_heater_patches", "lbm_init_droplets", "lbm_step",
+           "lbm_step_diagnostics", "lbm_get_diagnostics", "lbm_get_fields",
+           "lbm_get_pdfs", "lbm_set_pdfs", "lbm_get_level", "lbm_synchronize",
+           "lbm_stencil", "lbm_last_error", "lbm_version")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nu_L", ctypes.c_double), ("nu_H", ctypes.c_double),
+                ("rho_L", ctypes.c_double), ("rho_H", ctypes.c_double),
+                ("mobility", ctypes.c_double), ("xi", ctypes.c_double),
+                ("sigma_ref", ctypes.c_double), ("sigma_T", ctypes.c_double),
+                ("T_ref", ctypes.c_double), ("alpha_L", ctypes.c_double),
+                ("alpha_H", ctypes.c_double), ("gravity", ctypes.c_double * 3),
+                ("walls_z", ctypes.c_int32), ("T_bottom", ctypes.c_double),
+                ("T_top", ctypes.c_double), ("grad_T", ctypes.c_double * 3),
+                ("grad_T_origin", ctypes.c_double * 3), ("eps_n", ctypes.c_double),
+                ("omega_high", ctypes.c_double), ("rk_isotropic_fd", ctypes.c_int32)]
+
+
+class HeatSource(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("x", "y", "z", "Q", "w", "d")]
+
+
+class Droplet(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("cx", "cy", "cz", "R", "ux", "uy", "uz")]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("heat", ctypes.c_double),
+                ("kinetic", ctypes.c_double), ("mx", ctypes.c_double),
+                ("my", ctypes.c_double), ("mz", ctypes.c_double),
+                ("level", ctypes.c_int64), ("nonfinite", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k in ("mass", "heat", "kinetic", "mx", "my", "mz", "level")}
+        d["nonfinite"] = bool(self.nonfinite)
+        m = self.mass
+        d["centroid"] = (self.mx / m, self.my / m, self.mz / m) if m else (0.0, 0.0, 0.0)
+        return d
+
+
+class LBMError(RuntimeError):
+    def __init__(self, fn, status, msg):
+        super().__init__(f"{fn} -> {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load liblbm.so (built in-tree by ``build.build()``); raise if absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2401_03041_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    c_int, c_dbl, vp, sz = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+    P = ctypes.POINTER
+    sig = {
+        "lbm_default_params": (None, [P(Params)]),
+        "lbm_workspace_bytes": (sz, [c_int, c_int, c_int, c_int, c_int, c_int]),
+        "lbm_create_domain": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int, vp, vp, sz, P(vp)]),
+        "lbm_destroy_domain": (c_int, [vp]),
+        "lbm_set_params": (c_int, [vp, P(Params)]),
+        "lbm_set_heat_sources": (c_int, [vp, c_int, P(HeatSource)]),
+        "lbm_set_heater_patches": (c_int, [vp, c_int, c_int, c_int, c_int, P(ctypes.c_int32),
+                                           P(ctypes.c_int32), P(c_dbl)]),
+        "lbm_init_droplets": (c_int, [vp, c_int, P(Droplet)]),
+        "lbm_step": (c_int, [vp, c_int]),
+        "lbm_step_diagnostics": (c_int, [vp, c_int, P(Diag)]),
+        "lbm_get_diagnostics": (c_int, [vp, P(Diag)]),
+        "lbm_get_fields": (c_int, [vp, ctypes.c_uint, vp, c_int, c_int]),
+        "lbm_get_pdfs": (c_int, [vp, c_int, vp]),
+        "lbm_set_pdfs": (c_int, [vp, c_int, vp]),
+        "lbm_get_level": (c_int, [vp, P(ctypes.c_int64)]),
+        "lbm_synchronize": (c_int, [vp, c_int]),
+        "lbm_stencil": (c_int, [c_int, P(ctypes.c_int32), P(c_dbl)]),
+        "lbm_last_error": (ctypes.c_char_p, []),
+        "lbm_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = L
+    return L
+
+
+def _check(fn: str, status: int):
+    if status != LBM_OK:
+        raise LBMError(fn, status, lib().lbm_last_error().decode())
+
+
+def default_params() -> Params:
+    p = Params()
+    lib().lbm_default_params(ctypes.byref(p))
+    return p
+
+
+def make_params(src=None, **kw) -> Params:
+    """Params from the library defaults, overridden by the attributes of
+    ``src`` (any object with matching attribute names) and by keywords."""
+    p = default_params()
+    items = {}
+    if src is not None:
+        for name, _ in Params._fields_:
+            if hasattr(src, name):
+                items[name] = getattr(src, name)
+    items.update(kw)
+    for name, val in items.items():
+        if name in ("gravity", "grad_T", "grad_T_origin"):
+            getattr(p, name)[:] = [float(v) for v in val]
+        elif name in ("walls_z", "rk_isotropic_fd"):
+            setattr(p, name, int(bool(val)))
+        else:
+            setattr(p, name, float(val))
+    return p
+
+
+def stencil(Q: int):
+    """(c, w) of the library's stencil Q: lists of (cx, cy, cz) and weights."""
+    c = (ctypes.c_int32 * (3 * Q))()
+    w = (ctypes.c_double * Q)()
+    _check("lbm_stencil", lib().lbm_stencil(Q, c, w))
+    return [tuple(c[3 * i:3 * i + 3]) for i in range(Q)], list(w)
+
+
+class Domain:
+    """One lattice on the current CUDA device (see include/lbm.h).
+
+    The device workspace is a torch uint8 tensor; kernels run on ``stream``
+    (default: torch's current stream)."""
+
+    def __init__(self, nx, ny, nz, precision="fp64", thermal="D3Q7", q_phase=15,
+                 stream=None, device=None):
+        import torch
+        L = lib()
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.N = self.nx * self.ny * self.nz
+        self.precision, self.thermal, self.q_phase = precision, thermal, int(q_phase)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        nbytes = L.lbm_workspace_bytes(self.nx, self.ny, self.nz, PRECISION[precision],
+                                       THERMAL[thermal], self.q_phase)
+        if nbytes == 0:
+            raise LBMError("lbm_workspace_bytes", -1, "invalid domain description")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        _check("lbm_create_domain",
+               L.lbm_create_domain(self.nx, self.ny, self.nz, PRECISION[precision],
+                                   THERMAL[thermal], self.q_phase,
+                                   ctypes.c_void_p(self.stream.cuda_stream),
+                                   ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                   ctypes.byref(h)))
+        self._h = h
+
+    # -------------------------------------------------------------- lifecycle
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _check("lbm_destroy_domain", lib().lbm_destroy_domain(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -------------------------------------------------------------- setup
+    def set_params(self, src=None, **kw):
+        p = make_params(src, **kw)
+        _check("lbm_set_params", lib().lbm_set_params(self._h, ctypes.byref(p)))
+
+    def set_heat_sources(self, sources: Sequence):
+        arr = (HeatSource * max(1, len(sources)))()
+        for k, s in enumerate(sources):
+            d = getattr(s, "d", math.inf)
+            arr[k] = HeatSource(s.x, s.y, s.z, s.Q, s.w, -1.0 if not math.isfinite(d) else d)
+        _check("lbm_set_heat_sources", lib().lbm_set_heat_sources(self._h, len(sources), arr))
+
+    def set_heater_patches(self, z, sx, sy, x0, y0, intensity):
+        n = len(intensity)
+        X = (ctypes.c_int32 * max(1, n))(*x0)
+        Y = (ctypes.c_int32 * max(1, n))(*y0)
+        I = (ctypes.c_double * max(1, n))(*[float(v) for v in intensity])
+        _check("lbm_set_heater_patches",
+               lib().lbm_set_heater_patches(self._h, int(z), int(sx), int(sy), n, X, Y, I))
+
+    def init_droplets(self, droplets: Iterable):
+        ds = list(droplets)
+        arr = (Droplet * max(1, len(ds)))()
+        for k, d in enumerate(ds):
+            arr[k] = Droplet(d.cx, d.cy, d.cz, d.R, getattr(d, "ux", 0.0),
+                             getattr(d, "uy", 0.0), getattr(d, "uz", 0.0))
+        _check("lbm_init_droplets", lib().lbm_init_droplets(self._h, len(ds), arr))
+
+    # -------------------------------------------------------------- run
+    def step(self, n: int = 1):
+        _check("lbm_step", lib().lbm_step(self._h, int(n)))
+
+    def step_diagnostics(self, n: int = 1) -> dict:
+        d = Diag()
+        _check("lbm_step_diagnostics", lib().lbm_step_diagnostics(self._h, int(n), ctypes.byref(d)))
+        return d.as_dict()
+
+    def diagnostics(self) -> dict:
+        d = Diag()
+        _check("lbm_get_diagnostics", lib().lbm_get_diagnostics(self._h, ctypes.byref(d)))
+        return d.as_dict()
+
+    def level(self) -> int:
+        v = ctypes.c_int64()
+        _check("lbm_get_level", lib().lbm_get_level(self._h, ctypes.byref(v)))
+        return v.value
+
+    def synchronize(self, timeout_ms: int = 60000):
+        _check("lbm_synchronize", lib().lbm_synchronize(self._h, int(timeout_ms)))
+
+    # -------------------------------------------------------------- output
+    def fields(self, mask=FIELD_PHI | FIELD_U | FIELD_P | FIELD_T, dtype="f64", out=None):
+        """Macroscopic fields of the current level as a dict of torch tensors
+        (device tensors if ``out`` is None: written by the kernel directly)."""
+        import torch
+        tdt = torch.float64 if dtype == "f64" else torch.float32
+        comps = [(FIELD_PHI, "phi", 1), (FIELD_U, "u", 3), (FIELD_P, "p", 1), (FIELD_T, "T", 1)]
+        n = sum(c for bit, _, c in comps if mask & bit)
+        buf = out if out is not None else torch.empty((n, self.nz, self.ny, self.nx), dtype=tdt,
+                                                      device=self.device)
+        on_dev = int(buf.is_cuda)
+        _check("lbm_get_fields", lib().lbm_get_fields(self._h, mask, ctypes.c_void_p(buf.data_ptr()),
+                                                      on_dev, 0 if dtype == "f64" else 1))
+        res, k = {}, 0
+        for bit, name, c in comps:
+            if mask & bit:
+                res[name] = buf[k] if c == 1 else buf[k:k + c]
+                k += c
+        return res
+
+    def get_pdfs(self, which: str):
+        """One PDF set as a (Q, nz, ny, nx) float64 numpy array (un-shifted)."""
+        import numpy as np
+        idx = {"h": 0, "g": 1, "f": 2, "T": 3}[which]
+        Q = {"h": self.q_phase, "g": 27, "T": 1}.get(which)
+        if which == "f":
+            Q = int(self.thermal[3:])
+        arr = np.empty((Q, self.nz, self.ny, self.nx), dtype=np.float64)
+        _check("lbm_get_pdfs", lib().lbm_get_pdfs(self._h, idx, ctypes.c_void_p(arr.ctypes.data)))
+        return arr
+
+    def set_pdfs(self, which: str, values):
+        import numpy as np
+        idx = {"h": 0, "g": 1, "f": 2, "T": 3}[which]
+        arr = np.ascontiguousarray(values, dtype=np.float64)
+        _check("lbm_set_pdfs", lib().lbm_set_pdfs(self._h, idx, ctypes.c_void_p(arr.ctypes.data)))

@@ -1,0 +1,83 @@
+"""Shared set-up for the GPU parity tests: the same seeded workload on the
+CUDA path (through the C ABI binding) and on the FP64 oracle."""
+import numpy as np
+
+import workloads as W
+from oracle import model as om
+from oracle.stencils import stencil as ostencil
+
+
+def relerr(a, b):
+    """||a - b||_inf / ||b||_inf (vector fields: over all components)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    den = np.abs(b).max()
+    return float(np.abs(a - b).max() / (den if den > 0 else 1.0))
+
+
+def gpu_domain(w: W.Workload, precision=None):
+    from paper_2401_03041_gb300 import lbm
+    d = lbm.Domain(w.nx, w.ny, w.nz, precision or w.precision, w.thermal, w.q_phase)
+    d.set_params(w.params)
+    if w.sources:
+        d.set_heat_sources(w.sources)
+    if w.patches is not None:
+        p = w.patches
+        d.set_heater_patches(p.z, p.sx, p.sy, p.x0, p.y0, p.intensity)
+    d.init_droplets(w.droplets)
+    return d
+
+
+def perm_to_oracle(Q):
+    """perm[i_lib] = oracle index of the library's direction i."""
+    from paper_2401_03041_gb300 import lbm
+    c_lib, w_lib = lbm.stencil(Q)
+    S = ostencil(Q)
+    idx = [next(j for j in range(Q) if tuple(int(v) for v in S.c[j]) == c) for c in c_lib]
+    assert np.allclose(np.array(w_lib), S.w[idx], rtol=0, atol=1e-16)
+    return np.array(idx)
+
+
+def gpu_state_in_oracle_order(d, w):
+    out = {"h": d.get_pdfs("h")[np.argsort(perm_to_oracle(w.q_phase))],
+           "g": d.get_pdfs("g")[np.argsort(perm_to_oracle(27))]}
+    if w.thermal.startswith("D3Q"):
+        Q = int(w.thermal[3:])
+        out["f"] = d.get_pdfs("f")[np.argsort(perm_to_oracle(Q))]
+    else:
+        out["T"] = d.get_pdfs("T")[0]
+    return out
+
+
+def load_state_into_gpu(d, w, state):
+    """Upload an oracle-ordered state (dict h, g, f|T) to the GPU domain."""
+    d.set_pdfs("h", state["h"][perm_to_oracle(w.q_phase)])
+    d.set_pdfs("g", state["g"][perm_to_oracle(27)])
+    if "f" in state:
+        d.set_pdfs("f", state["f"][perm_to_oracle(int(w.thermal[3:]))])
+    else:
+        d.set_pdfs("T", state["T"][None])
+
+
+def gpu_fields(d):
+    f = d.fields(dtype="f64")
+    return {k: v.detach().cpu().numpy() for k, v in f.items()}
+
+
+def ragged_workload(thermal="D3Q7", q_phase=15, walls=True, precision="fp64"):
+    """A lattice that spans several 32 x 8 tiles with ragged tails in x and y,
+    two moving droplets, heaters, walls at z (or periodic)."""
+    p = W.Params(nu_L=0.08, nu_H=0.12, mobility=0.03, xi=4.0, sigma_ref=4e-3,
+                 sigma_T=-6e-4, T_ref=0.1, alpha_L=0.04, alpha_H=0.04,
+                 walls_z=walls, T_bottom=-0.3, T_top=0.4,
+                 grad_T=(0.0, 2e-3, 0.0) if not walls else (1e-3, 0.0, 0.0),
+                 grad_T_origin=(20.0, 10.0, 6.0), gravity=(0.0, 0.0, -1e-6))
+    drops = [W.Droplet(12.3, 9.1, 6.4, 5.0, 2e-3, -1e-3, 5e-4),
+             W.Droplet(33.0, 14.5, 7.0, 4.2, -1e-3, 0.0, 0.0)]
+    src = [W.HeatSource(20.0, 5.0, -0.5, 0.05, 6.0), W.HeatSource(35.0, 15.0, 3.0, 0.02, 4.0, 5.0)]
+    return W.Workload("ragged_40x20x13", 40, 20, 13, 20, p, drops, src, q_phase=q_phase,
+                      thermal=thermal, precision=precision)
+
+
+def oracle_for(w):
+    return om.build(w)

@@ -1,0 +1,78 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+symbol include/lbm.h declares; host-side validation runs without CUDA calls."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.stencils import stencil as ostencil
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2401_03041_gb300 import build, lbm
+    build.build()
+    return lbm.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    from paper_2401_03041_gb300 import lbm
+    names = _declared()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(lbm.SYMBOLS) == names
+
+
+@pytest.mark.parametrize("Q", [7, 15, 19, 27])
+def test_library_stencils_match_appendix_b(L, Q):
+    from paper_2401_03041_gb300 import lbm
+    c, w = lbm.stencil(Q)
+    S = ostencil(Q)
+    assert sorted(c) == sorted(tuple(int(v) for v in r) for r in S.c)
+    for ci, wi in zip(c, w):
+        j = next(j for j in range(Q) if tuple(int(v) for v in S.c[j]) == ci)
+        assert wi == S.w[j]
+
+
+def test_workspace_bytes(L):
+    nb = L.lbm_workspace_bytes(32, 32, 32, 0, 0, 15)
+    N = 32 ** 3
+    assert nb >= 2 * (15 + 27 + 7) * N * 8
+    assert nb < 2 * (15 + 27 + 7) * N * 8 + 4 * 1024 * 1024
+    nb32 = L.lbm_workspace_bytes(512, 512, 512, 1, 0, 15)
+    assert abs(nb32 - 2 * 49 * 512 ** 3 * 4) < 64 * 1024 * 1024
+    nb16 = L.lbm_workspace_bytes(64, 64, 64, 2, 4, 27)
+    assert nb16 >= 2 * (27 + 27) * 64 ** 3 * 2 + 5 * 64 ** 3 * 4
+    for bad in [(0, 4, 4, 0, 0, 15), (4, 4, 4, 3, 0, 15), (4, 4, 4, 0, 6, 15), (4, 4, 4, 0, 0, 19)]:
+        assert L.lbm_workspace_bytes(*bad) == 0
+
+
+def test_create_rejects_bad_arguments_without_cuda(L):
+    h = ctypes.c_void_p()
+    assert L.lbm_create_domain(0, 4, 4, 0, 0, 15, None, None, 0, ctypes.byref(h)) == -1
+    assert b"invalid" in L.lbm_last_error()
+    assert L.lbm_create_domain(4, 4, 4, 0, 0, 14, None, None, 0, ctypes.byref(h)) == -1
+    assert L.lbm_create_domain(4, 4, 4, 0, 0, 15, None, ctypes.c_void_p(0x1000), 16,
+                               ctypes.byref(h)) == -3
+    assert L.lbm_step(None, 1) == -1
+    assert L.lbm_set_params(None, None) == -1
+    assert L.lbm_stencil(9, None, None) == -1
+
+
+def test_params_roundtrip(L):
+    from paper_2401_03041_gb300 import lbm
+    import workloads as W
+    p = lbm.make_params(W.config2().params)
+    assert p.walls_z == 1 and p.T_top == 0.5 and p.nu_L == 0.05
+    assert p.omega_high == 1.0 and p.eps_n == 1e-12

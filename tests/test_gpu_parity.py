@@ -1,0 +1,238 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+FP64: the GPU must match the oracle within 1e-11 relative (||.||_inf of the
+difference over ||.||_inf of the oracle field, per field and per PDF set).
+FP32 / FP16-storage: errors are measured and bounded loosely; the numbers are
+printed (pytest -s) and recorded in the design notes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from harness import (gpu_domain, gpu_fields, gpu_state_in_oracle_order, load_state_into_gpu,
+                     oracle_for, ragged_workload, relerr)
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_03041_gb300 import build
+    build.build()
+
+
+def compare_all(d, o, w, tol, label=""):
+    gf = gpu_fields(d)
+    of = o.macro()
+    errs = {k: relerr(gf[k], of[k]) for k in ("phi", "p", "T")}
+    errs["u"] = relerr(gf["u"], of["u"])
+    st = gpu_state_in_oracle_order(d, w)
+    ost = o.state()
+    for k in st:
+        errs["pdf_" + k] = relerr(st[k], ost[k])
+    print(label, {k: f"{v:.2e}" for k, v in errs.items()})
+    for k, v in errs.items():
+        assert v < tol, f"{label}: {k} relative error {v:.3e} >= {tol}"
+    return errs
+
+
+_CFG1 = {}
+
+
+def config1_oracle():
+    """The oracle's 200-step config-1 run (computed once per session)."""
+    if not _CFG1:
+        w = W.config1()
+        o = oracle_for(w)
+        o.step(w.steps)
+        _CFG1["o"] = o
+    return _CFG1["o"]
+
+
+def test_config1_fp64_200_steps():
+    """32^3 periodic droplet, D3Q15 phase field, D3Q7 thermal, 200 steps."""
+    w = W.config1()
+    d = gpu_domain(w)
+    d.step(w.steps)
+    compare_all(d, config1_oracle(), w, TOL64, "config1 fp64 200 steps")
+
+
+@pytest.mark.parametrize("thermal", ["D3Q7", "D3Q15", "D3Q19", "D3Q27", "RK2", "RK4"])
+@pytest.mark.parametrize("q_phase", [15, 27])
+def test_ragged_walls_fp64(thermal, q_phase):
+    """40 x 20 x 13 (ragged against the 32 x 8 tile), walls, heaters, two
+    moving droplets, every energy solver and both phase-field stencils."""
+    w = ragged_workload(thermal, q_phase, walls=True)
+    d = gpu_domain(w)
+    o = oracle_for(w)
+    d.step(12)
+    o.step(12)
+    compare_all(d, o, w, TOL64, f"ragged walls {thermal} q{q_phase}")
+
+
+@pytest.mark.parametrize("thermal", ["D3Q7", "RK4"])
+def test_ragged_periodic_fp64(thermal):
+    w = ragged_workload(thermal, 15, walls=False)
+    d = gpu_domain(w)
+    o = oracle_for(w)
+    d.step(12)
+    o.step(12)
+    compare_all(d, o, w, TOL64, f"ragged periodic {thermal}")
+
+
+@pytest.mark.parametrize("thermal", ["D3Q19", "RK2"])
+def test_perturbed_state_one_step_fp64(thermal):
+    """Arbitrary non-equilibrium PDFs (equilibrium + seeded noise in every
+    direction) exercise every term of the collisions in one step."""
+    w = ragged_workload(thermal, 27, walls=True)
+    o = oracle_for(w)
+    o.step(3)
+    st = o.state()
+    rng = np.random.Generator(np.random.PCG64(77))
+    for k in st:
+        st[k] = st[k] + rng.standard_normal(st[k].shape) * 1e-4
+    o.h, o.g = st["h"], st["g"]
+    if "f" in st:
+        o.f = st["f"]
+    else:
+        o.T = st["T"]
+    d = gpu_domain(w)
+    load_state_into_gpu(d, w, st)
+    compare_all(d, o, w, 1e-14 * 1e3, "perturbed, before step")
+    d.step(1)
+    o.step(1)
+    compare_all(d, o, w, TOL64, f"perturbed one step {thermal}")
+
+
+def test_rk_isotropic_operator_and_patches_fp64():
+    w = ragged_workload("RK4", 15, walls=True)
+    w = w.replace(params=W.Params(**{**w.params.__dict__, "rk_isotropic_fd": True}),
+                  patches=W.HeaterPatches(z=0, sx=10, sy=5, x0=[0, 10, 20, 30], y0=[0, 5, 10, 15],
+                                          intensity=[0.1, 0.2, 0.05, 0.3]))
+    d = gpu_domain(w)
+    o = oracle_for(w)
+    d.step(8)
+    o.step(8)
+    compare_all(d, o, w, TOL64, "rk4 iso + patches")
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (3, 1, 2), (33, 9, 1), (5, 17, 3)])
+def test_tiny_and_degenerate_lattices_fp64(shape):
+    nx, ny, nz = shape
+    p = W.Params(grad_T=(1e-3, 0, 0), grad_T_origin=(nx / 2, ny / 2, nz / 2))
+    w = W.Workload("tiny", nx, ny, nz, 5, p, [W.Droplet(nx / 2, ny / 2, nz / 2, 1.5, 1e-3, 0, 0)],
+                   q_phase=15, thermal="D3Q7", precision="fp64")
+    d = gpu_domain(w)
+    o = oracle_for(w)
+    d.step(5)
+    o.step(5)
+    compare_all(d, o, w, TOL64, f"tiny {shape}")
+
+
+def test_no_droplets_and_walls_nz2_fp64():
+    p = W.Params(walls_z=True, T_bottom=-1.0, T_top=1.0)
+    w = W.Workload("empty", 8, 8, 2, 5, p, [], q_phase=15, thermal="D3Q15", precision="fp64")
+    d = gpu_domain(w)
+    o = oracle_for(w)
+    d.step(7)
+    o.step(7)
+    compare_all(d, o, w, TOL64, "no droplets nz=2")
+
+
+def test_diagnostics_fp64():
+    w = ragged_workload("D3Q7", 15, walls=True)
+    d = gpu_domain(w)
+    o = oracle_for(w)
+    d.step(4)
+    o.step(4)
+    gd = d.diagnostics()
+    od = o.diagnostics()
+    for k in ("mass", "heat", "kinetic", "mx", "my", "mz"):
+        assert abs(gd[k] - od[k]) <= 1e-11 * max(abs(od[k]), 1e-30), (k, gd[k], od[k])
+    assert gd["level"] == 4
+    # fused into the step: the level the step consumed
+    sd = d.step_diagnostics(1)
+    assert sd["level"] == 4 and abs(sd["mass"] - gd["mass"]) <= 1e-13 * abs(gd["mass"])
+    assert d.level() == 5
+
+
+def test_mass_conserved_fp64_long():
+    w = ragged_workload("D3Q7", 15, walls=True)
+    d = gpu_domain(w)
+    m0 = d.diagnostics()["mass"]
+    d.step(500)
+    m1 = d.diagnostics()["mass"]
+    assert abs(m1 - m0) / m0 < 1e-12
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 2e-4), ("fp16", 5e-2)])
+def test_config1_reduced_precision_error(precision, tol):
+    """FP32 / FP16-storage against the FP64 oracle on config 1 (200 steps):
+    phi L_inf, velocity L2 (relative), phi mass and centroid."""
+    w = W.config1()
+    d = gpu_domain(w, precision)
+    d.step(w.steps)
+    o = config1_oracle()
+    gf = gpu_fields(d)
+    of = o.macro()
+    phi_inf = relerr(gf["phi"], of["phi"])
+    du = gf["u"] - of["u"]
+    u_l2 = math.sqrt((du ** 2).sum() / (of["u"] ** 2).sum())
+    gd, od = d.diagnostics(), o.diagnostics()
+    mass = abs(gd["mass"] - od["mass"]) / od["mass"]
+    cen = max(abs(a - b) for a, b in zip(gd["centroid"], od["centroid"]))
+    print(f"{precision}: phi_inf={phi_inf:.3e} u_L2={u_l2:.3e} mass={mass:.3e} centroid={cen:.3e}")
+    assert phi_inf < tol
+    assert mass < tol
+    assert cen < 1e-2
+
+
+def test_full_size_sampled_fp32():
+    """512^3 periodic, 64 droplets (the throughput workload), FP32, in the
+    launch configuration the benchmark times: after one step, a 20^3 sample
+    cut across a droplet interface matches an oracle run on the surrounding
+    28^3 box (periodic wrap garbage stays > 2 cells from the sample)."""
+    import torch
+    w = W.config4("D3Q7", "fp32")
+    d = gpu_domain(w)
+    m0 = d.diagnostics()["mass"]
+    d.step(1)
+    gf = d.fields(dtype="f32")
+    # a droplet whose sample box does not cross the periodic boundary (the
+    # background temperature term G.(x - x0) uses unwrapped coordinates)
+    def centre(dr):
+        return [int(round(dr.cx + dr.R)), int(round(dr.cy)), int(round(dr.cz))]
+    drop = next(dr for dr in w.droplets
+                if all(14 <= v <= n - 15 for v, n in zip(centre(dr), (w.nx, w.ny, w.nz))))
+    c = centre(drop)
+    lo = [v - 14 for v in c]
+    idx = [np.arange(l, l + 28) % n for l, n in zip(lo, (w.nx, w.ny, w.nz))]
+    from oracle import model as om
+    o = om.build(w, origin=tuple(lo), shape=(28, 28, 28))
+    o.step(1)
+    of = o.macro()
+    inner = (slice(4, 24),) * 3
+    for name in ("phi", "p", "T", "u"):
+        g = gf[name].detach().cpu().numpy()
+        if name == "u":
+            sub = g[:, idx[2]][:, :, idx[1]][:, :, :, idx[0]]
+            ref = of["u"][(slice(None),) + inner]
+            got = sub[(slice(None),) + inner]
+        else:
+            sub = g[idx[2]][:, idx[1]][:, :, idx[0]]
+            ref = of[name][inner]
+            got = sub[inner]
+        e = relerr(got, ref)
+        print("512^3 sample", name, f"{e:.2e}")
+        assert e < (1e-4 if name != "T" else 1e-2)
+    m1 = d.diagnostics()["mass"]
+    assert abs(m1 - m0) / m0 < 1e-6
+    del d
+    torch.cuda.empty_cache()
