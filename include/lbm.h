@@ -14,9 +14,12 @@
  *   - pull "one step, two grid" stream-collide, sweep order     (Sec. 4.1, Alg. 1, Alg. 2)
  *
  * Conventions for every entry point:
- *   - Lattice units (dx = dt = 1).  Cell (x, y, z) sits at integer
- *     coordinates; x and y are periodic; z is periodic or bounded by two
- *     walls at z = -1/2 and z = nz - 1/2 (lbm_params.walls_z).
+ *   - Lattice units (dx = dt = 1).  Cell (i, j, k) has its centre at
+ *     (i + 1/2, j + 1/2, k + 1/2): an n-cell axis spans [0, n].  x and y are
+ *     periodic; z is periodic or bounded by two walls on the faces z = 0 and
+ *     z = nz (lbm_params.walls_z).  Droplet centres, heat-source positions,
+ *     the background-gradient origin and the diagnostics' first moments use
+ *     these coordinates; heater patches use integer cell indices.
  *   - Field layout: [z][y][x], x fastest; multi-component fields are stored
  *     component-major ([comp][z][y][x]).  N = nx * ny * nz.
  *   - The library owns its state (PDF double buffers and auxiliary fields),

@@ -193,6 +193,10 @@ def _minv27():
 class OracleLBM:
     """Literal FP64 implementation on a (nx, ny, nz) box.
 
+    Cell (i, j, k) has its centre at (i + 1/2, j + 1/2, k + 1/2); z walls are
+    the box faces z = 0 and z = nz.  Droplet, heat-source and background-
+    gradient positions are given in these coordinates; heater patches by
+    integer cell index.
     ``origin``/``global_shape`` place the box inside a larger periodic lattice
     (used to check sampled cells of a large run: the box is then treated as
     periodic and only cells at least 2 x steps away from its x/y edges are
@@ -216,10 +220,12 @@ class OracleLBM:
         self.walls = bool(params.walls_z)
         self.NX, self.NY, self.NZ = global_shape if global_shape else (nx, ny, nz)
         ox, oy, oz = origin
-        Z, Y, X = np.meshgrid(np.arange(nz, dtype=float) + oz,
-                              np.arange(ny, dtype=float) + oy,
-                              np.arange(nx, dtype=float) + ox, indexing="ij")
-        self.X, self.Y, self.Z = X, Y, Z
+        # integer cell indices and cell-centre coordinates (cell k at k + 1/2;
+        # walls, when present, are the box faces z = 0 and z = NZ)
+        Zi, Yi, Xi = np.meshgrid(np.arange(nz) + oz, np.arange(ny) + oy,
+                                 np.arange(nx) + ox, indexing="ij")
+        self.Xi, self.Yi, self.Zi = Xi, Yi, Zi
+        self.X, self.Y, self.Z = Xi + 0.5, Yi + 0.5, Zi + 0.5
         self.q = self._heat_source(sources, patches)
         self.time = 0
         self.h = self.g = self.f = self.T = None
@@ -236,9 +242,9 @@ class OracleLBM:
             q = q + val
         if patches is not None:
             for k, I in enumerate(patches.intensity):
-                m = ((self.Z == patches.z)
-                     & (self.X >= patches.x0[k]) & (self.X < patches.x0[k] + patches.sx)
-                     & (self.Y >= patches.y0[k]) & (self.Y < patches.y0[k] + patches.sy))
+                m = ((self.Zi == patches.z)
+                     & (self.Xi >= patches.x0[k]) & (self.Xi < patches.x0[k] + patches.sx)
+                     & (self.Yi >= patches.y0[k]) & (self.Yi < patches.y0[k] + patches.sy))
                 q = q + np.where(m, I, 0.0)
         return q
 
@@ -265,7 +271,7 @@ class OracleLBM:
             u[1] += pk * d.uy
             u[2] += pk * d.uz
         if self.walls:
-            T0 = p.T_bottom + (p.T_top - p.T_bottom) * (self.Z + 0.5) / self.NZ
+            T0 = p.T_bottom + (p.T_top - p.T_bottom) * self.Z / self.NZ
         else:
             T0 = np.zeros_like(phi)
         self.h = eq_scalar(phi, u, self.Sh)

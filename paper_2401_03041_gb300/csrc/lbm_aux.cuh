@@ -104,7 +104,7 @@ __global__ void init_kernel(const DevParams P, const double* __restrict__ drops,
     double phi = 0.0, ux = 0.0, uy = 0.0, uz = 0.0;
     for (int k = 0; k < nd; ++k) {
       const double* d = drops + 7 * k;
-      double dx = x - d[0], dy = y - d[1], dz = z - d[2];
+      double dx = x + 0.5 - d[0], dy = y + 0.5 - d[1], dz = z + 0.5 - d[2];
       dx -= P.nx * rint(dx / P.nx);
       dy -= P.ny * rint(dy / P.ny);
       if (!P.walls) dz -= P.nz * rint(dz / P.nz);

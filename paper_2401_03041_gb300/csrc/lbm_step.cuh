@@ -90,12 +90,12 @@ __device__ __forceinline__ typename Store<S>::R pulled_sum(const DevParams& P, c
   return s;
 }
 
-// Heat source density q_T at a cell: Gaussian sources (Eq. HeatSource, r <= d)
-// plus heater patches.
+// Heat source density q_T at cell (x, y, z) (centre (x+1/2, y+1/2, z+1/2)):
+// Gaussian sources (Eq. HeatSource, r <= d) plus heater patches (by index).
 __device__ __forceinline__ double heat_source(const DevParams& P, int x, int y, int z) {
   double q = 0.0;
   for (int k = 0; k < P.nsrc; ++k) {
-    const double dx = x - P.src[k][0], dy = y - P.src[k][1], dz = z - P.src[k][2];
+    const double dx = x + 0.5 - P.src[k][0], dy = y + 0.5 - P.src[k][1], dz = z + 0.5 - P.src[k][2];
     const double r2 = dx * dx + dy * dy + dz * dz;
     const double w = P.src[k][4];
     if (P.src[k][5] < 0.0 || r2 <= P.src[k][5]) q += P.src[k][3] * exp(-2.0 * r2 / (w * w));
@@ -198,8 +198,8 @@ step_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, int zc
       gtx *= (R)3; gty *= (R)3; gtz *= (R)3; lt *= (R)6;
       // background gradient: T_total = T + G.(x - x0)
       const R Gx = (R)P.grad[0], Gy = (R)P.grad[1], Gz = (R)P.grad[2];
-      const R Ttot = Tc + (R)(P.grad[0] * (x - P.origin[0]) + P.grad[1] * (y - P.origin[1]) +
-                              P.grad[2] * (z - P.origin[2]));
+      const R Ttot = Tc + (R)(P.grad[0] * (x + 0.5 - P.origin[0]) + P.grad[1] * (y + 0.5 - P.origin[1]) +
+                              P.grad[2] * (z + 0.5 - P.origin[2]));
       const R gTx = gtx + Gx, gTy = gty + Gy, gTz = gtz + Gz;
 
       // ---------------------------------------------------- a1/a2 hydro pull
@@ -239,9 +239,9 @@ step_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, int zc
         dsum[0] += dphi;
         dsum[1] += (double)Tc;
         dsum[2] += 0.5 * (double)rho * (double)uu;
-        dsum[3] += dphi * x;
-        dsum[4] += dphi * y;
-        dsum[5] += dphi * z;
+        dsum[3] += dphi * (x + 0.5);
+        dsum[4] += dphi * (y + 0.5);
+        dsum[5] += dphi * (z + 0.5);
         if (!isfinite(dphi) || !isfinite((double)Tc) || !isfinite((double)uu)) dsum[6] += 1.0;
       }
       const size_t cell = cell_index(P, x, y, z);

@@ -74,7 +74,7 @@ def ragged_workload(thermal="D3Q7", q_phase=15, walls=True, precision="fp64"):
                  grad_T_origin=(20.0, 10.0, 6.0), gravity=(0.0, 0.0, -1e-6))
     drops = [W.Droplet(12.3, 9.1, 6.4, 5.0, 2e-3, -1e-3, 5e-4),
              W.Droplet(33.0, 14.5, 7.0, 4.2, -1e-3, 0.0, 0.0)]
-    src = [W.HeatSource(20.0, 5.0, -0.5, 0.05, 6.0), W.HeatSource(35.0, 15.0, 3.0, 0.02, 4.0, 5.0)]
+    src = [W.HeatSource(20.0, 5.0, 0.0, 0.05, 6.0), W.HeatSource(35.0, 15.0, 3.0, 0.02, 4.0, 5.0)]
     return W.Workload("ragged_40x20x13", 40, 20, 13, 20, p, drops, src, q_phase=q_phase,
                       thermal=thermal, precision=precision)
 

@@ -197,7 +197,7 @@ def test_fd_exact_on_quadratics():
         return (cf[0] + cf[1] * x + cf[2] * y + cf[3] * z + cf[4] * x * x + cf[5] * y * y
                 + cf[6] * z * z + cf[7] * x * y + cf[8] * y * z + cf[9] * x * z)
     q = _padded_poly(o, f)
-    x, y, z = o.X, o.Y, o.Z
+    x, y, z = o.Xi, o.Yi, o.Zi   # the padded polynomial uses cell indices
     gx = cf[1] + 2 * cf[4] * x + cf[7] * y + cf[9] * z
     gy = cf[2] + 2 * cf[5] * y + cf[7] * x + cf[8] * z
     gz = cf[3] + 2 * cf[6] * z + cf[8] * y + cf[9] * x
@@ -216,7 +216,7 @@ def test_fd_sinusoid_symbols():
     o = _box(8)
     k = np.array([2 * np.pi / 8, 2 * np.pi / 4, 0.3])
     q = _padded_poly(o, lambda x, y, z: np.sin(k[0] * x + k[1] * y + k[2] * z))
-    psi = np.sin(k[0] * o.X + k[1] * o.Y + k[2] * o.Z)
+    psi = np.sin(k[0] * o.Xi + k[1] * o.Yi + k[2] * o.Zi)
     S = stencil(27)
     sym_iso = -(2 / om.CS2) * sum(S.w[i] * (1 - np.cos(k @ S.c[i])) for i in range(27))
     sym_std = sum(2 * np.cos(ka) - 2 for ka in k)

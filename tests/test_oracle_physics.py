@@ -160,7 +160,7 @@ def test_wall_conduction_linear_profile_exact(thermal):
     last cell; anti-bounce-back (LB) and the ghost 2T_w - T (RK) keep it exactly."""
     o = make(2, 2, 12, thermal=thermal, walls_z=True, T_bottom=-0.5, T_top=0.5)
     o.init_droplets([])
-    T_lin = -0.5 + (o.Z + 0.5) / 12.0
+    T_lin = -0.5 + o.Z / 12.0
     o.step(40)
     assert np.abs(o.macro()["T"] - T_lin).max() < 1e-14
 
@@ -237,15 +237,15 @@ def test_marangoni_shear_between_walls():
     H, nu, G, sT, xi = 32, 0.5, 1e-2, -5e-4, 5.0
     o = make(1, 1, H, nu_L=nu, nu_H=nu, sigma_T=sT, grad_T=(G, 0.0, 0.0),
              walls_z=True, alpha_L=0.05, alpha_H=0.05, xi=xi)
-    zi = H / 2 - 0.5
+    zi = H / 2
     set_fields(o, 0.5 * (1 + np.tanh(2 * (o.Z - zi) / xi)))
     o.step(1500)
     ux = o.macro()["u"][0][:, 0, 0]
-    lo, hi = -0.5, H - 0.5
+    lo, hi = 0.0, float(H)
     s = np.linspace(lo, hi, 200001)
     dphi = (1.0 / xi) / np.cosh(2 * (s - zi) / xi) ** 2
     f = 1.5 * xi * sT * G * dphi ** 2
-    z = np.arange(H, dtype=float)
+    z = np.arange(H, dtype=float) + 0.5
     exact = np.empty(H)
     for j, zz in enumerate(z):
         gr = np.where(zz <= s, (zz - lo) * (hi - s), (s - lo) * (hi - zz)) / (hi - lo)
@@ -262,8 +262,8 @@ def test_marangoni_shear_between_walls():
 
 def test_centred_droplet_does_not_move():
     o = make(16, 16, 16, sigma_T=-5e-4, grad_T=(0.0, 0.0, 0.0))
-    # centre between cells so that the lattice is mirror-symmetric about it
-    o.init_droplets([W.Droplet(7.5, 7.5, 7.5, 5.0)])
+    # the box centre: the lattice is mirror-symmetric about it
+    o.init_droplets([W.Droplet(8.0, 8.0, 8.0, 5.0)])
     c0 = np.array(o.diagnostics()["centroid"])
     o.step(40)
     c1 = np.array(o.diagnostics()["centroid"])
@@ -304,7 +304,7 @@ def test_heat_source_integral_and_cutoff():
     assert abs(o.q.sum() / full - 1) < 1e-9
     d = 8.0
     o2 = OracleLBM(48, 48, 48, W.Params(), 15, "D3Q7",
-                   sources=[W.HeatSource(24.0, 24.0, 24.0, Q, w, d)])
+                   sources=[W.HeatSource(24.5, 24.5, 24.5, Q, w, d)])
     s = sqrt(2) * d / w
     cut = full * (erf(s) - 2 * s * exp(-s * s) / sqrt(pi))
     # lattice sum of a truncated Gaussian: discretisation of the sharp edge
@@ -356,11 +356,12 @@ def test_initial_droplet_profile_properties():
     (Sec. 3.1 initialisation), periodic minimum-image distances."""
     p = W.Params()
     o = OracleLBM(32, 32, 32, p, 15, "D3Q7")
-    o.init_droplets([W.Droplet(16.0, 16.0, 16.0, 8.0), W.Droplet(1.0, 5.0, 16.0, 5.0)])
+    # cell k is centred at k + 1/2
+    o.init_droplets([W.Droplet(16.5, 16.5, 16.5, 8.0), W.Droplet(1.0, 5.0, 16.0, 5.0)])
     phi = o.h.sum(axis=0)
     assert abs(phi[16, 16, 24] - 0.5) < 1e-15 and abs(phi[16, 24, 16] - 0.5) < 1e-15
     assert phi[16, 16, 16] > 0.99
-    # second droplet wraps around x = 0: mirror images about x = 1
-    for d in range(1, 6):
-        assert phi[16, 5, (1 + d) % 32] == phi[16, 5, (1 - d) % 32]
+    # second droplet wraps around x = 0: cells 1 + j and -j mirror about x = 1
+    for j in range(0, 5):
+        assert phi[16, 5, (1 + j) % 32] == phi[16, 5, (-j) % 32]
     assert phi[16, 5, 31] > 0.9

@@ -1,5 +1,9 @@
 """Seeded synthetic workloads for the thermocapillary phase-field LBM.
 
+Coordinates are cell-centred: cell (i, j, k) sits at (i + 1/2, j + 1/2,
+k + 1/2), so an n-cell axis spans [0, n] and its centre is n/2.  Walls are
+the faces z = 0 and z = nz.  Heater patches are given by integer cell index.
+
 This module is shared by the FP64 oracle and the CUDA path.  It holds only
 *inputs*: lattice sizes, physical parameters, droplet and heater placements
 drawn from a seeded ``numpy.random.Generator(PCG64(seed))``.  It contains
@@ -41,8 +45,8 @@ class Params:
     alpha_H: float = 0.05        # thermal diffusivity, heavy phase
     gravity: tuple = (0.0, 0.0, 0.0)
     walls_z: bool = False        # no-slip walls at both z faces (x, y periodic)
-    T_bottom: float = 0.0        # wall temperature at z = -1/2
-    T_top: float = 0.0           # wall temperature at z = nz - 1/2
+    T_bottom: float = 0.0        # wall temperature at z = 0
+    T_top: float = 0.0           # wall temperature at z = nz
     grad_T: tuple = (0.0, 0.0, 0.0)     # imposed background temperature gradient
     grad_T_origin: tuple = (0.0, 0.0, 0.0)  # point where the background part is 0
     eps_n: float = 1e-12         # regulariser of the interface normal
@@ -130,7 +134,7 @@ def _place_droplets(rng, n, box, r_lo, r_hi, gap, walls_z, wall_clear=3.0,
         cy = float(rng.uniform(0, ny))
         if walls_z:
             lo = R + wall_clear
-            hi = nz - 1 - R - wall_clear
+            hi = nz - R - wall_clear
             if hi <= lo:
                 continue
             cz = float(rng.uniform(lo, hi))
@@ -190,7 +194,7 @@ def config3(precision: str = "fp32") -> Workload:
                sigma_T=-2e-4, T_ref=0.0, alpha_L=0.05, alpha_H=0.05,
                walls_z=True, T_bottom=0.0, T_top=0.0)
     sources = [HeatSource(float(rng.uniform(0, nx)), float(rng.uniform(0, ny)),
-                          -0.5, 0.2, 6.0) for _ in range(4)]
+                          0.0, 0.2, 6.0) for _ in range(4)]
     drops = _place_droplets(rng, 3, (nx, ny, nz), 10.0, 16.0, 2 * p.xi, True,
                             speed=1e-3)
     return Workload("cfg3_256x128x128_capture", nx, ny, nz, 20000, p, drops,
