@@ -1,0 +1,380 @@
+"""Benchmark of the fused thermocapillary phase-field LBM step on GB300.
+
+Workload: the 512^3 periodic throughput lattice (64 seeded droplets, R in
+[8, 20], weak gradient dT/dx = 1e-4), D3Q15 phase field, D3Q27 central-moment
+hydrodynamics, D3Q7 thermal LB, PDFs in FP32 (shifted storage).  A step is
+one full time step of all three LB sweeps (one fused kernel launch).  The
+state (52.6 GB) is far larger than L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  With --impl reference it times the FP64
+oracle on the host cores instead (bounded crop of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fused step MLUPS FP32 vs FP64 at stated error, % HBM roofline; adjoint/fwd cost"
+BYTES_PER_CELL = {  # algorithmic bytes per cell update: each PDF read once + written once
+    ("fp32", "D3Q7"): 2 * (15 + 27 + 7) * 4,
+    ("fp64", "D3Q7"): 2 * (15 + 27 + 7) * 8,
+    ("fp16", "D3Q7"): 2 * (15 + 27 + 7) * 2,
+}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2401_03041_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_cell():
+    """DRAM bytes per cell of the step kernel from the committed ncu summary,
+    or None if the kernel sources changed since those counters were taken."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    if d.get("source_sha") != kernel_source_sha():
+        return None
+    return float(d["dram_bytes_per_cell"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(seconds: float = 15.0, n: int = 48, thermal: str = "D3Q7"):
+    """Time the FP64 oracle, as it stands, on an n^3 crop of the throughput
+    workload in a fresh single-threaded process (spawned, no CUDA)."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+import workloads as W
+from oracle.model import build
+w = W.crop(W.config4({thermal!r}, 'fp64'), {n}, {n}, {n})
+o = build(w)
+o.step(1)
+t0 = time.perf_counter(); steps = 0
+while time.perf_counter() - t0 < {seconds}:
+    o.step(1); steps += 1
+dt = time.perf_counter() - t0
+print(json.dumps({{"mlups": w.cells * steps / dt / 1e6, "steps": steps, "seconds": dt,
+                   "cells": w.cells, "name": w.name}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError("oracle timing failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    # each reference step is one oracle step on a 32^3 crop of the workload
+    import workloads as W
+    from oracle.model import build
+    n = 32
+    w = W.crop(W.config4(args.thermal, "fp64"), n, n, n)
+    o = build(w)
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(1)
+    dt = time.perf_counter() - t0
+    mlups = w.cells * args.steps / dt / 1e6
+    sample = f"{w.name}: {n}^3 crop of the 512^3 workload, {args.steps} oracle steps (numpy FP64)"
+    line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "cfg4_512cube_periodic_64drops (oracle on a 32^3 crop)",
+                       "thermal": args.thermal, "precision": "fp64"},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=512, help="lattice edge (default 512)")
+    ap.add_argument("--thermal", default="D3Q7")
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2401_03041_gb300 import build as B
+    from paper_2401_03041_gb300 import lbm
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    B.build()
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([v], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return v
+
+    # CPU baseline first (spawned subprocess; no CUDA in it)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        try:
+            cpu = cpu_oracle_sample(seconds=15.0, n=48, thermal=args.thermal)
+        except Exception as e:  # reported, not fatal
+            cpu = {"error": str(e)[:300]}
+
+    w = W.config4(args.thermal, args.precision, n=args.n)
+
+    def make_domain(prec):
+        d = lbm.Domain(w.nx, w.ny, w.nz, prec, w.thermal, w.q_phase, device=dev)
+        d.set_params(w.params)
+        d.init_droplets(w.droplets)
+        return d
+
+    def timed_steps(d, steps, warmup, sampler=None):
+        d.step(warmup)
+        torch.cuda.synchronize(dev)
+        barrier()
+        st = d.stream
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        torch.cuda.synchronize(dev)
+        e0.record(st)
+        d.step(steps)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        clk = sampler.stop() if sampler else None
+        barrier()
+        return e0.elapsed_time(e1) / 1e3, clk
+
+    # ---------------- headline: FP32 (or --precision) fused step
+    d = make_domain(args.precision)
+    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    secs, clocks = timed_steps(d, args.steps, args.warmup, sampler)
+    secs = max_over_ranks(secs)
+    cells = w.cells
+    mlups = cells * args.steps * world / secs / 1e6
+    per_step = secs / args.steps
+    launches_per_step = 1 if w.thermal.startswith("D3Q") else (2 if w.thermal == "RK2" else 4)
+
+    # ---------------- e2e: a job through the C ABI with host buffers
+    # init from the host droplet table, K steps each returning FP64
+    # diagnostics to the host, final phi field copied to host memory.
+    host_phi = torch.empty((1, w.nz, w.ny, w.nx), dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize(dev)
+    barrier()
+    t0 = time.perf_counter()
+    d.init_droplets(w.droplets)
+    for _ in range(args.steps):
+        d.step_diagnostics(1)
+    d.fields(lbm.FIELD_PHI, dtype="f32", out=host_phi)
+    torch.cuda.synchronize(dev)
+    e2e_secs = max_over_ranks(time.perf_counter() - t0)
+    barrier()
+    e2e_mlups = cells * args.steps * world / e2e_secs / 1e6
+    h2d = len(w.droplets) * 7 * 8 / args.steps
+    d2h = (args.steps * 64 + 4 * cells) / args.steps
+    diag_final = d.diagnostics()
+    del d
+    torch.cuda.empty_cache()
+
+    # ---------------- FP64 leg (same workload, fewer steps)
+    fp64 = None
+    if not args.no_fp64 and args.precision != "fp64":
+        d64 = make_domain("fp64")
+        s64, _ = timed_steps(d64, args.fp64_steps, 3)
+        s64 = max_over_ranks(s64)
+        fp64 = {"mlups": cells * args.fp64_steps * world / s64 / 1e6,
+                "ms_per_step": s64 / args.fp64_steps * 1e3, "steps": args.fp64_steps}
+        del d64
+        torch.cuda.empty_cache()
+
+    # ---------------- stated error: reduced precision vs FP64 on the 32^3 droplet
+    err = None
+    if rank == 0:
+        c1 = W.config1()
+        res = {}
+        for prec in ("fp64", args.precision):
+            dd = lbm.Domain(c1.nx, c1.ny, c1.nz, prec, c1.thermal, c1.q_phase, device=dev)
+            dd.set_params(c1.params)
+            dd.init_droplets(c1.droplets)
+            dd.step(c1.steps)
+            f = dd.fields(dtype="f64")
+            res[prec] = ({k: v.detach().cpu().numpy() for k, v in f.items()}, dd.diagnostics())
+            dd.close()
+        (a, da), (b, db) = res[args.precision], res["fp64"]
+        du = a["u"] - b["u"]
+        err = {"workload": "cfg1 32^3 droplet, 200 steps, vs GPU FP64 (= oracle to 3e-13)",
+               "phi_linf": float(np.abs(a["phi"] - b["phi"]).max()),
+               "u_l2_rel": float(math.sqrt((du ** 2).sum() / (b["u"] ** 2).sum())),
+               "mass_rel": abs(da["mass"] - db["mass"]) / db["mass"],
+               "centroid_abs": max(abs(x - y) for x, y in zip(da["centroid"], db["centroid"]))}
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = peaks()
+    bpc = BYTES_PER_CELL.get((args.precision, w.thermal))
+    achieved = bpc * cells / per_step / 1e9 if bpc else None
+    tpc = traffic_per_cell()
+    line = {
+        "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else ("f64" if args.precision == "fp64" else "f16-store/f32"),
+        "data": "synthetic (seeded droplets, workloads.config4)",
+        "config": {"workload": w.name, "lattice": [w.nx, w.ny, w.nz], "precision": args.precision,
+                   "thermal": w.thermal, "q_phase": w.q_phase, "hydro": "D3Q27 central moment",
+                   "l2": "state 52.6 GB >> 129 MB L2: no flush needed",
+                   "parallelism": f"replicas x{world} (independent lattices, no collective)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None,
+                     "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                     "bytes_per_cell": bpc,
+                     "traffic": tpc * cells if tpc else None,
+                     "kernel": "lbm::step_kernel (fused h/g/f stream-collide)"},
+        "cpu_baseline": ({"value": cpu["mlups"], "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                          "sample": f"{cpu['name']}: {cpu['steps']} FP64 numpy oracle steps in "
+                                    f"{cpu['seconds']:.1f} s, single thread"}
+                         if cpu and "mlups" in cpu else cpu),
+        "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "what": "lbm_init_droplets from host table + K x lbm_step_diagnostics(1) "
+                        "(FP64 diagnostics to host each step) + final phi to pinned host"},
+        "gpu_launches": args.steps * launches_per_step,
+        "fp64": fp64,
+        "fp32_vs_fp64": fp64 and {"speedup": mlups / fp64["mlups"]},
+        "error_vs_fp64": err,
+        "final_diag": {"mass": diag_final["mass"], "level": diag_final["level"]},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

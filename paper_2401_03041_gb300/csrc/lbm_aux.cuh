@@ -35,10 +35,15 @@ __device__ __forceinline__ RF rk_rhs(const DevParams& P, const RF* __restrict__ 
     for (int k = 1; k < 27; ++k) {
       const RF v = stage_at(P, psi, x, y, z, q27_cx(k), q27_cy(k), q27_cz(k));
       const RF w = (RF)weight<27>(k);
-      if (q27_cx(k)) gx += (RF)q27_cx(k) * w * v;
-      if (q27_cy(k)) gy += (RF)q27_cy(k) * w * v;
-      if (q27_cz(k)) gz += (RF)q27_cz(k) * w * v;
       lap += w * (v - c);
+      // opposite-pair differences (exact zero on uniform fields)
+      const bool first = q27_cx(k) > 0 || (q27_cx(k) == 0 && (q27_cy(k) > 0 || (q27_cy(k) == 0 && q27_cz(k) > 0)));
+      if (first) {
+        const RF d = v - stage_at(P, psi, x, y, z, -q27_cx(k), -q27_cy(k), -q27_cz(k));
+        if (q27_cx(k)) gx += (RF)q27_cx(k) * w * d;
+        if (q27_cy(k)) gy += (RF)q27_cy(k) * w * d;
+        if (q27_cz(k)) gz += (RF)q27_cz(k) * w * d;
+      }
     }
     gx *= (RF)3; gy *= (RF)3; gz *= (RF)3; lap *= (RF)6;
   } else {

@@ -180,6 +180,9 @@ step_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, int zc
       const int c0 = (ty + 1) * HX + (tx + 1);
       const R phi = s_phi[sc][c0];
       const R Tc = s_T[sc][c0];
+      // Gradients as sums over the 13 opposite pairs of differences
+      // psi(x + c) - psi(x - c): exactly zero on uniform fields (with FMA
+      // contraction a sum of +w psi and -w psi terms is not).
       R gpx = 0, gpy = 0, gpz = 0, lp = 0, gtx = 0, gty = 0, gtz = 0, lt = 0;
 #pragma unroll
       for (int k = 1; k < 27; ++k) {
@@ -188,11 +191,19 @@ step_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, int zc
         const R vp = s_phi[sl][o];
         const R vt = s_T[sl][o];
         const R w = (R)weight<27>(k);
-        if (q27_cx(k)) { gpx += (R)q27_cx(k) * w * vp; gtx += (R)q27_cx(k) * w * vt; }
-        if (q27_cy(k)) { gpy += (R)q27_cy(k) * w * vp; gty += (R)q27_cy(k) * w * vt; }
-        if (q27_cz(k)) { gpz += (R)q27_cz(k) * w * vp; gtz += (R)q27_cz(k) * w * vt; }
         lp += w * (vp - phi);
         lt += w * (vt - Tc);
+        // the first direction of each pair: first non-zero component positive
+        const bool first = q27_cx(k) > 0 || (q27_cx(k) == 0 && (q27_cy(k) > 0 || (q27_cy(k) == 0 && q27_cz(k) > 0)));
+        if (first) {
+          const int slm = q27_cz(k) == 0 ? sc : (q27_cz(k) > 0 ? sm : sp);
+          const int om_ = c0 - q27_cy(k) * HX - q27_cx(k);
+          const R dp = vp - s_phi[slm][om_];
+          const R dt = vt - s_T[slm][om_];
+          if (q27_cx(k)) { gpx += (R)q27_cx(k) * w * dp; gtx += (R)q27_cx(k) * w * dt; }
+          if (q27_cy(k)) { gpy += (R)q27_cy(k) * w * dp; gty += (R)q27_cy(k) * w * dt; }
+          if (q27_cz(k)) { gpz += (R)q27_cz(k) * w * dp; gtz += (R)q27_cz(k) * w * dt; }
+        }
       }
       gpx *= (R)3; gpy *= (R)3; gpz *= (R)3; lp *= (R)6;
       gtx *= (R)3; gty *= (R)3; gtz *= (R)3; lt *= (R)6;

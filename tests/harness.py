@@ -7,12 +7,15 @@ from oracle import model as om
 from oracle.stencils import stencil as ostencil
 
 
-def relerr(a, b):
-    """||a - b||_inf / ||b||_inf (vector fields: over all components)."""
+def relerr(a, b, floor=1e-6):
+    """||a - b||_inf / max(||b||_inf, floor) (vector fields: over all
+    components).  The floor keeps fields that vanish identically (p* or u of
+    a uniform lattice, where both sides hold rounding noise of 1e-20) from
+    dividing noise by noise; every field of a meaningful run exceeds it."""
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
-    den = np.abs(b).max()
-    return float(np.abs(a - b).max() / (den if den > 0 else 1.0))
+    den = max(float(np.abs(b).max()), floor)
+    return float(np.abs(a - b).max() / den)
 
 
 def gpu_domain(w: W.Workload, precision=None):
