@@ -204,6 +204,14 @@ lbm_status lbm_get_level(lbm_domain* dom, int64_t* level);
  * LBM_ERR_TIMEOUT if the work has not finished after timeout_ms. */
 lbm_status lbm_synchronize(lbm_domain* dom, int timeout_ms);
 
+/* Launch configuration of the domain's step kernel: info[0] = 1 for the
+ * bulk-copy kernel (rows staged in shared memory by cp.async.bulk), 0 for
+ * the generic kernel; info[1..3] = grid x, y, z; info[4] = planes per CTA;
+ * info[5] = dynamic shared memory bytes.  info holds 6 int32 values.  The
+ * environment variable LBM_KERNEL=generic, read at creation, forces the
+ * generic kernel; LBM_ZCHUNK=<planes> sets the planes per CTA. */
+lbm_status lbm_kernel_info(lbm_domain* dom, int32_t* info);
+
 /* Message of the calling thread's most recent failed call ("" if none). */
 const char* lbm_last_error(void);
 

@@ -2,6 +2,7 @@
 // conversion, diagnostics reduction).
 #include "launchers.h"
 #include "lbm_aux.cuh"
+#include "lbm_bulk.cuh"
 
 namespace lbm {
 
@@ -32,6 +33,32 @@ void launch_pdf_convert(int Q, bool to_f64, void* pdf, double* f64, long long N,
     case 19: convert_q<S, 19>(to_f64, pdf, f64, N, shift, st); break;
     default: convert_q<S, 27>(to_f64, pdf, f64, N, shift, st); break;
   }
+}
+
+template <class S, int QH>
+static size_t bulk_bytes_qf(int qf) {
+  switch (qf) {
+    case 0: return BulkSmem<S, QH, 0>::bytes;
+    case 7: return BulkSmem<S, QH, 7>::bytes;
+    case 15: return BulkSmem<S, QH, 15>::bytes;
+    case 19: return BulkSmem<S, QH, 19>::bytes;
+    default: return BulkSmem<S, QH, 27>::bytes;
+  }
+}
+
+template <class S>
+static size_t bulk_bytes_s(int qh, int qf) {
+  return qh == 15 ? bulk_bytes_qf<S, 15>(qf) : bulk_bytes_qf<S, 27>(qf);
+}
+
+size_t bulk_smem_bytes(int prec, int qh, int qf) {
+  if (prec == 0) return bulk_bytes_s<double>(qh, qf);
+  if (prec == 1) return bulk_bytes_s<float>(qh, qf);
+  return bulk_bytes_s<__half>(qh, qf);
+}
+
+int bulk_tile_rows(int prec) {
+  return prec == 0 ? BulkGeom<double>::TYB : (prec == 1 ? BulkGeom<float>::TYB : BulkGeom<__half>::TYB);
 }
 
 void launch_diag_finalize(const double* partials, int nblocks, double* out, cudaStream_t st) {

@@ -5,12 +5,26 @@
 
 #include "launchers.h"
 #include "lbm_aux.cuh"
+#include "lbm_bulk.cuh"
 
 namespace lbm {
 
 template <class S, int QH, int QF>
 void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A, dim3 grid,
-                 int zchunk, int mode, cudaStream_t st) {
+                 int zchunk, int mode, int use_bulk, cudaStream_t st) {
+  constexpr size_t bytes = BulkSmem<S, QH, QF>::bytes;
+  if constexpr (bytes <= kMaxDynSmem) {
+    if (use_bulk) {
+      static bool attr_set = false;
+      if (!attr_set) {
+        cudaFuncSetAttribute(step_bulk_kernel<S, QH, QF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes);
+        attr_set = true;
+      }
+      step_bulk_kernel<S, QH, QF><<<grid, dim3(TX, BulkGeom<S>::TYB), bytes, st>>>(P, A, zchunk, mode);
+      return;
+    }
+  }
   step_kernel<S, QH, QF><<<grid, dim3(TX, TY), 0, st>>>(P, A, zchunk, mode);
 }
 
@@ -25,7 +39,7 @@ void launch_init(const DevParams& P, const double* drops, int nd, S* h, S* g, S*
 #define LBM_INST(QF)                                                                          \
   template void launch_step<LBM_S, LBM_QH, QF>(const DevParams&,                              \
                                                const StepPtrs<LBM_S, Store<LBM_S>::R>&, dim3, \
-                                               int, int, cudaStream_t);                       \
+                                               int, int, int, cudaStream_t);                  \
   template void launch_init<LBM_S, LBM_QH, QF>(const DevParams&, const double*, int, LBM_S*,  \
                                                LBM_S*, LBM_S*, Store<LBM_S>::R*, cudaStream_t);
 LBM_INST(0)

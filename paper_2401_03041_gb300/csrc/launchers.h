@@ -9,9 +9,17 @@
 
 namespace lbm {
 
+// use_bulk: the bulk-copy kernel (grid of TX x BulkGeom<S>::TYB tiles) if
+// its shared memory fits, else the generic kernel (TX x TY tiles).
 template <class S, int QH, int QF>
 void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A, dim3 grid,
-                 int zchunk, int mode, cudaStream_t st);
+                 int zchunk, int mode, int use_bulk, cudaStream_t st);
+
+// Dynamic shared memory of the bulk kernel for (precision, q_phase, q_f),
+// and the largest a CTA may use; also its tile height.
+size_t bulk_smem_bytes(int prec, int qh, int qf);
+int bulk_tile_rows(int prec);
+constexpr size_t kMaxDynSmem = 232448;
 
 template <class S, int QH, int QF>
 void launch_init(const DevParams& P, const double* drops, int nd, S* h, S* g, S* f,

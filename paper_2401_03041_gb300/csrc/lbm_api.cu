@@ -48,32 +48,51 @@ size_t store_bytes(lbm_precision p) { return p == LBM_FP64 ? 8 : (p == LBM_FP32 
 size_t field_bytes(lbm_precision p) { return p == LBM_FP64 ? 8 : 4; }
 
 struct Layout {
-  size_t h[2], g[2], f[2], T, u, sa, sb, acc, partials, diag, drops, total;
+  size_t h[2], g[2], f[2], T, u, sa, sb, acc, partials, diag, drops, errflag, total;
 };
 
-// Launch geometry of the step kernel: TX x TY columns, z split into chunks.
+// Launch geometry of the step kernel: TX x rows columns, z split into chunks.
 struct Geometry {
   dim3 grid;
   int zchunk;
   int nblocks;
+  int bulk;  // 1: bulk-copy kernel, 0: generic kernel
 };
 
-Geometry geometry(int nx, int ny, int nz) {
+int thermal_q(lbm_thermal th);
+
+// The bulk-copy kernel needs 16-byte aligned rows, rows at least one staged
+// row long, at least two tiles of rows, and shared memory that fits.
+bool bulk_ok(int nx, int ny, lbm_precision prec, int qh, int qf) {
+  const char* env = std::getenv("LBM_KERNEL");
+  if (env && std::strcmp(env, "generic") == 0) return false;
+  const int s = prec == LBM_FP64 ? 8 : (prec == LBM_FP32 ? 4 : 2);
+  const int gxp = 16 / s;
+  if ((nx * s) % 16 != 0) return false;
+  if (nx < TX + 2 * gxp) return false;
+  if (ny < 2 * bulk_tile_rows((int)prec)) return false;
+  return bulk_smem_bytes((int)prec, qh, qf) <= kMaxDynSmem;
+}
+
+Geometry geometry(int nx, int ny, int nz, lbm_precision prec, int qh, int qf) {
   Geometry g;
-  const int bx = (nx + TX - 1) / TX, by = (ny + TY - 1) / TY;
+  g.bulk = bulk_ok(nx, ny, prec, qh, qf) ? 1 : 0;
+  const int rows = g.bulk ? bulk_tile_rows((int)prec) : TY;
+  const int bx = (nx + TX - 1) / TX, by = (ny + rows - 1) / rows;
   const long long cols = (long long)bx * by;
-  int nchunks = 1;
   const char* env = std::getenv("LBM_ZCHUNK");
   int zc = env ? std::atoi(env) : 0;
   if (zc <= 0) {
-    // aim for about 8 CTAs per SM over the 152 SMs, chunks of >= 8 planes
-    const long long want = 152LL * 8;
-    nchunks = (int)((want + cols - 1) / cols);
-    if (nchunks > nz / 8) nchunks = nz / 8;
+    // bulk: one CTA per SM, aim for >= 4 waves with chunks of >= 32 planes
+    // (each chunk refills its copy pipeline); generic: ~8 CTAs per SM.
+    const long long want = g.bulk ? 152LL * 4 : 152LL * 8;
+    const int minc = g.bulk ? 32 : 8;
+    int nchunks = (int)((want + cols - 1) / cols);
+    if (nchunks > nz / minc) nchunks = nz / minc;
     if (nchunks < 1) nchunks = 1;
     zc = (nz + nchunks - 1) / nchunks;
   }
-  nchunks = (nz + zc - 1) / zc;
+  const int nchunks = (nz + zc - 1) / zc;
   g.grid = dim3(bx, by, nchunks);
   g.zchunk = zc;
   g.nblocks = (int)(cols * nchunks);
@@ -100,11 +119,12 @@ bool layout(int nx, int ny, int nz, lbm_precision prec, lbm_thermal th, int qh, 
   L->sa = off; off = align256(off + (rk ? N * fb : 0));
   L->sb = off; off = align256(off + (rk4 ? N * fb : 0));
   L->acc = off; off = align256(off + (rk4 ? N * fb : 0));
-  // room for the largest grid any z-chunk choice can produce
-  const size_t max_blocks = (size_t)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * nz;
+  // room for the largest grid any kernel / z-chunk choice can produce
+  const size_t max_blocks = (size_t)((nx + TX - 1) / TX) * ((ny + 3) / 4) * nz;
   L->partials = off; off = align256(off + max_blocks * kDiagVals * 8);
   L->diag = off; off = align256(off + 8 * 8);
   L->drops = off; off = align256(off + (size_t)LBM_MAX_DROPLETS * 7 * 8);
+  L->errflag = off; off = align256(off + sizeof(int));
   L->total = off;
   return true;
 }
@@ -176,17 +196,18 @@ StepPtrs<S, typename Store<S>::R> ptrs(lbm_domain* d) {
   A.acc_out = (R*)at(d, d->L.acc);
   A.rk_acc = d->th == LBM_TH_RK4;
   A.diag_partials = (double*)at(d, d->L.partials);
+  A.error_flag = (int*)at(d, d->L.errflag);
   return A;
 }
 
 template <class S, int QH>
 void step_qf(lbm_domain* d, const StepPtrs<S, typename Store<S>::R>& A, int mode) {
   switch (d->qf) {
-    case 0: launch_step<S, QH, 0>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
-    case 7: launch_step<S, QH, 7>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
-    case 15: launch_step<S, QH, 15>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
-    case 19: launch_step<S, QH, 19>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
-    default: launch_step<S, QH, 27>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
+    case 0: launch_step<S, QH, 0>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
+    case 7: launch_step<S, QH, 7>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
+    case 15: launch_step<S, QH, 15>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
+    case 19: launch_step<S, QH, 19>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
+    default: launch_step<S, QH, 27>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
   }
 }
 
@@ -237,6 +258,21 @@ lbm_status run_pass(lbm_domain* d, int mode, void* macro_out = nullptr, int macr
   return LBM_OK;
 }
 
+// A kernel whose bounded wait ran out raised the device error flag; read it
+// after a synchronisation and make it sticky.
+lbm_status check_error_flag(lbm_domain* d) {
+  int flag = 0;
+  lbm_status s = check_cuda(d, cudaMemcpy(&flag, at(d, d->L.errflag), sizeof(int), cudaMemcpyDeviceToHost),
+                            "error flag read");
+  if (s != LBM_OK) return s;
+  if (flag) {
+    d->sticky = LBM_ERR_TIMEOUT;
+    d->sticky_msg = "a step kernel's bounded wait for its bulk copies ran out";
+    return fail(LBM_ERR_TIMEOUT, d->sticky_msg);
+  }
+  return LBM_OK;
+}
+
 lbm_status finish_diag(lbm_domain* d, long long level, lbm_diag* out) {
   launch_diag_finalize((const double*)at(d, d->L.partials), d->geo.nblocks,
                        (double*)at(d, d->L.diag), d->stream);
@@ -247,6 +283,8 @@ lbm_status finish_diag(lbm_domain* d, long long level, lbm_diag* out) {
                  "diagnostics copy");
   if (s != LBM_OK) return s;
   s = check_cuda(d, cudaStreamSynchronize(d->stream), "diagnostics sync");
+  if (s != LBM_OK) return s;
+  s = check_error_flag(d);
   if (s != LBM_OK) return s;
   out->mass = v[0];
   out->heat = v[1];
@@ -338,7 +376,7 @@ lbm_status lbm_create_domain(int nx, int ny, int nz, lbm_precision prec, lbm_the
   d->prec = prec; d->th = thermal; d->qh = q_phase; d->qf = thermal_q(thermal);
   d->stream = (cudaStream_t)stream;
   d->L = L;
-  d->geo = geometry(nx, ny, nz);
+  d->geo = geometry(nx, ny, nz, prec, q_phase, thermal_q(thermal));
   d->sticky = LBM_OK;
   lbm_default_params(&d->params);
   if (workspace) {
@@ -358,6 +396,15 @@ lbm_status lbm_create_domain(int nx, int ny, int nz, lbm_precision prec, lbm_the
     d->owns_ws = true;
   }
   refresh_devparams(d);
+  {
+    const cudaError_t e = cudaMemsetAsync(at(d, L.errflag), 0, sizeof(int), d->stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (d->owns_ws) cudaFree(d->ws);
+      delete d;
+      return fail(LBM_ERR_CUDA, std::string("workspace init failed: ") + cudaGetErrorString(e));
+    }
+  }
   *out = d;
   return LBM_OK;
 }
@@ -645,6 +692,7 @@ lbm_status lbm_synchronize(lbm_domain* d, int timeout_ms) {
     std::this_thread::sleep_for(std::chrono::microseconds(200));
   }
   cudaEventDestroy(ev);
+  if (s == LBM_OK) s = check_error_flag(d);
   return s;
 }
 
@@ -663,6 +711,17 @@ lbm_status lbm_stencil(int Q, int32_t* c_out, double* w_out) {
       for (int a = 0; a < 3; ++a) c_out[3 * i + a] = c[a];
     if (w_out) w_out[i] = w;
   }
+  return LBM_OK;
+}
+
+lbm_status lbm_kernel_info(lbm_domain* d, int32_t* info) {
+  if (!d || !info) return fail(LBM_ERR_ARG, "null argument");
+  info[0] = d->geo.bulk;
+  info[1] = (int32_t)d->geo.grid.x;
+  info[2] = (int32_t)d->geo.grid.y;
+  info[3] = (int32_t)d->geo.grid.z;
+  info[4] = d->geo.zchunk;
+  info[5] = d->geo.bulk ? (int32_t)bulk_smem_bytes((int)d->prec, d->qh, d->qf) : 0;
   return LBM_OK;
 }
 

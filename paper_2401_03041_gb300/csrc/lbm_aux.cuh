@@ -57,7 +57,7 @@ __device__ __forceinline__ RF rk_rhs(const DevParams& P, const RF* __restrict__ 
   }
   const RF ux = u[cell], uy = u[P.N + cell], uz = u[2 * P.N + cell];
   return -(ux * (gx + (RF)P.grad[0]) + uy * (gy + (RF)P.grad[1]) + uz * (gz + (RF)P.grad[2])) +
-         (RF)P.alpha * lap + (RF)heat_source(P, x, y, z);
+         (RF)P.alpha * lap + heat_source<RF>(P, x, y, z);
 }
 
 enum : int { RK2_FINAL = 0, RK4_STAGE2 = 1, RK4_STAGE3 = 2, RK4_FINAL = 3 };

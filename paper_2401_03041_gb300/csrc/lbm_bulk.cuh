@@ -1,0 +1,382 @@
+// lbm_bulk.cuh - the fused time-step kernel with asynchronous bulk copies.
+//
+// Same arithmetic as the generic kernel (lbm_step.cuh, via lbm_cell.cuh); the
+// difference is how the pulled PDFs reach the SM.  A CTA owns a TX x TYB
+// column of cells and marches along z.  For every plane it stages, in shared
+// memory, the rows the pull scheme reads:
+//   HF(p): h and f rows for the (TYB + 2)-row halo tile of plane p, each row
+//          already shifted by -c_y (and taken from plane p - c_z); columns
+//          [x0 - GXP, x0 + TX + GXP) with GXP = 16 / sizeof(S) so that every
+//          row copy is a 16-byte aligned cp.async.bulk (the -c_x shift is
+//          applied when reading shared memory);
+//   G(p):  g rows for the TYB interior rows, same scheme.
+// Rows that cross the periodic x boundary are split into two copies; rows
+// whose source lies beyond a z wall come from the opposite direction's row
+// of the same cell (bounce-back), read without shift.  Copies complete on
+// mbarriers (expect_tx byte counts).  While plane z is computed, HF(z + 2)
+// and G(z + 1) are in flight: HF uses a ring of three buffers (z, z + 1 for
+// phi/T, z + 2 in flight), G a ring of two.  phi and T of the halo tile are
+// summed from HF and kept for planes z - 1, z, z + 1.
+//
+// Requirements (checked by the host): nx * sizeof(S) a multiple of 16 and
+// nx >= TX + 2 GXP.  Every wait is bounded (about 2 s); on a timeout the CTA
+// raises the domain's error flag, drains its outstanding copies (bounded
+// too) and returns.
+#pragma once
+
+#include "lbm_step.cuh"
+
+namespace lbm {
+
+// ----------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: false after ~2 s without completion.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > 2000000000ull) return false;
+  }
+  return true;
+}
+
+// Runtime velocity tables (for the copy tasks, whose direction index is not
+// a compile-time constant): D3Q27 order, Q15 maps through to27.
+struct DirTab {
+  signed char c[27][3];
+  signed char opp[27];
+};
+__host__ __device__ constexpr DirTab make_dirtab27() {
+  DirTab t{};
+  for (int i = 0; i < 27; ++i) {
+    t.c[i][0] = (signed char)q27_cx(i);
+    t.c[i][1] = (signed char)q27_cy(i);
+    t.c[i][2] = (signed char)q27_cz(i);
+    t.opp[i] = (signed char)opp<27>(i);
+  }
+  return t;
+}
+static __constant__ DirTab kDir27 = make_dirtab27();
+
+template <int Q>
+__device__ __forceinline__ int rt_to27(int i) { return (Q == 15 && i >= 7) ? i + 12 : i; }
+template <int Q>
+__device__ __forceinline__ int rt_from27(int k) { return (Q == 15 && k >= 19) ? k - 12 : k; }
+
+template <class S>
+struct BulkGeom {
+  static constexpr int GXP = 16 / (int)sizeof(S);       // halo columns on each side
+  static constexpr int W = TX + 2 * GXP;                // staged row length (elements)
+  static constexpr int TYB = sizeof(S) == 8 ? 4 : 8;    // rows per CTA
+  static constexpr int HXB = TX + 2;                    // phi/T plane pitch
+  static constexpr int HYB = TYB + 2;
+  static constexpr int HPB = HXB * HYB;
+  static constexpr int NT = TX * TYB;
+};
+
+template <class S, int QH, int QF>
+struct BulkSmem {
+  using R = typename Store<S>::R;
+  using G = BulkGeom<S>;
+  static constexpr int NHF = QH + QF;
+  static constexpr size_t hf_stage = (size_t)NHF * (G::TYB + 2) * G::W;   // elements
+  static constexpr size_t g_stage = (size_t)27 * G::TYB * G::W;
+  static constexpr size_t off_hf = 0;
+  static constexpr size_t off_g = off_hf + 3 * hf_stage * sizeof(S);
+  static constexpr size_t off_phi = (off_g + 2 * g_stage * sizeof(S) + 15) & ~size_t(15);
+  static constexpr size_t off_T = off_phi + 3 * G::HPB * sizeof(R);
+  static constexpr size_t off_bar = (off_T + 3 * G::HPB * sizeof(R) + 15) & ~size_t(15);
+  static constexpr size_t bytes = off_bar + 5 * sizeof(uint64_t);
+};
+
+// Issue the row copies of one stage.  Task t enumerates (direction, row);
+// every thread takes a strided subset.
+//   kind 0 (HF): rows r = 0..TYB+1 are halo rows y0 - 1 + r of plane p;
+//                directions 0..QH-1 from h, QH..QH+QF-1 from f.
+//   kind 1 (G):  rows r = 0..TYB-1 are rows y0 + r of plane p; g directions.
+template <class S, int QH, int QF>
+__device__ __forceinline__ void issue_stage(const DevParams& P, const S* hsrc, const S* gsrc,
+                                            const S* fsrc, S* dst_stage, uint64_t* bar, int kind,
+                                            int p, int x0, int y0, int tid, int nthr) {
+  using G = BulkGeom<S>;
+  const int nrows = kind == 0 ? G::TYB + 2 : G::TYB;
+  const int ndir = kind == 0 ? QH + QF : 27;
+  const int ntask = nrows * ndir;
+  // plane whose tile this is (walls: the ghost planes reuse the boundary plane)
+  int pe = p;
+  if (P.walls) pe = p < 0 ? 0 : (p >= P.nz ? P.nz - 1 : p);
+  else pe = p < 0 ? p + P.nz : (p >= P.nz ? p - P.nz : p);
+  const int xs = x0 - G::GXP;
+  for (int t = tid; t < ntask; t += nthr) {
+    const int d = t / nrows, r = t % nrows;
+    const S* base;
+    int k27;
+    if (kind == 1) {
+      base = gsrc;
+      k27 = d;
+    } else if (d < QH) {
+      base = hsrc;
+      k27 = rt_to27<QH>(d);
+    } else {
+      base = fsrc;
+      k27 = d - QH;   // Q7/Q19/Q27 are prefixes of the D3Q27 order; Q15 handled below
+      if (QF == 15) k27 = rt_to27<15>(k27);
+    }
+    const int cxv = kDir27.c[k27][0], cyv = kDir27.c[k27][1], czv = kDir27.c[k27][2];
+    int yr = y0 + r - (kind == 0 ? 1 : 0);
+    yr = yr < 0 ? yr + P.ny : (yr >= P.ny ? yr - P.ny : yr);
+    const int zsrc = pe - czv;
+    int q, zz, yy;
+    if (P.walls && (zsrc < 0 || zsrc >= P.nz)) {
+      // bounce-back: opposite direction, same cell
+      const int o27 = kDir27.opp[k27];
+      q = (kind == 0 && d >= QH) ? (QF == 15 ? rt_from27<15>(o27) : o27)
+                                 : (kind == 0 ? rt_from27<QH>(o27) : o27);
+      zz = pe;
+      yy = yr;
+    } else {
+      q = (kind == 0 && d >= QH) ? d - QH : d;
+      zz = zsrc < 0 ? zsrc + P.nz : (zsrc >= P.nz ? zsrc - P.nz : zsrc);
+      yy = yr - cyv;
+      yy = yy < 0 ? yy + P.ny : (yy >= P.ny ? yy - P.ny : yy);
+    }
+    const S* row = base + (size_t)q * P.N + ((size_t)zz * P.ny + yy) * P.nx;
+    S* dst = dst_stage + ((size_t)d * nrows + r) * G::W;
+    if (xs < 0) {
+      const int a = -xs;  // elements taken from the end of the row
+      bulk_copy_g2s(dst, row + (P.nx - a), a * sizeof(S), bar);
+      bulk_copy_g2s(dst + a, row, (G::W - a) * sizeof(S), bar);
+    } else if (xs + G::W > P.nx) {
+      const int a = P.nx - xs;  // elements up to the end of the row
+      bulk_copy_g2s(dst, row + xs, a * sizeof(S), bar);
+      bulk_copy_g2s(dst + a, row, (G::W - a) * sizeof(S), bar);
+    } else {
+      bulk_copy_g2s(dst, row + xs, G::W * sizeof(S), bar);
+    }
+  }
+}
+
+template <class S, int QH, int QF>
+__global__ void __launch_bounds__(BulkGeom<S>::NT, 1)
+step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, int zchunk, int mode) {
+  using R = typename Store<S>::R;
+  using G = BulkGeom<S>;
+  using L = BulkSmem<S, QH, QF>;
+  constexpr int NHF = QH + QF;
+  constexpr int NT = G::NT;
+  extern __shared__ __align__(16) unsigned char smem[];
+  S* hf = (S*)(smem + L::off_hf);
+  S* gb = (S*)(smem + L::off_g);
+  R* s_phi = (R*)(smem + L::off_phi);
+  R* s_T = (R*)(smem + L::off_T);
+  uint64_t* bar = (uint64_t*)(smem + L::off_bar);  // [0..2] HF ring, [3..4] G ring
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * TX + tx;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * G::TYB;
+  const int z0 = blockIdx.z * zchunk;
+  const int z1 = min(z0 + zchunk, P.nz);
+  const int x = x0 + tx, y = y0 + ty;
+  const bool active = (x < P.nx) && (y < P.ny);
+  const R shh = (R)P.shift_h, shf = (R)P.shift_f;
+  constexpr uint32_t hf_bytes = (uint32_t)(L::hf_stage * sizeof(S));
+  constexpr uint32_t g_bytes = (uint32_t)(L::g_stage * sizeof(S));
+
+  if (tid == 0) {
+    for (int k = 0; k < 5; ++k) mbar_init(&bar[k], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  // ring bookkeeping, relative to the chunk: HF plane p -> slot (p - z0 + 1) % 3
+  // and fill index (p - z0 + 1) / 3; G plane p -> slot (p - z0) % 2, index (p - z0) / 2
+  auto hf_slot = [&](int p) { return (p - z0 + 1) % 3; };
+  auto hf_par = [&](int p) { return (uint32_t)(((p - z0 + 1) / 3) & 1); };
+  auto g_slot = [&](int p) { return (p - z0) % 2; };
+  auto g_par = [&](int p) { return (uint32_t)(((p - z0) / 2) & 1); };
+  auto hf_ptr = [&](int p) { return hf + (size_t)hf_slot(p) * L::hf_stage; };
+  auto g_ptr = [&](int p) { return gb + (size_t)g_slot(p) * L::g_stage; };
+
+  // phi / T of the halo tile of plane p from HF(p) -> phi/T slot (p - z0 + 1) % 3
+  auto sum_plane = [&](int p) {
+    const S* st = hf_ptr(p);
+    int pe = p;
+    bool ghost = false;
+    if (P.walls) {
+      if (p < 0) { pe = 0; ghost = true; }
+      else if (p >= P.nz) { pe = P.nz - 1; ghost = true; }
+    }
+    const bool lo = P.walls && pe == 0, hi = P.walls && pe == P.nz - 1;
+    R* ph = s_phi + hf_slot(p) * G::HPB;
+    R* tt = s_T + hf_slot(p) * G::HPB;
+    for (int k = tid; k < G::HPB; k += NT) {
+      const int hr = k / G::HXB, hc = k % G::HXB;
+      const int col = hc + G::GXP - 1;
+      R phi = 0;
+#pragma unroll
+      for (int i = 0; i < QH; ++i) {
+        const bool b = (cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi);
+        const S* rowp = st + ((size_t)i * (G::TYB + 2) + hr) * G::W;
+        phi += Store<S>::ld_s(rowp + (b ? col : col - cx<QH>(i)));
+      }
+      phi += shh;  // sum_i w_i * shift_h
+      R T;
+      if constexpr (QF > 0) {
+        T = 0;
+#pragma unroll
+        for (int i = 0; i < QF; ++i) {
+          const bool b = (cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi);
+          const S* rowp = st + ((size_t)(QH + i) * (G::TYB + 2) + hr) * G::W;
+          const R v = Store<S>::ld_s(rowp + (b ? col : col - cx<QF>(i))) + (R)weight<QF>(i) * shf;
+          T += b ? (-v + (R)(2.0 * weight<QF>(i)) * (R)(cz<QF>(i) > 0 ? P.T_bottom : P.T_top)) : v;
+        }
+      } else {
+        int gx = x0 + hc - 1, gy = y0 + hr - 1;
+        gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
+        gy = gy < 0 ? gy + P.ny : (gy >= P.ny ? gy - P.ny : gy);
+        T = A.T[cell_index(P, gx, gy, pe)];
+      }
+      if (ghost) T = (R)(2.0 * (p < 0 ? P.T_bottom : P.T_top)) - T;
+      ph[k] = phi;
+      tt[k] = T;
+    }
+  };
+
+  double dsum[kDiagVals];
+#pragma unroll
+  for (int k = 0; k < kDiagVals; ++k) dsum[k] = 0.0;
+
+  bool ok = true;
+  // pending[k]: slot k has copies in flight with parity pend_par[k]
+  uint32_t pending = 0, pend_par = 0;
+  auto mark = [&](int k, uint32_t par) { pending |= 1u << k; pend_par = (pend_par & ~(1u << k)) | (par << k); };
+  auto wait_slot = [&](int k, uint32_t par) {
+    const bool r = mbar_wait(&bar[k], par);
+    if (r) pending &= ~(1u << k);
+    return r;
+  };
+
+  if (z0 < z1) {
+    // prologue: HF(z0-1), HF(z0), HF(z0+1), G(z0)
+    if (tid == 0) {
+      for (int p = z0 - 1; p <= z0 + 1; ++p) mbar_expect_tx(&bar[hf_slot(p)], hf_bytes);
+      mbar_expect_tx(&bar[3 + g_slot(z0)], g_bytes);
+    }
+    __syncthreads();
+    for (int p = z0 - 1; p <= z0 + 1; ++p) {
+      issue_stage<S, QH, QF>(P, A.h_src, A.g_src, A.f_src, hf_ptr(p), &bar[hf_slot(p)], 0, p, x0, y0, tid, NT);
+      mark(hf_slot(p), hf_par(p));
+    }
+    issue_stage<S, QH, QF>(P, A.h_src, A.g_src, A.f_src, g_ptr(z0), &bar[3 + g_slot(z0)], 1, z0, x0, y0, tid, NT);
+    mark(3 + g_slot(z0), g_par(z0));
+    ok = ok && wait_slot(hf_slot(z0 - 1), hf_par(z0 - 1));
+    if (ok) sum_plane(z0 - 1);
+    ok = ok && wait_slot(hf_slot(z0), hf_par(z0));
+    if (ok) sum_plane(z0);
+  }
+
+  for (int z = z0; z < z1 && ok; ++z) {
+    ok = ok && wait_slot(hf_slot(z + 1), hf_par(z + 1));
+    if (ok) sum_plane(z + 1);
+    ok = ok && wait_slot(3 + g_slot(z), g_par(z));
+    const bool more_hf = z + 2 <= z1, more_g = z + 1 < z1;
+    if (tid == 0 && ok) {
+      if (more_hf) mbar_expect_tx(&bar[hf_slot(z + 2)], hf_bytes);
+      if (more_g) mbar_expect_tx(&bar[3 + g_slot(z + 1)], g_bytes);
+    }
+    if (__syncthreads_or(!ok)) { ok = false; break; }
+    if (more_hf) {
+      issue_stage<S, QH, QF>(P, A.h_src, A.g_src, A.f_src, hf_ptr(z + 2), &bar[hf_slot(z + 2)], 0, z + 2, x0, y0, tid, NT);
+      mark(hf_slot(z + 2), hf_par(z + 2));
+    }
+    if (more_g) {
+      issue_stage<S, QH, QF>(P, A.h_src, A.g_src, A.f_src, g_ptr(z + 1), &bar[3 + g_slot(z + 1)], 1, z + 1, x0, y0, tid, NT);
+      mark(3 + g_slot(z + 1), g_par(z + 1));
+    }
+    if (active) {
+      const R* pm = s_phi + hf_slot(z - 1) * G::HPB;
+      const R* pc = s_phi + hf_slot(z) * G::HPB;
+      const R* pp = s_phi + hf_slot(z + 1) * G::HPB;
+      const R* tm = s_T + hf_slot(z - 1) * G::HPB;
+      const R* tc = s_T + hf_slot(z) * G::HPB;
+      const R* tp = s_T + hf_slot(z + 1) * G::HPB;
+      const int c0 = (ty + 1) * G::HXB + (tx + 1);
+      Stencil27<R> fd;
+      fd.template eval<G::HXB>(pm, pc, pp, tm, tc, tp, c0);
+      R rgx = 0, rgy = 0, rgz = 0, rlap = 0;
+      if constexpr (QF == 0) rk_std<R, G::HXB>(tm, tc, tp, c0, rgx, rgy, rgz, rlap);
+      const bool lo = P.walls && z == 0, hi = P.walls && z == P.nz - 1;
+      const S* hfz = hf_ptr(z);
+      const S* gz = g_ptr(z);
+      const int col = tx + G::GXP;
+      auto geth = [&](int i) {
+        const bool b = (cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi);
+        return Store<S>::ld_s(hfz + ((size_t)i * (G::TYB + 2) + ty + 1) * G::W + (b ? col : col - cx<QH>(i))) +
+               (R)weight<QH>(i) * shh;
+      };
+      auto getg = [&](int i) {
+        const bool b = (cz<27>(i) > 0 && lo) || (cz<27>(i) < 0 && hi);
+        return Store<S>::ld_s(gz + ((size_t)i * G::TYB + ty) * G::W + (b ? col : col - cx<27>(i)));
+      };
+      auto getf = [&](int i) {
+        if constexpr (QF > 0) {
+          const bool b = (cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi);
+          const R v = Store<S>::ld_s(hfz + ((size_t)(QH + i) * (G::TYB + 2) + ty + 1) * G::W +
+                                     (b ? col : col - cx<QF>(i))) +
+                      (R)weight<QF>(i) * shf;
+          return b ? (-v + (R)(2.0 * weight<QF>(i)) * (R)(cz<QF>(i) > 0 ? P.T_bottom : P.T_top)) : v;
+        } else {
+          return (R)0;
+        }
+      };
+      cell_update<S, QH, QF>(P, A, x, y, z, cell_index(P, x, y, z), mode, pc[c0], tc[c0], fd, rgx,
+                             rgy, rgz, rlap, geth, getg, getf, dsum);
+    }
+    if (__syncthreads_or(!ok)) { ok = false; break; }
+  }
+
+  if (!ok) {
+    // raise the error flag, drain outstanding copies (bounded), leave
+    if (tid == 0 && A.error_flag) atomicExch(A.error_flag, 1);
+    for (int k = 0; k < 5; ++k)
+      if (pending & (1u << k)) mbar_wait(&bar[k], (pend_par >> k) & 1u);
+    return;
+  }
+  if (mode & MODE_DIAG) diag_block_reduce<NT>(dsum, A.diag_partials);
+}
+
+}  // namespace lbm

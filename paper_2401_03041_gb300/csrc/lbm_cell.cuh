@@ -1,0 +1,319 @@
+// lbm_cell.cuh - the per-cell part of one time step (a4-a9 of the sweep),
+// shared by the generic and the bulk-copy step kernels.
+//
+// Inputs: the zeroth moments phi and T of the pulled PDFs, their finite
+// differences (isotropic D3Q27 gradient and Laplacian), the RK stencil values,
+// and accessors returning the pulled PDF values h*_i, g*_i, f*_i (un-shifted,
+// with wall rules applied).  Outputs: post-collision PDFs (stored shifted),
+// RK stage-1 fields, optional macroscopic fields and FP64 diagnostics.
+//
+// Central-moment collision in closed form.  With y = g* - g^eq + S/2 (S the
+// Guo source), relaxing each central moment kappa_k at rate w_k gives
+// g' = g^eq + S/2 + K(u)^-1 [(1 - w_k) kappa_k(y)].  The zeroth and first
+// central moments of y vanish identically (p* = sum g*, u = sum c g* + a/2)
+// and orders >= 3 have w_k = 1, so only the six second-order moments survive,
+// relaxed with w = 1/tau(phi):
+//   Pi_ab = sum g* c_a c_b - p* c_s^2 d_ab - u_a u_b + (u_a a_b + a_a u_b)/2.
+// K(u)^-1 is the tensor product of 1D inverse shifts; a unit central moment of
+// order e along one axis maps to the populations (c = 0, +1, -1)
+//   P0 = {1 - u^2, (u^2 + u)/2, (u^2 - u)/2},  P1 = {-2u, u + 1/2, u - 1/2},
+//   P2 = {-1, 1/2, 1/2},
+// and (K^-1 Pi)_i = sum over the six moments of P_ex(cx) P_ey(cy) P_ez(cz).
+// g^eq + S/2 splits into a part even and a part odd under c -> -c, evaluated
+// once per opposite pair.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+__device__ __forceinline__ size_t cell_index(const DevParams& P, int x, int y, int z) {
+  return ((size_t)z * P.ny + y) * P.nx + x;
+}
+
+// Heat source density q_T at cell (x, y, z) (centre (x+1/2, y+1/2, z+1/2)):
+// Gaussian sources (Eq. HeatSource, r <= d) plus heater patches (by index).
+template <class R>
+__device__ __forceinline__ R heat_source(const DevParams& P, int x, int y, int z) {
+  R q = 0;
+  for (int k = 0; k < P.nsrc; ++k) {
+    const R dx = (R)x + (R)0.5 - (R)P.src[k][0];
+    const R dy = (R)y + (R)0.5 - (R)P.src[k][1];
+    const R dz = (R)z + (R)0.5 - (R)P.src[k][2];
+    const R r2 = dx * dx + dy * dy + dz * dz;
+    const R w = (R)P.src[k][4];
+    if (P.src[k][5] < 0.0 || r2 <= (R)P.src[k][5]) q += (R)P.src[k][3] * exp((R)-2 * r2 / (w * w));
+  }
+  if (P.npatch > 0 && z == P.patch_z) {
+    for (int k = 0; k < P.npatch; ++k) {
+      if (x >= P.px0[k] && x < P.px0[k] + P.patch_sx && y >= P.py0[k] && y < P.py0[k] + P.patch_sy)
+        q += (R)P.pI[k];
+    }
+  }
+  return q;
+}
+
+template <class R>
+__device__ __forceinline__ R basis_pick(int c, R z, R p, R m) { return c == 0 ? z : (c > 0 ? p : m); }
+
+// Is direction i the first of its opposite pair (first non-zero component > 0)?
+template <int Q>
+__host__ __device__ constexpr bool pair_first(int i) {
+  return cx<Q>(i) > 0 || (cx<Q>(i) == 0 && (cy<Q>(i) > 0 || (cy<Q>(i) == 0 && cz<Q>(i) > 0)));
+}
+
+// Finite differences of one plane triple: the isotropic D3Q27 gradient and
+// Laplacian of phi and T from three shared-memory planes (row pitch HXv),
+// summed over opposite pairs so that uniform fields give exact zeros.
+template <class R>
+struct Stencil27 {
+  R gpx, gpy, gpz, lp, gtx, gty, gtz, lt;
+  template <int HXv>
+  __device__ __forceinline__ void eval(const R* pm, const R* pc, const R* pp, const R* tm,
+                                       const R* tc, const R* tp, int c0) {
+    const R phi = pc[c0], T = tc[c0];
+    gpx = gpy = gpz = lp = gtx = gty = gtz = lt = 0;
+#pragma unroll
+    for (int k = 1; k < 27; ++k) {
+      const R* P_ = q27_cz(k) == 0 ? pc : (q27_cz(k) > 0 ? pp : pm);
+      const R* T_ = q27_cz(k) == 0 ? tc : (q27_cz(k) > 0 ? tp : tm);
+      const int o = c0 + q27_cy(k) * HXv + q27_cx(k);
+      const R vp = P_[o], vt = T_[o];
+      const R w = (R)weight<27>(k);
+      lp += w * (vp - phi);
+      lt += w * (vt - T);
+      if (pair_first<27>(k)) {
+        const R* Pm = q27_cz(k) == 0 ? pc : (q27_cz(k) > 0 ? pm : pp);
+        const R* Tm = q27_cz(k) == 0 ? tc : (q27_cz(k) > 0 ? tm : tp);
+        const int om = c0 - q27_cy(k) * HXv - q27_cx(k);
+        const R dp = vp - Pm[om], dt = vt - Tm[om];
+        if (q27_cx(k)) { gpx += (R)q27_cx(k) * w * dp; gtx += (R)q27_cx(k) * w * dt; }
+        if (q27_cy(k)) { gpy += (R)q27_cy(k) * w * dp; gty += (R)q27_cy(k) * w * dt; }
+        if (q27_cz(k)) { gpz += (R)q27_cz(k) * w * dp; gtz += (R)q27_cz(k) * w * dt; }
+      }
+    }
+    gpx *= (R)3; gpy *= (R)3; gpz *= (R)3; lp *= (R)6;
+    gtx *= (R)3; gty *= (R)3; gtz *= (R)3; lt *= (R)6;
+  }
+};
+
+// RK stage-1 operator values at the cell (7-point Laplacian, central gradient)
+template <class R, int HXv>
+__device__ __forceinline__ void rk_std(const R* tm, const R* tc, const R* tp, int c0, R& gx, R& gy,
+                                       R& gz, R& lap) {
+  gx = (R)0.5 * (tc[c0 + 1] - tc[c0 - 1]);
+  gy = (R)0.5 * (tc[c0 + HXv] - tc[c0 - HXv]);
+  gz = (R)0.5 * (tp[c0] - tm[c0]);
+  lap = tc[c0 + 1] + tc[c0 - 1] + tc[c0 + HXv] + tc[c0 - HXv] + tp[c0] + tm[c0] - (R)6 * tc[c0];
+}
+
+// a4-a9 for one cell.  GH/GG/GF: accessors i -> pulled (un-shifted) value.
+template <class S, int QH, int QF, class GH, class GG, class GF>
+__device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
+                                            int x, int y, int z, size_t cell, int mode,
+                                            typename Store<S>::R phi, typename Store<S>::R Tc,
+                                            const Stencil27<typename Store<S>::R>& fdv,
+                                            typename Store<S>::R rgx, typename Store<S>::R rgy,
+                                            typename Store<S>::R rgz, typename Store<S>::R rlap,
+                                            GH geth, GG getg, GF getf, double* dsum) {
+  using R = typename Store<S>::R;
+  const R gpx = fdv.gpx, gpy = fdv.gpy, gpz = fdv.gpz, lp = fdv.lp;
+  const R Gx = (R)P.grad[0], Gy = (R)P.grad[1], Gz = (R)P.grad[2];
+  const R Ttot = Tc + Gx * ((R)x + (R)0.5 - (R)P.origin[0]) + Gy * ((R)y + (R)0.5 - (R)P.origin[1]) +
+                 Gz * ((R)z + (R)0.5 - (R)P.origin[2]);
+  const R gTx = fdv.gtx + Gx, gTy = fdv.gty + Gy, gTz = fdv.gtz + Gz;
+
+  // ---- a2 hydro moments of the pulled g (zeroth, first, second)
+  R pst = 0, jx = 0, jy = 0, jz = 0, sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
+#pragma unroll
+  for (int i = 0; i < 27; ++i) {
+    const R v = getg(i);
+    pst += v;
+    if (cx<27>(i)) { jx += (R)cx<27>(i) * v; sxx += v; }
+    if (cy<27>(i)) { jy += (R)cy<27>(i) * v; syy += v; }
+    if (cz<27>(i)) { jz += (R)cz<27>(i) * v; szz += v; }
+    if (cx<27>(i) * cy<27>(i)) sxy += (R)(cx<27>(i) * cy<27>(i)) * v;
+    if (cx<27>(i) * cz<27>(i)) sxz += (R)(cx<27>(i) * cz<27>(i)) * v;
+    if (cy<27>(i) * cz<27>(i)) syz += (R)(cy<27>(i) * cz<27>(i)) * v;
+  }
+
+  // ---- a4/a5 forces
+  const R xi = (R)P.xi;
+  const R sigma = (R)P.sigma_ref + (R)P.sigma_T * (Ttot - (R)P.T_ref);
+  const R beta = (R)12 * sigma / xi;
+  const R kap = (R)1.5 * sigma * xi;
+  const R mu = (R)4 * beta * phi * (phi - (R)1) * (phi - (R)0.5) - kap * lp;
+  const R g2 = gpx * gpx + gpy * gpy + gpz * gpz;
+  const R tdp = gTx * gpx + gTy * gpy + gTz * gpz;
+  const R cm = (R)1.5 * xi * (R)P.sigma_T;
+  const R rho = (R)P.rho_L + phi * (R)(P.rho_H - P.rho_L);
+  const R Fx = mu * gpx + cm * (g2 * gTx - tdp * gpx) + rho * (R)P.gravity[0];
+  const R Fy = mu * gpy + cm * (g2 * gTy - tdp * gpy) + rho * (R)P.gravity[1];
+  const R Fz = mu * gpz + cm * (g2 * gTz - tdp * gpz) + rho * (R)P.gravity[2];
+  const R irho = (R)1 / rho;
+  const R ax = Fx * irho, ay = Fy * irho, az = Fz * irho;
+  // ---- a6 velocity
+  const R ux = jx + (R)0.5 * ax, uy = jy + (R)0.5 * ay, uz = jz + (R)0.5 * az;
+  const R uu = ux * ux + uy * uy + uz * uz;
+
+  if (mode & MODE_DIAG) {
+    const double dphi = (double)phi;
+    dsum[0] += dphi;
+    dsum[1] += (double)Tc;
+    dsum[2] += 0.5 * (double)rho * (double)uu;
+    dsum[3] += dphi * (x + 0.5);
+    dsum[4] += dphi * (y + 0.5);
+    dsum[5] += dphi * (z + 0.5);
+    if (!isfinite(dphi) || !isfinite((double)Tc) || !isfinite((double)uu)) dsum[6] += 1.0;
+  }
+  if (mode & MODE_MACRO) {
+    const double vals[6] = {(double)phi, (double)ux, (double)uy, (double)uz, (double)pst, (double)Tc};
+    const unsigned cnt[4] = {1u, 3u, 1u, 1u};
+    int slot = 0, v = 0;
+    for (int f = 0; f < 4; ++f) {
+      if (A.macro_mask & (1u << f)) {
+        for (unsigned c = 0; c < cnt[f]; ++c) {
+          const size_t at = (size_t)(slot + c) * P.N + cell;
+          if (A.macro_dtype == 0) ((double*)A.macro_out)[at] = vals[v + c];
+          else ((float*)A.macro_out)[at] = (float)vals[v + c];
+        }
+        slot += cnt[f];
+      }
+      v += cnt[f];
+    }
+  }
+  if (!(mode & MODE_COLLIDE)) return;
+
+  // ---- a8 g collision (central moments, closed form)
+  {
+    const R om = (R)1 / ((R)P.tau_L + phi * (R)(P.tau_H - P.tau_L));
+    const R k1 = (R)1 - om;
+    const R p3 = pst * (R)(1.0 / 3.0);
+    const R Pxx = k1 * (sxx - p3 - ux * ux + ux * ax);
+    const R Pyy = k1 * (syy - p3 - uy * uy + uy * ay);
+    const R Pzz = k1 * (szz - p3 - uz * uz + uz * az);
+    const R Pxy = k1 * (sxy - ux * uy + (R)0.5 * (ux * ay + ax * uy));
+    const R Pxz = k1 * (sxz - ux * uz + (R)0.5 * (ux * az + ax * uz));
+    const R Pyz = k1 * (syz - uy * uz + (R)0.5 * (uy * az + ay * uz));
+    // per-axis inverse-shift bases
+    const R X0z = (R)1 - ux * ux, X0p = (R)0.5 * (ux * ux + ux), X0m = (R)0.5 * (ux * ux - ux);
+    const R X1z = (R)-2 * ux, X1p = ux + (R)0.5, X1m = ux - (R)0.5;
+    const R Y0z = (R)1 - uy * uy, Y0p = (R)0.5 * (uy * uy + uy), Y0m = (R)0.5 * (uy * uy - uy);
+    const R Y1z = (R)-2 * uy, Y1p = uy + (R)0.5, Y1m = uy - (R)0.5;
+    const R Z0z = (R)1 - uz * uz, Z0p = (R)0.5 * (uz * uz + uz), Z0m = (R)0.5 * (uz * uz - uz);
+    const R Z1z = (R)-2 * uz, Z1p = uz + (R)0.5, Z1m = uz - (R)0.5;
+    R A00[3], A10[3], A01[3], A20[3], A02[3], A11[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int zc = c == 0 ? 0 : (c == 1 ? 1 : -1);
+      const R p0 = basis_pick(zc, Z0z, Z0p, Z0m);
+      const R p1 = basis_pick(zc, Z1z, Z1p, Z1m);
+      const R p2 = zc == 0 ? (R)-1 : (R)0.5;
+      A00[c] = p2 * Pzz; A10[c] = p1 * Pxz; A01[c] = p1 * Pyz;
+      A20[c] = p0 * Pxx; A02[c] = p0 * Pyy; A11[c] = p0 * Pxy;
+    }
+    const R ua = ux * ax + uy * ay + uz * az;
+    const R base = pst - (R)1.5 * (uu + ua);
+    auto neq_of = [&](int ex, int ey, int ez) -> R {
+      const int c = ez == 0 ? 0 : (ez > 0 ? 1 : 2);
+      const R q0 = basis_pick(ey, Y0z, Y0p, Y0m);
+      const R q1 = basis_pick(ey, Y1z, Y1p, Y1m);
+      const R q2 = ey == 0 ? (R)-1 : (R)0.5;
+      const R B0 = q0 * A00[c] + q1 * A01[c] + q2 * A02[c];
+      const R B1 = q0 * A10[c] + q1 * A11[c];
+      const R B2 = q0 * A20[c];
+      const R r0 = basis_pick(ex, X0z, X0p, X0m);
+      const R r1 = basis_pick(ex, X1z, X1p, X1m);
+      const R r2 = ex == 0 ? (R)-1 : (R)0.5;
+      return r0 * B0 + r1 * B1 + r2 * B2;
+    };
+    S* dst = A.g_dst;
+    Store<S>::st(dst + cell, (R)weight<27>(0) * base + neq_of(0, 0, 0));
+#pragma unroll
+    for (int i = 1; i < 27; ++i) {
+      if (!pair_first<27>(i)) continue;
+      const int ex = cx<27>(i), ey = cy<27>(i), ez = cz<27>(i);
+      const R w = (R)weight<27>(i);
+      const R cu = (R)ex * ux + (R)ey * uy + (R)ez * uz;
+      const R ca = (R)ex * ax + (R)ey * ay + (R)ez * az;
+      // g^eq + S/2 = w [p* + 3cu + 9/2 cu^2 - 3/2 uu + 3/2 (ca - ua) + 9/2 cu ca]
+      const R even = w * (base + (R)4.5 * cu * (cu + ca));
+      const R odd = w * ((R)3 * cu + (R)1.5 * ca);
+      Store<S>::st(dst + (size_t)i * P.N + cell, even + odd + neq_of(ex, ey, ez));
+      Store<S>::st(dst + (size_t)opp<27>(i) * P.N + cell, even - odd + neq_of(-ex, -ey, -ez));
+    }
+  }
+  // ---- a7 h collision (single rate + Guo source of the interface force)
+  {
+    const R nrm = (R)1 / (sqrt(g2) + (R)P.eps_n);
+    const R th = (R)4 * phi * ((R)1 - phi) / xi * nrm;
+    const R fpx = th * gpx, fpy = th * gpy, fpz = th * gpz;
+    const R om = (R)P.omega_phi;
+    const R sc = (R)1 - (R)0.5 * om;
+    const R sh = (R)P.shift_h;
+    const R e0 = (R)1 - (R)1.5 * uu;
+    {
+      const R w = (R)weight<QH>(0);
+      const R hs = geth(0);
+      const R hn = hs - om * (hs - w * phi * e0);
+      Store<S>::st(A.h_dst + cell, hn - w * sh);
+    }
+#pragma unroll
+    for (int i = 1; i < QH; ++i) {
+      if (!pair_first<QH>(i)) continue;
+      const int j = opp<QH>(i);
+      const R w = (R)weight<QH>(i);
+      const R cu = (R)cx<QH>(i) * ux + (R)cy<QH>(i) * uy + (R)cz<QH>(i) * uz;
+      const R cf = (R)cx<QH>(i) * fpx + (R)cy<QH>(i) * fpy + (R)cz<QH>(i) * fpz;
+      const R even = w * phi * (e0 + (R)4.5 * cu * cu);
+      const R odd = w * phi * (R)3 * cu;
+      const R src = sc * w * cf;
+      const R hi = geth(i), hj = geth(j);
+      Store<S>::st(A.h_dst + (size_t)i * P.N + cell, hi - om * (hi - (even + odd)) + src - w * sh);
+      Store<S>::st(A.h_dst + (size_t)j * P.N + cell, hj - om * (hj - (even - odd)) - src - w * sh);
+    }
+  }
+  // ---- a9 / a9' thermal
+  const R q = heat_source<R>(P, x, y, z);
+  const R uG = ux * Gx + uy * Gy + uz * Gz;
+  if constexpr (QF > 0) {
+    const R om = (R)P.omega_T;
+    const R sf = (R)P.shift_f;
+    const R e0 = (R)1 - (R)1.5 * uu;
+    const R qs = q - uG;
+    {
+      const R w = (R)weight<QF>(0);
+      const R fs = getf(0);
+      const R fn = fs - om * (fs - w * Tc * e0) + w * qs;
+      Store<S>::st(A.f_dst + cell, fn - w * sf);
+    }
+#pragma unroll
+    for (int i = 1; i < QF; ++i) {
+      if (!pair_first<QF>(i)) continue;
+      const int j = opp<QF>(i);
+      const R w = (R)weight<QF>(i);
+      const R cu = (R)cx<QF>(i) * ux + (R)cy<QF>(i) * uy + (R)cz<QF>(i) * uz;
+      const R even = w * Tc * (e0 + (R)4.5 * cu * cu);
+      const R odd = w * Tc * (R)3 * cu;
+      const R fi = getf(i), fj = getf(j);
+      Store<S>::st(A.f_dst + (size_t)i * P.N + cell, fi - om * (fi - (even + odd)) + w * qs - w * sf);
+      Store<S>::st(A.f_dst + (size_t)j * P.N + cell, fj - om * (fj - (even - odd)) + w * qs - w * sf);
+    }
+  } else {
+    // RK stage 1: K1 = R(T^n) with the local u of this step
+    R gx_, gy_, gz_, lap;
+    if (P.rk_iso) {
+      gx_ = fdv.gtx; gy_ = fdv.gty; gz_ = fdv.gtz; lap = fdv.lt;
+    } else {
+      gx_ = rgx; gy_ = rgy; gz_ = rgz; lap = rlap;
+    }
+    const R K1 = -(ux * (gx_ + Gx) + uy * (gy_ + Gy) + uz * (gz_ + Gz)) + (R)P.alpha * lap + q;
+    A.u_out[cell] = ux;
+    A.u_out[P.N + cell] = uy;
+    A.u_out[2 * P.N + cell] = uz;
+    A.s1_out[cell] = Tc + (R)0.5 * K1;
+    if (A.rk_acc) A.acc_out[cell] = K1 * (R)(1.0 / 6.0);
+  }
+}
+
+}  // namespace lbm

@@ -64,16 +64,19 @@ template <class S> struct Store;
 template <> struct Store<double> {
   using R = double;
   __device__ __forceinline__ static R ld(const double* p) { return __ldg(p); }
+  __device__ __forceinline__ static R ld_s(const double* p) { return *p; }
   __device__ __forceinline__ static void st(double* p, R v) { *p = v; }
 };
 template <> struct Store<float> {
   using R = float;
   __device__ __forceinline__ static R ld(const float* p) { return __ldg(p); }
+  __device__ __forceinline__ static R ld_s(const float* p) { return *p; }
   __device__ __forceinline__ static void st(float* p, R v) { *p = v; }
 };
 template <> struct Store<__half> {
   using R = float;
   __device__ __forceinline__ static R ld(const __half* p) { return __half2float(__ldg(p)); }
+  __device__ __forceinline__ static R ld_s(const __half* p) { return __half2float(*p); }
   __device__ __forceinline__ static void st(__half* p, R v) { *p = __float2half_rn(v); }
 };
 
@@ -120,6 +123,7 @@ struct StepPtrs {
   // macroscopic output (MODE_MACRO): order phi, u(3), p, T, selected by mask
   void* macro_out; int macro_dtype; unsigned macro_mask;
   double* diag_partials;          // [grid blocks][kDiagVals] (MODE_DIAG)
+  int* error_flag;                // set to 1 by a CTA whose bounded wait ran out
 };
 
 }  // namespace lbm

@@ -27,7 +27,7 @@ SYMBOLS = ("lbm_default_params", "lbm_workspace_bytes", "lbm_create_domain",
            "lbm_set_heater_patches", "lbm_init_droplets", "lbm_step",
            "lbm_step_diagnostics", "lbm_get_diagnostics", "lbm_get_fields",
            "lbm_get_pdfs", "lbm_set_pdfs", "lbm_get_level", "lbm_synchronize",
-           "lbm_stencil", "lbm_last_error", "lbm_version")
+           "lbm_stencil", "lbm_kernel_info", "lbm_last_error", "lbm_version")
 
 
 class Params(ctypes.Structure):
@@ -109,6 +109,7 @@ def lib():
         "lbm_get_level": (c_int, [vp, P(ctypes.c_int64)]),
         "lbm_synchronize": (c_int, [vp, c_int]),
         "lbm_stencil": (c_int, [c_int, P(ctypes.c_int32), P(c_dbl)]),
+        "lbm_kernel_info": (c_int, [vp, P(ctypes.c_int32)]),
         "lbm_last_error": (ctypes.c_char_p, []),
         "lbm_version": (ctypes.c_char_p, []),
     }
@@ -252,6 +253,12 @@ class Domain:
         v = ctypes.c_int64()
         _check("lbm_get_level", lib().lbm_get_level(self._h, ctypes.byref(v)))
         return v.value
+
+    def kernel_info(self) -> dict:
+        v = (ctypes.c_int32 * 6)()
+        _check("lbm_kernel_info", lib().lbm_kernel_info(self._h, v))
+        return {"kernel": "bulk" if v[0] else "generic", "grid": (v[1], v[2], v[3]),
+                "zchunk": v[4], "smem_bytes": v[5]}
 
     def synchronize(self, timeout_ms: int = 60000):
         _check("lbm_synchronize", lib().lbm_synchronize(self._h, int(timeout_ms)))

@@ -18,9 +18,22 @@ def relerr(a, b, floor=1e-6):
     return float(np.abs(a - b).max() / den)
 
 
-def gpu_domain(w: W.Workload, precision=None):
+def gpu_domain(w: W.Workload, precision=None, kernel=None):
+    """kernel: None (library's choice), 'generic' (forced) or 'bulk'
+    (asserted to be the library's choice)."""
+    import os
     from paper_2401_03041_gb300 import lbm
-    d = lbm.Domain(w.nx, w.ny, w.nz, precision or w.precision, w.thermal, w.q_phase)
+    old = os.environ.pop("LBM_KERNEL", None)
+    if kernel == "generic":
+        os.environ["LBM_KERNEL"] = "generic"
+    try:
+        d = lbm.Domain(w.nx, w.ny, w.nz, precision or w.precision, w.thermal, w.q_phase)
+    finally:
+        os.environ.pop("LBM_KERNEL", None)
+        if old is not None:
+            os.environ["LBM_KERNEL"] = old
+    if kernel is not None:
+        assert d.kernel_info()["kernel"] == kernel, d.kernel_info()
     d.set_params(w.params)
     if w.sources:
         d.set_heat_sources(w.sources)
@@ -67,7 +80,7 @@ def gpu_fields(d):
     return {k: v.detach().cpu().numpy() for k, v in f.items()}
 
 
-def ragged_workload(thermal="D3Q7", q_phase=15, walls=True, precision="fp64"):
+def ragged_workload(thermal="D3Q7", q_phase=15, walls=True, precision="fp64", shape=(40, 20, 13)):
     """A lattice that spans several 32 x 8 tiles with ragged tails in x and y,
     two moving droplets, heaters, walls at z (or periodic)."""
     p = W.Params(nu_L=0.08, nu_H=0.12, mobility=0.03, xi=4.0, sigma_ref=4e-3,
@@ -78,8 +91,21 @@ def ragged_workload(thermal="D3Q7", q_phase=15, walls=True, precision="fp64"):
     drops = [W.Droplet(12.3, 9.1, 6.4, 5.0, 2e-3, -1e-3, 5e-4),
              W.Droplet(33.0, 14.5, 7.0, 4.2, -1e-3, 0.0, 0.0)]
     src = [W.HeatSource(20.0, 5.0, 0.0, 0.05, 6.0), W.HeatSource(35.0, 15.0, 3.0, 0.02, 4.0, 5.0)]
-    return W.Workload("ragged_40x20x13", 40, 20, 13, 20, p, drops, src, q_phase=q_phase,
+    nx, ny, nz = shape
+    return W.Workload(f"ragged_{nx}x{ny}x{nz}", nx, ny, nz, 20, p, drops, src, q_phase=q_phase,
                       thermal=thermal, precision=precision)
+
+
+def bulk_fits(precision, q_phase, thermal):
+    """Whether the bulk-copy kernel's shared memory fits for this combination."""
+    qf = int(thermal[3:]) if thermal.startswith("D3Q") else 0
+    nhf = q_phase + qf
+    s = {"fp64": 8, "fp32": 4, "fp16": 2}[precision]
+    rows = 4 if s == 8 else 8
+    W = 32 + 2 * (16 // s)
+    rs = 8 if s == 8 else 4
+    smem = 3 * nhf * (rows + 2) * W * s + 2 * 27 * rows * W * s + 6 * 34 * (rows + 2) * rs + 64
+    return smem <= 232448
 
 
 def oracle_for(w):

@@ -11,8 +11,8 @@ import numpy as np
 import pytest
 
 import workloads as W
-from harness import (gpu_domain, gpu_fields, gpu_state_in_oracle_order, load_state_into_gpu,
-                     oracle_for, ragged_workload, relerr)
+from harness import (bulk_fits, gpu_domain, gpu_fields, gpu_state_in_oracle_order,
+                     load_state_into_gpu, oracle_for, ragged_workload, relerr)
 
 pytestmark = pytest.mark.gpu
 
@@ -64,27 +64,66 @@ def test_config1_fp64_200_steps():
     compare_all(d, config1_oracle(), w, TOL64, "config1 fp64 200 steps")
 
 
+def _kernels(precision, q_phase, thermal):
+    return ["generic", "bulk"] if bulk_fits(precision, q_phase, thermal) else ["generic"]
+
+
 @pytest.mark.parametrize("thermal", ["D3Q7", "D3Q15", "D3Q19", "D3Q27", "RK2", "RK4"])
 @pytest.mark.parametrize("q_phase", [15, 27])
 def test_ragged_walls_fp64(thermal, q_phase):
-    """40 x 20 x 13 (ragged against the 32 x 8 tile), walls, heaters, two
-    moving droplets, every energy solver and both phase-field stencils."""
+    """40 x 20 x 13 (ragged against both kernels' tiles), walls, heaters, two
+    moving droplets, every energy solver and both phase-field stencils, on
+    the generic kernel and (where its shared memory fits) the bulk-copy one."""
     w = ragged_workload(thermal, q_phase, walls=True)
-    d = gpu_domain(w)
     o = oracle_for(w)
-    d.step(12)
     o.step(12)
-    compare_all(d, o, w, TOL64, f"ragged walls {thermal} q{q_phase}")
+    for kern in _kernels("fp64", q_phase, thermal):
+        d = gpu_domain(w, kernel=kern)
+        d.step(12)
+        compare_all(d, o, w, TOL64, f"ragged walls {thermal} q{q_phase} {kern}")
 
 
 @pytest.mark.parametrize("thermal", ["D3Q7", "RK4"])
 def test_ragged_periodic_fp64(thermal):
     w = ragged_workload(thermal, 15, walls=False)
-    d = gpu_domain(w)
     o = oracle_for(w)
-    d.step(12)
     o.step(12)
-    compare_all(d, o, w, TOL64, f"ragged periodic {thermal}")
+    for kern in _kernels("fp64", 15, thermal):
+        d = gpu_domain(w, kernel=kern)
+        d.step(12)
+        compare_all(d, o, w, TOL64, f"ragged periodic {thermal} {kern}")
+
+
+@pytest.mark.parametrize("walls", [True, False])
+def test_bulk_multi_tile_chunked_fp64(walls, monkeypatch):
+    """72 x 24 x 20: several bulk tiles in x (ragged) and y, the z range split
+    into chunks of 6 planes (pipeline prologue at every chunk start)."""
+    monkeypatch.setenv("LBM_ZCHUNK", "6")
+    w = ragged_workload("D3Q7", 15, walls=walls, shape=(72, 24, 20))
+    o = oracle_for(w)
+    o.step(10)
+    d = gpu_domain(w, kernel="bulk")
+    assert d.kernel_info()["grid"][2] == 4
+    d.step(10)
+    compare_all(d, o, w, TOL64, f"bulk chunked walls={walls}")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("thermal", ["D3Q7", "RK2"])
+def test_bulk_equals_generic_reduced_precision(precision, thermal):
+    """The two kernels compute the same arithmetic: in FP32 / FP16 storage
+    they agree to the storage rounding after 20 steps."""
+    w = ragged_workload(thermal, 15, walls=True, precision=precision, shape=(64, 24, 12))
+    a = gpu_domain(w, kernel="generic")
+    b = gpu_domain(w, kernel="bulk")
+    a.step(20)
+    b.step(20)
+    fa, fb = gpu_fields(a), gpu_fields(b)
+    tol = 1e-5 if precision == "fp32" else 1e-2
+    for k in ("phi", "u", "p", "T"):
+        e = relerr(fb[k], fa[k])
+        print(precision, thermal, k, f"{e:.2e}")
+        assert e < tol, (k, e)
 
 
 @pytest.mark.parametrize("thermal", ["D3Q19", "RK2"])
@@ -201,7 +240,7 @@ def test_full_size_sampled_fp32():
     28^3 box (periodic wrap garbage stays > 2 cells from the sample)."""
     import torch
     w = W.config4("D3Q7", "fp32")
-    d = gpu_domain(w)
+    d = gpu_domain(w, kernel="bulk")
     m0 = d.diagnostics()["mass"]
     d.step(1)
     gf = d.fields(dtype="f32")

@@ -202,9 +202,12 @@ def config3(precision: str = "fp32") -> Workload:
 
 
 def config4(thermal: str = "D3Q7", precision: str = "fp32", n: int = 512,
-            n_droplets: int = 64) -> Workload:
+            n_droplets: Optional[int] = None) -> Workload:
     """n^3 periodic throughput lattice (n = 512 by default), a seeded array of
-    droplets (R ~ U[8, 20], gap >= 2 xi), weak gradient dT/dx = 1e-4."""
+    droplets (R ~ U[8, 20], gap >= 2 xi; 64 droplets at 512^3, the same
+    density at other sizes), weak gradient dT/dx = 1e-4."""
+    if n_droplets is None:
+        n_droplets = max(1, int(round(64 * (n / 512.0) ** 3)))
     rng = _rng(4)
     p = Params(nu_L=0.05, nu_H=0.05, mobility=0.02, xi=5.0, sigma_ref=5e-3,
                sigma_T=-5e-4, T_ref=0.0, alpha_L=0.05, alpha_H=0.05,
