@@ -239,6 +239,8 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
     if (P.walls) {
       if (p < 0) { pe = 0; ghost = true; }
       else if (p >= P.nz) { pe = P.nz - 1; ghost = true; }
+    } else {
+      pe = p < 0 ? p + P.nz : (p >= P.nz ? p - P.nz : p);  // periodic z
     }
     const bool lo = P.walls && pe == 0, hi = P.walls && pe == P.nz - 1;
     R* ph = s_phi + hf_slot(p) * G::HPB;

@@ -83,7 +83,7 @@ def test_ragged_walls_fp64(thermal, q_phase):
         compare_all(d, o, w, TOL64, f"ragged walls {thermal} q{q_phase} {kern}")
 
 
-@pytest.mark.parametrize("thermal", ["D3Q7", "RK4"])
+@pytest.mark.parametrize("thermal", ["D3Q7", "D3Q19", "RK2", "RK4"])
 def test_ragged_periodic_fp64(thermal):
     w = ragged_workload(thermal, 15, walls=False)
     o = oracle_for(w)
