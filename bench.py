@@ -246,15 +246,17 @@ def main():
         return d
 
     def timed_steps(d, steps, warmup, sampler=None):
+        # the clock sampler starts before the warm-up: nvidia-smi's start-up
+        # must not fall inside the timed region (it stalls kernel launches)
+        if sampler:
+            sampler.start()
+            time.sleep(1.5)
         d.step(warmup)
         torch.cuda.synchronize(dev)
         barrier()
         st = d.stream
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        if sampler:
-            sampler.start()
-            time.sleep(0.3)
         torch.cuda.synchronize(dev)
         e0.record(st)
         d.step(steps)
@@ -266,6 +268,7 @@ def main():
 
     # ---------------- headline: FP32 (or --precision) fused step
     d = make_domain(args.precision)
+    kinfo = d.kernel_info()
     sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
                            if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
     secs, clocks = timed_steps(d, args.steps, args.warmup, sampler)
@@ -345,6 +348,7 @@ def main():
         "dtype": "f32" if args.precision == "fp32" else ("f64" if args.precision == "fp64" else "f16-store/f32"),
         "data": "synthetic (seeded droplets, workloads.config4)",
         "config": {"workload": w.name, "lattice": [w.nx, w.ny, w.nz], "precision": args.precision,
+                   "kernel": kinfo,
                    "thermal": w.thermal, "q_phase": w.q_phase, "hydro": "D3Q27 central moment",
                    "l2": "state 52.6 GB >> 129 MB L2: no flush needed",
                    "parallelism": f"replicas x{world} (independent lattices, no collective)"},
@@ -353,7 +357,8 @@ def main():
                      "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
                      "bytes_per_cell": bpc,
                      "traffic": tpc * cells if tpc else None,
-                     "kernel": "lbm::step_kernel (fused h/g/f stream-collide)"},
+                     "kernel": "lbm::step_bulk_kernel (fused h/g/f stream-collide, cp.async.bulk staging)"
+                               if kinfo["kernel"] == "bulk" else "lbm::step_kernel (fused, generic)"},
         "cpu_baseline": ({"value": cpu["mlups"], "unit": "MLUPS", "cores": 1, "kind": "oracle",
                           "sample": f"{cpu['name']}: {cpu['steps']} FP64 numpy oracle steps in "
                                     f"{cpu['seconds']:.1f} s, single thread"}

@@ -305,28 +305,34 @@ bool finite_all(const double* v, int n) {
   return true;
 }
 
+template <class R>
+void fill_real(RealParams<R>& r, const lbm_params& p, lbm_precision prec) {
+  const double cs2 = 1.0 / 3.0;
+  r.omega_phi = (R)(1.0 / (0.5 + p.mobility / cs2));
+  r.omega_T = (R)(1.0 / (0.5 + p.alpha_L / cs2));
+  r.tau_L = (R)(p.nu_L / cs2 + 0.5);
+  r.tau_H = (R)(p.nu_H / cs2 + 0.5);
+  r.rho_L = (R)p.rho_L; r.rho_H = (R)p.rho_H; r.xi = (R)p.xi;
+  r.sigma_ref = (R)p.sigma_ref; r.sigma_T = (R)p.sigma_T; r.T_ref = (R)p.T_ref; r.alpha = (R)p.alpha_L;
+  for (int k = 0; k < 3; ++k) {
+    r.gravity[k] = (R)p.gravity[k];
+    r.grad[k] = (R)p.grad_T[k];
+    r.origin[k] = (R)p.grad_T_origin[k];
+  }
+  r.T_bottom = (R)p.T_bottom; r.T_top = (R)p.T_top;
+  r.eps_n = (R)p.eps_n;
+  r.shift_h = (R)(prec == LBM_FP64 ? 0.0 : 0.5);
+  r.shift_f = (R)(prec == LBM_FP64 ? 0.0 : p.T_ref);
+}
+
 void refresh_devparams(lbm_domain* d) {
   DevParams& q = d->dp;
   const lbm_params& p = d->params;
-  const double cs2 = 1.0 / 3.0;
   q.nx = d->nx; q.ny = d->ny; q.nz = d->nz; q.N = d->N;
   q.walls = p.walls_z ? 1 : 0;
-  q.omega_phi = 1.0 / (0.5 + p.mobility / cs2);
-  q.omega_T = 1.0 / (0.5 + p.alpha_L / cs2);
-  q.tau_L = p.nu_L / cs2 + 0.5;
-  q.tau_H = p.nu_H / cs2 + 0.5;
-  q.rho_L = p.rho_L; q.rho_H = p.rho_H; q.xi = p.xi;
-  q.sigma_ref = p.sigma_ref; q.sigma_T = p.sigma_T; q.T_ref = p.T_ref; q.alpha = p.alpha_L;
-  for (int k = 0; k < 3; ++k) {
-    q.gravity[k] = p.gravity[k];
-    q.grad[k] = p.grad_T[k];
-    q.origin[k] = p.grad_T_origin[k];
-  }
-  q.T_bottom = p.T_bottom; q.T_top = p.T_top;
-  q.eps_n = p.eps_n;
-  q.shift_h = d->prec == LBM_FP64 ? 0.0 : 0.5;
-  q.shift_f = d->prec == LBM_FP64 ? 0.0 : p.T_ref;
   q.rk_iso = p.rk_isotropic_fd ? 1 : 0;
+  fill_real(q.pd, p, d->prec);
+  fill_real(q.pf, p, d->prec);
 }
 
 }  // namespace
@@ -459,9 +465,12 @@ lbm_status lbm_set_heat_sources(lbm_domain* d, int n, const lbm_heat_source* src
   }
   d->dp.nsrc = n;
   for (int k = 0; k < n; ++k) {
-    d->dp.src[k][0] = src[k].x; d->dp.src[k][1] = src[k].y; d->dp.src[k][2] = src[k].z;
-    d->dp.src[k][3] = src[k].Q; d->dp.src[k][4] = src[k].w;
-    d->dp.src[k][5] = (src[k].d > 0 && std::isfinite(src[k].d)) ? src[k].d * src[k].d : -1.0;
+    const double v[6] = {src[k].x, src[k].y, src[k].z, src[k].Q, src[k].w,
+                         (src[k].d > 0 && std::isfinite(src[k].d)) ? src[k].d * src[k].d : -1.0};
+    for (int j = 0; j < 6; ++j) {
+      d->dp.pd.src[k][j] = v[j];
+      d->dp.pf.src[k][j] = (float)v[j];
+    }
   }
   return LBM_OK;
 }
@@ -481,7 +490,8 @@ lbm_status lbm_set_heater_patches(lbm_domain* d, int z, int sx, int sy, int n, c
   for (int k = 0; k < n; ++k) {
     d->dp.px0[k] = x0[k];
     d->dp.py0[k] = y0[k];
-    d->dp.pI[k] = intensity[k];
+    d->dp.pd.pI[k] = intensity[k];
+    d->dp.pf.pI[k] = (float)intensity[k];
   }
   return LBM_OK;
 }
@@ -616,7 +626,7 @@ static lbm_status pdf_io(lbm_domain* d, int which, double* host, bool to_host) {
   if (which == 2 && d->qf == 0) return fail(LBM_ERR_ARG, "no thermal PDFs with an RK solver");
   if (which == 3 && d->qf != 0) return fail(LBM_ERR_ARG, "no T field with an LB thermal solver");
   int Q = which == 0 ? d->qh : (which == 1 ? 27 : (which == 2 ? d->qf : 1));
-  double shift = which == 0 ? d->dp.shift_h : (which == 2 ? d->dp.shift_f : 0.0);
+  double shift = which == 0 ? d->dp.pd.shift_h : (which == 2 ? d->dp.pd.shift_f : 0.0);
   void* buf = which == 0 ? at(d, d->L.h[d->cur])
             : which == 1 ? at(d, d->L.g[d->cur])
             : which == 2 ? at(d, d->L.f[d->cur]) : at(d, d->L.T);

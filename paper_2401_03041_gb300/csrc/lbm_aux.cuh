@@ -11,11 +11,12 @@ namespace lbm {
 template <class RF>
 __device__ __forceinline__ RF stage_at(const DevParams& P, const RF* __restrict__ psi, int x, int y,
                                        int z, int dx, int dy, int dz) {
+  const auto& rp = RP<RF>(P);
   const int xx = wrap(x + dx, P.nx), yy = wrap(y + dy, P.ny);
   int zz = z + dz;
   if (P.walls) {
-    if (zz < 0) return (RF)(2.0 * P.T_bottom) - psi[cell_index(P, xx, yy, 0)];
-    if (zz >= P.nz) return (RF)(2.0 * P.T_top) - psi[cell_index(P, xx, yy, P.nz - 1)];
+    if (zz < 0) return (RF)2 * rp.T_bottom - psi[cell_index(P, xx, yy, 0)];
+    if (zz >= P.nz) return (RF)2 * rp.T_top - psi[cell_index(P, xx, yy, P.nz - 1)];
   } else {
     zz = wrap(zz, P.nz);
   }
@@ -27,6 +28,7 @@ __device__ __forceinline__ RF stage_at(const DevParams& P, const RF* __restrict_
 template <class RF>
 __device__ __forceinline__ RF rk_rhs(const DevParams& P, const RF* __restrict__ psi, const RF* u,
                                      int x, int y, int z, size_t cell) {
+  const auto& rp = RP<RF>(P);
   const RF c = psi[cell];
   RF gx, gy, gz, lap;
   if (P.rk_iso) {
@@ -56,8 +58,8 @@ __device__ __forceinline__ RF rk_rhs(const DevParams& P, const RF* __restrict__ 
     lap = xp + xm + yp + ym + zp + zm - (RF)6 * c;
   }
   const RF ux = u[cell], uy = u[P.N + cell], uz = u[2 * P.N + cell];
-  return -(ux * (gx + (RF)P.grad[0]) + uy * (gy + (RF)P.grad[1]) + uz * (gz + (RF)P.grad[2])) +
-         (RF)P.alpha * lap + heat_source<RF>(P, x, y, z);
+  return -(ux * (gx + (RF)rp.grad[0]) + uy * (gy + (RF)rp.grad[1]) + uz * (gz + (RF)rp.grad[2])) +
+         (RF)rp.alpha * lap + heat_source<RF>(P, x, y, z);
 }
 
 enum : int { RK2_FINAL = 0, RK4_STAGE2 = 1, RK4_STAGE3 = 2, RK4_FINAL = 3 };
@@ -100,6 +102,7 @@ template <class S, int QH, int QF>
 __global__ void init_kernel(const DevParams P, const double* __restrict__ drops, int nd, S* h, S* g,
                             S* f, typename Store<S>::R* Tfield) {
   using R = typename Store<S>::R;
+  const auto& rp = P.pd;  // initialisation runs in FP64 in every mode
   const size_t n = (size_t)P.N;
   for (size_t cell = blockIdx.x * (size_t)blockDim.x + threadIdx.x; cell < n;
        cell += (size_t)gridDim.x * blockDim.x) {
@@ -114,19 +117,19 @@ __global__ void init_kernel(const DevParams P, const double* __restrict__ drops,
       dy -= P.ny * rint(dy / P.ny);
       if (!P.walls) dz -= P.nz * rint(dz / P.nz);
       const double r = sqrt(dx * dx + dy * dy + dz * dz);
-      const double pk = 0.5 * (1.0 + tanh(2.0 * (d[3] - r) / P.xi));
+      const double pk = 0.5 * (1.0 + tanh(2.0 * (d[3] - r) / rp.xi));
       phi = fmax(phi, pk);
       ux += pk * d[4];
       uy += pk * d[5];
       uz += pk * d[6];
     }
-    const double T0 = P.walls ? P.T_bottom + (P.T_top - P.T_bottom) * (z + 0.5) / P.nz : 0.0;
+    const double T0 = P.walls ? rp.T_bottom + (rp.T_top - rp.T_bottom) * (z + 0.5) / P.nz : 0.0;
     const double uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
     for (int i = 0; i < QH; ++i) {
       const double cu = cx<QH>(i) * ux + cy<QH>(i) * uy + cz<QH>(i) * uz;
       const double e = weight<QH>(i) * phi * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-      Store<S>::st(h + (size_t)i * n + cell, (R)(e - weight<QH>(i) * P.shift_h));
+      Store<S>::st(h + (size_t)i * n + cell, (R)(e - weight<QH>(i) * rp.shift_h));
     }
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
@@ -139,7 +142,7 @@ __global__ void init_kernel(const DevParams P, const double* __restrict__ drops,
       for (int i = 0; i < QF; ++i) {
         const double cu = cx<QF>(i) * ux + cy<QF>(i) * uy + cz<QF>(i) * uz;
         const double e = weight<QF>(i) * T0 * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-        Store<S>::st(f + (size_t)i * n + cell, (R)(e - weight<QF>(i) * P.shift_f));
+        Store<S>::st(f + (size_t)i * n + cell, (R)(e - weight<QF>(i) * rp.shift_f));
       }
     } else {
       Tfield[cell] = (R)T0;

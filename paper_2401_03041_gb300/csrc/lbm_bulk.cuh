@@ -24,6 +24,8 @@
 // too) and returns.
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_step.cuh"
 
 namespace lbm {
@@ -194,6 +196,7 @@ template <class S, int QH, int QF>
 __global__ void __launch_bounds__(BulkGeom<S>::NT, 1)
 step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, int zchunk, int mode) {
   using R = typename Store<S>::R;
+  const auto& rp = RP<R>(P);
   using G = BulkGeom<S>;
   using L = BulkSmem<S, QH, QF>;
   constexpr int NHF = QH + QF;
@@ -212,7 +215,7 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
   const int z1 = min(z0 + zchunk, P.nz);
   const int x = x0 + tx, y = y0 + ty;
   const bool active = (x < P.nx) && (y < P.ny);
-  const R shh = (R)P.shift_h, shf = (R)P.shift_f;
+  const R shh = (R)rp.shift_h, shf = (R)rp.shift_f;
   constexpr uint32_t hf_bytes = (uint32_t)(L::hf_stage * sizeof(S));
   constexpr uint32_t g_bytes = (uint32_t)(L::g_stage * sizeof(S));
 
@@ -231,9 +234,48 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
   auto hf_ptr = [&](int p) { return hf + (size_t)hf_slot(p) * L::hf_stage; };
   auto g_ptr = [&](int p) { return gb + (size_t)g_slot(p) * L::g_stage; };
 
-  // phi / T of the halo tile of plane p from HF(p) -> phi/T slot (p - z0 + 1) % 3
-  auto sum_plane = [&](int p) {
+  // phi / T of the halo tile of plane p from HF(p) -> phi/T slot (p - z0 + 1) % 3.
+  // Planes next to a wall take the bounce-back branch (BOUNCE = true); all
+  // other planes run the select-free variant.
+  auto sum_plane_impl = [&](auto btag, int p, int pe, bool ghost, bool lo, bool hi) {
+    constexpr bool BOUNCE = decltype(btag)::value;
     const S* st = hf_ptr(p);
+    R* ph = s_phi + hf_slot(p) * G::HPB;
+    R* tt = s_T + hf_slot(p) * G::HPB;
+    for (int k = tid; k < G::HPB; k += NT) {
+      const int hr = k / G::HXB, hc = k % G::HXB;
+      const int col = hc + G::GXP - 1;
+      const S* rowb = st + (size_t)hr * G::W + col;
+      R phi = 0;
+#pragma unroll
+      for (int i = 0; i < QH; ++i) {
+        const bool b = BOUNCE && ((cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi));
+        const S* rowp = rowb + (size_t)i * (G::TYB + 2) * G::W;
+        phi += Store<S>::ld_s(b ? rowp : rowp - cx<QH>(i));
+      }
+      phi += shh;  // sum_i w_i * shift_h
+      R T;
+      if constexpr (QF > 0) {
+        T = 0;
+#pragma unroll
+        for (int i = 0; i < QF; ++i) {
+          const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
+          const S* rowp = rowb + (size_t)(QH + i) * (G::TYB + 2) * G::W;
+          const R v = Store<S>::ld_s(b ? rowp : rowp - cx<QF>(i)) + (R)weight<QF>(i) * shf;
+          T += b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? rp.T_bottom : rp.T_top)) : v;
+        }
+      } else {
+        int gx = x0 + hc - 1, gy = y0 + hr - 1;
+        gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
+        gy = gy < 0 ? gy + P.ny : (gy >= P.ny ? gy - P.ny : gy);
+        T = A.T[cell_index(P, gx, gy, pe)];
+      }
+      if (ghost) T = (R)2 * (p < 0 ? rp.T_bottom : rp.T_top) - T;
+      ph[k] = phi;
+      tt[k] = T;
+    }
+  };
+  auto sum_plane = [&](int p) {
     int pe = p;
     bool ghost = false;
     if (P.walls) {
@@ -243,39 +285,8 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
       pe = p < 0 ? p + P.nz : (p >= P.nz ? p - P.nz : p);  // periodic z
     }
     const bool lo = P.walls && pe == 0, hi = P.walls && pe == P.nz - 1;
-    R* ph = s_phi + hf_slot(p) * G::HPB;
-    R* tt = s_T + hf_slot(p) * G::HPB;
-    for (int k = tid; k < G::HPB; k += NT) {
-      const int hr = k / G::HXB, hc = k % G::HXB;
-      const int col = hc + G::GXP - 1;
-      R phi = 0;
-#pragma unroll
-      for (int i = 0; i < QH; ++i) {
-        const bool b = (cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi);
-        const S* rowp = st + ((size_t)i * (G::TYB + 2) + hr) * G::W;
-        phi += Store<S>::ld_s(rowp + (b ? col : col - cx<QH>(i)));
-      }
-      phi += shh;  // sum_i w_i * shift_h
-      R T;
-      if constexpr (QF > 0) {
-        T = 0;
-#pragma unroll
-        for (int i = 0; i < QF; ++i) {
-          const bool b = (cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi);
-          const S* rowp = st + ((size_t)(QH + i) * (G::TYB + 2) + hr) * G::W;
-          const R v = Store<S>::ld_s(rowp + (b ? col : col - cx<QF>(i))) + (R)weight<QF>(i) * shf;
-          T += b ? (-v + (R)(2.0 * weight<QF>(i)) * (R)(cz<QF>(i) > 0 ? P.T_bottom : P.T_top)) : v;
-        }
-      } else {
-        int gx = x0 + hc - 1, gy = y0 + hr - 1;
-        gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
-        gy = gy < 0 ? gy + P.ny : (gy >= P.ny ? gy - P.ny : gy);
-        T = A.T[cell_index(P, gx, gy, pe)];
-      }
-      if (ghost) T = (R)(2.0 * (p < 0 ? P.T_bottom : P.T_top)) - T;
-      ph[k] = phi;
-      tt[k] = T;
-    }
+    if (lo || hi) sum_plane_impl(std::true_type{}, p, pe, ghost, lo, hi);
+    else sum_plane_impl(std::false_type{}, p, pe, ghost, false, false);
   };
 
   double dsum[kDiagVals];
@@ -342,31 +353,37 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
       R rgx = 0, rgy = 0, rgz = 0, rlap = 0;
       if constexpr (QF == 0) rk_std<R, G::HXB>(tm, tc, tp, c0, rgx, rgy, rgz, rlap);
       const bool lo = P.walls && z == 0, hi = P.walls && z == P.nz - 1;
-      const S* hfz = hf_ptr(z);
-      const S* gz = g_ptr(z);
       const int col = tx + G::GXP;
-      auto geth = [&](int i) {
-        const bool b = (cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi);
-        return Store<S>::ld_s(hfz + ((size_t)i * (G::TYB + 2) + ty + 1) * G::W + (b ? col : col - cx<QH>(i))) +
-               (R)weight<QH>(i) * shh;
+      const S* hrow = hf_ptr(z) + (size_t)(ty + 1) * G::W + col;   // direction 0, this cell
+      const S* grow = g_ptr(z) + (size_t)ty * G::W + col;
+      const size_t cell = cell_index(P, x, y, z);
+      auto cell_step = [&](auto btag) {
+        constexpr bool BOUNCE = decltype(btag)::value;
+        auto geth = [&](int i) {
+          const bool b = BOUNCE && ((cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi));
+          const S* p_ = hrow + (size_t)i * (G::TYB + 2) * G::W;
+          return Store<S>::ld_s(b ? p_ : p_ - cx<QH>(i)) + (R)weight<QH>(i) * shh;
+        };
+        auto getg = [&](int i) {
+          const bool b = BOUNCE && ((cz<27>(i) > 0 && lo) || (cz<27>(i) < 0 && hi));
+          const S* p_ = grow + (size_t)i * G::TYB * G::W;
+          return Store<S>::ld_s(b ? p_ : p_ - cx<27>(i));
+        };
+        auto getf = [&](int i) {
+          if constexpr (QF > 0) {
+            const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
+            const S* p_ = hrow + (size_t)(QH + i) * (G::TYB + 2) * G::W;
+            const R v = Store<S>::ld_s(b ? p_ : p_ - cx<QF>(i)) + (R)weight<QF>(i) * shf;
+            return b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? rp.T_bottom : rp.T_top)) : v;
+          } else {
+            return (R)0;
+          }
+        };
+        cell_update<S, QH, QF>(P, A, x, y, z, cell, mode, pc[c0], tc[c0], fd, rgx, rgy, rgz, rlap,
+                               geth, getg, getf, dsum);
       };
-      auto getg = [&](int i) {
-        const bool b = (cz<27>(i) > 0 && lo) || (cz<27>(i) < 0 && hi);
-        return Store<S>::ld_s(gz + ((size_t)i * G::TYB + ty) * G::W + (b ? col : col - cx<27>(i)));
-      };
-      auto getf = [&](int i) {
-        if constexpr (QF > 0) {
-          const bool b = (cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi);
-          const R v = Store<S>::ld_s(hfz + ((size_t)(QH + i) * (G::TYB + 2) + ty + 1) * G::W +
-                                     (b ? col : col - cx<QF>(i))) +
-                      (R)weight<QF>(i) * shf;
-          return b ? (-v + (R)(2.0 * weight<QF>(i)) * (R)(cz<QF>(i) > 0 ? P.T_bottom : P.T_top)) : v;
-        } else {
-          return (R)0;
-        }
-      };
-      cell_update<S, QH, QF>(P, A, x, y, z, cell_index(P, x, y, z), mode, pc[c0], tc[c0], fd, rgx,
-                             rgy, rgz, rlap, geth, getg, getf, dsum);
+      if (lo || hi) cell_step(std::true_type{});
+      else cell_step(std::false_type{});
     }
     if (__syncthreads_or(!ok)) { ok = false; break; }
   }

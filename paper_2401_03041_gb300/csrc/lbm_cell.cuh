@@ -35,19 +35,20 @@ __device__ __forceinline__ size_t cell_index(const DevParams& P, int x, int y, i
 // Gaussian sources (Eq. HeatSource, r <= d) plus heater patches (by index).
 template <class R>
 __device__ __forceinline__ R heat_source(const DevParams& P, int x, int y, int z) {
+  const auto& rp = RP<R>(P);
   R q = 0;
   for (int k = 0; k < P.nsrc; ++k) {
-    const R dx = (R)x + (R)0.5 - (R)P.src[k][0];
-    const R dy = (R)y + (R)0.5 - (R)P.src[k][1];
-    const R dz = (R)z + (R)0.5 - (R)P.src[k][2];
+    const R dx = (R)x + (R)0.5 - (R)rp.src[k][0];
+    const R dy = (R)y + (R)0.5 - (R)rp.src[k][1];
+    const R dz = (R)z + (R)0.5 - (R)rp.src[k][2];
     const R r2 = dx * dx + dy * dy + dz * dz;
-    const R w = (R)P.src[k][4];
-    if (P.src[k][5] < 0.0 || r2 <= (R)P.src[k][5]) q += (R)P.src[k][3] * exp((R)-2 * r2 / (w * w));
+    const R w = (R)rp.src[k][4];
+    if (rp.src[k][5] < (R)0 || r2 <= (R)rp.src[k][5]) q += (R)rp.src[k][3] * exp((R)-2 * r2 / (w * w));
   }
   if (P.npatch > 0 && z == P.patch_z) {
     for (int k = 0; k < P.npatch; ++k) {
       if (x >= P.px0[k] && x < P.px0[k] + P.patch_sx && y >= P.py0[k] && y < P.py0[k] + P.patch_sy)
-        q += (R)P.pI[k];
+        q += (R)rp.pI[k];
     }
   }
   return q;
@@ -117,10 +118,11 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
                                             typename Store<S>::R rgz, typename Store<S>::R rlap,
                                             GH geth, GG getg, GF getf, double* dsum) {
   using R = typename Store<S>::R;
+  const auto& rp = RP<R>(P);
   const R gpx = fdv.gpx, gpy = fdv.gpy, gpz = fdv.gpz, lp = fdv.lp;
-  const R Gx = (R)P.grad[0], Gy = (R)P.grad[1], Gz = (R)P.grad[2];
-  const R Ttot = Tc + Gx * ((R)x + (R)0.5 - (R)P.origin[0]) + Gy * ((R)y + (R)0.5 - (R)P.origin[1]) +
-                 Gz * ((R)z + (R)0.5 - (R)P.origin[2]);
+  const R Gx = (R)rp.grad[0], Gy = (R)rp.grad[1], Gz = (R)rp.grad[2];
+  const R Ttot = Tc + Gx * ((R)x + (R)0.5 - (R)rp.origin[0]) + Gy * ((R)y + (R)0.5 - (R)rp.origin[1]) +
+                 Gz * ((R)z + (R)0.5 - (R)rp.origin[2]);
   const R gTx = fdv.gtx + Gx, gTy = fdv.gty + Gy, gTz = fdv.gtz + Gz;
 
   // ---- a2 hydro moments of the pulled g (zeroth, first, second)
@@ -138,18 +140,18 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
   }
 
   // ---- a4/a5 forces
-  const R xi = (R)P.xi;
-  const R sigma = (R)P.sigma_ref + (R)P.sigma_T * (Ttot - (R)P.T_ref);
+  const R xi = (R)rp.xi;
+  const R sigma = (R)rp.sigma_ref + (R)rp.sigma_T * (Ttot - (R)rp.T_ref);
   const R beta = (R)12 * sigma / xi;
   const R kap = (R)1.5 * sigma * xi;
   const R mu = (R)4 * beta * phi * (phi - (R)1) * (phi - (R)0.5) - kap * lp;
   const R g2 = gpx * gpx + gpy * gpy + gpz * gpz;
   const R tdp = gTx * gpx + gTy * gpy + gTz * gpz;
-  const R cm = (R)1.5 * xi * (R)P.sigma_T;
-  const R rho = (R)P.rho_L + phi * (R)(P.rho_H - P.rho_L);
-  const R Fx = mu * gpx + cm * (g2 * gTx - tdp * gpx) + rho * (R)P.gravity[0];
-  const R Fy = mu * gpy + cm * (g2 * gTy - tdp * gpy) + rho * (R)P.gravity[1];
-  const R Fz = mu * gpz + cm * (g2 * gTz - tdp * gpz) + rho * (R)P.gravity[2];
+  const R cm = (R)1.5 * xi * (R)rp.sigma_T;
+  const R rho = (R)rp.rho_L + phi * (R)(rp.rho_H - rp.rho_L);
+  const R Fx = mu * gpx + cm * (g2 * gTx - tdp * gpx) + rho * (R)rp.gravity[0];
+  const R Fy = mu * gpy + cm * (g2 * gTy - tdp * gpy) + rho * (R)rp.gravity[1];
+  const R Fz = mu * gpz + cm * (g2 * gTz - tdp * gpz) + rho * (R)rp.gravity[2];
   const R irho = (R)1 / rho;
   const R ax = Fx * irho, ay = Fy * irho, az = Fz * irho;
   // ---- a6 velocity
@@ -186,7 +188,7 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
 
   // ---- a8 g collision (central moments, closed form)
   {
-    const R om = (R)1 / ((R)P.tau_L + phi * (R)(P.tau_H - P.tau_L));
+    const R om = (R)1 / ((R)rp.tau_L + phi * (R)(rp.tau_H - rp.tau_L));
     const R k1 = (R)1 - om;
     const R p3 = pst * (R)(1.0 / 3.0);
     const R Pxx = k1 * (sxx - p3 - ux * ux + ux * ax);
@@ -245,12 +247,12 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
   }
   // ---- a7 h collision (single rate + Guo source of the interface force)
   {
-    const R nrm = (R)1 / (sqrt(g2) + (R)P.eps_n);
+    const R nrm = (R)1 / (sqrt(g2) + (R)rp.eps_n);
     const R th = (R)4 * phi * ((R)1 - phi) / xi * nrm;
     const R fpx = th * gpx, fpy = th * gpy, fpz = th * gpz;
-    const R om = (R)P.omega_phi;
+    const R om = (R)rp.omega_phi;
     const R sc = (R)1 - (R)0.5 * om;
-    const R sh = (R)P.shift_h;
+    const R sh = (R)rp.shift_h;
     const R e0 = (R)1 - (R)1.5 * uu;
     {
       const R w = (R)weight<QH>(0);
@@ -277,8 +279,8 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
   const R q = heat_source<R>(P, x, y, z);
   const R uG = ux * Gx + uy * Gy + uz * Gz;
   if constexpr (QF > 0) {
-    const R om = (R)P.omega_T;
-    const R sf = (R)P.shift_f;
+    const R om = (R)rp.omega_T;
+    const R sf = (R)rp.shift_f;
     const R e0 = (R)1 - (R)1.5 * uu;
     const R qs = q - uG;
     {
@@ -307,7 +309,7 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
     } else {
       gx_ = rgx; gy_ = rgy; gz_ = rgz; lap = rlap;
     }
-    const R K1 = -(ux * (gx_ + Gx) + uy * (gy_ + Gy) + uz * (gz_ + Gz)) + (R)P.alpha * lap + q;
+    const R K1 = -(ux * (gx_ + Gx) + uy * (gy_ + Gy) + uz * (gz_ + Gz)) + (R)rp.alpha * lap + q;
     A.u_out[cell] = ux;
     A.u_out[P.N + cell] = uy;
     A.u_out[2 * P.N + cell] = uz;

@@ -88,24 +88,37 @@ constexpr int TY = 8;
 constexpr int kMaxSources = 64;
 constexpr int kMaxPatches = 64;
 
+// Scalar model parameters in one precision.  The kernels read the copy of
+// their compute type, so the FP32 path carries no double arithmetic or
+// conversions.
+template <class R>
+struct RealParams {
+  R omega_phi, omega_T, tau_L, tau_H;
+  R rho_L, rho_H, xi, sigma_ref, sigma_T, T_ref, alpha;
+  R gravity[3];
+  R T_bottom, T_top;
+  R grad[3], origin[3];
+  R eps_n;
+  R shift_h, shift_f;             // storage shifts (w_i * shift) for h and f
+  R src[kMaxSources][6];          // x, y, z, Q, w, d^2 (d^2 < 0: no cut-off)
+  R pI[kMaxPatches];
+};
+
 // Everything a kernel needs, passed by value (lives in the constant bank).
 struct DevParams {
   int nx, ny, nz, walls;
   long long N;
-  double omega_phi, omega_T, tau_L, tau_H;
-  double rho_L, rho_H, xi, sigma_ref, sigma_T, T_ref, alpha;
-  double gravity[3];
-  double T_bottom, T_top;
-  double grad[3], origin[3];
-  double eps_n;
-  double shift_h, shift_f;        // storage shifts (w_i * shift) for h and f
   int rk_iso;
   int nsrc;
-  double src[kMaxSources][6];     // x, y, z, Q, w, d^2 (d^2 < 0: no cut-off)
   int npatch, patch_z, patch_sx, patch_sy;
   int px0[kMaxPatches], py0[kMaxPatches];
-  double pI[kMaxPatches];
+  RealParams<double> pd;
+  RealParams<float> pf;
 };
+
+template <class R> __host__ __device__ __forceinline__ const RealParams<R>& RP(const DevParams& P);
+template <> __host__ __device__ __forceinline__ const RealParams<double>& RP<double>(const DevParams& P) { return P.pd; }
+template <> __host__ __device__ __forceinline__ const RealParams<float>& RP<float>(const DevParams& P) { return P.pf; }
 
 // Kernel modes (bit set).
 enum : int { MODE_COLLIDE = 1, MODE_DIAG = 2, MODE_MACRO = 4 };

@@ -39,12 +39,13 @@ __device__ __forceinline__ typename Store<S>::R pull(const DevParams& P, const S
                                                      int i, int x, int y, int z,
                                                      typename Store<S>::R shift) {
   using R = typename Store<S>::R;
+  const auto& rp = RP<R>(P);
   const int zs = z - cz<Q>(i);
   const R wsh = (R)weight<Q>(i) * shift;
   if (P.walls && (zs < 0 || zs >= P.nz)) {
     const R v = Store<S>::ld(base + (size_t)opp<Q>(i) * P.N + cell_index(P, x, y, z)) + wsh;
     if (ABB) {
-      const R Tw = (R)(zs < 0 ? P.T_bottom : P.T_top);
+      const R Tw = (R)(zs < 0 ? rp.T_bottom : rp.T_top);
       return -v + (R)(2.0 * weight<Q>(i)) * Tw;
     }
     return v;
@@ -92,6 +93,7 @@ template <class S, int QH, int QF>
 __global__ void __launch_bounds__(NTHREADS)
 step_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, int zchunk, int mode) {
   using R = typename Store<S>::R;
+  const auto& rp = RP<R>(P);
   __shared__ R s_phi[3][HP];
   __shared__ R s_T[3][HP];
 
@@ -102,7 +104,7 @@ step_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, int zc
   const int z1 = min(z0 + zchunk, P.nz);
   const int x = x0 + tx, y = y0 + ty;
   const bool active = (x < P.nx) && (y < P.ny);
-  const R shh = (R)P.shift_h, shf = (R)P.shift_f;
+  const R shh = (R)rp.shift_h, shf = (R)rp.shift_f;
 
   // phi and T on the (TX+2) x (TY+2) plane zp -> slot
   auto fill = [&](int zp, int slot) {
@@ -121,7 +123,7 @@ step_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, int zc
       R T;
       if constexpr (QF > 0) T = pulled_sum<QF, true>(P, A.f_src, gx, gy, zz, shf);
       else T = A.T[cell_index(P, gx, gy, zz)];
-      if (ghost) T = (R)(2.0 * (zp < 0 ? P.T_bottom : P.T_top)) - T;  // phi: mirror
+      if (ghost) T = (R)2 * (zp < 0 ? rp.T_bottom : rp.T_top) - T;  // phi: mirror
       s_phi[slot][k] = phi;
       s_T[slot][k] = T;
     }
