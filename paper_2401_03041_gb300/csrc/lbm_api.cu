@@ -197,6 +197,11 @@ StepPtrs<S, typename Store<S>::R> ptrs(lbm_domain* d) {
   A.rk_acc = d->th == LBM_TH_RK4;
   A.diag_partials = (double*)at(d, d->L.partials);
   A.error_flag = (int*)at(d, d->L.errflag);
+  for (int i = 0; i < 27; ++i) {
+    A.hd[i] = i < d->qh ? A.h_dst + (size_t)i * d->N : nullptr;
+    A.gd[i] = A.g_dst + (size_t)i * d->N;
+    A.fd[i] = i < d->qf ? A.f_dst + (size_t)i * d->N : nullptr;
+  }
   return A;
 }
 

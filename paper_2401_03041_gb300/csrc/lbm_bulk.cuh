@@ -127,68 +127,67 @@ struct BulkSmem {
 
 // Issue the row copies of one stage.  Task t enumerates (direction, row);
 // every thread takes a strided subset.
-//   kind 0 (HF): rows r = 0..TYB+1 are halo rows y0 - 1 + r of plane p;
+//   KIND 0 (HF): rows r = 0..TYB+1 are halo rows y0 - 1 + r of plane p;
 //                directions 0..QH-1 from h, QH..QH+QF-1 from f.
-//   kind 1 (G):  rows r = 0..TYB-1 are rows y0 + r of plane p; g directions.
-template <class S, int QH, int QF>
+//   KIND 1 (G):  rows r = 0..TYB-1 are rows y0 + r of plane p; g directions.
+// Only planes next to a wall can need bounce-back rows; elsewhere the
+// select-free branch runs (uniform per stage).
+template <class S, int QH, int QF, int KIND>
 __device__ __forceinline__ void issue_stage(const DevParams& P, const S* hsrc, const S* gsrc,
-                                            const S* fsrc, S* dst_stage, uint64_t* bar, int kind,
-                                            int p, int x0, int y0, int tid, int nthr) {
+                                            const S* fsrc, S* dst_stage, uint64_t* bar, int p,
+                                            int x0, int y0, int tid, int nthr) {
   using G = BulkGeom<S>;
-  const int nrows = kind == 0 ? G::TYB + 2 : G::TYB;
-  const int ndir = kind == 0 ? QH + QF : 27;
-  const int ntask = nrows * ndir;
+  constexpr int nrows = KIND == 0 ? G::TYB + 2 : G::TYB;
+  constexpr int ndir = KIND == 0 ? QH + QF : 27;
+  constexpr int ntask = nrows * ndir;
   // plane whose tile this is (walls: the ghost planes reuse the boundary plane)
   int pe = p;
   if (P.walls) pe = p < 0 ? 0 : (p >= P.nz ? P.nz - 1 : p);
   else pe = p < 0 ? p + P.nz : (p >= P.nz ? p - P.nz : p);
+  const bool wall_plane = P.walls && (pe == 0 || pe == P.nz - 1);
   const int xs = x0 - G::GXP;
+  // CTA-uniform x segmentation of every row: [xs, xs + W) mod nx
+  const int seg_a = xs < 0 ? -xs : (xs + G::W > P.nx ? P.nx - xs : G::W);
+  const int src_x0 = xs < 0 ? P.nx - seg_a : xs;   // first segment start
+  const size_t plane = (size_t)P.ny * P.nx;
   for (int t = tid; t < ntask; t += nthr) {
-    const int d = t / nrows, r = t % nrows;
+    const int d = t / nrows, r = t - (t / nrows) * nrows;
     const S* base;
-    int k27;
-    if (kind == 1) {
+    int k27, q;
+    if (KIND == 1) {
       base = gsrc;
       k27 = d;
+      q = d;
     } else if (d < QH) {
       base = hsrc;
       k27 = rt_to27<QH>(d);
+      q = d;
     } else {
       base = fsrc;
-      k27 = d - QH;   // Q7/Q19/Q27 are prefixes of the D3Q27 order; Q15 handled below
-      if (QF == 15) k27 = rt_to27<15>(k27);
+      q = d - QH;
+      k27 = QF == 15 ? rt_to27<15>(q) : q;   // Q7/Q19/Q27 are prefixes of the D3Q27 order
     }
-    const int cxv = kDir27.c[k27][0], cyv = kDir27.c[k27][1], czv = kDir27.c[k27][2];
-    int yr = y0 + r - (kind == 0 ? 1 : 0);
+    int yr = y0 + r - (KIND == 0 ? 1 : 0);
     yr = yr < 0 ? yr + P.ny : (yr >= P.ny ? yr - P.ny : yr);
-    const int zsrc = pe - czv;
-    int q, zz, yy;
-    if (P.walls && (zsrc < 0 || zsrc >= P.nz)) {
+    const int czv = kDir27.c[k27][2];
+    int zz = pe - czv, yy;
+    if (wall_plane && (zz < 0 || zz >= P.nz)) {
       // bounce-back: opposite direction, same cell
       const int o27 = kDir27.opp[k27];
-      q = (kind == 0 && d >= QH) ? (QF == 15 ? rt_from27<15>(o27) : o27)
-                                 : (kind == 0 ? rt_from27<QH>(o27) : o27);
+      if (KIND == 1) q = o27;
+      else if (d < QH) q = rt_from27<QH>(o27);
+      else q = QF == 15 ? rt_from27<15>(o27) : o27;
       zz = pe;
       yy = yr;
     } else {
-      q = (kind == 0 && d >= QH) ? d - QH : d;
-      zz = zsrc < 0 ? zsrc + P.nz : (zsrc >= P.nz ? zsrc - P.nz : zsrc);
-      yy = yr - cyv;
+      zz = zz < 0 ? zz + P.nz : (zz >= P.nz ? zz - P.nz : zz);
+      yy = yr - kDir27.c[k27][1];
       yy = yy < 0 ? yy + P.ny : (yy >= P.ny ? yy - P.ny : yy);
     }
-    const S* row = base + (size_t)q * P.N + ((size_t)zz * P.ny + yy) * P.nx;
-    S* dst = dst_stage + ((size_t)d * nrows + r) * G::W;
-    if (xs < 0) {
-      const int a = -xs;  // elements taken from the end of the row
-      bulk_copy_g2s(dst, row + (P.nx - a), a * sizeof(S), bar);
-      bulk_copy_g2s(dst + a, row, (G::W - a) * sizeof(S), bar);
-    } else if (xs + G::W > P.nx) {
-      const int a = P.nx - xs;  // elements up to the end of the row
-      bulk_copy_g2s(dst, row + xs, a * sizeof(S), bar);
-      bulk_copy_g2s(dst + a, row, (G::W - a) * sizeof(S), bar);
-    } else {
-      bulk_copy_g2s(dst, row + xs, G::W * sizeof(S), bar);
-    }
+    const S* row = base + (size_t)q * P.N + (size_t)zz * plane + (size_t)yy * P.nx;
+    S* dst = dst_stage + (d * nrows + r) * G::W;
+    bulk_copy_g2s(dst, row + src_x0, seg_a * sizeof(S), bar);
+    if (seg_a < G::W) bulk_copy_g2s(dst + seg_a, row, (G::W - seg_a) * sizeof(S), bar);
   }
 }
 
@@ -311,10 +310,10 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
     }
     __syncthreads();
     for (int p = z0 - 1; p <= z0 + 1; ++p) {
-      issue_stage<S, QH, QF>(P, A.h_src, A.g_src, A.f_src, hf_ptr(p), &bar[hf_slot(p)], 0, p, x0, y0, tid, NT);
+      issue_stage<S, QH, QF, 0>(P, A.h_src, A.g_src, A.f_src, hf_ptr(p), &bar[hf_slot(p)], p, x0, y0, tid, NT);
       mark(hf_slot(p), hf_par(p));
     }
-    issue_stage<S, QH, QF>(P, A.h_src, A.g_src, A.f_src, g_ptr(z0), &bar[3 + g_slot(z0)], 1, z0, x0, y0, tid, NT);
+    issue_stage<S, QH, QF, 1>(P, A.h_src, A.g_src, A.f_src, g_ptr(z0), &bar[3 + g_slot(z0)], z0, x0, y0, tid, NT);
     mark(3 + g_slot(z0), g_par(z0));
     ok = ok && wait_slot(hf_slot(z0 - 1), hf_par(z0 - 1));
     if (ok) sum_plane(z0 - 1);
@@ -333,11 +332,11 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
     }
     if (__syncthreads_or(!ok)) { ok = false; break; }
     if (more_hf) {
-      issue_stage<S, QH, QF>(P, A.h_src, A.g_src, A.f_src, hf_ptr(z + 2), &bar[hf_slot(z + 2)], 0, z + 2, x0, y0, tid, NT);
+      issue_stage<S, QH, QF, 0>(P, A.h_src, A.g_src, A.f_src, hf_ptr(z + 2), &bar[hf_slot(z + 2)], z + 2, x0, y0, tid, NT);
       mark(hf_slot(z + 2), hf_par(z + 2));
     }
     if (more_g) {
-      issue_stage<S, QH, QF>(P, A.h_src, A.g_src, A.f_src, g_ptr(z + 1), &bar[3 + g_slot(z + 1)], 1, z + 1, x0, y0, tid, NT);
+      issue_stage<S, QH, QF, 1>(P, A.h_src, A.g_src, A.f_src, g_ptr(z + 1), &bar[3 + g_slot(z + 1)], z + 1, x0, y0, tid, NT);
       mark(3 + g_slot(z + 1), g_par(z + 1));
     }
     if (active) {

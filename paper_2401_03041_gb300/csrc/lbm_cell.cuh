@@ -72,26 +72,27 @@ struct Stencil27 {
   template <int HXv>
   __device__ __forceinline__ void eval(const R* pm, const R* pc, const R* pp, const R* tm,
                                        const R* tc, const R* tp, int c0) {
+    // sum over the 13 opposite pairs (c, -c): gradient from v(c) - v(-c),
+    // Laplacian from v(c) + v(-c) - 2 v(0) (exact zeros on uniform fields)
     const R phi = pc[c0], T = tc[c0];
     gpx = gpy = gpz = lp = gtx = gty = gtz = lt = 0;
 #pragma unroll
     for (int k = 1; k < 27; ++k) {
+      if (!pair_first<27>(k)) continue;
       const R* P_ = q27_cz(k) == 0 ? pc : (q27_cz(k) > 0 ? pp : pm);
       const R* T_ = q27_cz(k) == 0 ? tc : (q27_cz(k) > 0 ? tp : tm);
+      const R* Pm = q27_cz(k) == 0 ? pc : (q27_cz(k) > 0 ? pm : pp);
+      const R* Tm = q27_cz(k) == 0 ? tc : (q27_cz(k) > 0 ? tm : tp);
       const int o = c0 + q27_cy(k) * HXv + q27_cx(k);
-      const R vp = P_[o], vt = T_[o];
+      const int om = c0 - q27_cy(k) * HXv - q27_cx(k);
+      const R vp = P_[o], vm = Pm[om], tp_ = T_[o], tm_ = Tm[om];
       const R w = (R)weight<27>(k);
-      lp += w * (vp - phi);
-      lt += w * (vt - T);
-      if (pair_first<27>(k)) {
-        const R* Pm = q27_cz(k) == 0 ? pc : (q27_cz(k) > 0 ? pm : pp);
-        const R* Tm = q27_cz(k) == 0 ? tc : (q27_cz(k) > 0 ? tm : tp);
-        const int om = c0 - q27_cy(k) * HXv - q27_cx(k);
-        const R dp = vp - Pm[om], dt = vt - Tm[om];
-        if (q27_cx(k)) { gpx += (R)q27_cx(k) * w * dp; gtx += (R)q27_cx(k) * w * dt; }
-        if (q27_cy(k)) { gpy += (R)q27_cy(k) * w * dp; gty += (R)q27_cy(k) * w * dt; }
-        if (q27_cz(k)) { gpz += (R)q27_cz(k) * w * dp; gtz += (R)q27_cz(k) * w * dt; }
-      }
+      lp += w * ((vp - phi) + (vm - phi));
+      lt += w * ((tp_ - T) + (tm_ - T));
+      const R dp = vp - vm, dt = tp_ - tm_;
+      if (q27_cx(k)) { gpx += (R)q27_cx(k) * w * dp; gtx += (R)q27_cx(k) * w * dt; }
+      if (q27_cy(k)) { gpy += (R)q27_cy(k) * w * dp; gty += (R)q27_cy(k) * w * dt; }
+      if (q27_cz(k)) { gpz += (R)q27_cz(k) * w * dp; gtz += (R)q27_cz(k) * w * dt; }
     }
     gpx *= (R)3; gpy *= (R)3; gpz *= (R)3; lp *= (R)6;
     gtx *= (R)3; gty *= (R)3; gtz *= (R)3; lt *= (R)6;
@@ -125,18 +126,22 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
                  Gz * ((R)z + (R)0.5 - (R)rp.origin[2]);
   const R gTx = fdv.gtx + Gx, gTy = fdv.gty + Gy, gTz = fdv.gtz + Gz;
 
-  // ---- a2 hydro moments of the pulled g (zeroth, first, second)
-  R pst = 0, jx = 0, jy = 0, jz = 0, sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
+  // ---- a2 hydro moments of the pulled g (zeroth, first, second), per
+  // opposite pair: s = g(c) + g(-c) enters even moments, d = g(c) - g(-c) odd
+  R pst = getg(0), jx = 0, jy = 0, jz = 0, sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
 #pragma unroll
-  for (int i = 0; i < 27; ++i) {
-    const R v = getg(i);
-    pst += v;
-    if (cx<27>(i)) { jx += (R)cx<27>(i) * v; sxx += v; }
-    if (cy<27>(i)) { jy += (R)cy<27>(i) * v; syy += v; }
-    if (cz<27>(i)) { jz += (R)cz<27>(i) * v; szz += v; }
-    if (cx<27>(i) * cy<27>(i)) sxy += (R)(cx<27>(i) * cy<27>(i)) * v;
-    if (cx<27>(i) * cz<27>(i)) sxz += (R)(cx<27>(i) * cz<27>(i)) * v;
-    if (cy<27>(i) * cz<27>(i)) syz += (R)(cy<27>(i) * cz<27>(i)) * v;
+  for (int i = 1; i < 27; ++i) {
+    if (!pair_first<27>(i)) continue;
+    const R a_ = getg(i), b_ = getg(opp<27>(i));
+    const R s_ = a_ + b_, d_ = a_ - b_;
+    const int ex = cx<27>(i), ey = cy<27>(i), ez = cz<27>(i);
+    pst += s_;
+    if (ex) { jx += (R)ex * d_; sxx += s_; }
+    if (ey) { jy += (R)ey * d_; syy += s_; }
+    if (ez) { jz += (R)ez * d_; szz += s_; }
+    if (ex * ey) sxy += (R)(ex * ey) * s_;
+    if (ex * ez) sxz += (R)(ex * ez) * s_;
+    if (ey * ez) syz += (R)(ey * ez) * s_;
   }
 
   // ---- a4/a5 forces
@@ -229,8 +234,7 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
       const R r2 = ex == 0 ? (R)-1 : (R)0.5;
       return r0 * B0 + r1 * B1 + r2 * B2;
     };
-    S* dst = A.g_dst;
-    Store<S>::st(dst + cell, (R)weight<27>(0) * base + neq_of(0, 0, 0));
+    Store<S>::st(A.gd[0] + cell, (R)weight<27>(0) * base + neq_of(0, 0, 0));
 #pragma unroll
     for (int i = 1; i < 27; ++i) {
       if (!pair_first<27>(i)) continue;
@@ -241,8 +245,8 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
       // g^eq + S/2 = w [p* + 3cu + 9/2 cu^2 - 3/2 uu + 3/2 (ca - ua) + 9/2 cu ca]
       const R even = w * (base + (R)4.5 * cu * (cu + ca));
       const R odd = w * ((R)3 * cu + (R)1.5 * ca);
-      Store<S>::st(dst + (size_t)i * P.N + cell, even + odd + neq_of(ex, ey, ez));
-      Store<S>::st(dst + (size_t)opp<27>(i) * P.N + cell, even - odd + neq_of(-ex, -ey, -ez));
+      Store<S>::st(A.gd[i] + cell, even + odd + neq_of(ex, ey, ez));
+      Store<S>::st(A.gd[opp<27>(i)] + cell, even - odd + neq_of(-ex, -ey, -ez));
     }
   }
   // ---- a7 h collision (single rate + Guo source of the interface force)
@@ -258,7 +262,7 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
       const R w = (R)weight<QH>(0);
       const R hs = geth(0);
       const R hn = hs - om * (hs - w * phi * e0);
-      Store<S>::st(A.h_dst + cell, hn - w * sh);
+      Store<S>::st(A.hd[0] + cell, hn - w * sh);
     }
 #pragma unroll
     for (int i = 1; i < QH; ++i) {
@@ -271,8 +275,8 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
       const R odd = w * phi * (R)3 * cu;
       const R src = sc * w * cf;
       const R hi = geth(i), hj = geth(j);
-      Store<S>::st(A.h_dst + (size_t)i * P.N + cell, hi - om * (hi - (even + odd)) + src - w * sh);
-      Store<S>::st(A.h_dst + (size_t)j * P.N + cell, hj - om * (hj - (even - odd)) - src - w * sh);
+      Store<S>::st(A.hd[i] + cell, hi - om * (hi - (even + odd)) + src - w * sh);
+      Store<S>::st(A.hd[j] + cell, hj - om * (hj - (even - odd)) - src - w * sh);
     }
   }
   // ---- a9 / a9' thermal
@@ -287,7 +291,7 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
       const R w = (R)weight<QF>(0);
       const R fs = getf(0);
       const R fn = fs - om * (fs - w * Tc * e0) + w * qs;
-      Store<S>::st(A.f_dst + cell, fn - w * sf);
+      Store<S>::st(A.fd[0] + cell, fn - w * sf);
     }
 #pragma unroll
     for (int i = 1; i < QF; ++i) {
@@ -298,8 +302,8 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
       const R even = w * Tc * (e0 + (R)4.5 * cu * cu);
       const R odd = w * Tc * (R)3 * cu;
       const R fi = getf(i), fj = getf(j);
-      Store<S>::st(A.f_dst + (size_t)i * P.N + cell, fi - om * (fi - (even + odd)) + w * qs - w * sf);
-      Store<S>::st(A.f_dst + (size_t)j * P.N + cell, fj - om * (fj - (even - odd)) + w * qs - w * sf);
+      Store<S>::st(A.fd[i] + cell, fi - om * (fi - (even + odd)) + w * qs - w * sf);
+      Store<S>::st(A.fd[j] + cell, fj - om * (fj - (even - odd)) + w * qs - w * sf);
     }
   } else {
     // RK stage 1: K1 = R(T^n) with the local u of this step

@@ -137,6 +137,11 @@ struct StepPtrs {
   void* macro_out; int macro_dtype; unsigned macro_mask;
   double* diag_partials;          // [grid blocks][kDiagVals] (MODE_DIAG)
   int* error_flag;                // set to 1 by a CTA whose bounded wait ran out
+  // per-direction destination rows (dst + i * N), so a store address is one
+  // multiply-add of the cell index onto a constant-bank pointer
+  S* hd[27];
+  S* gd[27];
+  S* fd[27];
 };
 
 }  // namespace lbm
