@@ -57,6 +57,10 @@ size_t bulk_smem_bytes(int prec, int qh, int qf) {
   return bulk_bytes_s<__half>(qh, qf);
 }
 
+int bulk_tile_cols(int prec) {
+  return prec == 0 ? BulkGeom<double>::TXB : (prec == 1 ? BulkGeom<float>::TXB : BulkGeom<__half>::TXB);
+}
+
 int bulk_tile_rows(int prec) {
   return prec == 0 ? BulkGeom<double>::TYB : (prec == 1 ? BulkGeom<float>::TYB : BulkGeom<__half>::TYB);
 }

@@ -19,6 +19,7 @@ void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
 // and the largest a CTA may use; also its tile height.
 size_t bulk_smem_bytes(int prec, int qh, int qf);
 int bulk_tile_rows(int prec);
+int bulk_tile_cols(int prec);
 constexpr size_t kMaxDynSmem = 232448;
 
 template <class S, int QH, int QF>

@@ -69,7 +69,7 @@ bool bulk_ok(int nx, int ny, lbm_precision prec, int qh, int qf) {
   const int s = prec == LBM_FP64 ? 8 : (prec == LBM_FP32 ? 4 : 2);
   const int gxp = 16 / s;
   if ((nx * s) % 16 != 0) return false;
-  if (nx < TX + 2 * gxp) return false;
+  if (nx < bulk_tile_cols((int)prec) + 2 * gxp) return false;
   if (ny < 2 * bulk_tile_rows((int)prec)) return false;
   return bulk_smem_bytes((int)prec, qh, qf) <= kMaxDynSmem;
 }
@@ -78,7 +78,8 @@ Geometry geometry(int nx, int ny, int nz, lbm_precision prec, int qh, int qf) {
   Geometry g;
   g.bulk = bulk_ok(nx, ny, prec, qh, qf) ? 1 : 0;
   const int rows = g.bulk ? bulk_tile_rows((int)prec) : TY;
-  const int bx = (nx + TX - 1) / TX, by = (ny + rows - 1) / rows;
+  const int cols_ = g.bulk ? bulk_tile_cols((int)prec) : TX;
+  const int bx = (nx + cols_ - 1) / cols_, by = (ny + rows - 1) / rows;
   const long long cols = (long long)bx * by;
   const char* env = std::getenv("LBM_ZCHUNK");
   int zc = env ? std::atoi(env) : 0;

@@ -102,12 +102,13 @@ __device__ __forceinline__ int rt_from27(int k) { return (Q == 15 && k >= 19) ? 
 template <class S>
 struct BulkGeom {
   static constexpr int GXP = 16 / (int)sizeof(S);       // halo columns on each side
-  static constexpr int W = TX + 2 * GXP;                // staged row length (elements)
-  static constexpr int TYB = sizeof(S) == 8 ? 4 : 8;    // rows per CTA
-  static constexpr int HXB = TX + 2;                    // phi/T plane pitch
+  static constexpr int TXB = sizeof(S) == 8 ? 32 : 64;  // columns per CTA
+  static constexpr int W = TXB + 2 * GXP;               // staged row length (elements)
+  static constexpr int TYB = 4;                         // rows per CTA
+  static constexpr int HXB = TXB + 2;                   // phi/T plane pitch
   static constexpr int HYB = TYB + 2;
   static constexpr int HPB = HXB * HYB;
-  static constexpr int NT = TX * TYB;
+  static constexpr int NT = TXB * TYB;
 };
 
 template <class S, int QH, int QF>
@@ -208,8 +209,8 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
   uint64_t* bar = (uint64_t*)(smem + L::off_bar);  // [0..2] HF ring, [3..4] G ring
 
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int tid = ty * TX + tx;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * G::TYB;
+  const int tid = ty * G::TXB + tx;
+  const int x0 = blockIdx.x * G::TXB, y0 = blockIdx.y * G::TYB;
   const int z0 = blockIdx.z * zchunk;
   const int z1 = min(z0 + zchunk, P.nz);
   const int x = x0 + tx, y = y0 + ty;

@@ -101,10 +101,12 @@ def bulk_fits(precision, q_phase, thermal):
     qf = int(thermal[3:]) if thermal.startswith("D3Q") else 0
     nhf = q_phase + qf
     s = {"fp64": 8, "fp32": 4, "fp16": 2}[precision]
-    rows = 4 if s == 8 else 8
-    W = 32 + 2 * (16 // s)
+    rows = 4
+    cols = 32 if s == 8 else 64
+    W = cols + 2 * (16 // s)
     rs = 8 if s == 8 else 4
-    smem = 3 * nhf * (rows + 2) * W * s + 2 * 27 * rows * W * s + 6 * 34 * (rows + 2) * rs + 64
+    smem = (3 * nhf * (rows + 2) * W * s + 2 * 27 * rows * W * s
+            + 6 * (cols + 2) * (rows + 2) * rs + 64)
     return smem <= 232448
 
 

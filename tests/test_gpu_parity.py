@@ -113,7 +113,7 @@ def test_bulk_multi_tile_chunked_fp64(walls, monkeypatch):
 def test_bulk_equals_generic_reduced_precision(precision, thermal):
     """The two kernels compute the same arithmetic: in FP32 / FP16 storage
     they agree to the storage rounding after 20 steps."""
-    w = ragged_workload(thermal, 15, walls=True, precision=precision, shape=(64, 24, 12))
+    w = ragged_workload(thermal, 15, walls=True, precision=precision, shape=(80, 24, 12))
     a = gpu_domain(w, kernel="generic")
     b = gpu_domain(w, kernel="bulk")
     a.step(20)
