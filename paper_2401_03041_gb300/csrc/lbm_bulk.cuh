@@ -303,8 +303,19 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
     return r;
   };
 
+  // Copy schedule: HF(p) lands in slot (p - z0 + 1) % 3, G(p) in (p - z0) % 2.
+  // At the start of iteration z both HF(z + 2) and G(z + 1) are issued into
+  // the slots that iteration z - 1 has just released, so their latency is
+  // hidden behind the whole of iteration z (phi/T sum and collision).  Thread
+  // 0 posts the expected byte counts before the barrier that precedes the
+  // copies.
+  auto expect_for = [&](int z) {
+    if (z + 2 <= z1) mbar_expect_tx(&bar[hf_slot(z + 2)], hf_bytes);
+    if (z + 1 < z1) mbar_expect_tx(&bar[3 + g_slot(z + 1)], g_bytes);
+  };
   if (z0 < z1) {
-    // prologue: HF(z0-1), HF(z0), HF(z0+1), G(z0)
+    // prologue: HF(z0-1), HF(z0), HF(z0+1), G(z0) now; HF(z0+2), G(z0+1) at
+    // the start of the first iteration
     if (tid == 0) {
       for (int p = z0 - 1; p <= z0 + 1; ++p) mbar_expect_tx(&bar[hf_slot(p)], hf_bytes);
       mbar_expect_tx(&bar[3 + g_slot(z0)], g_bytes);
@@ -320,26 +331,26 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
     if (ok) sum_plane(z0 - 1);
     ok = ok && wait_slot(hf_slot(z0), hf_par(z0));
     if (ok) sum_plane(z0);
+    // every thread has waited on HF(z0 - 1), whose slot HF(z0 + 2) reuses
+    if (__syncthreads_or(!ok)) ok = false;
+    if (tid == 0 && ok) expect_for(z0);
+    __syncthreads();
   }
 
   for (int z = z0; z < z1 && ok; ++z) {
-    ok = ok && wait_slot(hf_slot(z + 1), hf_par(z + 1));
-    if (ok) sum_plane(z + 1);
-    ok = ok && wait_slot(3 + g_slot(z), g_par(z));
-    const bool more_hf = z + 2 <= z1, more_g = z + 1 < z1;
-    if (tid == 0 && ok) {
-      if (more_hf) mbar_expect_tx(&bar[hf_slot(z + 2)], hf_bytes);
-      if (more_g) mbar_expect_tx(&bar[3 + g_slot(z + 1)], g_bytes);
-    }
-    if (__syncthreads_or(!ok)) { ok = false; break; }
-    if (more_hf) {
+    // slots of HF(z - 1) and G(z - 1) are free: refill them
+    if (z + 2 <= z1) {
       issue_stage<S, QH, QF, 0>(P, A.h_src, A.g_src, A.f_src, hf_ptr(z + 2), &bar[hf_slot(z + 2)], z + 2, x0, y0, tid, NT);
       mark(hf_slot(z + 2), hf_par(z + 2));
     }
-    if (more_g) {
+    if (z + 1 < z1) {
       issue_stage<S, QH, QF, 1>(P, A.h_src, A.g_src, A.f_src, g_ptr(z + 1), &bar[3 + g_slot(z + 1)], z + 1, x0, y0, tid, NT);
       mark(3 + g_slot(z + 1), g_par(z + 1));
     }
+    ok = ok && wait_slot(hf_slot(z + 1), hf_par(z + 1));
+    if (ok) sum_plane(z + 1);
+    ok = ok && wait_slot(3 + g_slot(z), g_par(z));
+    if (__syncthreads_or(!ok)) { ok = false; break; }
     if (active) {
       const R* pm = s_phi + hf_slot(z - 1) * G::HPB;
       const R* pc = s_phi + hf_slot(z) * G::HPB;
@@ -385,6 +396,7 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
       if (lo || hi) cell_step(std::true_type{});
       else cell_step(std::false_type{});
     }
+    if (tid == 0 && ok) expect_for(z + 1);
     if (__syncthreads_or(!ok)) { ok = false; break; }
   }
 
