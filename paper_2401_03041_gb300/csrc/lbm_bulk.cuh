@@ -247,23 +247,23 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
       const int col = hc + G::GXP - 1;
       const S* rowb = st + (size_t)hr * G::W + col;
       R phi = 0;
-#pragma unroll
-      for (int i = 0; i < QH; ++i) {
+      static_for<0, QH>([&](auto I) {
+        constexpr int i = decltype(I)::value;
         const bool b = BOUNCE && ((cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi));
         const S* rowp = rowb + (size_t)i * (G::TYB + 2) * G::W;
         phi += Store<S>::ld_s(b ? rowp : rowp - cx<QH>(i));
-      }
+      });
       phi += shh;  // sum_i w_i * shift_h
       R T;
       if constexpr (QF > 0) {
         T = 0;
-#pragma unroll
-        for (int i = 0; i < QF; ++i) {
+        static_for<0, QF>([&](auto I) {
+          constexpr int i = decltype(I)::value;
           const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
           const S* rowp = rowb + (size_t)(QH + i) * (G::TYB + 2) * G::W;
           const R v = Store<S>::ld_s(b ? rowp : rowp - cx<QF>(i)) + (R)weight<QF>(i) * shf;
           T += b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? rp.T_bottom : rp.T_top)) : v;
-        }
+        });
       } else {
         int gx = x0 + hc - 1, gy = y0 + hr - 1;
         gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
@@ -370,17 +370,20 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
       const size_t cell = cell_index(P, x, y, z);
       auto cell_step = [&](auto btag) {
         constexpr bool BOUNCE = decltype(btag)::value;
-        auto geth = [&](int i) {
+        auto geth = [&](auto I) {
+          constexpr int i = decltype(I)::value;
           const bool b = BOUNCE && ((cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi));
           const S* p_ = hrow + (size_t)i * (G::TYB + 2) * G::W;
           return Store<S>::ld_s(b ? p_ : p_ - cx<QH>(i)) + (R)weight<QH>(i) * shh;
         };
-        auto getg = [&](int i) {
+        auto getg = [&](auto I) {
+          constexpr int i = decltype(I)::value;
           const bool b = BOUNCE && ((cz<27>(i) > 0 && lo) || (cz<27>(i) < 0 && hi));
           const S* p_ = grow + (size_t)i * G::TYB * G::W;
           return Store<S>::ld_s(b ? p_ : p_ - cx<27>(i));
         };
-        auto getf = [&](int i) {
+        auto getf = [&](auto I) {
+          constexpr int i = decltype(I)::value;
           if constexpr (QF > 0) {
             const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
             const S* p_ = hrow + (size_t)(QH + i) * (G::TYB + 2) * G::W;
@@ -390,7 +393,7 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
             return (R)0;
           }
         };
-        cell_update<S, QH, QF>(P, A, x, y, z, cell, mode, pc[c0], tc[c0], fd, rgx, rgy, rgz, rlap,
+        cell_update<S, QH, QF>(P, A, x, y, z, cell, cell, mode, pc[c0], tc[c0], fd, rgx, rgy, rgz, rlap,
                                geth, getg, getf, dsum);
       };
       if (lo || hi) cell_step(std::true_type{});

@@ -76,24 +76,25 @@ struct Stencil27 {
     // Laplacian from v(c) + v(-c) - 2 v(0) (exact zeros on uniform fields)
     const R phi = pc[c0], T = tc[c0];
     gpx = gpy = gpz = lp = gtx = gty = gtz = lt = 0;
-#pragma unroll
-    for (int k = 1; k < 27; ++k) {
-      if (!pair_first<27>(k)) continue;
-      const R* P_ = q27_cz(k) == 0 ? pc : (q27_cz(k) > 0 ? pp : pm);
-      const R* T_ = q27_cz(k) == 0 ? tc : (q27_cz(k) > 0 ? tp : tm);
-      const R* Pm = q27_cz(k) == 0 ? pc : (q27_cz(k) > 0 ? pm : pp);
-      const R* Tm = q27_cz(k) == 0 ? tc : (q27_cz(k) > 0 ? tm : tp);
-      const int o = c0 + q27_cy(k) * HXv + q27_cx(k);
-      const int om = c0 - q27_cy(k) * HXv - q27_cx(k);
-      const R vp = P_[o], vm = Pm[om], tp_ = T_[o], tm_ = Tm[om];
-      const R w = (R)weight<27>(k);
-      lp += w * ((vp - phi) + (vm - phi));
-      lt += w * ((tp_ - T) + (tm_ - T));
-      const R dp = vp - vm, dt = tp_ - tm_;
-      if (q27_cx(k)) { gpx += (R)q27_cx(k) * w * dp; gtx += (R)q27_cx(k) * w * dt; }
-      if (q27_cy(k)) { gpy += (R)q27_cy(k) * w * dp; gty += (R)q27_cy(k) * w * dt; }
-      if (q27_cz(k)) { gpz += (R)q27_cz(k) * w * dp; gtz += (R)q27_cz(k) * w * dt; }
-    }
+    static_for<1, 27>([&](auto K) {
+      constexpr int k = decltype(K)::value;
+      if constexpr (pair_first<27>(k)) {
+        constexpr int ex = q27_cx(k), ey = q27_cy(k), ez = q27_cz(k);
+        const R* P_ = ez == 0 ? pc : (ez > 0 ? pp : pm);
+        const R* T_ = ez == 0 ? tc : (ez > 0 ? tp : tm);
+        const R* Pm = ez == 0 ? pc : (ez > 0 ? pm : pp);
+        const R* Tm = ez == 0 ? tc : (ez > 0 ? tm : tp);
+        constexpr int o = ey * HXv + ex;
+        const R vp = P_[c0 + o], vm = Pm[c0 - o], tp_ = T_[c0 + o], tm_ = Tm[c0 - o];
+        constexpr R w = (R)weight<27>(k);
+        lp += w * ((vp - phi) + (vm - phi));
+        lt += w * ((tp_ - T) + (tm_ - T));
+        const R dp = vp - vm, dt = tp_ - tm_;
+        if constexpr (ex != 0) { gpx += (R)ex * w * dp; gtx += (R)ex * w * dt; }
+        if constexpr (ey != 0) { gpy += (R)ey * w * dp; gty += (R)ey * w * dt; }
+        if constexpr (ez != 0) { gpz += (R)ez * w * dp; gtz += (R)ez * w * dt; }
+      }
+    });
     gpx *= (R)3; gpy *= (R)3; gpz *= (R)3; lp *= (R)6;
     gtx *= (R)3; gty *= (R)3; gtz *= (R)3; lt *= (R)6;
   }
@@ -112,7 +113,7 @@ __device__ __forceinline__ void rk_std(const R* tm, const R* tc, const R* tp, in
 // a4-a9 for one cell.  GH/GG/GF: accessors i -> pulled (un-shifted) value.
 template <class S, int QH, int QF, class GH, class GG, class GF>
 __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
-                                            int x, int y, int z, size_t cell, int mode,
+                                            int x, int y, int z, size_t cell, size_t pcell, int mode,
                                             typename Store<S>::R phi, typename Store<S>::R Tc,
                                             const Stencil27<typename Store<S>::R>& fdv,
                                             typename Store<S>::R rgx, typename Store<S>::R rgy,
@@ -128,21 +129,23 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
 
   // ---- a2 hydro moments of the pulled g (zeroth, first, second), per
   // opposite pair: s = g(c) + g(-c) enters even moments, d = g(c) - g(-c) odd
-  R pst = getg(0), jx = 0, jy = 0, jz = 0, sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
-#pragma unroll
-  for (int i = 1; i < 27; ++i) {
-    if (!pair_first<27>(i)) continue;
-    const R a_ = getg(i), b_ = getg(opp<27>(i));
-    const R s_ = a_ + b_, d_ = a_ - b_;
-    const int ex = cx<27>(i), ey = cy<27>(i), ez = cz<27>(i);
-    pst += s_;
-    if (ex) { jx += (R)ex * d_; sxx += s_; }
-    if (ey) { jy += (R)ey * d_; syy += s_; }
-    if (ez) { jz += (R)ez * d_; szz += s_; }
-    if (ex * ey) sxy += (R)(ex * ey) * s_;
-    if (ex * ez) sxz += (R)(ex * ez) * s_;
-    if (ey * ez) syz += (R)(ey * ez) * s_;
-  }
+  R pst = getg(std::integral_constant<int, 0>{}), jx = 0, jy = 0, jz = 0, sxx = 0, syy = 0, szz = 0, sxy = 0,
+    sxz = 0, syz = 0;
+  static_for<1, 27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (pair_first<27>(i)) {
+      const R a_ = getg(I), b_ = getg(std::integral_constant<int, opp<27>(i)>{});
+      const R s_ = a_ + b_, d_ = a_ - b_;
+      constexpr int ex = cx<27>(i), ey = cy<27>(i), ez = cz<27>(i);
+      pst += s_;
+      if constexpr (ex != 0) { jx += (R)ex * d_; sxx += s_; }
+      if constexpr (ey != 0) { jy += (R)ey * d_; syy += s_; }
+      if constexpr (ez != 0) { jz += (R)ez * d_; szz += s_; }
+      if constexpr (ex * ey != 0) sxy += (R)(ex * ey) * s_;
+      if constexpr (ex * ez != 0) sxz += (R)(ex * ez) * s_;
+      if constexpr (ey * ez != 0) syz += (R)(ey * ez) * s_;
+    }
+  });
 
   // ---- a4/a5 forces
   const R xi = (R)rp.xi;
@@ -234,20 +237,21 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
       const R r2 = ex == 0 ? (R)-1 : (R)0.5;
       return r0 * B0 + r1 * B1 + r2 * B2;
     };
-    Store<S>::st(A.gd[0] + cell, (R)weight<27>(0) * base + neq_of(0, 0, 0));
-#pragma unroll
-    for (int i = 1; i < 27; ++i) {
-      if (!pair_first<27>(i)) continue;
-      const int ex = cx<27>(i), ey = cy<27>(i), ez = cz<27>(i);
-      const R w = (R)weight<27>(i);
-      const R cu = (R)ex * ux + (R)ey * uy + (R)ez * uz;
-      const R ca = (R)ex * ax + (R)ey * ay + (R)ez * az;
-      // g^eq + S/2 = w [p* + 3cu + 9/2 cu^2 - 3/2 uu + 3/2 (ca - ua) + 9/2 cu ca]
-      const R even = w * (base + (R)4.5 * cu * (cu + ca));
-      const R odd = w * ((R)3 * cu + (R)1.5 * ca);
-      Store<S>::st(A.gd[i] + cell, even + odd + neq_of(ex, ey, ez));
-      Store<S>::st(A.gd[opp<27>(i)] + cell, even - odd + neq_of(-ex, -ey, -ez));
-    }
+    Store<S>::st(A.gd[0] + pcell, (R)weight<27>(0) * base + neq_of(0, 0, 0));
+    static_for<1, 27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      if constexpr (pair_first<27>(i)) {
+        constexpr int ex = cx<27>(i), ey = cy<27>(i), ez = cz<27>(i);
+        constexpr R w = (R)weight<27>(i);
+        const R cu = (R)ex * ux + (R)ey * uy + (R)ez * uz;
+        const R ca = (R)ex * ax + (R)ey * ay + (R)ez * az;
+        // g^eq + S/2 = w [p* + 3cu + 9/2 cu^2 - 3/2 uu + 3/2 (ca - ua) + 9/2 cu ca]
+        const R even = w * (base + (R)4.5 * cu * (cu + ca));
+        const R odd = w * ((R)3 * cu + (R)1.5 * ca);
+        Store<S>::st(A.gd[i] + pcell, even + odd + neq_of(ex, ey, ez));
+        Store<S>::st(A.gd[opp<27>(i)] + pcell, even - odd + neq_of(-ex, -ey, -ez));
+      }
+    });
   }
   // ---- a7 h collision (single rate + Guo source of the interface force)
   {
@@ -259,25 +263,26 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
     const R sh = (R)rp.shift_h;
     const R e0 = (R)1 - (R)1.5 * uu;
     {
-      const R w = (R)weight<QH>(0);
-      const R hs = geth(0);
+      constexpr R w = (R)weight<QH>(0);
+      const R hs = geth(std::integral_constant<int, 0>{});
       const R hn = hs - om * (hs - w * phi * e0);
-      Store<S>::st(A.hd[0] + cell, hn - w * sh);
+      Store<S>::st(A.hd[0] + pcell, hn - w * sh);
     }
-#pragma unroll
-    for (int i = 1; i < QH; ++i) {
-      if (!pair_first<QH>(i)) continue;
-      const int j = opp<QH>(i);
-      const R w = (R)weight<QH>(i);
-      const R cu = (R)cx<QH>(i) * ux + (R)cy<QH>(i) * uy + (R)cz<QH>(i) * uz;
-      const R cf = (R)cx<QH>(i) * fpx + (R)cy<QH>(i) * fpy + (R)cz<QH>(i) * fpz;
-      const R even = w * phi * (e0 + (R)4.5 * cu * cu);
-      const R odd = w * phi * (R)3 * cu;
-      const R src = sc * w * cf;
-      const R hi = geth(i), hj = geth(j);
-      Store<S>::st(A.hd[i] + cell, hi - om * (hi - (even + odd)) + src - w * sh);
-      Store<S>::st(A.hd[j] + cell, hj - om * (hj - (even - odd)) - src - w * sh);
-    }
+    static_for<1, QH>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      if constexpr (pair_first<QH>(i)) {
+        constexpr int j = opp<QH>(i);
+        constexpr R w = (R)weight<QH>(i);
+        const R cu = (R)cx<QH>(i) * ux + (R)cy<QH>(i) * uy + (R)cz<QH>(i) * uz;
+        const R cf = (R)cx<QH>(i) * fpx + (R)cy<QH>(i) * fpy + (R)cz<QH>(i) * fpz;
+        const R even = w * phi * (e0 + (R)4.5 * cu * cu);
+        const R odd = w * phi * (R)3 * cu;
+        const R src = sc * w * cf;
+        const R hi = geth(I), hj = geth(std::integral_constant<int, j>{});
+        Store<S>::st(A.hd[i] + pcell, hi - om * (hi - (even + odd)) + src - w * sh);
+        Store<S>::st(A.hd[j] + pcell, hj - om * (hj - (even - odd)) - src - w * sh);
+      }
+    });
   }
   // ---- a9 / a9' thermal
   const R q = heat_source<R>(P, x, y, z);
@@ -288,23 +293,24 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
     const R e0 = (R)1 - (R)1.5 * uu;
     const R qs = q - uG;
     {
-      const R w = (R)weight<QF>(0);
-      const R fs = getf(0);
+      constexpr R w = (R)weight<QF>(0);
+      const R fs = getf(std::integral_constant<int, 0>{});
       const R fn = fs - om * (fs - w * Tc * e0) + w * qs;
-      Store<S>::st(A.fd[0] + cell, fn - w * sf);
+      Store<S>::st(A.fd[0] + pcell, fn - w * sf);
     }
-#pragma unroll
-    for (int i = 1; i < QF; ++i) {
-      if (!pair_first<QF>(i)) continue;
-      const int j = opp<QF>(i);
-      const R w = (R)weight<QF>(i);
-      const R cu = (R)cx<QF>(i) * ux + (R)cy<QF>(i) * uy + (R)cz<QF>(i) * uz;
-      const R even = w * Tc * (e0 + (R)4.5 * cu * cu);
-      const R odd = w * Tc * (R)3 * cu;
-      const R fi = getf(i), fj = getf(j);
-      Store<S>::st(A.fd[i] + cell, fi - om * (fi - (even + odd)) + w * qs - w * sf);
-      Store<S>::st(A.fd[j] + cell, fj - om * (fj - (even - odd)) + w * qs - w * sf);
-    }
+    static_for<1, QF>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      if constexpr (pair_first<QF>(i)) {
+        constexpr int j = opp<QF>(i);
+        constexpr R w = (R)weight<QF>(i);
+        const R cu = (R)cx<QF>(i) * ux + (R)cy<QF>(i) * uy + (R)cz<QF>(i) * uz;
+        const R even = w * Tc * (e0 + (R)4.5 * cu * cu);
+        const R odd = w * Tc * (R)3 * cu;
+        const R fi = getf(I), fj = getf(std::integral_constant<int, j>{});
+        Store<S>::st(A.fd[i] + pcell, fi - om * (fi - (even + odd)) + w * qs - w * sf);
+        Store<S>::st(A.fd[j] + pcell, fj - om * (fj - (even - odd)) + w * qs - w * sf);
+      }
+    });
   } else {
     // RK stage 1: K1 = R(T^n) with the local u of this step
     R gx_, gy_, gz_, lap;

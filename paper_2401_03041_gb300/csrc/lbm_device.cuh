@@ -11,7 +11,20 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace lbm {
+
+// Compile-time loop: f(std::integral_constant<int, i>) for i in [B, E).  Every
+// direction loop uses it, so lattice velocities and weights are constants by
+// construction (no reliance on the unroller).
+template <int B, int E, class F>
+__host__ __device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
 
 // ----------------------------------------------------------------- lattices
 // Direction k of D3Q27 (the superset).  Other stencils index into it.

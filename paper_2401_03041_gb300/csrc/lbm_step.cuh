@@ -31,29 +31,29 @@ __device__ __forceinline__ int wrap_any(int v, int n) {
   return r < 0 ? r + n : r;
 }
 
-// Value of direction i pulled into cell (x, y, z): p_i(x - c_i), with
+// Value of direction I pulled into cell (x, y, z): p_I(x - c_I), with
 // half-way bounce-back (ABB=false) or anti-bounce-back (ABB=true) when the
 // source lies beyond a z wall.  Returns the un-shifted value.
-template <int Q, bool ABB, class S>
+template <int Q, bool ABB, int I, class S>
 __device__ __forceinline__ typename Store<S>::R pull(const DevParams& P, const S* __restrict__ base,
-                                                     int i, int x, int y, int z,
-                                                     typename Store<S>::R shift) {
+                                                     int x, int y, int z, typename Store<S>::R shift) {
   using R = typename Store<S>::R;
   const auto& rp = RP<R>(P);
-  const int zs = z - cz<Q>(i);
-  const R wsh = (R)weight<Q>(i) * shift;
+  const int zs = z - cz<Q>(I);
+  constexpr R w = (R)weight<Q>(I);
+  const R wsh = w * shift;
   if (P.walls && (zs < 0 || zs >= P.nz)) {
-    const R v = Store<S>::ld(base + (size_t)opp<Q>(i) * P.N + cell_index(P, x, y, z)) + wsh;
-    if (ABB) {
-      const R Tw = (R)(zs < 0 ? rp.T_bottom : rp.T_top);
-      return -v + (R)(2.0 * weight<Q>(i)) * Tw;
+    const R v = Store<S>::ld(base + (size_t)opp<Q>(I) * P.N + cell_index(P, x, y, z)) + wsh;
+    if constexpr (ABB) {
+      const R Tw = zs < 0 ? rp.T_bottom : rp.T_top;
+      return -v + (R)2 * w * Tw;
     }
     return v;
   }
-  const int xs = wrap(x - cx<Q>(i), P.nx);
-  const int ys = wrap(y - cy<Q>(i), P.ny);
+  const int xs = wrap(x - cx<Q>(I), P.nx);
+  const int ys = wrap(y - cy<Q>(I), P.ny);
   const int zz = P.walls ? zs : wrap(zs, P.nz);
-  return Store<S>::ld(base + (size_t)i * P.N + cell_index(P, xs, ys, zz)) + wsh;
+  return Store<S>::ld(base + (size_t)I * P.N + cell_index(P, xs, ys, zz)) + wsh;
 }
 
 template <int Q, bool ABB, class S>
@@ -62,8 +62,7 @@ __device__ __forceinline__ typename Store<S>::R pulled_sum(const DevParams& P, c
                                                            typename Store<S>::R shift) {
   using R = typename Store<S>::R;
   R s = 0;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) s += pull<Q, ABB>(P, base, i, x, y, z, shift);
+  static_for<0, Q>([&](auto I) { s += pull<Q, ABB, decltype(I)::value>(P, base, x, y, z, shift); });
   return s;
 }
 
@@ -148,13 +147,13 @@ step_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, int zc
       R rgx = 0, rgy = 0, rgz = 0, rlap = 0;
       if constexpr (QF == 0) rk_std<R, HX>(s_T[sm], s_T[sc], s_T[sp], c0, rgx, rgy, rgz, rlap);
       const size_t cell = cell_index(P, x, y, z);
-      auto geth = [&](int i) { return pull<QH, false>(P, A.h_src, i, x, y, z, shh); };
-      auto getg = [&](int i) { return pull<27, false>(P, A.g_src, i, x, y, z, (R)0); };
-      auto getf = [&](int i) {
-        if constexpr (QF > 0) return pull<QF, true>(P, A.f_src, i, x, y, z, shf);
+      auto geth = [&](auto I) { return pull<QH, false, decltype(I)::value>(P, A.h_src, x, y, z, shh); };
+      auto getg = [&](auto I) { return pull<27, false, decltype(I)::value>(P, A.g_src, x, y, z, (R)0); };
+      auto getf = [&](auto I) {
+        if constexpr (QF > 0) return pull<QF, true, decltype(I)::value>(P, A.f_src, x, y, z, shf);
         else return (R)0;
       };
-      cell_update<S, QH, QF>(P, A, x, y, z, cell, mode, s_phi[sc][c0], s_T[sc][c0], fd, rgx, rgy,
+      cell_update<S, QH, QF>(P, A, x, y, z, cell, cell, mode, s_phi[sc][c0], s_T[sc][c0], fd, rgx, rgy,
                              rgz, rlap, geth, getg, getf, dsum);
     }
     __syncthreads();
