@@ -76,7 +76,9 @@ _LIB = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The in-tree library, or the file named by LBM_LIBRARY (an alternative
+    build of the same sources)."""
+    return os.environ.get("LBM_LIBRARY") or _build.LIB
 
 
 def lib():
