@@ -16,23 +16,31 @@ void launch_rk_stage(const DevParams& P, const typename Store<S>::R* psi, typena
 }
 
 template <class S, int Q>
-static void convert_q(bool to_f64, void* pdf, double* f64, long long N, double shift, cudaStream_t st) {
-  const long long blocks = ((long long)Q * N + 255) / 256;
+static void convert_q(const DevParams& P, bool to_f64, void* pdf, double* f64, double shift, cudaStream_t st) {
+  const long long blocks = ((long long)Q * P.N + 255) / 256;
   const int grid = (int)(blocks < 152 * 64 ? blocks : 152 * 64);
-  if (to_f64) pdf_to_f64_kernel<S, Q><<<grid, 256, 0, st>>>((const S*)pdf, f64, N, shift);
-  else f64_to_pdf_kernel<S, Q><<<grid, 256, 0, st>>>(f64, (S*)pdf, N, shift);
+  if (to_f64) pdf_to_f64_kernel<S, Q><<<grid, 256, 0, st>>>(P, (const S*)pdf, f64, shift);
+  else f64_to_pdf_kernel<S, Q><<<grid, 256, 0, st>>>(P, f64, (S*)pdf, shift);
 }
 
 template <class S>
-void launch_pdf_convert(int Q, bool to_f64, void* pdf, double* f64, long long N, double shift,
+void launch_pdf_convert(const DevParams& P, int Q, bool to_f64, void* pdf, double* f64, double shift,
                         cudaStream_t st) {
   switch (Q) {
-    case 1: convert_q<S, 1>(to_f64, pdf, f64, N, shift, st); break;
-    case 7: convert_q<S, 7>(to_f64, pdf, f64, N, shift, st); break;
-    case 15: convert_q<S, 15>(to_f64, pdf, f64, N, shift, st); break;
-    case 19: convert_q<S, 19>(to_f64, pdf, f64, N, shift, st); break;
-    default: convert_q<S, 27>(to_f64, pdf, f64, N, shift, st); break;
+    case 7: convert_q<S, 7>(P, to_f64, pdf, f64, shift, st); break;
+    case 15: convert_q<S, 15>(P, to_f64, pdf, f64, shift, st); break;
+    case 19: convert_q<S, 19>(P, to_f64, pdf, f64, shift, st); break;
+    default: convert_q<S, 27>(P, to_f64, pdf, f64, shift, st); break;
   }
+}
+
+template <class S>
+void launch_ghost_fill(const DevParams& P, void* buf, int nq, cudaStream_t st) {
+  const long long per_plane = 2LL * P.GX * P.ny + 2LL * P.GY * P.NXP;
+  const long long total = per_plane * P.nz * nq;
+  const long long blocks = (total + 255) / 256;
+  const int grid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
+  if (total > 0) ghost_fill_kernel<S><<<grid, 256, 0, st>>>(P, (S*)buf, nq);
 }
 
 template <class S, int QH>
@@ -61,6 +69,10 @@ int bulk_tile_cols(int prec) {
   return prec == 0 ? BulkGeom<double>::TXB : (prec == 1 ? BulkGeom<float>::TXB : BulkGeom<__half>::TXB);
 }
 
+int bulk_box_cols(int prec) {
+  return prec == 0 ? BulkGeom<double>::W : (prec == 1 ? BulkGeom<float>::W : BulkGeom<__half>::W);
+}
+
 int bulk_tile_rows(int prec) {
   return prec == 0 ? BulkGeom<double>::TYB : (prec == 1 ? BulkGeom<float>::TYB : BulkGeom<__half>::TYB);
 }
@@ -75,8 +87,11 @@ template void launch_rk_stage<float>(const DevParams&, const float*, float*, con
                                      float*, int, cudaStream_t);
 template void launch_rk_stage<__half>(const DevParams&, const float*, float*, const float*, float*,
                                       float*, int, cudaStream_t);
-template void launch_pdf_convert<double>(int, bool, void*, double*, long long, double, cudaStream_t);
-template void launch_pdf_convert<float>(int, bool, void*, double*, long long, double, cudaStream_t);
-template void launch_pdf_convert<__half>(int, bool, void*, double*, long long, double, cudaStream_t);
+template void launch_pdf_convert<double>(const DevParams&, int, bool, void*, double*, double, cudaStream_t);
+template void launch_pdf_convert<float>(const DevParams&, int, bool, void*, double*, double, cudaStream_t);
+template void launch_pdf_convert<__half>(const DevParams&, int, bool, void*, double*, double, cudaStream_t);
+template void launch_ghost_fill<double>(const DevParams&, void*, int, cudaStream_t);
+template void launch_ghost_fill<float>(const DevParams&, void*, int, cudaStream_t);
+template void launch_ghost_fill<__half>(const DevParams&, void*, int, cudaStream_t);
 
 }  // namespace lbm

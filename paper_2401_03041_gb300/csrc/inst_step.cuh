@@ -10,8 +10,8 @@
 namespace lbm {
 
 template <class S, int QH, int QF>
-void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A, dim3 grid,
-                 int zchunk, int mode, int use_bulk, cudaStream_t st) {
+void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A, const TMaps& maps,
+                 dim3 grid, int zchunk, int mode, int use_bulk, cudaStream_t st) {
   constexpr size_t bytes = BulkSmem<S, QH, QF>::bytes;
   if constexpr (bytes <= kMaxDynSmem) {
     if (use_bulk) {
@@ -21,7 +21,8 @@ void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                              (int)bytes);
         attr_set = true;
       }
-      step_bulk_kernel<S, QH, QF><<<grid, dim3(BulkGeom<S>::TXB, BulkGeom<S>::TYB), bytes, st>>>(P, A, zchunk, mode);
+      step_bulk_kernel<S, QH, QF><<<grid, dim3(BulkGeom<S>::TXB, BulkGeom<S>::TYB), bytes, st>>>(
+          P, A, maps.h, maps.g, maps.f, zchunk, mode);
       return;
     }
   }
@@ -38,8 +39,8 @@ void launch_init(const DevParams& P, const double* drops, int nd, S* h, S* g, S*
 
 #define LBM_INST(QF)                                                                          \
   template void launch_step<LBM_S, LBM_QH, QF>(const DevParams&,                              \
-                                               const StepPtrs<LBM_S, Store<LBM_S>::R>&, dim3, \
-                                               int, int, int, cudaStream_t);                  \
+                                               const StepPtrs<LBM_S, Store<LBM_S>::R>&,       \
+                                               const TMaps&, dim3, int, int, int, cudaStream_t); \
   template void launch_init<LBM_S, LBM_QH, QF>(const DevParams&, const double*, int, LBM_S*,  \
                                                LBM_S*, LBM_S*, Store<LBM_S>::R*, cudaStream_t);
 LBM_INST(0)

@@ -3,6 +3,7 @@
 // per storage precision) so that they compile in parallel.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "lbm_device.cuh"
@@ -11,15 +12,25 @@ namespace lbm {
 
 // use_bulk: the bulk-copy kernel (grid of TX x BulkGeom<S>::TYB tiles) if
 // its shared memory fits, else the generic kernel (TX x TY tiles).
+// Tensor maps of the current source PDF buffers (bulk kernel only).
+struct TMaps {
+  CUtensorMap h, g, f;
+};
+
 template <class S, int QH, int QF>
-void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A, dim3 grid,
-                 int zchunk, int mode, int use_bulk, cudaStream_t st);
+void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A, const TMaps& maps,
+                 dim3 grid, int zchunk, int mode, int use_bulk, cudaStream_t st);
+
+// Refresh the periodic ghost cells of nq consecutive padded directions at buf.
+template <class S>
+void launch_ghost_fill(const DevParams& P, void* buf, int nq, cudaStream_t st);
 
 // Dynamic shared memory of the bulk kernel for (precision, q_phase, q_f),
 // and the largest a CTA may use; also its tile height.
 size_t bulk_smem_bytes(int prec, int qh, int qf);
 int bulk_tile_rows(int prec);
 int bulk_tile_cols(int prec);
+int bulk_box_cols(int prec);   // staged row length W of the bulk kernel
 constexpr size_t kMaxDynSmem = 232448;
 
 template <class S, int QH, int QF>
@@ -32,7 +43,7 @@ void launch_rk_stage(const DevParams& P, const typename Store<S>::R* psi, typena
                      typename Store<S>::R* out, int kind, cudaStream_t st);
 
 template <class S>
-void launch_pdf_convert(int Q, bool to_f64, void* pdf, double* f64, long long N, double shift,
+void launch_pdf_convert(const DevParams& P, int Q, bool to_f64, void* pdf, double* f64, double shift,
                         cudaStream_t st);
 
 void launch_diag_finalize(const double* partials, int nblocks, double* out, cudaStream_t st);

@@ -66,17 +66,14 @@ int thermal_q(lbm_thermal th);
 bool bulk_ok(int nx, int ny, lbm_precision prec, int qh, int qf) {
   const char* env = std::getenv("LBM_KERNEL");
   if (env && std::strcmp(env, "generic") == 0) return false;
-  const int s = prec == LBM_FP64 ? 8 : (prec == LBM_FP32 ? 4 : 2);
-  const int gxp = 16 / s;
-  if ((nx * s) % 16 != 0) return false;
-  if (nx < bulk_tile_cols((int)prec) + 2 * gxp) return false;
+  if (nx < bulk_box_cols((int)prec)) return false;
   if (ny < 2 * bulk_tile_rows((int)prec)) return false;
   return bulk_smem_bytes((int)prec, qh, qf) <= kMaxDynSmem;
 }
 
-Geometry geometry(int nx, int ny, int nz, lbm_precision prec, int qh, int qf) {
+Geometry geometry(int nx, int ny, int nz, lbm_precision prec, int qh, int qf, bool allow_bulk = true) {
   Geometry g;
-  g.bulk = bulk_ok(nx, ny, prec, qh, qf) ? 1 : 0;
+  g.bulk = allow_bulk && bulk_ok(nx, ny, prec, qh, qf) ? 1 : 0;
   const int rows = g.bulk ? bulk_tile_rows((int)prec) : TY;
   const int cols_ = g.bulk ? bulk_tile_cols((int)prec) : TX;
   const int bx = (nx + cols_ - 1) / cols_, by = (ny + rows - 1) / rows;
@@ -100,6 +97,25 @@ Geometry geometry(int nx, int ny, int nz, lbm_precision prec, int qh, int qf) {
   return g;
 }
 
+// Padded PDF geometry: GX = 16 / sizeof(storage) ghost columns and
+// kGhostRows ghost rows on each side; the row pitch is a multiple of 16 bytes.
+struct Pad {
+  int GX, GY, NXP, NYP;
+  size_t Np;
+};
+
+Pad padding(int nx, int ny, int nz, lbm_precision prec) {
+  Pad p;
+  const int s = (int)store_bytes(prec);
+  p.GX = 16 / s;
+  p.GY = kGhostRows;
+  const int align = 16 / s;
+  p.NXP = ((nx + 2 * p.GX + align - 1) / align) * align;
+  p.NYP = ny + 2 * p.GY;
+  p.Np = (size_t)nz * p.NYP * p.NXP;
+  return p;
+}
+
 bool layout(int nx, int ny, int nz, lbm_precision prec, lbm_thermal th, int qh, Layout* L) {
   if (nx < 1 || ny < 1 || nz < 1) return false;
   if (qh != 15 && qh != 27) return false;
@@ -107,12 +123,18 @@ bool layout(int nx, int ny, int nz, lbm_precision prec, lbm_thermal th, int qh, 
   if (th < LBM_TH_D3Q7 || th > LBM_TH_RK4) return false;
   const size_t N = (size_t)nx * ny * nz;
   if (N >= (size_t(1) << 40)) return false;
+  const Pad pd = padding(nx, ny, nz, prec);
   const size_t sb = store_bytes(prec), fb = field_bytes(prec);
   const int qf = thermal_q(th);
   size_t off = 0;
-  for (int k = 0; k < 2; ++k) { L->h[k] = off; off = align256(off + qh * N * sb); }
-  for (int k = 0; k < 2; ++k) { L->g[k] = off; off = align256(off + 27 * N * sb); }
-  for (int k = 0; k < 2; ++k) { L->f[k] = off; off = align256(off + (size_t)qf * N * sb); }
+  // one PDF set = [h (qh) | g (27) | f (qf)] directions of Np elements each,
+  // contiguous, so that one ghost-fill launch covers the whole set
+  for (int k = 0; k < 2; ++k) {
+    L->h[k] = off;
+    L->g[k] = off + (size_t)qh * pd.Np * sb;
+    L->f[k] = L->g[k] + (size_t)27 * pd.Np * sb;
+    off = align256(L->f[k] + (size_t)qf * pd.Np * sb);
+  }
   const bool rk = qf == 0;
   const bool rk4 = th == LBM_TH_RK4;
   L->T = off; off = align256(off + (rk ? N * fb : 0));
@@ -153,6 +175,7 @@ struct lbm_domain {
   size_t staging_bytes;
   lbm_status sticky;
   std::string sticky_msg;
+  TMaps maps[2];  // tensor maps of PDF set 0 / 1 (bulk kernel)
 };
 
 namespace {
@@ -198,10 +221,11 @@ StepPtrs<S, typename Store<S>::R> ptrs(lbm_domain* d) {
   A.rk_acc = d->th == LBM_TH_RK4;
   A.diag_partials = (double*)at(d, d->L.partials);
   A.error_flag = (int*)at(d, d->L.errflag);
+  const size_t np = (size_t)d->dp.Np;
   for (int i = 0; i < 27; ++i) {
-    A.hd[i] = i < d->qh ? A.h_dst + (size_t)i * d->N : nullptr;
-    A.gd[i] = A.g_dst + (size_t)i * d->N;
-    A.fd[i] = i < d->qf ? A.f_dst + (size_t)i * d->N : nullptr;
+    A.hd[i] = i < d->qh ? A.h_dst + (size_t)i * np : nullptr;
+    A.gd[i] = A.g_dst + (size_t)i * np;
+    A.fd[i] = i < d->qf ? A.f_dst + (size_t)i * np : nullptr;
   }
   return A;
 }
@@ -209,11 +233,11 @@ StepPtrs<S, typename Store<S>::R> ptrs(lbm_domain* d) {
 template <class S, int QH>
 void step_qf(lbm_domain* d, const StepPtrs<S, typename Store<S>::R>& A, int mode) {
   switch (d->qf) {
-    case 0: launch_step<S, QH, 0>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
-    case 7: launch_step<S, QH, 7>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
-    case 15: launch_step<S, QH, 15>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
-    case 19: launch_step<S, QH, 19>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
-    default: launch_step<S, QH, 27>(d->dp, A, d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
+    case 0: launch_step<S, QH, 0>(d->dp, A, d->maps[d->cur], d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
+    case 7: launch_step<S, QH, 7>(d->dp, A, d->maps[d->cur], d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
+    case 15: launch_step<S, QH, 15>(d->dp, A, d->maps[d->cur], d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
+    case 19: launch_step<S, QH, 19>(d->dp, A, d->maps[d->cur], d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
+    default: launch_step<S, QH, 27>(d->dp, A, d->maps[d->cur], d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
   }
 }
 
@@ -240,6 +264,16 @@ void rk_tail(lbm_domain* d) {
   }
 }
 
+// Refresh the periodic ghost cells of PDF set k (bulk kernel only).
+void ghost_fill(lbm_domain* d, int k) {
+  if (!d->geo.bulk) return;
+  void* base = at(d, d->L.h[k]);
+  const int nq = d->qh + 27 + d->qf;
+  if (d->prec == LBM_FP64) launch_ghost_fill<double>(d->dp, base, nq, d->stream);
+  else if (d->prec == LBM_FP32) launch_ghost_fill<float>(d->dp, base, nq, d->stream);
+  else launch_ghost_fill<__half>(d->dp, base, nq, d->stream);
+}
+
 // One step (mode: MODE_COLLIDE [| MODE_DIAG]), or a read-only pass.
 lbm_status run_pass(lbm_domain* d, int mode, void* macro_out = nullptr, int macro_dtype = 0,
                     unsigned mask = 0) {
@@ -250,6 +284,7 @@ lbm_status run_pass(lbm_domain* d, int mode, void* macro_out = nullptr, int macr
     A.macro_dtype = macro_dtype;
     A.macro_mask = mask;
     step_launch<S>(d, A, mode);
+    if (mode & MODE_COLLIDE) ghost_fill(d, d->cur ^ 1);
     if ((mode & MODE_COLLIDE) && d->qf == 0) rk_tail<S>(d);
   };
   if (d->prec == LBM_FP64) go(double{});
@@ -335,10 +370,69 @@ void refresh_devparams(lbm_domain* d) {
   DevParams& q = d->dp;
   const lbm_params& p = d->params;
   q.nx = d->nx; q.ny = d->ny; q.nz = d->nz; q.N = d->N;
+  const Pad pd = padding(d->nx, d->ny, d->nz, d->prec);
+  q.GX = pd.GX; q.GY = pd.GY; q.NXP = pd.NXP; q.NYP = pd.NYP; q.Np = (long long)pd.Np;
   q.walls = p.walls_z ? 1 : 0;
   q.rk_iso = p.rk_isotropic_fd ? 1 : 0;
   fill_real(q.pd, p, d->prec);
   fill_real(q.pf, p, d->prec);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// 4D map (x, y, z, direction) over one padded PDF array of Q directions,
+// boxes of box_w x box_rows x 1 x 1 elements.
+bool make_map(CUtensorMap* m, void* base, lbm_precision prec, const DevParams& P, int Q, int box_w,
+              int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const size_t s = store_bytes(prec);
+  const CUtensorMapDataType dt = prec == LBM_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                               : prec == LBM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                  : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  const cuuint64_t dims[4] = {(cuuint64_t)P.NXP, (cuuint64_t)P.NYP, (cuuint64_t)P.nz, (cuuint64_t)Q};
+  const cuuint64_t strides[3] = {(cuuint64_t)P.NXP * s, (cuuint64_t)P.NXP * P.NYP * s,
+                                 (cuuint64_t)P.Np * s};
+  const cuuint32_t box[4] = {(cuuint32_t)box_w, (cuuint32_t)box_rows, 1, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return enc(m, dt, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool make_maps(lbm_domain* d) {
+  const int w = bulk_box_cols((int)d->prec), rows = bulk_tile_rows((int)d->prec);
+  for (int k = 0; k < 2; ++k) {
+    TMaps& t = d->maps[k];
+    if (!make_map(&t.h, at(d, d->L.h[k]), d->prec, d->dp, d->qh, w, rows + 2)) return false;
+    if (!make_map(&t.g, at(d, d->L.g[k]), d->prec, d->dp, 27, w, rows)) return false;
+    if (d->qf > 0) {
+      if (!make_map(&t.f, at(d, d->L.f[k]), d->prec, d->dp, d->qf, w, rows + 2)) return false;
+    } else {
+      t.f = t.h;  // unused with an RK energy solver
+    }
+  }
+  return true;
 }
 
 }  // namespace
@@ -408,6 +502,10 @@ lbm_status lbm_create_domain(int nx, int ny, int nz, lbm_precision prec, lbm_the
     d->owns_ws = true;
   }
   refresh_devparams(d);
+  if (d->geo.bulk && !make_maps(d)) {
+    // no tensor-map support: run the generic kernel
+    d->geo = geometry(nx, ny, nz, prec, q_phase, thermal_q(thermal), false);
+  }
   {
     const cudaError_t e = cudaMemsetAsync(at(d, L.errflag), 0, sizeof(int), d->stream);
     if (e != cudaSuccess) {
@@ -544,6 +642,7 @@ lbm_status lbm_init_droplets(lbm_domain* d, int n, const lbm_droplet* drops) {
   if (d->prec == LBM_FP64) go(double{});
   else if (d->prec == LBM_FP32) go(float{});
   else go(__half{});
+  ghost_fill(d, 0);
   s = check_launch(d, "init kernel launch");
   if (s != LBM_OK) return s;
   if (n > 0) {
@@ -631,36 +730,49 @@ static lbm_status pdf_io(lbm_domain* d, int which, double* host, bool to_host) {
   if (which < 0 || which > 3) return fail(LBM_ERR_ARG, "which must be 0..3");
   if (which == 2 && d->qf == 0) return fail(LBM_ERR_ARG, "no thermal PDFs with an RK solver");
   if (which == 3 && d->qf != 0) return fail(LBM_ERR_ARG, "no T field with an LB thermal solver");
-  int Q = which == 0 ? d->qh : (which == 1 ? 27 : (which == 2 ? d->qf : 1));
-  double shift = which == 0 ? d->dp.pd.shift_h : (which == 2 ? d->dp.pd.shift_f : 0.0);
-  void* buf = which == 0 ? at(d, d->L.h[d->cur])
-            : which == 1 ? at(d, d->L.g[d->cur])
-            : which == 2 ? at(d, d->L.f[d->cur]) : at(d, d->L.T);
-  const size_t bytes = (size_t)Q * d->N * 8;
+  const size_t N = (size_t)d->N;
+  if (which == 3) {
+    // the T field is dense, in the compute type, not shifted: convert on the host
+    void* buf = at(d, d->L.T);
+    if (d->prec == LBM_FP64) {
+      s = check_cuda(d, cudaMemcpyAsync(to_host ? (void*)host : buf, to_host ? buf : (void*)host, N * 8,
+                                        to_host ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice, d->stream),
+                     "T copy");
+      if (s == LBM_OK) s = check_cuda(d, cudaStreamSynchronize(d->stream), "T sync");
+      return s;
+    }
+    std::vector<float> tmpf(N);
+    if (to_host) {
+      s = check_cuda(d, cudaMemcpyAsync(tmpf.data(), buf, N * 4, cudaMemcpyDeviceToHost, d->stream), "T copy");
+      if (s == LBM_OK) s = check_cuda(d, cudaStreamSynchronize(d->stream), "T sync");
+      if (s == LBM_OK)
+        for (size_t k = 0; k < N; ++k) host[k] = tmpf[k];
+    } else {
+      for (size_t k = 0; k < N; ++k) tmpf[k] = (float)host[k];
+      s = check_cuda(d, cudaMemcpyAsync(buf, tmpf.data(), N * 4, cudaMemcpyHostToDevice, d->stream), "T copy");
+      if (s == LBM_OK) s = check_cuda(d, cudaStreamSynchronize(d->stream), "T sync");
+    }
+    return s;
+  }
+  const int Q = which == 0 ? d->qh : (which == 1 ? 27 : d->qf);
+  const double shift = which == 0 ? d->dp.pd.shift_h : (which == 2 ? d->dp.pd.shift_f : 0.0);
+  void* buf = which == 0 ? at(d, d->L.h[d->cur]) : which == 1 ? at(d, d->L.g[d->cur]) : at(d, d->L.f[d->cur]);
+  const size_t bytes = (size_t)Q * N * 8;
   double* tmp = nullptr;
   s = check_cuda(d, cudaMalloc(&tmp, bytes), "conversion buffer");
   if (s != LBM_OK) return s;
-  if (which == 3) {
-    // T field is stored in the compute type, not shifted
-    if (to_host) {
-      if (d->prec == LBM_FP64) s = check_cuda(d, cudaMemcpyAsync(tmp, buf, bytes, cudaMemcpyDeviceToDevice, d->stream), "copy");
-      else launch_pdf_convert<float>(1, true, buf, tmp, d->N, 0.0, d->stream);
-    } else {
-      s = check_cuda(d, cudaMemcpyAsync(tmp, host, bytes, cudaMemcpyHostToDevice, d->stream), "upload");
-      if (d->prec == LBM_FP64) s = check_cuda(d, cudaMemcpyAsync(buf, tmp, bytes, cudaMemcpyDeviceToDevice, d->stream), "copy");
-      else launch_pdf_convert<float>(1, false, buf, tmp, d->N, 0.0, d->stream);
-    }
-  } else {
-    auto conv = [&](auto tag, bool dir) {
-      using S = decltype(tag);
-      launch_pdf_convert<S>(Q, dir, buf, tmp, d->N, shift, d->stream);
-    };
-    if (!to_host) s = check_cuda(d, cudaMemcpyAsync(tmp, host, bytes, cudaMemcpyHostToDevice, d->stream), "upload");
+  auto conv = [&](auto tag, bool dir) {
+    using S = decltype(tag);
+    launch_pdf_convert<S>(d->dp, Q, dir, buf, tmp, shift, d->stream);
+  };
+  if (!to_host) s = check_cuda(d, cudaMemcpyAsync(tmp, host, bytes, cudaMemcpyHostToDevice, d->stream), "upload");
+  if (s == LBM_OK) {
     if (d->prec == LBM_FP64) conv(double{}, to_host);
     else if (d->prec == LBM_FP32) conv(float{}, to_host);
     else conv(__half{}, to_host);
+    s = check_launch(d, "conversion kernel");
   }
-  if (s == LBM_OK) s = check_launch(d, "conversion kernel");
+  if (s == LBM_OK && !to_host) ghost_fill(d, d->cur);
   if (s == LBM_OK && to_host)
     s = check_cuda(d, cudaMemcpyAsync(host, tmp, bytes, cudaMemcpyDeviceToHost, d->stream), "download");
   if (s == LBM_OK) s = check_cuda(d, cudaStreamSynchronize(d->stream), "conversion sync");

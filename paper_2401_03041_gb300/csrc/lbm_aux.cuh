@@ -124,25 +124,27 @@ __global__ void init_kernel(const DevParams P, const double* __restrict__ drops,
       uz += pk * d[6];
     }
     const double T0 = P.walls ? rp.T_bottom + (rp.T_top - rp.T_bottom) * (z + 0.5) / P.nz : 0.0;
+    const size_t pc = pdf_index(P, x, y, z);
+    const size_t np = (size_t)P.Np;
     const double uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
     for (int i = 0; i < QH; ++i) {
       const double cu = cx<QH>(i) * ux + cy<QH>(i) * uy + cz<QH>(i) * uz;
       const double e = weight<QH>(i) * phi * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-      Store<S>::st(h + (size_t)i * n + cell, (R)(e - weight<QH>(i) * rp.shift_h));
+      Store<S>::st(h + (size_t)i * np + pc, (R)(e - weight<QH>(i) * rp.shift_h));
     }
 #pragma unroll
     for (int i = 0; i < 27; ++i) {
       const double cu = cx<27>(i) * ux + cy<27>(i) * uy + cz<27>(i) * uz;
       const double e = weight<27>(i) * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-      Store<S>::st(g + (size_t)i * n + cell, (R)e);
+      Store<S>::st(g + (size_t)i * np + pc, (R)e);
     }
     if constexpr (QF > 0) {
 #pragma unroll
       for (int i = 0; i < QF; ++i) {
         const double cu = cx<QF>(i) * ux + cy<QF>(i) * uy + cz<QF>(i) * uz;
         const double e = weight<QF>(i) * T0 * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-        Store<S>::st(f + (size_t)i * n + cell, (R)(e - weight<QF>(i) * rp.shift_f));
+        Store<S>::st(f + (size_t)i * np + pc, (R)(e - weight<QF>(i) * rp.shift_f));
       }
     } else {
       Tfield[cell] = (R)T0;
@@ -150,35 +152,77 @@ __global__ void init_kernel(const DevParams P, const double* __restrict__ drops,
   }
 }
 
-// Stored (shifted) PDFs <-> FP64 values, [Q][N] layout.
+// Stored (shifted) PDFs in the padded layout <-> dense FP64 values [Q][N].
 template <class S, int Q>
-__global__ void pdf_to_f64_kernel(const S* __restrict__ src, double* __restrict__ dst, long long N,
+__global__ void pdf_to_f64_kernel(const DevParams P, const S* __restrict__ src, double* __restrict__ dst,
                                   double shift) {
-  const size_t total = (size_t)Q * N;
+  const size_t N = (size_t)P.N, total = (size_t)Q * N;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
        k += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(k / N);
+    const size_t c = k - (size_t)i * N;
+    const int x = (int)(c % P.nx), y = (int)((c / P.nx) % P.ny), z = (int)(c / ((size_t)P.nx * P.ny));
     double w = 0.0;
 #pragma unroll
     for (int j = 0; j < Q; ++j)
       if (j == i) w = weight<Q>(j);
-    dst[k] = (double)Store<S>::ld(src + k) + w * shift;
+    dst[k] = (double)Store<S>::ld(src + (size_t)i * P.Np + pdf_index(P, x, y, z)) + w * shift;
   }
 }
 
 template <class S, int Q>
-__global__ void f64_to_pdf_kernel(const double* __restrict__ src, S* __restrict__ dst, long long N,
+__global__ void f64_to_pdf_kernel(const DevParams P, const double* __restrict__ src, S* __restrict__ dst,
                                   double shift) {
   using R = typename Store<S>::R;
-  const size_t total = (size_t)Q * N;
+  const size_t N = (size_t)P.N, total = (size_t)Q * N;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
        k += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(k / N);
+    const size_t c = k - (size_t)i * N;
+    const int x = (int)(c % P.nx), y = (int)((c / P.nx) % P.ny), z = (int)(c / ((size_t)P.nx * P.ny));
     double w = 0.0;
 #pragma unroll
     for (int j = 0; j < Q; ++j)
       if (j == i) w = weight<Q>(j);
-    Store<S>::st(dst + k, (R)(src[k] - w * shift));
+    Store<S>::st(dst + (size_t)i * P.Np + pdf_index(P, x, y, z), (R)(src[k] - w * shift));
+  }
+}
+
+// Periodic ghost cells of one padded PDF buffer of nq directions: every
+// ghost position (x, y) outside [0, nx) x [0, ny) receives the value of cell
+// (x mod nx, y mod ny) of the same plane and direction (the single-GPU form
+// of a ghost-layer exchange).  Ghost positions of a plane are enumerated as
+// the left/right column strips of the interior rows, then the full top and
+// bottom row strips.
+template <class S>
+__global__ void ghost_fill_kernel(const DevParams P, S* __restrict__ buf, int nq) {
+  const int GX = P.GX, GY = P.GY;
+  const long long side = 2LL * GX * P.ny;          // column strips
+  const long long rows = 2LL * GY * P.NXP;         // row strips (incl. corners)
+  const long long per_plane = side + rows;
+  const long long total = per_plane * P.nz * nq;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long qz = k / per_plane;
+    long long r = k - qz * per_plane;
+    const int z = (int)(qz % P.nz), q = (int)(qz / P.nz);
+    int x, y;
+    if (r < side) {
+      y = (int)(r / (2 * GX));
+      const int j = (int)(r % (2 * GX));
+      x = j < GX ? j - GX : P.nx + (j - GX);
+    } else {
+      r -= side;
+      const int j = (int)(r / P.NXP);            // 0 .. 2 GY - 1
+      x = (int)(r % P.NXP) - GX;
+      y = j < GY ? j - GY : P.ny + (j - GY);
+    }
+    // padded columns past nx + GX (row pitch padding) are not addressed by anyone
+    if (x >= P.nx + GX) continue;
+    int xs = x % P.nx; if (xs < 0) xs += P.nx;
+    int ys = y % P.ny; if (ys < 0) ys += P.ny;
+    S* base = buf + (size_t)q * P.Np;
+    base[pdf_index(P, x, y, z)] = base[pdf_index(P, xs, ys, z)];
   }
 }
 

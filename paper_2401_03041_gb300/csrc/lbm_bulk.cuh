@@ -1,28 +1,30 @@
-// lbm_bulk.cuh - the fused time-step kernel with asynchronous bulk copies.
+// lbm_bulk.cuh - the fused time-step kernel with tensor-TMA staging.
 //
 // Same arithmetic as the generic kernel (lbm_step.cuh, via lbm_cell.cuh); the
-// difference is how the pulled PDFs reach the SM.  A CTA owns a TX x TYB
+// difference is how the pulled PDFs reach the SM.  A CTA owns a TXB x TYB
 // column of cells and marches along z.  For every plane it stages, in shared
-// memory, the rows the pull scheme reads:
-//   HF(p): h and f rows for the (TYB + 2)-row halo tile of plane p, each row
-//          already shifted by -c_y (and taken from plane p - c_z); columns
-//          [x0 - GXP, x0 + TX + GXP) with GXP = 16 / sizeof(S) so that every
-//          row copy is a 16-byte aligned cp.async.bulk (the -c_x shift is
-//          applied when reading shared memory);
-//   G(p):  g rows for the TYB interior rows, same scheme.
-// Rows that cross the periodic x boundary are split into two copies; rows
-// whose source lies beyond a z wall come from the opposite direction's row
-// of the same cell (bounce-back), read without shift.  Copies complete on
-// mbarriers (expect_tx byte counts).  While plane z is computed, HF(z + 2)
-// and G(z + 1) are in flight: HF uses a ring of three buffers (z, z + 1 for
-// phi/T, z + 2 in flight), G a ring of two.  phi and T of the halo tile are
-// summed from HF and kept for planes z - 1, z, z + 1.
+// memory, the PDF boxes the pull scheme reads, one 4D tensor-TMA box
+// (x, y, z, direction) per direction:
+//   HF(p): h and f over the (TYB + 2)-row halo tile of plane p, each box
+//          shifted by -c_y and taken from plane p - c_z; columns
+//          [x0 - GXP, x0 + TXB + GXP) with GXP = 16 / sizeof(S), so that every
+//          box starts on a 16-byte boundary (the -c_x shift is applied when
+//          reading shared memory);
+//   G(p):  g over the TYB interior rows, same scheme.
+// The PDF arrays carry periodic ghost cells (GXP columns, two rows) that a
+// ghost-fill pass refreshes after every step, so no box wraps.  Boxes whose
+// source lies beyond a z wall come from the opposite direction at the same
+// cell (bounce-back) and are read without shift.  Boxes complete on mbarriers
+// (expect_tx byte counts).  While plane z is computed, HF(z + 2) and G(z + 1)
+// are in flight: HF uses a ring of three buffers (z, z + 1 for phi/T, z + 2 in
+// flight), G a ring of two.  phi and T of the halo tile are summed from HF and
+// kept for planes z - 1, z, z + 1.
 //
-// Requirements (checked by the host): nx * sizeof(S) a multiple of 16 and
-// nx >= TX + 2 GXP.  Every wait is bounded (about 2 s); on a timeout the CTA
-// raises the domain's error flag, drains its outstanding copies (bounded
-// too) and returns.
+// Every wait is bounded (about 2 s); on a timeout the CTA raises the domain's
+// error flag, drains its outstanding copies (bounded too) and returns.
 #pragma once
+
+#include <cuda.h>
 
 #include <type_traits>
 
@@ -45,11 +47,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+// 4D tensor box (x, y, z, direction) global -> shared, completing on bar.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            int c3, uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
       : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
@@ -101,7 +105,7 @@ __device__ __forceinline__ int rt_from27(int k) { return (Q == 15 && k >= 19) ? 
 
 template <class S>
 struct BulkGeom {
-  static constexpr int GXP = 16 / (int)sizeof(S);       // halo columns on each side
+  static constexpr int GXP = 16 / (int)sizeof(S);       // halo columns on each side (= ghost width)
   static constexpr int TXB = sizeof(S) == 8 ? 32 : 64;  // columns per CTA
   static constexpr int W = TXB + 2 * GXP;               // staged row length (elements)
   static constexpr int TYB = 4;                         // rows per CTA
@@ -109,6 +113,9 @@ struct BulkGeom {
   static constexpr int HYB = TYB + 2;
   static constexpr int HPB = HXB * HYB;
   static constexpr int NT = TXB * TYB;
+  // shared-memory pitch of one box (128-byte aligned destinations)
+  static constexpr int HFB = (int)(((size_t)W * (TYB + 2) * sizeof(S) + 127) / 128 * 128 / sizeof(S));
+  static constexpr int GB = (int)(((size_t)W * TYB * sizeof(S) + 127) / 128 * 128 / sizeof(S));
 };
 
 template <class S, int QH, int QF>
@@ -116,92 +123,85 @@ struct BulkSmem {
   using R = typename Store<S>::R;
   using G = BulkGeom<S>;
   static constexpr int NHF = QH + QF;
-  static constexpr size_t hf_stage = (size_t)NHF * (G::TYB + 2) * G::W;   // elements
-  static constexpr size_t g_stage = (size_t)27 * G::TYB * G::W;
+  static constexpr size_t hf_stage = (size_t)NHF * G::HFB;   // elements
+  static constexpr size_t g_stage = (size_t)27 * G::GB;
   static constexpr size_t off_hf = 0;
   static constexpr size_t off_g = off_hf + 3 * hf_stage * sizeof(S);
   static constexpr size_t off_phi = (off_g + 2 * g_stage * sizeof(S) + 15) & ~size_t(15);
   static constexpr size_t off_T = off_phi + 3 * G::HPB * sizeof(R);
   static constexpr size_t off_bar = (off_T + 3 * G::HPB * sizeof(R) + 15) & ~size_t(15);
-  static constexpr size_t bytes = off_bar + 5 * sizeof(uint64_t);
+  // + 128: the kernel aligns the start of its dynamic shared memory to 128
+  // bytes at run time (tensor boxes need 128-byte aligned destinations)
+  static constexpr size_t bytes = off_bar + 5 * sizeof(uint64_t) + 128;
+  // bytes one stage's boxes deliver (box padding is not written)
+  static constexpr uint32_t hf_tx = (uint32_t)((size_t)NHF * G::W * (G::TYB + 2) * sizeof(S));
+  static constexpr uint32_t g_tx = (uint32_t)((size_t)27 * G::W * G::TYB * sizeof(S));
 };
 
-// Issue the row copies of one stage.  Task t enumerates (direction, row);
-// every thread takes a strided subset.
-//   KIND 0 (HF): rows r = 0..TYB+1 are halo rows y0 - 1 + r of plane p;
-//                directions 0..QH-1 from h, QH..QH+QF-1 from f.
-//   KIND 1 (G):  rows r = 0..TYB-1 are rows y0 + r of plane p; g directions.
-// Only planes next to a wall can need bounce-back rows; elsewhere the
-// select-free branch runs (uniform per stage).
+// Issue the boxes of one stage, one direction per thread (threads 0..ndir-1).
+//   KIND 0 (HF): rows y0 - 1 .. y0 + TYB of plane p; directions 0..QH-1 from
+//                h (map mh), QH..QH+QF-1 from f (map mf).
+//   KIND 1 (G):  rows y0 .. y0 + TYB - 1 of plane p; g directions (map mg).
+// Tensor coordinates are those of the padded arrays: (x + GX, y + GY, z, q).
 template <class S, int QH, int QF, int KIND>
-__device__ __forceinline__ void issue_stage(const DevParams& P, const S* hsrc, const S* gsrc,
-                                            const S* fsrc, S* dst_stage, uint64_t* bar, int p,
-                                            int x0, int y0, int tid, int nthr) {
+__device__ __forceinline__ void issue_stage(const DevParams& P, const CUtensorMap* mh,
+                                            const CUtensorMap* mg, const CUtensorMap* mf,
+                                            S* dst_stage, uint64_t* bar, int p, int x0, int y0,
+                                            int tid) {
   using G = BulkGeom<S>;
-  constexpr int nrows = KIND == 0 ? G::TYB + 2 : G::TYB;
   constexpr int ndir = KIND == 0 ? QH + QF : 27;
-  constexpr int ntask = nrows * ndir;
+  if (tid >= ndir) return;
+  const int d = tid;
   // plane whose tile this is (walls: the ghost planes reuse the boundary plane)
   int pe = p;
   if (P.walls) pe = p < 0 ? 0 : (p >= P.nz ? P.nz - 1 : p);
   else pe = p < 0 ? p + P.nz : (p >= P.nz ? p - P.nz : p);
-  const bool wall_plane = P.walls && (pe == 0 || pe == P.nz - 1);
-  const int xs = x0 - G::GXP;
-  // CTA-uniform x segmentation of every row: [xs, xs + W) mod nx
-  const int seg_a = xs < 0 ? -xs : (xs + G::W > P.nx ? P.nx - xs : G::W);
-  const int src_x0 = xs < 0 ? P.nx - seg_a : xs;   // first segment start
-  const size_t plane = (size_t)P.ny * P.nx;
-  for (int t = tid; t < ntask; t += nthr) {
-    const int d = t / nrows, r = t - (t / nrows) * nrows;
-    const S* base;
-    int k27, q;
-    if (KIND == 1) {
-      base = gsrc;
-      k27 = d;
-      q = d;
-    } else if (d < QH) {
-      base = hsrc;
-      k27 = rt_to27<QH>(d);
-      q = d;
-    } else {
-      base = fsrc;
-      q = d - QH;
-      k27 = QF == 15 ? rt_to27<15>(q) : q;   // Q7/Q19/Q27 are prefixes of the D3Q27 order
-    }
-    int yr = y0 + r - (KIND == 0 ? 1 : 0);
-    yr = yr < 0 ? yr + P.ny : (yr >= P.ny ? yr - P.ny : yr);
-    const int czv = kDir27.c[k27][2];
-    int zz = pe - czv, yy;
-    if (wall_plane && (zz < 0 || zz >= P.nz)) {
-      // bounce-back: opposite direction, same cell
-      const int o27 = kDir27.opp[k27];
-      if (KIND == 1) q = o27;
-      else if (d < QH) q = rt_from27<QH>(o27);
-      else q = QF == 15 ? rt_from27<15>(o27) : o27;
-      zz = pe;
-      yy = yr;
-    } else {
-      zz = zz < 0 ? zz + P.nz : (zz >= P.nz ? zz - P.nz : zz);
-      yy = yr - kDir27.c[k27][1];
-      yy = yy < 0 ? yy + P.ny : (yy >= P.ny ? yy - P.ny : yy);
-    }
-    const S* row = base + (size_t)q * P.N + (size_t)zz * plane + (size_t)yy * P.nx;
-    S* dst = dst_stage + (d * nrows + r) * G::W;
-    bulk_copy_g2s(dst, row + src_x0, seg_a * sizeof(S), bar);
-    if (seg_a < G::W) bulk_copy_g2s(dst + seg_a, row, (G::W - seg_a) * sizeof(S), bar);
+  int k27, q;
+  const CUtensorMap* map;
+  if (KIND == 1) {
+    map = mg;
+    k27 = d;
+    q = d;
+  } else if (d < QH) {
+    map = mh;
+    k27 = rt_to27<QH>(d);
+    q = d;
+  } else {
+    map = mf;
+    q = d - QH;
+    k27 = QF == 15 ? rt_to27<15>(q) : q;   // Q7/Q19/Q27 are prefixes of the D3Q27 order
   }
+  const int ylo = y0 - (KIND == 0 ? 1 : 0);
+  int zz = pe - kDir27.c[k27][2], yy;
+  if (P.walls && (zz < 0 || zz >= P.nz)) {
+    // bounce-back: opposite direction, same cells
+    const int o27 = kDir27.opp[k27];
+    if (KIND == 1) q = o27;
+    else if (d < QH) q = rt_from27<QH>(o27);
+    else q = QF == 15 ? rt_from27<15>(o27) : o27;
+    zz = pe;
+    yy = ylo;
+  } else {
+    zz = zz < 0 ? zz + P.nz : (zz >= P.nz ? zz - P.nz : zz);
+    yy = ylo - kDir27.c[k27][1];
+  }
+  S* dst = dst_stage + (size_t)d * (KIND == 0 ? G::HFB : G::GB);
+  tma_load_4d(dst, map, x0 - G::GXP + P.GX, yy + P.GY, zz, q, bar);
 }
 
 template <class S, int QH, int QF>
 __global__ void __launch_bounds__(BulkGeom<S>::NT, 1)
-step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, int zchunk, int mode) {
+step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
+                 const __grid_constant__ CUtensorMap mh, const __grid_constant__ CUtensorMap mg,
+                 const __grid_constant__ CUtensorMap mf, int zchunk, int mode) {
   using R = typename Store<S>::R;
   const auto& rp = RP<R>(P);
   using G = BulkGeom<S>;
   using L = BulkSmem<S, QH, QF>;
   constexpr int NHF = QH + QF;
   constexpr int NT = G::NT;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
   S* hf = (S*)(smem + L::off_hf);
   S* gb = (S*)(smem + L::off_g);
   R* s_phi = (R*)(smem + L::off_phi);
@@ -216,8 +216,8 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
   const int x = x0 + tx, y = y0 + ty;
   const bool active = (x < P.nx) && (y < P.ny);
   const R shh = (R)rp.shift_h, shf = (R)rp.shift_f;
-  constexpr uint32_t hf_bytes = (uint32_t)(L::hf_stage * sizeof(S));
-  constexpr uint32_t g_bytes = (uint32_t)(L::g_stage * sizeof(S));
+  constexpr uint32_t hf_bytes = L::hf_tx;
+  constexpr uint32_t g_bytes = L::g_tx;
 
   if (tid == 0) {
     for (int k = 0; k < 5; ++k) mbar_init(&bar[k], 1);
@@ -250,7 +250,7 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
       static_for<0, QH>([&](auto I) {
         constexpr int i = decltype(I)::value;
         const bool b = BOUNCE && ((cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi));
-        const S* rowp = rowb + (size_t)i * (G::TYB + 2) * G::W;
+        const S* rowp = rowb + (size_t)i * G::HFB;
         phi += Store<S>::ld_s(b ? rowp : rowp - cx<QH>(i));
       });
       phi += shh;  // sum_i w_i * shift_h
@@ -260,7 +260,7 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
         static_for<0, QF>([&](auto I) {
           constexpr int i = decltype(I)::value;
           const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
-          const S* rowp = rowb + (size_t)(QH + i) * (G::TYB + 2) * G::W;
+          const S* rowp = rowb + (size_t)(QH + i) * G::HFB;
           const R v = Store<S>::ld_s(b ? rowp : rowp - cx<QF>(i)) + (R)weight<QF>(i) * shf;
           T += b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? rp.T_bottom : rp.T_top)) : v;
         });
@@ -322,10 +322,10 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
     }
     __syncthreads();
     for (int p = z0 - 1; p <= z0 + 1; ++p) {
-      issue_stage<S, QH, QF, 0>(P, A.h_src, A.g_src, A.f_src, hf_ptr(p), &bar[hf_slot(p)], p, x0, y0, tid, NT);
+      issue_stage<S, QH, QF, 0>(P, &mh, &mg, &mf, hf_ptr(p), &bar[hf_slot(p)], p, x0, y0, tid);
       mark(hf_slot(p), hf_par(p));
     }
-    issue_stage<S, QH, QF, 1>(P, A.h_src, A.g_src, A.f_src, g_ptr(z0), &bar[3 + g_slot(z0)], z0, x0, y0, tid, NT);
+    issue_stage<S, QH, QF, 1>(P, &mh, &mg, &mf, g_ptr(z0), &bar[3 + g_slot(z0)], z0, x0, y0, tid);
     mark(3 + g_slot(z0), g_par(z0));
     ok = ok && wait_slot(hf_slot(z0 - 1), hf_par(z0 - 1));
     if (ok) sum_plane(z0 - 1);
@@ -340,11 +340,11 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
   for (int z = z0; z < z1 && ok; ++z) {
     // slots of HF(z - 1) and G(z - 1) are free: refill them
     if (z + 2 <= z1) {
-      issue_stage<S, QH, QF, 0>(P, A.h_src, A.g_src, A.f_src, hf_ptr(z + 2), &bar[hf_slot(z + 2)], z + 2, x0, y0, tid, NT);
+      issue_stage<S, QH, QF, 0>(P, &mh, &mg, &mf, hf_ptr(z + 2), &bar[hf_slot(z + 2)], z + 2, x0, y0, tid);
       mark(hf_slot(z + 2), hf_par(z + 2));
     }
     if (z + 1 < z1) {
-      issue_stage<S, QH, QF, 1>(P, A.h_src, A.g_src, A.f_src, g_ptr(z + 1), &bar[3 + g_slot(z + 1)], z + 1, x0, y0, tid, NT);
+      issue_stage<S, QH, QF, 1>(P, &mh, &mg, &mf, g_ptr(z + 1), &bar[3 + g_slot(z + 1)], z + 1, x0, y0, tid);
       mark(3 + g_slot(z + 1), g_par(z + 1));
     }
     ok = ok && wait_slot(hf_slot(z + 1), hf_par(z + 1));
@@ -373,27 +373,27 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, i
         auto geth = [&](auto I) {
           constexpr int i = decltype(I)::value;
           const bool b = BOUNCE && ((cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi));
-          const S* p_ = hrow + (size_t)i * (G::TYB + 2) * G::W;
+          const S* p_ = hrow + (size_t)i * G::HFB;
           return Store<S>::ld_s(b ? p_ : p_ - cx<QH>(i)) + (R)weight<QH>(i) * shh;
         };
         auto getg = [&](auto I) {
           constexpr int i = decltype(I)::value;
           const bool b = BOUNCE && ((cz<27>(i) > 0 && lo) || (cz<27>(i) < 0 && hi));
-          const S* p_ = grow + (size_t)i * G::TYB * G::W;
+          const S* p_ = grow + (size_t)i * G::GB;
           return Store<S>::ld_s(b ? p_ : p_ - cx<27>(i));
         };
         auto getf = [&](auto I) {
           constexpr int i = decltype(I)::value;
           if constexpr (QF > 0) {
             const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
-            const S* p_ = hrow + (size_t)(QH + i) * (G::TYB + 2) * G::W;
+            const S* p_ = hrow + (size_t)(QH + i) * G::HFB;
             const R v = Store<S>::ld_s(b ? p_ : p_ - cx<QF>(i)) + (R)weight<QF>(i) * shf;
             return b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? rp.T_bottom : rp.T_top)) : v;
           } else {
             return (R)0;
           }
         };
-        cell_update<S, QH, QF>(P, A, x, y, z, cell, cell, mode, pc[c0], tc[c0], fd, rgx, rgy, rgz, rlap,
+        cell_update<S, QH, QF>(P, A, x, y, z, cell, pdf_index(P, x, y, z), mode, pc[c0], tc[c0], fd, rgx, rgy, rgz, rlap,
                                geth, getg, getf, dsum);
       };
       if (lo || hi) cell_step(std::true_type{});

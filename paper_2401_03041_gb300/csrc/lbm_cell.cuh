@@ -31,6 +31,12 @@ __device__ __forceinline__ size_t cell_index(const DevParams& P, int x, int y, i
   return ((size_t)z * P.ny + y) * P.nx + x;
 }
 
+// Element offset of cell (x, y, z) inside one direction of a padded PDF array
+// (x in [-GX, nx + GX), y in [-GY, ny + GY) address the ghost cells).
+__device__ __forceinline__ size_t pdf_index(const DevParams& P, int x, int y, int z) {
+  return ((size_t)z * P.NYP + (y + P.GY)) * P.NXP + (x + P.GX);
+}
+
 // Heat source density q_T at cell (x, y, z) (centre (x+1/2, y+1/2, z+1/2)):
 // Gaussian sources (Eq. HeatSource, r <= d) plus heater patches (by index).
 template <class R>

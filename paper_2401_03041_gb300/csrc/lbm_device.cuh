@@ -118,9 +118,18 @@ struct RealParams {
 };
 
 // Everything a kernel needs, passed by value (lives in the constant bank).
+// PDF arrays are stored with periodic ghost cells: GX columns on each side
+// in x and GY rows on each side in y (no ghosts in z), row pitch NXP and NYP
+// rows per plane; Np = nz * NYP * NXP elements per direction.  Cell (x, y, z)
+// of direction i lives at i * Np + pdf_index(x, y, z).  Fields (T, u, stage
+// buffers, outputs) are dense [z][y][x] arrays of N = nx * ny * nz.
+constexpr int kGhostRows = 2;
+
 struct DevParams {
   int nx, ny, nz, walls;
   long long N;
+  int NXP, NYP, GX, GY;
+  long long Np;
   int rk_iso;
   int nsrc;
   int npatch, patch_z, patch_sx, patch_sy;

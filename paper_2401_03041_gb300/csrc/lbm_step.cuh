@@ -43,7 +43,7 @@ __device__ __forceinline__ typename Store<S>::R pull(const DevParams& P, const S
   constexpr R w = (R)weight<Q>(I);
   const R wsh = w * shift;
   if (P.walls && (zs < 0 || zs >= P.nz)) {
-    const R v = Store<S>::ld(base + (size_t)opp<Q>(I) * P.N + cell_index(P, x, y, z)) + wsh;
+    const R v = Store<S>::ld(base + (size_t)opp<Q>(I) * P.Np + pdf_index(P, x, y, z)) + wsh;
     if constexpr (ABB) {
       const R Tw = zs < 0 ? rp.T_bottom : rp.T_top;
       return -v + (R)2 * w * Tw;
@@ -53,7 +53,7 @@ __device__ __forceinline__ typename Store<S>::R pull(const DevParams& P, const S
   const int xs = wrap(x - cx<Q>(I), P.nx);
   const int ys = wrap(y - cy<Q>(I), P.ny);
   const int zz = P.walls ? zs : wrap(zs, P.nz);
-  return Store<S>::ld(base + (size_t)I * P.N + cell_index(P, xs, ys, zz)) + wsh;
+  return Store<S>::ld(base + (size_t)I * P.Np + pdf_index(P, xs, ys, zz)) + wsh;
 }
 
 template <int Q, bool ABB, class S>
@@ -153,7 +153,7 @@ step_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, int zc
         if constexpr (QF > 0) return pull<QF, true, decltype(I)::value>(P, A.f_src, x, y, z, shf);
         else return (R)0;
       };
-      cell_update<S, QH, QF>(P, A, x, y, z, cell, cell, mode, s_phi[sc][c0], s_T[sc][c0], fd, rgx, rgy,
+      cell_update<S, QH, QF>(P, A, x, y, z, cell, pdf_index(P, x, y, z), mode, s_phi[sc][c0], s_T[sc][c0], fd, rgx, rgy,
                              rgz, rlap, geth, getg, getf, dsum);
     }
     __syncthreads();

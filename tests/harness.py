@@ -97,7 +97,8 @@ def ragged_workload(thermal="D3Q7", q_phase=15, walls=True, precision="fp64", sh
 
 
 def bulk_fits(precision, q_phase, thermal):
-    """Whether the bulk-copy kernel's shared memory fits for this combination."""
+    """Whether the bulk kernel's shared memory (three h/f box stages, two g
+    stages, phi/T planes) fits for this combination."""
     qf = int(thermal[3:]) if thermal.startswith("D3Q") else 0
     nhf = q_phase + qf
     s = {"fp64": 8, "fp32": 4, "fp16": 2}[precision]
@@ -105,8 +106,9 @@ def bulk_fits(precision, q_phase, thermal):
     cols = 32 if s == 8 else 64
     W = cols + 2 * (16 // s)
     rs = 8 if s == 8 else 4
-    smem = (3 * nhf * (rows + 2) * W * s + 2 * 27 * rows * W * s
-            + 6 * (cols + 2) * (rows + 2) * rs + 64)
+    hfb = -(-W * (rows + 2) * s // 128) * 128
+    gb = -(-W * rows * s // 128) * 128
+    smem = 3 * nhf * hfb + 2 * 27 * gb + 6 * (cols + 2) * (rows + 2) * rs + 64 + 128
     return smem <= 232448
 
 
