@@ -36,11 +36,10 @@ void launch_pdf_convert(const DevParams& P, int Q, bool to_f64, void* pdf, doubl
 
 template <class S>
 void launch_ghost_fill(const DevParams& P, void* buf, int nq, cudaStream_t st) {
-  const long long per_plane = 2LL * P.GX * P.ny + 2LL * P.GY * P.NXP;
-  const long long total = per_plane * P.nz * nq;
-  const long long blocks = (total + 255) / 256;
-  const int grid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
-  if (total > 0) ghost_fill_kernel<S><<<grid, 256, 0, st>>>(P, (S*)buf, nq);
+  const int per_plane = 2 * P.GX * P.ny + 2 * P.GY * P.NXP;
+  const int bx = (per_plane + 255) / 256;
+  // grid y = z and grid z = direction; nz is bounded by 65535 in the API
+  ghost_fill_kernel<S><<<dim3(bx, P.nz, nq), 256, 0, st>>>(P, (S*)buf);
 }
 
 template <class S, int QH>

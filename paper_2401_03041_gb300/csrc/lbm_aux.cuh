@@ -195,33 +195,28 @@ __global__ void f64_to_pdf_kernel(const DevParams P, const double* __restrict__ 
 // the left/right column strips of the interior rows, then the full top and
 // bottom row strips.
 template <class S>
-__global__ void ghost_fill_kernel(const DevParams P, S* __restrict__ buf, int nq) {
+__global__ void ghost_fill_kernel(const DevParams P, S* __restrict__ buf) {
+  // grid: x over the ghost positions of one plane, y = z, z = direction
   const int GX = P.GX, GY = P.GY;
-  const long long side = 2LL * GX * P.ny;          // column strips
-  const long long rows = 2LL * GY * P.NXP;         // row strips (incl. corners)
-  const long long per_plane = side + rows;
-  const long long total = per_plane * P.nz * nq;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
-       k += (long long)gridDim.x * blockDim.x) {
-    const long long qz = k / per_plane;
-    long long r = k - qz * per_plane;
-    const int z = (int)(qz % P.nz), q = (int)(qz / P.nz);
+  const int side = 2 * GX * P.ny;            // column strips of the interior rows
+  const int per_plane = side + 2 * GY * P.NXP;
+  const int z = blockIdx.y, q = blockIdx.z;
+  S* base = buf + (size_t)q * P.Np;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < per_plane; r += gridDim.x * blockDim.x) {
     int x, y;
     if (r < side) {
-      y = (int)(r / (2 * GX));
-      const int j = (int)(r % (2 * GX));
+      y = r / (2 * GX);
+      const int j = r - y * (2 * GX);
       x = j < GX ? j - GX : P.nx + (j - GX);
     } else {
-      r -= side;
-      const int j = (int)(r / P.NXP);            // 0 .. 2 GY - 1
-      x = (int)(r % P.NXP) - GX;
+      const int rr = r - side;
+      const int j = rr / P.NXP;              // 0 .. 2 GY - 1
+      x = rr - j * P.NXP - GX;
       y = j < GY ? j - GY : P.ny + (j - GY);
     }
-    // padded columns past nx + GX (row pitch padding) are not addressed by anyone
-    if (x >= P.nx + GX) continue;
+    if (x >= P.nx + GX) continue;            // row-pitch padding: never read
     int xs = x % P.nx; if (xs < 0) xs += P.nx;
     int ys = y % P.ny; if (ys < 0) ys += P.ny;
-    S* base = buf + (size_t)q * P.Np;
     base[pdf_index(P, x, y, z)] = base[pdf_index(P, xs, ys, z)];
   }
 }
