@@ -276,7 +276,10 @@ def main():
     cells = w.cells
     mlups = cells * args.steps * world / secs / 1e6
     per_step = secs / args.steps
-    launches_per_step = 1 if w.thermal.startswith("D3Q") else (2 if w.thermal == "RK2" else 4)
+    # one step-kernel launch, + one ghost-fill launch with the bulk kernel,
+    # + the RK stages of the finite-difference energy solvers
+    launches_per_step = (1 + (1 if kinfo["kernel"] == "bulk" else 0)
+                         + (0 if w.thermal.startswith("D3Q") else (1 if w.thermal == "RK2" else 3)))
 
     # ---------------- e2e: a job through the C ABI with host buffers
     # init from the host droplet table, K steps each returning FP64

@@ -47,6 +47,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                : "memory");
 }
+// Bring a tensor-map descriptor into the descriptor cache.
+__device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
+}
+
 // 4D tensor box (x, y, z, direction) global -> shared, completing on bar.
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
                                             int c3, uint64_t* bar) {
@@ -138,7 +143,9 @@ struct BulkSmem {
   static constexpr uint32_t g_tx = (uint32_t)((size_t)27 * G::W * G::TYB * sizeof(S));
 };
 
-// Issue the boxes of one stage, one direction per thread (threads 0..ndir-1).
+// Issue the boxes of one stage.  Box issue is spread over the warps (lane j
+// of warp w issues direction w + j * nwarps): box issues by lanes of one warp
+// serialise, so a single warp issuing every box would stall the whole CTA.
 //   KIND 0 (HF): rows y0 - 1 .. y0 + TYB of plane p; directions 0..QH-1 from
 //                h (map mh), QH..QH+QF-1 from f (map mf).
 //   KIND 1 (G):  rows y0 .. y0 + TYB - 1 of plane p; g directions (map mg).
@@ -150,8 +157,9 @@ __device__ __forceinline__ void issue_stage(const DevParams& P, const CUtensorMa
                                             int tid) {
   using G = BulkGeom<S>;
   constexpr int ndir = KIND == 0 ? QH + QF : 27;
-  if (tid >= ndir) return;
-  const int d = tid;
+  constexpr int nwarps = G::NT / 32;
+  const int d = (tid >> 5) + (tid & 31) * nwarps;
+  if (d >= ndir) return;
   // plane whose tile this is (walls: the ghost planes reuse the boundary plane)
   int pe = p;
   if (P.walls) pe = p < 0 ? 0 : (p >= P.nz ? P.nz - 1 : p);
@@ -222,6 +230,10 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
   if (tid == 0) {
     for (int k = 0; k < 5; ++k) mbar_init(&bar[k], 1);
     mbar_fence_init();
+  } else if (tid == 32) {
+    tma_prefetch_desc(&mh);
+    tma_prefetch_desc(&mg);
+    tma_prefetch_desc(&mf);
   }
   __syncthreads();
 
