@@ -197,7 +197,11 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="time the step kernel only (no CPU, e2e, FP64 or error legs; for profiling)")
     args = ap.parse_args()
+    if args.kernel_only:
+        args.no_cpu = args.no_fp64 = True
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
@@ -284,20 +288,24 @@ def main():
     # ---------------- e2e: a job through the C ABI with host buffers
     # init from the host droplet table, K steps each returning FP64
     # diagnostics to the host, final phi field copied to host memory.
-    host_phi = torch.empty((1, w.nz, w.ny, w.nx), dtype=torch.float32, pin_memory=True)
-    torch.cuda.synchronize(dev)
-    barrier()
-    t0 = time.perf_counter()
-    d.init_droplets(w.droplets)
-    for _ in range(args.steps):
-        d.step_diagnostics(1)
-    d.fields(lbm.FIELD_PHI, dtype="f32", out=host_phi)
-    torch.cuda.synchronize(dev)
-    e2e_secs = max_over_ranks(time.perf_counter() - t0)
-    barrier()
-    e2e_mlups = cells * args.steps * world / e2e_secs / 1e6
-    h2d = len(w.droplets) * 7 * 8 / args.steps
-    d2h = (args.steps * 64 + 4 * cells) / args.steps
+    e2e = None
+    if not args.kernel_only:
+        host_phi = torch.empty((1, w.nz, w.ny, w.nx), dtype=torch.float32, pin_memory=True)
+        torch.cuda.synchronize(dev)
+        barrier()
+        t0 = time.perf_counter()
+        d.init_droplets(w.droplets)
+        for _ in range(args.steps):
+            d.step_diagnostics(1)
+        d.fields(lbm.FIELD_PHI, dtype="f32", out=host_phi)
+        torch.cuda.synchronize(dev)
+        e2e_secs = max_over_ranks(time.perf_counter() - t0)
+        barrier()
+        e2e = {"value": cells * args.steps * world / e2e_secs / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": len(w.droplets) * 7 * 8 / args.steps,
+               "d2h_bytes_per_step": (args.steps * 64 + 4 * cells) / args.steps,
+               "what": "lbm_init_droplets from host table + K x lbm_step_diagnostics(1) "
+                       "(FP64 diagnostics to host each step) + final phi to pinned host"}
     diag_final = d.diagnostics()
     del d
     torch.cuda.empty_cache()
@@ -315,7 +323,7 @@ def main():
 
     # ---------------- stated error: reduced precision vs FP64 on the 32^3 droplet
     err = None
-    if rank == 0:
+    if rank == 0 and not args.kernel_only:
         c1 = W.config1()
         res = {}
         for prec in ("fp64", args.precision):
@@ -366,10 +374,7 @@ def main():
                           "sample": f"{cpu['name']}: {cpu['steps']} FP64 numpy oracle steps in "
                                     f"{cpu['seconds']:.1f} s, single thread"}
                          if cpu and "mlups" in cpu else cpu),
-        "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h,
-                "what": "lbm_init_droplets from host table + K x lbm_step_diagnostics(1) "
-                        "(FP64 diagnostics to host each step) + final phi to pinned host"},
+        "e2e": e2e,
         "gpu_launches": args.steps * launches_per_step,
         "fp64": fp64,
         "fp32_vs_fp64": fp64 and {"speedup": mlups / fp64["mlups"]},

@@ -127,7 +127,8 @@ void lbm_default_params(lbm_params* p);
 size_t lbm_workspace_bytes(int nx, int ny, int nz, lbm_precision prec,
                            lbm_thermal thermal, int q_phase);
 
-/* Create a domain of nx * ny * nz cells (each >= 1, nz <= 65535; N < 2^40).
+/* Create a domain of nx * ny * nz cells (each >= 1, ny <= 262140, nz <= 65535;
+ * N < 2^40).
  *   q_phase:   15 (D3Q15) or 27 (D3Q27) for the phase-field PDFs h.
  *   stream:    a cudaStream_t (NULL = legacy default stream).
  *   workspace: device pointer of at least lbm_workspace_bytes(...) bytes,

@@ -36,10 +36,11 @@ void launch_pdf_convert(const DevParams& P, int Q, bool to_f64, void* pdf, doubl
 
 template <class S>
 void launch_ghost_fill(const DevParams& P, void* buf, int nq, cudaStream_t st) {
-  const int per_plane = 2 * P.GX * P.ny + 2 * P.GY * P.NXP;
-  const int bx = (per_plane + 255) / 256;
+  constexpr int V = 16 / (int)sizeof(S);
+  const int per_plane = P.NYP + 2 * P.GY * ((P.nx + V - 1) / V);
+  const int bx = (per_plane + 127) / 128;
   // grid y = z and grid z = direction; nz is bounded by 65535 in the API
-  ghost_fill_kernel<S><<<dim3(bx, P.nz, nq), 256, 0, st>>>(P, (S*)buf);
+  ghost_fill_kernel<S><<<dim3(bx, P.nz, nq), 128, 0, st>>>(P, (S*)buf);
 }
 
 template <class S, int QH>

@@ -32,9 +32,9 @@ void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
 template <class S, int QH, int QF>
 void launch_init(const DevParams& P, const double* drops, int nd, S* h, S* g, S* f,
                  typename Store<S>::R* T, cudaStream_t st) {
-  const long long blocks = (P.N + 255) / 256;
-  const int grid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
-  init_kernel<S, QH, QF><<<grid, 256, 0, st>>>(P, drops, nd, h, g, f, T);
+  const dim3 grid((P.nx + kInitTX - 1) / kInitTX, (P.ny + kInitTY - 1) / kInitTY,
+                  (P.nz + kInitTZ - 1) / kInitTZ);
+  init_kernel<S, QH, QF><<<grid, kInitTX * kInitTY * kInitTZ, 0, st>>>(P, drops, nd, h, g, f, T);
 }
 
 #define LBM_INST(QF)                                                                          \

@@ -117,7 +117,8 @@ Pad padding(int nx, int ny, int nz, lbm_precision prec) {
 }
 
 bool layout(int nx, int ny, int nz, lbm_precision prec, lbm_thermal th, int qh, Layout* L) {
-  if (nx < 1 || ny < 1 || nz < 1 || nz > 65535) return false;
+  // launch grids put nz (one plane per z block) and ny / 4 on the 16-bit grid axes
+  if (nx < 1 || ny < 1 || nz < 1 || nz > 65535 || ny > 262140) return false;
   if (qh != 15 && qh != 27) return false;
   if (prec < LBM_FP64 || prec > LBM_FP16_STORE) return false;
   if (th < LBM_TH_D3Q7 || th > LBM_TH_RK4) return false;

@@ -98,57 +98,110 @@ __global__ void rk_stage_kernel(const DevParams P, const RF* __restrict__ psi, R
 
 // Initial state: tanh droplets (periodic minimum image), u = sum phi_k v_k,
 // conduction profile between walls; equilibria of Sec. 2.2 evaluated in FP64.
+//
+// A block covers a 32 x 4 x 2 tile of cells.  Before the per-cell loop it
+// culls the droplet table against the tile's bounding box: droplet k matters
+// to a cell only where 2 (r - R_k) / xi <= 40 (beyond that tanh rounds to -1
+// in FP64 and the droplet's term is exactly zero; it is taken as zero).  The
+// box test uses a lower bound on r with one lattice unit of margin, so it
+// never drops a droplet the per-cell test would keep.  Surviving droplets are
+// kept as bit masks, 1024 droplets per pass, and visited in ascending order.
+constexpr int kInitTX = 32, kInitTY = 4, kInitTZ = 2;
+
+__device__ __forceinline__ double min_image(double d, int n) { return d - n * rint(d / n); }
+
 template <class S, int QH, int QF>
-__global__ void init_kernel(const DevParams P, const double* __restrict__ drops, int nd, S* h, S* g,
-                            S* f, typename Store<S>::R* Tfield) {
+__global__ void __launch_bounds__(kInitTX * kInitTY * kInitTZ)
+init_kernel(const DevParams P, const double* __restrict__ drops, int nd, S* h, S* g, S* f,
+            typename Store<S>::R* Tfield) {
   using R = typename Store<S>::R;
+  constexpr int NT = kInitTX * kInitTY * kInitTZ;
   const auto& rp = P.pd;  // initialisation runs in FP64 in every mode
-  const size_t n = (size_t)P.N;
-  for (size_t cell = blockIdx.x * (size_t)blockDim.x + threadIdx.x; cell < n;
-       cell += (size_t)gridDim.x * blockDim.x) {
-    const int x = (int)(cell % P.nx);
-    const int y = (int)((cell / P.nx) % P.ny);
-    const int z = (int)(cell / ((size_t)P.nx * P.ny));
-    double phi = 0.0, ux = 0.0, uy = 0.0, uz = 0.0;
-    for (int k = 0; k < nd; ++k) {
-      const double* d = drops + 7 * k;
-      double dx = x + 0.5 - d[0], dy = y + 0.5 - d[1], dz = z + 0.5 - d[2];
-      dx -= P.nx * rint(dx / P.nx);
-      dy -= P.ny * rint(dy / P.ny);
-      if (!P.walls) dz -= P.nz * rint(dz / P.nz);
-      const double r = sqrt(dx * dx + dy * dy + dz * dz);
-      const double pk = 0.5 * (1.0 + tanh(2.0 * (d[3] - r) / rp.xi));
-      phi = fmax(phi, pk);
-      ux += pk * d[4];
-      uy += pk * d[5];
-      uz += pk * d[6];
-    }
-    const double T0 = P.walls ? rp.T_bottom + (rp.T_top - rp.T_bottom) * (z + 0.5) / P.nz : 0.0;
-    const size_t pc = pdf_index(P, x, y, z);
-    const size_t np = (size_t)P.Np;
-    const double uu = ux * ux + uy * uy + uz * uz;
-#pragma unroll
-    for (int i = 0; i < QH; ++i) {
-      const double cu = cx<QH>(i) * ux + cy<QH>(i) * uy + cz<QH>(i) * uz;
-      const double e = weight<QH>(i) * phi * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-      Store<S>::st(h + (size_t)i * np + pc, (R)(e - weight<QH>(i) * rp.shift_h));
-    }
-#pragma unroll
-    for (int i = 0; i < 27; ++i) {
-      const double cu = cx<27>(i) * ux + cy<27>(i) * uy + cz<27>(i) * uz;
-      const double e = weight<27>(i) * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-      Store<S>::st(g + (size_t)i * np + pc, (R)e);
-    }
-    if constexpr (QF > 0) {
-#pragma unroll
-      for (int i = 0; i < QF; ++i) {
-        const double cu = cx<QF>(i) * ux + cy<QF>(i) * uy + cz<QF>(i) * uz;
-        const double e = weight<QF>(i) * T0 * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-        Store<S>::st(f + (size_t)i * np + pc, (R)(e - weight<QF>(i) * rp.shift_f));
+  __shared__ uint32_t mask[32];
+  const int tid = threadIdx.x;
+  const int x = blockIdx.x * kInitTX + (tid % kInitTX);
+  const int y = blockIdx.y * kInitTY + (tid / kInitTX) % kInitTY;
+  const int z = blockIdx.z * kInitTZ + tid / (kInitTX * kInitTY);
+  const bool inside = x < P.nx && y < P.ny && z < P.nz;
+  // tile bounding box of cell centres: centre and half extent per axis
+  const int bx0 = blockIdx.x * kInitTX, bx1 = min(bx0 + kInitTX, P.nx);
+  const int by0 = blockIdx.y * kInitTY, by1 = min(by0 + kInitTY, P.ny);
+  const int bz0 = blockIdx.z * kInitTZ, bz1 = min(bz0 + kInitTZ, P.nz);
+  const double bcx = 0.5 * (bx0 + bx1), bhx = 0.5 * (bx1 - bx0 - 1);
+  const double bcy = 0.5 * (by0 + by1), bhy = 0.5 * (by1 - by0 - 1);
+  const double bcz = 0.5 * (bz0 + bz1), bhz = 0.5 * (bz1 - bz0 - 1);
+  const double reach = 20.0 * rp.xi + 1.0;
+
+  double phi = 0.0, ux = 0.0, uy = 0.0, uz = 0.0;
+  for (int k0 = 0; k0 < nd; k0 += 1024) {
+    for (int j = tid; j < 1024; j += NT) {   // every warp takes whole 32-droplet words
+      const int k = k0 + j;
+      bool near = false;
+      if (k < nd) {
+        const double* d = drops + 7 * k;
+        double dx = bcx - d[0], dy = bcy - d[1], dz = bcz - d[2];
+        dx = min_image(dx, P.nx);
+        dy = min_image(dy, P.ny);
+        if (!P.walls) dz = min_image(dz, P.nz);
+        dx = fmax(fabs(dx) - bhx, 0.0);
+        dy = fmax(fabs(dy) - bhy, 0.0);
+        dz = fmax(fabs(dz) - bhz, 0.0);
+        const double lim = d[3] + reach;
+        near = dx * dx + dy * dy + dz * dz <= lim * lim;
       }
-    } else {
-      Tfield[cell] = (R)T0;
+      const unsigned bits = __ballot_sync(0xffffffffu, near);
+      if ((j & 31) == 0) mask[j >> 5] = bits;
     }
+    __syncthreads();
+    if (inside) {
+      for (int wd = 0; wd < 32; ++wd) {
+        for (uint32_t m = mask[wd]; m; m &= m - 1) {
+          const int k = k0 + wd * 32 + __ffs(m) - 1;
+          const double* d = drops + 7 * k;
+          double dx = x + 0.5 - d[0], dy = y + 0.5 - d[1], dz = z + 0.5 - d[2];
+          dx = min_image(dx, P.nx);
+          dy = min_image(dy, P.ny);
+          if (!P.walls) dz = min_image(dz, P.nz);
+          const double r = sqrt(dx * dx + dy * dy + dz * dz);
+          const double a = 2.0 * (d[3] - r) / rp.xi;
+          if (a < -40.0) continue;
+          const double pk = 0.5 * (1.0 + tanh(a));
+          phi = fmax(phi, pk);
+          ux += pk * d[4];
+          uy += pk * d[5];
+          uz += pk * d[6];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (!inside) return;
+  const size_t cell = ((size_t)z * P.ny + y) * P.nx + x;
+  const double T0 = P.walls ? rp.T_bottom + (rp.T_top - rp.T_bottom) * (z + 0.5) / P.nz : 0.0;
+  const size_t pc = pdf_index(P, x, y, z);
+  const size_t np = (size_t)P.Np;
+  const double uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+  for (int i = 0; i < QH; ++i) {
+    const double cu = cx<QH>(i) * ux + cy<QH>(i) * uy + cz<QH>(i) * uz;
+    const double e = weight<QH>(i) * phi * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    Store<S>::st(h + (size_t)i * np + pc, (R)(e - weight<QH>(i) * rp.shift_h));
+  }
+#pragma unroll
+  for (int i = 0; i < 27; ++i) {
+    const double cu = cx<27>(i) * ux + cy<27>(i) * uy + cz<27>(i) * uz;
+    const double e = weight<27>(i) * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    Store<S>::st(g + (size_t)i * np + pc, (R)e);
+  }
+  if constexpr (QF > 0) {
+#pragma unroll
+    for (int i = 0; i < QF; ++i) {
+      const double cu = cx<QF>(i) * ux + cy<QF>(i) * uy + cz<QF>(i) * uz;
+      const double e = weight<QF>(i) * T0 * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+      Store<S>::st(f + (size_t)i * np + pc, (R)(e - weight<QF>(i) * rp.shift_f));
+    }
+  } else {
+    Tfield[cell] = (R)T0;
   }
 }
 
@@ -191,33 +244,59 @@ __global__ void f64_to_pdf_kernel(const DevParams P, const double* __restrict__ 
 // Periodic ghost cells of one padded PDF buffer of nq directions: every
 // ghost position (x, y) outside [0, nx) x [0, ny) receives the value of cell
 // (x mod nx, y mod ny) of the same plane and direction (the single-GPU form
-// of a ghost-layer exchange).  Ghost positions of a plane are enumerated as
-// the left/right column strips of the interior rows, then the full top and
-// bottom row strips.
+// of a ghost-layer exchange).  Grid: x over the items of one plane, y = z,
+// z = direction.  Items [0, NYP): the ghost columns of padded row y (ghost
+// rows included, sources taken from row y mod ny); items [NYP, NYP + 2 GY
+// nvec): one 16-byte vector of interior columns of a ghost row.  With nx a
+// multiple of V = 16 / sizeof(S) (GX = V) a row's two ghost blocks are 16-byte
+// vectors; with nx a multiple of 2V each is written together with the
+// interior half of its 32-byte sector (the same values that half holds), so
+// that no sector is written partially.
 template <class S>
-__global__ void ghost_fill_kernel(const DevParams P, S* __restrict__ buf) {
-  // grid: x over the ghost positions of one plane, y = z, z = direction
-  const int GX = P.GX, GY = P.GY;
-  const int side = 2 * GX * P.ny;            // column strips of the interior rows
-  const int per_plane = side + 2 * GY * P.NXP;
+__global__ void __launch_bounds__(128) ghost_fill_kernel(const DevParams P, S* __restrict__ buf) {
+  constexpr int V = 16 / (int)sizeof(S);
+  const int GX = P.GX, GY = P.GY, nx = P.nx, ny = P.ny;
   const int z = blockIdx.y, q = blockIdx.z;
-  S* base = buf + (size_t)q * P.Np;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < per_plane; r += gridDim.x * blockDim.x) {
-    int x, y;
-    if (r < side) {
-      y = r / (2 * GX);
-      const int j = r - y * (2 * GX);
-      x = j < GX ? j - GX : P.nx + (j - GX);
+  S* plane = buf + (size_t)q * P.Np + (size_t)z * P.NYP * P.NXP;
+  const int nvec = (nx + V - 1) / V;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  auto wrap_y = [&](int y) { int ys = y % ny; return ys < 0 ? ys + ny : ys; };
+  if (r < P.NYP) {
+    const int y = r - GY;
+    S* row = plane + (size_t)r * P.NXP;                        // element x at row[x + GX]
+    const S* src = plane + (size_t)(wrap_y(y) + GY) * P.NXP;
+    if (nx % V == 0) {
+      const uint4 a = *reinterpret_cast<const uint4*>(src + GX);           // x = 0 .. V-1
+      const uint4 b = *reinterpret_cast<const uint4*>(src + GX + nx - V);  // x = nx-V .. nx-1
+      if (nx % (2 * V) == 0) {
+        // sectors [x -V .. V-1] and [x nx-V .. nx+V-1] both become (b, a)
+        uint4* s0 = reinterpret_cast<uint4*>(row);
+        uint4* s1 = reinterpret_cast<uint4*>(row + GX + nx - V);
+        s0[0] = b; s0[1] = a;
+        s1[0] = b; s1[1] = a;
+      } else {
+        *reinterpret_cast<uint4*>(row) = b;
+        *reinterpret_cast<uint4*>(row + GX + nx) = a;
+      }
     } else {
-      const int rr = r - side;
-      const int j = rr / P.NXP;              // 0 .. 2 GY - 1
-      x = rr - j * P.NXP - GX;
-      y = j < GY ? j - GY : P.ny + (j - GY);
+      for (int j = 0; j < GX; ++j) {
+        int xl = (j - GX) % nx; if (xl < 0) xl += nx;               // ghost x = j - GX
+        row[j] = src[GX + xl];
+        row[GX + nx + j] = src[GX + (j % nx)];                      // ghost x = nx + j
+      }
     }
-    if (x >= P.nx + GX) continue;            // row-pitch padding: never read
-    int xs = x % P.nx; if (xs < 0) xs += P.nx;
-    int ys = y % P.ny; if (ys < 0) ys += P.ny;
-    base[pdf_index(P, x, y, z)] = base[pdf_index(P, xs, ys, z)];
+  } else {
+    const int k = r - P.NYP;
+    if (k >= 2 * GY * nvec) return;
+    const int which = k / nvec, j = k - which * nvec;
+    const int y = which < GY ? which - GY : ny + (which - GY);      // ghost row
+    S* dst = plane + (size_t)(y + GY) * P.NXP + GX + j * V;
+    const S* src = plane + (size_t)(wrap_y(y) + GY) * P.NXP + GX + j * V;
+    if (j * V + V <= nx) {
+      *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
+    } else {
+      for (int e = 0; e < nx - j * V; ++e) dst[e] = src[e];
+    }
   }
 }
 

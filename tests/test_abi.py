@@ -63,7 +63,9 @@ def test_workspace_bytes(L):
     assert pdf32 < 1.03 * 2 * 49 * 512 ** 3 * 4        # ghost cells cost < 3 %
     nb16 = L.lbm_workspace_bytes(64, 64, 64, 2, 4, 27)
     assert nb16 >= 2 * (27 + 27) * _padded(64, 64, 64, 2) * 2 + 5 * 64 ** 3 * 4
-    for bad in [(0, 4, 4, 0, 0, 15), (4, 4, 4, 3, 0, 15), (4, 4, 4, 0, 6, 15), (4, 4, 4, 0, 0, 19)]:
+    assert L.lbm_workspace_bytes(1, 262140, 1, 1, 0, 15) > 0
+    for bad in [(0, 4, 4, 0, 0, 15), (4, 4, 4, 3, 0, 15), (4, 4, 4, 0, 6, 15), (4, 4, 4, 0, 0, 19),
+                (1, 262141, 1, 1, 0, 15), (1, 1, 65536, 1, 0, 15)]:
         assert L.lbm_workspace_bytes(*bad) == 0
 
 

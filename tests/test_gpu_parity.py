@@ -108,6 +108,35 @@ def test_bulk_multi_tile_chunked_fp64(walls, monkeypatch):
     compare_all(d, o, w, TOL64, f"bulk chunked walls={walls}")
 
 
+@pytest.mark.parametrize("nx", [74, 75])
+def test_bulk_ghost_fill_paths_fp64(nx):
+    """Periodic in x and y with nx a multiple of the 16-byte vector width but
+    not of two vectors (74) or not of one (75): the two slower ghost-fill
+    paths, against the oracle."""
+    w = ragged_workload("D3Q7", 15, walls=False, shape=(nx, 16, 8))
+    o = oracle_for(w)
+    o.step(8)
+    d = gpu_domain(w, kernel="bulk")
+    d.step(8)
+    compare_all(d, o, w, TOL64, f"bulk ghost paths nx={nx}")
+
+
+@pytest.mark.parametrize("precision,nx", [("fp32", 76), ("fp32", 78), ("fp16", 88), ("fp16", 84)])
+def test_bulk_ghost_fill_paths_reduced_precision(precision, nx):
+    """The same ghost-fill paths in FP32 / FP16 storage: bulk equals generic
+    to the storage rounding after 12 periodic steps."""
+    w = ragged_workload("D3Q7", 15, walls=False, precision=precision, shape=(nx, 16, 8))
+    a = gpu_domain(w, kernel="generic")
+    b = gpu_domain(w, kernel="bulk")
+    a.step(12)
+    b.step(12)
+    fa, fb = gpu_fields(a), gpu_fields(b)
+    tol = 1e-5 if precision == "fp32" else 1e-2
+    for k in ("phi", "u", "p", "T"):
+        e = relerr(fb[k], fa[k])
+        assert e < tol, (precision, nx, k, e)
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
 @pytest.mark.parametrize("thermal", ["D3Q7", "RK2"])
 def test_bulk_equals_generic_reduced_precision(precision, thermal):
