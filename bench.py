@@ -26,11 +26,23 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "fused step MLUPS FP32 vs FP64 at stated error, % HBM roofline; adjoint/fwd cost"
-BYTES_PER_CELL = {  # algorithmic bytes per cell update: each PDF read once + written once
-    ("fp32", "D3Q7"): 2 * (15 + 27 + 7) * 4,
-    ("fp64", "D3Q7"): 2 * (15 + 27 + 7) * 8,
-    ("fp16", "D3Q7"): 2 * (15 + 27 + 7) * 2,
-}
+STORE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2}
+FIELD_BYTES = {"fp64": 8, "fp32": 4, "fp16": 4}
+# Field values moved per cell and step by the RK schedules: RK2 = step kernel
+# (T read, u and S1 written) + final stage (S1, u, T read, T written) = 11;
+# RK4 = step kernel (T read; u, S1, acc written) + two middle stages (stage
+# field, u, T read; next stage field written; acc read and written) + final
+# stage (S3, u, T, acc read; T written) = 29.
+RK_FIELDS = {"RK2": 11, "RK4": 29}
+
+
+def bytes_per_cell(precision: str, thermal: str, q_phase: int = 15) -> int:
+    """Algorithmic bytes per cell update: every PDF read once and written once,
+    plus the stage fields of the RK energy solvers; halo re-reads (L2) and
+    derived fields (phi, T, u computed in the kernel) are not counted."""
+    qf = int(thermal[3:]) if thermal.startswith("D3Q") else 0
+    pdf = 2 * (q_phase + 27 + qf) * STORE_BYTES[precision]
+    return pdf + RK_FIELDS.get(thermal, 0) * FIELD_BYTES[precision]
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -45,18 +57,21 @@ def peaks():
 
 
 def kernel_source_sha() -> str:
+    """Hash of the device-code sources (headers and instantiation units; the
+    host-side API file is not part of any kernel)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2401_03041_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
+        if name.endswith(".cuh") or (name.startswith("inst_") and name.endswith(".cu")):
             with open(os.path.join(csrc, name), "rb") as fh:
                 h.update(name.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
-def traffic_per_cell():
-    """DRAM bytes per cell of the step kernel from the committed ncu summary,
-    or None if the kernel sources changed since those counters were taken."""
+def traffic_per_cell(precision: str, thermal: str, n: int):
+    """DRAM bytes per cell of the step kernel from the committed ncu summary
+    (one capture of this workload), or None if the kernel sources changed
+    since those counters were taken or the capture was of another workload."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     try:
         with open(path) as fh:
@@ -64,6 +79,8 @@ def traffic_per_cell():
     except Exception:
         return None
     if d.get("source_sha") != kernel_source_sha():
+        return None
+    if (d.get("precision"), d.get("thermal"), d.get("n")) != (precision, thermal, n):
         return None
     return float(d["dram_bytes_per_cell"])
 
@@ -262,21 +279,26 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
+        d.profile_read()            # discard launches timed before this region
+        d.profile_steps(True)
         e0.record(st)
         d.step(steps)
         e1.record(st)
         torch.cuda.synchronize(dev)
+        d.profile_steps(False)
+        kms, kn = d.profile_read()  # step-kernel launches alone (events on the same stream)
         clk = sampler.stop() if sampler else None
         barrier()
-        return e0.elapsed_time(e1) / 1e3, clk
+        return e0.elapsed_time(e1) / 1e3, clk, (kms / kn / 1e3 if kn else None)
 
     # ---------------- headline: FP32 (or --precision) fused step
     d = make_domain(args.precision)
     kinfo = d.kernel_info()
     sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
                            if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
-    secs, clocks = timed_steps(d, args.steps, args.warmup, sampler)
+    secs, clocks, kernel_secs = timed_steps(d, args.steps, args.warmup, sampler)
     secs = max_over_ranks(secs)
+    kernel_secs = max_over_ranks(kernel_secs) if kernel_secs else None
     cells = w.cells
     mlups = cells * args.steps * world / secs / 1e6
     per_step = secs / args.steps
@@ -314,7 +336,7 @@ def main():
     fp64 = None
     if not args.no_fp64 and args.precision != "fp64":
         d64 = make_domain("fp64")
-        s64, _ = timed_steps(d64, args.fp64_steps, 3)
+        s64, _, _ = timed_steps(d64, args.fp64_steps, 3)
         s64 = max_over_ranks(s64)
         fp64 = {"mlups": cells * args.fp64_steps * world / s64 / 1e6,
                 "ms_per_step": s64 / args.fp64_steps * 1e3, "steps": args.fp64_steps}
@@ -349,9 +371,11 @@ def main():
         return 0
 
     peak, peak_kind = peaks()
-    bpc = BYTES_PER_CELL.get((args.precision, w.thermal))
-    achieved = bpc * cells / per_step / 1e9 if bpc else None
-    tpc = traffic_per_cell()
+    bpc = bytes_per_cell(args.precision, w.thermal, w.q_phase)
+    # the dominant kernel's own average launch time (CUDA events around each
+    # step-kernel launch on the domain's stream, inside the timed region)
+    achieved = bpc * cells / kernel_secs / 1e9 if (bpc and kernel_secs) else None
+    tpc = traffic_per_cell(args.precision, w.thermal, args.n)
     line = {
         "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
@@ -367,6 +391,8 @@ def main():
                      "frac": achieved / peak if achieved else None,
                      "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
                      "bytes_per_cell": bpc,
+                     "kernel_ms_per_launch": kernel_secs * 1e3 if kernel_secs else None,
+                     "step_ms": per_step * 1e3,
                      "traffic": tpc * cells if tpc else None,
                      "kernel": "lbm::step_bulk_kernel (fused h/g/f stream-collide, cp.async.bulk staging)"
                                if kinfo["kernel"] == "bulk" else "lbm::step_kernel (fused, generic)"},

@@ -206,12 +206,23 @@ lbm_status lbm_get_level(lbm_domain* dom, int64_t* level);
 lbm_status lbm_synchronize(lbm_domain* dom, int timeout_ms);
 
 /* Launch configuration of the domain's step kernel: info[0] = 1 for the
- * bulk-copy kernel (rows staged in shared memory by cp.async.bulk), 0 for
+ * bulk kernel (PDF boxes staged in shared memory by tensor-TMA copies), 0 for
  * the generic kernel; info[1..3] = grid x, y, z; info[4] = planes per CTA;
  * info[5] = dynamic shared memory bytes.  info holds 6 int32 values.  The
  * environment variable LBM_KERNEL=generic, read at creation, forces the
  * generic kernel; LBM_ZCHUNK=<planes> sets the planes per CTA. */
 lbm_status lbm_kernel_info(lbm_domain* dom, int32_t* info);
+
+/* Step-kernel timing, a measurement aid (the paper has no counterpart).
+ * After lbm_profile_steps(dom, 1) each launch of the step kernel by lbm_step /
+ * lbm_step_diagnostics (the first LBM_MAX_PROFILED since the last read) is
+ * bracketed by CUDA events recorded on the domain's stream; the ghost-fill
+ * and RK-stage launches are not included.  lbm_profile_steps(dom, 0) stops
+ * recording.  lbm_profile_read synchronises the stream, returns the summed
+ * duration (ms) and the number of timed launches, and resets the count. */
+#define LBM_MAX_PROFILED 4096
+lbm_status lbm_profile_steps(lbm_domain* dom, int enable);
+lbm_status lbm_profile_read(lbm_domain* dom, double* ms_total, int32_t* launches);
 
 /* Message of the calling thread's most recent failed call ("" if none). */
 const char* lbm_last_error(void);

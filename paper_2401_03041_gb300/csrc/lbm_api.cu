@@ -177,6 +177,10 @@ struct lbm_domain {
   lbm_status sticky;
   std::string sticky_msg;
   TMaps maps[2];  // tensor maps of PDF set 0 / 1 (bulk kernel)
+  // step-kernel timing (lbm_profile_steps): event pairs around each launch
+  std::vector<cudaEvent_t> prof_ev;
+  bool prof_on = false;
+  int prof_n = 0;
 };
 
 namespace {
@@ -284,7 +288,10 @@ lbm_status run_pass(lbm_domain* d, int mode, void* macro_out = nullptr, int macr
     A.macro_out = macro_out;
     A.macro_dtype = macro_dtype;
     A.macro_mask = mask;
+    const bool timed = d->prof_on && (size_t)(2 * d->prof_n + 1) < d->prof_ev.size();
+    if (timed) cudaEventRecord(d->prof_ev[2 * d->prof_n], d->stream);
     step_launch<S>(d, A, mode);
+    if (timed) cudaEventRecord(d->prof_ev[2 * d->prof_n++ + 1], d->stream);
     if (mode & MODE_COLLIDE) ghost_fill(d, d->cur ^ 1);
     if ((mode & MODE_COLLIDE) && d->qf == 0) rk_tail<S>(d);
   };
@@ -523,6 +530,7 @@ lbm_status lbm_create_domain(int nx, int ny, int nz, lbm_precision prec, lbm_the
 lbm_status lbm_destroy_domain(lbm_domain* d) {
   if (!d) return fail(LBM_ERR_ARG, "null domain");
   cudaStreamSynchronize(d->stream);
+  for (cudaEvent_t e : d->prof_ev) cudaEventDestroy(e);
   if (d->owns_ws) cudaFree(d->ws);
   if (d->staging) cudaFree(d->staging);
   delete d;
@@ -851,6 +859,40 @@ lbm_status lbm_kernel_info(lbm_domain* d, int32_t* info) {
   info[3] = (int32_t)d->geo.grid.z;
   info[4] = d->geo.zchunk;
   info[5] = d->geo.bulk ? (int32_t)bulk_smem_bytes((int)d->prec, d->qh, d->qf) : 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_profile_steps(lbm_domain* d, int enable) {
+  lbm_status s = usable(d);
+  if (s != LBM_OK) return s;
+  if (enable && d->prof_ev.empty()) {
+    d->prof_ev.resize(2 * LBM_MAX_PROFILED);
+    for (cudaEvent_t& e : d->prof_ev) {
+      s = check_cuda(d, cudaEventCreate(&e), "profiling event creation");
+      if (s != LBM_OK) return s;
+    }
+  }
+  d->prof_on = enable != 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_profile_read(lbm_domain* d, double* ms_total, int32_t* launches) {
+  lbm_status s = usable(d);
+  if (s != LBM_OK) return s;
+  if (!ms_total || !launches) return fail(LBM_ERR_ARG, "null argument");
+  s = check_cuda(d, cudaStreamSynchronize(d->stream), "profiling sync");
+  if (s != LBM_OK) return s;
+  double total = 0.0;
+  for (int k = 0; k < d->prof_n; ++k) {
+    float ms = 0.f;
+    s = check_cuda(d, cudaEventElapsedTime(&ms, d->prof_ev[2 * k], d->prof_ev[2 * k + 1]),
+                   "profiling event time");
+    if (s != LBM_OK) return s;
+    total += ms;
+  }
+  *ms_total = total;
+  *launches = d->prof_n;
+  d->prof_n = 0;
   return LBM_OK;
 }
 

@@ -27,7 +27,8 @@ SYMBOLS = ("lbm_default_params", "lbm_workspace_bytes", "lbm_create_domain",
            "lbm_set_heater_patches", "lbm_init_droplets", "lbm_step",
            "lbm_step_diagnostics", "lbm_get_diagnostics", "lbm_get_fields",
            "lbm_get_pdfs", "lbm_set_pdfs", "lbm_get_level", "lbm_synchronize",
-           "lbm_stencil", "lbm_kernel_info", "lbm_last_error", "lbm_version")
+           "lbm_stencil", "lbm_kernel_info", "lbm_profile_steps", "lbm_profile_read",
+           "lbm_last_error", "lbm_version")
 
 
 class Params(ctypes.Structure):
@@ -112,6 +113,8 @@ def lib():
         "lbm_synchronize": (c_int, [vp, c_int]),
         "lbm_stencil": (c_int, [c_int, P(ctypes.c_int32), P(c_dbl)]),
         "lbm_kernel_info": (c_int, [vp, P(ctypes.c_int32)]),
+        "lbm_profile_steps": (c_int, [vp, c_int]),
+        "lbm_profile_read": (c_int, [vp, P(c_dbl), P(ctypes.c_int32)]),
         "lbm_last_error": (ctypes.c_char_p, []),
         "lbm_version": (ctypes.c_char_p, []),
     }
@@ -261,6 +264,16 @@ class Domain:
         _check("lbm_kernel_info", lib().lbm_kernel_info(self._h, v))
         return {"kernel": "bulk" if v[0] else "generic", "grid": (v[1], v[2], v[3]),
                 "zchunk": v[4], "smem_bytes": v[5]}
+
+    def profile_steps(self, enable: bool = True):
+        """Bracket each step-kernel launch with CUDA events on the domain's stream."""
+        _check("lbm_profile_steps", lib().lbm_profile_steps(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """(summed step-kernel milliseconds, timed launches) since the last read."""
+        ms, n = ctypes.c_double(), ctypes.c_int32()
+        _check("lbm_profile_read", lib().lbm_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
     def synchronize(self, timeout_ms: int = 60000):
         _check("lbm_synchronize", lib().lbm_synchronize(self._h, int(timeout_ms)))
