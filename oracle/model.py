@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).  Every array is
 float64; PDF arrays are shaped (Q, nz, ny, nx), scalar fields (nz, ny, nx),
 vector fields (3, nz, ny, nx); x is the fastest axis.
 
-Time stepping (Sec. 2.5 / Sec. 4.1, Alg. 1 and Alg. 2; pull "one step, two
+Time stepping (Sec. 4.1, Alg. 1 and Alg. 2; pull "one step, two
 grid" scheme): the stored PDFs are post-collision values.  One step
 
   a1  pulls every PDF, p*_i(x) = p_i(x - c_i)   (half-way bounce-back for
