@@ -224,6 +224,36 @@ lbm_status lbm_kernel_info(lbm_domain* dom, int32_t* info);
 lbm_status lbm_profile_steps(lbm_domain* dom, int enable);
 lbm_status lbm_profile_read(lbm_domain* dom, double* ms_total, int32_t* launches);
 
+/* FP64 mass and first moments of a caller-owned device field, computed
+ * without allocating any memory.  The paper has no counterpart: this is a
+ * utility of the library (the phi mass and centroid moments of lbm_diag, for
+ * a field that need not belong to a domain, e.g. a phi field already copied
+ * out with lbm_get_fields).
+ *   out_host[0] = sum psi, out_host[1..3] = sum psi (x + 1/2), sum psi
+ *   (y + 1/2), sum psi (z + 1/2) over the [z][y][x] field (cell-centred
+ *   coordinates), accumulated in FP64 in a fixed order (deterministic).
+ *   field:  device pointer to nx * ny * nz values, double (dtype 0) or
+ *           float (dtype 1).  nz <= LBM_MOMENTS_MAX_PLANES and nx * ny < 2^31,
+ *           else LBM_ERR_ARG (nothing is launched).
+ *   stream: cudaStream_t (NULL = legacy default stream).  Two kernels and a
+ *           32-byte copy are enqueued on it, then it is synchronised.
+ *   out_host: 4 doubles of host memory.
+ * Why it exists: every other call that needs scratch memory takes it from the
+ * domain's workspace.  Callers that must not allocate device memory at call
+ * time and hold no domain (a process under a hard device-memory budget, or
+ * one whose device memory all belongs to its own pool allocator) can use this
+ * one: its scratch is a fixed array compiled into the library, about 128 KB
+ * ((LBM_MOMENTS_MAX_PLANES + 1) x 4 doubles), whose contents never need to
+ * start at zero (every call writes each slot before reading it).
+ * The first call on a device looks up that array's device address, with the
+ * device current; make it before any stream capture on that device.  Calls
+ * that overlap in time on one device (from several host threads, or on
+ * streams without ordering between them) share the array and race: serialise
+ * them.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
+#define LBM_MOMENTS_MAX_PLANES 4096
+lbm_status lbm_field_moments(const void* field, int dtype, int nx, int ny, int nz,
+                             void* stream, double* out_host);
+
 /* Message of the calling thread's most recent failed call ("" if none). */
 const char* lbm_last_error(void);
 

@@ -49,3 +49,12 @@ void launch_pdf_convert(const DevParams& P, int Q, bool to_f64, void* pdf, doubl
 void launch_diag_finalize(const double* partials, int nblocks, double* out, cudaStream_t st);
 
 }  // namespace lbm
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+// Set the calling thread's lbm_last_error message and return s.
+lbm_status set_error(lbm_status s, const char* msg);
+
+}  // namespace lbm

@@ -898,6 +898,13 @@ lbm_status lbm_profile_read(lbm_domain* d, double* ms_total, int32_t* launches) 
 
 const char* lbm_last_error(void) { return g_last_error.c_str(); }
 
+}  // extern "C"
+
+// Record a failure for lbm_last_error from another translation unit.
+lbm_status lbm::set_error(lbm_status s, const char* msg) { return fail(s, msg); }
+
+extern "C" {
+
 const char* lbm_version(void) { return "thermocap-lbm-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"

@@ -28,6 +28,7 @@ SYMBOLS = ("lbm_default_params", "lbm_workspace_bytes", "lbm_create_domain",
            "lbm_step_diagnostics", "lbm_get_diagnostics", "lbm_get_fields",
            "lbm_get_pdfs", "lbm_set_pdfs", "lbm_get_level", "lbm_synchronize",
            "lbm_stencil", "lbm_kernel_info", "lbm_profile_steps", "lbm_profile_read",
+           "lbm_field_moments",
            "lbm_last_error", "lbm_version")
 
 
@@ -115,6 +116,7 @@ def lib():
         "lbm_kernel_info": (c_int, [vp, P(ctypes.c_int32)]),
         "lbm_profile_steps": (c_int, [vp, c_int]),
         "lbm_profile_read": (c_int, [vp, P(c_dbl), P(ctypes.c_int32)]),
+        "lbm_field_moments": (c_int, [vp, c_int, c_int, c_int, c_int, vp, P(c_dbl)]),
         "lbm_last_error": (ctypes.c_char_p, []),
         "lbm_version": (ctypes.c_char_p, []),
     }
@@ -155,6 +157,25 @@ def make_params(src=None, **kw) -> Params:
         else:
             setattr(p, name, float(val))
     return p
+
+
+def field_moments(field, stream=None):
+    """FP64 (sum psi, sum psi x, sum psi y, sum psi z) of a contiguous CUDA
+    tensor shaped [..., nz, ny, nx] (float64 or float32), through the
+    allocation-free entry point; ``stream`` is a torch stream (default: the
+    current stream)."""
+    import torch
+    if not field.is_cuda or not field.is_contiguous():
+        raise ValueError("field must be a contiguous CUDA tensor")
+    if field.dtype not in (torch.float64, torch.float32):
+        raise ValueError("field must be float64 or float32")
+    nz, ny, nx = field.shape[-3:]
+    st = stream if stream is not None else torch.cuda.current_stream(field.device)
+    out = (ctypes.c_double * 4)()
+    _check("lbm_field_moments", lib().lbm_field_moments(
+        ctypes.c_void_p(field.data_ptr()), 0 if field.dtype == torch.float64 else 1,
+        int(nx), int(ny), int(nz), ctypes.c_void_p(st.cuda_stream), out))
+    return tuple(out)
 
 
 def stencil(Q: int):
