@@ -214,11 +214,12 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-cost leg")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time the step kernel only (no CPU, e2e, FP64 or error legs; for profiling)")
     args = ap.parse_args()
     if args.kernel_only:
-        args.no_cpu = args.no_fp64 = True
+        args.no_cpu = args.no_fp64 = args.no_adjoint = True
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
@@ -343,6 +344,41 @@ def main():
         del d64
         torch.cuda.empty_cache()
 
+    # ---------------- adjoint cost: gradient of the droplet-capture objective
+    # (64^3, 2000 steps, checkpoints every 100) vs the same forward steps
+    adj = None
+    if rank == 0 and not args.no_adjoint:
+        c5 = W.config5(n=64)
+
+        def c5_domain():
+            dd = lbm.Domain(c5.nx, c5.ny, c5.nz, "fp64", c5.thermal, c5.q_phase, device=dev)
+            dd.set_params(c5.params)
+            pt = c5.patches
+            dd.set_heater_patches(pt.z, pt.sx, pt.sy, pt.x0, pt.y0, pt.intensity)
+            dd.init_droplets(c5.droplets)
+            return dd
+
+        dd = c5_domain()
+        dd.step(3)
+        dd.close()
+        dd = c5_domain()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        dd.step(c5.steps)
+        dd.diagnostics()            # synchronises; the J evaluation of a forward run
+        t_fwd = time.perf_counter() - t0
+        dd.close()
+        dd = c5_domain()
+        t0 = time.perf_counter()
+        J5, g5 = dd.adjoint_run(c5.steps, 100, c5.target, normal_cap=30.0)
+        t_adj = time.perf_counter() - t0
+        dd.close()
+        adj = {"workload": c5.name, "steps": c5.steps, "ckpt_every": 100, "normal_cap": 30.0,
+               "forward_s": t_fwd, "adjoint_run_s": t_adj, "cost_ratio": t_adj / t_fwd,
+               "what": "lbm_adjoint_run (forward with checkpoints + replay + adjoint steps) wall time "
+                       "over the plain forward run of the same steps; FP64",
+               "J": J5, "grad_inf": float(np.abs(g5).max())}
+
     # ---------------- stated error: reduced precision vs FP64 on the 32^3 droplet
     err = None
     if rank == 0 and not args.kernel_only:
@@ -402,6 +438,7 @@ def main():
                          if cpu and "mlups" in cpu else cpu),
         "e2e": e2e,
         "gpu_launches": args.steps * launches_per_step,
+        "adjoint": adj,
         "fp64": fp64,
         "fp32_vs_fp64": fp64 and {"speedup": mlups / fp64["mlups"]},
         "error_vs_fp64": err,

@@ -213,6 +213,48 @@ lbm_status lbm_synchronize(lbm_domain* dom, int timeout_ms);
  * generic kernel; LBM_ZCHUNK=<planes> sets the planes per CTA. */
 lbm_status lbm_kernel_info(lbm_domain* dom, int32_t* info);
 
+/* Gradient of a droplet-capture objective with respect to the heater-patch
+ * intensities, by the discrete adjoint of the time step.  The paper has no
+ * adjoint: this is the exact transpose of the linearised FP64 step of
+ * lbm_step (Sec. 2.2-2.3 model, Alg. 1 sweep order), for FP64 storage with
+ * the D3Q7 thermal LB and nx * ny < 2^31 (else LBM_ERR_UNSUPPORTED).
+ *   Starting from the current state (level n0), runs nsteps steps forward,
+ *   keeping a copy of the state every ckpt_every steps, and evaluates
+ *   J = |c - target|^2, c = (sum phi x, sum phi y, sum phi z) / sum phi at
+ *   level n0 + nsteps (cell-centred coordinates, no periodic unwrapping).
+ *   Then it runs the adjoint steps backwards, replaying each checkpoint
+ *   segment forward to recover the states it needs, and accumulates
+ *   dJ/dI_k (I_k = intensity of patch k of lbm_set_heater_patches).
+ *   On return the domain holds the forward result (level n0 + nsteps), *J_out
+ *   is J and dJdI_host[k] (host memory, one double per patch; may be NULL)
+ *   the gradient.
+ *   normal_cap <= 0: the exact discrete adjoint.  normal_cap > 0: the
+ *   interface normal n = grad phi / (|grad phi| + eps_n) is differentiated
+ *   only in cells where |4 phi (1 - phi) / xi| <= normal_cap |grad phi| (on
+ *   the equilibrium tanh profile the two sides are equal) and held fixed
+ *   elsewhere.  In far-field tails and at extrema of phi the exact derivative
+ *   of n grows like 4 phi (1 - phi) / (xi |grad phi|) without bound; over long
+ *   horizons (thousands of steps) the exact linearised step then amplifies
+ *   round-off-level perturbations there that the step itself keeps bounded,
+ *   and the exact gradient no longer describes finite changes of J.
+ *   Synchronises.  Allocates its checkpoint and adjoint buffers
+ *   (about (nsteps / ckpt_every + ckpt_every + 1) PDF sets plus 3 dense
+ *   adjoint sets) for the duration of the call: LBM_ERR_OOM if they do not fit.
+ * Errors: LBM_ERR_ARG (nsteps < 1, ckpt_every < 1, null target / J_out, NaN normal_cap),
+ * LBM_ERR_STATE (not initialised, zero phi mass), LBM_ERR_UNSUPPORTED. */
+lbm_status lbm_adjoint_run(lbm_domain* dom, int nsteps, int ckpt_every, const double* target,
+                           double normal_cap, double* J_out, double* dJdI_host);
+
+/* One adjoint step at the current state s: lam_out = (d Phi / d s)^T lam_in,
+ * where Phi is one lbm_step.  lam_in and lam_out are host arrays of
+ * (q_phase + 27 + 7) * N doubles in the order of lbm_get_pdfs (h, then g,
+ * then f, each [direction][z][y][x]); normal_cap as in lbm_adjoint_run.
+ * Same requirements as lbm_adjoint_run;
+ * allocates its buffers for the call; synchronises.  (The building block of
+ * lbm_adjoint_run, exposed for dot-product tests against the linearised step.) */
+lbm_status lbm_adjoint_step(lbm_domain* dom, const double* lam_in_host, double* lam_out_host,
+                            double normal_cap);
+
 /* Step-kernel timing, a measurement aid (the paper has no counterpart).
  * After lbm_profile_steps(dom, 1) each launch of the step kernel by lbm_step /
  * lbm_step_diagnostics (the first LBM_MAX_PROFILED since the last read) is

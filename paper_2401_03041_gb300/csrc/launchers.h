@@ -54,6 +54,16 @@ void launch_diag_finalize(const double* partials, int nblocks, double* out, cuda
 
 namespace lbm {
 
+// Adjoint step (FP64, LB thermal; inst_adjoint.cu).
+bool adj_supported(int qh, int qf);
+void adj_cell(const DevParams& P, const AdjPtrs& A, int qh, int qf, cudaStream_t st);
+void adj_fields(const DevParams& P, const AdjPtrs& A, cudaStream_t st);
+void adj_pull(const DevParams& P, const AdjPtrs& A, int qh, int qf, cudaStream_t st);
+void adj_seed(const DevParams& P, const double* dJdphi, double* lam, int qh, int qf, cudaStream_t st);
+void adj_centroid_seed(const DevParams& P, double mass, const double* c, const double* t, double* out,
+                       cudaStream_t st);
+void adj_patch_grad(const DevParams& P, const double* lam, double* dJdI, int qh, int qf, cudaStream_t st);
+
 // Set the calling thread's lbm_last_error message and return s.
 lbm_status set_error(lbm_status s, const char* msg);
 

@@ -8,6 +8,7 @@
 // Each step reads buffer `cur` and writes `cur ^ 1`, then flips `cur`.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -860,6 +861,179 @@ lbm_status lbm_kernel_info(lbm_domain* d, int32_t* info) {
   info[4] = d->geo.zchunk;
   info[5] = d->geo.bulk ? (int32_t)bulk_smem_bytes((int)d->prec, d->qh, d->qf) : 0;
   return LBM_OK;
+}
+
+// ---------------------------------------------------------------- adjoint
+
+}  // extern "C"
+
+namespace {
+
+// Device buffers of an adjoint computation (one allocation, released by the caller).
+struct AdjBuffers {
+  char* base = nullptr;
+  double *lam_a = nullptr, *lam_b = nullptr, *lstar = nullptr, *fld = nullptr, *tot = nullptr;
+  double *dJdphi = nullptr, *dJdI = nullptr;
+  char* sets = nullptr;  // nsets padded PDF sets
+  size_t set_bytes = 0;
+};
+
+size_t pdf_set_bytes(const lbm_domain* d) {
+  return (size_t)(d->qh + 27 + d->qf) * (size_t)d->dp.Np * sizeof(double);
+}
+
+lbm_status adj_alloc(lbm_domain* d, int nsets, AdjBuffers* B) {
+  const size_t N = (size_t)d->N, nq = (size_t)(d->qh + 27 + d->qf);
+  B->set_bytes = pdf_set_bytes(d);
+  size_t off = 0;
+  size_t o_la = off; off = align256(off + nq * N * 8);
+  size_t o_lb = off; off = align256(off + nq * N * 8);
+  size_t o_ls = off; off = align256(off + nq * N * 8);
+  size_t o_fl = off; off = align256(off + 9 * N * 8);
+  size_t o_to = off; off = align256(off + 2 * N * 8);
+  size_t o_dp = off; off = align256(off + N * 8);
+  size_t o_di = off; off = align256(off + LBM_MAX_PATCHES * 8);
+  size_t o_se = off; off = align256(off + (size_t)nsets * B->set_bytes);
+  if (cudaMalloc(&B->base, off) != cudaSuccess) {
+    cudaGetLastError();
+    B->base = nullptr;
+    return fail(LBM_ERR_OOM, "adjoint: device allocation of checkpoint and adjoint buffers failed");
+  }
+  B->lam_a = (double*)(B->base + o_la);
+  B->lam_b = (double*)(B->base + o_lb);
+  B->lstar = (double*)(B->base + o_ls);
+  B->fld = (double*)(B->base + o_fl);
+  B->tot = (double*)(B->base + o_to);
+  B->dJdphi = (double*)(B->base + o_dp);
+  B->dJdI = (double*)(B->base + o_di);
+  B->sets = B->base + o_se;
+  return LBM_OK;
+}
+
+char* cur_set(lbm_domain* d) { return d->ws + d->L.h[d->cur]; }
+
+// lam_out = (dPhi/ds)^T lam_in for the forward state held in 'state' (a
+// padded set).  Also accumulates dJ/dI from lam_in into B.dJdI if patches.
+lbm_status adj_one_step(lbm_domain* d, const char* state, const double* lam_in, double* lam_out,
+                        AdjBuffers& B, bool patch_grad, double ncap) {
+  const size_t np = (size_t)d->dp.Np;
+  AdjPtrs A;
+  A.s_h = (const double*)state;
+  A.s_g = A.s_h + (size_t)d->qh * np;
+  A.s_f = A.s_g + 27 * np;
+  A.lam_in = lam_in;
+  A.lstar = B.lstar;
+  A.fld = B.fld;
+  A.tot = B.tot;
+  A.lam_out = lam_out;
+  A.ncap = ncap;
+  if (patch_grad) adj_patch_grad(d->dp, lam_in, B.dJdI, d->qh, d->qf, d->stream);
+  adj_cell(d->dp, A, d->qh, d->qf, d->stream);
+  adj_fields(d->dp, A, d->stream);
+  adj_pull(d->dp, A, d->qh, d->qf, d->stream);
+  return check_launch(d, "adjoint step kernels");
+}
+
+lbm_status adj_check(lbm_domain* d) {
+  lbm_status s = usable(d);
+  if (s != LBM_OK) return s;
+  if (!d->inited) return fail(LBM_ERR_STATE, "domain not initialised");
+  if (d->prec != LBM_FP64 || !adj_supported(d->qh, d->qf))
+    return fail(LBM_ERR_UNSUPPORTED, "the adjoint needs FP64 storage and the D3Q7 thermal LB");
+  if ((long long)d->nx * d->ny >= (1LL << 31))
+    return fail(LBM_ERR_UNSUPPORTED, "the adjoint needs nx * ny < 2^31");
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_adjoint_step(lbm_domain* d, const double* lam_in_host, double* lam_out_host, double normal_cap) {
+  lbm_status s = adj_check(d);
+  if (s != LBM_OK) return s;
+  if (!lam_in_host || !lam_out_host) return fail(LBM_ERR_ARG, "null argument");
+  AdjBuffers B;
+  s = adj_alloc(d, 0, &B);
+  if (s != LBM_OK) return s;
+  const size_t bytes = (size_t)(d->qh + 27 + d->qf) * (size_t)d->N * 8;
+  s = check_cuda(d, cudaMemcpyAsync(B.lam_a, lam_in_host, bytes, cudaMemcpyHostToDevice, d->stream),
+                 "adjoint input copy");
+  if (s == LBM_OK) s = adj_one_step(d, cur_set(d), B.lam_a, B.lam_b, B, false, normal_cap);
+  if (s == LBM_OK)
+    s = check_cuda(d, cudaMemcpyAsync(lam_out_host, B.lam_b, bytes, cudaMemcpyDeviceToHost, d->stream),
+                   "adjoint output copy");
+  if (s == LBM_OK) s = check_cuda(d, cudaStreamSynchronize(d->stream), "adjoint sync");
+  cudaFree(B.base);
+  return s;
+}
+
+lbm_status lbm_adjoint_run(lbm_domain* d, int nsteps, int ckpt_every, const double* target, double normal_cap,
+                           double* J_out, double* dJdI_host) {
+  lbm_status s = adj_check(d);
+  if (s != LBM_OK) return s;
+  if (nsteps < 1 || ckpt_every < 1 || !target || !J_out || !(normal_cap == normal_cap))
+    return fail(LBM_ERR_ARG, "invalid argument");
+  if (ckpt_every > nsteps) ckpt_every = nsteps;
+  const int K = ckpt_every;
+  const int nseg = (nsteps + K - 1) / K;
+  AdjBuffers B;
+  // sets: nseg checkpoints, K replay states, the final state
+  s = adj_alloc(d, nseg + K + 1, &B);
+  if (s != LBM_OK) return s;
+  auto set_ptr = [&](int k) { return B.sets + (size_t)k * B.set_bytes; };
+  char* ckpt0 = set_ptr(0);
+  char* replay0 = set_ptr(nseg);
+  char* final_set = set_ptr(nseg + K);
+  auto copy_set = [&](char* dst, const char* src) {
+    return check_cuda(d, cudaMemcpyAsync(dst, src, B.set_bytes, cudaMemcpyDeviceToDevice, d->stream),
+                      "adjoint state copy");
+  };
+  const long long level0 = d->level;
+  // forward, checkpoint every K steps
+  for (int n = 0; n < nsteps && s == LBM_OK; ++n) {
+    if (n % K == 0) s = copy_set(ckpt0 + (size_t)(n / K) * B.set_bytes, cur_set(d));
+    if (s == LBM_OK) s = run_pass(d, MODE_COLLIDE);
+  }
+  if (s == LBM_OK) s = copy_set(final_set, cur_set(d));
+  lbm_diag dg;
+  if (s == LBM_OK) s = lbm_get_diagnostics(d, &dg);
+  double J = 0.0;
+  if (s == LBM_OK) {
+    if (!(dg.mass != 0.0)) s = fail(LBM_ERR_STATE, "adjoint: zero phi mass");
+  }
+  if (s == LBM_OK) {
+    const double c[3] = {dg.mx / dg.mass, dg.my / dg.mass, dg.mz / dg.mass};
+    for (int a = 0; a < 3; ++a) J += (c[a] - target[a]) * (c[a] - target[a]);
+    adj_centroid_seed(d->dp, dg.mass, c, target, B.dJdphi, d->stream);
+    adj_seed(d->dp, B.dJdphi, B.lam_a, d->qh, d->qf, d->stream);
+    s = check_launch(d, "adjoint seed");
+  }
+  if (s == LBM_OK) s = check_cuda(d, cudaMemsetAsync(B.dJdI, 0, LBM_MAX_PATCHES * 8, d->stream), "adjoint memset");
+  // backward over the segments, replaying each from its checkpoint
+  for (int seg = nseg - 1; seg >= 0 && s == LBM_OK; --seg) {
+    const int n0 = seg * K, n1 = std::min(n0 + K, nsteps);
+    s = copy_set(cur_set(d), ckpt0 + (size_t)seg * B.set_bytes);
+    for (int n = n0; n < n1 && s == LBM_OK; ++n) {
+      s = copy_set(replay0 + (size_t)(n - n0) * B.set_bytes, cur_set(d));
+      if (s == LBM_OK && n + 1 < n1) s = run_pass(d, MODE_COLLIDE);
+    }
+    for (int n = n1 - 1; n >= n0 && s == LBM_OK; --n) {
+      s = adj_one_step(d, replay0 + (size_t)(n - n0) * B.set_bytes, B.lam_a, B.lam_b, B, true, normal_cap);
+      std::swap(B.lam_a, B.lam_b);
+    }
+  }
+  // leave the domain at the forward result
+  if (s == LBM_OK) s = copy_set(cur_set(d), final_set);
+  if (s == LBM_OK && d->dp.npatch > 0 && dJdI_host)
+    s = check_cuda(d, cudaMemcpyAsync(dJdI_host, B.dJdI, (size_t)d->dp.npatch * 8, cudaMemcpyDeviceToHost,
+                                      d->stream),
+                   "adjoint gradient copy");
+  if (s == LBM_OK) s = check_cuda(d, cudaStreamSynchronize(d->stream), "adjoint sync");
+  d->level = level0 + nsteps;
+  cudaFree(B.base);
+  if (s == LBM_OK) *J_out = J;
+  return s;
 }
 
 lbm_status lbm_profile_steps(lbm_domain* d, int enable) {

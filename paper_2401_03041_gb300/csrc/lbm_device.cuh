@@ -166,4 +166,19 @@ struct StepPtrs {
   S* fd[27];
 };
 
+// Buffers of one adjoint step (lbm_adjoint.cuh): the forward state s^n as a
+// padded FP64 PDF set, and dense FP64 adjoint arrays (N values per direction
+// or field).
+struct AdjPtrs {
+  const double* s_h;      // forward state s^n: padded PDF arrays (direction stride Np)
+  const double* s_g;
+  const double* s_f;
+  const double* lam_in;   // lam^{n+1}, dense [(QH + 27 + QF)][N]
+  double* lstar;          // lam* (direct parts), dense [(QH + 27 + QF)][N]
+  double* fld;            // [9][N]: local adjoints of phi, T, grad phi (3), lap phi, grad T (3)
+  double* tot;            // [2][N]: total adjoints of phi and T
+  double* lam_out;        // lam^n, dense [(QH + 27 + QF)][N]
+  double ncap;            // > 0: interface normal differentiated only where |4 phi (1 - phi) / xi| <= ncap |grad phi|
+};
+
 }  // namespace lbm

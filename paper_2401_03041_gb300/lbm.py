@@ -28,7 +28,7 @@ SYMBOLS = ("lbm_default_params", "lbm_workspace_bytes", "lbm_create_domain",
            "lbm_step_diagnostics", "lbm_get_diagnostics", "lbm_get_fields",
            "lbm_get_pdfs", "lbm_set_pdfs", "lbm_get_level", "lbm_synchronize",
            "lbm_stencil", "lbm_kernel_info", "lbm_profile_steps", "lbm_profile_read",
-           "lbm_field_moments",
+           "lbm_field_moments", "lbm_adjoint_run", "lbm_adjoint_step",
            "lbm_last_error", "lbm_version")
 
 
@@ -117,6 +117,8 @@ def lib():
         "lbm_profile_steps": (c_int, [vp, c_int]),
         "lbm_profile_read": (c_int, [vp, P(c_dbl), P(ctypes.c_int32)]),
         "lbm_field_moments": (c_int, [vp, c_int, c_int, c_int, c_int, vp, P(c_dbl)]),
+        "lbm_adjoint_run": (c_int, [vp, c_int, c_int, P(c_dbl), c_dbl, P(c_dbl), P(c_dbl)]),
+        "lbm_adjoint_step": (c_int, [vp, vp, vp, c_dbl]),
         "lbm_last_error": (ctypes.c_char_p, []),
         "lbm_version": (ctypes.c_char_p, []),
     }
@@ -214,6 +216,7 @@ class Domain:
                                    ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
                                    ctypes.byref(h)))
         self._h = h
+        self._npatch = 0
 
     # -------------------------------------------------------------- lifecycle
     def close(self):
@@ -252,6 +255,7 @@ class Domain:
         I = (ctypes.c_double * max(1, n))(*[float(v) for v in intensity])
         _check("lbm_set_heater_patches",
                lib().lbm_set_heater_patches(self._h, int(z), int(sx), int(sy), n, X, Y, I))
+        self._npatch = n
 
     def init_droplets(self, droplets: Iterable):
         ds = list(droplets)
@@ -285,6 +289,32 @@ class Domain:
         _check("lbm_kernel_info", lib().lbm_kernel_info(self._h, v))
         return {"kernel": "bulk" if v[0] else "generic", "grid": (v[1], v[2], v[3]),
                 "zchunk": v[4], "smem_bytes": v[5]}
+
+    def adjoint_run(self, steps: int, ckpt_every: int, target, normal_cap: float = 0.0):
+        """Run ``steps`` steps from the current state and return (J, dJ/dI) for
+        J = |centroid - target|^2 at the end, I = heater-patch intensities
+        (numpy array, one value per patch), by the discrete adjoint
+        (``normal_cap`` <= 0: exact; > 0: see lbm_adjoint_run)."""
+        import numpy as np
+        tgt = (ctypes.c_double * 3)(*[float(v) for v in target])
+        J = ctypes.c_double()
+        npatch = self._npatch
+        g = np.zeros(max(npatch, 1), dtype=np.float64)
+        _check("lbm_adjoint_run", lib().lbm_adjoint_run(
+            self._h, int(steps), int(ckpt_every), tgt, float(normal_cap), ctypes.byref(J),
+            g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return J.value, g[:npatch]
+
+    def adjoint_step(self, lam, normal_cap: float = 0.0):
+        """(d step / d state)^T lam for the current state; lam is a float64
+        array of (q_phase + 34) * N values in get_pdfs order (h, g, f)."""
+        import numpy as np
+        lam_in = np.ascontiguousarray(lam, dtype=np.float64)
+        out = np.empty_like(lam_in)
+        _check("lbm_adjoint_step", lib().lbm_adjoint_step(self._h, ctypes.c_void_p(lam_in.ctypes.data),
+                                                          ctypes.c_void_p(out.ctypes.data),
+                                                          float(normal_cap)))
+        return out
 
     def profile_steps(self, enable: bool = True):
         """Bracket each step-kernel launch with CUDA events on the domain's stream."""
@@ -335,3 +365,43 @@ class Domain:
         idx = {"h": 0, "g": 1, "f": 2, "T": 3}[which]
         arr = np.ascontiguousarray(values, dtype=np.float64)
         _check("lbm_set_pdfs", lib().lbm_set_pdfs(self._h, idx, ctypes.c_void_p(arr.ctypes.data)))
+
+
+_CAPTURE_FN = None
+
+
+def capture_objective(intensities, setup, steps: int, ckpt_every: int, target,
+                      normal_cap: float = 0.0):
+    """J(I) = |droplet centroid after ``steps`` steps - target|^2 as a
+    differentiable function of the heater-patch intensities I (a 1-D tensor).
+
+    ``setup(I)`` must return an initialised FP64 D3Q7 :class:`Domain` whose
+    heater patches carry the intensities ``I`` (a list of floats).  The
+    forward pass runs the steps through ``Domain.adjoint_run``, which also
+    computes dJ/dI with the adjoint kernels; backward returns it scaled by the
+    incoming gradient.
+    """
+    import torch
+    global _CAPTURE_FN
+    if _CAPTURE_FN is None:
+        class _Capture(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, I, setup_, steps_, ckpt_, target_, cap_):
+                d = setup_([float(v) for v in I.detach().cpu().tolist()])
+                try:
+                    J, g = d.adjoint_run(steps_, ckpt_, target_, cap_)
+                finally:
+                    d.close()
+                ctx.save_for_backward(torch.as_tensor(g, dtype=torch.float64))
+                ctx.in_dtype, ctx.in_device = I.dtype, I.device
+                return torch.tensor(J, dtype=torch.float64)
+
+            @staticmethod
+            def backward(ctx, gJ):
+                (g,) = ctx.saved_tensors
+                grad = (gJ.detach().to("cpu", torch.float64) * g).to(ctx.in_device, ctx.in_dtype)
+                return grad, None, None, None, None, None
+
+        _CAPTURE_FN = _Capture
+    return _CAPTURE_FN.apply(intensities, setup, int(steps), int(ckpt_every), tuple(target),
+                             float(normal_cap))
