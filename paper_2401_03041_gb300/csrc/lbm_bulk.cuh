@@ -117,7 +117,8 @@ struct BulkGeom {
   static constexpr int HXB = TXB + 2;                   // phi/T plane pitch
   static constexpr int HYB = TYB + 2;
   static constexpr int HPB = HXB * HYB;
-  static constexpr int NT = TXB * TYB;
+  static constexpr int NT = TXB * TYB;                  // cells per CTA
+  static constexpr int NTHR = 2 * NT;                   // threads: two roles per cell
   // shared-memory pitch of one box (128-byte aligned destinations)
   static constexpr int HFB = (int)(((size_t)W * (TYB + 2) * sizeof(S) + 127) / 128 * 128 / sizeof(S));
   static constexpr int GB = (int)(((size_t)W * TYB * sizeof(S) + 127) / 128 * 128 / sizeof(S));
@@ -134,7 +135,11 @@ struct BulkSmem {
   static constexpr size_t off_g = off_hf + 3 * hf_stage * sizeof(S);
   static constexpr size_t off_phi = (off_g + 2 * g_stage * sizeof(S) + 15) & ~size_t(15);
   static constexpr size_t off_T = off_phi + 3 * G::HPB * sizeof(R);
-  static constexpr size_t off_bar = (off_T + 3 * G::HPB * sizeof(R) + 15) & ~size_t(15);
+  // per-cell exchange between the two roles: phi, T, grad phi (3), lap phi,
+  // grad T (3) from the h/f role; j (3), p* from the g role
+  static constexpr int NX = 13;
+  static constexpr size_t off_x = (off_T + 3 * G::HPB * sizeof(R) + 15) & ~size_t(15);
+  static constexpr size_t off_bar = (off_x + (size_t)NX * G::NT * sizeof(R) + 15) & ~size_t(15);
   // + 128: the kernel aligns the start of its dynamic shared memory to 128
   // bytes at run time (tensor boxes need 128-byte aligned destinations)
   static constexpr size_t bytes = off_bar + 5 * sizeof(uint64_t) + 128;
@@ -157,7 +162,7 @@ __device__ __forceinline__ void issue_stage(const DevParams& P, const CUtensorMa
                                             int tid) {
   using G = BulkGeom<S>;
   constexpr int ndir = KIND == 0 ? QH + QF : 27;
-  constexpr int nwarps = G::NT / 32;
+  constexpr int nwarps = G::NTHR / 32;
   const int d = (tid >> 5) + (tid & 31) * nwarps;
   if (d >= ndir) return;
   // plane whose tile this is (walls: the ghost planes reuse the boundary plane)
@@ -198,7 +203,7 @@ __device__ __forceinline__ void issue_stage(const DevParams& P, const CUtensorMa
 }
 
 template <class S, int QH, int QF>
-__global__ void __launch_bounds__(BulkGeom<S>::NT, 1)
+__global__ void __launch_bounds__(BulkGeom<S>::NTHR, 1)
 step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
                  const __grid_constant__ CUtensorMap mh, const __grid_constant__ CUtensorMap mg,
                  const __grid_constant__ CUtensorMap mf, int zchunk, int mode) {
@@ -206,18 +211,24 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
   const auto& rp = RP<R>(P);
   using G = BulkGeom<S>;
   using L = BulkSmem<S, QH, QF>;
-  constexpr int NHF = QH + QF;
-  constexpr int NT = G::NT;
+  constexpr int NC = G::NT;       // cells per CTA
+  constexpr int NT = G::NTHR;     // threads per CTA
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
   S* hf = (S*)(smem + L::off_hf);
   S* gb = (S*)(smem + L::off_g);
   R* s_phi = (R*)(smem + L::off_phi);
   R* s_T = (R*)(smem + L::off_T);
+  R* xch = (R*)(smem + L::off_x);                  // [NX][NC] role exchange
   uint64_t* bar = (uint64_t*)(smem + L::off_bar);  // [0..2] HF ring, [3..4] G ring
 
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int tid = ty * G::TXB + tx;
+  // Two threads per cell: threads [0, NC) run the g part of the update (role
+  // A), threads [NC, 2 NC) the phi / T stencils and the h and f parts (role
+  // B).  Warp w of role A and warp w + NC/32 of role B hold the same 32 cells.
+  const int tid = threadIdx.x;
+  const bool role_g = tid < NC;
+  const int cidx = role_g ? tid : tid - NC;
+  const int tx = cidx % G::TXB, ty = cidx / G::TXB;
   const int x0 = blockIdx.x * G::TXB, y0 = blockIdx.y * G::TYB;
   const int z0 = blockIdx.z * zchunk;
   const int z1 = min(z0 + zchunk, P.nz);
@@ -363,53 +374,102 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     if (ok) sum_plane(z + 1);
     ok = ok && wait_slot(3 + g_slot(z), g_par(z));
     if (__syncthreads_or(!ok)) { ok = false; break; }
-    if (active) {
-      const R* pm = s_phi + hf_slot(z - 1) * G::HPB;
-      const R* pc = s_phi + hf_slot(z) * G::HPB;
-      const R* pp = s_phi + hf_slot(z + 1) * G::HPB;
-      const R* tm = s_T + hf_slot(z - 1) * G::HPB;
-      const R* tc = s_T + hf_slot(z) * G::HPB;
-      const R* tp = s_T + hf_slot(z + 1) * G::HPB;
-      const int c0 = (ty + 1) * G::HXB + (tx + 1);
-      Stencil27<R> fd;
-      fd.template eval<G::HXB>(pm, pc, pp, tm, tc, tp, c0);
-      R rgx = 0, rgy = 0, rgz = 0, rlap = 0;
-      if constexpr (QF == 0) rk_std<R, G::HXB>(tm, tc, tp, c0, rgx, rgy, rgz, rlap);
+    {
       const bool lo = P.walls && z == 0, hi = P.walls && z == P.nz - 1;
       const int col = tx + G::GXP;
       const S* hrow = hf_ptr(z) + (size_t)(ty + 1) * G::W + col;   // direction 0, this cell
       const S* grow = g_ptr(z) + (size_t)ty * G::W + col;
       const size_t cell = cell_index(P, x, y, z);
-      auto cell_step = [&](auto btag) {
-        constexpr bool BOUNCE = decltype(btag)::value;
-        auto geth = [&](auto I) {
-          constexpr int i = decltype(I)::value;
-          const bool b = BOUNCE && ((cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi));
-          const S* p_ = hrow + (size_t)i * G::HFB;
-          return Store<S>::ld_s(b ? p_ : p_ - cx<QH>(i)) + (R)weight<QH>(i) * shh;
-        };
-        auto getg = [&](auto I) {
-          constexpr int i = decltype(I)::value;
-          const bool b = BOUNCE && ((cz<27>(i) > 0 && lo) || (cz<27>(i) < 0 && hi));
-          const S* p_ = grow + (size_t)i * G::GB;
-          return Store<S>::ld_s(b ? p_ : p_ - cx<27>(i));
-        };
-        auto getf = [&](auto I) {
-          constexpr int i = decltype(I)::value;
-          if constexpr (QF > 0) {
-            const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
-            const S* p_ = hrow + (size_t)(QH + i) * G::HFB;
-            const R v = Store<S>::ld_s(b ? p_ : p_ - cx<QF>(i)) + (R)weight<QF>(i) * shf;
-            return b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? rp.T_bottom : rp.T_top)) : v;
-          } else {
-            return (R)0;
+      const size_t pcell = pdf_index(P, x, y, z);
+      // pairs warp w (role A) with warp w + NC/32 (role B): named barrier 1 + w
+      const int pair_id = 1 + (cidx >> 5);
+      auto pair_sync = [&]() { asm volatile("bar.sync %0, 64;" ::"r"(pair_id) : "memory"); };
+      if (role_g) {
+        auto run = [&](auto btag) {
+          constexpr bool BOUNCE = decltype(btag)::value;
+          auto getg = [&](auto I) {
+            constexpr int i = decltype(I)::value;
+            const bool b = BOUNCE && ((cz<27>(i) > 0 && lo) || (cz<27>(i) < 0 && hi));
+            const S* p_ = grow + (size_t)i * G::GB;
+            return Store<S>::ld_s(b ? p_ : p_ - cx<27>(i));
+          };
+          GMoments<R> m;
+          if (active) {
+            m = g_moments<R>(getg);
+            xch[9 * NC + cidx] = m.jx;
+            xch[10 * NC + cidx] = m.jy;
+            xch[11 * NC + cidx] = m.jz;
+            xch[12 * NC + cidx] = m.pst;
+          }
+          pair_sync();
+          if (active && (mode & MODE_COLLIDE)) {
+            const R phi = xch[cidx];
+            const CellFlow<R> f = cell_flow<R>(P, x, y, z, phi, xch[NC + cidx], xch[2 * NC + cidx],
+                                               xch[3 * NC + cidx], xch[4 * NC + cidx], xch[5 * NC + cidx],
+                                               xch[6 * NC + cidx], xch[7 * NC + cidx], xch[8 * NC + cidx], m.jx,
+                                               m.jy, m.jz);
+            collide_g<S>(P, A, pcell, phi, m, f);
           }
         };
-        cell_update<S, QH, QF>(P, A, x, y, z, cell, pdf_index(P, x, y, z), mode, pc[c0], tc[c0], fd, rgx, rgy, rgz, rlap,
-                               geth, getg, getf, dsum);
-      };
-      if (lo || hi) cell_step(std::true_type{});
-      else cell_step(std::false_type{});
+        if (lo || hi) run(std::true_type{});
+        else run(std::false_type{});
+      } else {
+        const R* pm = s_phi + hf_slot(z - 1) * G::HPB;
+        const R* pc = s_phi + hf_slot(z) * G::HPB;
+        const R* pp = s_phi + hf_slot(z + 1) * G::HPB;
+        const R* tm = s_T + hf_slot(z - 1) * G::HPB;
+        const R* tc = s_T + hf_slot(z) * G::HPB;
+        const R* tp = s_T + hf_slot(z + 1) * G::HPB;
+        const int c0 = (ty + 1) * G::HXB + (tx + 1);
+        Stencil27<R> fd;
+        R rgx = 0, rgy = 0, rgz = 0, rlap = 0;
+        if (active) {
+          fd.template eval<G::HXB>(pm, pc, pp, tm, tc, tp, c0);
+          if constexpr (QF == 0) rk_std<R, G::HXB>(tm, tc, tp, c0, rgx, rgy, rgz, rlap);
+          xch[cidx] = pc[c0];
+          xch[NC + cidx] = tc[c0];
+          xch[2 * NC + cidx] = fd.gpx;
+          xch[3 * NC + cidx] = fd.gpy;
+          xch[4 * NC + cidx] = fd.gpz;
+          xch[5 * NC + cidx] = fd.lp;
+          xch[6 * NC + cidx] = fd.gtx;
+          xch[7 * NC + cidx] = fd.gty;
+          xch[8 * NC + cidx] = fd.gtz;
+        }
+        pair_sync();
+        if (active) {
+          const R phi = pc[c0], Tc = tc[c0];
+          const CellFlow<R> f = cell_flow<R>(P, x, y, z, phi, Tc, fd.gpx, fd.gpy, fd.gpz, fd.lp, fd.gtx, fd.gty,
+                                             fd.gtz, xch[9 * NC + cidx], xch[10 * NC + cidx], xch[11 * NC + cidx]);
+          cell_outputs<S>(P, A, x, y, z, cell, mode, phi, Tc, xch[12 * NC + cidx], f, dsum);
+          if (mode & MODE_COLLIDE) {
+            auto run = [&](auto btag) {
+              constexpr bool BOUNCE = decltype(btag)::value;
+              auto geth = [&](auto I) {
+                constexpr int i = decltype(I)::value;
+                const bool b = BOUNCE && ((cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi));
+                const S* p_ = hrow + (size_t)i * G::HFB;
+                return Store<S>::ld_s(b ? p_ : p_ - cx<QH>(i)) + (R)weight<QH>(i) * shh;
+              };
+              auto getf = [&](auto I) {
+                constexpr int i = decltype(I)::value;
+                if constexpr (QF > 0) {
+                  const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
+                  const S* p_ = hrow + (size_t)(QH + i) * G::HFB;
+                  const R v = Store<S>::ld_s(b ? p_ : p_ - cx<QF>(i)) + (R)weight<QF>(i) * shf;
+                  return b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? rp.T_bottom : rp.T_top)) : v;
+                } else {
+                  return (R)0;
+                }
+              };
+              collide_h<S, QH>(P, A, pcell, phi, fd.gpx, fd.gpy, fd.gpz, f, geth);
+              collide_f<S, QF>(P, A, x, y, z, cell, pcell, Tc, fd, rgx, rgy, rgz, rlap, f, getf);
+            };
+            if (lo || hi) run(std::true_type{});
+            else run(std::false_type{});
+          }
+        }
+      }
     }
     if (tid == 0 && ok) expect_for(z + 1);
     if (__syncthreads_or(!ok)) { ok = false; break; }

@@ -116,44 +116,58 @@ __device__ __forceinline__ void rk_std(const R* tm, const R* tc, const R* tp, in
   lap = tc[c0 + 1] + tc[c0 - 1] + tc[c0 + HXv] + tc[c0 - HXv] + tp[c0] + tm[c0] - (R)6 * tc[c0];
 }
 
-// a4-a9 for one cell.  GH/GG/GF: accessors i -> pulled (un-shifted) value.
-template <class S, int QH, int QF, class GH, class GG, class GF>
-__device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
-                                            int x, int y, int z, size_t cell, size_t pcell, int mode,
-                                            typename Store<S>::R phi, typename Store<S>::R Tc,
-                                            const Stencil27<typename Store<S>::R>& fdv,
-                                            typename Store<S>::R rgx, typename Store<S>::R rgy,
-                                            typename Store<S>::R rgz, typename Store<S>::R rlap,
-                                            GH geth, GG getg, GF getf, double* dsum) {
-  using R = typename Store<S>::R;
-  const auto& rp = RP<R>(P);
-  const R gpx = fdv.gpx, gpy = fdv.gpy, gpz = fdv.gpz, lp = fdv.lp;
-  const R Gx = (R)rp.grad[0], Gy = (R)rp.grad[1], Gz = (R)rp.grad[2];
-  const R Ttot = Tc + Gx * ((R)x + (R)0.5 - (R)rp.origin[0]) + Gy * ((R)y + (R)0.5 - (R)rp.origin[1]) +
-                 Gz * ((R)z + (R)0.5 - (R)rp.origin[2]);
-  const R gTx = fdv.gtx + Gx, gTy = fdv.gty + Gy, gTz = fdv.gtz + Gz;
+// ---------------------------------------------------------------- pieces
+// The cell update a2-a9 in pieces, so that the bulk kernel can hand the g part
+// and the h / f part of one cell to two threads (roles) while the generic
+// kernel runs them in sequence (cell_update).
 
-  // ---- a2 hydro moments of the pulled g (zeroth, first, second), per
-  // opposite pair: s = g(c) + g(-c) enters even moments, d = g(c) - g(-c) odd
-  R pst = getg(std::integral_constant<int, 0>{}), jx = 0, jy = 0, jz = 0, sxx = 0, syy = 0, szz = 0, sxy = 0,
-    sxz = 0, syz = 0;
+// a2: zeroth, first and second moments of the pulled g, per opposite pair
+// (s = g(c) + g(-c) enters even moments, d = g(c) - g(-c) odd ones).
+template <class R>
+struct GMoments {
+  R pst, jx, jy, jz, sxx, syy, szz, sxy, sxz, syz;
+};
+
+template <class R, class GG>
+__device__ __forceinline__ GMoments<R> g_moments(GG getg) {
+  GMoments<R> m;
+  m.pst = getg(std::integral_constant<int, 0>{});
+  m.jx = m.jy = m.jz = m.sxx = m.syy = m.szz = m.sxy = m.sxz = m.syz = 0;
   static_for<1, 27>([&](auto I) {
     constexpr int i = decltype(I)::value;
     if constexpr (pair_first<27>(i)) {
       const R a_ = getg(I), b_ = getg(std::integral_constant<int, opp<27>(i)>{});
       const R s_ = a_ + b_, d_ = a_ - b_;
       constexpr int ex = cx<27>(i), ey = cy<27>(i), ez = cz<27>(i);
-      pst += s_;
-      if constexpr (ex != 0) { jx += (R)ex * d_; sxx += s_; }
-      if constexpr (ey != 0) { jy += (R)ey * d_; syy += s_; }
-      if constexpr (ez != 0) { jz += (R)ez * d_; szz += s_; }
-      if constexpr (ex * ey != 0) sxy += (R)(ex * ey) * s_;
-      if constexpr (ex * ez != 0) sxz += (R)(ex * ez) * s_;
-      if constexpr (ey * ez != 0) syz += (R)(ey * ez) * s_;
+      m.pst += s_;
+      if constexpr (ex != 0) { m.jx += (R)ex * d_; m.sxx += s_; }
+      if constexpr (ey != 0) { m.jy += (R)ey * d_; m.syy += s_; }
+      if constexpr (ez != 0) { m.jz += (R)ez * d_; m.szz += s_; }
+      if constexpr (ex * ey != 0) m.sxy += (R)(ex * ey) * s_;
+      if constexpr (ex * ez != 0) m.sxz += (R)(ex * ez) * s_;
+      if constexpr (ey * ez != 0) m.syz += (R)(ey * ez) * s_;
     }
   });
+  return m;
+}
 
-  // ---- a4/a5 forces
+// a4-a6: surface-tension and Marangoni force, body force, acceleration and
+// velocity of one cell from phi, T, their finite differences and the first
+// moment j of the pulled g.
+template <class R>
+struct CellFlow {
+  R ux, uy, uz, ax, ay, az, uu, rho;
+};
+
+template <class R>
+__device__ __forceinline__ CellFlow<R> cell_flow(const DevParams& P, int x, int y, int z, R phi, R Tc,
+                                                 R gpx, R gpy, R gpz, R lp, R gtx, R gty, R gtz, R jx, R jy,
+                                                 R jz) {
+  const auto& rp = RP<R>(P);
+  const R Gx = (R)rp.grad[0], Gy = (R)rp.grad[1], Gz = (R)rp.grad[2];
+  const R Ttot = Tc + Gx * ((R)x + (R)0.5 - (R)rp.origin[0]) + Gy * ((R)y + (R)0.5 - (R)rp.origin[1]) +
+                 Gz * ((R)z + (R)0.5 - (R)rp.origin[2]);
+  const R gTx = gtx + Gx, gTy = gty + Gy, gTz = gtz + Gz;
   const R xi = (R)rp.xi;
   const R sigma = (R)rp.sigma_ref + (R)rp.sigma_T * (Ttot - (R)rp.T_ref);
   const R beta = (R)12 * sigma / xi;
@@ -162,135 +176,172 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
   const R g2 = gpx * gpx + gpy * gpy + gpz * gpz;
   const R tdp = gTx * gpx + gTy * gpy + gTz * gpz;
   const R cm = (R)1.5 * xi * (R)rp.sigma_T;
-  const R rho = (R)rp.rho_L + phi * (R)(rp.rho_H - rp.rho_L);
-  const R Fx = mu * gpx + cm * (g2 * gTx - tdp * gpx) + rho * (R)rp.gravity[0];
-  const R Fy = mu * gpy + cm * (g2 * gTy - tdp * gpy) + rho * (R)rp.gravity[1];
-  const R Fz = mu * gpz + cm * (g2 * gTz - tdp * gpz) + rho * (R)rp.gravity[2];
-  const R irho = (R)1 / rho;
-  const R ax = Fx * irho, ay = Fy * irho, az = Fz * irho;
-  // ---- a6 velocity
-  const R ux = jx + (R)0.5 * ax, uy = jy + (R)0.5 * ay, uz = jz + (R)0.5 * az;
-  const R uu = ux * ux + uy * uy + uz * uz;
+  CellFlow<R> f;
+  f.rho = (R)rp.rho_L + phi * (R)(rp.rho_H - rp.rho_L);
+  const R Fx = mu * gpx + cm * (g2 * gTx - tdp * gpx) + f.rho * (R)rp.gravity[0];
+  const R Fy = mu * gpy + cm * (g2 * gTy - tdp * gpy) + f.rho * (R)rp.gravity[1];
+  const R Fz = mu * gpz + cm * (g2 * gTz - tdp * gpz) + f.rho * (R)rp.gravity[2];
+  const R irho = (R)1 / f.rho;
+  f.ax = Fx * irho; f.ay = Fy * irho; f.az = Fz * irho;
+  f.ux = jx + (R)0.5 * f.ax; f.uy = jy + (R)0.5 * f.ay; f.uz = jz + (R)0.5 * f.az;
+  f.uu = f.ux * f.ux + f.uy * f.uy + f.uz * f.uz;
+  return f;
+}
 
+// a10 diagnostics (FP64 partial sums) and the macroscopic output pass.
+template <class S>
+__device__ __forceinline__ void cell_outputs(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
+                                             int x, int y, int z, size_t cell, int mode,
+                                             typename Store<S>::R phi, typename Store<S>::R Tc,
+                                             typename Store<S>::R pst,
+                                             const CellFlow<typename Store<S>::R>& f, double* dsum) {
   if (mode & MODE_DIAG) {
     const double dphi = (double)phi;
     dsum[0] += dphi;
     dsum[1] += (double)Tc;
-    dsum[2] += 0.5 * (double)rho * (double)uu;
+    dsum[2] += 0.5 * (double)f.rho * (double)f.uu;
     dsum[3] += dphi * (x + 0.5);
     dsum[4] += dphi * (y + 0.5);
     dsum[5] += dphi * (z + 0.5);
-    if (!isfinite(dphi) || !isfinite((double)Tc) || !isfinite((double)uu)) dsum[6] += 1.0;
+    if (!isfinite(dphi) || !isfinite((double)Tc) || !isfinite((double)f.uu)) dsum[6] += 1.0;
   }
   if (mode & MODE_MACRO) {
-    const double vals[6] = {(double)phi, (double)ux, (double)uy, (double)uz, (double)pst, (double)Tc};
+    const double vals[6] = {(double)phi, (double)f.ux, (double)f.uy, (double)f.uz, (double)pst, (double)Tc};
     const unsigned cnt[4] = {1u, 3u, 1u, 1u};
     int slot = 0, v = 0;
-    for (int f = 0; f < 4; ++f) {
-      if (A.macro_mask & (1u << f)) {
-        for (unsigned c = 0; c < cnt[f]; ++c) {
+    for (int k = 0; k < 4; ++k) {
+      if (A.macro_mask & (1u << k)) {
+        for (unsigned c = 0; c < cnt[k]; ++c) {
           const size_t at = (size_t)(slot + c) * P.N + cell;
           if (A.macro_dtype == 0) ((double*)A.macro_out)[at] = vals[v + c];
           else ((float*)A.macro_out)[at] = (float)vals[v + c];
         }
-        slot += cnt[f];
+        slot += cnt[k];
       }
-      v += cnt[f];
+      v += cnt[k];
     }
   }
-  if (!(mode & MODE_COLLIDE)) return;
+}
 
-  // ---- a8 g collision (central moments, closed form)
-  {
-    const R om = (R)1 / ((R)rp.tau_L + phi * (R)(rp.tau_H - rp.tau_L));
-    const R k1 = (R)1 - om;
-    const R p3 = pst * (R)(1.0 / 3.0);
-    const R Pxx = k1 * (sxx - p3 - ux * ux + ux * ax);
-    const R Pyy = k1 * (syy - p3 - uy * uy + uy * ay);
-    const R Pzz = k1 * (szz - p3 - uz * uz + uz * az);
-    const R Pxy = k1 * (sxy - ux * uy + (R)0.5 * (ux * ay + ax * uy));
-    const R Pxz = k1 * (sxz - ux * uz + (R)0.5 * (ux * az + ax * uz));
-    const R Pyz = k1 * (syz - uy * uz + (R)0.5 * (uy * az + ay * uz));
-    // per-axis inverse-shift bases
-    const R X0z = (R)1 - ux * ux, X0p = (R)0.5 * (ux * ux + ux), X0m = (R)0.5 * (ux * ux - ux);
-    const R X1z = (R)-2 * ux, X1p = ux + (R)0.5, X1m = ux - (R)0.5;
-    const R Y0z = (R)1 - uy * uy, Y0p = (R)0.5 * (uy * uy + uy), Y0m = (R)0.5 * (uy * uy - uy);
-    const R Y1z = (R)-2 * uy, Y1p = uy + (R)0.5, Y1m = uy - (R)0.5;
-    const R Z0z = (R)1 - uz * uz, Z0p = (R)0.5 * (uz * uz + uz), Z0m = (R)0.5 * (uz * uz - uz);
-    const R Z1z = (R)-2 * uz, Z1p = uz + (R)0.5, Z1m = uz - (R)0.5;
-    R A00[3], A10[3], A01[3], A20[3], A02[3], A11[3];
+// a8: g collision (central moments, closed form)
+template <class S>
+__device__ __forceinline__ void collide_g(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
+                                          size_t pcell, typename Store<S>::R phi,
+                                          const GMoments<typename Store<S>::R>& m,
+                                          const CellFlow<typename Store<S>::R>& f) {
+  using R = typename Store<S>::R;
+  const auto& rp = RP<R>(P);
+  const R ux = f.ux, uy = f.uy, uz = f.uz, ax = f.ax, ay = f.ay, az = f.az, uu = f.uu;
+  const R om = (R)1 / ((R)rp.tau_L + phi * (R)(rp.tau_H - rp.tau_L));
+  const R k1 = (R)1 - om;
+  const R p3 = m.pst * (R)(1.0 / 3.0);
+  const R Pxx = k1 * (m.sxx - p3 - ux * ux + ux * ax);
+  const R Pyy = k1 * (m.syy - p3 - uy * uy + uy * ay);
+  const R Pzz = k1 * (m.szz - p3 - uz * uz + uz * az);
+  const R Pxy = k1 * (m.sxy - ux * uy + (R)0.5 * (ux * ay + ax * uy));
+  const R Pxz = k1 * (m.sxz - ux * uz + (R)0.5 * (ux * az + ax * uz));
+  const R Pyz = k1 * (m.syz - uy * uz + (R)0.5 * (uy * az + ay * uz));
+  // per-axis inverse-shift bases
+  const R X0z = (R)1 - ux * ux, X0p = (R)0.5 * (ux * ux + ux), X0m = (R)0.5 * (ux * ux - ux);
+  const R X1z = (R)-2 * ux, X1p = ux + (R)0.5, X1m = ux - (R)0.5;
+  const R Y0z = (R)1 - uy * uy, Y0p = (R)0.5 * (uy * uy + uy), Y0m = (R)0.5 * (uy * uy - uy);
+  const R Y1z = (R)-2 * uy, Y1p = uy + (R)0.5, Y1m = uy - (R)0.5;
+  const R Z0z = (R)1 - uz * uz, Z0p = (R)0.5 * (uz * uz + uz), Z0m = (R)0.5 * (uz * uz - uz);
+  const R Z1z = (R)-2 * uz, Z1p = uz + (R)0.5, Z1m = uz - (R)0.5;
+  R A00[3], A10[3], A01[3], A20[3], A02[3], A11[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int zc = c == 0 ? 0 : (c == 1 ? 1 : -1);
-      const R p0 = basis_pick(zc, Z0z, Z0p, Z0m);
-      const R p1 = basis_pick(zc, Z1z, Z1p, Z1m);
-      const R p2 = zc == 0 ? (R)-1 : (R)0.5;
-      A00[c] = p2 * Pzz; A10[c] = p1 * Pxz; A01[c] = p1 * Pyz;
-      A20[c] = p0 * Pxx; A02[c] = p0 * Pyy; A11[c] = p0 * Pxy;
-    }
-    const R ua = ux * ax + uy * ay + uz * az;
-    const R base = pst - (R)1.5 * (uu + ua);
-    auto neq_of = [&](int ex, int ey, int ez) -> R {
-      const int c = ez == 0 ? 0 : (ez > 0 ? 1 : 2);
-      const R q0 = basis_pick(ey, Y0z, Y0p, Y0m);
-      const R q1 = basis_pick(ey, Y1z, Y1p, Y1m);
-      const R q2 = ey == 0 ? (R)-1 : (R)0.5;
-      const R B0 = q0 * A00[c] + q1 * A01[c] + q2 * A02[c];
-      const R B1 = q0 * A10[c] + q1 * A11[c];
-      const R B2 = q0 * A20[c];
-      const R r0 = basis_pick(ex, X0z, X0p, X0m);
-      const R r1 = basis_pick(ex, X1z, X1p, X1m);
-      const R r2 = ex == 0 ? (R)-1 : (R)0.5;
-      return r0 * B0 + r1 * B1 + r2 * B2;
-    };
-    Store<S>::st(A.gd[0] + pcell, (R)weight<27>(0) * base + neq_of(0, 0, 0));
-    static_for<1, 27>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      if constexpr (pair_first<27>(i)) {
-        constexpr int ex = cx<27>(i), ey = cy<27>(i), ez = cz<27>(i);
-        constexpr R w = (R)weight<27>(i);
-        const R cu = (R)ex * ux + (R)ey * uy + (R)ez * uz;
-        const R ca = (R)ex * ax + (R)ey * ay + (R)ez * az;
-        // g^eq + S/2 = w [p* + 3cu + 9/2 cu^2 - 3/2 uu + 3/2 (ca - ua) + 9/2 cu ca]
-        const R even = w * (base + (R)4.5 * cu * (cu + ca));
-        const R odd = w * ((R)3 * cu + (R)1.5 * ca);
-        Store<S>::st(A.gd[i] + pcell, even + odd + neq_of(ex, ey, ez));
-        Store<S>::st(A.gd[opp<27>(i)] + pcell, even - odd + neq_of(-ex, -ey, -ez));
-      }
-    });
+  for (int c = 0; c < 3; ++c) {
+    const int zc = c == 0 ? 0 : (c == 1 ? 1 : -1);
+    const R p0 = basis_pick(zc, Z0z, Z0p, Z0m);
+    const R p1 = basis_pick(zc, Z1z, Z1p, Z1m);
+    const R p2 = zc == 0 ? (R)-1 : (R)0.5;
+    A00[c] = p2 * Pzz; A10[c] = p1 * Pxz; A01[c] = p1 * Pyz;
+    A20[c] = p0 * Pxx; A02[c] = p0 * Pyy; A11[c] = p0 * Pxy;
   }
-  // ---- a7 h collision (single rate + Guo source of the interface force)
+  const R ua = ux * ax + uy * ay + uz * az;
+  const R base = m.pst - (R)1.5 * (uu + ua);
+  auto neq_of = [&](int ex, int ey, int ez) -> R {
+    const int c = ez == 0 ? 0 : (ez > 0 ? 1 : 2);
+    const R q0 = basis_pick(ey, Y0z, Y0p, Y0m);
+    const R q1 = basis_pick(ey, Y1z, Y1p, Y1m);
+    const R q2 = ey == 0 ? (R)-1 : (R)0.5;
+    const R B0 = q0 * A00[c] + q1 * A01[c] + q2 * A02[c];
+    const R B1 = q0 * A10[c] + q1 * A11[c];
+    const R B2 = q0 * A20[c];
+    const R r0 = basis_pick(ex, X0z, X0p, X0m);
+    const R r1 = basis_pick(ex, X1z, X1p, X1m);
+    const R r2 = ex == 0 ? (R)-1 : (R)0.5;
+    return r0 * B0 + r1 * B1 + r2 * B2;
+  };
+  Store<S>::st(A.gd[0] + pcell, (R)weight<27>(0) * base + neq_of(0, 0, 0));
+  static_for<1, 27>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (pair_first<27>(i)) {
+      constexpr int ex = cx<27>(i), ey = cy<27>(i), ez = cz<27>(i);
+      constexpr R w = (R)weight<27>(i);
+      const R cu = (R)ex * ux + (R)ey * uy + (R)ez * uz;
+      const R ca = (R)ex * ax + (R)ey * ay + (R)ez * az;
+      // g^eq + S/2 = w [p* + 3cu + 9/2 cu^2 - 3/2 uu + 3/2 (ca - ua) + 9/2 cu ca]
+      const R even = w * (base + (R)4.5 * cu * (cu + ca));
+      const R odd = w * ((R)3 * cu + (R)1.5 * ca);
+      Store<S>::st(A.gd[i] + pcell, even + odd + neq_of(ex, ey, ez));
+      Store<S>::st(A.gd[opp<27>(i)] + pcell, even - odd + neq_of(-ex, -ey, -ez));
+    }
+  });
+}
+
+// a7: h collision (single rate + Guo source of the interface force)
+template <class S, int QH, class GH>
+__device__ __forceinline__ void collide_h(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
+                                          size_t pcell, typename Store<S>::R phi, typename Store<S>::R gpx,
+                                          typename Store<S>::R gpy, typename Store<S>::R gpz,
+                                          const CellFlow<typename Store<S>::R>& f, GH geth) {
+  using R = typename Store<S>::R;
+  const auto& rp = RP<R>(P);
+  const R ux = f.ux, uy = f.uy, uz = f.uz, uu = f.uu;
+  const R g2 = gpx * gpx + gpy * gpy + gpz * gpz;
+  const R nrm = (R)1 / (sqrt(g2) + (R)rp.eps_n);
+  const R th = (R)4 * phi * ((R)1 - phi) / (R)rp.xi * nrm;
+  const R fpx = th * gpx, fpy = th * gpy, fpz = th * gpz;
+  const R om = (R)rp.omega_phi;
+  const R sc = (R)1 - (R)0.5 * om;
+  const R sh = (R)rp.shift_h;
+  const R e0 = (R)1 - (R)1.5 * uu;
   {
-    const R nrm = (R)1 / (sqrt(g2) + (R)rp.eps_n);
-    const R th = (R)4 * phi * ((R)1 - phi) / xi * nrm;
-    const R fpx = th * gpx, fpy = th * gpy, fpz = th * gpz;
-    const R om = (R)rp.omega_phi;
-    const R sc = (R)1 - (R)0.5 * om;
-    const R sh = (R)rp.shift_h;
-    const R e0 = (R)1 - (R)1.5 * uu;
-    {
-      constexpr R w = (R)weight<QH>(0);
-      const R hs = geth(std::integral_constant<int, 0>{});
-      const R hn = hs - om * (hs - w * phi * e0);
-      Store<S>::st(A.hd[0] + pcell, hn - w * sh);
-    }
-    static_for<1, QH>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      if constexpr (pair_first<QH>(i)) {
-        constexpr int j = opp<QH>(i);
-        constexpr R w = (R)weight<QH>(i);
-        const R cu = (R)cx<QH>(i) * ux + (R)cy<QH>(i) * uy + (R)cz<QH>(i) * uz;
-        const R cf = (R)cx<QH>(i) * fpx + (R)cy<QH>(i) * fpy + (R)cz<QH>(i) * fpz;
-        const R even = w * phi * (e0 + (R)4.5 * cu * cu);
-        const R odd = w * phi * (R)3 * cu;
-        const R src = sc * w * cf;
-        const R hi = geth(I), hj = geth(std::integral_constant<int, j>{});
-        Store<S>::st(A.hd[i] + pcell, hi - om * (hi - (even + odd)) + src - w * sh);
-        Store<S>::st(A.hd[j] + pcell, hj - om * (hj - (even - odd)) - src - w * sh);
-      }
-    });
+    constexpr R w = (R)weight<QH>(0);
+    const R hs = geth(std::integral_constant<int, 0>{});
+    const R hn = hs - om * (hs - w * phi * e0);
+    Store<S>::st(A.hd[0] + pcell, hn - w * sh);
   }
-  // ---- a9 / a9' thermal
+  static_for<1, QH>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (pair_first<QH>(i)) {
+      constexpr int j = opp<QH>(i);
+      constexpr R w = (R)weight<QH>(i);
+      const R cu = (R)cx<QH>(i) * ux + (R)cy<QH>(i) * uy + (R)cz<QH>(i) * uz;
+      const R cf = (R)cx<QH>(i) * fpx + (R)cy<QH>(i) * fpy + (R)cz<QH>(i) * fpz;
+      const R even = w * phi * (e0 + (R)4.5 * cu * cu);
+      const R odd = w * phi * (R)3 * cu;
+      const R src = sc * w * cf;
+      const R hi = geth(I), hj = geth(std::integral_constant<int, j>{});
+      Store<S>::st(A.hd[i] + pcell, hi - om * (hi - (even + odd)) + src - w * sh);
+      Store<S>::st(A.hd[j] + pcell, hj - om * (hj - (even - odd)) - src - w * sh);
+    }
+  });
+}
+
+// a9 / a9': thermal LB collision, or RK stage 1 (QF = 0)
+template <class S, int QF, class GF>
+__device__ __forceinline__ void collide_f(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
+                                          int x, int y, int z, size_t cell, size_t pcell,
+                                          typename Store<S>::R Tc, const Stencil27<typename Store<S>::R>& fdv,
+                                          typename Store<S>::R rgx, typename Store<S>::R rgy,
+                                          typename Store<S>::R rgz, typename Store<S>::R rlap,
+                                          const CellFlow<typename Store<S>::R>& f, GF getf) {
+  using R = typename Store<S>::R;
+  const auto& rp = RP<R>(P);
+  const R ux = f.ux, uy = f.uy, uz = f.uz, uu = f.uu;
+  const R Gx = (R)rp.grad[0], Gy = (R)rp.grad[1], Gz = (R)rp.grad[2];
   const R q = heat_source<R>(P, x, y, z);
   const R uG = ux * Gx + uy * Gy + uz * Gz;
   if constexpr (QF > 0) {
@@ -332,6 +383,27 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
     A.s1_out[cell] = Tc + (R)0.5 * K1;
     if (A.rk_acc) A.acc_out[cell] = K1 * (R)(1.0 / 6.0);
   }
+}
+
+// a2-a10 for one cell in sequence.  GH/GG/GF: accessors i -> pulled
+// (un-shifted) value.
+template <class S, int QH, int QF, class GH, class GG, class GF>
+__device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
+                                            int x, int y, int z, size_t cell, size_t pcell, int mode,
+                                            typename Store<S>::R phi, typename Store<S>::R Tc,
+                                            const Stencil27<typename Store<S>::R>& fdv,
+                                            typename Store<S>::R rgx, typename Store<S>::R rgy,
+                                            typename Store<S>::R rgz, typename Store<S>::R rlap,
+                                            GH geth, GG getg, GF getf, double* dsum) {
+  using R = typename Store<S>::R;
+  const GMoments<R> m = g_moments<R>(getg);
+  const CellFlow<R> f = cell_flow<R>(P, x, y, z, phi, Tc, fdv.gpx, fdv.gpy, fdv.gpz, fdv.lp, fdv.gtx, fdv.gty,
+                                     fdv.gtz, m.jx, m.jy, m.jz);
+  cell_outputs<S>(P, A, x, y, z, cell, mode, phi, Tc, m.pst, f, dsum);
+  if (!(mode & MODE_COLLIDE)) return;
+  collide_g<S>(P, A, pcell, phi, m, f);
+  collide_h<S, QH>(P, A, pcell, phi, fdv.gpx, fdv.gpy, fdv.gpz, f, geth);
+  collide_f<S, QF>(P, A, x, y, z, cell, pcell, Tc, fdv, rgx, rgy, rgz, rlap, f, getf);
 }
 
 }  // namespace lbm

@@ -108,7 +108,7 @@ def bulk_fits(precision, q_phase, thermal):
     rs = 8 if s == 8 else 4
     hfb = -(-W * (rows + 2) * s // 128) * 128
     gb = -(-W * rows * s // 128) * 128
-    smem = 3 * nhf * hfb + 2 * 27 * gb + 6 * (cols + 2) * (rows + 2) * rs + 64 + 128
+    smem = 3 * nhf * hfb + 2 * 27 * gb + 6 * (cols + 2) * (rows + 2) * rs + 13 * cols * rows * rs + 64 + 128
     return smem <= 232448
 
 
