@@ -237,9 +237,11 @@ lbm_status lbm_kernel_info(lbm_domain* dom, int32_t* info);
  *   horizons (thousands of steps) the exact linearised step then amplifies
  *   round-off-level perturbations there that the step itself keeps bounded,
  *   and the exact gradient no longer describes finite changes of J.
- *   Synchronises.  Allocates its checkpoint and adjoint buffers
- *   (about (nsteps / ckpt_every + ckpt_every + 1) PDF sets plus 3 dense
- *   adjoint sets) for the duration of the call: LBM_ERR_OOM if they do not fit.
+ *   Synchronises.  Allocates its buffers for the duration of the call:
+ *   nsteps / ckpt_every + 1 PDF sets (checkpoints, final state), ckpt_every
+ *   x 19 doubles per cell (the replayed steps' intermediates) and 3 dense
+ *   adjoint sets (q_phase + 34 doubles per cell each): LBM_ERR_OOM if they do
+ *   not fit.
  * Errors: LBM_ERR_ARG (nsteps < 1, ckpt_every < 1, null target / J_out, NaN normal_cap),
  * LBM_ERR_STATE (not initialised, zero phi mass), LBM_ERR_UNSUPPORTED. */
 lbm_status lbm_adjoint_run(lbm_domain* dom, int nsteps, int ckpt_every, const double* target,

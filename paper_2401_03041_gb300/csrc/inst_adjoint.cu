@@ -12,30 +12,20 @@ int grid_1d(size_t work) {
   return (int)(b < 152 * 16 ? b : 152 * 16);
 }
 
-template <int QH, int QF>
-void cell_qh(const DevParams& P, const AdjPtrs& A, cudaStream_t st) {
-  const int bx = (P.nx + TX - 1) / TX, by = (P.ny + TY - 1) / TY;
-  const long long cols = (long long)bx * by;
-  int nchunks = (int)((152LL * 8 + cols - 1) / cols);
-  if (nchunks > P.nz) nchunks = P.nz;
-  if (nchunks < 1) nchunks = 1;
-  const int zc = (P.nz + nchunks - 1) / nchunks;
-  adj_cell_kernel<QH, QF><<<dim3(bx, by, (P.nz + zc - 1) / zc), dim3(TX, TY), 0, st>>>(P, A, zc);
-}
-
 }  // namespace
 
 bool adj_supported(int qh, int qf) { return (qh == 15 || qh == 27) && qf == 7; }
 
-void adj_cell(const DevParams& P, const AdjPtrs& A, int qh, int qf, cudaStream_t st) {
-  (void)qf;
-  if (qh == 15) cell_qh<15, 7>(P, A, st);
-  else cell_qh<27, 7>(P, A, st);
-}
-
 // plane-indexed grids: x over nx * ny (< 2^31), y = z (<= 65535)
 static unsigned plane_blocks(const DevParams& P) {
   return (unsigned)(((size_t)P.nx * P.ny + 255) / 256);
+}
+
+void adj_cell(const DevParams& P, const AdjPtrs& A, int qh, int qf, cudaStream_t st) {
+  (void)qf;
+  const dim3 grid(plane_blocks(P), P.nz);
+  if (qh == 15) adj_point_kernel<15, 7><<<grid, 256, 0, st>>>(P, A);
+  else adj_point_kernel<27, 7><<<grid, 256, 0, st>>>(P, A);
 }
 
 void adj_fields(const DevParams& P, const AdjPtrs& A, cudaStream_t st) {
@@ -43,7 +33,7 @@ void adj_fields(const DevParams& P, const AdjPtrs& A, cudaStream_t st) {
 }
 
 void adj_pull(const DevParams& P, const AdjPtrs& A, int qh, int qf, cudaStream_t st) {
-  const dim3 grid(plane_blocks(P), P.nz, qh + 27 + qf);
+  const dim3 grid(plane_blocks(P), P.nz);
   if (qh == 15) adj_pull_kernel<15, 7><<<grid, 256, 0, st>>>(P, A);
   else adj_pull_kernel<27, 7><<<grid, 256, 0, st>>>(P, A);
 }

@@ -8,9 +8,10 @@
 // Notation: s^n = post-collision PDFs of level n (what the arrays store), the
 // step s^{n+1} = Phi(s^n; I).  Given lam' = dJ/ds^{n+1} the adjoint step forms
 // lam = (dPhi/ds^n)^T lam' in three passes:
-//   A  (adj_cell_kernel)   per cell x: recompute the forward quantities of x
-//      from s^n (pulled PDFs, phi and T on the halo, finite differences), then
-//      reverse the f, h and g collisions, u, F, F^phi, mu and sigma(T).
+//   A  (adj_point_kernel)  per cell x: from the intermediates the forward step
+//      saved for x (phi, T, their finite differences, moments of the pulled g;
+//      MODE_SAVE of the replayed step), reverse the f, h and g collisions, u,
+//      F, F^phi, mu and sigma(T).
 //      Writes the direct adjoints of the pulled PDFs (lam*_i(x), without the
 //      phi / T terms), the local adjoints of phi and T, and the adjoints of
 //      grad phi, lap phi and grad T at x (9 fields).
@@ -23,7 +24,7 @@
 //      where A_i(x) = lam*_i(x) + lam_phi(x) (h), lam*_i(x) (g),
 //      lam*_i(x) + lam_T(x) (f).
 // Adjoint arrays are dense [direction][z][y][x] FP64 (N values per direction,
-// h | g | f directions in one block); the forward state is a padded PDF set.
+// h | g | f directions in one block).
 //
 // Reverse-mode identities used for the central-moment collision (per axis, a
 // unit central moment of order e maps to the 1D basis b_e(c; u) of the
@@ -47,30 +48,85 @@ __device__ __forceinline__ double bas(int e, int c, double u) {
   return c == 0 ? -1.0 : 0.5;
 }
 
-// Pass A for one cell.  h*, g*, f* accessors return pulled FP64 values.
-template <int QH, int QF, class GG>
+// Weighted moments of per-direction adjoints L_i over stencil Q:
+// m0 = sum w L, m1 = sum w L c, m2 = sum w L c c (symmetric), summed per
+// opposite pair.  The accessor is called once per direction.
+struct WMoments {
+  double m0, m1[3], xx, yy, zz, xy, xz, yz;
+  __device__ __forceinline__ void m2_times(const double* v, double* out) const {
+    out[0] = xx * v[0] + xy * v[1] + xz * v[2];
+    out[1] = xy * v[0] + yy * v[1] + yz * v[2];
+    out[2] = xz * v[0] + yz * v[1] + zz * v[2];
+  }
+};
+
+template <int Q, class LF>
+__device__ __forceinline__ WMoments wmoments(LF lam) {
+  WMoments M;
+  M.m0 = weight<Q>(0) * lam(std::integral_constant<int, 0>{});
+  M.m1[0] = M.m1[1] = M.m1[2] = M.xx = M.yy = M.zz = M.xy = M.xz = M.yz = 0.0;
+  static_for<1, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (pair_first<Q>(i)) {
+      constexpr int ex = cx<Q>(i), ey = cy<Q>(i), ez = cz<Q>(i);
+      constexpr double w = weight<Q>(i);
+      const double a = lam(I), b = lam(std::integral_constant<int, opp<Q>(i)>{});
+      const double s = w * (a + b), d = w * (a - b);
+      M.m0 += s;
+      if constexpr (ex != 0) { M.m1[0] += ex * d; M.xx += s; }
+      if constexpr (ey != 0) { M.m1[1] += ey * d; M.yy += s; }
+      if constexpr (ez != 0) { M.m1[2] += ez * d; M.zz += s; }
+      if constexpr (ex * ey != 0) M.xy += (ex * ey) * s;
+      if constexpr (ex * ez != 0) M.xz += (ex * ez) * s;
+      if constexpr (ey * ez != 0) M.yz += (ey * ez) * s;
+    }
+  });
+  return M;
+}
+
+// Pass A for one cell, from the intermediates the forward step saved for it
+// (MODE_SAVE: phi, T, their finite differences and the moments of the pulled
+// g, exactly as the step used them).
+__device__ __forceinline__ void cell_adjoint_inputs(const DevParams& P, const double* __restrict__ sv,
+                                                    size_t cell, double& phi, double& Tc,
+                                                    Stencil27<double>& fdv, GMoments<double>& m) {
+  const size_t N = (size_t)P.N;
+  phi = sv[SAVE_PHI * N + cell];
+  Tc = sv[SAVE_T * N + cell];
+  fdv.gpx = sv[SAVE_GPX * N + cell];
+  fdv.gpy = sv[SAVE_GPY * N + cell];
+  fdv.gpz = sv[SAVE_GPZ * N + cell];
+  fdv.lp = sv[SAVE_LP * N + cell];
+  fdv.gtx = sv[SAVE_GTX * N + cell];
+  fdv.gty = sv[SAVE_GTY * N + cell];
+  fdv.gtz = sv[SAVE_GTZ * N + cell];
+  m.pst = sv[SAVE_PST * N + cell];
+  m.jx = sv[SAVE_JX * N + cell];
+  m.jy = sv[SAVE_JY * N + cell];
+  m.jz = sv[SAVE_JZ * N + cell];
+  m.sxx = sv[SAVE_SXX * N + cell];
+  m.syy = sv[SAVE_SYY * N + cell];
+  m.szz = sv[SAVE_SZZ * N + cell];
+  m.sxy = sv[SAVE_SXY * N + cell];
+  m.sxz = sv[SAVE_SXZ * N + cell];
+  m.syz = sv[SAVE_SYZ * N + cell];
+}
+
+template <int QH, int QF>
 __device__ __forceinline__ void cell_adjoint(const DevParams& P, const AdjPtrs& A, int x, int y, int z,
                                              size_t cell, double phi, double Tc,
-                                             const Stencil27<double>& fdv, GG getg) {
+                                             const Stencil27<double>& fdv, const GMoments<double>& gm) {
   const auto& rp = P.pd;
   const size_t N = (size_t)P.N;
   constexpr int OG = QH, OF = QH + 27;
-  // ---------------- forward recomputation (as cell_update, FP64)
+  // ---------------- forward quantities (as cell_flow / collide_*, FP64)
   const double gpx = fdv.gpx, gpy = fdv.gpy, gpz = fdv.gpz, lp = fdv.lp;
   const double Gx = rp.grad[0], Gy = rp.grad[1], Gz = rp.grad[2];
   const double Ttot = Tc + Gx * (x + 0.5 - rp.origin[0]) + Gy * (y + 0.5 - rp.origin[1]) +
                       Gz * (z + 0.5 - rp.origin[2]);
   const double gTx = fdv.gtx + Gx, gTy = fdv.gty + Gy, gTz = fdv.gtz + Gz;
-  double pst = 0, jx = 0, jy = 0, jz = 0, sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
-  static_for<0, 27>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    constexpr int ex = cx<27>(i), ey = cy<27>(i), ez = cz<27>(i);
-    const double v = getg(I);
-    pst += v;
-    jx += ex * v; jy += ey * v; jz += ez * v;
-    sxx += ex * ex * v; syy += ey * ey * v; szz += ez * ez * v;
-    sxy += ex * ey * v; sxz += ex * ez * v; syz += ey * ez * v;
-  });
+  const double pst = gm.pst, jx = gm.jx, jy = gm.jy, jz = gm.jz;
+  const double sxx = gm.sxx, syy = gm.syy, szz = gm.szz, sxy = gm.sxy, sxz = gm.sxz, syz = gm.syz;
   const double xi = rp.xi;
   const double sigma = rp.sigma_ref + rp.sigma_T * (Ttot - rp.T_ref);
   const double beta = 12.0 * sigma / xi, kap = 1.5 * sigma * xi;
@@ -101,75 +157,112 @@ __device__ __forceinline__ void cell_adjoint(const DevParams& P, const AdjPtrs& 
   const double cphi = 4.0 * phi * (1.0 - phi) / xi;
 
   // ---------------- reverse
+  // Sums over the directions enter only through low moments of the weighted
+  // adjoints w_i L_i (M0, M1, M2 below) and, for the central-moment part,
+  // through the contractions T(a, b, c) = sum_i L_i X_a(cx) Y_b(cy) Z_c(cz).
   double l_ux = 0, l_uy = 0, l_uz = 0, l_ax = 0, l_ay = 0, l_az = 0;
   double l_phi = 0, l_T = 0, l_pst = 0;
-  // f collision: f' = f* - omT (f* - w Tc E) + w (q - u.G)
+  const double u_[3] = {ux, uy, uz}, a_[3] = {ax, ay, az};
+  // f collision: f' = f* - omT (f* - w Tc E) + w (q - u.G), E = 1 - 1.5 uu + 4.5 cu^2 + 3 cu
   if constexpr (QF > 0) {
     const double omT = rp.omega_T;
-    double sw = 0;
-    static_for<0, QF>([&](auto I) {
+    const WMoments M = wmoments<QF>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      constexpr double w = weight<QF>(i);
-      constexpr int ex = cx<QF>(i), ey = cy<QF>(i), ez = cz<QF>(i);
       const double L = A.lam_in[(size_t)(OF + i) * N + cell];
-      const double cu = ex * ux + ey * uy + ez * uz;
       A.lstar[(size_t)(OF + i) * N + cell] = (1.0 - omT) * L;
-      l_T += omT * L * w * (1.0 - 1.5 * uu + 4.5 * cu * cu + 3.0 * cu);
-      const double k = omT * L * w * Tc;
-      l_ux += k * (-3.0 * ux + 9.0 * cu * ex + 3.0 * ex);
-      l_uy += k * (-3.0 * uy + 9.0 * cu * ey + 3.0 * ey);
-      l_uz += k * (-3.0 * uz + 9.0 * cu * ez + 3.0 * ez);
-      sw += L * w;
+      return L;
     });
-    l_ux -= sw * Gx; l_uy -= sw * Gy; l_uz -= sw * Gz;
+    double Mu[3];
+    M.m2_times(u_, Mu);
+    l_T += omT * ((1.0 - 1.5 * uu) * M.m0 + 4.5 * (Mu[0] * ux + Mu[1] * uy + Mu[2] * uz) +
+                  3.0 * (M.m1[0] * ux + M.m1[1] * uy + M.m1[2] * uz));
+    const double k = omT * Tc;
+    l_ux += k * (-3.0 * ux * M.m0 + 9.0 * Mu[0] + 3.0 * M.m1[0]) - M.m0 * Gx;
+    l_uy += k * (-3.0 * uy * M.m0 + 9.0 * Mu[1] + 3.0 * M.m1[1]) - M.m0 * Gy;
+    l_uz += k * (-3.0 * uz * M.m0 + 9.0 * Mu[2] + 3.0 * M.m1[2]) - M.m0 * Gz;
   }
   // h collision: h' = h* - om (h* - w phi E) + sc w c.Fphi
-  double l_Fpx = 0, l_Fpy = 0, l_Fpz = 0;
+  double l_Fpx, l_Fpy, l_Fpz;
   {
     const double om = rp.omega_phi, sc = 1.0 - 0.5 * om;
-    static_for<0, QH>([&](auto I) {
+    const WMoments M = wmoments<QH>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      constexpr double w = weight<QH>(i);
-      constexpr int ex = cx<QH>(i), ey = cy<QH>(i), ez = cz<QH>(i);
       const double L = A.lam_in[(size_t)i * N + cell];
-      const double cu = ex * ux + ey * uy + ez * uz;
       A.lstar[(size_t)i * N + cell] = (1.0 - om) * L;
-      l_phi += om * L * w * (1.0 - 1.5 * uu + 4.5 * cu * cu + 3.0 * cu);
-      const double k = om * L * w * phi;
-      l_ux += k * (-3.0 * ux + 9.0 * cu * ex + 3.0 * ex);
-      l_uy += k * (-3.0 * uy + 9.0 * cu * ey + 3.0 * ey);
-      l_uz += k * (-3.0 * uz + 9.0 * cu * ez + 3.0 * ez);
-      l_Fpx += sc * L * w * ex; l_Fpy += sc * L * w * ey; l_Fpz += sc * L * w * ez;
+      return L;
     });
+    double Mu[3];
+    M.m2_times(u_, Mu);
+    l_phi += om * ((1.0 - 1.5 * uu) * M.m0 + 4.5 * (Mu[0] * ux + Mu[1] * uy + Mu[2] * uz) +
+                   3.0 * (M.m1[0] * ux + M.m1[1] * uy + M.m1[2] * uz));
+    const double k = om * phi;
+    l_ux += k * (-3.0 * ux * M.m0 + 9.0 * Mu[0] + 3.0 * M.m1[0]);
+    l_uy += k * (-3.0 * uy * M.m0 + 9.0 * Mu[1] + 3.0 * M.m1[1]);
+    l_uz += k * (-3.0 * uz * M.m0 + 9.0 * Mu[2] + 3.0 * M.m1[2]);
+    l_Fpx = sc * M.m1[0]; l_Fpy = sc * M.m1[1]; l_Fpz = sc * M.m1[2];
   }
   // g collision: g' = w [p* - 1.5 (uu + ua) + 3 cu + 1.5 ca + 4.5 cu^2 + 4.5 cu ca] + sum_m P_m B_m(c; u)
-  double lPxx = 0, lPyy = 0, lPzz = 0, lPxy = 0, lPxz = 0, lPyz = 0;
-  static_for<0, 27>([&](auto I) {
-    constexpr int i = decltype(I)::value;
-    constexpr double w = weight<27>(i);
-    constexpr int ex = cx<27>(i), ey = cy<27>(i), ez = cz<27>(i);
-    const double L = A.lam_in[(size_t)(OG + i) * N + cell];
-    const double cu = ex * ux + ey * uy + ez * uz, ca = ex * ax + ey * ay + ez * az;
-    const double wl = w * L;
-    l_pst += wl;
-    l_ux += wl * (-1.5 * (2.0 * ux + ax) + 3.0 * ex + 9.0 * cu * ex + 4.5 * ca * ex);
-    l_uy += wl * (-1.5 * (2.0 * uy + ay) + 3.0 * ey + 9.0 * cu * ey + 4.5 * ca * ey);
-    l_uz += wl * (-1.5 * (2.0 * uz + az) + 3.0 * ez + 9.0 * cu * ez + 4.5 * ca * ez);
-    l_ax += wl * (-1.5 * ux + 1.5 * ex + 4.5 * cu * ex);
-    l_ay += wl * (-1.5 * uy + 1.5 * ey + 4.5 * cu * ey);
-    l_az += wl * (-1.5 * uz + 1.5 * ez + 4.5 * cu * ez);
-    const double X0 = bas(0, ex, ux), X1 = bas(1, ex, ux), X2 = bas(2, ex, ux);
-    const double Y0 = bas(0, ey, uy), Y1 = bas(1, ey, uy), Y2 = bas(2, ey, uy);
-    const double Z0 = bas(0, ez, uz), Z1 = bas(1, ez, uz), Z2 = bas(2, ez, uz);
-    lPxx += L * X2 * Y0 * Z0; lPyy += L * X0 * Y2 * Z0; lPzz += L * X0 * Y0 * Z2;
-    lPxy += L * X1 * Y1 * Z0; lPxz += L * X1 * Y0 * Z1; lPyz += L * X0 * Y1 * Z1;
-    l_ux += L * (Pyy * X1 * Y2 * Z0 + Pzz * X1 * Y0 * Z2 + 2.0 * Pxy * X2 * Y1 * Z0 + 2.0 * Pxz * X2 * Y0 * Z1 +
-                 Pyz * X1 * Y1 * Z1);
-    l_uy += L * (Pxx * X2 * Y1 * Z0 + Pzz * X0 * Y1 * Z2 + 2.0 * Pxy * X1 * Y2 * Z0 + Pxz * X1 * Y1 * Z1 +
-                 2.0 * Pyz * X0 * Y2 * Z1);
-    l_uz += L * (Pxx * X2 * Y0 * Z1 + Pyy * X0 * Y2 * Z1 + Pxy * X1 * Y1 * Z1 + 2.0 * Pxz * X1 * Y0 * Z2 +
-                 2.0 * Pyz * X0 * Y1 * Z2);
-  });
+  double Lg[3][3][3];  // [iz][iy][ix], axis index 0 / 1 / 2 for c = 0 / +1 / -1
+  {
+    const WMoments M = wmoments<27>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      constexpr int ix = cx<27>(i) == 0 ? 0 : (cx<27>(i) > 0 ? 1 : 2);
+      constexpr int iy = cy<27>(i) == 0 ? 0 : (cy<27>(i) > 0 ? 1 : 2);
+      constexpr int iz = cz<27>(i) == 0 ? 0 : (cz<27>(i) > 0 ? 1 : 2);
+      const double L = A.lam_in[(size_t)(OG + i) * N + cell];
+      Lg[iz][iy][ix] = L;
+      return L;
+    });
+    double Mu[3], Ma[3];
+    M.m2_times(u_, Mu);
+    M.m2_times(a_, Ma);
+    l_pst += M.m0;
+    l_ux += -1.5 * (2.0 * ux + ax) * M.m0 + 3.0 * M.m1[0] + 9.0 * Mu[0] + 4.5 * Ma[0];
+    l_uy += -1.5 * (2.0 * uy + ay) * M.m0 + 3.0 * M.m1[1] + 9.0 * Mu[1] + 4.5 * Ma[1];
+    l_uz += -1.5 * (2.0 * uz + az) * M.m0 + 3.0 * M.m1[2] + 9.0 * Mu[2] + 4.5 * Ma[2];
+    l_ax += -1.5 * ux * M.m0 + 1.5 * M.m1[0] + 4.5 * Mu[0];
+    l_ay += -1.5 * uy * M.m0 + 1.5 * M.m1[1] + 4.5 * Mu[1];
+    l_az += -1.5 * uz * M.m0 + 1.5 * M.m1[2] + 4.5 * Mu[2];
+  }
+  // T(a, b, c) by three 1D contractions
+  double Xb[3][3], Yb[3][3], Zb[3][3];  // [order][axis index]
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int cv = c == 0 ? 0 : (c == 1 ? 1 : -1);
+      Xb[e][c] = bas(e, cv, ux);
+      Yb[e][c] = bas(e, cv, uy);
+      Zb[e][c] = bas(e, cv, uz);
+    }
+  }
+  double Tx[3][3][3];  // [a][iz][iy]
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int iz = 0; iz < 3; ++iz)
+#pragma unroll
+      for (int iy = 0; iy < 3; ++iy)
+        Tx[a][iz][iy] = Lg[iz][iy][0] * Xb[a][0] + Lg[iz][iy][1] * Xb[a][1] + Lg[iz][iy][2] * Xb[a][2];
+  double Txy[3][3][3];  // [a][b][iz]
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int bb = 0; bb < 3; ++bb)
+#pragma unroll
+      for (int iz = 0; iz < 3; ++iz)
+        Txy[a][bb][iz] = Tx[a][iz][0] * Yb[bb][0] + Tx[a][iz][1] * Yb[bb][1] + Tx[a][iz][2] * Yb[bb][2];
+  auto T3 = [&](int a, int bb, int c) {
+    return Txy[a][bb][0] * Zb[c][0] + Txy[a][bb][1] * Zb[c][1] + Txy[a][bb][2] * Zb[c][2];
+  };
+  const double lPxx = T3(2, 0, 0), lPyy = T3(0, 2, 0), lPzz = T3(0, 0, 2);
+  const double lPxy = T3(1, 1, 0), lPxz = T3(1, 0, 1), lPyz = T3(0, 1, 1);
+  const double T120 = T3(1, 2, 0), T102 = T3(1, 0, 2), T210 = T3(2, 1, 0), T201 = T3(2, 0, 1);
+  const double T111 = T3(1, 1, 1), T012 = T3(0, 1, 2), T021 = T3(0, 2, 1);
+  // d/du of the bases raises the order: d b_0 = b_1, d b_1 = 2 b_2
+  l_ux += Pyy * T120 + Pzz * T102 + 2.0 * Pxy * T210 + 2.0 * Pxz * T201 + Pyz * T111;
+  l_uy += Pxx * T210 + Pzz * T012 + 2.0 * Pxy * T120 + Pxz * T111 + 2.0 * Pyz * T021;
+  l_uz += Pxx * T201 + Pyy * T021 + Pxy * T111 + 2.0 * Pxz * T102 + 2.0 * Pyz * T012;
   // P_m = k1 B_m(s, p*, u, a)
   const double l_k1 = lPxx * Bxx + lPyy * Byy + lPzz * Bzz + lPxy * Bxy + lPxz * Bxz + lPyz * Byz;
   const double l_sxx = k1 * lPxx, l_syy = k1 * lPyy, l_szz = k1 * lPzz;
@@ -236,60 +329,21 @@ __device__ __forceinline__ void cell_adjoint(const DevParams& P, const AdjPtrs& 
   A.fld[(size_t)ADJ_GTZ * N + cell] = l_gTz;
 }
 
-// Pass A: the generic kernel's z-march (phi / T halo planes from the pulled
-// state s^n in shared memory), then cell_adjoint per cell.
+// Pass A: pointwise, from the saved intermediates of the step.  Grid: x over
+// the cells of one plane (32-bit index), y = z.
 template <int QH, int QF>
-__global__ void __launch_bounds__(NTHREADS) adj_cell_kernel(const DevParams P, const AdjPtrs A, int zchunk) {
-  __shared__ double s_phi[3][HP];
-  __shared__ double s_T[3][HP];
-  const auto& rp = P.pd;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int tid = ty * TX + tx;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int z0 = blockIdx.z * zchunk;
-  const int z1 = min(z0 + zchunk, P.nz);
-  const int x = x0 + tx, y = y0 + ty;
-  const bool active = (x < P.nx) && (y < P.ny);
-  auto fill = [&](int zp, int slot) {
-    for (int k = tid; k < HP; k += NTHREADS) {
-      const int gx = wrap_any(x0 + (k % HX) - 1, P.nx);
-      const int gy = wrap_any(y0 + (k / HX) - 1, P.ny);
-      int zz = zp;
-      bool ghost = false;
-      if (P.walls) {
-        if (zp < 0) { zz = 0; ghost = true; }
-        else if (zp >= P.nz) { zz = P.nz - 1; ghost = true; }
-      } else {
-        zz = wrap(zp, P.nz);
-      }
-      const double phi = pulled_sum<QH, false>(P, A.s_h, gx, gy, zz, 0.0);
-      double T = pulled_sum<QF, true>(P, A.s_f, gx, gy, zz, 0.0);
-      if (ghost) T = 2.0 * (zp < 0 ? rp.T_bottom : rp.T_top) - T;
-      s_phi[slot][k] = phi;
-      s_T[slot][k] = T;
-    }
-  };
-  int sm = 0, sc = 1, sp = 2;
-  if (z0 < z1) {
-    fill(z0 - 1, sm);
-    fill(z0, sc);
-  }
-  for (int z = z0; z < z1; ++z) {
-    fill(z + 1, sp);
-    __syncthreads();
-    if (active) {
-      const int c0 = (ty + 1) * HX + (tx + 1);
-      Stencil27<double> fd;
-      fd.template eval<HX>(s_phi[sm], s_phi[sc], s_phi[sp], s_T[sm], s_T[sc], s_T[sp], c0);
-      auto getg = [&](auto I) { return pull<27, false, decltype(I)::value>(P, A.s_g, x, y, z, 0.0); };
-      cell_adjoint<QH, QF>(P, A, x, y, z, cell_index(P, x, y, z), s_phi[sc][c0], s_T[sc][c0], fd, getg);
-    }
-    __syncthreads();
-    const int t = sm;
-    sm = sc;
-    sc = sp;
-    sp = t;
-  }
+__global__ void adj_point_kernel(const DevParams P, const AdjPtrs A) {
+  const unsigned plane = (unsigned)P.nx * (unsigned)P.ny;
+  const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= plane) return;
+  const int y = (int)(r / (unsigned)P.nx), x = (int)(r - (unsigned)y * (unsigned)P.nx);
+  const int z = blockIdx.y;
+  const size_t cell = (size_t)z * plane + r;
+  double phi, Tc;
+  Stencil27<double> fd;
+  GMoments<double> m;
+  cell_adjoint_inputs(P, A.save, cell, phi, Tc, fd, m);
+  cell_adjoint<QH, QF>(P, A, x, y, z, cell, phi, Tc, fd, m);
 }
 
 // Pass B1: total adjoints of phi and T (stencil transposes).  Grid: x over
@@ -298,67 +352,68 @@ __global__ void adj_fields_kernel(const DevParams P, const AdjPtrs A) {
   const size_t N = (size_t)P.N;
   const unsigned plane = (unsigned)P.nx * (unsigned)P.ny;
   const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < plane) {
-    const int y = (int)(r / (unsigned)P.nx), x = (int)(r - (unsigned)y * (unsigned)P.nx);
-    const int z = blockIdx.y;
-    const size_t cell = (size_t)z * plane + r;
-    double lphi = A.fld[(size_t)ADJ_PHI * N + cell];
-    double lT = A.fld[(size_t)ADJ_T * N + cell];
-    // central term of the Laplacian: lap(x) = 6 sum_k w_k (v(x + c_k) - v(x))
-    lphi -= 6.0 * (1.0 - weight<27>(0)) * A.fld[(size_t)ADJ_LP * N + cell];
-    // x reads v at x + c_k: every (x, k) whose read resolves to this cell
-    auto add_from = [&](int xs, int ys, int zs, int k, double sgn_T) {
-      const size_t c = cell_index(P, xs, ys, zs);
-      const double w = weight<27>(k);
-      const int ex = q27_cx(k), ey = q27_cy(k), ez = q27_cz(k);
-      lphi += 3.0 * w * (ex * A.fld[(size_t)ADJ_GPX * N + c] + ey * A.fld[(size_t)ADJ_GPY * N + c] +
-                         ez * A.fld[(size_t)ADJ_GPZ * N + c]) +
-              6.0 * w * A.fld[(size_t)ADJ_LP * N + c];
-      lT += sgn_T * 3.0 * w * (ex * A.fld[(size_t)ADJ_GTX * N + c] + ey * A.fld[(size_t)ADJ_GTY * N + c] +
-                               ez * A.fld[(size_t)ADJ_GTZ * N + c]);
-    };
-    for (int k = 1; k < 27; ++k) {
-      const int ex = q27_cx(k), ey = q27_cy(k), ez = q27_cz(k);
-      const int xs = wrap(x - ex, P.nx), ys = wrap(y - ey, P.ny);
-      int zs = z - ez;
-      if (P.walls) {
-        if (zs >= 0 && zs < P.nz) add_from(xs, ys, zs, k, 1.0);
-        // wall ghosts: a cell of the boundary layer reading across the wall
-        // reads this (same-layer) cell: phi mirrored, T as 2 T_w - T
-        if (z == 0 && ez == -1) add_from(xs, ys, 0, k, -1.0);
-        if (z == P.nz - 1 && ez == 1) add_from(xs, ys, P.nz - 1, k, -1.0);
-      } else {
-        add_from(xs, ys, wrap(zs, P.nz), k, 1.0);
+  if (r >= plane) return;
+  const int y = (int)(r / (unsigned)P.nx), x = (int)(r - (unsigned)y * (unsigned)P.nx);
+  const int z = blockIdx.y;
+  const size_t cell = (size_t)z * plane + r;
+  const double* F = A.fld;
+  double lphi = F[(size_t)ADJ_PHI * N + cell];
+  double lT = F[(size_t)ADJ_T * N + cell];
+  // central term of the Laplacian: lap(x) = 6 sum_k w_k (v(x + c_k) - v(x))
+  lphi -= 6.0 * (1.0 - weight<27>(0)) * F[(size_t)ADJ_LP * N + cell];
+  // x reads v at x + c_k: every (x, k) whose read resolves to this cell
+  auto add_from = [&](size_t c, double w, int ex, int ey, int ez, double sgn_T) {
+    double gphi = 0.0, gT = 0.0;
+    if (ex) { gphi += ex * F[(size_t)ADJ_GPX * N + c]; gT += ex * F[(size_t)ADJ_GTX * N + c]; }
+    if (ey) { gphi += ey * F[(size_t)ADJ_GPY * N + c]; gT += ey * F[(size_t)ADJ_GTY * N + c]; }
+    if (ez) { gphi += ez * F[(size_t)ADJ_GPZ * N + c]; gT += ez * F[(size_t)ADJ_GTZ * N + c]; }
+    lphi += 3.0 * w * gphi + 6.0 * w * F[(size_t)ADJ_LP * N + c];
+    lT += sgn_T * 3.0 * w * gT;
+  };
+  static_for<1, 27>([&](auto K) {
+    constexpr int k = decltype(K)::value;
+    constexpr int ex = q27_cx(k), ey = q27_cy(k), ez = q27_cz(k);
+    constexpr double w = weight<27>(k);
+    const int xs = wrap(x - ex, P.nx), ys = wrap(y - ey, P.ny);
+    const int zs = z - ez;
+    if (P.walls) {
+      if (zs >= 0 && zs < P.nz) add_from(cell_index(P, xs, ys, zs), w, ex, ey, ez, 1.0);
+      // wall ghosts: a cell of the boundary layer reading across the wall
+      // reads this (same-layer) cell: phi mirrored, T as 2 T_w - T
+      if constexpr (ez == -1) {
+        if (z == 0) add_from(cell_index(P, xs, ys, 0), w, ex, ey, ez, -1.0);
       }
+      if constexpr (ez == 1) {
+        if (z == P.nz - 1) add_from(cell_index(P, xs, ys, P.nz - 1), w, ex, ey, ez, -1.0);
+      }
+    } else {
+      add_from(cell_index(P, xs, ys, wrap(zs, P.nz)), w, ex, ey, ez, 1.0);
     }
-    A.tot[cell] = lphi;
-    A.tot[N + cell] = lT;
-  }
+  });
+  A.tot[cell] = lphi;
+  A.tot[N + cell] = lT;
 }
 
-// Pass B2: transpose of the pull (with bounce-back / anti-bounce-back).
-// Grid: x over the cells of one plane (32-bit index), y = z, z = direction.
+// Pass B2: transpose of the pull (with bounce-back / anti-bounce-back), one
+// thread per cell for all directions.  Grid: x over the cells of one plane
+// (32-bit index), y = z.
 template <int QH, int QF>
 __global__ void adj_pull_kernel(const DevParams P, const AdjPtrs A) {
   const size_t N = (size_t)P.N;
   const unsigned plane = (unsigned)P.nx * (unsigned)P.ny;
   const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < plane) {
-    const int y = (int)(r / (unsigned)P.nx), x = (int)(r - (unsigned)y * (unsigned)P.nx);
-    const int z = blockIdx.y, d = blockIdx.z;
-    const size_t cell = (size_t)z * plane + r;
-    const size_t k = (size_t)d * N + cell;
-    int set, j, ex, ey, ez, jb;
-    if (d < QH) {
-      set = 0; j = d; ex = cx<QH>(j); ey = cy<QH>(j); ez = cz<QH>(j);
-      jb = opp<QH>(j);
-    } else if (d < QH + 27) {
-      set = 1; j = d - QH; ex = cx<27>(j); ey = cy<27>(j); ez = cz<27>(j);
-      jb = QH + opp<27>(j);
-    } else {
-      set = 2; j = d - QH - 27; ex = cx<QF>(j); ey = cy<QF>(j); ez = cz<QF>(j);
-      jb = QH + 27 + opp<QF>(j);
-    }
+  if (r >= plane) return;
+  const int y = (int)(r / (unsigned)P.nx), x = (int)(r - (unsigned)y * (unsigned)P.nx);
+  const int z = blockIdx.y;
+  const size_t cell = (size_t)z * plane + r;
+  const double tphi = A.tot[cell], tT = A.tot[N + cell];
+  // set 0: h (+ phi), 1: g, 2: f (+ T, anti-bounce-back)
+  auto one = [&](auto SET, auto J) {
+    constexpr int set = decltype(SET)::value, j = decltype(J)::value;
+    constexpr int Q = set == 0 ? QH : (set == 1 ? 27 : QF);
+    constexpr int off = set == 0 ? 0 : (set == 1 ? QH : QH + 27);
+    constexpr int ex = cx<Q>(j), ey = cy<Q>(j), ez = cz<Q>(j);
+    constexpr int jb = opp<Q>(j);
     int zt = z + ez;
     bool inside = true;
     if (P.walls) inside = zt >= 0 && zt < P.nz;
@@ -366,16 +421,19 @@ __global__ void adj_pull_kernel(const DevParams P, const AdjPtrs A) {
     double v;
     if (inside) {
       const size_t c = cell_index(P, wrap(x + ex, P.nx), wrap(y + ey, P.ny), zt);
-      v = A.lstar[(size_t)d * N + c];
-      if (set == 0) v += A.tot[c];
-      else if (set == 2) v += A.tot[N + c];
+      v = A.lstar[(size_t)(off + j) * N + c];
+      if constexpr (set == 0) v += A.tot[c];
+      if constexpr (set == 2) v += A.tot[N + c];
     } else {
-      v = A.lstar[(size_t)jb * N + cell];
-      if (set == 0) v += A.tot[cell];
-      else if (set == 2) v = -(v + A.tot[N + cell]);
+      v = A.lstar[(size_t)(off + jb) * N + cell];
+      if constexpr (set == 0) v += tphi;
+      if constexpr (set == 2) v = -(v + tT);
     }
-    A.lam_out[k] = v;
-  }
+    A.lam_out[(size_t)(off + j) * N + cell] = v;
+  };
+  static_for<0, QH>([&](auto J) { one(std::integral_constant<int, 0>{}, J); });
+  static_for<0, 27>([&](auto J) { one(std::integral_constant<int, 1>{}, J); });
+  static_for<0, QF>([&](auto J) { one(std::integral_constant<int, 2>{}, J); });
 }
 
 // Seed lam^N for J(phi^N): dJ/dphi given per cell (dense, N values) -> the

@@ -82,10 +82,10 @@ Geometry geometry(int nx, int ny, int nz, lbm_precision prec, int qh, int qf, bo
   const char* env = std::getenv("LBM_ZCHUNK");
   int zc = env ? std::atoi(env) : 0;
   if (zc <= 0) {
-    // bulk: one CTA per SM, aim for >= 4 waves with chunks of >= 32 planes
+    // bulk: one CTA per SM, aim for >= 4 waves with chunks of >= 16 planes
     // (each chunk refills its copy pipeline); generic: ~8 CTAs per SM.
     const long long want = g.bulk ? 152LL * 4 : 152LL * 8;
-    const int minc = g.bulk ? 32 : 8;
+    const int minc = g.bulk ? 16 : 8;
     int nchunks = (int)((want + cols - 1) / cols);
     if (nchunks > nz / minc) nchunks = nz / minc;
     if (nchunks < 1) nchunks = 1;
@@ -178,6 +178,8 @@ struct lbm_domain {
   lbm_status sticky;
   std::string sticky_msg;
   TMaps maps[2];  // tensor maps of PDF set 0 / 1 (bulk kernel)
+  // MODE_SAVE target of the next passes (FP64 adjoint; [SAVE_N][N] doubles)
+  double* save_ptr = nullptr;
   // step-kernel timing (lbm_profile_steps): event pairs around each launch
   std::vector<cudaEvent_t> prof_ev;
   bool prof_on = false;
@@ -226,6 +228,7 @@ StepPtrs<S, typename Store<S>::R> ptrs(lbm_domain* d) {
   A.acc_out = (R*)at(d, d->L.acc);
   A.rk_acc = d->th == LBM_TH_RK4;
   A.diag_partials = (double*)at(d, d->L.partials);
+  A.save = std::is_same<R, double>::value ? (R*)d->save_ptr : nullptr;
   A.error_flag = (int*)at(d, d->L.errflag);
   const size_t np = (size_t)d->dp.Np;
   for (int i = 0; i < 27; ++i) {
@@ -874,15 +877,17 @@ struct AdjBuffers {
   char* base = nullptr;
   double *lam_a = nullptr, *lam_b = nullptr, *lstar = nullptr, *fld = nullptr, *tot = nullptr;
   double *dJdphi = nullptr, *dJdI = nullptr;
-  char* sets = nullptr;  // nsets padded PDF sets
+  char* sets = nullptr;   // nsets padded PDF sets (checkpoints)
   size_t set_bytes = 0;
+  double* saves = nullptr;  // nsaves x [SAVE_N][N] step intermediates
+  size_t save_elems = 0;
 };
 
 size_t pdf_set_bytes(const lbm_domain* d) {
   return (size_t)(d->qh + 27 + d->qf) * (size_t)d->dp.Np * sizeof(double);
 }
 
-lbm_status adj_alloc(lbm_domain* d, int nsets, AdjBuffers* B) {
+lbm_status adj_alloc(lbm_domain* d, int nsets, int nsaves, AdjBuffers* B) {
   const size_t N = (size_t)d->N, nq = (size_t)(d->qh + 27 + d->qf);
   B->set_bytes = pdf_set_bytes(d);
   size_t off = 0;
@@ -894,6 +899,8 @@ lbm_status adj_alloc(lbm_domain* d, int nsets, AdjBuffers* B) {
   size_t o_dp = off; off = align256(off + N * 8);
   size_t o_di = off; off = align256(off + LBM_MAX_PATCHES * 8);
   size_t o_se = off; off = align256(off + (size_t)nsets * B->set_bytes);
+  B->save_elems = (size_t)SAVE_N * N;
+  size_t o_sv = off; off = align256(off + (size_t)nsaves * B->save_elems * 8);
   if (cudaMalloc(&B->base, off) != cudaSuccess) {
     cudaGetLastError();
     B->base = nullptr;
@@ -907,20 +914,18 @@ lbm_status adj_alloc(lbm_domain* d, int nsets, AdjBuffers* B) {
   B->dJdphi = (double*)(B->base + o_dp);
   B->dJdI = (double*)(B->base + o_di);
   B->sets = B->base + o_se;
+  B->saves = (double*)(B->base + o_sv);
   return LBM_OK;
 }
 
 char* cur_set(lbm_domain* d) { return d->ws + d->L.h[d->cur]; }
 
-// lam_out = (dPhi/ds)^T lam_in for the forward state held in 'state' (a
-// padded set).  Also accumulates dJ/dI from lam_in into B.dJdI if patches.
-lbm_status adj_one_step(lbm_domain* d, const char* state, const double* lam_in, double* lam_out,
+// lam_out = (dPhi/ds)^T lam_in for the step whose intermediates (MODE_SAVE)
+// are in 'save'.  Also accumulates dJ/dI from lam_in into B.dJdI if patches.
+lbm_status adj_one_step(lbm_domain* d, const double* save, const double* lam_in, double* lam_out,
                         AdjBuffers& B, bool patch_grad, double ncap) {
-  const size_t np = (size_t)d->dp.Np;
   AdjPtrs A;
-  A.s_h = (const double*)state;
-  A.s_g = A.s_h + (size_t)d->qh * np;
-  A.s_f = A.s_g + 27 * np;
+  A.save = save;
   A.lam_in = lam_in;
   A.lstar = B.lstar;
   A.fld = B.fld;
@@ -954,12 +959,16 @@ lbm_status lbm_adjoint_step(lbm_domain* d, const double* lam_in_host, double* la
   if (s != LBM_OK) return s;
   if (!lam_in_host || !lam_out_host) return fail(LBM_ERR_ARG, "null argument");
   AdjBuffers B;
-  s = adj_alloc(d, 0, &B);
+  s = adj_alloc(d, 0, 1, &B);
   if (s != LBM_OK) return s;
   const size_t bytes = (size_t)(d->qh + 27 + d->qf) * (size_t)d->N * 8;
   s = check_cuda(d, cudaMemcpyAsync(B.lam_a, lam_in_host, bytes, cudaMemcpyHostToDevice, d->stream),
                  "adjoint input copy");
-  if (s == LBM_OK) s = adj_one_step(d, cur_set(d), B.lam_a, B.lam_b, B, false, normal_cap);
+  // intermediates of the step from the current state (read-only pass)
+  d->save_ptr = B.saves;
+  if (s == LBM_OK) s = run_pass(d, MODE_SAVE);
+  d->save_ptr = nullptr;
+  if (s == LBM_OK) s = adj_one_step(d, B.saves, B.lam_a, B.lam_b, B, false, normal_cap);
   if (s == LBM_OK)
     s = check_cuda(d, cudaMemcpyAsync(lam_out_host, B.lam_b, bytes, cudaMemcpyDeviceToHost, d->stream),
                    "adjoint output copy");
@@ -978,13 +987,13 @@ lbm_status lbm_adjoint_run(lbm_domain* d, int nsteps, int ckpt_every, const doub
   const int K = ckpt_every;
   const int nseg = (nsteps + K - 1) / K;
   AdjBuffers B;
-  // sets: nseg checkpoints, K replay states, the final state
-  s = adj_alloc(d, nseg + K + 1, &B);
+  // sets: nseg checkpoints and the final state; K step-intermediate slots
+  s = adj_alloc(d, nseg + 1, K, &B);
   if (s != LBM_OK) return s;
   auto set_ptr = [&](int k) { return B.sets + (size_t)k * B.set_bytes; };
+  auto save_slot = [&](int k) { return B.saves + (size_t)k * B.save_elems; };
   char* ckpt0 = set_ptr(0);
-  char* replay0 = set_ptr(nseg);
-  char* final_set = set_ptr(nseg + K);
+  char* final_set = set_ptr(nseg);
   auto copy_set = [&](char* dst, const char* src) {
     return check_cuda(d, cudaMemcpyAsync(dst, src, B.set_bytes, cudaMemcpyDeviceToDevice, d->stream),
                       "adjoint state copy");
@@ -1010,19 +1019,23 @@ lbm_status lbm_adjoint_run(lbm_domain* d, int nsteps, int ckpt_every, const doub
     s = check_launch(d, "adjoint seed");
   }
   if (s == LBM_OK) s = check_cuda(d, cudaMemsetAsync(B.dJdI, 0, LBM_MAX_PATCHES * 8, d->stream), "adjoint memset");
-  // backward over the segments, replaying each from its checkpoint
+  // backward over the segments, replaying each from its checkpoint; the
+  // replayed steps save the intermediates the adjoint steps read
   for (int seg = nseg - 1; seg >= 0 && s == LBM_OK; --seg) {
     const int n0 = seg * K, n1 = std::min(n0 + K, nsteps);
     s = copy_set(cur_set(d), ckpt0 + (size_t)seg * B.set_bytes);
     for (int n = n0; n < n1 && s == LBM_OK; ++n) {
-      s = copy_set(replay0 + (size_t)(n - n0) * B.set_bytes, cur_set(d));
-      if (s == LBM_OK && n + 1 < n1) s = run_pass(d, MODE_COLLIDE);
+      d->save_ptr = save_slot(n - n0);
+      // the last step of a segment only needs its intermediates
+      s = run_pass(d, n + 1 < n1 ? (MODE_COLLIDE | MODE_SAVE) : MODE_SAVE);
     }
+    d->save_ptr = nullptr;
     for (int n = n1 - 1; n >= n0 && s == LBM_OK; --n) {
-      s = adj_one_step(d, replay0 + (size_t)(n - n0) * B.set_bytes, B.lam_a, B.lam_b, B, true, normal_cap);
+      s = adj_one_step(d, save_slot(n - n0), B.lam_a, B.lam_b, B, true, normal_cap);
       std::swap(B.lam_a, B.lam_b);
     }
   }
+  d->save_ptr = nullptr;
   // leave the domain at the forward result
   if (s == LBM_OK) s = copy_set(cur_set(d), final_set);
   if (s == LBM_OK && d->dp.npatch > 0 && dJdI_host)

@@ -396,6 +396,7 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
           GMoments<R> m;
           if (active) {
             m = g_moments<R>(getg);
+            if (mode & MODE_SAVE) save_moments<S>(P, A, cell, m);
             xch[9 * NC + cidx] = m.jx;
             xch[10 * NC + cidx] = m.jy;
             xch[11 * NC + cidx] = m.jz;
@@ -426,6 +427,7 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
         if (active) {
           fd.template eval<G::HXB>(pm, pc, pp, tm, tc, tp, c0);
           if constexpr (QF == 0) rk_std<R, G::HXB>(tm, tc, tp, c0, rgx, rgy, rgz, rlap);
+          if (mode & MODE_SAVE) save_stencil<S>(P, A, cell, pc[c0], tc[c0], fd);
           xch[cidx] = pc[c0];
           xch[NC + cidx] = tc[c0];
           xch[2 * NC + cidx] = fd.gpx;

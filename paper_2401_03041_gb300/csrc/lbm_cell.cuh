@@ -385,6 +385,40 @@ __device__ __forceinline__ void collide_f(const DevParams& P, const StepPtrs<S, 
   }
 }
 
+// MODE_SAVE: the stencil part (phi, T and their finite differences) and the
+// g-moment part of one cell's intermediates.
+template <class S>
+__device__ __forceinline__ void save_stencil(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
+                                             size_t cell, typename Store<S>::R phi, typename Store<S>::R Tc,
+                                             const Stencil27<typename Store<S>::R>& fdv) {
+  const size_t N = (size_t)P.N;
+  A.save[SAVE_PHI * N + cell] = phi;
+  A.save[SAVE_T * N + cell] = Tc;
+  A.save[SAVE_GPX * N + cell] = fdv.gpx;
+  A.save[SAVE_GPY * N + cell] = fdv.gpy;
+  A.save[SAVE_GPZ * N + cell] = fdv.gpz;
+  A.save[SAVE_LP * N + cell] = fdv.lp;
+  A.save[SAVE_GTX * N + cell] = fdv.gtx;
+  A.save[SAVE_GTY * N + cell] = fdv.gty;
+  A.save[SAVE_GTZ * N + cell] = fdv.gtz;
+}
+
+template <class S>
+__device__ __forceinline__ void save_moments(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
+                                             size_t cell, const GMoments<typename Store<S>::R>& m) {
+  const size_t N = (size_t)P.N;
+  A.save[SAVE_PST * N + cell] = m.pst;
+  A.save[SAVE_JX * N + cell] = m.jx;
+  A.save[SAVE_JY * N + cell] = m.jy;
+  A.save[SAVE_JZ * N + cell] = m.jz;
+  A.save[SAVE_SXX * N + cell] = m.sxx;
+  A.save[SAVE_SYY * N + cell] = m.syy;
+  A.save[SAVE_SZZ * N + cell] = m.szz;
+  A.save[SAVE_SXY * N + cell] = m.sxy;
+  A.save[SAVE_SXZ * N + cell] = m.sxz;
+  A.save[SAVE_SYZ * N + cell] = m.syz;
+}
+
 // a2-a10 for one cell in sequence.  GH/GG/GF: accessors i -> pulled
 // (un-shifted) value.
 template <class S, int QH, int QF, class GH, class GG, class GF>
@@ -397,6 +431,10 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
                                             GH geth, GG getg, GF getf, double* dsum) {
   using R = typename Store<S>::R;
   const GMoments<R> m = g_moments<R>(getg);
+  if (mode & MODE_SAVE) {
+    save_stencil<S>(P, A, cell, phi, Tc, fdv);
+    save_moments<S>(P, A, cell, m);
+  }
   const CellFlow<R> f = cell_flow<R>(P, x, y, z, phi, Tc, fdv.gpx, fdv.gpy, fdv.gpz, fdv.lp, fdv.gtx, fdv.gty,
                                      fdv.gtz, m.jx, m.jy, m.jz);
   cell_outputs<S>(P, A, x, y, z, cell, mode, phi, Tc, m.pst, f, dsum);

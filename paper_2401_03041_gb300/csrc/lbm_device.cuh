@@ -143,7 +143,14 @@ template <> __host__ __device__ __forceinline__ const RealParams<double>& RP<dou
 template <> __host__ __device__ __forceinline__ const RealParams<float>& RP<float>(const DevParams& P) { return P.pf; }
 
 // Kernel modes (bit set).
-enum : int { MODE_COLLIDE = 1, MODE_DIAG = 2, MODE_MACRO = 4 };
+enum : int { MODE_COLLIDE = 1, MODE_DIAG = 2, MODE_MACRO = 4, MODE_SAVE = 8 };
+
+// Per-cell quantities of a step written in MODE_SAVE (the adjoint's inputs):
+// dense [SAVE_N][N] arrays of the compute type.
+enum : int {
+  SAVE_PHI = 0, SAVE_T, SAVE_GPX, SAVE_GPY, SAVE_GPZ, SAVE_LP, SAVE_GTX, SAVE_GTY, SAVE_GTZ,
+  SAVE_PST, SAVE_JX, SAVE_JY, SAVE_JZ, SAVE_SXX, SAVE_SYY, SAVE_SZZ, SAVE_SXY, SAVE_SXZ, SAVE_SYZ, SAVE_N
+};
 
 constexpr int kDiagVals = 7;  // mass, heat, kinetic, mx, my, mz, nonfinite count
 
@@ -158,6 +165,7 @@ struct StepPtrs {
   // macroscopic output (MODE_MACRO): order phi, u(3), p, T, selected by mask
   void* macro_out; int macro_dtype; unsigned macro_mask;
   double* diag_partials;          // [grid blocks][kDiagVals] (MODE_DIAG)
+  RF* save;                       // [SAVE_N][N] (MODE_SAVE)
   int* error_flag;                // set to 1 by a CTA whose bounded wait ran out
   // per-direction destination rows (dst + i * N), so a store address is one
   // multiply-add of the cell index onto a constant-bank pointer
@@ -166,13 +174,10 @@ struct StepPtrs {
   S* fd[27];
 };
 
-// Buffers of one adjoint step (lbm_adjoint.cuh): the forward state s^n as a
-// padded FP64 PDF set, and dense FP64 adjoint arrays (N values per direction
-// or field).
+// Buffers of one adjoint step (lbm_adjoint.cuh): dense FP64 arrays (N values
+// per direction or field).
 struct AdjPtrs {
-  const double* s_h;      // forward state s^n: padded PDF arrays (direction stride Np)
-  const double* s_g;
-  const double* s_f;
+  const double* save;     // intermediates of step n (MODE_SAVE), [SAVE_N][N]
   const double* lam_in;   // lam^{n+1}, dense [(QH + 27 + QF)][N]
   double* lstar;          // lam* (direct parts), dense [(QH + 27 + QF)][N]
   double* fld;            // [9][N]: local adjoints of phi, T, grad phi (3), lap phi, grad T (3)
