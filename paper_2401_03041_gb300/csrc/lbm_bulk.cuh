@@ -133,8 +133,9 @@ struct BulkSmem {
   static constexpr size_t g_stage = (size_t)27 * G::GB;
   static constexpr size_t off_hf = 0;
   static constexpr size_t off_g = off_hf + 3 * hf_stage * sizeof(S);
+  // (phi, T) of the halo tile, interleaved, for planes z - 1, z, z + 1
   static constexpr size_t off_phi = (off_g + 2 * g_stage * sizeof(S) + 15) & ~size_t(15);
-  static constexpr size_t off_T = off_phi + 3 * G::HPB * sizeof(R);
+  static constexpr size_t off_T = off_phi + 3 * G::HPB * sizeof(R);   // end of the first half
   // per-cell exchange between the two roles: phi, T, grad phi (3), lap phi,
   // grad T (3) from the h/f role; j (3), p* from the g role
   static constexpr int NX = 13;
@@ -217,8 +218,8 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
   unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
   S* hf = (S*)(smem + L::off_hf);
   S* gb = (S*)(smem + L::off_g);
-  R* s_phi = (R*)(smem + L::off_phi);
-  R* s_T = (R*)(smem + L::off_T);
+  using P2 = typename PairOf<R>::type;
+  P2* s_pt = (P2*)(smem + L::off_phi);             // [3][HPB] (phi, T)
   R* xch = (R*)(smem + L::off_x);                  // [NX][NC] role exchange
   uint64_t* bar = (uint64_t*)(smem + L::off_bar);  // [0..2] HF ring, [3..4] G ring
 
@@ -263,8 +264,7 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
   auto sum_plane_impl = [&](auto btag, int p, int pe, bool ghost, bool lo, bool hi) {
     constexpr bool BOUNCE = decltype(btag)::value;
     const S* st = hf_ptr(p);
-    R* ph = s_phi + hf_slot(p) * G::HPB;
-    R* tt = s_T + hf_slot(p) * G::HPB;
+    P2* pt = s_pt + hf_slot(p) * G::HPB;
     for (int k = tid; k < G::HPB; k += NT) {
       const int hr = k / G::HXB, hc = k % G::HXB;
       const int col = hc + G::GXP - 1;
@@ -294,8 +294,10 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
         T = A.T[cell_index(P, gx, gy, pe)];
       }
       if (ghost) T = (R)2 * (p < 0 ? rp.T_bottom : rp.T_top) - T;
-      ph[k] = phi;
-      tt[k] = T;
+      P2 v;
+      v.x = phi;
+      v.y = T;
+      pt[k] = v;
     }
   };
   auto sum_plane = [&](int p) {
@@ -415,21 +417,19 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
         if (lo || hi) run(std::true_type{});
         else run(std::false_type{});
       } else {
-        const R* pm = s_phi + hf_slot(z - 1) * G::HPB;
-        const R* pc = s_phi + hf_slot(z) * G::HPB;
-        const R* pp = s_phi + hf_slot(z + 1) * G::HPB;
-        const R* tm = s_T + hf_slot(z - 1) * G::HPB;
-        const R* tc = s_T + hf_slot(z) * G::HPB;
-        const R* tp = s_T + hf_slot(z + 1) * G::HPB;
+        const P2* pm = s_pt + hf_slot(z - 1) * G::HPB;
+        const P2* pc = s_pt + hf_slot(z) * G::HPB;
+        const P2* pp = s_pt + hf_slot(z + 1) * G::HPB;
         const int c0 = (ty + 1) * G::HXB + (tx + 1);
         Stencil27<R> fd;
         R rgx = 0, rgy = 0, rgz = 0, rlap = 0;
+        const P2 cen = pc[c0];
         if (active) {
-          fd.template eval<G::HXB>(pm, pc, pp, tm, tc, tp, c0);
-          if constexpr (QF == 0) rk_std<R, G::HXB>(tm, tc, tp, c0, rgx, rgy, rgz, rlap);
-          if (mode & MODE_SAVE) save_stencil<S>(P, A, cell, pc[c0], tc[c0], fd);
-          xch[cidx] = pc[c0];
-          xch[NC + cidx] = tc[c0];
+          eval_pairs<G::HXB>(fd, pm, pc, pp, c0);
+          if constexpr (QF == 0) rk_std_pairs<P2, R, G::HXB>(pm, pc, pp, c0, rgx, rgy, rgz, rlap);
+          if (mode & MODE_SAVE) save_stencil<S>(P, A, cell, cen.x, cen.y, fd);
+          xch[cidx] = cen.x;
+          xch[NC + cidx] = cen.y;
           xch[2 * NC + cidx] = fd.gpx;
           xch[3 * NC + cidx] = fd.gpy;
           xch[4 * NC + cidx] = fd.gpz;
@@ -440,7 +440,7 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
         }
         pair_sync();
         if (active) {
-          const R phi = pc[c0], Tc = tc[c0];
+          const R phi = cen.x, Tc = cen.y;
           const CellFlow<R> f = cell_flow<R>(P, x, y, z, phi, Tc, fd.gpx, fd.gpy, fd.gpz, fd.lp, fd.gtx, fd.gty,
                                              fd.gtz, xch[9 * NC + cidx], xch[10 * NC + cidx], xch[11 * NC + cidx]);
           cell_outputs<S>(P, A, x, y, z, cell, mode, phi, Tc, xch[12 * NC + cidx], f, dsum);

@@ -106,6 +106,76 @@ struct Stencil27 {
   }
 };
 
+// (phi, T) pairs of the bulk kernel's interleaved shared-memory planes.
+template <class R> struct PairOf;
+template <> struct PairOf<float> { using type = float2; };
+template <> struct PairOf<double> { using type = double2; };
+
+// Stencil27 from interleaved (phi, T) planes.  FP32: both fields at once with
+// packed FP32 arithmetic (same per-lane operations and rounding as eval).
+template <int HXv>
+__device__ __forceinline__ void eval_pairs(Stencil27<float>& fd, const float2* pm, const float2* pc,
+                                           const float2* pp, int c0) {
+  const float2 c = pc[c0];
+  const float2 nc = make_float2(-c.x, -c.y);
+  const float2 m1 = make_float2(-1.f, -1.f);
+  float2 L = make_float2(0.f, 0.f), Gx = L, Gy = L, Gz = L;
+  static_for<1, 27>([&](auto K) {
+    constexpr int k = decltype(K)::value;
+    if constexpr (pair_first<27>(k)) {
+      constexpr int ex = q27_cx(k), ey = q27_cy(k), ez = q27_cz(k);
+      const float2* P_ = ez == 0 ? pc : (ez > 0 ? pp : pm);
+      const float2* Pm = ez == 0 ? pc : (ez > 0 ? pm : pp);
+      constexpr int o = ey * HXv + ex;
+      const float2 vp = P_[c0 + o], vm = Pm[c0 - o];
+      constexpr float w = (float)weight<27>(k);
+      L = __ffma2_rn(make_float2(w, w), __fadd2_rn(__fadd2_rn(vp, nc), __fadd2_rn(vm, nc)), L);
+      const float2 d = __ffma2_rn(vm, m1, vp);  // vp - vm
+      if constexpr (ex != 0) Gx = __ffma2_rn(make_float2((float)ex * w, (float)ex * w), d, Gx);
+      if constexpr (ey != 0) Gy = __ffma2_rn(make_float2((float)ey * w, (float)ey * w), d, Gy);
+      if constexpr (ez != 0) Gz = __ffma2_rn(make_float2((float)ez * w, (float)ez * w), d, Gz);
+    }
+  });
+  fd.gpx = 3.f * Gx.x; fd.gpy = 3.f * Gy.x; fd.gpz = 3.f * Gz.x; fd.lp = 6.f * L.x;
+  fd.gtx = 3.f * Gx.y; fd.gty = 3.f * Gy.y; fd.gtz = 3.f * Gz.y; fd.lt = 6.f * L.y;
+}
+
+template <int HXv>
+__device__ __forceinline__ void eval_pairs(Stencil27<double>& fd, const double2* pm, const double2* pc,
+                                           const double2* pp, int c0) {
+  const double phi = pc[c0].x, T = pc[c0].y;
+  fd.gpx = fd.gpy = fd.gpz = fd.lp = fd.gtx = fd.gty = fd.gtz = fd.lt = 0;
+  static_for<1, 27>([&](auto K) {
+    constexpr int k = decltype(K)::value;
+    if constexpr (pair_first<27>(k)) {
+      constexpr int ex = q27_cx(k), ey = q27_cy(k), ez = q27_cz(k);
+      const double2* P_ = ez == 0 ? pc : (ez > 0 ? pp : pm);
+      const double2* Pm = ez == 0 ? pc : (ez > 0 ? pm : pp);
+      constexpr int o = ey * HXv + ex;
+      const double2 vp = P_[c0 + o], vm = Pm[c0 - o];
+      constexpr double w = weight<27>(k);
+      fd.lp += w * ((vp.x - phi) + (vm.x - phi));
+      fd.lt += w * ((vp.y - T) + (vm.y - T));
+      const double dp = vp.x - vm.x, dt = vp.y - vm.y;
+      if constexpr (ex != 0) { fd.gpx += (double)ex * w * dp; fd.gtx += (double)ex * w * dt; }
+      if constexpr (ey != 0) { fd.gpy += (double)ey * w * dp; fd.gty += (double)ey * w * dt; }
+      if constexpr (ez != 0) { fd.gpz += (double)ez * w * dp; fd.gtz += (double)ez * w * dt; }
+    }
+  });
+  fd.gpx *= 3.0; fd.gpy *= 3.0; fd.gpz *= 3.0; fd.lp *= 6.0;
+  fd.gtx *= 3.0; fd.gty *= 3.0; fd.gtz *= 3.0; fd.lt *= 6.0;
+}
+
+// RK stage-1 operator values from interleaved (phi, T) planes (T = .y).
+template <class P2, class R, int HXv>
+__device__ __forceinline__ void rk_std_pairs(const P2* tm, const P2* tc, const P2* tp, int c0, R& gx, R& gy,
+                                             R& gz, R& lap) {
+  gx = (R)0.5 * (tc[c0 + 1].y - tc[c0 - 1].y);
+  gy = (R)0.5 * (tc[c0 + HXv].y - tc[c0 - HXv].y);
+  gz = (R)0.5 * (tp[c0].y - tm[c0].y);
+  lap = tc[c0 + 1].y + tc[c0 - 1].y + tc[c0 + HXv].y + tc[c0 - HXv].y + tp[c0].y + tm[c0].y - (R)6 * tc[c0].y;
+}
+
 // RK stage-1 operator values at the cell (7-point Laplacian, central gradient)
 template <class R, int HXv>
 __device__ __forceinline__ void rk_std(const R* tm, const R* tc, const R* tp, int c0, R& gx, R& gy,
