@@ -430,7 +430,8 @@ def main():
                      "kernel_ms_per_launch": kernel_secs * 1e3 if kernel_secs else None,
                      "step_ms": per_step * 1e3,
                      "traffic": tpc * cells if tpc else None,
-                     "kernel": "lbm::step_bulk_kernel (fused h/g/f stream-collide, cp.async.bulk staging)"
+                     "kernel": "lbm::step_bulk_kernel (fused h/g/f stream-collide, tensor-TMA staging, "
+                               "two threads per cell)"
                                if kinfo["kernel"] == "bulk" else "lbm::step_kernel (fused, generic)"},
         "cpu_baseline": ({"value": cpu["mlups"], "unit": "MLUPS", "cores": 1, "kind": "oracle",
                           "sample": f"{cpu['name']}: {cpu['steps']} FP64 numpy oracle steps in "

@@ -1,6 +1,7 @@
 """Shared set-up for the GPU parity tests: the same seeded workload on the
 CUDA path (through the C ABI binding) and on the FP64 oracle."""
 import numpy as np
+import pytest
 
 import workloads as W
 from oracle import model as om
@@ -114,3 +115,44 @@ def bulk_fits(precision, q_phase, thermal):
 
 def oracle_for(w):
     return om.build(w)
+
+
+def droplet_centroids(phi, periodic_xy=True):
+    """Per-droplet centroids (sorted), the droplet-tracking rule of the
+    design: connected components of phi > 1/2 (merged across the periodic x
+    and y faces), phi-weighted means, circular means on the periodic axes,
+    cell-centred coordinates.  phi: (nz, ny, nx) array."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    lab, n = ndimage.label(phi > 0.5)
+    nz, ny, nx = phi.shape
+    parent = list(range(n + 1))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    if periodic_xy:
+        pairs = list(zip(lab[:, :, 0].ravel(), lab[:, :, -1].ravel()))
+        pairs += list(zip(lab[:, 0, :].ravel(), lab[:, -1, :].ravel()))
+        for a, b in pairs:
+            if a and b and find(a) != find(b):
+                parent[find(a)] = find(b)
+    roots = sorted({find(a) for a in range(1, n + 1)})
+    z, y, x = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5, indexing="ij")
+    out = []
+    for r in roots:
+        mask = np.isin(lab, [a for a in range(1, n + 1) if find(a) == r])
+        wgt = phi[mask]
+        c = []
+        for coord, L in ((x, nx), (y, ny)):
+            if periodic_xy:
+                th = 2 * np.pi * coord[mask] / L
+                ang = np.arctan2((wgt * np.sin(th)).sum(), (wgt * np.cos(th)).sum())
+                c.append((ang % (2 * np.pi)) * L / (2 * np.pi))
+            else:
+                c.append((wgt * coord[mask]).sum() / wgt.sum())
+        c.append((wgt * z[mask]).sum() / wgt.sum())
+        out.append(c)
+    return np.array(sorted(out))

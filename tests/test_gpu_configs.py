@@ -1,0 +1,80 @@
+"""The thermocapillary migration and droplet-capture workloads on the GPU
+(shortened runs; the full-length numbers are recorded in the design notes).
+
+The FP64 GPU path is the reference here: it matches the FP64 oracle to
+1e-11 (test_gpu_parity), and the oracle itself is far too slow for runs of
+thousands of steps on these lattices.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from harness import droplet_centroids, gpu_domain
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_03041_gb300 import build
+    build.build()
+
+
+def _centroid_z(d):
+    g = d.diagnostics()
+    return g["mz"] / g["mass"], g["mass"]
+
+
+def test_config2_migration_all_thermal_options():
+    """64 x 64 x 128 channel, walls at T = -0.5 / +0.5, droplet R = 12: after
+    1000 steps the droplet has moved towards the hot wall by the same
+    distance for every energy solver (LB D3Q7/15/19/27, RK2, RK4) to 1e-3, in
+    FP32 as in FP64, phi mass is conserved to 1e-12 (FP64), and the migration
+    speed is of the order of the Young-Goldstein-Block value
+    2 |sigma_T| G R / (15 mu) = 1.25e-4 lu/step (0.3 - 1.5 x; the periodic
+    images 64 lu apart and the start-up transient slow it down)."""
+    steps = 1000
+    disp = {}
+    for th in ("D3Q7", "D3Q15", "D3Q19", "D3Q27", "RK2", "RK4"):
+        d = gpu_domain(W.config2(th, "fp64"))
+        z0, m0 = _centroid_z(d)
+        d.step(steps - 100)
+        za, _ = _centroid_z(d)
+        d.step(100)
+        z1, m1 = _centroid_z(d)
+        assert abs(m1 - m0) <= 1e-12 * m0, th
+        disp[th] = z1 - z0
+        if th == "D3Q7":
+            v = (z1 - za) / 100
+            assert 0.3 * 1.25e-4 < v < 1.5 * 1.25e-4, v
+        d.close()
+    ref = disp["D3Q7"]
+    assert ref > 0
+    for th, v in disp.items():
+        assert abs(v - ref) <= 1e-3 * ref, (th, v, ref)
+    d = gpu_domain(W.config2("D3Q7", "fp32"))
+    z0, _ = _centroid_z(d)
+    d.step(steps)
+    z1, _ = _centroid_z(d)
+    assert abs((z1 - z0) - ref) <= 1e-3 * ref
+
+
+def test_config3_fp32_tracks_fp64():
+    """256 x 128 x 128 capture workload (3 moving droplets, 4 heaters on the
+    bottom wall): after 1000 steps the three droplet centroids of the FP32
+    shifted-storage run agree with FP64 to 1e-3 lu; phi mass drifts by
+    < 1e-12 (FP64) and < 1e-4 (FP32)."""
+    steps = 1000
+    d64, d32 = gpu_domain(W.config3("fp64")), gpu_domain(W.config3("fp32"))
+    m64, m32 = d64.diagnostics()["mass"], d32.diagnostics()["mass"]
+    d64.step(steps)
+    d32.step(steps)
+    c64 = droplet_centroids(d64.fields(1, dtype="f64")["phi"].cpu().numpy())
+    c32 = droplet_centroids(d32.fields(1, dtype="f64")["phi"].cpu().numpy())
+    assert c64.shape == (3, 3) and c32.shape == (3, 3)
+    assert np.abs(c64 - c32).max() <= 1e-3, np.abs(c64 - c32).max()
+    assert abs(d64.diagnostics()["mass"] - m64) <= 1e-12 * m64
+    assert abs(d32.diagnostics()["mass"] - m32) <= 1e-4 * m32
