@@ -17,7 +17,8 @@
 // cell (bounce-back) and are read without shift.  Boxes complete on mbarriers
 // (expect_tx byte counts).  While plane z is computed, HF(z + 2) and G(z + 1)
 // are in flight: HF uses a ring of three buffers (z, z + 1 for phi/T, z + 2 in
-// flight), G a ring of two.  phi and T of the halo tile are summed from HF and
+// flight), G a ring of two (or of one, issued mid-plane, where two do not fit
+// in shared memory).  phi and T of the halo tile are summed from HF and
 // kept for planes z - 1, z, z + 1.
 //
 // Every wait is bounded (about 2 s); on a timeout the CTA raises the domain's
@@ -131,10 +132,16 @@ struct BulkSmem {
   static constexpr int NHF = QH + QF;
   static constexpr size_t hf_stage = (size_t)NHF * G::HFB;   // elements
   static constexpr size_t g_stage = (size_t)27 * G::GB;
+  // g ring depth: two stages (G(z + 1) in flight during all of plane z) where
+  // the layout fits in 227 KB, else one (G(z + 1) issued once every g-role
+  // thread has taken the moments of G(z))
+  static constexpr size_t fixed_bytes = 3 * hf_stage * sizeof(S) + 3 * G::HPB * 2 * sizeof(R) +
+                                        13 * G::NT * sizeof(R) + 5 * sizeof(uint64_t) + 128 + 64;
+  static constexpr int GR = fixed_bytes + 2 * g_stage * sizeof(S) <= 232448 ? 2 : 1;
   static constexpr size_t off_hf = 0;
   static constexpr size_t off_g = off_hf + 3 * hf_stage * sizeof(S);
   // (phi, T) of the halo tile, interleaved, for planes z - 1, z, z + 1
-  static constexpr size_t off_phi = (off_g + 2 * g_stage * sizeof(S) + 15) & ~size_t(15);
+  static constexpr size_t off_phi = (off_g + GR * g_stage * sizeof(S) + 15) & ~size_t(15);
   static constexpr size_t off_T = off_phi + 3 * G::HPB * sizeof(R);   // end of the first half
   // per-cell exchange between the two roles: phi, T, grad phi (3), lap phi,
   // grad T (3) from the h/f role; j (3), p* from the g role
@@ -160,10 +167,9 @@ template <class S, int QH, int QF, int KIND>
 __device__ __forceinline__ void issue_stage(const DevParams& P, const CUtensorMap* mh,
                                             const CUtensorMap* mg, const CUtensorMap* mf,
                                             S* dst_stage, uint64_t* bar, int p, int x0, int y0,
-                                            int tid) {
+                                            int tid, int nwarps = BulkGeom<S>::NTHR / 32) {
   using G = BulkGeom<S>;
   constexpr int ndir = KIND == 0 ? QH + QF : 27;
-  constexpr int nwarps = G::NTHR / 32;
   const int d = (tid >> 5) + (tid & 31) * nwarps;
   if (d >= ndir) return;
   // plane whose tile this is (walls: the ghost planes reuse the boundary plane)
@@ -253,8 +259,9 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
   // and fill index (p - z0 + 1) / 3; G plane p -> slot (p - z0) % 2, index (p - z0) / 2
   auto hf_slot = [&](int p) { return (p - z0 + 1) % 3; };
   auto hf_par = [&](int p) { return (uint32_t)(((p - z0 + 1) / 3) & 1); };
-  auto g_slot = [&](int p) { return (p - z0) % 2; };
-  auto g_par = [&](int p) { return (uint32_t)(((p - z0) / 2) & 1); };
+  constexpr int GR = L::GR;
+  auto g_slot = [&](int p) { return (p - z0) % GR; };
+  auto g_par = [&](int p) { return (uint32_t)(((p - z0) / GR) & 1); };
   auto hf_ptr = [&](int p) { return hf + (size_t)hf_slot(p) * L::hf_stage; };
   auto g_ptr = [&](int p) { return gb + (size_t)g_slot(p) * L::g_stage; };
 
@@ -336,7 +343,7 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
   // copies.
   auto expect_for = [&](int z) {
     if (z + 2 <= z1) mbar_expect_tx(&bar[hf_slot(z + 2)], hf_bytes);
-    if (z + 1 < z1) mbar_expect_tx(&bar[3 + g_slot(z + 1)], g_bytes);
+    if (GR == 2 && z + 1 < z1) mbar_expect_tx(&bar[3 + g_slot(z + 1)], g_bytes);
   };
   if (z0 < z1) {
     // prologue: HF(z0-1), HF(z0), HF(z0+1), G(z0) now; HF(z0+2), G(z0+1) at
@@ -368,7 +375,7 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
       issue_stage<S, QH, QF, 0>(P, &mh, &mg, &mf, hf_ptr(z + 2), &bar[hf_slot(z + 2)], z + 2, x0, y0, tid);
       mark(hf_slot(z + 2), hf_par(z + 2));
     }
-    if (z + 1 < z1) {
+    if (GR == 2 && z + 1 < z1) {
       issue_stage<S, QH, QF, 1>(P, &mh, &mg, &mf, g_ptr(z + 1), &bar[3 + g_slot(z + 1)], z + 1, x0, y0, tid);
       mark(3 + g_slot(z + 1), g_par(z + 1));
     }
@@ -403,6 +410,20 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
             xch[10 * NC + cidx] = m.jy;
             xch[11 * NC + cidx] = m.jz;
             xch[12 * NC + cidx] = m.pst;
+          }
+          if constexpr (GR == 1) {
+            // every g-role thread has read G(z): warp 0 of the role refills
+            // the single G slot with G(z + 1)
+            asm volatile("bar.sync 15, %0;" ::"r"(NC) : "memory");
+            if (z + 1 < z1) {
+              if (tid < 32) {
+                if (tid == 0) mbar_expect_tx(&bar[3 + g_slot(z + 1)], g_bytes);
+                __syncwarp();
+                issue_stage<S, QH, QF, 1>(P, &mh, &mg, &mf, g_ptr(z + 1), &bar[3 + g_slot(z + 1)], z + 1, x0,
+                                          y0, tid, 1);
+              }
+              mark(3 + g_slot(z + 1), g_par(z + 1));
+            }
           }
           pair_sync();
           if (active && (mode & MODE_COLLIDE)) {

@@ -109,8 +109,9 @@ def bulk_fits(precision, q_phase, thermal):
     rs = 8 if s == 8 else 4
     hfb = -(-W * (rows + 2) * s // 128) * 128
     gb = -(-W * rows * s // 128) * 128
-    smem = 3 * nhf * hfb + 2 * 27 * gb + 6 * (cols + 2) * (rows + 2) * rs + 13 * cols * rows * rs + 64 + 128
-    return smem <= 232448
+    fixed = 3 * nhf * hfb + 6 * (cols + 2) * (rows + 2) * rs + 13 * cols * rows * rs + 64 + 128
+    ring = 2 if fixed + 2 * 27 * gb <= 232448 else 1      # g ring of two stages, else one
+    return fixed + ring * 27 * gb <= 232448
 
 
 def oracle_for(w):

@@ -83,7 +83,7 @@ def test_ragged_walls_fp64(thermal, q_phase):
         compare_all(d, o, w, TOL64, f"ragged walls {thermal} q{q_phase} {kern}")
 
 
-@pytest.mark.parametrize("thermal", ["D3Q7", "D3Q19", "RK2", "RK4"])
+@pytest.mark.parametrize("thermal", ["D3Q7", "D3Q15", "D3Q19", "RK2", "RK4"])
 def test_ragged_periodic_fp64(thermal):
     w = ragged_workload(thermal, 15, walls=False)
     o = oracle_for(w)
@@ -94,18 +94,20 @@ def test_ragged_periodic_fp64(thermal):
         compare_all(d, o, w, TOL64, f"ragged periodic {thermal} {kern}")
 
 
+@pytest.mark.parametrize("thermal", ["D3Q7", "D3Q15"])
 @pytest.mark.parametrize("walls", [True, False])
-def test_bulk_multi_tile_chunked_fp64(walls, monkeypatch):
+def test_bulk_multi_tile_chunked_fp64(walls, thermal, monkeypatch):
     """72 x 24 x 20: several bulk tiles in x (ragged) and y, the z range split
-    into chunks of 6 planes (pipeline prologue at every chunk start)."""
+    into chunks of 6 planes (pipeline prologue at every chunk start); D3Q15
+    thermal runs the one-stage g ring."""
     monkeypatch.setenv("LBM_ZCHUNK", "6")
-    w = ragged_workload("D3Q7", 15, walls=walls, shape=(72, 24, 20))
+    w = ragged_workload(thermal, 15, walls=walls, shape=(72, 24, 20))
     o = oracle_for(w)
     o.step(10)
     d = gpu_domain(w, kernel="bulk")
     assert d.kernel_info()["grid"][2] == 4
     d.step(10)
-    compare_all(d, o, w, TOL64, f"bulk chunked walls={walls}")
+    compare_all(d, o, w, TOL64, f"bulk chunked walls={walls} {thermal}")
 
 
 @pytest.mark.parametrize("nx", [74, 75])
@@ -138,7 +140,7 @@ def test_bulk_ghost_fill_paths_reduced_precision(precision, nx):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
-@pytest.mark.parametrize("thermal", ["D3Q7", "RK2"])
+@pytest.mark.parametrize("thermal", ["D3Q7", "D3Q15", "RK2"])
 def test_bulk_equals_generic_reduced_precision(precision, thermal):
     """The two kernels compute the same arithmetic: in FP32 / FP16 storage
     they agree to the storage rounding after 20 steps."""
