@@ -163,6 +163,26 @@ print(json.dumps({{"mlups": w.cells * steps / dt / 1e6, "steps": steps, "seconds
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def max_over_ranks(v, world: int, device=None):
+    """Maximum of a per-rank scalar over all ranks (the job's time is that of
+    its slowest replica); device is where the collective's tensor lives
+    (the rank's GPU under NCCL, the CPU under gloo)."""
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(cells_per_rank: int, steps: int, world: int, secs_max: float) -> float:
+    """Whole-job throughput of N independent replicas (weak scaling): every
+    rank updates cells_per_rank cells per step; the job takes as long as the
+    slowest rank."""
+    return cells_per_rank * steps * world / secs_max / 1e6
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -243,13 +263,8 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
-    def max_over_ranks(v):
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([v], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return v
+    def reduce_max(v):
+        return max_over_ranks(v, world, dev)
 
     # CPU baseline first (spawned subprocess; no CUDA in it)
     cpu = None
@@ -298,10 +313,10 @@ def main():
     sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
                            if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
     secs, clocks, kernel_secs = timed_steps(d, args.steps, args.warmup, sampler)
-    secs = max_over_ranks(secs)
-    kernel_secs = max_over_ranks(kernel_secs) if kernel_secs else None
+    secs = reduce_max(secs)
+    kernel_secs = reduce_max(kernel_secs) if kernel_secs else None
     cells = w.cells
-    mlups = cells * args.steps * world / secs / 1e6
+    mlups = job_mlups(cells, args.steps, world, secs)
     per_step = secs / args.steps
     # one step-kernel launch, + one ghost-fill launch with the bulk kernel,
     # + the RK stages of the finite-difference energy solvers
@@ -322,7 +337,7 @@ def main():
             d.step_diagnostics(1)
         d.fields(lbm.FIELD_PHI, dtype="f32", out=host_phi)
         torch.cuda.synchronize(dev)
-        e2e_secs = max_over_ranks(time.perf_counter() - t0)
+        e2e_secs = reduce_max(time.perf_counter() - t0)
         barrier()
         e2e = {"value": cells * args.steps * world / e2e_secs / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": len(w.droplets) * 7 * 8 / args.steps,
@@ -338,7 +353,7 @@ def main():
     if not args.no_fp64 and args.precision != "fp64":
         d64 = make_domain("fp64")
         s64, _, _ = timed_steps(d64, args.fp64_steps, 3)
-        s64 = max_over_ranks(s64)
+        s64 = reduce_max(s64)
         fp64 = {"mlups": cells * args.fp64_steps * world / s64 / 1e6,
                 "ms_per_step": s64 / args.fp64_steps * 1e3, "steps": args.fp64_steps}
         del d64
