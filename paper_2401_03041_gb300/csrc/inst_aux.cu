@@ -73,8 +73,26 @@ int bulk_box_cols(int prec) {
   return prec == 0 ? BulkGeom<double>::W : (prec == 1 ? BulkGeom<float>::W : BulkGeom<__half>::W);
 }
 
-int bulk_tile_rows(int prec) {
-  return prec == 0 ? BulkGeom<double>::TYB : (prec == 1 ? BulkGeom<float>::TYB : BulkGeom<__half>::TYB);
+template <class S, int QH>
+static int bulk_rows_qf(int qf) {
+  switch (qf) {
+    case 0: return BulkSmem<S, QH, 0>::G::TYB;
+    case 7: return BulkSmem<S, QH, 7>::G::TYB;
+    case 15: return BulkSmem<S, QH, 15>::G::TYB;
+    case 19: return BulkSmem<S, QH, 19>::G::TYB;
+    default: return BulkSmem<S, QH, 27>::G::TYB;
+  }
+}
+
+template <class S>
+static int bulk_rows_s(int qh, int qf) {
+  return qh == 15 ? bulk_rows_qf<S, 15>(qf) : bulk_rows_qf<S, 27>(qf);
+}
+
+int bulk_tile_rows(int prec, int qh, int qf) {
+  if (prec == 0) return bulk_rows_s<double>(qh, qf);
+  if (prec == 1) return bulk_rows_s<float>(qh, qf);
+  return bulk_rows_s<__half>(qh, qf);
 }
 
 void launch_diag_finalize(const double* partials, int nblocks, double* out, cudaStream_t st) {

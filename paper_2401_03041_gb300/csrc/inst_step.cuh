@@ -21,7 +21,7 @@ void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                              (int)bytes);
         attr_set = true;
       }
-      step_bulk_kernel<S, QH, QF><<<grid, BulkGeom<S>::NTHR, bytes, st>>>(
+      step_bulk_kernel<S, QH, QF><<<grid, BulkSmem<S, QH, QF>::G::NTHR, bytes, st>>>(
           P, A, maps.h, maps.g, maps.f, zchunk, mode);
       return;
     }

@@ -28,7 +28,7 @@ void launch_ghost_fill(const DevParams& P, void* buf, int nq, cudaStream_t st);
 // Dynamic shared memory of the bulk kernel for (precision, q_phase, q_f),
 // and the largest a CTA may use; also its tile height.
 size_t bulk_smem_bytes(int prec, int qh, int qf);
-int bulk_tile_rows(int prec);
+int bulk_tile_rows(int prec, int qh, int qf);
 int bulk_tile_cols(int prec);
 int bulk_box_cols(int prec);   // staged row length W of the bulk kernel
 constexpr size_t kMaxDynSmem = 232448;

@@ -68,14 +68,15 @@ bool bulk_ok(int nx, int ny, lbm_precision prec, int qh, int qf) {
   const char* env = std::getenv("LBM_KERNEL");
   if (env && std::strcmp(env, "generic") == 0) return false;
   if (nx < bulk_box_cols((int)prec)) return false;
-  if (ny < 2 * bulk_tile_rows((int)prec)) return false;
+  const int rows = bulk_tile_rows((int)prec, qh, qf);
+  if (ny < 2 * rows || (ny + rows - 1) / rows > 65535) return false;
   return bulk_smem_bytes((int)prec, qh, qf) <= kMaxDynSmem;
 }
 
 Geometry geometry(int nx, int ny, int nz, lbm_precision prec, int qh, int qf, bool allow_bulk = true) {
   Geometry g;
   g.bulk = allow_bulk && bulk_ok(nx, ny, prec, qh, qf) ? 1 : 0;
-  const int rows = g.bulk ? bulk_tile_rows((int)prec) : TY;
+  const int rows = g.bulk ? bulk_tile_rows((int)prec, qh, qf) : TY;
   const int cols_ = g.bulk ? bulk_tile_cols((int)prec) : TX;
   const int bx = (nx + cols_ - 1) / cols_, by = (ny + rows - 1) / rows;
   const long long cols = (long long)bx * by;
@@ -433,7 +434,7 @@ bool make_map(CUtensorMap* m, void* base, lbm_precision prec, const DevParams& P
 }
 
 bool make_maps(lbm_domain* d) {
-  const int w = bulk_box_cols((int)d->prec), rows = bulk_tile_rows((int)d->prec);
+  const int w = bulk_box_cols((int)d->prec), rows = bulk_tile_rows((int)d->prec, d->qh, d->qf);
   for (int k = 0; k < 2; ++k) {
     TMaps& t = d->maps[k];
     if (!make_map(&t.h, at(d, d->L.h[k]), d->prec, d->dp, d->qh, w, rows + 2)) return false;

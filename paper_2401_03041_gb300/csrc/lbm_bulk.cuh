@@ -109,12 +109,12 @@ __device__ __forceinline__ int rt_to27(int i) { return (Q == 15 && i >= 7) ? i +
 template <int Q>
 __device__ __forceinline__ int rt_from27(int k) { return (Q == 15 && k >= 19) ? k - 12 : k; }
 
-template <class S>
+template <class S, int TYB_ = 4>
 struct BulkGeom {
   static constexpr int GXP = 16 / (int)sizeof(S);       // halo columns on each side (= ghost width)
   static constexpr int TXB = sizeof(S) == 8 ? 32 : 64;  // columns per CTA
   static constexpr int W = TXB + 2 * GXP;               // staged row length (elements)
-  static constexpr int TYB = 4;                         // rows per CTA
+  static constexpr int TYB = TYB_;                      // rows per CTA
   static constexpr int HXB = TXB + 2;                   // phi/T plane pitch
   static constexpr int HYB = TYB + 2;
   static constexpr int HPB = HXB * HYB;
@@ -125,10 +125,10 @@ struct BulkGeom {
   static constexpr int GB = (int)(((size_t)W * TYB * sizeof(S) + 127) / 128 * 128 / sizeof(S));
 };
 
-template <class S, int QH, int QF>
-struct BulkSmem {
+template <class S, int QH, int QF, int TYB_>
+struct BulkSmemT {
   using R = typename Store<S>::R;
-  using G = BulkGeom<S>;
+  using G = BulkGeom<S, TYB_>;
   static constexpr int NHF = QH + QF;
   static constexpr size_t hf_stage = (size_t)NHF * G::HFB;   // elements
   static constexpr size_t g_stage = (size_t)27 * G::GB;
@@ -156,6 +156,11 @@ struct BulkSmem {
   static constexpr uint32_t g_tx = (uint32_t)((size_t)27 * G::W * G::TYB * sizeof(S));
 };
 
+// Tiles of four rows where that layout fits in 227 KB of shared memory, else
+// of two rows (large thermal stencils, h on D3Q27): half the cells per CTA.
+template <class S, int QH, int QF>
+using BulkSmem = BulkSmemT<S, QH, QF, (BulkSmemT<S, QH, QF, 4>::bytes <= 232448 ? 4 : 2)>;
+
 // Issue the boxes of one stage.  Box issue is spread over the warps (lane j
 // of warp w issues direction w + j * nwarps): box issues by lanes of one warp
 // serialise, so a single warp issuing every box would stall the whole CTA.
@@ -163,12 +168,11 @@ struct BulkSmem {
 //                h (map mh), QH..QH+QF-1 from f (map mf).
 //   KIND 1 (G):  rows y0 .. y0 + TYB - 1 of plane p; g directions (map mg).
 // Tensor coordinates are those of the padded arrays: (x + GX, y + GY, z, q).
-template <class S, int QH, int QF, int KIND>
+template <class S, class G, int QH, int QF, int KIND>
 __device__ __forceinline__ void issue_stage(const DevParams& P, const CUtensorMap* mh,
                                             const CUtensorMap* mg, const CUtensorMap* mf,
                                             S* dst_stage, uint64_t* bar, int p, int x0, int y0,
-                                            int tid, int nwarps = BulkGeom<S>::NTHR / 32) {
-  using G = BulkGeom<S>;
+                                            int tid, int nwarps = G::NTHR / 32) {
   constexpr int ndir = KIND == 0 ? QH + QF : 27;
   const int d = (tid >> 5) + (tid & 31) * nwarps;
   if (d >= ndir) return;
@@ -210,14 +214,14 @@ __device__ __forceinline__ void issue_stage(const DevParams& P, const CUtensorMa
 }
 
 template <class S, int QH, int QF>
-__global__ void __launch_bounds__(BulkGeom<S>::NTHR, 1)
+__global__ void __launch_bounds__(BulkSmem<S, QH, QF>::G::NTHR, 1)
 step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
                  const __grid_constant__ CUtensorMap mh, const __grid_constant__ CUtensorMap mg,
                  const __grid_constant__ CUtensorMap mf, int zchunk, int mode) {
   using R = typename Store<S>::R;
   const auto& rp = RP<R>(P);
-  using G = BulkGeom<S>;
   using L = BulkSmem<S, QH, QF>;
+  using G = typename L::G;
   constexpr int NC = G::NT;       // cells per CTA
   constexpr int NT = G::NTHR;     // threads per CTA
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -354,10 +358,10 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     }
     __syncthreads();
     for (int p = z0 - 1; p <= z0 + 1; ++p) {
-      issue_stage<S, QH, QF, 0>(P, &mh, &mg, &mf, hf_ptr(p), &bar[hf_slot(p)], p, x0, y0, tid);
+      issue_stage<S, G, QH, QF, 0>(P, &mh, &mg, &mf, hf_ptr(p), &bar[hf_slot(p)], p, x0, y0, tid);
       mark(hf_slot(p), hf_par(p));
     }
-    issue_stage<S, QH, QF, 1>(P, &mh, &mg, &mf, g_ptr(z0), &bar[3 + g_slot(z0)], z0, x0, y0, tid);
+    issue_stage<S, G, QH, QF, 1>(P, &mh, &mg, &mf, g_ptr(z0), &bar[3 + g_slot(z0)], z0, x0, y0, tid);
     mark(3 + g_slot(z0), g_par(z0));
     ok = ok && wait_slot(hf_slot(z0 - 1), hf_par(z0 - 1));
     if (ok) sum_plane(z0 - 1);
@@ -372,11 +376,11 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
   for (int z = z0; z < z1 && ok; ++z) {
     // slots of HF(z - 1) and G(z - 1) are free: refill them
     if (z + 2 <= z1) {
-      issue_stage<S, QH, QF, 0>(P, &mh, &mg, &mf, hf_ptr(z + 2), &bar[hf_slot(z + 2)], z + 2, x0, y0, tid);
+      issue_stage<S, G, QH, QF, 0>(P, &mh, &mg, &mf, hf_ptr(z + 2), &bar[hf_slot(z + 2)], z + 2, x0, y0, tid);
       mark(hf_slot(z + 2), hf_par(z + 2));
     }
     if (GR == 2 && z + 1 < z1) {
-      issue_stage<S, QH, QF, 1>(P, &mh, &mg, &mf, g_ptr(z + 1), &bar[3 + g_slot(z + 1)], z + 1, x0, y0, tid);
+      issue_stage<S, G, QH, QF, 1>(P, &mh, &mg, &mf, g_ptr(z + 1), &bar[3 + g_slot(z + 1)], z + 1, x0, y0, tid);
       mark(3 + g_slot(z + 1), g_par(z + 1));
     }
     ok = ok && wait_slot(hf_slot(z + 1), hf_par(z + 1));
@@ -419,7 +423,7 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
               if (tid < 32) {
                 if (tid == 0) mbar_expect_tx(&bar[3 + g_slot(z + 1)], g_bytes);
                 __syncwarp();
-                issue_stage<S, QH, QF, 1>(P, &mh, &mg, &mf, g_ptr(z + 1), &bar[3 + g_slot(z + 1)], z + 1, x0,
+                issue_stage<S, G, QH, QF, 1>(P, &mh, &mg, &mf, g_ptr(z + 1), &bar[3 + g_slot(z + 1)], z + 1, x0,
                                           y0, tid, 1);
               }
               mark(3 + g_slot(z + 1), g_par(z + 1));

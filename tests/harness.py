@@ -98,20 +98,23 @@ def ragged_workload(thermal="D3Q7", q_phase=15, walls=True, precision="fp64", sh
 
 
 def bulk_fits(precision, q_phase, thermal):
-    """Whether the bulk kernel's shared memory (three h/f box stages, two g
-    stages, phi/T planes) fits for this combination."""
+    """Whether one of the bulk kernel's shared-memory layouts (three h/f box
+    stages, one or two g stages, (phi, T) planes, the role exchange) fits in
+    227 KB for this combination: tiles of four rows, else of two."""
     qf = int(thermal[3:]) if thermal.startswith("D3Q") else 0
     nhf = q_phase + qf
     s = {"fp64": 8, "fp32": 4, "fp16": 2}[precision]
-    rows = 4
     cols = 32 if s == 8 else 64
     W = cols + 2 * (16 // s)
     rs = 8 if s == 8 else 4
-    hfb = -(-W * (rows + 2) * s // 128) * 128
-    gb = -(-W * rows * s // 128) * 128
-    fixed = 3 * nhf * hfb + 6 * (cols + 2) * (rows + 2) * rs + 13 * cols * rows * rs + 64 + 128
-    ring = 2 if fixed + 2 * 27 * gb <= 232448 else 1      # g ring of two stages, else one
-    return fixed + ring * 27 * gb <= 232448
+    for rows in (4, 2):
+        hfb = -(-W * (rows + 2) * s // 128) * 128
+        gb = -(-W * rows * s // 128) * 128
+        fixed = 3 * nhf * hfb + 6 * (cols + 2) * (rows + 2) * rs + 13 * cols * rows * rs + 64 + 128
+        ring = 2 if fixed + 2 * 27 * gb <= 232448 else 1      # g ring of two stages, else one
+        if fixed + ring * 27 * gb <= 232448:
+            return True
+    return False
 
 
 def oracle_for(w):
