@@ -210,7 +210,12 @@ lbm_status lbm_synchronize(lbm_domain* dom, int timeout_ms);
  * the generic kernel; info[1..3] = grid x, y, z; info[4] = planes per CTA;
  * info[5] = dynamic shared memory bytes.  info holds 6 int32 values.  The
  * environment variable LBM_KERNEL=generic, read at creation, forces the
- * generic kernel; LBM_ZCHUNK=<planes> sets the planes per CTA. */
+ * generic kernel; LBM_ZCHUNK=<planes> sets the planes per CTA.
+ * LBM_TEST_STALL=1, read at creation, tests failure detection: the bulk
+ * kernel's first copy wait of every CTA then runs out (after about 2 s per
+ * wait, no fault), the kernel raises the domain's error flag and returns, and
+ * the next call that synchronises (lbm_synchronize, lbm_get_diagnostics, ...)
+ * returns LBM_ERR_TIMEOUT, which then sticks to the domain. */
 lbm_status lbm_kernel_info(lbm_domain* dom, int32_t* info);
 
 /* Gradient of a droplet-capture objective with respect to the heater-patch

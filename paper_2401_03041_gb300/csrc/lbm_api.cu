@@ -179,6 +179,7 @@ struct lbm_domain {
   lbm_status sticky;
   std::string sticky_msg;
   TMaps maps[2];  // tensor maps of PDF set 0 / 1 (bulk kernel)
+  int test_stall = 0;  // LBM_TEST_STALL at creation
   // MODE_SAVE target of the next passes (FP64 adjoint; [SAVE_N][N] doubles)
   double* save_ptr = nullptr;
   // step-kernel timing (lbm_profile_steps): event pairs around each launch
@@ -387,6 +388,7 @@ void refresh_devparams(lbm_domain* d) {
   q.GX = pd.GX; q.GY = pd.GY; q.NXP = pd.NXP; q.NYP = pd.NYP; q.Np = (long long)pd.Np;
   q.walls = p.walls_z ? 1 : 0;
   q.rk_iso = p.rk_isotropic_fd ? 1 : 0;
+  q.test_stall = d->test_stall;
   fill_real(q.pd, p, d->prec);
   fill_real(q.pf, p, d->prec);
 }
@@ -497,6 +499,7 @@ lbm_status lbm_create_domain(int nx, int ny, int nz, lbm_precision prec, lbm_the
   d->L = L;
   d->geo = geometry(nx, ny, nz, prec, q_phase, thermal_q(thermal));
   d->sticky = LBM_OK;
+  if (const char* env = std::getenv("LBM_TEST_STALL")) d->test_stall = std::atoi(env) != 0;
   lbm_default_params(&d->params);
   if (workspace) {
     d->ws = (char*)workspace;

@@ -353,7 +353,10 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     // prologue: HF(z0-1), HF(z0), HF(z0+1), G(z0) now; HF(z0+2), G(z0+1) at
     // the start of the first iteration
     if (tid == 0) {
-      for (int p = z0 - 1; p <= z0 + 1; ++p) mbar_expect_tx(&bar[hf_slot(p)], hf_bytes);
+      // (test of the timeout path: 16 bytes more than the copies deliver, so
+      // the first stage never completes and its bounded wait runs out)
+      for (int p = z0 - 1; p <= z0 + 1; ++p)
+        mbar_expect_tx(&bar[hf_slot(p)], hf_bytes + (P.test_stall && p == z0 - 1 ? 16u : 0u));
       mbar_expect_tx(&bar[3 + g_slot(z0)], g_bytes);
     }
     __syncthreads();

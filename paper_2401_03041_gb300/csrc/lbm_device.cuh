@@ -131,6 +131,7 @@ struct DevParams {
   int NXP, NYP, GX, GY;
   long long Np;
   int rk_iso;
+  int test_stall;  // test of the timeout path: the bulk kernel's first copy wait runs out
   int nsrc;
   int npatch, patch_z, patch_sx, patch_sy;
   int px0[kMaxPatches], py0[kMaxPatches];
