@@ -10,7 +10,7 @@
 
 namespace lbm {
 
-// use_bulk: the bulk-copy kernel (grid of TX x BulkGeom<S>::TYB tiles) if
+// use_bulk: the bulk kernel (tensor-TMA staging; tiles of BulkSmem<S, QH, QF>::G) if
 // its shared memory fits, else the generic kernel (TX x TY tiles).
 // Tensor maps of the current source PDF buffers (bulk kernel only).
 struct TMaps {

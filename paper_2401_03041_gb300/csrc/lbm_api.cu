@@ -57,12 +57,12 @@ struct Geometry {
   dim3 grid;
   int zchunk;
   int nblocks;
-  int bulk;  // 1: bulk-copy kernel, 0: generic kernel
+  int bulk;  // 1: bulk kernel (tensor-TMA staging), 0: generic kernel
 };
 
 int thermal_q(lbm_thermal th);
 
-// The bulk-copy kernel needs 16-byte aligned rows, rows at least one staged
+// The bulk kernel needs 16-byte aligned rows, rows at least one staged
 // row long, at least two tiles of rows, and shared memory that fits.
 bool bulk_ok(int nx, int ny, lbm_precision prec, int qh, int qf) {
   const char* env = std::getenv("LBM_KERNEL");

@@ -1,5 +1,5 @@
 // lbm_cell.cuh - the per-cell part of one time step (a4-a9 of the sweep),
-// shared by the generic and the bulk-copy step kernels.
+// shared by the generic and the bulk step kernels.
 //
 // Inputs: the zeroth moments phi and T of the pulled PDFs, their finite
 // differences (isotropic D3Q27 gradient and Laplacian), the RK stencil values,

@@ -7,7 +7,7 @@
 // are zeroth moments of *pulled* PDFs, so the CTA recomputes them for every
 // (TX+2) x (TY+2) plane it meets and keeps three planes (z-1, z, z+1) in
 // shared memory.  PDFs are read straight from global memory with periodic
-// wrap and wall rules.  The bulk-copy kernel (lbm_bulk.cuh) is the fast path;
+// wrap and wall rules.  The bulk kernel (lbm_bulk.cuh) is the fast path;
 // this one serves lattices that path does not cover and is its cross-check.
 #pragma once
 

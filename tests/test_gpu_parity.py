@@ -73,7 +73,7 @@ def _kernels(precision, q_phase, thermal):
 def test_ragged_walls_fp64(thermal, q_phase):
     """40 x 20 x 13 (ragged against both kernels' tiles), walls, heaters, two
     moving droplets, every energy solver and both phase-field stencils, on
-    the generic kernel and (where its shared memory fits) the bulk-copy one."""
+    the generic kernel and on the bulk (tensor-TMA) one."""
     w = ragged_workload(thermal, q_phase, walls=True)
     o = oracle_for(w)
     o.step(12)
