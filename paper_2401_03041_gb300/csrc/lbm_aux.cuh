@@ -97,7 +97,8 @@ __global__ void rk_stage_kernel(const DevParams P, const RF* __restrict__ psi, R
 }
 
 // Initial state: tanh droplets (periodic minimum image), u = sum phi_k v_k,
-// conduction profile between walls; equilibria of Sec. 2.2 evaluated in FP64.
+// conduction profile between walls, all in FP64; the equilibria of Sec. 2.2
+// are then evaluated in the compute type of the storage (FP64 in FP64 mode).
 //
 // A block covers a 32 x 4 x 2 tile of cells.  Before the per-cell loop it
 // culls the droplet table against the tile's bounding box: droplet k matters
@@ -116,7 +117,7 @@ init_kernel(const DevParams P, const double* __restrict__ drops, int nd, S* h, S
             typename Store<S>::R* Tfield) {
   using R = typename Store<S>::R;
   constexpr int NT = kInitTX * kInitTY * kInitTZ;
-  const auto& rp = P.pd;  // initialisation runs in FP64 in every mode
+  const auto& rp = P.pd;  // droplet profiles and velocities in FP64 in every mode
   __shared__ uint32_t mask[32];
   const int tid = threadIdx.x;
   const int x = blockIdx.x * kInitTX + (tid % kInitTX);
@@ -180,25 +181,30 @@ init_kernel(const DevParams P, const double* __restrict__ drops, int nd, S* h, S
   const double T0 = P.walls ? rp.T_bottom + (rp.T_top - rp.T_bottom) * (z + 0.5) / P.nz : 0.0;
   const size_t pc = pdf_index(P, x, y, z);
   const size_t np = (size_t)P.Np;
-  const double uu = ux * ux + uy * uy + uz * uz;
+  // equilibria in the compute type of the storage (FP64 in FP64 mode)
+  const auto& rq = RP<R>(P);
+  const R phR = (R)phi, TR = (R)T0, uxR = (R)ux, uyR = (R)uy, uzR = (R)uz;
+  const R uu = uxR * uxR + uyR * uyR + uzR * uzR;
 #pragma unroll
   for (int i = 0; i < QH; ++i) {
-    const double cu = cx<QH>(i) * ux + cy<QH>(i) * uy + cz<QH>(i) * uz;
-    const double e = weight<QH>(i) * phi * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-    Store<S>::st(h + (size_t)i * np + pc, (R)(e - weight<QH>(i) * rp.shift_h));
+    const R cu = (R)cx<QH>(i) * uxR + (R)cy<QH>(i) * uyR + (R)cz<QH>(i) * uzR;
+    const R w = (R)weight<QH>(i);
+    const R e = w * phR * ((R)1 + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu);
+    Store<S>::st(h + (size_t)i * np + pc, e - w * (R)rq.shift_h);
   }
 #pragma unroll
   for (int i = 0; i < 27; ++i) {
-    const double cu = cx<27>(i) * ux + cy<27>(i) * uy + cz<27>(i) * uz;
-    const double e = weight<27>(i) * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-    Store<S>::st(g + (size_t)i * np + pc, (R)e);
+    const R cu = (R)cx<27>(i) * uxR + (R)cy<27>(i) * uyR + (R)cz<27>(i) * uzR;
+    const R e = (R)weight<27>(i) * ((R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu);
+    Store<S>::st(g + (size_t)i * np + pc, e);
   }
   if constexpr (QF > 0) {
 #pragma unroll
     for (int i = 0; i < QF; ++i) {
-      const double cu = cx<QF>(i) * ux + cy<QF>(i) * uy + cz<QF>(i) * uz;
-      const double e = weight<QF>(i) * T0 * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-      Store<S>::st(f + (size_t)i * np + pc, (R)(e - weight<QF>(i) * rp.shift_f));
+      const R cu = (R)cx<QF>(i) * uxR + (R)cy<QF>(i) * uyR + (R)cz<QF>(i) * uzR;
+      const R w = (R)weight<QF>(i);
+      const R e = w * TR * ((R)1 + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu);
+      Store<S>::st(f + (size_t)i * np + pc, e - w * (R)rq.shift_f);
     }
   } else {
     Tfield[cell] = (R)T0;
