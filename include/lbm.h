@@ -198,6 +198,22 @@ lbm_status lbm_get_pdfs(lbm_domain* dom, int which, double* dst_host);
  * lbm_get_pdfs; shifted and rounded to the storage precision). */
 lbm_status lbm_set_pdfs(lbm_domain* dom, int which, const double* src_host);
 
+/* Checkpoint / resume (the paper describes none; a utility of the library).
+ * lbm_state_bytes: bytes of a saved state of this domain (a header naming
+ * the domain's sizes, precision, stencils and time level; the current PDF set
+ * in its stored form, ghost cells included; for the RK energy solvers the T
+ * field); 0 for a null domain.
+ * lbm_save_state: copies the current state to host memory (host_buf, at
+ * least lbm_state_bytes bytes, owned by the caller).  Synchronises.
+ * LBM_ERR_ARG (null or short buffer), LBM_ERR_STATE (not initialised).
+ * lbm_load_state: restores a state saved from a domain of the same sizes,
+ * precision, thermal solver and phase-field stencil, including its time
+ * level; the next step continues exactly as the saved run would have.
+ * Synchronises.  LBM_ERR_ARG if the buffer is not such a state. */
+size_t lbm_state_bytes(lbm_domain* dom);
+lbm_status lbm_save_state(lbm_domain* dom, void* host_buf, size_t bytes);
+lbm_status lbm_load_state(lbm_domain* dom, const void* host_buf, size_t bytes);
+
 /* Current time level (number of steps since lbm_init_droplets). */
 lbm_status lbm_get_level(lbm_domain* dom, int64_t* level);
 

@@ -211,6 +211,8 @@ lbm_status usable(lbm_domain* d) {
 }
 
 void* at(lbm_domain* d, size_t off) { return d->ws + off; }
+// the current PDF set ([h | g | f], padded, storage precision)
+char* cur_set_ptr(lbm_domain* d) { return d->ws + d->L.h[d->cur]; }
 
 // ----------------------------------------------------------------- dispatch
 template <class S>
@@ -805,6 +807,92 @@ lbm_status lbm_set_pdfs(lbm_domain* d, int which, const double* src_host) {
   lbm_status s = pdf_io(d, which, const_cast<double*>(src_host), false);
   if (s == LBM_OK) d->inited = true;
   return s;
+}
+
+// ---------------------------------------------------------------- checkpoint
+
+}  // extern "C"
+
+namespace {
+
+// Header of a saved state: the domain description it belongs to.
+struct StateHeader {
+  char magic[8];
+  int32_t version, nx, ny, nz, prec, thermal, q_phase, pad_;
+  int64_t level;
+  uint64_t pdf_bytes, field_bytes;
+};
+constexpr char kStateMagic[8] = {'L', 'B', 'M', 'S', 'T', 'A', 'T', 'E'};
+
+size_t state_pdf_bytes(const lbm_domain* d) {
+  return (size_t)(d->qh + 27 + d->qf) * (size_t)d->dp.Np * store_bytes(d->prec);
+}
+size_t state_field_bytes(const lbm_domain* d) {
+  return d->qf == 0 ? (size_t)d->N * field_bytes(d->prec) : 0;   // T of the RK solvers
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_state_bytes(lbm_domain* d) {
+  if (!d) return 0;
+  return sizeof(StateHeader) + state_pdf_bytes(d) + state_field_bytes(d);
+}
+
+lbm_status lbm_save_state(lbm_domain* d, void* host_buf, size_t bytes) {
+  lbm_status s = usable(d);
+  if (s != LBM_OK) return s;
+  if (!host_buf) return fail(LBM_ERR_ARG, "buffer is null");
+  if (bytes < lbm_state_bytes(d)) return fail(LBM_ERR_ARG, "buffer smaller than lbm_state_bytes");
+  if (!d->inited) return fail(LBM_ERR_STATE, "domain not initialised");
+  StateHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, kStateMagic, 8);
+  h.version = 1;
+  h.nx = d->nx; h.ny = d->ny; h.nz = d->nz;
+  h.prec = (int32_t)d->prec; h.thermal = (int32_t)d->th; h.q_phase = d->qh;
+  h.level = d->level;
+  h.pdf_bytes = state_pdf_bytes(d);
+  h.field_bytes = state_field_bytes(d);
+  char* out = (char*)host_buf;
+  std::memcpy(out, &h, sizeof(h));
+  s = check_cuda(d, cudaMemcpyAsync(out + sizeof(h), cur_set_ptr(d), h.pdf_bytes, cudaMemcpyDeviceToHost,
+                                    d->stream), "state copy");
+  if (s == LBM_OK && h.field_bytes)
+    s = check_cuda(d, cudaMemcpyAsync(out + sizeof(h) + h.pdf_bytes, at(d, d->L.T), h.field_bytes,
+                                      cudaMemcpyDeviceToHost, d->stream), "state field copy");
+  if (s == LBM_OK) s = check_cuda(d, cudaStreamSynchronize(d->stream), "state sync");
+  return s;
+}
+
+lbm_status lbm_load_state(lbm_domain* d, const void* host_buf, size_t bytes) {
+  lbm_status s = usable(d);
+  if (s != LBM_OK) return s;
+  if (!host_buf) return fail(LBM_ERR_ARG, "buffer is null");
+  if (bytes < sizeof(StateHeader)) return fail(LBM_ERR_ARG, "buffer too small for a state header");
+  StateHeader h;
+  std::memcpy(&h, host_buf, sizeof(h));
+  if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 1)
+    return fail(LBM_ERR_ARG, "not a saved state (bad magic or version)");
+  if (h.nx != d->nx || h.ny != d->ny || h.nz != d->nz || h.prec != (int32_t)d->prec ||
+      h.thermal != (int32_t)d->th || h.q_phase != d->qh)
+    return fail(LBM_ERR_ARG, "saved state belongs to a domain of another size, precision or stencil");
+  if (h.pdf_bytes != state_pdf_bytes(d) || h.field_bytes != state_field_bytes(d) ||
+      bytes < lbm_state_bytes(d))
+    return fail(LBM_ERR_ARG, "saved state has an unexpected size");
+  const char* in = (const char*)host_buf;
+  s = check_cuda(d, cudaMemcpyAsync(cur_set_ptr(d), in + sizeof(h), h.pdf_bytes, cudaMemcpyHostToDevice,
+                                    d->stream), "state copy");
+  if (s == LBM_OK && h.field_bytes)
+    s = check_cuda(d, cudaMemcpyAsync(at(d, d->L.T), in + sizeof(h) + h.pdf_bytes, h.field_bytes,
+                                      cudaMemcpyHostToDevice, d->stream), "state field copy");
+  // pageable source: complete before returning
+  if (s == LBM_OK) s = check_cuda(d, cudaStreamSynchronize(d->stream), "state sync");
+  if (s != LBM_OK) return s;
+  d->level = h.level;
+  d->inited = true;
+  return LBM_OK;
 }
 
 lbm_status lbm_get_level(lbm_domain* d, int64_t* level) {

@@ -29,6 +29,7 @@ SYMBOLS = ("lbm_default_params", "lbm_workspace_bytes", "lbm_create_domain",
            "lbm_get_pdfs", "lbm_set_pdfs", "lbm_get_level", "lbm_synchronize",
            "lbm_stencil", "lbm_kernel_info", "lbm_profile_steps", "lbm_profile_read",
            "lbm_field_moments", "lbm_adjoint_run", "lbm_adjoint_step",
+           "lbm_state_bytes", "lbm_save_state", "lbm_load_state",
            "lbm_last_error", "lbm_version")
 
 
@@ -119,6 +120,9 @@ def lib():
         "lbm_field_moments": (c_int, [vp, c_int, c_int, c_int, c_int, vp, P(c_dbl)]),
         "lbm_adjoint_run": (c_int, [vp, c_int, c_int, P(c_dbl), c_dbl, P(c_dbl), P(c_dbl)]),
         "lbm_adjoint_step": (c_int, [vp, vp, vp, c_dbl]),
+        "lbm_state_bytes": (sz, [vp]),
+        "lbm_save_state": (c_int, [vp, vp, sz]),
+        "lbm_load_state": (c_int, [vp, vp, sz]),
         "lbm_last_error": (ctypes.c_char_p, []),
         "lbm_version": (ctypes.c_char_p, []),
     }
@@ -315,6 +319,18 @@ class Domain:
                                                           ctypes.c_void_p(out.ctypes.data),
                                                           float(normal_cap)))
         return out
+
+    def save_state(self) -> bytes:
+        """The current state (PDFs, RK temperature, time level) as bytes."""
+        n = lib().lbm_state_bytes(self._h)
+        buf = ctypes.create_string_buffer(n)
+        _check("lbm_save_state", lib().lbm_save_state(self._h, buf, n))
+        return buf.raw
+
+    def load_state(self, state: bytes):
+        """Restore a state returned by save_state of a domain of the same kind."""
+        buf = ctypes.create_string_buffer(bytes(state), len(state))
+        _check("lbm_load_state", lib().lbm_load_state(self._h, buf, len(state)))
 
     def profile_steps(self, enable: bool = True):
         """Bracket each step-kernel launch with CUDA events on the domain's stream."""
