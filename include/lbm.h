@@ -160,6 +160,19 @@ lbm_status lbm_set_heater_patches(lbm_domain* dom, int z, int sx, int sy, int n,
                                   const int32_t* x0, const int32_t* y0,
                                   const double* intensity);
 
+/* Add a caller-given heat-source density field to q_T (the source term of
+ * the temperature equation, Sec. 2.3), on top of the Gaussian sources and the
+ * heater patches.  q_dev is a dense [nz][ny][nx] array (x fastest) in device
+ * memory of the current device, of type double (dtype LBM_FP64) or float
+ * (LBM_FP32), aligned to its element size.  It is NOT copied: the caller owns
+ * it and keeps it alive and unchanged while steps that read it are in flight
+ * (every later lbm_step / lbm_step_diagnostics / lbm_adjoint_run reads it).
+ * NULL removes the field.  The source does not depend on the state, so the
+ * adjoint of the state is unchanged by it.
+ * Errors: LBM_ERR_ARG for a bad dtype, a misaligned, host or other-device
+ * pointer; a domain's sticky error is returned again. */
+lbm_status lbm_set_heater_field(lbm_domain* dom, const void* q_dev, int dtype);
+
 /* Initialise the state from n droplets (0 <= n <= LBM_MAX_DROPLETS, host
  * array): phi = max_k phi_k (periodic minimum-image distances), u = sum_k phi_k v_k,
  * T = linear conduction profile between the walls (walls_z) else 0;

@@ -248,6 +248,12 @@ class OracleLBM:
                 q = q + np.where(m, I, 0.0)
         return q
 
+    def add_heat_field(self, q):
+        """A given per-cell heat-source density (dense [z][y][x]) added to the
+        source q_T of the energy equation (Sec. 2.3), on top of the Gaussian
+        sources and heater patches."""
+        self.q = self.q + np.asarray(q, dtype=np.float64).reshape(self.nz, self.ny, self.nx)
+
     def init_droplets(self, droplets: Iterable):
         """Initial state: phi = max_k tanh profiles (Sec. 3.1 initial profile,
         phi0 + (phiH - phiL)/2 tanh(r/(xi/2))), u = sum_k phi_k v_k,

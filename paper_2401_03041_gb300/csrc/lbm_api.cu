@@ -619,6 +619,34 @@ lbm_status lbm_set_heater_patches(lbm_domain* d, int z, int sx, int sy, int n, c
   return LBM_OK;
 }
 
+lbm_status lbm_set_heater_field(lbm_domain* d, const void* q_dev, int dtype) {
+  lbm_status s = usable(d);
+  if (s != LBM_OK) return s;
+  if (!q_dev) {
+    d->dp.qfield = nullptr;
+    d->dp.qfield_f32 = 0;
+    return LBM_OK;
+  }
+  if (dtype != LBM_FP64 && dtype != LBM_FP32) return fail(LBM_ERR_ARG, "heater field dtype must be LBM_FP64 or LBM_FP32");
+  const size_t esz = dtype == LBM_FP64 ? sizeof(double) : sizeof(float);
+  if (reinterpret_cast<uintptr_t>(q_dev) % esz != 0) return fail(LBM_ERR_ARG, "heater field is not aligned to its element size");
+  cudaPointerAttributes a{};
+  cudaError_t e = cudaPointerGetAttributes(&a, q_dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LBM_ERR_ARG, std::string("heater field is not a device pointer: ") + cudaGetErrorString(e));
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+    return fail(LBM_ERR_ARG, "heater field is not device memory");
+  int dev = -1;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return check_cuda(d, e, "cudaGetDevice");
+  if (a.device != dev) return fail(LBM_ERR_ARG, "heater field lives on another device");
+  d->dp.qfield = q_dev;
+  d->dp.qfield_f32 = dtype == LBM_FP32 ? 1 : 0;
+  return LBM_OK;
+}
+
 lbm_status lbm_init_droplets(lbm_domain* d, int n, const lbm_droplet* drops) {
   lbm_status s = usable(d);
   if (s != LBM_OK) return s;

@@ -38,7 +38,8 @@ __device__ __forceinline__ size_t pdf_index(const DevParams& P, int x, int y, in
 }
 
 // Heat source density q_T at cell (x, y, z) (centre (x+1/2, y+1/2, z+1/2)):
-// Gaussian sources (Eq. HeatSource, r <= d) plus heater patches (by index).
+// Gaussian sources (Eq. HeatSource, r <= d) plus heater patches (by index)
+// plus the caller's per-cell heater field.
 template <class R>
 __device__ __forceinline__ R heat_source(const DevParams& P, int x, int y, int z) {
   const auto& rp = RP<R>(P);
@@ -56,6 +57,11 @@ __device__ __forceinline__ R heat_source(const DevParams& P, int x, int y, int z
       if (x >= P.px0[k] && x < P.px0[k] + P.patch_sx && y >= P.py0[k] && y < P.py0[k] + P.patch_sy)
         q += (R)rp.pI[k];
     }
+  }
+  if (P.qfield) {
+    const size_t c = cell_index(P, x, y, z);
+    q += P.qfield_f32 ? (R)__ldg(static_cast<const float*>(P.qfield) + c)
+                      : (R)__ldg(static_cast<const double*>(P.qfield) + c);
   }
   return q;
 }

@@ -132,6 +132,8 @@ struct DevParams {
   long long Np;
   int rk_iso;
   int test_stall;  // test of the timeout path: the bulk kernel's first copy wait runs out
+  int qfield_f32;  // element type of qfield: 0 double, 1 float
+  const void* qfield;  // caller-owned dense [z][y][x] heat-source density, or null
   int nsrc;
   int npatch, patch_z, patch_sx, patch_sy;
   int px0[kMaxPatches], py0[kMaxPatches];

@@ -24,7 +24,7 @@ FIELD_PHI, FIELD_U, FIELD_P, FIELD_T = 1, 2, 4, 8
 # Every symbol include/lbm.h declares.
 SYMBOLS = ("lbm_default_params", "lbm_workspace_bytes", "lbm_create_domain",
            "lbm_destroy_domain", "lbm_set_params", "lbm_set_heat_sources",
-           "lbm_set_heater_patches", "lbm_init_droplets", "lbm_step",
+           "lbm_set_heater_patches", "lbm_set_heater_field", "lbm_init_droplets", "lbm_step",
            "lbm_step_diagnostics", "lbm_get_diagnostics", "lbm_get_fields",
            "lbm_get_pdfs", "lbm_set_pdfs", "lbm_get_level", "lbm_synchronize",
            "lbm_stencil", "lbm_kernel_info", "lbm_profile_steps", "lbm_profile_read",
@@ -104,6 +104,7 @@ def lib():
         "lbm_set_heat_sources": (c_int, [vp, c_int, P(HeatSource)]),
         "lbm_set_heater_patches": (c_int, [vp, c_int, c_int, c_int, c_int, P(ctypes.c_int32),
                                            P(ctypes.c_int32), P(c_dbl)]),
+        "lbm_set_heater_field": (c_int, [vp, vp, c_int]),
         "lbm_init_droplets": (c_int, [vp, c_int, P(Droplet)]),
         "lbm_step": (c_int, [vp, c_int]),
         "lbm_step_diagnostics": (c_int, [vp, c_int, P(Diag)]),
@@ -260,6 +261,24 @@ class Domain:
         _check("lbm_set_heater_patches",
                lib().lbm_set_heater_patches(self._h, int(z), int(sx), int(sy), n, X, Y, I))
         self._npatch = n
+
+    def set_heater_field(self, q):
+        """Per-cell heat-source density added to q_T: a contiguous float64 or
+        float32 CUDA tensor of nx * ny * nz elements ([z][y][x]), or None to
+        remove it.  The domain keeps a reference, so the tensor stays alive
+        while steps read it; change it only between synchronised steps."""
+        import torch
+        if q is None:
+            _check("lbm_set_heater_field", lib().lbm_set_heater_field(self._h, None, 0))
+            self._qfield = None
+            return
+        if not q.is_cuda or not q.is_contiguous() or q.numel() != self.nx * self.ny * self.nz:
+            raise ValueError("heater field must be a contiguous CUDA tensor of nx*ny*nz elements")
+        dt = {torch.float64: 0, torch.float32: 1}.get(q.dtype)
+        if dt is None:
+            raise ValueError("heater field must be float64 or float32")
+        _check("lbm_set_heater_field", lib().lbm_set_heater_field(self._h, ctypes.c_void_p(q.data_ptr()), dt))
+        self._qfield = q
 
     def init_droplets(self, droplets: Iterable):
         ds = list(droplets)

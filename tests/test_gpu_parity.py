@@ -193,6 +193,75 @@ def test_rk_isotropic_operator_and_patches_fp64():
     compare_all(d, o, w, TOL64, "rk4 iso + patches")
 
 
+def _field_tensor(q, dtype):
+    import torch
+    return torch.tensor(np.ascontiguousarray(q).ravel(), dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("thermal,fdtype", [("D3Q7", "f64"), ("D3Q19", "f32"), ("RK4", "f32"),
+                                            ("RK2", "f64")])
+def test_heater_field_fp64(thermal, fdtype):
+    """lbm_set_heater_field: a seeded per-cell heat field (Gaussian spots plus
+    noise) on top of the Gaussian sources, FP64 state, FP64 or FP32 field (the
+    oracle gets the FP32-rounded values), generic and bulk kernels."""
+    import torch
+    w = ragged_workload(thermal, 15, walls=True)
+    q = W.heater_field(3, (w.nz, w.ny, w.nx))
+    if fdtype == "f32":
+        q = q.astype(np.float32).astype(np.float64)
+    o = oracle_for(w)
+    o.add_heat_field(q)
+    o.step(12)
+    qt = _field_tensor(q, torch.float64 if fdtype == "f64" else torch.float32)
+    for kern in _kernels("fp64", 15, thermal):
+        d = gpu_domain(w, kernel=kern)
+        d.set_heater_field(qt)
+        d.step(12)
+        compare_all(d, o, w, TOL64, f"heater field {thermal} {fdtype} {kern}")
+
+
+def test_heater_field_equals_patches_and_rejects_bad_pointers():
+    """A field holding the heater patches' values gives bit for bit the run
+    with the patches; removing the field restores the plain run; host,
+    misaligned pointers and unknown dtypes are rejected."""
+    import ctypes
+
+    import torch
+    from paper_2401_03041_gb300 import lbm
+    w = ragged_workload("D3Q7", 15, walls=True, precision="fp32", shape=(80, 24, 12))
+    pw = w.replace(patches=W.HeaterPatches(z=2, sx=9, sy=5, x0=[3, 40], y0=[2, 12],
+                                           intensity=[0.03, 0.07]))
+    box = np.zeros((w.nz, w.ny, w.nx))
+    for k in range(2):
+        box[2, pw.patches.y0[k]:pw.patches.y0[k] + 5, pw.patches.x0[k]:pw.patches.x0[k] + 9] = \
+            pw.patches.intensity[k]
+    a = gpu_domain(pw)
+    a.step(9)
+    b = gpu_domain(w)
+    b.set_heater_field(_field_tensor(box, torch.float64))
+    b.step(9)
+    fa, fb = gpu_fields(a), gpu_fields(b)
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    c = gpu_domain(w)
+    c.set_heater_field(_field_tensor(box, torch.float32))
+    c.set_heater_field(None)
+    c.step(9)
+    e = gpu_domain(w)
+    e.step(9)
+    fc, fe = gpu_fields(c), gpu_fields(e)
+    assert not np.array_equal(fa["T"], fe["T"])
+    for k in fc:
+        assert np.array_equal(fc[k], fe[k]), k
+    L = lbm.lib()
+    host = np.zeros(w.cells)
+    assert L.lbm_set_heater_field(e._h, ctypes.c_void_p(host.ctypes.data), 0) == -1
+    dev = _field_tensor(box, torch.float64)
+    assert L.lbm_set_heater_field(e._h, ctypes.c_void_p(dev.data_ptr() + 4), 0) == -1
+    assert L.lbm_set_heater_field(e._h, ctypes.c_void_p(dev.data_ptr()), 2) == -1
+    assert L.lbm_set_heater_field(e._h, ctypes.c_void_p(dev.data_ptr()), 0) == 0
+
+
 @pytest.mark.parametrize("shape", [(1, 1, 1), (3, 1, 2), (33, 9, 1), (5, 17, 3)])
 def test_tiny_and_degenerate_lattices_fp64(shape):
     nx, ny, nz = shape

@@ -312,6 +312,47 @@ def test_heat_source_integral_and_cutoff():
     assert o2.q[24, 24, 24] == Q
 
 
+def test_heat_field_layout_matches_sources_and_patches():
+    """A per-cell heat field laid out [z][y][x] (x fastest) is the same q_T
+    as the Gaussian source and the heater patch it samples, on a box whose
+    three sides differ (a transposed layout puts the heat elsewhere)."""
+    nx, ny, nz = 7, 5, 4
+    src = W.HeatSource(2.3, 3.1, 1.6, 0.01, 1.5)
+    z, y, x = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5,
+                          indexing="ij")
+    gauss = src.Q * np.exp(-2.0 * ((x - src.x) ** 2 + (y - src.y) ** 2 + (z - src.z) ** 2)
+                           / src.w ** 2)
+    a = OracleLBM(nx, ny, nz, W.Params(), 15, "D3Q7", sources=[src])
+    b = OracleLBM(nx, ny, nz, W.Params(), 15, "D3Q7")
+    b.add_heat_field(gauss.ravel())
+    assert np.allclose(a.q, b.q, rtol=1e-14, atol=0) and a.q.max() > 0
+    patches = W.HeaterPatches(z=1, sx=2, sy=3, x0=[4], y0=[1], intensity=[0.02])
+    c = OracleLBM(nx, ny, nz, W.Params(), 15, "D3Q7", patches=patches)
+    box = np.zeros(nx * ny * nz)
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                if k == 1 and 1 <= j < 4 and 4 <= i < 6:
+                    box[(k * ny + j) * nx + i] = 0.02
+    e = OracleLBM(nx, ny, nz, W.Params(), 15, "D3Q7")
+    e.add_heat_field(box)
+    assert np.array_equal(c.q, e.q)
+
+
+@pytest.mark.parametrize("thermal", ["D3Q7", "D3Q19", "RK2", "RK4"])
+def test_heat_field_total_heat_grows_by_its_sum(thermal):
+    """Periodic box at rest: streaming and the periodic difference operators
+    conserve sum T, so n steps with a heat field q add exactly n * sum q."""
+    o = make(6, 5, 4, thermal=thermal)
+    set_fields(o, 0.0, T=0.0)
+    q = W.heater_field(9, (4, 5, 6))
+    o.add_heat_field(q)
+    o.step(5)
+    T = o.macro()["T"]
+    assert abs(T.sum() / (5 * q.sum()) - 1) < 1e-12
+    assert np.abs(T).max() < 5 * q.max()        # diffusion spread the spots
+
+
 @pytest.mark.parametrize("thermal", ["D3Q7", "RK2", "RK4"])
 def test_background_gradient_advection_source(thermal):
     """T_total = T + G.(x - x0): a uniform flow U across the imposed gradient

@@ -255,3 +255,20 @@ def crop(w: Workload, nx: int, ny: int, nz: int) -> Workload:
 def random_state(seed: int, shape, scale: float = 1.0) -> np.ndarray:
     """Seeded FP64 noise (used to perturb PDFs in parity tests)."""
     return _rng(seed).standard_normal(shape) * scale
+
+
+def heater_field(seed: int, shape, peak: float = 2e-3) -> np.ndarray:
+    """Seeded per-cell heat-source density, dense [z][y][x] FP64: a few
+    randomly placed Gaussian spots of random width (the shape of laser
+    heating) plus uniform background noise of 1 % of the peak."""
+    rng = _rng(seed)
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5,
+                          indexing="ij")
+    q = 0.01 * peak * rng.uniform(0.0, 1.0, shape)
+    for _ in range(3):
+        c = rng.uniform(0.0, 1.0, 3) * np.array([nx, ny, nz])
+        w = float(rng.uniform(2.0, 6.0))
+        q += peak * float(rng.uniform(0.3, 1.0)) * np.exp(
+            -2.0 * ((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2) / (w * w))
+    return q
