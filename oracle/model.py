@@ -221,9 +221,15 @@ class OracleLBM:
         self.NX, self.NY, self.NZ = global_shape if global_shape else (nx, ny, nz)
         ox, oy, oz = origin
         # integer cell indices and cell-centre coordinates (cell k at k + 1/2;
-        # walls, when present, are the box faces z = 0 and z = NZ)
-        Zi, Yi, Xi = np.meshgrid(np.arange(nz) + oz, np.arange(ny) + oy,
-                                 np.arange(nx) + ox, indexing="ij")
+        # walls, when present, are the box faces z = 0 and z = NZ).  Along a
+        # periodic axis a box cell past the lattice's end is the lattice cell
+        # of index k mod N: it gets that cell's position (heat sources,
+        # patches, background gradient, first moments).
+        zk = np.arange(nz) + oz
+        if not self.walls:
+            zk = zk % self.NZ
+        Zi, Yi, Xi = np.meshgrid(zk, (np.arange(ny) + oy) % self.NY,
+                                 (np.arange(nx) + ox) % self.NX, indexing="ij")
         self.Xi, self.Yi, self.Zi = Xi, Yi, Zi
         self.X, self.Y, self.Z = Xi + 0.5, Yi + 0.5, Zi + 0.5
         self.q = self._heat_source(sources, patches)
