@@ -78,8 +78,12 @@ typedef struct {
   double mobility;         /* Allen-Cahn mobility M; omega_phi = 1 / (1/2 + M / c_s^2) */
   double xi;               /* interface width */
   double sigma_ref, sigma_T, T_ref;  /* sigma(T) = sigma_ref + sigma_T (T - T_ref) */
-  double alpha_L, alpha_H; /* thermal diffusivity kappa / (rho c_p); requires alpha_L == alpha_H;
-                              omega_T = 1 / (1/2 + alpha / c_s^2) */
+  double alpha_L, alpha_H; /* thermal diffusivity kappa / (rho c_p) of the light / heavy phase,
+                              with rho c_p = 1: alpha(phi) = alpha_L + phi (alpha_H - alpha_L)
+                              (Sec. 2.3, kappa linear in phi).  LB: per-cell rate
+                              omega_T = 1 / (1/2 + alpha(phi) / c_s^2); RK: alpha(phi) lap T
+                              + (alpha_H - alpha_L) grad phi . grad T_total.  The adjoint
+                              needs alpha_L == alpha_H. */
   double gravity[3];       /* body-force acceleration g (F_b = rho g) */
   int32_t walls_z;         /* 1: no-slip walls at both z faces, else periodic in z */
   double T_bottom, T_top;  /* wall temperatures (walls_z == 1) */
@@ -145,8 +149,8 @@ lbm_status lbm_destroy_domain(lbm_domain* dom);
 
 /* Set the model parameters (Sec. 2.1-2.3).  Copied; takes effect for the
  * next launch.  LBM_ERR_ARG for non-physical values (nu <= 0, M <= 0,
- * xi <= 0, alpha <= 0, non-finite); LBM_ERR_UNSUPPORTED for rho_L != rho_H,
- * alpha_L != alpha_H or omega_high != 1. */
+ * xi <= 0, alpha <= 0, non-finite); LBM_ERR_UNSUPPORTED for rho_L != rho_H
+ * or omega_high != 1. */
 lbm_status lbm_set_params(lbm_domain* dom, const lbm_params* p);
 
 /* Replace the Gaussian heat sources (0 <= n <= LBM_MAX_SOURCES; Eq. HeatSource,

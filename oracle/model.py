@@ -208,8 +208,6 @@ class OracleLBM:
                  global_shape=None):
         if params.rho_L != params.rho_H:
             raise NotImplementedError("density ratio != 1 (F_p, F_mu) not supported")
-        if params.alpha_L != params.alpha_H:
-            raise NotImplementedError("conductivity ratio != 1 not supported")
         self.nx, self.ny, self.nz = nx, ny, nz
         self.p = params
         self.Sh = stencil(q_phase)
@@ -408,18 +406,34 @@ class OracleLBM:
                     lphi=lphi, gT=gT, g2=g2)
 
     # ------------------------------------------------------------ RK (a9')
-    def rk_rhs(self, psi, u):
-        """R(T) = -u.grad T - u.G + alpha lap T + q_T (Eq. temperature with
-        uniform kappa, rho c_p; standard 7-point / central operators)."""
+    def alpha(self, phi):
+        """Thermal diffusivity kappa / (rho c_p) interpolated linearly in phi
+        like kappa and c_p (Sec. 2.3), with rho c_p = 1: alpha_L at phi = 0,
+        alpha_H at phi = 1."""
+        p = self.p
+        return p.alpha_L + phi * (p.alpha_H - p.alpha_L)
+
+    def rk_rhs(self, psi, u, phi):
+        """R(T) = -u.(grad T + G) + alpha(phi) lap T
+                  + (alpha_H - alpha_L) grad phi . (grad T + G) + q_T
+        (Eq. temperature with rho c_p = 1: grad kappa . grad T_total plus
+        kappa lap T, where T_total = T + G.(x - x0) and lap of the linear
+        background is zero); standard 7-point / central operators, or the
+        isotropic D3Q27 ones, for T and phi alike (phi mirrored at walls)."""
         p = self.p
         q = self._pad(psi, "dirichlet")
+        qp = self._pad(phi, "mirror")
         if p.rk_isotropic_fd:
-            gr, lp = self.grad_iso(q), self.lap_iso(q)
+            gr, lp, gp = self.grad_iso(q), self.lap_iso(q), self.grad_iso(qp)
         else:
-            gr, lp = self.grad_std(q), self.lap_std(q)
+            gr, lp, gp = self.grad_std(q), self.lap_std(q), self.grad_std(qp)
         G = p.grad_T
-        adv = u[0] * (gr[0] + G[0]) + u[1] * (gr[1] + G[1]) + u[2] * (gr[2] + G[2])
-        return -adv + p.alpha_L * lp + self.q
+        gt = [gr[k] + G[k] for k in range(3)]
+        adv = u[0] * gt[0] + u[1] * gt[1] + u[2] * gt[2]
+        cond = self.alpha(phi) * lp
+        if p.alpha_H != p.alpha_L:
+            cond = cond + (p.alpha_H - p.alpha_L) * (gp[0] * gt[0] + gp[1] * gt[1] + gp[2] * gt[2])
+        return -adv + cond + self.q
 
     # ------------------------------------------------------------ step
     def macro(self):
@@ -467,22 +481,28 @@ class OracleLBM:
         G = p.grad_T
         uG = u[0] * G[0] + u[1] * G[1] + u[2] * G[2]
         if self.lb_thermal:
-            w_T = 1.0 / (0.5 + p.alpha_L / CS2)
+            # per-cell rate from alpha(phi); the LB recovers div(alpha grad T),
+            # and the background part of T_total adds grad alpha . G
+            w_T = 1.0 / (0.5 + self.alpha(phi) / CS2)
+            src = self.q - uG
+            if p.alpha_H != p.alpha_L:
+                gphi = m["gphi"]
+                src = src + (p.alpha_H - p.alpha_L) * (gphi[0] * G[0] + gphi[1] * G[1] + gphi[2] * G[2])
             feq = eq_scalar(m["T"], u, self.Sf)
             f_new = np.empty_like(fs)
             for i in range(self.Sf.Q):
-                f_new[i] = fs[i] - w_T * (fs[i] - feq[i]) + self.Sf.w[i] * (self.q - uG)
+                f_new[i] = fs[i] - w_T * (fs[i] - feq[i]) + self.Sf.w[i] * src
             self.f = f_new
         else:
             T = self.T
             if self.thermal == "RK2":
-                K1 = self.rk_rhs(T, u)
-                self.T = T + self.rk_rhs(T + 0.5 * K1, u)
+                K1 = self.rk_rhs(T, u, phi)
+                self.T = T + self.rk_rhs(T + 0.5 * K1, u, phi)
             else:
-                K1 = self.rk_rhs(T, u)
-                K2 = self.rk_rhs(T + 0.5 * K1, u)
-                K3 = self.rk_rhs(T + 0.5 * K2, u)
-                K4 = self.rk_rhs(T + K3, u)
+                K1 = self.rk_rhs(T, u, phi)
+                K2 = self.rk_rhs(T + 0.5 * K1, u, phi)
+                K3 = self.rk_rhs(T + 0.5 * K2, u, phi)
+                K4 = self.rk_rhs(T + K3, u, phi)
                 self.T = T + K1 / 6.0 + K2 / 3.0 + K3 / 3.0 + K4 / 6.0
         self.h, self.g = h_new, g_new
         self.time += 1

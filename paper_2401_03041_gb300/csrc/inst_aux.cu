@@ -8,11 +8,11 @@ namespace lbm {
 
 template <class S>
 void launch_rk_stage(const DevParams& P, const typename Store<S>::R* psi, typename Store<S>::R* T,
-                     const typename Store<S>::R* u, typename Store<S>::R* acc,
-                     typename Store<S>::R* out, int kind, cudaStream_t st) {
+                     const typename Store<S>::R* u, const typename Store<S>::R* phi,
+                     typename Store<S>::R* acc, typename Store<S>::R* out, int kind, cudaStream_t st) {
   const long long blocks = (P.N + 255) / 256;
   const int grid = (int)(blocks < 152 * 64 ? blocks : 152 * 64);
-  rk_stage_kernel<typename Store<S>::R><<<grid, 256, 0, st>>>(P, psi, T, u, acc, out, kind);
+  rk_stage_kernel<typename Store<S>::R><<<grid, 256, 0, st>>>(P, psi, T, u, phi, acc, out, kind);
 }
 
 template <class S, int Q>
@@ -100,11 +100,11 @@ void launch_diag_finalize(const double* partials, int nblocks, double* out, cuda
 }
 
 template void launch_rk_stage<double>(const DevParams&, const double*, double*, const double*,
-                                      double*, double*, int, cudaStream_t);
-template void launch_rk_stage<float>(const DevParams&, const float*, float*, const float*, float*,
-                                     float*, int, cudaStream_t);
-template void launch_rk_stage<__half>(const DevParams&, const float*, float*, const float*, float*,
-                                      float*, int, cudaStream_t);
+                                      const double*, double*, double*, int, cudaStream_t);
+template void launch_rk_stage<float>(const DevParams&, const float*, float*, const float*, const float*,
+                                     float*, float*, int, cudaStream_t);
+template void launch_rk_stage<__half>(const DevParams&, const float*, float*, const float*, const float*,
+                                      float*, float*, int, cudaStream_t);
 template void launch_pdf_convert<double>(const DevParams&, int, bool, void*, double*, double, cudaStream_t);
 template void launch_pdf_convert<float>(const DevParams&, int, bool, void*, double*, double, cudaStream_t);
 template void launch_pdf_convert<__half>(const DevParams&, int, bool, void*, double*, double, cudaStream_t);

@@ -39,8 +39,8 @@ void launch_init(const DevParams& P, const double* drops, int nd, S* h, S* g, S*
 
 template <class S>
 void launch_rk_stage(const DevParams& P, const typename Store<S>::R* psi, typename Store<S>::R* T,
-                     const typename Store<S>::R* u, typename Store<S>::R* acc,
-                     typename Store<S>::R* out, int kind, cudaStream_t st);
+                     const typename Store<S>::R* u, const typename Store<S>::R* phi,
+                     typename Store<S>::R* acc, typename Store<S>::R* out, int kind, cudaStream_t st);
 
 template <class S>
 void launch_pdf_convert(const DevParams& P, int Q, bool to_f64, void* pdf, double* f64, double shift,

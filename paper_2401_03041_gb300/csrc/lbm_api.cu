@@ -49,7 +49,7 @@ size_t store_bytes(lbm_precision p) { return p == LBM_FP64 ? 8 : (p == LBM_FP32 
 size_t field_bytes(lbm_precision p) { return p == LBM_FP64 ? 8 : 4; }
 
 struct Layout {
-  size_t h[2], g[2], f[2], T, u, sa, sb, acc, partials, diag, drops, errflag, total;
+  size_t h[2], g[2], f[2], T, u, sa, sb, acc, phi, partials, diag, drops, errflag, total;
 };
 
 // Launch geometry of the step kernel: TX x rows columns, z split into chunks.
@@ -145,6 +145,7 @@ bool layout(int nx, int ny, int nz, lbm_precision prec, lbm_thermal th, int qh, 
   L->sa = off; off = align256(off + (rk ? N * fb : 0));
   L->sb = off; off = align256(off + (rk4 ? N * fb : 0));
   L->acc = off; off = align256(off + (rk4 ? N * fb : 0));
+  L->phi = off; off = align256(off + (rk ? N * fb : 0));   // phi of the step (conductivity ratio)
   // room for the largest grid any kernel / z-chunk choice can produce
   const size_t max_blocks = (size_t)((nx + TX - 1) / TX) * ((ny + 3) / 4) * nz;
   L->partials = off; off = align256(off + max_blocks * kDiagVals * 8);
@@ -230,6 +231,7 @@ StepPtrs<S, typename Store<S>::R> ptrs(lbm_domain* d) {
   A.u_out = (R*)at(d, d->L.u);
   A.s1_out = (R*)at(d, d->L.sa);
   A.acc_out = (R*)at(d, d->L.acc);
+  A.phi_out = (R*)at(d, d->L.phi);
   A.rk_acc = d->th == LBM_TH_RK4;
   A.diag_partials = (double*)at(d, d->L.partials);
   A.save = std::is_same<R, double>::value ? (R*)d->save_ptr : nullptr;
@@ -268,12 +270,13 @@ void rk_tail(lbm_domain* d) {
   R* sa = (R*)at(d, d->L.sa);
   R* sb = (R*)at(d, d->L.sb);
   R* acc = (R*)at(d, d->L.acc);
+  const R* phi = d->dp.alpha_ratio ? (const R*)at(d, d->L.phi) : nullptr;
   if (d->th == LBM_TH_RK2) {
-    launch_rk_stage<S>(d->dp, sa, T, u, nullptr, nullptr, 0, d->stream);
+    launch_rk_stage<S>(d->dp, sa, T, u, phi, nullptr, nullptr, 0, d->stream);
   } else {
-    launch_rk_stage<S>(d->dp, sa, T, u, acc, sb, 1, d->stream);   // S2 -> sb
-    launch_rk_stage<S>(d->dp, sb, T, u, acc, sa, 2, d->stream);   // S3 -> sa
-    launch_rk_stage<S>(d->dp, sa, T, u, acc, nullptr, 3, d->stream);
+    launch_rk_stage<S>(d->dp, sa, T, u, phi, acc, sb, 1, d->stream);   // S2 -> sb
+    launch_rk_stage<S>(d->dp, sb, T, u, phi, acc, sa, 2, d->stream);   // S3 -> sa
+    launch_rk_stage<S>(d->dp, sa, T, u, phi, acc, nullptr, 3, d->stream);
   }
 }
 
@@ -371,6 +374,7 @@ void fill_real(RealParams<R>& r, const lbm_params& p, lbm_precision prec) {
   r.tau_H = (R)(p.nu_H / cs2 + 0.5);
   r.rho_L = (R)p.rho_L; r.rho_H = (R)p.rho_H; r.xi = (R)p.xi;
   r.sigma_ref = (R)p.sigma_ref; r.sigma_T = (R)p.sigma_T; r.T_ref = (R)p.T_ref; r.alpha = (R)p.alpha_L;
+  r.dalpha = (R)(p.alpha_H - p.alpha_L);
   for (int k = 0; k < 3; ++k) {
     r.gravity[k] = (R)p.gravity[k];
     r.grad[k] = (R)p.grad_T[k];
@@ -390,6 +394,7 @@ void refresh_devparams(lbm_domain* d) {
   q.GX = pd.GX; q.GY = pd.GY; q.NXP = pd.NXP; q.NYP = pd.NYP; q.Np = (long long)pd.Np;
   q.walls = p.walls_z ? 1 : 0;
   q.rk_iso = p.rk_isotropic_fd ? 1 : 0;
+  q.alpha_ratio = p.alpha_H != p.alpha_L ? 1 : 0;
   q.test_stall = d->test_stall;
   fill_real(q.pd, p, d->prec);
   fill_real(q.pf, p, d->prec);
@@ -566,8 +571,6 @@ lbm_status lbm_set_params(lbm_domain* d, const lbm_params* p) {
   if (p->eps_n < 0) return fail(LBM_ERR_ARG, "eps_n must be >= 0");
   if (p->rho_L != p->rho_H)
     return fail(LBM_ERR_UNSUPPORTED, "density ratio != 1 (pressure/viscous correction forces) not built");
-  if (p->alpha_L != p->alpha_H)
-    return fail(LBM_ERR_UNSUPPORTED, "conductivity ratio != 1 not built");
   if (p->omega_high != 1.0)
     return fail(LBM_ERR_UNSUPPORTED, "higher-order central-moment rate != 1 not built");
   d->params = *p;
@@ -1065,6 +1068,8 @@ lbm_status adj_check(lbm_domain* d) {
   if (!d->inited) return fail(LBM_ERR_STATE, "domain not initialised");
   if (d->prec != LBM_FP64 || !adj_supported(d->qh, d->qf))
     return fail(LBM_ERR_UNSUPPORTED, "the adjoint needs FP64 storage and the D3Q7 thermal LB");
+  if (d->dp.alpha_ratio)
+    return fail(LBM_ERR_UNSUPPORTED, "the adjoint is built for equal diffusivities (alpha_L == alpha_H)");
   if ((long long)d->nx * d->ny >= (1LL << 31))
     return fail(LBM_ERR_UNSUPPORTED, "the adjoint needs nx * ny < 2^31");
   return LBM_OK;

@@ -23,11 +23,52 @@ __device__ __forceinline__ RF stage_at(const DevParams& P, const RF* __restrict_
   return psi[cell_index(P, xx, yy, zz)];
 }
 
+// phi at (x+dx, y+dy, z+dz): periodic in x, y (and z without walls); beyond a
+// wall the mirror ghost phi(first cell).
+template <class RF>
+__device__ __forceinline__ RF phi_at(const DevParams& P, const RF* __restrict__ phi, int x, int y, int z,
+                                     int dx, int dy, int dz) {
+  const int xx = wrap(x + dx, P.nx), yy = wrap(y + dy, P.ny);
+  int zz = z + dz;
+  if (P.walls) zz = zz < 0 ? 0 : (zz >= P.nz ? P.nz - 1 : zz);
+  else zz = wrap(zz, P.nz);
+  return phi[cell_index(P, xx, yy, zz)];
+}
+
+// Gradient of phi by the RK solver's operator (central differences, or the
+// isotropic D3Q27 gradient summed over opposite pairs).
+template <class RF>
+__device__ __forceinline__ void rk_phi_grad(const DevParams& P, const RF* __restrict__ phi, int x, int y, int z,
+                                            RF& gx, RF& gy, RF& gz) {
+  if (P.rk_iso) {
+    gx = gy = gz = 0;
+#pragma unroll
+    for (int k = 1; k < 27; ++k) {
+      const bool first = q27_cx(k) > 0 || (q27_cx(k) == 0 && (q27_cy(k) > 0 || (q27_cy(k) == 0 && q27_cz(k) > 0)));
+      if (first) {
+        const RF w = (RF)weight<27>(k);
+        const RF d = phi_at(P, phi, x, y, z, q27_cx(k), q27_cy(k), q27_cz(k)) -
+                     phi_at(P, phi, x, y, z, -q27_cx(k), -q27_cy(k), -q27_cz(k));
+        if (q27_cx(k)) gx += (RF)q27_cx(k) * w * d;
+        if (q27_cy(k)) gy += (RF)q27_cy(k) * w * d;
+        if (q27_cz(k)) gz += (RF)q27_cz(k) * w * d;
+      }
+    }
+    gx *= (RF)3; gy *= (RF)3; gz *= (RF)3;
+  } else {
+    gx = (RF)0.5 * (phi_at(P, phi, x, y, z, 1, 0, 0) - phi_at(P, phi, x, y, z, -1, 0, 0));
+    gy = (RF)0.5 * (phi_at(P, phi, x, y, z, 0, 1, 0) - phi_at(P, phi, x, y, z, 0, -1, 0));
+    gz = (RF)0.5 * (phi_at(P, phi, x, y, z, 0, 0, 1) - phi_at(P, phi, x, y, z, 0, 0, -1));
+  }
+}
+
 // R(psi) = -u.(grad psi + G) + alpha lap psi + q_T  (Eq. temperature, uniform
 // kappa and rho c_p); 7-point / central operators or the isotropic D3Q27 ones.
+// With a conductivity ratio (phi != null): alpha(phi) lap psi plus
+// (alpha_H - alpha_L) grad phi . (grad psi + G), phi of this step.
 template <class RF>
 __device__ __forceinline__ RF rk_rhs(const DevParams& P, const RF* __restrict__ psi, const RF* u,
-                                     int x, int y, int z, size_t cell) {
+                                     const RF* __restrict__ phi, int x, int y, int z, size_t cell) {
   const auto& rp = RP<RF>(P);
   const RF c = psi[cell];
   RF gx, gy, gz, lap;
@@ -58,6 +99,13 @@ __device__ __forceinline__ RF rk_rhs(const DevParams& P, const RF* __restrict__ 
     lap = xp + xm + yp + ym + zp + zm - (RF)6 * c;
   }
   const RF ux = u[cell], uy = u[P.N + cell], uz = u[2 * P.N + cell];
+  if (phi) {
+    RF pgx, pgy, pgz;
+    rk_phi_grad(P, phi, x, y, z, pgx, pgy, pgz);
+    return -(ux * (gx + (RF)rp.grad[0]) + uy * (gy + (RF)rp.grad[1]) + uz * (gz + (RF)rp.grad[2])) +
+           alpha_of<RF>(P, phi[cell]) * lap + heat_source<RF>(P, x, y, z) +
+           cond_cross<RF>(P, pgx, pgy, pgz, gx, gy, gz);
+  }
   return -(ux * (gx + (RF)rp.grad[0]) + uy * (gy + (RF)rp.grad[1]) + uz * (gz + (RF)rp.grad[2])) +
          (RF)rp.alpha * lap + heat_source<RF>(P, x, y, z);
 }
@@ -73,14 +121,14 @@ enum : int { RK2_FINAL = 0, RK4_STAGE2 = 1, RK4_STAGE3 = 2, RK4_FINAL = 3 };
 // update it in place; the stencil reads go to psi, a different buffer.
 template <class RF>
 __global__ void rk_stage_kernel(const DevParams P, const RF* __restrict__ psi, RF* T, const RF* u,
-                                RF* acc, RF* out, int kind) {
+                                const RF* __restrict__ phi, RF* acc, RF* out, int kind) {
   const size_t n = (size_t)P.N;
   for (size_t cell = blockIdx.x * (size_t)blockDim.x + threadIdx.x; cell < n;
        cell += (size_t)gridDim.x * blockDim.x) {
     const int x = (int)(cell % P.nx);
     const int y = (int)((cell / P.nx) % P.ny);
     const int z = (int)(cell / ((size_t)P.nx * P.ny));
-    const RF K = rk_rhs(P, psi, u, x, y, z, cell);
+    const RF K = rk_rhs(P, psi, u, phi, x, y, z, cell);
     const RF Tc = T[cell];
     if (kind == RK2_FINAL) {
       T[cell] = Tc + K;

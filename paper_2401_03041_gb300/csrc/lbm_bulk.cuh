@@ -450,11 +450,14 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
         const P2* pp = s_pt + hf_slot(z + 1) * G::HPB;
         const int c0 = (ty + 1) * G::HXB + (tx + 1);
         Stencil27<R> fd;
-        R rgx = 0, rgy = 0, rgz = 0, rlap = 0;
+        R rgx = 0, rgy = 0, rgz = 0, rlap = 0, pgx = 0, pgy = 0, pgz = 0;
         const P2 cen = pc[c0];
         if (active) {
           eval_pairs<G::HXB>(fd, pm, pc, pp, c0);
-          if constexpr (QF == 0) rk_std_pairs<P2, R, G::HXB>(pm, pc, pp, c0, rgx, rgy, rgz, rlap);
+          if constexpr (QF == 0) {
+            rk_std_pairs<P2, R, G::HXB>(pm, pc, pp, c0, rgx, rgy, rgz, rlap);
+            if (P.alpha_ratio && !P.rk_iso) central_phi_pairs<P2, R, G::HXB>(pm, pc, pp, c0, pgx, pgy, pgz);
+          }
           if (mode & MODE_SAVE) save_stencil<S>(P, A, cell, cen.x, cen.y, fd);
           xch[cidx] = cen.x;
           xch[NC + cidx] = cen.y;
@@ -493,7 +496,7 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
                 }
               };
               collide_h<S, QH>(P, A, pcell, phi, fd.gpx, fd.gpy, fd.gpz, f, geth);
-              collide_f<S, QF>(P, A, x, y, z, cell, pcell, Tc, fd, rgx, rgy, rgz, rlap, f, getf);
+              collide_f<S, QF>(P, A, x, y, z, cell, pcell, phi, Tc, fd, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf);
             };
             if (lo || hi) run(std::true_type{});
             else run(std::false_type{});

@@ -69,6 +69,24 @@ __device__ __forceinline__ R heat_source(const DevParams& P, int x, int y, int z
 template <class R>
 __device__ __forceinline__ R basis_pick(int c, R z, R p, R m) { return c == 0 ? z : (c > 0 ? p : m); }
 
+// Conductivity ratio (Sec. 2.3, kappa and c_p linear in phi; rho c_p = 1 here):
+// alpha(phi) = alpha_L + phi (alpha_H - alpha_L).
+template <class R>
+__device__ __forceinline__ R alpha_of(const DevParams& P, R phi) {
+  const auto& rp = RP<R>(P);
+  return (R)rp.alpha + phi * (R)rp.dalpha;
+}
+
+// The grad alpha term of the energy equation, (alpha_H - alpha_L) grad phi .
+// (grad T + G), from the solver's own gradient operators.  The LB recovers
+// div(alpha grad T) by itself and takes only the background part
+// (gT = 0 there).
+template <class R>
+__device__ __forceinline__ R cond_cross(const DevParams& P, R gpx, R gpy, R gpz, R gtx, R gty, R gtz) {
+  const auto& rp = RP<R>(P);
+  return (R)rp.dalpha * (gpx * (gtx + (R)rp.grad[0]) + gpy * (gty + (R)rp.grad[1]) + gpz * (gtz + (R)rp.grad[2]));
+}
+
 // Is direction i the first of its opposite pair (first non-zero component > 0)?
 template <int Q>
 __host__ __device__ constexpr bool pair_first(int i) {
@@ -180,6 +198,15 @@ __device__ __forceinline__ void rk_std_pairs(const P2* tm, const P2* tc, const P
   gy = (R)0.5 * (tc[c0 + HXv].y - tc[c0 - HXv].y);
   gz = (R)0.5 * (tp[c0].y - tm[c0].y);
   lap = tc[c0 + 1].y + tc[c0 - 1].y + tc[c0 + HXv].y + tc[c0 - HXv].y + tp[c0].y + tm[c0].y - (R)6 * tc[c0].y;
+}
+
+// Central gradient of phi (.x) from interleaved (phi, T) planes.
+template <class P2, class R, int HXv>
+__device__ __forceinline__ void central_phi_pairs(const P2* tm, const P2* tc, const P2* tp, int c0, R& gx, R& gy,
+                                                  R& gz) {
+  gx = (R)0.5 * (tc[c0 + 1].x - tc[c0 - 1].x);
+  gy = (R)0.5 * (tc[c0 + HXv].x - tc[c0 - HXv].x);
+  gz = (R)0.5 * (tp[c0].x - tm[c0].x);
 }
 
 // RK stage-1 operator values at the cell (7-point Laplacian, central gradient)
@@ -406,13 +433,21 @@ __device__ __forceinline__ void collide_h(const DevParams& P, const StepPtrs<S, 
   });
 }
 
-// a9 / a9': thermal LB collision, or RK stage 1 (QF = 0)
+// a9 / a9': thermal LB collision, or RK stage 1 (QF = 0).  With a
+// conductivity ratio the LB relaxes at the cell's own rate
+// 1 / (1/2 + alpha(phi) / c_s^2) and adds the background part of the grad alpha
+// term as a source; RK stage 1 takes alpha(phi) lap T plus the whole grad alpha
+// term, with grad phi from its own operator (pgx.. central differences for the
+// 7-point set, the isotropic gradient otherwise).
 template <class S, int QF, class GF>
 __device__ __forceinline__ void collide_f(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                                           int x, int y, int z, size_t cell, size_t pcell,
-                                          typename Store<S>::R Tc, const Stencil27<typename Store<S>::R>& fdv,
+                                          typename Store<S>::R phi, typename Store<S>::R Tc,
+                                          const Stencil27<typename Store<S>::R>& fdv,
                                           typename Store<S>::R rgx, typename Store<S>::R rgy,
                                           typename Store<S>::R rgz, typename Store<S>::R rlap,
+                                          typename Store<S>::R pgx, typename Store<S>::R pgy,
+                                          typename Store<S>::R pgz,
                                           const CellFlow<typename Store<S>::R>& f, GF getf) {
   using R = typename Store<S>::R;
   const auto& rp = RP<R>(P);
@@ -421,10 +456,14 @@ __device__ __forceinline__ void collide_f(const DevParams& P, const StepPtrs<S, 
   const R q = heat_source<R>(P, x, y, z);
   const R uG = ux * Gx + uy * Gy + uz * Gz;
   if constexpr (QF > 0) {
-    const R om = (R)rp.omega_T;
+    R om = (R)rp.omega_T;
+    R qs = q - uG;
+    if (P.alpha_ratio) {
+      om = (R)1 / ((R)0.5 + (R)3 * alpha_of<R>(P, phi));
+      qs += cond_cross<R>(P, fdv.gpx, fdv.gpy, fdv.gpz, (R)0, (R)0, (R)0);
+    }
     const R sf = (R)rp.shift_f;
     const R e0 = (R)1 - (R)1.5 * uu;
-    const R qs = q - uG;
     {
       constexpr R w = (R)weight<QF>(0);
       const R fs = getf(std::integral_constant<int, 0>{});
@@ -452,7 +491,13 @@ __device__ __forceinline__ void collide_f(const DevParams& P, const StepPtrs<S, 
     } else {
       gx_ = rgx; gy_ = rgy; gz_ = rgz; lap = rlap;
     }
-    const R K1 = -(ux * (gx_ + Gx) + uy * (gy_ + Gy) + uz * (gz_ + Gz)) + (R)rp.alpha * lap + q;
+    R K1 = -(ux * (gx_ + Gx) + uy * (gy_ + Gy) + uz * (gz_ + Gz)) + (R)rp.alpha * lap + q;
+    if (P.alpha_ratio) {
+      K1 = -(ux * (gx_ + Gx) + uy * (gy_ + Gy) + uz * (gz_ + Gz)) + alpha_of<R>(P, phi) * lap + q;
+      K1 += P.rk_iso ? cond_cross<R>(P, fdv.gpx, fdv.gpy, fdv.gpz, gx_, gy_, gz_)
+                     : cond_cross<R>(P, pgx, pgy, pgz, gx_, gy_, gz_);
+      A.phi_out[cell] = phi;
+    }
     A.u_out[cell] = ux;
     A.u_out[P.N + cell] = uy;
     A.u_out[2 * P.N + cell] = uz;
@@ -504,7 +549,8 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
                                             const Stencil27<typename Store<S>::R>& fdv,
                                             typename Store<S>::R rgx, typename Store<S>::R rgy,
                                             typename Store<S>::R rgz, typename Store<S>::R rlap,
-                                            GH geth, GG getg, GF getf, double* dsum) {
+                                            typename Store<S>::R pgx, typename Store<S>::R pgy,
+                                            typename Store<S>::R pgz, GH geth, GG getg, GF getf, double* dsum) {
   using R = typename Store<S>::R;
   const GMoments<R> m = g_moments<R>(getg);
   if (mode & MODE_SAVE) {
@@ -517,7 +563,7 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
   if (!(mode & MODE_COLLIDE)) return;
   collide_g<S>(P, A, pcell, phi, m, f);
   collide_h<S, QH>(P, A, pcell, phi, fdv.gpx, fdv.gpy, fdv.gpz, f, geth);
-  collide_f<S, QF>(P, A, x, y, z, cell, pcell, Tc, fdv, rgx, rgy, rgz, rlap, f, getf);
+  collide_f<S, QF>(P, A, x, y, z, cell, pcell, phi, Tc, fdv, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf);
 }
 
 }  // namespace lbm

@@ -108,6 +108,7 @@ template <class R>
 struct RealParams {
   R omega_phi, omega_T, tau_L, tau_H;
   R rho_L, rho_H, xi, sigma_ref, sigma_T, T_ref, alpha;
+  R dalpha;                       // alpha_H - alpha_L (conductivity ratio != 1)
   R gravity[3];
   R T_bottom, T_top;
   R grad[3], origin[3];
@@ -133,6 +134,7 @@ struct DevParams {
   int rk_iso;
   int test_stall;  // test of the timeout path: the bulk kernel's first copy wait runs out
   int qfield_f32;  // element type of qfield: 0 double, 1 float
+  int alpha_ratio;  // alpha_H != alpha_L: alpha(phi) per cell and the grad alpha terms
   const void* qfield;  // caller-owned dense [z][y][x] heat-source density, or null
   int nsrc;
   int npatch, patch_z, patch_sx, patch_sy;
@@ -164,6 +166,7 @@ struct StepPtrs {
   const S* f_src; S* f_dst;
   // RK thermal fields (RF = double in FP64 mode, float otherwise)
   const RF* T; RF* u_out; RF* s1_out; RF* acc_out;
+  RF* phi_out;                    // RK with a conductivity ratio: phi for stages 2..4
   int rk_acc;                     // RK4: write acc = K1/6
   // macroscopic output (MODE_MACRO): order phi, u(3), p, T, selected by mask
   void* macro_out; int macro_dtype; unsigned macro_mask;

@@ -145,7 +145,11 @@ step_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, int zc
       Stencil27<R> fd;
       fd.template eval<HX>(s_phi[sm], s_phi[sc], s_phi[sp], s_T[sm], s_T[sc], s_T[sp], c0);
       R rgx = 0, rgy = 0, rgz = 0, rlap = 0;
-      if constexpr (QF == 0) rk_std<R, HX>(s_T[sm], s_T[sc], s_T[sp], c0, rgx, rgy, rgz, rlap);
+      R pgx = 0, pgy = 0, pgz = 0, plap;
+      if constexpr (QF == 0) {
+        rk_std<R, HX>(s_T[sm], s_T[sc], s_T[sp], c0, rgx, rgy, rgz, rlap);
+        if (P.alpha_ratio && !P.rk_iso) rk_std<R, HX>(s_phi[sm], s_phi[sc], s_phi[sp], c0, pgx, pgy, pgz, plap);
+      }
       const size_t cell = cell_index(P, x, y, z);
       auto geth = [&](auto I) { return pull<QH, false, decltype(I)::value>(P, A.h_src, x, y, z, shh); };
       auto getg = [&](auto I) { return pull<27, false, decltype(I)::value>(P, A.g_src, x, y, z, (R)0); };
@@ -154,7 +158,7 @@ step_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, int zc
         else return (R)0;
       };
       cell_update<S, QH, QF>(P, A, x, y, z, cell, pdf_index(P, x, y, z), mode, s_phi[sc][c0], s_T[sc][c0], fd, rgx, rgy,
-                             rgz, rlap, geth, getg, getf, dsum);
+                             rgz, rlap, pgx, pgy, pgz, geth, getg, getf, dsum);
     }
     __syncthreads();
     const int t = sm;

@@ -167,3 +167,13 @@ def test_capture_objective_autograd():
     J_ref, g_ref = d.adjoint_run(40, 10, w.target)
     assert abs(J.item() - J_ref) <= 1e-6 * J_ref   # intensities round-tripped through float32
     assert np.allclose(I.grad.numpy(), g_ref, rtol=1e-5, atol=0)
+
+
+def test_adjoint_rejects_conductivity_ratio():
+    from paper_2401_03041_gb300 import lbm
+    w = W.config5(n=16)
+    w = w.replace(params=W.Params(**dict(w.params.__dict__, alpha_H=0.01)))
+    d = gpu_domain(w)
+    with pytest.raises(lbm.LBMError) as e:
+        d.adjoint_run(4, 2, w.target)
+    assert e.value.status == -7

@@ -193,6 +193,44 @@ def test_rk_isotropic_operator_and_patches_fp64():
     compare_all(d, o, w, TOL64, "rk4 iso + patches")
 
 
+def _ratio_workload(thermal, walls=True, iso=False):
+    w = ragged_workload(thermal, 15, walls=walls)
+    kw = dict(w.params.__dict__, alpha_L=0.1, alpha_H=0.02, rk_isotropic_fd=iso)
+    return w.replace(params=W.Params(**kw))
+
+
+@pytest.mark.parametrize("thermal,walls,iso", [("D3Q7", True, False), ("D3Q19", True, False),
+                                               ("D3Q15", False, False), ("RK2", True, False),
+                                               ("RK4", True, False), ("RK4", False, True)])
+def test_conductivity_ratio_fp64(thermal, walls, iso):
+    """alpha_H = alpha_L / 5 (Sec. 2.3, kappa linear in phi): per-cell LB rate
+    and background source, or the RK grad alpha term in stage 1 (step kernel)
+    and stages 2..4 (stage kernel, phi of the step); with a tilted background
+    gradient, walls or periodic z, generic and bulk kernels."""
+    w = _ratio_workload(thermal, walls, iso)
+    o = oracle_for(w)
+    o.step(12)
+    for kern in _kernels("fp64", 15, thermal):
+        d = gpu_domain(w, kernel=kern)
+        d.step(12)
+        compare_all(d, o, w, TOL64, f"conductivity ratio {thermal} walls={walls} iso={iso} {kern}")
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 2e-4), ("fp16", 5e-2)])
+def test_conductivity_ratio_reduced_precision(precision, tol):
+    """FP32 / FP16-storage runs of the ratio workload (D3Q7 and RK4) stay
+    within the reduced-precision error of the FP64 GPU run after 40 steps."""
+    for thermal in ("D3Q7", "RK4"):
+        w = _ratio_workload(thermal)
+        ref = gpu_domain(w)
+        ref.step(40)
+        d = gpu_domain(w, precision=precision)
+        d.step(40)
+        a, b = gpu_fields(d), gpu_fields(ref)
+        for k in ("phi", "T"):
+            assert relerr(a[k], b[k]) < tol, (precision, thermal, k, relerr(a[k], b[k]))
+
+
 def _field_tensor(q, dtype):
     import torch
     return torch.tensor(np.ascontiguousarray(q).ravel(), dtype=dtype, device="cuda")

@@ -353,6 +353,48 @@ def test_heat_field_total_heat_grows_by_its_sum(thermal):
     assert np.abs(T).max() < 5 * q.max()        # diffusion spread the spots
 
 
+@pytest.mark.parametrize("thermal,tol", [("D3Q7", 4e-3), ("RK4", 3e-2)])
+def test_two_layer_conduction_steady_state(thermal, tol):
+    """Conductivity ratio 1/5 across a planar diffuse interface between two
+    walls (T = 1 below, 0 above), no flow.  The steady state of
+    dT/dt = div(alpha(phi) grad T) carries a constant flux, so
+    T(z) = 1 - int_0^z dz'/alpha / int_0^H dz'/alpha (quadrature of the
+    tanh profile's alpha).  The LB (conservative by construction) and the RK
+    finite differences (alpha lap T + grad alpha . grad T) must reach it to
+    their discretisation error; a dropped or sign-flipped grad alpha . grad T
+    term moves the interface temperature by more than 0.3."""
+    from scipy.integrate import quad
+    nz, xi, aL, aH, zc = 16, 3.0, 0.5, 0.1, 8.0
+    o = make(1, 1, nz, thermal=thermal, alpha_L=aL, alpha_H=aH, xi=xi, sigma_ref=1e-4,
+             sigma_T=0.0, walls_z=True, T_bottom=1.0, T_top=0.0)
+    phi = 0.5 * (1 + np.tanh(2 * (o.Z - zc) / xi))
+    set_fields(o, phi, T=1.0 - o.Z / nz)
+    o.step(1200)
+    T = o.macro()["T"][:, 0, 0]
+
+    def inv_alpha(z):
+        return 1.0 / (aL + 0.5 * (1 + math.tanh(2 * (z - zc) / xi)) * (aH - aL))
+
+    total = quad(inv_alpha, 0, nz, points=[zc])[0]
+    exact = np.array([1 - quad(inv_alpha, 0, z, points=[zc] if z > zc else None)[0] / total
+                      for z in o.Z[:, 0, 0]])
+    assert np.abs(T - exact).max() < tol
+    assert np.abs(o.macro()["u"]).max() < 1e-6
+
+
+def test_conductivity_ratio_lb_conserves_heat():
+    """Periodic box at rest, alpha_H = alpha_L / 5 with a droplet-shaped phi:
+    the per-cell relaxation rate leaves sum T unchanged (no sources)."""
+    o = make(8, 6, 5, thermal="D3Q15", alpha_L=0.2, alpha_H=0.04, sigma_T=0.0)
+    z, y, x = o.Z, o.Y, o.X
+    phi = 0.5 * (1 + np.tanh(2 * (2.5 - np.sqrt((x - 4) ** 2 + (y - 3) ** 2 + (z - 2.5) ** 2)) / 2.0))
+    T = W.random_state(4, (5, 6, 8), 0.1)
+    set_fields(o, phi, T=T)
+    s0 = o.macro()["T"].sum()
+    o.step(6)
+    assert abs(o.macro()["T"].sum() - s0) < 1e-13 * np.abs(T).sum()
+
+
 @pytest.mark.parametrize("thermal", ["D3Q7", "RK2", "RK4"])
 def test_background_gradient_advection_source(thermal):
     """T_total = T + G.(x - x0): a uniform flow U across the imposed gradient
