@@ -93,6 +93,9 @@ typedef struct {
   double omega_high;       /* rate of central moments of order >= 3; this build requires 1 */
   int32_t rk_isotropic_fd; /* RK solvers: 0 = 7-point Laplacian and central gradient,
                               1 = isotropic D3Q27 operators */
+  double T_bottom_amp;     /* bottom wall temperature T_bottom + T_bottom_amp cos(omega x), */
+  int32_t T_bottom_waves;  /* omega = 2 pi T_bottom_waves / nx, x the cell centre (Sec. 3.1
+                              planar heated channel); 0 = uniform T_bottom */
 } lbm_params;
 
 /* Gaussian laser heat source, Eq. HeatSource: q = Q exp(-2 r^2 / w^2) where

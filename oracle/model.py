@@ -281,7 +281,8 @@ class OracleLBM:
             u[1] += pk * d.uy
             u[2] += pk * d.uz
         if self.walls:
-            T0 = p.T_bottom + (p.T_top - p.T_bottom) * self.Z / self.NZ
+            Tb = self.T_wall_bottom()
+            T0 = Tb + (p.T_top - Tb) * self.Z / self.NZ
         else:
             T0 = np.zeros_like(phi)
         self.h = eq_scalar(phi, u, self.Sh)
@@ -291,6 +292,19 @@ class OracleLBM:
         else:
             self.T = T0.copy()
         self.time = 0
+
+    def T_wall_bottom(self):
+        """Bottom wall temperature above each column, shape (ny, nx):
+        T_bottom + T_bottom_amp cos(omega x) at the cell centre x, with
+        omega = 2 pi k / NX (the planar heated channel's heated wall, Sec. 3.1);
+        uniform T_bottom when no modulation is set."""
+        p = self.p
+        X = self.X[0]
+        amp = getattr(p, "T_bottom_amp", 0.0)
+        k = getattr(p, "T_bottom_waves", 0)
+        if amp == 0.0 or k == 0:
+            return np.full(X.shape, float(p.T_bottom))
+        return p.T_bottom + amp * np.cos(2.0 * math.pi * k * X / self.NX)
 
     # ------------------------------------------------------------ a1 stream
     def _pull(self, pdf, S, rule=None, Tb=0.0, Tt=0.0):
@@ -321,7 +335,7 @@ class OracleLBM:
                 q[0] = q[1]
                 q[-1] = q[-2]
             else:
-                q[0] = 2.0 * self.p.T_bottom - q[1]
+                q[0] = 2.0 * np.pad(self.T_wall_bottom(), 1, mode="wrap") - q[1]
                 q[-1] = 2.0 * self.p.T_top - q[-2]
         return q
 
@@ -441,7 +455,7 @@ class OracleLBM:
         computes from its pulled PDFs), without advancing."""
         hs = self._pull(self.h, self.Sh)
         gs = self._pull(self.g, self.S27)
-        fs = (self._pull(self.f, self.Sf, "abb", self.p.T_bottom, self.p.T_top)
+        fs = (self._pull(self.f, self.Sf, "abb", self.T_wall_bottom(), self.p.T_top)
               if self.lb_thermal else None)
         return self._macro_from_pulled(hs, gs, fs)
 
@@ -453,7 +467,7 @@ class OracleLBM:
         p = self.p
         hs = self._pull(self.h, self.Sh)
         gs = self._pull(self.g, self.S27)
-        fs = (self._pull(self.f, self.Sf, "abb", p.T_bottom, p.T_top)
+        fs = (self._pull(self.f, self.Sf, "abb", self.T_wall_bottom(), p.T_top)
               if self.lb_thermal else None)
         m = self._macro_from_pulled(hs, gs, fs)
         phi, u, a = m["phi"], m["u"], m["a"]

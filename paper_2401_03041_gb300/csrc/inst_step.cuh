@@ -17,12 +17,18 @@ void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
     if (use_bulk) {
       static bool attr_set = false;
       if (!attr_set) {
-        cudaFuncSetAttribute(step_bulk_kernel<S, QH, QF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(step_bulk_kernel<S, QH, QF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes);
+        cudaFuncSetAttribute(step_bulk_kernel<S, QH, QF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bytes);
         attr_set = true;
       }
-      step_bulk_kernel<S, QH, QF><<<grid, BulkSmem<S, QH, QF>::G::NTHR, bytes, st>>>(
-          P, A, maps.h, maps.g, maps.f, zchunk, mode);
+      if (P.alpha_ratio || P.tw_waves)
+        step_bulk_kernel<S, QH, QF, true><<<grid, BulkSmem<S, QH, QF>::G::NTHR, bytes, st>>>(
+            P, A, maps.h, maps.g, maps.f, zchunk, mode);
+      else
+        step_bulk_kernel<S, QH, QF, false><<<grid, BulkSmem<S, QH, QF>::G::NTHR, bytes, st>>>(
+            P, A, maps.h, maps.g, maps.f, zchunk, mode);
       return;
     }
   }

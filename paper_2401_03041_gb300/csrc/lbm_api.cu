@@ -374,13 +374,14 @@ void fill_real(RealParams<R>& r, const lbm_params& p, lbm_precision prec) {
   r.tau_H = (R)(p.nu_H / cs2 + 0.5);
   r.rho_L = (R)p.rho_L; r.rho_H = (R)p.rho_H; r.xi = (R)p.xi;
   r.sigma_ref = (R)p.sigma_ref; r.sigma_T = (R)p.sigma_T; r.T_ref = (R)p.T_ref; r.alpha = (R)p.alpha_L;
-  r.dalpha = (R)(p.alpha_H - p.alpha_L);
+
   for (int k = 0; k < 3; ++k) {
     r.gravity[k] = (R)p.gravity[k];
     r.grad[k] = (R)p.grad_T[k];
     r.origin[k] = (R)p.grad_T_origin[k];
   }
   r.T_bottom = (R)p.T_bottom; r.T_top = (R)p.T_top;
+
   r.eps_n = (R)p.eps_n;
   r.shift_h = (R)(prec == LBM_FP64 ? 0.0 : 0.5);
   r.shift_f = (R)(prec == LBM_FP64 ? 0.0 : p.T_ref);
@@ -395,6 +396,11 @@ void refresh_devparams(lbm_domain* d) {
   q.walls = p.walls_z ? 1 : 0;
   q.rk_iso = p.rk_isotropic_fd ? 1 : 0;
   q.alpha_ratio = p.alpha_H != p.alpha_L ? 1 : 0;
+  q.tw_waves = p.T_bottom_amp != 0.0 ? p.T_bottom_waves : 0;
+  q.dalpha_d = p.alpha_H - p.alpha_L;
+  q.dalpha_f = (float)(p.alpha_H - p.alpha_L);
+  q.T_bottom_amp_d = p.T_bottom_amp;
+  q.T_bottom_amp_f = (float)p.T_bottom_amp;
   q.test_stall = d->test_stall;
   fill_real(q.pd, p, d->prec);
   fill_real(q.pf, p, d->prec);
@@ -560,7 +566,7 @@ lbm_status lbm_set_params(lbm_domain* d, const lbm_params* p) {
                          p->sigma_T, p->T_ref, p->alpha_L, p->alpha_H, p->gravity[0], p->gravity[1],
                          p->gravity[2], p->T_bottom, p->T_top, p->grad_T[0], p->grad_T[1],
                          p->grad_T[2], p->grad_T_origin[0], p->grad_T_origin[1],
-                         p->grad_T_origin[2], p->eps_n, p->omega_high};
+                         p->grad_T_origin[2], p->eps_n, p->omega_high, p->T_bottom_amp};
   if (!finite_all(vals, (int)(sizeof(vals) / sizeof(vals[0]))))
     return fail(LBM_ERR_ARG, "non-finite parameter");
   if (p->nu_L <= 0 || p->nu_H <= 0) return fail(LBM_ERR_ARG, "viscosity must be > 0");
@@ -569,6 +575,7 @@ lbm_status lbm_set_params(lbm_domain* d, const lbm_params* p) {
   if (p->alpha_L <= 0 || p->alpha_H <= 0) return fail(LBM_ERR_ARG, "diffusivity must be > 0");
   if (p->rho_L <= 0 || p->rho_H <= 0) return fail(LBM_ERR_ARG, "density must be > 0");
   if (p->eps_n < 0) return fail(LBM_ERR_ARG, "eps_n must be >= 0");
+  if (p->T_bottom_waves < 0) return fail(LBM_ERR_ARG, "T_bottom_waves must be >= 0");
   if (p->rho_L != p->rho_H)
     return fail(LBM_ERR_UNSUPPORTED, "density ratio != 1 (pressure/viscous correction forces) not built");
   if (p->omega_high != 1.0)

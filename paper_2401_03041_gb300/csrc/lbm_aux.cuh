@@ -15,7 +15,7 @@ __device__ __forceinline__ RF stage_at(const DevParams& P, const RF* __restrict_
   const int xx = wrap(x + dx, P.nx), yy = wrap(y + dy, P.ny);
   int zz = z + dz;
   if (P.walls) {
-    if (zz < 0) return (RF)2 * rp.T_bottom - psi[cell_index(P, xx, yy, 0)];
+    if (zz < 0) return (RF)2 * wall_T<RF>(P, xx, true) - psi[cell_index(P, xx, yy, 0)];
     if (zz >= P.nz) return (RF)2 * rp.T_top - psi[cell_index(P, xx, yy, P.nz - 1)];
   } else {
     zz = wrap(zz, P.nz);
@@ -226,7 +226,8 @@ init_kernel(const DevParams P, const double* __restrict__ drops, int nd, S* h, S
   }
   if (!inside) return;
   const size_t cell = ((size_t)z * P.ny + y) * P.nx + x;
-  const double T0 = P.walls ? rp.T_bottom + (rp.T_top - rp.T_bottom) * (z + 0.5) / P.nz : 0.0;
+  const double Tb = wall_T<double>(P, x, true);
+  const double T0 = P.walls ? Tb + (rp.T_top - Tb) * (z + 0.5) / P.nz : 0.0;
   const size_t pc = pdf_index(P, x, y, z);
   const size_t np = (size_t)P.Np;
   // equilibria in the compute type of the storage (FP64 in FP64 mode)

@@ -213,7 +213,10 @@ __device__ __forceinline__ void issue_stage(const DevParams& P, const CUtensorMa
   tma_load_4d(dst, map, x0 - G::GXP + P.GX, yy + P.GY, zz, q, bar);
 }
 
-template <class S, int QH, int QF>
+// EXT: the extensions of the uniform-property model (conductivity ratio,
+// modulated bottom wall) are compiled in; lattices without them run the
+// EXT = false instantiation, which carries none of their code.
+template <class S, int QH, int QF, bool EXT>
 __global__ void __launch_bounds__(BulkSmem<S, QH, QF>::G::NTHR, 1)
 step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
                  const __grid_constant__ CUtensorMap mh, const __grid_constant__ CUtensorMap mg,
@@ -289,14 +292,25 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
       });
       phi += shh;  // sum_i w_i * shift_h
       R T;
+      // wall temperature below this halo column (its x wrapped into the lattice)
+      auto bottom_T = [&]() {
+        int gx = x0 + hc - 1;
+        gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
+        return wall_T<R>(P, gx, true);
+      };
       if constexpr (QF > 0) {
         T = 0;
+        R Tb = 0;
+        if constexpr (BOUNCE) {
+          if constexpr (EXT) Tb = bottom_T();
+          else Tb = (R)rp.T_bottom;
+        }
         static_for<0, QF>([&](auto I) {
           constexpr int i = decltype(I)::value;
           const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
           const S* rowp = rowb + (size_t)(QH + i) * G::HFB;
           const R v = Store<S>::ld_s(b ? rowp : rowp - cx<QF>(i)) + (R)weight<QF>(i) * shf;
-          T += b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? rp.T_bottom : rp.T_top)) : v;
+          T += b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? Tb : (R)rp.T_top)) : v;
         });
       } else {
         int gx = x0 + hc - 1, gy = y0 + hr - 1;
@@ -304,7 +318,11 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
         gy = gy < 0 ? gy + P.ny : (gy >= P.ny ? gy - P.ny : gy);
         T = A.T[cell_index(P, gx, gy, pe)];
       }
-      if (ghost) T = (R)2 * (p < 0 ? rp.T_bottom : rp.T_top) - T;
+      if constexpr (EXT) {
+        if (ghost) T = (R)2 * (p < 0 ? bottom_T() : (R)rp.T_top) - T;
+      } else {
+        if (ghost) T = (R)2 * (p < 0 ? rp.T_bottom : rp.T_top) - T;
+      }
       P2 v;
       v.x = phi;
       v.y = T;
@@ -456,7 +474,8 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
           eval_pairs<G::HXB>(fd, pm, pc, pp, c0);
           if constexpr (QF == 0) {
             rk_std_pairs<P2, R, G::HXB>(pm, pc, pp, c0, rgx, rgy, rgz, rlap);
-            if (P.alpha_ratio && !P.rk_iso) central_phi_pairs<P2, R, G::HXB>(pm, pc, pp, c0, pgx, pgy, pgz);
+            if constexpr (EXT)
+              if (P.alpha_ratio && !P.rk_iso) central_phi_pairs<P2, R, G::HXB>(pm, pc, pp, c0, pgx, pgy, pgz);
           }
           if (mode & MODE_SAVE) save_stencil<S>(P, A, cell, cen.x, cen.y, fd);
           xch[cidx] = cen.x;
@@ -484,19 +503,27 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
                 const S* p_ = hrow + (size_t)i * G::HFB;
                 return Store<S>::ld_s(b ? p_ : p_ - cx<QH>(i)) + (R)weight<QH>(i) * shh;
               };
+              R Tb = 0;
+              if constexpr (BOUNCE && QF > 0) {
+                if constexpr (EXT) Tb = wall_T<R>(P, x, true);
+                else Tb = (R)rp.T_bottom;
+              }
               auto getf = [&](auto I) {
                 constexpr int i = decltype(I)::value;
                 if constexpr (QF > 0) {
                   const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
                   const S* p_ = hrow + (size_t)(QH + i) * G::HFB;
                   const R v = Store<S>::ld_s(b ? p_ : p_ - cx<QF>(i)) + (R)weight<QF>(i) * shf;
-                  return b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? rp.T_bottom : rp.T_top)) : v;
+                  return b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? Tb : (R)rp.T_top)) : v;
                 } else {
                   return (R)0;
                 }
               };
               collide_h<S, QH>(P, A, pcell, phi, fd.gpx, fd.gpy, fd.gpz, f, geth);
-              collide_f<S, QF>(P, A, x, y, z, cell, pcell, phi, Tc, fd, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf);
+              if (EXT && P.alpha_ratio)
+                collide_f<S, QF, EXT>(P, A, x, y, z, cell, pcell, phi, Tc, fd, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf);
+              else
+                collide_f<S, QF, false>(P, A, x, y, z, cell, pcell, phi, Tc, fd, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf);
             };
             if (lo || hi) run(std::true_type{});
             else run(std::false_type{});

@@ -74,7 +74,7 @@ __device__ __forceinline__ R basis_pick(int c, R z, R p, R m) { return c == 0 ? 
 template <class R>
 __device__ __forceinline__ R alpha_of(const DevParams& P, R phi) {
   const auto& rp = RP<R>(P);
-  return (R)rp.alpha + phi * (R)rp.dalpha;
+  return (R)rp.alpha + phi * dalpha_of<R>(P);
 }
 
 // The grad alpha term of the energy equation, (alpha_H - alpha_L) grad phi .
@@ -84,7 +84,7 @@ __device__ __forceinline__ R alpha_of(const DevParams& P, R phi) {
 template <class R>
 __device__ __forceinline__ R cond_cross(const DevParams& P, R gpx, R gpy, R gpz, R gtx, R gty, R gtz) {
   const auto& rp = RP<R>(P);
-  return (R)rp.dalpha * (gpx * (gtx + (R)rp.grad[0]) + gpy * (gty + (R)rp.grad[1]) + gpz * (gtz + (R)rp.grad[2]));
+  return dalpha_of<R>(P) * (gpx * (gtx + (R)rp.grad[0]) + gpy * (gty + (R)rp.grad[1]) + gpz * (gtz + (R)rp.grad[2]));
 }
 
 // Is direction i the first of its opposite pair (first non-zero component > 0)?
@@ -438,8 +438,9 @@ __device__ __forceinline__ void collide_h(const DevParams& P, const StepPtrs<S, 
 // 1 / (1/2 + alpha(phi) / c_s^2) and adds the background part of the grad alpha
 // term as a source; RK stage 1 takes alpha(phi) lap T plus the whole grad alpha
 // term, with grad phi from its own operator (pgx.. central differences for the
-// 7-point set, the isotropic gradient otherwise).
-template <class S, int QF, class GF>
+// 7-point set, the isotropic gradient otherwise).  RATIO = P.alpha_ratio,
+// resolved by the caller so that the equal-diffusivity path carries none of it.
+template <class S, int QF, bool RATIO, class GF>
 __device__ __forceinline__ void collide_f(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                                           int x, int y, int z, size_t cell, size_t pcell,
                                           typename Store<S>::R phi, typename Store<S>::R Tc,
@@ -458,7 +459,7 @@ __device__ __forceinline__ void collide_f(const DevParams& P, const StepPtrs<S, 
   if constexpr (QF > 0) {
     R om = (R)rp.omega_T;
     R qs = q - uG;
-    if (P.alpha_ratio) {
+    if constexpr (RATIO) {
       om = (R)1 / ((R)0.5 + (R)3 * alpha_of<R>(P, phi));
       qs += cond_cross<R>(P, fdv.gpx, fdv.gpy, fdv.gpz, (R)0, (R)0, (R)0);
     }
@@ -492,7 +493,7 @@ __device__ __forceinline__ void collide_f(const DevParams& P, const StepPtrs<S, 
       gx_ = rgx; gy_ = rgy; gz_ = rgz; lap = rlap;
     }
     R K1 = -(ux * (gx_ + Gx) + uy * (gy_ + Gy) + uz * (gz_ + Gz)) + (R)rp.alpha * lap + q;
-    if (P.alpha_ratio) {
+    if constexpr (RATIO) {
       K1 = -(ux * (gx_ + Gx) + uy * (gy_ + Gy) + uz * (gz_ + Gz)) + alpha_of<R>(P, phi) * lap + q;
       K1 += P.rk_iso ? cond_cross<R>(P, fdv.gpx, fdv.gpy, fdv.gpz, gx_, gy_, gz_)
                      : cond_cross<R>(P, pgx, pgy, pgz, gx_, gy_, gz_);
@@ -563,7 +564,8 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
   if (!(mode & MODE_COLLIDE)) return;
   collide_g<S>(P, A, pcell, phi, m, f);
   collide_h<S, QH>(P, A, pcell, phi, fdv.gpx, fdv.gpy, fdv.gpz, f, geth);
-  collide_f<S, QF>(P, A, x, y, z, cell, pcell, phi, Tc, fdv, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf);
+  if (P.alpha_ratio) collide_f<S, QF, true>(P, A, x, y, z, cell, pcell, phi, Tc, fdv, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf);
+  else collide_f<S, QF, false>(P, A, x, y, z, cell, pcell, phi, Tc, fdv, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf);
 }
 
 }  // namespace lbm

@@ -108,7 +108,6 @@ template <class R>
 struct RealParams {
   R omega_phi, omega_T, tau_L, tau_H;
   R rho_L, rho_H, xi, sigma_ref, sigma_T, T_ref, alpha;
-  R dalpha;                       // alpha_H - alpha_L (conductivity ratio != 1)
   R gravity[3];
   R T_bottom, T_top;
   R grad[3], origin[3];
@@ -134,18 +133,45 @@ struct DevParams {
   int rk_iso;
   int test_stall;  // test of the timeout path: the bulk kernel's first copy wait runs out
   int qfield_f32;  // element type of qfield: 0 double, 1 float
-  int alpha_ratio;  // alpha_H != alpha_L: alpha(phi) per cell and the grad alpha terms
   const void* qfield;  // caller-owned dense [z][y][x] heat-source density, or null
   int nsrc;
   int npatch, patch_z, patch_sx, patch_sy;
   int px0[kMaxPatches], py0[kMaxPatches];
   RealParams<double> pd;
   RealParams<float> pf;
+  // Extensions of the uniform-property model, kept after everything else so
+  // that the fields above keep their constant-bank offsets.
+  int alpha_ratio;  // alpha_H != alpha_L: alpha(phi) per cell and the grad alpha terms
+  int tw_waves;     // k > 0: modulated bottom wall temperature (T_bottom_amp != 0)
+  double dalpha_d, T_bottom_amp_d;  // alpha_H - alpha_L; bottom wall modulation amplitude
+  float dalpha_f, T_bottom_amp_f;
 };
 
 template <class R> __host__ __device__ __forceinline__ const RealParams<R>& RP(const DevParams& P);
 template <> __host__ __device__ __forceinline__ const RealParams<double>& RP<double>(const DevParams& P) { return P.pd; }
 template <> __host__ __device__ __forceinline__ const RealParams<float>& RP<float>(const DevParams& P) { return P.pf; }
+
+template <class R> __device__ __forceinline__ R dalpha_of(const DevParams& P);
+template <> __device__ __forceinline__ double dalpha_of<double>(const DevParams& P) { return P.dalpha_d; }
+template <> __device__ __forceinline__ float dalpha_of<float>(const DevParams& P) { return P.dalpha_f; }
+template <class R> __device__ __forceinline__ R t_amp_of(const DevParams& P);
+template <> __device__ __forceinline__ double t_amp_of<double>(const DevParams& P) { return P.T_bottom_amp_d; }
+template <> __device__ __forceinline__ float t_amp_of<float>(const DevParams& P) { return P.T_bottom_amp_f; }
+
+__device__ __forceinline__ double cos_pi(double a) { return cospi(a); }
+__device__ __forceinline__ float cos_pi(float a) { return cospif(a); }
+
+// Wall temperature above column x (0 <= x < nx): T_top at the top wall; at
+// the bottom T_bottom, plus T_bottom_amp cos(omega (x + 1/2)) with
+// omega = 2 pi k / nx when a modulation is set.
+template <class R>
+__device__ __forceinline__ R wall_T(const DevParams& P, int x, bool bottom) {
+  const auto& rp = RP<R>(P);
+  if (!bottom) return (R)rp.T_top;
+  R t = (R)rp.T_bottom;
+  if (P.tw_waves) t += t_amp_of<R>(P) * cos_pi((R)(2 * P.tw_waves) * ((R)x + (R)0.5) / (R)P.nx);
+  return t;
+}
 
 // Kernel modes (bit set).
 enum : int { MODE_COLLIDE = 1, MODE_DIAG = 2, MODE_MACRO = 4, MODE_SAVE = 8 };
@@ -166,7 +192,6 @@ struct StepPtrs {
   const S* f_src; S* f_dst;
   // RK thermal fields (RF = double in FP64 mode, float otherwise)
   const RF* T; RF* u_out; RF* s1_out; RF* acc_out;
-  RF* phi_out;                    // RK with a conductivity ratio: phi for stages 2..4
   int rk_acc;                     // RK4: write acc = K1/6
   // macroscopic output (MODE_MACRO): order phi, u(3), p, T, selected by mask
   void* macro_out; int macro_dtype; unsigned macro_mask;
@@ -178,6 +203,7 @@ struct StepPtrs {
   S* hd[27];
   S* gd[27];
   S* fd[27];
+  RF* phi_out;                    // RK with a conductivity ratio: phi for stages 2..4
 };
 
 // Buffers of one adjoint step (lbm_adjoint.cuh): dense FP64 arrays (N values

@@ -45,7 +45,7 @@ __device__ __forceinline__ typename Store<S>::R pull(const DevParams& P, const S
   if (P.walls && (zs < 0 || zs >= P.nz)) {
     const R v = Store<S>::ld(base + (size_t)opp<Q>(I) * P.Np + pdf_index(P, x, y, z)) + wsh;
     if constexpr (ABB) {
-      const R Tw = zs < 0 ? rp.T_bottom : rp.T_top;
+      const R Tw = wall_T<R>(P, x, zs < 0);
       return -v + (R)2 * w * Tw;
     }
     return v;
@@ -122,7 +122,7 @@ step_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, int zc
       R T;
       if constexpr (QF > 0) T = pulled_sum<QF, true>(P, A.f_src, gx, gy, zz, shf);
       else T = A.T[cell_index(P, gx, gy, zz)];
-      if (ghost) T = (R)2 * (zp < 0 ? rp.T_bottom : rp.T_top) - T;  // phi: mirror
+      if (ghost) T = (R)2 * wall_T<R>(P, gx, zp < 0) - T;  // phi: mirror
       s_phi[slot][k] = phi;
       s_T[slot][k] = T;
     }

@@ -43,7 +43,8 @@ class Params(ctypes.Structure):
                 ("walls_z", ctypes.c_int32), ("T_bottom", ctypes.c_double),
                 ("T_top", ctypes.c_double), ("grad_T", ctypes.c_double * 3),
                 ("grad_T_origin", ctypes.c_double * 3), ("eps_n", ctypes.c_double),
-                ("omega_high", ctypes.c_double), ("rk_isotropic_fd", ctypes.c_int32)]
+                ("omega_high", ctypes.c_double), ("rk_isotropic_fd", ctypes.c_int32),
+                ("T_bottom_amp", ctypes.c_double), ("T_bottom_waves", ctypes.c_int32)]
 
 
 class HeatSource(ctypes.Structure):
@@ -161,6 +162,8 @@ def make_params(src=None, **kw) -> Params:
             getattr(p, name)[:] = [float(v) for v in val]
         elif name in ("walls_z", "rk_isotropic_fd"):
             setattr(p, name, int(bool(val)))
+        elif name == "T_bottom_waves":
+            setattr(p, name, int(val))
         else:
             setattr(p, name, float(val))
     return p

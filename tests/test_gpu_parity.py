@@ -216,6 +216,21 @@ def test_conductivity_ratio_fp64(thermal, walls, iso):
         compare_all(d, o, w, TOL64, f"conductivity ratio {thermal} walls={walls} iso={iso} {kern}")
 
 
+@pytest.mark.parametrize("thermal,ratio", [("D3Q7", False), ("D3Q19", True), ("RK4", True), ("RK2", False)])
+def test_modulated_bottom_wall_fp64(thermal, ratio):
+    """Bottom wall at T_bottom + 0.3 cos(2 pi 2 (x + 1/2) / nx) (the heated
+    channel's wall): anti-bounce-back, the Dirichlet ghosts of the stencils
+    and the initial conduction profile all take the column's wall value."""
+    w = _ratio_workload(thermal) if ratio else ragged_workload(thermal, 15, walls=True)
+    w = w.replace(params=W.Params(**dict(w.params.__dict__, T_bottom_amp=0.3, T_bottom_waves=2)))
+    o = oracle_for(w)
+    o.step(10)
+    for kern in _kernels("fp64", 15, thermal):
+        d = gpu_domain(w, kernel=kern)
+        d.step(10)
+        compare_all(d, o, w, TOL64, f"modulated wall {thermal} ratio={ratio} {kern}")
+
+
 @pytest.mark.parametrize("precision,tol", [("fp32", 2e-4), ("fp16", 5e-2)])
 def test_conductivity_ratio_reduced_precision(precision, tol):
     """FP32 / FP16-storage runs of the ratio workload (D3Q7 and RK4) stay

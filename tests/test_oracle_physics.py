@@ -382,6 +382,25 @@ def test_two_layer_conduction_steady_state(thermal, tol):
     assert np.abs(o.macro()["u"]).max() < 1e-6
 
 
+@pytest.mark.parametrize("thermal,tol", [("D3Q7", 0.05), ("RK4", 0.03)])
+def test_modulated_wall_conduction_closed_form(thermal, tol):
+    """Bottom wall T_h + T_0 cos(omega x) (the heated channel's wall,
+    Sec. 3.1), top wall T_c, no flow: the steady state solves Laplace's
+    equation, T = T_h + (T_c - T_h) z / H + T_0 cos(omega x) sinh(omega (H - z))
+    / sinh(omega H), walls on the faces z = 0 and z = H, x at cell centres.
+    Second order in omega (the error falls 3.6x when omega halves); a
+    half-cell shift of x or a flipped amplitude is off by 0.4 or more."""
+    nx, nz = 32, 16
+    o = make(nx, 1, nz, thermal=thermal, alpha_L=0.2, alpha_H=0.2, sigma_T=0.0, walls_z=True,
+             T_bottom=20.0, T_top=10.0, T_bottom_amp=4.0, T_bottom_waves=1)
+    set_fields(o, 0.0, T=20.0 - 10.0 * o.Z / nz)
+    o.step(800)
+    w = 2 * math.pi / nx
+    exact = (20.0 - 10.0 * o.Z / nz
+             + 4.0 * np.cos(w * o.X) * np.sinh(w * (nz - o.Z)) / np.sinh(w * nz))
+    assert np.abs(o.macro()["T"] - exact).max() < tol
+
+
 def test_conductivity_ratio_lb_conserves_heat():
     """Periodic box at rest, alpha_H = alpha_L / 5 with a droplet-shaped phi:
     the per-cell relaxation rate leaves sum T unchanged (no sources)."""

@@ -52,6 +52,8 @@ class Params:
     eps_n: float = 1e-12         # regulariser of the interface normal
     omega_high: float = 1.0      # relaxation rate of central moments of order >= 3
     rk_isotropic_fd: bool = False  # RK path: isotropic D3Q27 operators instead of 7-point
+    T_bottom_amp: float = 0.0    # bottom wall T_bottom + T_bottom_amp cos(2 pi k x / nx)
+    T_bottom_waves: int = 0      # k (0: uniform bottom wall)
 
 
 @dataclass
