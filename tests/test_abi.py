@@ -87,3 +87,22 @@ def test_params_roundtrip(L):
     p = lbm.make_params(W.config2().params)
     assert p.walls_z == 1 and p.T_top == 0.5 and p.nu_L == 0.05
     assert p.omega_high == 1.0 and p.eps_n == 1e-12
+
+
+def test_header_is_plain_c_and_usable_from_c(L, tmp_path):
+    """include/lbm.h compiles as strict C99 and a C program linked against
+    liblbm.so runs the entry points that need no GPU."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lib_dir = os.path.join(ROOT, "paper_2401_03041_gb300")
+    exe = str(tmp_path / "abi_from_c")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                        "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "c", "abi_from_c.c"),
+                        "-o", exe, "-L", lib_dir, "-llbm", "-Wl,-rpath," + lib_dir, "-lm"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
