@@ -84,7 +84,7 @@ def central_moments(pdf: np.ndarray, u: np.ndarray, c: np.ndarray) -> np.ndarray
     for a in range(3):
         d = c[:, a].astype(float).reshape(shp) - u[a][None]
         powers.append((np.ones_like(d), d, d * d))
-    out = np.zeros((len(MOMENT_EXPONENTS),) + pdf.shape[1:])
+    out = np.zeros((len(MOMENT_EXPONENTS),) + pdf.shape[1:], dtype=np.result_type(pdf, u))
     for k, e in enumerate(MOMENT_EXPONENTS):
         out[k] = (pdf * powers[0][e[0]] * powers[1][e[1]] * powers[2][e[2]]).sum(axis=0)
     return out
@@ -111,7 +111,7 @@ def raw_from_central(kappa: np.ndarray, u: np.ndarray) -> np.ndarray:
     """Binomial shift back to raw moments:
     m_e = sum_{e' <= e} prod_a C(e_a, e'_a) u_a^(e_a - e'_a) kappa_e'."""
     upow = [(np.ones_like(u[a]), u[a], u[a] * u[a]) for a in range(3)]
-    m = np.zeros_like(kappa)
+    m = np.zeros(kappa.shape, dtype=np.result_type(kappa, u))
     for k, k2, b, d in _SHIFT_TERMS:
         m[k] += b * upow[0][d[0]] * upow[1][d[1]] * upow[2][d[2]] * kappa[k2]
     return m
@@ -126,7 +126,7 @@ def eq_scalar(psi, u, S):
     """h^eq / f^eq of Sec. 2.2 (Eq. for h_i^eq; same form for f^eq, Sec. 2.3):
     psi w_i [1 + c.u/c_s^2 + (c.u)^2/(2 c_s^4) - u.u/(2 c_s^2)]."""
     uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2]
-    out = np.empty((S.Q,) + psi.shape)
+    out = np.empty((S.Q,) + psi.shape, dtype=np.result_type(psi, u))
     for i in range(S.Q):
         cu = S.c[i, 0] * u[0] + S.c[i, 1] * u[1] + S.c[i, 2] * u[2]
         out[i] = S.w[i] * psi * (1.0 + cu / CS2 + cu * cu / (2 * CS2 * CS2) - uu / (2 * CS2))
@@ -137,7 +137,7 @@ def eq_hydro(p, u, S):
     """Incompressible (velocity-based) g^eq of Sec. 2.2:
     w_i (p* + [c.u/c_s^2 + (c.u)^2/(2 c_s^4) - u.u/(2 c_s^2)])."""
     uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2]
-    out = np.empty((S.Q,) + p.shape)
+    out = np.empty((S.Q,) + p.shape, dtype=np.result_type(p, u))
     for i in range(S.Q):
         cu = S.c[i, 0] * u[0] + S.c[i, 1] * u[1] + S.c[i, 2] * u[2]
         out[i] = S.w[i] * (p + cu / CS2 + cu * cu / (2 * CS2 * CS2) - uu / (2 * CS2))
@@ -146,7 +146,7 @@ def eq_hydro(p, u, S):
 
 def guo_source(u, a, S):
     """Guo source S_i = w_i [(c_i - u)/c_s^2 + (c_i.u) c_i / c_s^4] . a."""
-    out = np.empty((S.Q,) + u.shape[1:])
+    out = np.empty((S.Q,) + u.shape[1:], dtype=np.result_type(u, a))
     for i in range(S.Q):
         cu = S.c[i, 0] * u[0] + S.c[i, 1] * u[1] + S.c[i, 2] * u[2]
         acc = 0.0
@@ -166,7 +166,7 @@ def cm_collide(gs, geq, src, u, omega2, omega_high=1.0, omega_all=None):
     k = central_moments(gs, u, S27.c)
     keq = central_moments(geq, u, S27.c)
     kF = central_moments(src, u, S27.c)
-    post = np.empty_like(k)
+    post = np.empty(k.shape, dtype=np.result_type(k, keq, kF, omega2))
     for m, e in enumerate(MOMENT_EXPONENTS):
         order = int(e.sum())
         if omega_all is not None:
@@ -478,7 +478,7 @@ class OracleLBM:
         nrm = np.sqrt(m["g2"]) + p.eps_n
         Fphi = 4.0 * phi * (1.0 - phi) / p.xi * gphi / nrm
         heq = eq_scalar(phi, u, self.Sh)
-        h_new = np.empty_like(hs)
+        h_new = np.empty(hs.shape, dtype=np.result_type(hs, Fphi, heq))
         for i in range(self.Sh.Q):
             cF = self.Sh.c[i, 0] * Fphi[0] + self.Sh.c[i, 1] * Fphi[1] + self.Sh.c[i, 2] * Fphi[2]
             h_new[i] = hs[i] - w_phi * (hs[i] - heq[i]) + (1.0 - 0.5 * w_phi) * self.Sh.w[i] * cF
@@ -503,7 +503,7 @@ class OracleLBM:
                 gphi = m["gphi"]
                 src = src + (p.alpha_H - p.alpha_L) * (gphi[0] * G[0] + gphi[1] * G[1] + gphi[2] * G[2])
             feq = eq_scalar(m["T"], u, self.Sf)
-            f_new = np.empty_like(fs)
+            f_new = np.empty(fs.shape, dtype=np.result_type(fs, feq, src, w_T))
             for i in range(self.Sf.Q):
                 f_new[i] = fs[i] - w_T * (fs[i] - feq[i]) + self.Sf.w[i] * src
             self.f = f_new

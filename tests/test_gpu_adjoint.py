@@ -7,7 +7,8 @@ Checks, all in FP64:
     heat sources);
   * the exact gradient dJ/dI of the droplet-capture objective against central
     finite differences of the FP64 *oracle* (independent of the CUDA path) on
-    the 16^3 adjoint workload (40 steps);
+    the 16^3 adjoint workload (40 steps), and against the oracle's exact
+    complex-step derivatives (stored golden values);
   * on the full 64^3, 2000-step workload the exact linearisation diverges
     (the interface normal's derivative in far-field tails); the adjoint that
     holds the normal fixed where |4 phi (1 - phi) / xi| > 30 |grad phi| is
@@ -110,6 +111,24 @@ def test_adjoint_gradient_matches_oracle_finite_differences():
     err = np.abs(g - fd).max() / np.abs(fd).max()
     print("adjoint vs oracle FD", err, g[:4], fd[:4])
     assert err <= 1e-6
+
+
+def test_adjoint_gradient_matches_complex_step_oracle():
+    """16^3 adjoint workload, 40 steps: the GPU adjoint dJ/dI against the
+    exact derivatives of the FP64 oracle (complex-step, one complex oracle
+    run per patch; tests/golden/adjoint_cfg5_16cube_40steps.txt, written by
+    tests/golden/make_adjoint_golden.py), to 1e-7 of max |dJ/dI|."""
+    import os
+    golden = np.loadtxt(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                     "adjoint_cfg5_16cube_40steps.txt"), comments="#")
+    J_ref, g_ref = golden[0], golden[1:]
+    w = W.config5(n=16)
+    d = gpu_domain(w)
+    J, g = d.adjoint_run(40, 10, w.target)
+    assert abs(J - J_ref) <= 1e-11 * J_ref
+    err = np.abs(g - g_ref).max() / np.abs(g_ref).max()
+    print("adjoint vs complex-step oracle", err)
+    assert err <= 1e-7
 
 
 def test_adjoint_checkpoint_spacing_is_exact():
