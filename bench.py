@@ -68,10 +68,15 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_per_cell(precision: str, thermal: str, n: int):
-    """DRAM bytes per cell of the step kernel from the committed ncu summary
-    (one capture of this workload), or None if the kernel sources changed
-    since those counters were taken or the capture was of another workload."""
+def traffic_per_cell(precision: str, thermal: str):
+    """DRAM bytes per cell update of the step kernel from the committed ncu
+    record, with the lattice edge it was captured at, or None if the kernel
+    sources changed since those counters were taken or the record is of
+    another precision / thermal option.  The capture is of a lattice whose
+    state is far larger than L2 (>= 128^3), so the DRAM bytes per cell carry
+    over to larger lattices of the same workload (the kernel's traffic is a
+    fixed amount per cell plus per-tile halo re-reads that scale the same
+    way)."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     try:
         with open(path) as fh:
@@ -80,9 +85,31 @@ def traffic_per_cell(precision: str, thermal: str, n: int):
         return None
     if d.get("source_sha") != kernel_source_sha():
         return None
-    if (d.get("precision"), d.get("thermal"), d.get("n")) != (precision, thermal, n):
+    if (d.get("precision"), d.get("thermal")) != (precision, thermal) or int(d.get("n", 0)) < 128:
         return None
-    return float(d["dram_bytes_per_cell"])
+    return float(d["dram_bytes_per_cell"]), int(d["n"])
+
+
+def cpu_model() -> str:
+    """Host CPU model name (lscpu, else /proc/cpuinfo, else the platform)."""
+    import platform
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                v = line.split(":", 1)[1].strip()
+                if v and not v.isdigit():
+                    return v
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
 
 
 class ClockSampler:
@@ -136,12 +163,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_sample(seconds: float = 15.0, n: int = 48, thermal: str = "D3Q7"):
-    """Time the FP64 oracle, as it stands, on an n^3 crop of the throughput
-    workload in a fresh single-threaded process (spawned, no CUDA)."""
-    code = f"""
+_ORACLE_TIMER = """
 import os, sys, time, json
-sys.path.insert(0, {ROOT!r})
+sys.path.insert(0, {root!r})
 import workloads as W
 from oracle.model import build
 w = W.crop(W.config4({thermal!r}, 'fp64'), {n}, {n}, {n})
@@ -154,13 +178,31 @@ dt = time.perf_counter() - t0
 print(json.dumps({{"mlups": w.cells * steps / dt / 1e6, "steps": steps, "seconds": dt,
                    "cells": w.cells, "name": w.name}}))
 """
+
+
+def cpu_oracle_sample(seconds: float = 15.0, n: int = 48, thermal: str = "D3Q7", procs: int = 1):
+    """Time the FP64 oracle, as it stands, on an n^3 crop of the throughput
+    workload: ``procs`` fresh single-threaded processes (no CUDA in them) each
+    step their own copy of the crop at the same time, one per host core (numpy
+    runs one thread per process), like the GPU replicas.  Throughput is the
+    sum over the processes of cells x steps / their own time."""
+    code = _ORACLE_TIMER.format(root=ROOT, thermal=thermal, n=n, seconds=seconds)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
                MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                       timeout=600)
-    if r.returncode != 0:
-        raise RuntimeError("oracle timing failed: " + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                           stderr=subprocess.PIPE, text=True, env=env) for _ in range(procs)]
+    outs = []
+    for p in ps:
+        out, err = p.communicate(timeout=600)
+        if p.returncode != 0:
+            raise RuntimeError("oracle timing failed: " + err[-2000:])
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    r = dict(outs[0])
+    r["mlups"] = sum(o["mlups"] for o in outs)
+    r["steps"] = sum(o["steps"] for o in outs)
+    r["seconds"] = max(o["seconds"] for o in outs)
+    r["procs"] = procs
+    return r
 
 
 def max_over_ranks(v, world: int, device=None):
@@ -235,11 +277,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-cost leg")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the thermal option x storage sweep (kernel-only timing of each)")
+    ap.add_argument("--sweep-steps", type=int, default=8)
     ap.add_argument("--kernel-only", action="store_true",
-                    help="time the step kernel only (no CPU, e2e, FP64 or error legs; for profiling)")
+                    help="time the step kernel only (no CPU, e2e, FP64, sweep or error legs; for profiling)")
     args = ap.parse_args()
     if args.kernel_only:
-        args.no_cpu = args.no_fp64 = args.no_adjoint = True
+        args.no_cpu = args.no_fp64 = args.no_adjoint = args.no_sweep = True
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
@@ -267,12 +312,17 @@ def main():
         return max_over_ranks(v, world, dev)
 
     # CPU baseline first (spawned subprocess; no CUDA in it)
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and not args.no_cpu:
         try:
-            cpu = cpu_oracle_sample(seconds=15.0, n=48, thermal=args.thermal)
+            cpu = cpu_oracle_sample(seconds=12.0, n=48, thermal=args.thermal)
         except Exception as e:  # reported, not fatal
             cpu = {"error": str(e)[:300]}
+        try:
+            cpu_all = cpu_oracle_sample(seconds=12.0, n=48, thermal=args.thermal,
+                                        procs=max(1, os.cpu_count() or 1))
+        except Exception as e:
+            cpu_all = {"error": str(e)[:300]}
 
     w = W.config4(args.thermal, args.precision, n=args.n)
 
@@ -394,26 +444,64 @@ def main():
                        "over the plain forward run of the same steps; FP64",
                "J": J5, "grad_inf": float(np.abs(g5).max())}
 
-    # ---------------- stated error: reduced precision vs FP64 on the 32^3 droplet
+    # ---------------- stated error: FP32 and FP16 storage vs FP64 on a bulk-kernel
+    # lattice of the same workload (128^3, 8 droplets, 200 steps); the FP64
+    # bulk kernel equals the oracle to <= 1e-11 over 200 steps (parity tests)
     err = None
     if rank == 0 and not args.kernel_only:
-        c1 = W.config1()
+        ce = W.config4(args.thermal, "fp64", n=128, n_droplets=8)
+        esteps = 200
         res = {}
-        for prec in ("fp64", args.precision):
-            dd = lbm.Domain(c1.nx, c1.ny, c1.nz, prec, c1.thermal, c1.q_phase, device=dev)
-            dd.set_params(c1.params)
-            dd.init_droplets(c1.droplets)
-            dd.step(c1.steps)
+        for prec in ("fp64", "fp32", "fp16"):
+            dd = lbm.Domain(ce.nx, ce.ny, ce.nz, prec, ce.thermal, ce.q_phase, device=dev)
+            dd.set_params(ce.params)
+            dd.init_droplets(ce.droplets)
+            kern = dd.kernel_info()["kernel"]
+            dd.step(esteps)
             f = dd.fields(dtype="f64")
-            res[prec] = ({k: v.detach().cpu().numpy() for k, v in f.items()}, dd.diagnostics())
+            res[prec] = ({k: v.detach().cpu().numpy() for k, v in f.items()}, dd.diagnostics(), kern)
             dd.close()
-        (a, da), (b, db) = res[args.precision], res["fp64"]
-        du = a["u"] - b["u"]
-        err = {"workload": "cfg1 32^3 droplet, 200 steps, vs GPU FP64 (= oracle to 3e-13)",
-               "phi_linf": float(np.abs(a["phi"] - b["phi"]).max()),
-               "u_l2_rel": float(math.sqrt((du ** 2).sum() / (b["u"] ** 2).sum())),
-               "mass_rel": abs(da["mass"] - db["mass"]) / db["mass"],
-               "centroid_abs": max(abs(x - y) for x, y in zip(da["centroid"], db["centroid"]))}
+        b, db, kb = res["fp64"]
+        err = {"workload": f"{ce.name}, {esteps} steps, {ce.thermal}; reduced storage vs the FP64 "
+                           f"GPU run (FP64 bulk kernel = oracle to <= 1e-11 over 200 steps)",
+               "kernel_fp64": kb}
+        for prec in ("fp32", "fp16"):
+            a, da, ka = res[prec]
+            du = a["u"] - b["u"]
+            err[prec] = {"kernel": ka,
+                         "phi_linf": float(np.abs(a["phi"] - b["phi"]).max()),
+                         "u_l2_rel": float(math.sqrt((du ** 2).sum() / (b["u"] ** 2).sum())),
+                         "T_linf": float(np.abs(a["T"] - b["T"]).max()),
+                         "mass_rel": abs(da["mass"] - db["mass"]) / db["mass"],
+                         "centroid_abs": max(abs(x - y) for x, y in zip(da["centroid"], db["centroid"]))}
+
+    # ---------------- sweep: every thermal option x storage precision at the
+    # headline lattice, step kernel timed alone (CUDA events around each launch)
+    sweep = None
+    if not args.no_sweep:
+        sweep = []
+        peak_s, _ = peaks()
+        for prec in ("fp32", "fp16", "fp64"):
+            for th in ("D3Q7", "D3Q15", "D3Q19", "D3Q27", "RK2", "RK4"):
+                ws = W.config4(th, prec, n=args.n)
+                nst = args.sweep_steps if prec != "fp64" else 2
+                ds = lbm.Domain(ws.nx, ws.ny, ws.nz, prec, ws.thermal, ws.q_phase, device=dev)
+                ds.set_params(ws.params)
+                ds.init_droplets(ws.droplets)
+                ssecs, _, kser = timed_steps(ds, nst, 3)
+                ssecs = reduce_max(ssecs)
+                kser = reduce_max(kser) if kser else None
+                bpc_s = bytes_per_cell(prec, th, ws.q_phase)
+                ach = bpc_s * ws.cells / kser / 1e9 if kser else None
+                sweep.append({"precision": prec, "thermal": th, "kernel": ds.kernel_info()["kernel"],
+                              "mlups": job_mlups(ws.cells, nst, world, ssecs),
+                              "step_ms": ssecs / nst * 1e3,
+                              "kernel_ms": kser * 1e3 if kser else None,
+                              "bytes_per_cell": bpc_s, "achieved_gbs": ach,
+                              "frac": ach / peak_s if ach else None, "steps": nst})
+                ds.close()
+                del ds
+                torch.cuda.empty_cache()
 
     if rank != 0:
         if world > 1:
@@ -426,7 +514,8 @@ def main():
     # the dominant kernel's own average launch time (CUDA events around each
     # step-kernel launch on the domain's stream, inside the timed region)
     achieved = bpc * cells / kernel_secs / 1e9 if (bpc and kernel_secs) else None
-    tpc = traffic_per_cell(args.precision, w.thermal, args.n)
+    tr = traffic_per_cell(args.precision, w.thermal)
+    tpc, tr_n = tr if tr else (None, None)
     line = {
         "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
@@ -445,12 +534,22 @@ def main():
                      "kernel_ms_per_launch": kernel_secs * 1e3 if kernel_secs else None,
                      "step_ms": per_step * 1e3,
                      "traffic": tpc * cells if tpc else None,
+                     "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of one step-kernel "
+                                        f"launch at {tr_n}^3 (profiles/step_kernel_traffic.json): "
+                                        f"{tpc:.1f} B/cell, scaled by the cell count"
+                                        if tpc else "no ncu record for the current kernel sources"),
                      "kernel": "lbm::step_bulk_kernel (fused h/g/f stream-collide, tensor-TMA staging, "
                                "two threads per cell)"
                                if kinfo["kernel"] == "bulk" else "lbm::step_kernel (fused, generic)"},
         "cpu_baseline": ({"value": cpu["mlups"], "unit": "MLUPS", "cores": 1, "kind": "oracle",
                           "sample": f"{cpu['name']}: {cpu['steps']} FP64 numpy oracle steps in "
-                                    f"{cpu['seconds']:.1f} s, single thread"}
+                                    f"{cpu['seconds']:.1f} s, single thread",
+                          "cpu_model": cpu_model(),
+                          "all_cores": ({"value": cpu_all["mlups"], "unit": "MLUPS", "cores": cpu_all["procs"],
+                                         "sample": f"{cpu_all['procs']} single-threaded oracle processes, each "
+                                                   f"on its own copy of {cpu_all['name']}, at the same time: "
+                                                   f"{cpu_all['steps']} steps in {cpu_all['seconds']:.1f} s"}
+                                        if cpu_all and "mlups" in cpu_all else cpu_all)}
                          if cpu and "mlups" in cpu else cpu),
         "e2e": e2e,
         "gpu_launches": args.steps * launches_per_step,
@@ -458,6 +557,7 @@ def main():
         "fp64": fp64,
         "fp32_vs_fp64": fp64 and {"speedup": mlups / fp64["mlups"]},
         "error_vs_fp64": err,
+        "sweep": sweep,
         "final_diag": {"mass": diag_final["mass"], "level": diag_final["level"]},
         "clocks": clocks,
     }

@@ -317,11 +317,15 @@ lbm_status lbm_profile_read(lbm_domain* dom, double* ms_total, int32_t* launches
  *   out_host[0] = sum psi, out_host[1..3] = sum psi (x + 1/2), sum psi
  *   (y + 1/2), sum psi (z + 1/2) over the [z][y][x] field (cell-centred
  *   coordinates), accumulated in FP64 in a fixed order (deterministic).
- *   field:  device pointer to nx * ny * nz values, double (dtype 0) or
- *           float (dtype 1).  nz <= LBM_MOMENTS_MAX_PLANES and nx * ny < 2^31,
- *           else LBM_ERR_ARG (nothing is launched).
- *   stream: cudaStream_t (NULL = legacy default stream).  Two kernels and a
- *           32-byte copy are enqueued on it, then it is synchronised.
+ *   field:  pointer to nx * ny * nz values, double (dtype 0) or float
+ *           (dtype 1), in device (or managed) memory of the CURRENT device;
+ *           a host pointer or memory of another device is rejected with
+ *           LBM_ERR_ARG before anything is launched.  nz <=
+ *           LBM_MOMENTS_MAX_PLANES and nx * ny < 2^31, else LBM_ERR_ARG
+ *           (nothing is launched).
+ *   stream: cudaStream_t of the current device (NULL = legacy default
+ *           stream); a stream of another device is LBM_ERR_ARG.  Two kernels
+ *           and a 32-byte copy are enqueued on it, then it is synchronised.
  *   out_host: 4 doubles of host memory.
  * Why it exists: every other call that needs scratch memory takes it from the
  * domain's workspace.  Callers that must not allocate device memory at call
@@ -331,7 +335,8 @@ lbm_status lbm_profile_read(lbm_domain* dom, double* ms_total, int32_t* launches
  * ((LBM_MOMENTS_MAX_PLANES + 1) x 4 doubles), whose contents never need to
  * start at zero (every call writes each slot before reading it).
  * The first call on a device looks up that array's device address, with the
- * device current; make it before any stream capture on that device.  Calls
+ * device current; make it before any stream capture on that device.  A
+ * lookup that fails is reported (LBM_ERR_CUDA) and retried by the next call.  Calls
  * that overlap in time on one device (from several host threads, or on
  * streams without ordering between them) share the array and race: serialise
  * them.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */

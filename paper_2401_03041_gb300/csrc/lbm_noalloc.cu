@@ -6,8 +6,9 @@
 // applied to a field in memory.  Its intermediate partials (one group of four
 // per z plane) and its four results live in a fixed array compiled into the
 // library, not in a workspace, so the call needs no allocation by the library
-// or by the caller.  The device address of that array is looked up once per
-// device, with that device current, on the first call made on it.
+// or by the caller.  The device address of that array is looked up with the
+// device current, on the first call made on it; a failed lookup is not kept,
+// so a later call on that device tries again.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -25,9 +26,23 @@ constexpr int kMaxDevices = 64;
 // need to start at zero.
 static __device__ __align__(256) double g_moment_scratch[(LBM_MOMENTS_MAX_PLANES + 1) * 4];
 
+// Per-device address of g_moment_scratch (nullptr until a lookup succeeded).
 double* g_scratch_addr[kMaxDevices];
-cudaError_t g_scratch_err[kMaxDevices];
-std::once_flag g_scratch_once[kMaxDevices];
+std::mutex g_scratch_mutex;
+
+// Device address of the scratch array on device dev (current), looked up
+// once; errors are returned, not remembered.
+cudaError_t scratch_for(int dev, double** out) {
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_moment_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return cudaSuccess;
+}
 
 // Fixed-order sum of one value over a block: warp shuffles, then the warps'
 // totals in warp order.
@@ -102,16 +117,30 @@ extern "C" lbm_status lbm_field_moments(const void* field, int dtype, int nx, in
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return lbm::set_error(LBM_ERR_CUDA, cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return lbm::set_error(LBM_ERR_ARG, "lbm_field_moments: device index too large");
-  // set-up, once per device, with that device current
-  std::call_once(g_scratch_once[dev], [dev] {
-    g_scratch_err[dev] = cudaGetSymbolAddress(reinterpret_cast<void**>(&g_scratch_addr[dev]), g_moment_scratch);
-  });
-  if (g_scratch_err[dev] != cudaSuccess)
-    return lbm::set_error(LBM_ERR_CUDA, cudaGetErrorString(g_scratch_err[dev]));
-  double* scratch = g_scratch_addr[dev];
+  // the field must be device (or managed) memory of the current device: the
+  // kernels run there and read it directly
+  cudaPointerAttributes pa{};
+  e = cudaPointerGetAttributes(&pa, field);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return lbm::set_error(LBM_ERR_ARG, "lbm_field_moments: field is not a CUDA pointer");
+  }
+  if ((pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) || pa.device != dev)
+    return lbm::set_error(LBM_ERR_ARG,
+                          "lbm_field_moments: field must be device memory of the current device");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (st) {
+    int sdev = -1;
+    e = cudaStreamGetDevice(st, &sdev);
+    if (e != cudaSuccess) return lbm::set_error(LBM_ERR_CUDA, cudaGetErrorString(e));
+    if (sdev != dev) return lbm::set_error(LBM_ERR_ARG, "lbm_field_moments: stream belongs to another device");
+  }
+  // set-up on the first call on this device, with that device current
+  double* scratch = nullptr;
+  e = scratch_for(dev, &scratch);
+  if (e != cudaSuccess) return lbm::set_error(LBM_ERR_CUDA, cudaGetErrorString(e));
   double* results = scratch + 4 * LBM_MOMENTS_MAX_PLANES;
 
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   plane_moments_kernel<<<nz, kThreads, 0, st>>>(field, dtype, nx, ny, scratch);
   e = cudaGetLastError();
   if (e != cudaSuccess) return lbm::set_error(LBM_ERR_CUDA, cudaGetErrorString(e));

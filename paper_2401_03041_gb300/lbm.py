@@ -170,21 +170,27 @@ def make_params(src=None, **kw) -> Params:
 
 
 def field_moments(field, stream=None):
-    """FP64 (sum psi, sum psi x, sum psi y, sum psi z) of a contiguous CUDA
-    tensor shaped [..., nz, ny, nx] (float64 or float32), through the
-    allocation-free entry point; ``stream`` is a torch stream (default: the
-    current stream)."""
+    """FP64 (sum psi, sum psi x, sum psi y, sum psi z) of one contiguous CUDA
+    tensor shaped [nz, ny, nx] (leading dimensions of size 1 allowed; float64
+    or float32), through the allocation-free entry point; ``stream`` is a
+    torch stream on the field's device (default: that device's current
+    stream).  The call runs with the field's device current."""
     import torch
     if not field.is_cuda or not field.is_contiguous():
         raise ValueError("field must be a contiguous CUDA tensor")
     if field.dtype not in (torch.float64, torch.float32):
         raise ValueError("field must be float64 or float32")
+    if field.dim() < 3 or any(s != 1 for s in field.shape[:-3]):
+        raise ValueError("field must be shaped [nz, ny, nx] (leading dimensions of size 1 only)")
     nz, ny, nx = field.shape[-3:]
-    st = stream if stream is not None else torch.cuda.current_stream(field.device)
-    out = (ctypes.c_double * 4)()
-    _check("lbm_field_moments", lib().lbm_field_moments(
-        ctypes.c_void_p(field.data_ptr()), 0 if field.dtype == torch.float64 else 1,
-        int(nx), int(ny), int(nz), ctypes.c_void_p(st.cuda_stream), out))
+    with torch.cuda.device(field.device):
+        st = stream if stream is not None else torch.cuda.current_stream(field.device)
+        if st.device != field.device:
+            raise ValueError("stream must belong to the field's device")
+        out = (ctypes.c_double * 4)()
+        _check("lbm_field_moments", lib().lbm_field_moments(
+            ctypes.c_void_p(field.data_ptr()), 0 if field.dtype == torch.float64 else 1,
+            int(nx), int(ny), int(nz), ctypes.c_void_p(st.cuda_stream), out))
     return tuple(out)
 
 

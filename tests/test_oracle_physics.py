@@ -91,6 +91,30 @@ def test_uniform_body_force_momentum_growth():
             assert abs(j[a].sum() - n * g[a] * 64) < 1e-16
 
 
+@pytest.mark.parametrize("rho", [1.0, 2.5])
+def test_kinetic_energy_of_uniform_flow(rho):
+    """The kinetic-energy diagnostic (a10, 1/2 sum rho |u|^2) of a uniform
+    flow u = U at density rho over N cells is exactly 1/2 rho |U|^2 N.  A
+    droplet is present (phi varies) but sigma = 0 and no gravity, so no force
+    acts and u = U in every cell; a missing 1/2, a missing rho or a wrong u
+    (e.g. a half-force shift or a lost component) all change the value.  The
+    box is periodic: the pulled g of a uniform equilibrium is that
+    equilibrium again, so the level's velocity is exactly U."""
+    U = (0.012, -0.021, 0.0047)
+    nx, ny, nz = 10, 8, 6
+    o = make(nx, ny, nz, rho_L=rho, rho_H=rho, sigma_ref=0.0, sigma_T=0.0)
+    X = (np.arange(nx) + 0.5)[None, None, :]
+    Y = (np.arange(ny) + 0.5)[None, :, None]
+    Z = (np.arange(nz) + 0.5)[:, None, None]
+    r = np.sqrt((X - nx / 2) ** 2 + (Y - ny / 2) ** 2 + (Z - nz / 2) ** 2)
+    phi = 0.5 * (1.0 + np.tanh(2.0 * (2.5 - r) / 2.0))
+    set_fields(o, phi, u=np.array(U)[:, None, None, None])
+    d = o.diagnostics()
+    N = nx * ny * nz
+    exact = 0.5 * rho * (U[0] ** 2 + U[1] ** 2 + U[2] ** 2) * N
+    assert abs(d["kinetic"] - exact) <= 1e-13 * exact, (d["kinetic"], exact)
+
+
 @pytest.mark.parametrize("thermal", ["D3Q7", "D3Q19", "RK2", "RK4"])
 def test_uniform_heat_source(thermal):
     o = make(4, 3, 5, thermal=thermal)
