@@ -36,13 +36,27 @@ FIELD_BYTES = {"fp64": 8, "fp32": 4, "fp16": 4}
 RK_FIELDS = {"RK2": 11, "RK4": 29}
 
 
+# Of those, the step kernel itself moves: RK2 T read, u (3) and S1 written = 5;
+# RK4 the same plus acc written = 6 (the rest belongs to the stage kernels).
+RK_FIELDS_STEP_KERNEL = {"RK2": 5, "RK4": 6}
+
+
 def bytes_per_cell(precision: str, thermal: str, q_phase: int = 15) -> int:
-    """Algorithmic bytes per cell update: every PDF read once and written once,
-    plus the stage fields of the RK energy solvers; halo re-reads (L2) and
-    derived fields (phi, T, u computed in the kernel) are not counted."""
+    """Algorithmic bytes per cell update of a whole step: every PDF read once
+    and written once, plus the stage fields of the RK energy solvers; halo
+    re-reads (L2) and derived fields (phi, T, u computed in the kernel) are
+    not counted."""
     qf = int(thermal[3:]) if thermal.startswith("D3Q") else 0
     pdf = 2 * (q_phase + 27 + qf) * STORE_BYTES[precision]
     return pdf + RK_FIELDS.get(thermal, 0) * FIELD_BYTES[precision]
+
+
+def step_kernel_bytes_per_cell(precision: str, thermal: str, q_phase: int = 15) -> int:
+    """Algorithmic bytes per cell of the step kernel alone (the RK stage
+    kernels' field traffic excluded)."""
+    qf = int(thermal[3:]) if thermal.startswith("D3Q") else 0
+    pdf = 2 * (q_phase + 27 + qf) * STORE_BYTES[precision]
+    return pdf + RK_FIELDS_STEP_KERNEL.get(thermal, 0) * FIELD_BYTES[precision]
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -68,16 +82,16 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_per_cell(precision: str, thermal: str):
-    """DRAM bytes per cell update of the step kernel from the committed ncu
-    record, with the lattice edge it was captured at, or None if the kernel
-    sources changed since those counters were taken or the record is of
-    another precision / thermal option.  The capture is of a lattice whose
-    state is far larger than L2 (>= 128^3), so the DRAM bytes per cell carry
-    over to larger lattices of the same workload (the kernel's traffic is a
-    fixed amount per cell plus per-tile halo re-reads that scale the same
-    way)."""
-    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+# FP64 peak of the GB300 (nominal): 152 SMs x 2 FP64 FMA lanes per cycle x 2 FLOP
+# per FMA x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def counters_record(precision: str, thermal: str):
+    """The committed ncu counters of one step-kernel launch for this precision
+    and thermal option (profiles/step_kernel_counters.json), or None if the
+    kernel sources changed since they were taken."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_counters.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
@@ -85,9 +99,24 @@ def traffic_per_cell(precision: str, thermal: str):
         return None
     if d.get("source_sha") != kernel_source_sha():
         return None
-    if (d.get("precision"), d.get("thermal")) != (precision, thermal) or int(d.get("n", 0)) < 128:
+    for r in d.get("records", []):
+        if (r.get("precision"), r.get("thermal")) == (precision, thermal):
+            return r
+    return None
+
+
+def traffic_per_cell(precision: str, thermal: str):
+    """DRAM bytes per cell update of the step kernel from the committed ncu
+    record, with the lattice edge it was captured at, or None if the kernel
+    sources changed since those counters were taken.  The capture is of a
+    lattice whose state is far larger than L2 (>= 128^3), so the DRAM bytes
+    per cell carry over to larger lattices of the same workload (the kernel's
+    traffic is a fixed amount per cell plus per-tile halo re-reads that scale
+    the same way)."""
+    r = counters_record(precision, thermal)
+    if not r or "dram_bytes_per_cell" not in r or int(r.get("n", 0)) < 128:
         return None
-    return float(d["dram_bytes_per_cell"]), int(d["n"])
+    return float(r["dram_bytes_per_cell"]), int(r["n"])
 
 
 def cpu_model() -> str:
@@ -402,10 +431,28 @@ def main():
     fp64 = None
     if not args.no_fp64 and args.precision != "fp64":
         d64 = make_domain("fp64")
-        s64, _, _ = timed_steps(d64, args.fp64_steps, 3)
+        s64, _, k64 = timed_steps(d64, args.fp64_steps, 3)
         s64 = reduce_max(s64)
+        k64 = reduce_max(k64) if k64 else None
         fp64 = {"mlups": cells * args.fp64_steps * world / s64 / 1e6,
-                "ms_per_step": s64 / args.fp64_steps * 1e3, "steps": args.fp64_steps}
+                "ms_per_step": s64 / args.fp64_steps * 1e3, "steps": args.fp64_steps,
+                "kernel_ms_per_launch": k64 * 1e3 if k64 else None}
+        rec = counters_record("fp64", w.thermal)
+        if rec and k64:
+            # FP64 is bound by the FP64 pipe: FLOPs and FP64 instructions per
+            # cell from the ncu record, against the pipe's nominal rate
+            flop = rec["fp64_flop_per_cell"]
+            inst = rec["fp64_inst_per_cell"]
+            fp64["roofline"] = {
+                "bound": "alu", "unit": "TFLOP/s",
+                "achieved": flop * cells / k64 / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "frac": flop * cells / k64 / 1e12 / FP64_PEAK_TFLOPS,
+                "fp64_inst_frac": inst * cells / k64 / (FP64_PEAK_TFLOPS * 1e12 / 2),
+                "flop_per_cell": flop, "fp64_inst_per_cell": inst,
+                "source": f"ncu FP64 instruction counters of one step-kernel launch at {rec['n']}^3 "
+                          f"(profiles/step_kernel_counters.json)",
+                "peak_kind": "nominal: 152 SMs x 2 FP64 FMA lanes per cycle x 2 FLOP x 2.07 GHz "
+                             "(no measured FP64 peak on this pool)"}
         del d64
         torch.cuda.empty_cache()
 
@@ -492,13 +539,16 @@ def main():
                 ssecs = reduce_max(ssecs)
                 kser = reduce_max(kser) if kser else None
                 bpc_s = bytes_per_cell(prec, th, ws.q_phase)
-                ach = bpc_s * ws.cells / kser / 1e9 if kser else None
+                bpk = step_kernel_bytes_per_cell(prec, th, ws.q_phase)
+                ach = bpk * ws.cells / kser / 1e9 if kser else None
+                step_gbs = bpc_s * ws.cells * nst / ssecs / 1e9
                 sweep.append({"precision": prec, "thermal": th, "kernel": ds.kernel_info()["kernel"],
                               "mlups": job_mlups(ws.cells, nst, world, ssecs),
                               "step_ms": ssecs / nst * 1e3,
                               "kernel_ms": kser * 1e3 if kser else None,
-                              "bytes_per_cell": bpc_s, "achieved_gbs": ach,
-                              "frac": ach / peak_s if ach else None, "steps": nst})
+                              "bytes_per_cell": bpc_s, "step_kernel_bytes_per_cell": bpk,
+                              "achieved_gbs": ach, "frac": ach / peak_s if ach else None,
+                              "step_frac": step_gbs / peak_s, "steps": nst})
                 ds.close()
                 del ds
                 torch.cuda.empty_cache()
@@ -510,7 +560,7 @@ def main():
         return 0
 
     peak, peak_kind = peaks()
-    bpc = bytes_per_cell(args.precision, w.thermal, w.q_phase)
+    bpc = step_kernel_bytes_per_cell(args.precision, w.thermal, w.q_phase)
     # the dominant kernel's own average launch time (CUDA events around each
     # step-kernel launch on the domain's stream, inside the timed region)
     achieved = bpc * cells / kernel_secs / 1e9 if (bpc and kernel_secs) else None
@@ -535,7 +585,7 @@ def main():
                      "step_ms": per_step * 1e3,
                      "traffic": tpc * cells if tpc else None,
                      "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of one step-kernel "
-                                        f"launch at {tr_n}^3 (profiles/step_kernel_traffic.json): "
+                                        f"launch at {tr_n}^3 (profiles/step_kernel_counters.json): "
                                         f"{tpc:.1f} B/cell, scaled by the cell count"
                                         if tpc else "no ncu record for the current kernel sources"),
                      "kernel": "lbm::step_bulk_kernel (fused h/g/f stream-collide, tensor-TMA staging, "

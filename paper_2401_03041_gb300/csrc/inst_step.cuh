@@ -11,7 +11,7 @@ namespace lbm {
 
 template <class S, int QH, int QF>
 void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A, const TMaps& maps,
-                 dim3 grid, int zchunk, int mode, int use_bulk, cudaStream_t st) {
+                 dim3 grid, int zchunk, const BulkSched& sched, int mode, int use_bulk, cudaStream_t st) {
   constexpr size_t bytes = BulkSmem<S, QH, QF>::bytes;
   if constexpr (bytes <= kMaxDynSmem) {
     if (use_bulk) {
@@ -23,12 +23,13 @@ void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                              (int)bytes);
         attr_set = true;
       }
+      const dim3 bgrid((unsigned)bulk_sched_blocks(sched));
       if (P.alpha_ratio || P.tw_waves)
-        step_bulk_kernel<S, QH, QF, true><<<grid, BulkSmem<S, QH, QF>::G::NTHR, bytes, st>>>(
-            P, A, maps.h, maps.g, maps.f, zchunk, mode);
+        step_bulk_kernel<S, QH, QF, true><<<bgrid, BulkSmem<S, QH, QF>::G::NTHR, bytes, st>>>(
+            P, A, maps.h, maps.g, maps.f, sched, mode);
       else
-        step_bulk_kernel<S, QH, QF, false><<<grid, BulkSmem<S, QH, QF>::G::NTHR, bytes, st>>>(
-            P, A, maps.h, maps.g, maps.f, zchunk, mode);
+        step_bulk_kernel<S, QH, QF, false><<<bgrid, BulkSmem<S, QH, QF>::G::NTHR, bytes, st>>>(
+            P, A, maps.h, maps.g, maps.f, sched, mode);
       return;
     }
   }
@@ -46,7 +47,8 @@ void launch_init(const DevParams& P, const double* drops, int nd, S* h, S* g, S*
 #define LBM_INST(QF)                                                                          \
   template void launch_step<LBM_S, LBM_QH, QF>(const DevParams&,                              \
                                                const StepPtrs<LBM_S, Store<LBM_S>::R>&,       \
-                                               const TMaps&, dim3, int, int, int, cudaStream_t); \
+                                               const TMaps&, dim3, int, const BulkSched&, int, int, \
+                                               cudaStream_t);                                 \
   template void launch_init<LBM_S, LBM_QH, QF>(const DevParams&, const double*, int, LBM_S*,  \
                                                LBM_S*, LBM_S*, Store<LBM_S>::R*, cudaStream_t);
 LBM_INST(0)

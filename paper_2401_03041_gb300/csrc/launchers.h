@@ -17,9 +17,11 @@ struct TMaps {
   CUtensorMap h, g, f;
 };
 
+// grid / zchunk: the generic kernel's launch (TX x TY tiles, z-chunks);
+// sched: the bulk kernel's work assignment (one-dimensional grid).
 template <class S, int QH, int QF>
 void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A, const TMaps& maps,
-                 dim3 grid, int zchunk, int mode, int use_bulk, cudaStream_t st);
+                 dim3 grid, int zchunk, const BulkSched& sched, int mode, int use_bulk, cudaStream_t st);
 
 // Refresh the periodic ghost cells of nq consecutive padded directions at buf.
 template <class S>

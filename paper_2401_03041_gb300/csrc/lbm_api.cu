@@ -52,12 +52,14 @@ struct Layout {
   size_t h[2], g[2], f[2], T, u, sa, sb, acc, phi, partials, diag, drops, errflag, total;
 };
 
-// Launch geometry of the step kernel: TX x rows columns, z split into chunks.
+// Launch geometry of the step kernel: TX x rows columns, z split into chunks;
+// the bulk kernel's grid is one-dimensional (sched, see BulkSched).
 struct Geometry {
-  dim3 grid;
+  dim3 grid;       // generic kernel: (tiles x, tiles y, chunks); bulk: the same counts (reported only)
   int zchunk;
-  int nblocks;
-  int bulk;  // 1: bulk kernel (tensor-TMA staging), 0: generic kernel
+  int nblocks;     // blocks of one launch (diagnostics partials)
+  int bulk;        // 1: bulk kernel (tensor-TMA staging), 0: generic kernel
+  BulkSched sched;
 };
 
 int thermal_q(lbm_thermal th);
@@ -73,7 +75,45 @@ bool bulk_ok(int nx, int ny, lbm_precision prec, int qh, int qf) {
   return bulk_smem_bytes((int)prec, qh, qf) <= kMaxDynSmem;
 }
 
-Geometry geometry(int nx, int ny, int nz, lbm_precision prec, int qh, int qf, bool allow_bulk = true) {
+// Bulk kernel: one CTA per SM.  The schedule minimises the modelled time of
+// the launch, (waves of whole units) x (planes + prologue) + (waves of tail
+// pieces) x (planes / npiece + prologue), over the chunk count (>= 16 planes
+// per chunk) and the tail split (>= 8 planes per piece); the prologue (three
+// h/f stages and one g stage before the first plane) costs about two planes.
+BulkSched bulk_schedule(int bx, int by, int nz, int sms, int forced_zchunk) {
+  const long long cols = (long long)bx * by;
+  BulkSched best{bx, by, 1, nz, (int)cols, 1};
+  if (forced_zchunk > 0) {
+    best.zchunk = forced_zchunk;
+    best.nchunk = (nz + forced_zchunk - 1) / forced_zchunk;
+    best.nfull = (int)(cols * best.nchunk);
+    return best;
+  }
+  const double prologue = 2.0;
+  double best_cost = 1e300;
+  const int max_chunks = nz / 16 > 1 ? nz / 16 : 1;
+  for (int k = 1; k <= max_chunks; ++k) {
+    const int zc = (nz + k - 1) / k;
+    const int nchunk = (nz + zc - 1) / zc;
+    const long long units = cols * nchunk;
+    const long long full_waves = units / sms;
+    const long long rem = units - full_waves * sms;
+    for (int p = 1; p <= 8; ++p) {
+      if (p > 1 && (rem == 0 || zc / p < 8)) break;
+      double cost = (double)full_waves * (zc + prologue);
+      if (rem > 0) cost += (double)((rem * p + sms - 1) / sms) * ((double)zc / p + prologue);
+      if (cost < best_cost - 1e-9) {
+        best_cost = cost;
+        // p == 1: every unit runs whole; else the units past the last full
+        // wave are cut into p pieces
+        best = BulkSched{bx, by, nchunk, zc, (int)(p == 1 ? units : units - rem), p};
+      }
+    }
+  }
+  return best;
+}
+
+Geometry geometry(int nx, int ny, int nz, lbm_precision prec, int qh, int qf, int sms, bool allow_bulk = true) {
   Geometry g;
   g.bulk = allow_bulk && bulk_ok(nx, ny, prec, qh, qf) ? 1 : 0;
   const int rows = g.bulk ? bulk_tile_rows((int)prec, qh, qf) : TY;
@@ -81,14 +121,20 @@ Geometry geometry(int nx, int ny, int nz, lbm_precision prec, int qh, int qf, bo
   const int bx = (nx + cols_ - 1) / cols_, by = (ny + rows - 1) / rows;
   const long long cols = (long long)bx * by;
   const char* env = std::getenv("LBM_ZCHUNK");
-  int zc = env ? std::atoi(env) : 0;
+  const int forced = env ? std::atoi(env) : 0;
+  if (g.bulk) {
+    g.sched = bulk_schedule(bx, by, nz, sms > 0 ? sms : 1, forced);
+    g.zchunk = g.sched.zchunk;
+    g.grid = dim3(bx, by, g.sched.nchunk);
+    g.nblocks = bulk_sched_blocks(g.sched);
+    return g;
+  }
+  int zc = forced;
   if (zc <= 0) {
-    // bulk: one CTA per SM, aim for >= 4 waves with chunks of >= 16 planes
-    // (each chunk refills its copy pipeline); generic: ~8 CTAs per SM.
-    const long long want = g.bulk ? 152LL * 4 : 152LL * 8;
-    const int minc = g.bulk ? 16 : 8;
+    // generic: ~8 CTAs per SM, chunks of >= 8 planes
+    const long long want = (long long)(sms > 0 ? sms : 1) * 8;
     int nchunks = (int)((want + cols - 1) / cols);
-    if (nchunks > nz / minc) nchunks = nz / minc;
+    if (nchunks > nz / 8) nchunks = nz / 8;
     if (nchunks < 1) nchunks = 1;
     zc = (nz + nchunks - 1) / nchunks;
   }
@@ -96,6 +142,7 @@ Geometry geometry(int nx, int ny, int nz, lbm_precision prec, int qh, int qf, bo
   g.grid = dim3(bx, by, nchunks);
   g.zchunk = zc;
   g.nblocks = (int)(cols * nchunks);
+  g.sched = BulkSched{bx, by, nchunks, zc, g.nblocks, 1};
   return g;
 }
 
@@ -170,6 +217,7 @@ struct lbm_domain {
   bool owns_ws;
   Layout L;
   Geometry geo;
+  int sms;  // multiprocessors of the device (launch geometry)
   int cur;
   bool params_set, inited;
   long long level;
@@ -248,11 +296,11 @@ StepPtrs<S, typename Store<S>::R> ptrs(lbm_domain* d) {
 template <class S, int QH>
 void step_qf(lbm_domain* d, const StepPtrs<S, typename Store<S>::R>& A, int mode) {
   switch (d->qf) {
-    case 0: launch_step<S, QH, 0>(d->dp, A, d->maps[d->cur], d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
-    case 7: launch_step<S, QH, 7>(d->dp, A, d->maps[d->cur], d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
-    case 15: launch_step<S, QH, 15>(d->dp, A, d->maps[d->cur], d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
-    case 19: launch_step<S, QH, 19>(d->dp, A, d->maps[d->cur], d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
-    default: launch_step<S, QH, 27>(d->dp, A, d->maps[d->cur], d->geo.grid, d->geo.zchunk, mode, d->geo.bulk, d->stream); break;
+    case 0: launch_step<S, QH, 0>(d->dp, A, d->maps[d->cur], d->geo.grid, d->geo.zchunk, d->geo.sched, mode, d->geo.bulk, d->stream); break;
+    case 7: launch_step<S, QH, 7>(d->dp, A, d->maps[d->cur], d->geo.grid, d->geo.zchunk, d->geo.sched, mode, d->geo.bulk, d->stream); break;
+    case 15: launch_step<S, QH, 15>(d->dp, A, d->maps[d->cur], d->geo.grid, d->geo.zchunk, d->geo.sched, mode, d->geo.bulk, d->stream); break;
+    case 19: launch_step<S, QH, 19>(d->dp, A, d->maps[d->cur], d->geo.grid, d->geo.zchunk, d->geo.sched, mode, d->geo.bulk, d->stream); break;
+    default: launch_step<S, QH, 27>(d->dp, A, d->maps[d->cur], d->geo.grid, d->geo.zchunk, d->geo.sched, mode, d->geo.bulk, d->stream); break;
   }
 }
 
@@ -404,6 +452,16 @@ void refresh_devparams(lbm_domain* d) {
   q.test_stall = d->test_stall;
   fill_real(q.pd, p, d->prec);
   fill_real(q.pf, p, d->prec);
+  q.uniform_rho = p.rho_L == p.rho_H ? 1 : 0;
+  q.uniform_tau = p.nu_L == p.nu_H ? 1 : 0;
+  q.four_over_xi_d = 4.0 / p.xi;
+  q.twelve_over_xi_d = 12.0 / p.xi;
+  q.inv_rho_d = 1.0 / p.rho_L;
+  q.omega_g_d = 1.0 / q.pd.tau_L;
+  q.four_over_xi_f = (float)q.four_over_xi_d;
+  q.twelve_over_xi_f = (float)q.twelve_over_xi_d;
+  q.inv_rho_f = (float)q.inv_rho_d;
+  q.omega_g_f = 1.0f / q.pf.tau_L;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -510,7 +568,16 @@ lbm_status lbm_create_domain(int nx, int ny, int nz, lbm_precision prec, lbm_the
   d->prec = prec; d->th = thermal; d->qh = q_phase; d->qf = thermal_q(thermal);
   d->stream = (cudaStream_t)stream;
   d->L = L;
-  d->geo = geometry(nx, ny, nz, prec, q_phase, thermal_q(thermal));
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+      cudaGetLastError();
+      sms = 152;
+    }
+    d->sms = sms;
+  }
+  d->geo = geometry(nx, ny, nz, prec, q_phase, thermal_q(thermal), d->sms);
   d->sticky = LBM_OK;
   if (const char* env = std::getenv("LBM_TEST_STALL")) d->test_stall = std::atoi(env) != 0;
   lbm_default_params(&d->params);
@@ -533,7 +600,7 @@ lbm_status lbm_create_domain(int nx, int ny, int nz, lbm_precision prec, lbm_the
   refresh_devparams(d);
   if (d->geo.bulk && !make_maps(d)) {
     // no tensor-map support: run the generic kernel
-    d->geo = geometry(nx, ny, nz, prec, q_phase, thermal_q(thermal), false);
+    d->geo = geometry(nx, ny, nz, prec, q_phase, thermal_q(thermal), d->sms, false);
   }
   {
     const cudaError_t e = cudaMemsetAsync(at(d, L.errflag), 0, sizeof(int), d->stream);

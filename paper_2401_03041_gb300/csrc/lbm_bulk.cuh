@@ -136,16 +136,16 @@ struct BulkSmemT {
   // the layout fits in 227 KB, else one (G(z + 1) issued once every g-role
   // thread has taken the moments of G(z))
   static constexpr size_t fixed_bytes = 3 * hf_stage * sizeof(S) + 3 * G::HPB * 2 * sizeof(R) +
-                                        13 * G::NT * sizeof(R) + 5 * sizeof(uint64_t) + 128 + 64;
+                                        8 * G::NT * sizeof(R) + 5 * sizeof(uint64_t) + 128 + 64;
   static constexpr int GR = fixed_bytes + 2 * g_stage * sizeof(S) <= 232448 ? 2 : 1;
   static constexpr size_t off_hf = 0;
   static constexpr size_t off_g = off_hf + 3 * hf_stage * sizeof(S);
   // (phi, T) of the halo tile, interleaved, for planes z - 1, z, z + 1
   static constexpr size_t off_phi = (off_g + GR * g_stage * sizeof(S) + 15) & ~size_t(15);
   static constexpr size_t off_T = off_phi + 3 * G::HPB * sizeof(R);   // end of the first half
-  // per-cell exchange between the two roles: phi, T, grad phi (3), lap phi,
-  // grad T (3) from the h/f role; j (3), p* from the g role
-  static constexpr int NX = 13;
+  // per-cell exchange between the two roles: phi and the acceleration a (3)
+  // from the h/f role; j (3), p* from the g role
+  static constexpr int NX = 8;
   static constexpr size_t off_x = (off_T + 3 * G::HPB * sizeof(R) + 15) & ~size_t(15);
   static constexpr size_t off_bar = (off_x + (size_t)NX * G::NT * sizeof(R) + 15) & ~size_t(15);
   // + 128: the kernel aligns the start of its dynamic shared memory to 128
@@ -220,7 +220,7 @@ template <class S, int QH, int QF, bool EXT>
 __global__ void __launch_bounds__(BulkSmem<S, QH, QF>::G::NTHR, 1)
 step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
                  const __grid_constant__ CUtensorMap mh, const __grid_constant__ CUtensorMap mg,
-                 const __grid_constant__ CUtensorMap mf, int zchunk, int mode) {
+                 const __grid_constant__ CUtensorMap mf, const BulkSched sched, int mode) {
   using R = typename Store<S>::R;
   const auto& rp = RP<R>(P);
   using L = BulkSmem<S, QH, QF>;
@@ -243,9 +243,9 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
   const bool role_g = tid < NC;
   const int cidx = role_g ? tid : tid - NC;
   const int tx = cidx % G::TXB, ty = cidx / G::TXB;
-  const int x0 = blockIdx.x * G::TXB, y0 = blockIdx.y * G::TYB;
-  const int z0 = blockIdx.z * zchunk;
-  const int z1 = min(z0 + zchunk, P.nz);
+  int tcol, trow, z0, z1;
+  bulk_unit(sched, P.nz, (int)blockIdx.x, tcol, trow, z0, z1);
+  const int x0 = tcol * G::TXB, y0 = trow * G::TYB;
   const int x = x0 + tx, y = y0 + ty;
   const bool active = (x < P.nx) && (y < P.ny);
   const R shh = (R)rp.shift_h, shf = (R)rp.shift_f;
@@ -299,18 +299,21 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
         return wall_T<R>(P, gx, true);
       };
       if constexpr (QF > 0) {
-        T = 0;
-        R Tb = 0;
+        // stored values (shifted by w_i s, s = shift_f; sum_i w_i = 1);
+        // anti-bounce-back in stored form: -v_s + 2 w_i (T_w - s)
+        T = shf;
+        R Tb = 0, Tt = 0;
         if constexpr (BOUNCE) {
-          if constexpr (EXT) Tb = bottom_T();
-          else Tb = (R)rp.T_bottom;
+          if constexpr (EXT) Tb = bottom_T() - shf;
+          else Tb = (R)rp.T_bottom - shf;
+          Tt = (R)rp.T_top - shf;
         }
         static_for<0, QF>([&](auto I) {
           constexpr int i = decltype(I)::value;
           const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
           const S* rowp = rowb + (size_t)(QH + i) * G::HFB;
-          const R v = Store<S>::ld_s(b ? rowp : rowp - cx<QF>(i)) + (R)weight<QF>(i) * shf;
-          T += b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? Tb : (R)rp.T_top)) : v;
+          const R v = Store<S>::ld_s(b ? rowp : rowp - cx<QF>(i));
+          T += b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? Tb : Tt)) : v;
         });
       } else {
         int gx = x0 + hc - 1, gy = y0 + hr - 1;
@@ -431,10 +434,10 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
           if (active) {
             m = g_moments<R>(getg);
             if (mode & MODE_SAVE) save_moments<S>(P, A, cell, m);
-            xch[9 * NC + cidx] = m.jx;
-            xch[10 * NC + cidx] = m.jy;
-            xch[11 * NC + cidx] = m.jz;
-            xch[12 * NC + cidx] = m.pst;
+            xch[4 * NC + cidx] = m.jx;
+            xch[5 * NC + cidx] = m.jy;
+            xch[6 * NC + cidx] = m.jz;
+            xch[7 * NC + cidx] = m.pst;
           }
           if constexpr (GR == 1) {
             // every g-role thread has read G(z): warp 0 of the role refills
@@ -453,10 +456,8 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
           pair_sync();
           if (active && (mode & MODE_COLLIDE)) {
             const R phi = xch[cidx];
-            const CellFlow<R> f = cell_flow<R>(P, x, y, z, phi, xch[NC + cidx], xch[2 * NC + cidx],
-                                               xch[3 * NC + cidx], xch[4 * NC + cidx], xch[5 * NC + cidx],
-                                               xch[6 * NC + cidx], xch[7 * NC + cidx], xch[8 * NC + cidx], m.jx,
-                                               m.jy, m.jz);
+            const CellFlow<R> f = cell_velocity<R>(xch[NC + cidx], xch[2 * NC + cidx], xch[3 * NC + cidx],
+                                                   (R)1, m.jx, m.jy, m.jz);
             collide_g<S>(P, A, pcell, phi, m, f);
           }
         };
@@ -470,6 +471,7 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
         Stencil27<R> fd;
         R rgx = 0, rgy = 0, rgz = 0, rlap = 0, pgx = 0, pgy = 0, pgz = 0;
         const P2 cen = pc[c0];
+        CellForce<R> F;
         if (active) {
           eval_pairs<G::HXB>(fd, pm, pc, pp, c0);
           if constexpr (QF == 0) {
@@ -478,43 +480,44 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
               if (P.alpha_ratio && !P.rk_iso) central_phi_pairs<P2, R, G::HXB>(pm, pc, pp, c0, pgx, pgy, pgz);
           }
           if (mode & MODE_SAVE) save_stencil<S>(P, A, cell, cen.x, cen.y, fd);
+          // a4-a5 need nothing from the g role: the force is computed here,
+          // once, and only phi and a go across
+          F = cell_force<R>(P, x, y, z, cen.x, cen.y, fd.gpx, fd.gpy, fd.gpz, fd.lp, fd.gtx, fd.gty, fd.gtz);
           xch[cidx] = cen.x;
-          xch[NC + cidx] = cen.y;
-          xch[2 * NC + cidx] = fd.gpx;
-          xch[3 * NC + cidx] = fd.gpy;
-          xch[4 * NC + cidx] = fd.gpz;
-          xch[5 * NC + cidx] = fd.lp;
-          xch[6 * NC + cidx] = fd.gtx;
-          xch[7 * NC + cidx] = fd.gty;
-          xch[8 * NC + cidx] = fd.gtz;
+          xch[NC + cidx] = F.ax;
+          xch[2 * NC + cidx] = F.ay;
+          xch[3 * NC + cidx] = F.az;
         }
         pair_sync();
         if (active) {
           const R phi = cen.x, Tc = cen.y;
-          const CellFlow<R> f = cell_flow<R>(P, x, y, z, phi, Tc, fd.gpx, fd.gpy, fd.gpz, fd.lp, fd.gtx, fd.gty,
-                                             fd.gtz, xch[9 * NC + cidx], xch[10 * NC + cidx], xch[11 * NC + cidx]);
-          cell_outputs<S>(P, A, x, y, z, cell, mode, phi, Tc, xch[12 * NC + cidx], f, dsum);
+          const CellFlow<R> f = cell_velocity<R>(F.ax, F.ay, F.az, F.rho, xch[4 * NC + cidx], xch[5 * NC + cidx],
+                                                 xch[6 * NC + cidx]);
+          cell_outputs<S>(P, A, x, y, z, cell, mode, phi, Tc, xch[7 * NC + cidx], f, dsum);
           if (mode & MODE_COLLIDE) {
             auto run = [&](auto btag) {
               constexpr bool BOUNCE = decltype(btag)::value;
+              // pulled values as stored (collide_h / collide_f work on them)
               auto geth = [&](auto I) {
                 constexpr int i = decltype(I)::value;
                 const bool b = BOUNCE && ((cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi));
                 const S* p_ = hrow + (size_t)i * G::HFB;
-                return Store<S>::ld_s(b ? p_ : p_ - cx<QH>(i)) + (R)weight<QH>(i) * shh;
+                return Store<S>::ld_s(b ? p_ : p_ - cx<QH>(i));
               };
-              R Tb = 0;
+              R Tb = 0, Tt = 0;
               if constexpr (BOUNCE && QF > 0) {
-                if constexpr (EXT) Tb = wall_T<R>(P, x, true);
-                else Tb = (R)rp.T_bottom;
+                if constexpr (EXT) Tb = wall_T<R>(P, x, true) - shf;
+                else Tb = (R)rp.T_bottom - shf;
+                Tt = (R)rp.T_top - shf;
               }
               auto getf = [&](auto I) {
                 constexpr int i = decltype(I)::value;
                 if constexpr (QF > 0) {
                   const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
                   const S* p_ = hrow + (size_t)(QH + i) * G::HFB;
-                  const R v = Store<S>::ld_s(b ? p_ : p_ - cx<QF>(i)) + (R)weight<QF>(i) * shf;
-                  return b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? Tb : (R)rp.T_top)) : v;
+                  const R v = Store<S>::ld_s(b ? p_ : p_ - cx<QF>(i));
+                  // anti-bounce-back in stored form: -v_s + 2 w_i (T_w - s)
+                  return b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? Tb : Tt)) : v;
                 } else {
                   return (R)0;
                 }

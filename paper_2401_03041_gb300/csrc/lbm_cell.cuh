@@ -3,8 +3,9 @@
 //
 // Inputs: the zeroth moments phi and T of the pulled PDFs, their finite
 // differences (isotropic D3Q27 gradient and Laplacian), the RK stencil values,
-// and accessors returning the pulled PDF values h*_i, g*_i, f*_i (un-shifted,
-// with wall rules applied).  Outputs: post-collision PDFs (stored shifted),
+// and accessors returning the pulled PDF values h*_i, g*_i, f*_i as stored
+// (h and f shifted by w_i s, g unshifted; wall rules applied).  Outputs:
+// post-collision PDFs (stored shifted),
 // RK stage-1 fields, optional macroscopic fields and FP64 diagnostics.
 //
 // Central-moment collision in closed form.  With y = g* - g^eq + S/2 (S the
@@ -254,41 +255,64 @@ __device__ __forceinline__ GMoments<R> g_moments(GG getg) {
   return m;
 }
 
-// a4-a6: surface-tension and Marangoni force, body force, acceleration and
-// velocity of one cell from phi, T, their finite differences and the first
-// moment j of the pulled g.
+// a4-a5: surface-tension and Marangoni force and body force of one cell from
+// phi, T and their finite differences, as the acceleration a = F / rho.
+// Everything here is known before the moments of the pulled g, so the bulk
+// kernel's stencil role computes it alone and hands a to the g role.
 template <class R>
-struct CellFlow {
-  R ux, uy, uz, ax, ay, az, uu, rho;
+struct CellForce {
+  R ax, ay, az, rho;
 };
 
 template <class R>
-__device__ __forceinline__ CellFlow<R> cell_flow(const DevParams& P, int x, int y, int z, R phi, R Tc,
-                                                 R gpx, R gpy, R gpz, R lp, R gtx, R gty, R gtz, R jx, R jy,
-                                                 R jz) {
+__device__ __forceinline__ CellForce<R> cell_force(const DevParams& P, int x, int y, int z, R phi, R Tc,
+                                                   R gpx, R gpy, R gpz, R lp, R gtx, R gty, R gtz) {
   const auto& rp = RP<R>(P);
+  const Derived<R> dv = derived<R>(P);
   const R Gx = (R)rp.grad[0], Gy = (R)rp.grad[1], Gz = (R)rp.grad[2];
   const R Ttot = Tc + Gx * ((R)x + (R)0.5 - (R)rp.origin[0]) + Gy * ((R)y + (R)0.5 - (R)rp.origin[1]) +
                  Gz * ((R)z + (R)0.5 - (R)rp.origin[2]);
   const R gTx = gtx + Gx, gTy = gty + Gy, gTz = gtz + Gz;
   const R xi = (R)rp.xi;
   const R sigma = (R)rp.sigma_ref + (R)rp.sigma_T * (Ttot - (R)rp.T_ref);
-  const R beta = (R)12 * sigma / xi;
+  const R beta = sigma * dv.twelve_over_xi;   // 12 sigma / xi
   const R kap = (R)1.5 * sigma * xi;
   const R mu = (R)4 * beta * phi * (phi - (R)1) * (phi - (R)0.5) - kap * lp;
   const R g2 = gpx * gpx + gpy * gpy + gpz * gpz;
   const R tdp = gTx * gpx + gTy * gpy + gTz * gpz;
   const R cm = (R)1.5 * xi * (R)rp.sigma_T;
-  CellFlow<R> f;
+  CellForce<R> f;
   f.rho = (R)rp.rho_L + phi * (R)(rp.rho_H - rp.rho_L);
   const R Fx = mu * gpx + cm * (g2 * gTx - tdp * gpx) + f.rho * (R)rp.gravity[0];
   const R Fy = mu * gpy + cm * (g2 * gTy - tdp * gpy) + f.rho * (R)rp.gravity[1];
   const R Fz = mu * gpz + cm * (g2 * gTz - tdp * gpz) + f.rho * (R)rp.gravity[2];
-  const R irho = (R)1 / f.rho;
+  const R irho = P.uniform_rho ? dv.inv_rho : (R)1 / f.rho;
   f.ax = Fx * irho; f.ay = Fy * irho; f.az = Fz * irho;
-  f.ux = jx + (R)0.5 * f.ax; f.uy = jy + (R)0.5 * f.ay; f.uz = jz + (R)0.5 * f.az;
+  return f;
+}
+
+// a6: velocity u = j + a/2 (Guo) from the first moment j of the pulled g.
+template <class R>
+struct CellFlow {
+  R ux, uy, uz, ax, ay, az, uu, rho;
+};
+
+template <class R>
+__device__ __forceinline__ CellFlow<R> cell_velocity(R ax, R ay, R az, R rho, R jx, R jy, R jz) {
+  CellFlow<R> f;
+  f.ax = ax; f.ay = ay; f.az = az; f.rho = rho;
+  f.ux = jx + (R)0.5 * ax; f.uy = jy + (R)0.5 * ay; f.uz = jz + (R)0.5 * az;
   f.uu = f.ux * f.ux + f.uy * f.uy + f.uz * f.uz;
   return f;
+}
+
+// a4-a6 in one piece.
+template <class R>
+__device__ __forceinline__ CellFlow<R> cell_flow(const DevParams& P, int x, int y, int z, R phi, R Tc,
+                                                 R gpx, R gpy, R gpz, R lp, R gtx, R gty, R gtz, R jx, R jy,
+                                                 R jz) {
+  const CellForce<R> F = cell_force<R>(P, x, y, z, phi, Tc, gpx, gpy, gpz, lp, gtx, gty, gtz);
+  return cell_velocity<R>(F.ax, F.ay, F.az, F.rho, jx, jy, jz);
 }
 
 // a10 diagnostics (FP64 partial sums) and the macroscopic output pass.
@@ -335,7 +359,7 @@ __device__ __forceinline__ void collide_g(const DevParams& P, const StepPtrs<S, 
   using R = typename Store<S>::R;
   const auto& rp = RP<R>(P);
   const R ux = f.ux, uy = f.uy, uz = f.uz, ax = f.ax, ay = f.ay, az = f.az, uu = f.uu;
-  const R om = (R)1 / ((R)rp.tau_L + phi * (R)(rp.tau_H - rp.tau_L));
+  const R om = P.uniform_tau ? derived<R>(P).omega_g : (R)1 / ((R)rp.tau_L + phi * (R)(rp.tau_H - rp.tau_L));
   const R k1 = (R)1 - om;
   const R p3 = m.pst * (R)(1.0 / 3.0);
   const R Pxx = k1 * (m.sxx - p3 - ux * ux + ux * ax);
@@ -393,7 +417,12 @@ __device__ __forceinline__ void collide_g(const DevParams& P, const StepPtrs<S, 
   });
 }
 
-// a7: h collision (single rate + Guo source of the interface force)
+// a7: h collision (single rate + Guo source of the interface force).
+// geth(I) returns the pulled population as STORED, hs_i = h*_i - w_i s
+// (s = shift_h, 0 in FP64).  With h^eq_i = w_i phi E_i the relaxation
+//   h'_i - w_i s = hs_i - omega (hs_i - w_i (phi E_i - s)) + S_i
+// works on stored values throughout, so the shift costs nothing per
+// direction.
 template <class S, int QH, class GH>
 __device__ __forceinline__ void collide_h(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                                           size_t pcell, typename Store<S>::R phi, typename Store<S>::R gpx,
@@ -404,17 +433,17 @@ __device__ __forceinline__ void collide_h(const DevParams& P, const StepPtrs<S, 
   const R ux = f.ux, uy = f.uy, uz = f.uz, uu = f.uu;
   const R g2 = gpx * gpx + gpy * gpy + gpz * gpz;
   const R nrm = (R)1 / (sqrt(g2) + (R)rp.eps_n);
-  const R th = (R)4 * phi * ((R)1 - phi) / (R)rp.xi * nrm;
+  const R th = derived<R>(P).four_over_xi * phi * ((R)1 - phi) * nrm;   // 4 phi (1 - phi) / xi / |grad phi|
   const R fpx = th * gpx, fpy = th * gpy, fpz = th * gpz;
   const R om = (R)rp.omega_phi;
   const R sc = (R)1 - (R)0.5 * om;
   const R sh = (R)rp.shift_h;
-  const R e0 = (R)1 - (R)1.5 * uu;
+  const R base = phi * ((R)1 - (R)1.5 * uu) - sh;   // phi e0 - s
+  const R p45 = (R)4.5 * phi, p3 = (R)3 * phi;
   {
     constexpr R w = (R)weight<QH>(0);
     const R hs = geth(std::integral_constant<int, 0>{});
-    const R hn = hs - om * (hs - w * phi * e0);
-    Store<S>::st(A.hd[0] + pcell, hn - w * sh);
+    Store<S>::st(A.hd[0] + pcell, hs - om * (hs - w * base));
   }
   static_for<1, QH>([&](auto I) {
     constexpr int i = decltype(I)::value;
@@ -423,12 +452,12 @@ __device__ __forceinline__ void collide_h(const DevParams& P, const StepPtrs<S, 
       constexpr R w = (R)weight<QH>(i);
       const R cu = (R)cx<QH>(i) * ux + (R)cy<QH>(i) * uy + (R)cz<QH>(i) * uz;
       const R cf = (R)cx<QH>(i) * fpx + (R)cy<QH>(i) * fpy + (R)cz<QH>(i) * fpz;
-      const R even = w * phi * (e0 + (R)4.5 * cu * cu);
-      const R odd = w * phi * (R)3 * cu;
+      const R even = w * (base + p45 * cu * cu);
+      const R odd = w * (p3 * cu);
       const R src = sc * w * cf;
       const R hi = geth(I), hj = geth(std::integral_constant<int, j>{});
-      Store<S>::st(A.hd[i] + pcell, hi - om * (hi - (even + odd)) + src - w * sh);
-      Store<S>::st(A.hd[j] + pcell, hj - om * (hj - (even - odd)) - src - w * sh);
+      Store<S>::st(A.hd[i] + pcell, hi - om * (hi - (even + odd)) + src);
+      Store<S>::st(A.hd[j] + pcell, hj - om * (hj - (even - odd)) - src);
     }
   });
 }
@@ -463,13 +492,18 @@ __device__ __forceinline__ void collide_f(const DevParams& P, const StepPtrs<S, 
       om = (R)1 / ((R)0.5 + (R)3 * alpha_of<R>(P, phi));
       qs += cond_cross<R>(P, fdv.gpx, fdv.gpy, fdv.gpz, (R)0, (R)0, (R)0);
     }
+    // stored values throughout, as in collide_h (s = shift_f)
     const R sf = (R)rp.shift_f;
-    const R e0 = (R)1 - (R)1.5 * uu;
-    {
+    const R base = Tc * ((R)1 - (R)1.5 * uu) - sf;   // T e0 - s
+    const R t45 = (R)4.5 * Tc, t3 = (R)3 * Tc;
+    if constexpr (weight<QF>(0) != 0.0) {
       constexpr R w = (R)weight<QF>(0);
       const R fs = getf(std::integral_constant<int, 0>{});
-      const R fn = fs - om * (fs - w * Tc * e0) + w * qs;
-      Store<S>::st(A.fd[0] + pcell, fn - w * sf);
+      Store<S>::st(A.fd[0] + pcell, fs - om * (fs - w * base) + w * qs);
+    } else {
+      // D3Q7 (w_0 = 0): the rest population relaxes to 0
+      const R fs = getf(std::integral_constant<int, 0>{});
+      Store<S>::st(A.fd[0] + pcell, fs - om * fs);
     }
     static_for<1, QF>([&](auto I) {
       constexpr int i = decltype(I)::value;
@@ -477,11 +511,12 @@ __device__ __forceinline__ void collide_f(const DevParams& P, const StepPtrs<S, 
         constexpr int j = opp<QF>(i);
         constexpr R w = (R)weight<QF>(i);
         const R cu = (R)cx<QF>(i) * ux + (R)cy<QF>(i) * uy + (R)cz<QF>(i) * uz;
-        const R even = w * Tc * (e0 + (R)4.5 * cu * cu);
-        const R odd = w * Tc * (R)3 * cu;
+        const R even = w * (base + t45 * cu * cu);
+        const R odd = w * (t3 * cu);
+        const R wq = w * qs;
         const R fi = getf(I), fj = getf(std::integral_constant<int, j>{});
-        Store<S>::st(A.fd[i] + pcell, fi - om * (fi - (even + odd)) + w * qs - w * sf);
-        Store<S>::st(A.fd[j] + pcell, fj - om * (fj - (even - odd)) + w * qs - w * sf);
+        Store<S>::st(A.fd[i] + pcell, fi - om * (fi - (even + odd)) + wq);
+        Store<S>::st(A.fd[j] + pcell, fj - om * (fj - (even - odd)) + wq);
       }
     });
   } else {
@@ -541,8 +576,8 @@ __device__ __forceinline__ void save_moments(const DevParams& P, const StepPtrs<
   A.save[SAVE_SYZ * N + cell] = m.syz;
 }
 
-// a2-a10 for one cell in sequence.  GH/GG/GF: accessors i -> pulled
-// (un-shifted) value.
+// a2-a10 for one cell in sequence.  GH/GG/GF: accessors i -> pulled value
+// as stored (h and f shifted by w_i s; g unshifted).
 template <class S, int QH, int QF, class GH, class GG, class GF>
 __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                                             int x, int y, int z, size_t cell, size_t pcell, int mode,

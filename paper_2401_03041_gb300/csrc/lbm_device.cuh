@@ -145,6 +145,12 @@ struct DevParams {
   int tw_waves;     // k > 0: modulated bottom wall temperature (T_bottom_amp != 0)
   double dalpha_d, T_bottom_amp_d;  // alpha_H - alpha_L; bottom wall modulation amplitude
   float dalpha_f, T_bottom_amp_f;
+  // Constants derived once on the host, so that no kernel divides by a
+  // parameter: 4/xi, 12/xi, and for uniform density / viscosity (flags set)
+  // 1/rho and 1/tau of the g collision.
+  int uniform_rho, uniform_tau;
+  double four_over_xi_d, twelve_over_xi_d, inv_rho_d, omega_g_d;
+  float four_over_xi_f, twelve_over_xi_f, inv_rho_f, omega_g_f;
 };
 
 template <class R> __host__ __device__ __forceinline__ const RealParams<R>& RP(const DevParams& P);
@@ -154,6 +160,15 @@ template <> __host__ __device__ __forceinline__ const RealParams<float>& RP<floa
 template <class R> __device__ __forceinline__ R dalpha_of(const DevParams& P);
 template <> __device__ __forceinline__ double dalpha_of<double>(const DevParams& P) { return P.dalpha_d; }
 template <> __device__ __forceinline__ float dalpha_of<float>(const DevParams& P) { return P.dalpha_f; }
+template <class R> struct Derived { R four_over_xi, twelve_over_xi, inv_rho, omega_g; };
+template <class R> __device__ __forceinline__ Derived<R> derived(const DevParams& P);
+template <> __device__ __forceinline__ Derived<double> derived<double>(const DevParams& P) {
+  return {P.four_over_xi_d, P.twelve_over_xi_d, P.inv_rho_d, P.omega_g_d};
+}
+template <> __device__ __forceinline__ Derived<float> derived<float>(const DevParams& P) {
+  return {P.four_over_xi_f, P.twelve_over_xi_f, P.inv_rho_f, P.omega_g_f};
+}
+
 template <class R> __device__ __forceinline__ R t_amp_of(const DevParams& P);
 template <> __device__ __forceinline__ double t_amp_of<double>(const DevParams& P) { return P.T_bottom_amp_d; }
 template <> __device__ __forceinline__ float t_amp_of<float>(const DevParams& P) { return P.T_bottom_amp_f; }
@@ -171,6 +186,51 @@ __device__ __forceinline__ R wall_T(const DevParams& P, int x, bool bottom) {
   R t = (R)rp.T_bottom;
   if (P.tw_waves) t += t_amp_of<R>(P) * cos_pi((R)(2 * P.tw_waves) * ((R)x + (R)0.5) / (R)P.nx);
   return t;
+}
+
+// Work assignment of the bulk step kernel's one-dimensional grid.  The
+// lattice is bx x by tile columns; each column is cut into nchunk z-chunks of
+// zchunk planes (the last may be shorter).  A unit is one (chunk, column)
+// pair, numbered chunk-major so that the CTAs of one wave hold neighbouring
+// columns at the same planes (their shared halo rows then meet in L2).  The
+// first nfull units run whole, one CTA each; every remaining unit is cut into
+// npiece z-pieces, one CTA each, so that what would be a partial last wave of
+// whole units becomes npiece times as many short pieces spread over all SMs.
+struct BulkSched {
+  int bx, by, nchunk, zchunk, nfull, npiece;
+};
+
+__host__ __device__ __forceinline__ int bulk_sched_units(const BulkSched& s) { return s.bx * s.by * s.nchunk; }
+__host__ __device__ __forceinline__ int bulk_sched_blocks(const BulkSched& s) {
+  return s.nfull + (bulk_sched_units(s) - s.nfull) * s.npiece;
+}
+
+// Tile column (tx, ty) and plane range [z0, z1) of block b.
+__host__ __device__ __forceinline__ void bulk_unit(const BulkSched& s, int nz, int b, int& tx, int& ty, int& z0,
+                                                   int& z1) {
+  const int cols = s.bx * s.by;
+  int u, piece = 0;
+  if (b < s.nfull) {
+    u = b;
+  } else {
+    const int rem = bulk_sched_units(s) - s.nfull;
+    const int r = b - s.nfull;
+    piece = r / rem;
+    u = s.nfull + r % rem;
+  }
+  const int c = u / cols, t = u % cols;
+  tx = t % s.bx;
+  ty = t / s.bx;
+  int lo = c * s.zchunk, hi = lo + s.zchunk;
+  if (hi > nz) hi = nz;
+  if (b >= s.nfull) {
+    const int len = hi - lo;
+    const int a = lo + (int)((long long)len * piece / s.npiece);
+    hi = lo + (int)((long long)len * (piece + 1) / s.npiece);
+    lo = a;
+  }
+  z0 = lo;
+  z1 = hi;
 }
 
 // Kernel modes (bit set).

@@ -31,37 +31,38 @@ __device__ __forceinline__ int wrap_any(int v, int n) {
   return r < 0 ? r + n : r;
 }
 
-// Value of direction I pulled into cell (x, y, z): p_I(x - c_I), with
-// half-way bounce-back (ABB=false) or anti-bounce-back (ABB=true) when the
-// source lies beyond a z wall.  Returns the un-shifted value.
+// Value of direction I pulled into cell (x, y, z): p_I(x - c_I) as stored
+// (shifted by w_I s, s = shift), with half-way bounce-back (ABB=false) or
+// anti-bounce-back (ABB=true; in stored form -p_opp + 2 w_I (T_w - s)) when
+// the source lies beyond a z wall.
 template <int Q, bool ABB, int I, class S>
 __device__ __forceinline__ typename Store<S>::R pull(const DevParams& P, const S* __restrict__ base,
                                                      int x, int y, int z, typename Store<S>::R shift) {
   using R = typename Store<S>::R;
-  const auto& rp = RP<R>(P);
   const int zs = z - cz<Q>(I);
   constexpr R w = (R)weight<Q>(I);
-  const R wsh = w * shift;
   if (P.walls && (zs < 0 || zs >= P.nz)) {
-    const R v = Store<S>::ld(base + (size_t)opp<Q>(I) * P.Np + pdf_index(P, x, y, z)) + wsh;
+    const R v = Store<S>::ld(base + (size_t)opp<Q>(I) * P.Np + pdf_index(P, x, y, z));
     if constexpr (ABB) {
       const R Tw = wall_T<R>(P, x, zs < 0);
-      return -v + (R)2 * w * Tw;
+      return -v + (R)2 * w * (Tw - shift);
     }
     return v;
   }
   const int xs = wrap(x - cx<Q>(I), P.nx);
   const int ys = wrap(y - cy<Q>(I), P.ny);
   const int zz = P.walls ? zs : wrap(zs, P.nz);
-  return Store<S>::ld(base + (size_t)I * P.Np + pdf_index(P, xs, ys, zz)) + wsh;
+  return Store<S>::ld(base + (size_t)I * P.Np + pdf_index(P, xs, ys, zz));
 }
 
+// Zeroth moment of the pulled populations (un-shifted: the stored values plus
+// sum_i w_i s = s).
 template <int Q, bool ABB, class S>
 __device__ __forceinline__ typename Store<S>::R pulled_sum(const DevParams& P, const S* __restrict__ base,
                                                            int x, int y, int z,
                                                            typename Store<S>::R shift) {
   using R = typename Store<S>::R;
-  R s = 0;
+  R s = shift;
   static_for<0, Q>([&](auto I) { s += pull<Q, ABB, decltype(I)::value>(P, base, x, y, z, shift); });
   return s;
 }

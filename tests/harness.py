@@ -110,7 +110,7 @@ def bulk_fits(precision, q_phase, thermal):
     for rows in (4, 2):
         hfb = -(-W * (rows + 2) * s // 128) * 128
         gb = -(-W * rows * s // 128) * 128
-        fixed = 3 * nhf * hfb + 6 * (cols + 2) * (rows + 2) * rs + 13 * cols * rows * rs + 64 + 128
+        fixed = 3 * nhf * hfb + 6 * (cols + 2) * (rows + 2) * rs + 8 * cols * rows * rs + 64 + 128
         ring = 2 if fixed + 2 * 27 * gb <= 232448 else 1      # g ring of two stages, else one
         if fixed + ring * 27 * gb <= 232448:
             return True
