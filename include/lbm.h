@@ -74,7 +74,13 @@ typedef enum {
 typedef struct {
   double nu_L, nu_H;       /* kinematic viscosity of the light (phi=0) / heavy (phi=1) phase;
                               tau(phi) = tau_L + phi (tau_H - tau_L), tau = nu / c_s^2 + 1/2 */
-  double rho_L, rho_H;     /* densities; this build requires rho_L == rho_H */
+  double rho_L, rho_H;     /* densities of the light / heavy phase, rho(phi) = rho_L
+                              + phi (rho_H - rho_L).  With rho_L != rho_H the pressure and
+                              viscous correction forces F_p = -p* c_s^2 (rho_H - rho_L) grad phi
+                              and F_mu = nu (rho_H - rho_L) [grad u + grad u^T] . grad phi act
+                              (Sec. 2.2; strain from the non-equilibrium moments of g).  The
+                              energy equation keeps rho c_p = 1 (alpha_* are diffusivities).
+                              The adjoint needs rho_L == rho_H. */
   double mobility;         /* Allen-Cahn mobility M; omega_phi = 1 / (1/2 + M / c_s^2) */
   double xi;               /* interface width */
   double sigma_ref, sigma_T, T_ref;  /* sigma(T) = sigma_ref + sigma_T (T - T_ref) */
@@ -152,8 +158,8 @@ lbm_status lbm_destroy_domain(lbm_domain* dom);
 
 /* Set the model parameters (Sec. 2.1-2.3).  Copied; takes effect for the
  * next launch.  LBM_ERR_ARG for non-physical values (nu <= 0, M <= 0,
- * xi <= 0, alpha <= 0, non-finite); LBM_ERR_UNSUPPORTED for rho_L != rho_H
- * or omega_high != 1. */
+ * xi <= 0, rho <= 0, alpha <= 0, non-finite); LBM_ERR_UNSUPPORTED for
+ * omega_high != 1. */
 lbm_status lbm_set_params(lbm_domain* dom, const lbm_params* p);
 
 /* Replace the Gaussian heat sources (0 <= n <= LBM_MAX_SOURCES; Eq. HeatSource,

@@ -206,8 +206,6 @@ class OracleLBM:
     def __init__(self, nx, ny, nz, params, q_phase=15, thermal="D3Q7",
                  sources: Sequence = (), patches=None, origin=(0, 0, 0),
                  global_shape=None):
-        if params.rho_L != params.rho_H:
-            raise NotImplementedError("density ratio != 1 (F_p, F_mu) not supported")
         self.nx, self.ny, self.nz = nx, ny, nz
         self.p = params
         self.Sh = stencil(q_phase)
@@ -410,14 +408,43 @@ class OracleLBM:
         g2 = gphi[0] ** 2 + gphi[1] ** 2 + gphi[2] ** 2
         gTgphi = gT[0] * gphi[0] + gT[1] * gphi[1] + gT[2] * gphi[2]
         Fs = mu * gphi + 1.5 * p.xi * p.sigma_T * (g2 * gT - gTgphi * gphi)  # Eq. F_s
-        rho = p.rho_L + phi * (p.rho_H - p.rho_L)
-        Fb = rho * np.array(p.gravity).reshape(3, 1, 1, 1)
+        rho = p.rho_L + phi * (p.rho_H - p.rho_L)                   # Eq. rho(phi)
+        Fb = rho * np.array(p.gravity).reshape(3, 1, 1, 1)           # Eq. F_b
         F = Fs + Fb
-        a = F / rho
         jg = np.einsum("iq,i...->q...", self.S27.c.astype(float), gs)
+        drho = p.rho_H - p.rho_L
+        if drho != 0.0:
+            F = F + self._density_ratio_forces(gs, pstar, phi, rho, gphi, jg, F)
+        a = F / rho
         u = jg + 0.5 * a
         return dict(phi=phi, p=pstar, T=T, u=u, a=a, F=F, rho=rho, gphi=gphi,
                     lphi=lphi, gT=gT, g2=g2)
+
+    def _density_ratio_forces(self, gs, pstar, phi, rho, gphi, jg, Fsb):
+        """F_p + F_mu of Sec. 2.2 (the pressure and viscous correction forces
+        of the velocity-based formulation, zero at density ratio 1):
+          F_p  = -p* c_s^2 (rho_H - rho_L) grad phi,
+          F_mu = nu (rho_H - rho_L) [grad u + (grad u)^T] . grad phi,
+        nu = c_s^2 (tau(phi) - 1/2), tau(phi) = tau_L + phi (tau_H - tau_L).
+        The strain rate comes from the non-equilibrium second moments of the
+        pulled g (the paper's remark after the F_mu equation), by the
+        Chapman-Enskog relation of the forced BGK/CM scheme,
+          sum_i c_ia c_ib (g*_i - g^eq_i + S_i / 2) = -tau c_s^2 (d_a u_b + d_b u_a),
+        with g^eq, the Guo source S and the velocity evaluated from the forces
+        known before F_mu: u0 = j + a0 / 2, a0 = (F_s + F_b + F_p) / rho."""
+        p = self.p
+        drho = p.rho_H - p.rho_L
+        Fp = -pstar * CS2 * drho * gphi
+        a0 = (Fsb + Fp) / rho
+        u0 = jg + 0.5 * a0
+        neq = gs - eq_hydro(pstar, u0, self.S27) + 0.5 * guo_source(u0, a0, self.S27)
+        c = self.S27.c.astype(float)
+        Pi = np.einsum("ia,ib,i...->ab...", c, c, neq)
+        tau = (p.nu_L / CS2 + 0.5) + phi * ((p.nu_H - p.nu_L) / CS2)
+        strain = -Pi / (tau * CS2)
+        nu = CS2 * (tau - 0.5)
+        Fmu = nu * drho * np.einsum("ab...,b...->a...", strain, gphi)
+        return Fp + Fmu
 
     # ------------------------------------------------------------ RK (a9')
     def alpha(self, phi):

@@ -24,7 +24,7 @@ void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
         attr_set = true;
       }
       const dim3 bgrid((unsigned)bulk_sched_blocks(sched));
-      if (P.alpha_ratio || P.tw_waves)
+      if (P.alpha_ratio || P.tw_waves || P.rho_ratio)
         step_bulk_kernel<S, QH, QF, true><<<bgrid, BulkSmem<S, QH, QF>::G::NTHR, bytes, st>>>(
             P, A, maps.h, maps.g, maps.f, sched, mode);
       else

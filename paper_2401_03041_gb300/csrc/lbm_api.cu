@@ -453,6 +453,7 @@ void refresh_devparams(lbm_domain* d) {
   fill_real(q.pd, p, d->prec);
   fill_real(q.pf, p, d->prec);
   q.uniform_rho = p.rho_L == p.rho_H ? 1 : 0;
+  q.rho_ratio = q.uniform_rho ? 0 : 1;
   q.uniform_tau = p.nu_L == p.nu_H ? 1 : 0;
   q.four_over_xi_d = 4.0 / p.xi;
   q.twelve_over_xi_d = 12.0 / p.xi;
@@ -643,8 +644,6 @@ lbm_status lbm_set_params(lbm_domain* d, const lbm_params* p) {
   if (p->rho_L <= 0 || p->rho_H <= 0) return fail(LBM_ERR_ARG, "density must be > 0");
   if (p->eps_n < 0) return fail(LBM_ERR_ARG, "eps_n must be >= 0");
   if (p->T_bottom_waves < 0) return fail(LBM_ERR_ARG, "T_bottom_waves must be >= 0");
-  if (p->rho_L != p->rho_H)
-    return fail(LBM_ERR_UNSUPPORTED, "density ratio != 1 (pressure/viscous correction forces) not built");
   if (p->omega_high != 1.0)
     return fail(LBM_ERR_UNSUPPORTED, "higher-order central-moment rate != 1 not built");
   d->params = *p;
@@ -1144,6 +1143,8 @@ lbm_status adj_check(lbm_domain* d) {
     return fail(LBM_ERR_UNSUPPORTED, "the adjoint needs FP64 storage and the D3Q7 thermal LB");
   if (d->dp.alpha_ratio)
     return fail(LBM_ERR_UNSUPPORTED, "the adjoint is built for equal diffusivities (alpha_L == alpha_H)");
+  if (d->dp.rho_ratio)
+    return fail(LBM_ERR_UNSUPPORTED, "the adjoint is built for equal densities (rho_L == rho_H)");
   if ((long long)d->nx * d->ny >= (1LL << 31))
     return fail(LBM_ERR_UNSUPPORTED, "the adjoint needs nx * ny < 2^31");
   return LBM_OK;

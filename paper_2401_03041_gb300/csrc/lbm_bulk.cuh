@@ -430,14 +430,21 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
             const S* p_ = grow + (size_t)i * G::GB;
             return Store<S>::ld_s(b ? p_ : p_ - cx<27>(i));
           };
+          // density ratio (EXT only): the g role adds F_p and F_mu, which need
+          // the moments of g, and hands u and p* back after a second pair
+          // barrier; the exchange slots then carry phi, a, grad phi (h/f role)
+          // and u, p* (g role)
+          const bool ratio = EXT && P.rho_ratio;
           GMoments<R> m;
           if (active) {
             m = g_moments<R>(getg);
             if (mode & MODE_SAVE) save_moments<S>(P, A, cell, m);
-            xch[4 * NC + cidx] = m.jx;
-            xch[5 * NC + cidx] = m.jy;
-            xch[6 * NC + cidx] = m.jz;
-            xch[7 * NC + cidx] = m.pst;
+            if (!ratio) {
+              xch[4 * NC + cidx] = m.jx;
+              xch[5 * NC + cidx] = m.jy;
+              xch[6 * NC + cidx] = m.jz;
+              xch[7 * NC + cidx] = m.pst;
+            }
           }
           if constexpr (GR == 1) {
             // every g-role thread has read G(z): warp 0 of the role refills
@@ -454,6 +461,26 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
             }
           }
           pair_sync();
+          if constexpr (EXT) {
+            if (ratio) {
+              CellFlow<R> f;
+              const R phi = active ? xch[cidx] : (R)0;
+              if (active) {
+                CellForce<R> F;
+                F.ax = xch[NC + cidx]; F.ay = xch[2 * NC + cidx]; F.az = xch[3 * NC + cidx];
+                F.rho = (R)rp.rho_L + phi * (R)(rp.rho_H - rp.rho_L);
+                density_ratio_accel<R>(P, phi, xch[4 * NC + cidx], xch[5 * NC + cidx], xch[6 * NC + cidx], m, F);
+                f = cell_velocity<R>(F.ax, F.ay, F.az, F.rho, m.jx, m.jy, m.jz);
+                xch[cidx] = f.ux;
+                xch[NC + cidx] = f.uy;
+                xch[2 * NC + cidx] = f.uz;
+                xch[3 * NC + cidx] = m.pst;
+              }
+              pair_sync();
+              if (active && (mode & MODE_COLLIDE)) collide_g<S>(P, A, pcell, phi, m, f);
+              return;
+            }
+          }
           if (active && (mode & MODE_COLLIDE)) {
             const R phi = xch[cidx];
             const CellFlow<R> f = cell_velocity<R>(xch[NC + cidx], xch[2 * NC + cidx], xch[3 * NC + cidx],
@@ -487,13 +514,38 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
           xch[NC + cidx] = F.ax;
           xch[2 * NC + cidx] = F.ay;
           xch[3 * NC + cidx] = F.az;
+          if (EXT && P.rho_ratio) {
+            xch[4 * NC + cidx] = fd.gpx;
+            xch[5 * NC + cidx] = fd.gpy;
+            xch[6 * NC + cidx] = fd.gpz;
+          }
         }
         pair_sync();
+        R ex_u[3] = {0, 0, 0}, ex_p = 0;
+        if (EXT && P.rho_ratio) {
+          // u and p* from the g role, which added F_p and F_mu
+          pair_sync();
+          if (active) {
+            ex_u[0] = xch[cidx]; ex_u[1] = xch[NC + cidx]; ex_u[2] = xch[2 * NC + cidx];
+            ex_p = xch[3 * NC + cidx];
+          }
+        }
         if (active) {
           const R phi = cen.x, Tc = cen.y;
-          const CellFlow<R> f = cell_velocity<R>(F.ax, F.ay, F.az, F.rho, xch[4 * NC + cidx], xch[5 * NC + cidx],
-                                                 xch[6 * NC + cidx]);
-          cell_outputs<S>(P, A, x, y, z, cell, mode, phi, Tc, xch[7 * NC + cidx], f, dsum);
+          CellFlow<R> f;
+          R pst;
+          if (EXT && P.rho_ratio) {
+            f.ux = ex_u[0]; f.uy = ex_u[1]; f.uz = ex_u[2];
+            f.uu = f.ux * f.ux + f.uy * f.uy + f.uz * f.uz;
+            f.rho = F.rho;
+            f.ax = f.ay = f.az = (R)0;   // (not used by the h / f collisions)
+            pst = ex_p;
+          } else {
+            f = cell_velocity<R>(F.ax, F.ay, F.az, F.rho, xch[4 * NC + cidx], xch[5 * NC + cidx],
+                                 xch[6 * NC + cidx]);
+            pst = xch[7 * NC + cidx];
+          }
+          cell_outputs<S>(P, A, x, y, z, cell, mode, phi, Tc, pst, f, dsum);
           if (mode & MODE_COLLIDE) {
             auto run = [&](auto btag) {
               constexpr bool BOUNCE = decltype(btag)::value;
@@ -545,7 +597,10 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
       if (pending & (1u << k)) mbar_wait(&bar[k], (pend_par >> k) & 1u);
     return;
   }
-  if (mode & MODE_DIAG) diag_block_reduce<NT>(dsum, A.diag_partials);
+  // the reduction's scratch reuses the h/f ring (no copies are in flight and
+  // every thread has passed the last plane's barrier), so the kernel needs
+  // no static shared memory beyond its dynamic layout
+  if (mode & MODE_DIAG) diag_block_reduce_in<NT>(dsum, A.diag_partials, reinterpret_cast<double*>(smem + L::off_hf));
 }
 
 }  // namespace lbm

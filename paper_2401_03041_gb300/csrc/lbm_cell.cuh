@@ -291,6 +291,39 @@ __device__ __forceinline__ CellForce<R> cell_force(const DevParams& P, int x, in
   return f;
 }
 
+// a5 with a density ratio (Sec. 2.2): adds the pressure and viscous
+// correction forces of the velocity-based formulation to a = (F_s + F_b) / rho,
+//   F_p  = -p* c_s^2 (rho_H - rho_L) grad phi,
+//   F_mu = nu (rho_H - rho_L) [grad u + (grad u)^T] . grad phi,
+// nu = c_s^2 (tau(phi) - 1/2).  The strain rate is taken from the second
+// moments of the pulled g (no finite differences of u): with u0 = j + a0/2,
+// a0 = (F_s + F_b + F_p) / rho,
+//   Pi_ab = sum_i g*_i c_ia c_ib - p* c_s^2 d_ab - u0_a u0_b + (u0_a a0_b + a0_a u0_b) / 2
+// (the non-equilibrium second moment plus half the Guo source's) equals
+// -tau c_s^2 (d_a u_b + d_b u_a), so F_mu = -((tau - 1/2) / tau) (rho_H - rho_L) Pi . grad phi.
+template <class R>
+__device__ __forceinline__ void density_ratio_accel(const DevParams& P, R phi, R gpx, R gpy, R gpz,
+                                                    const GMoments<R>& m, CellForce<R>& F) {
+  const auto& rp = RP<R>(P);
+  const R drho = (R)(rp.rho_H - rp.rho_L);
+  const R irho = (R)1 / F.rho;
+  const R fp = -m.pst * (R)(1.0 / 3.0) * drho * irho;
+  const R a0x = F.ax + fp * gpx, a0y = F.ay + fp * gpy, a0z = F.az + fp * gpz;
+  const R ux = m.jx + (R)0.5 * a0x, uy = m.jy + (R)0.5 * a0y, uz = m.jz + (R)0.5 * a0z;
+  const R p3 = m.pst * (R)(1.0 / 3.0);
+  const R Pxx = m.sxx - p3 - ux * ux + ux * a0x;
+  const R Pyy = m.syy - p3 - uy * uy + uy * a0y;
+  const R Pzz = m.szz - p3 - uz * uz + uz * a0z;
+  const R Pxy = m.sxy - ux * uy + (R)0.5 * (ux * a0y + a0x * uy);
+  const R Pxz = m.sxz - ux * uz + (R)0.5 * (ux * a0z + a0x * uz);
+  const R Pyz = m.syz - uy * uz + (R)0.5 * (uy * a0z + a0y * uz);
+  const R tau = (R)rp.tau_L + phi * (R)(rp.tau_H - rp.tau_L);
+  const R coef = -(tau - (R)0.5) / tau * drho * irho;
+  F.ax = a0x + coef * (Pxx * gpx + Pxy * gpy + Pxz * gpz);
+  F.ay = a0y + coef * (Pxy * gpx + Pyy * gpy + Pyz * gpz);
+  F.az = a0z + coef * (Pxz * gpx + Pyz * gpy + Pzz * gpz);
+}
+
 // a6: velocity u = j + a/2 (Guo) from the first moment j of the pulled g.
 template <class R>
 struct CellFlow {
@@ -593,8 +626,9 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
     save_stencil<S>(P, A, cell, phi, Tc, fdv);
     save_moments<S>(P, A, cell, m);
   }
-  const CellFlow<R> f = cell_flow<R>(P, x, y, z, phi, Tc, fdv.gpx, fdv.gpy, fdv.gpz, fdv.lp, fdv.gtx, fdv.gty,
-                                     fdv.gtz, m.jx, m.jy, m.jz);
+  CellForce<R> F = cell_force<R>(P, x, y, z, phi, Tc, fdv.gpx, fdv.gpy, fdv.gpz, fdv.lp, fdv.gtx, fdv.gty, fdv.gtz);
+  if (P.rho_ratio) density_ratio_accel<R>(P, phi, fdv.gpx, fdv.gpy, fdv.gpz, m, F);
+  const CellFlow<R> f = cell_velocity<R>(F.ax, F.ay, F.az, F.rho, m.jx, m.jy, m.jz);
   cell_outputs<S>(P, A, x, y, z, cell, mode, phi, Tc, m.pst, f, dsum);
   if (!(mode & MODE_COLLIDE)) return;
   collide_g<S>(P, A, pcell, phi, m, f);

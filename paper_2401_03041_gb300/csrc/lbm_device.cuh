@@ -149,6 +149,7 @@ struct DevParams {
   // parameter: 4/xi, 12/xi, and for uniform density / viscosity (flags set)
   // 1/rho and 1/tau of the g collision.
   int uniform_rho, uniform_tau;
+  int rho_ratio;   // rho_H != rho_L: the pressure and viscous correction forces F_p, F_mu
   double four_over_xi_d, twelve_over_xi_d, inv_rho_d, omega_g_d;
   float four_over_xi_f, twelve_over_xi_f, inv_rho_f, omega_g_f;
 };

@@ -67,25 +67,31 @@ __device__ __forceinline__ typename Store<S>::R pulled_sum(const DevParams& P, c
   return s;
 }
 
-// Fixed-order block reduction of the FP64 diagnostics partials.
+// Fixed-order block reduction of the FP64 diagnostics partials, through
+// red[NT / 32][kDiagVals] doubles of shared memory.
 template <int NT>
-__device__ __forceinline__ void diag_block_reduce(const double* dsum, double* out_partials) {
-  __shared__ double s_red[NT / 32][kDiagVals];
+__device__ __forceinline__ void diag_block_reduce_in(const double* dsum, double* out_partials, double* red) {
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
 #pragma unroll
   for (int k = 0; k < kDiagVals; ++k) {
     double v = dsum[k];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if ((tid & 31) == 0) s_red[tid >> 5][k] = v;
+    if ((tid & 31) == 0) red[(tid >> 5) * kDiagVals + k] = v;
   }
   __syncthreads();
   if (tid < kDiagVals) {
     double v = 0.0;
-    for (int w = 0; w < NT / 32; ++w) v += s_red[w][tid];
+    for (int w = 0; w < NT / 32; ++w) v += red[w * kDiagVals + tid];
     const size_t b = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     out_partials[b * kDiagVals + tid] = v;
   }
+}
+
+template <int NT>
+__device__ __forceinline__ void diag_block_reduce(const double* dsum, double* out_partials) {
+  __shared__ double s_red[NT / 32 * kDiagVals];
+  diag_block_reduce_in<NT>(dsum, out_partials, s_red);
 }
 
 // QF = 0: RK thermal (T stored as a field); QF in {7, 15, 19, 27}: LB thermal.

@@ -188,10 +188,11 @@ def test_capture_objective_autograd():
     assert np.allclose(I.grad.numpy(), g_ref, rtol=1e-5, atol=0)
 
 
-def test_adjoint_rejects_conductivity_ratio():
+@pytest.mark.parametrize("change", [{"alpha_H": 0.01}, {"rho_H": 3.0}])
+def test_adjoint_rejects_conductivity_and_density_ratio(change):
     from paper_2401_03041_gb300 import lbm
     w = W.config5(n=16)
-    w = w.replace(params=W.Params(**dict(w.params.__dict__, alpha_H=0.01)))
+    w = w.replace(params=W.Params(**dict(w.params.__dict__, **change)))
     d = gpu_domain(w)
     with pytest.raises(lbm.LBMError) as e:
         d.adjoint_run(4, 2, w.target)

@@ -231,6 +231,58 @@ def test_modulated_bottom_wall_fp64(thermal, ratio):
         compare_all(d, o, w, TOL64, f"modulated wall {thermal} ratio={ratio} {kern}")
 
 
+def _density_workload(thermal, walls=True, q_phase=15, ratio=10.0, shape=(40, 20, 13), alpha_ratio=False):
+    w = ragged_workload(thermal, q_phase, walls=walls, shape=shape)
+    kw = dict(w.params.__dict__, rho_L=1.0, rho_H=ratio)
+    if alpha_ratio:
+        kw.update(alpha_L=0.1, alpha_H=0.02)
+    return w.replace(params=W.Params(**kw))
+
+
+@pytest.mark.parametrize("thermal,walls,q_phase,alpha_ratio",
+                         [("D3Q7", True, 15, False), ("D3Q19", False, 15, False), ("RK4", True, 27, False),
+                          ("D3Q15", True, 15, True), ("RK2", False, 15, True), ("D3Q27", True, 27, False)])
+def test_density_ratio_fp64(thermal, walls, q_phase, alpha_ratio):
+    """rho_H / rho_L = 10 (Sec. 2.2 pressure and viscous correction forces,
+    strain from the non-equilibrium moments of g), unequal viscosities,
+    gravity, moving droplets, with and without a conductivity ratio, walls
+    or periodic z, both phase-field stencils: generic and bulk kernels match
+    the oracle within 1e-11 after 12 steps."""
+    w = _density_workload(thermal, walls, q_phase, alpha_ratio=alpha_ratio)
+    o = oracle_for(w)
+    o.step(12)
+    for kern in _kernels("fp64", q_phase, thermal):
+        d = gpu_domain(w, kernel=kern)
+        d.step(12)
+        compare_all(d, o, w, TOL64, f"density ratio {thermal} walls={walls} q{q_phase} {kern}")
+
+
+@pytest.mark.parametrize("walls", [True, False])
+def test_density_ratio_bulk_fp64_60_steps(walls):
+    """The bulk kernel's density-ratio path (second exchange between its two
+    roles) over 60 steps on a 72-wide lattice."""
+    w = _density_workload("D3Q7", walls, shape=(72, 24, 20))
+    o = oracle_for(w)
+    o.step(60)
+    d = gpu_domain(w, kernel="bulk")
+    d.step(60)
+    compare_all(d, o, w, TOL64, f"density ratio bulk 60 steps walls={walls}")
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 2e-4), ("fp16", 5e-2)])
+def test_density_ratio_reduced_precision(precision, tol):
+    """FP32 / FP16-storage density-ratio runs (bulk kernel) stay within the
+    reduced-precision error of the FP64 run after 40 steps."""
+    w = _density_workload("D3Q7", True, shape=(88, 24, 12))
+    ref = gpu_domain(w)
+    ref.step(40)
+    d = gpu_domain(w, precision=precision, kernel="bulk")
+    d.step(40)
+    a, b = gpu_fields(d), gpu_fields(ref)
+    for k in ("phi", "T"):
+        assert relerr(a[k], b[k]) < tol, (precision, k, relerr(a[k], b[k]))
+
+
 @pytest.mark.parametrize("precision,tol", [("fp32", 2e-4), ("fp16", 5e-2)])
 def test_conductivity_ratio_reduced_precision(precision, tol):
     """FP32 / FP16-storage runs of the ratio workload (D3Q7 and RK4) stay
