@@ -2,7 +2,7 @@
 // conversion, diagnostics reduction).
 #include "launchers.h"
 #include "lbm_aux.cuh"
-#include "lbm_bulk.cuh"
+#include "lbm_skew.cuh"
 
 namespace lbm {
 
@@ -57,6 +57,28 @@ static size_t bulk_bytes_qf(int qf) {
 template <class S>
 static size_t bulk_bytes_s(int qh, int qf) {
   return qh == 15 ? bulk_bytes_qf<S, 15>(qf) : bulk_bytes_qf<S, 27>(qf);
+}
+
+template <class S, int QH, int QF>
+static constexpr size_t skew_bytes_one() {
+  return skew_fits<S, QH, QF>() ? SkewSmem<S, QH, QF>::bytes : 0;
+}
+
+template <class S, int QH>
+static size_t skew_bytes_qf(int qf) {
+  switch (qf) {
+    case 0: return skew_bytes_one<S, QH, 0>();
+    case 7: return skew_bytes_one<S, QH, 7>();
+    case 15: return skew_bytes_one<S, QH, 15>();
+    case 19: return skew_bytes_one<S, QH, 19>();
+    default: return skew_bytes_one<S, QH, 27>();
+  }
+}
+
+size_t skew_smem_bytes(int prec, int qh, int qf) {
+  if (prec == 0) return qh == 15 ? skew_bytes_qf<double, 15>(qf) : skew_bytes_qf<double, 27>(qf);
+  if (prec == 1) return qh == 15 ? skew_bytes_qf<float, 15>(qf) : skew_bytes_qf<float, 27>(qf);
+  return qh == 15 ? skew_bytes_qf<__half, 15>(qf) : skew_bytes_qf<__half, 27>(qf);
 }
 
 size_t bulk_smem_bytes(int prec, int qh, int qf) {

@@ -5,7 +5,7 @@
 
 #include "launchers.h"
 #include "lbm_aux.cuh"
-#include "lbm_bulk.cuh"
+#include "lbm_skew.cuh"
 
 namespace lbm {
 
@@ -14,6 +14,29 @@ void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                  dim3 grid, int zchunk, const BulkSched& sched, int mode, int use_bulk, cudaStream_t st) {
   constexpr size_t bytes = BulkSmem<S, QH, QF>::bytes;
   if constexpr (bytes <= kMaxDynSmem) {
+    const dim3 bgrid((unsigned)bulk_sched_blocks(sched));
+    if constexpr (skew_fits<S, QH, QF>()) {
+      // the skewed kernel, except with a density ratio (its forces need the
+      // moments and the stencils of one plane together)
+      if (use_bulk == 2 && !P.rho_ratio) {
+        constexpr size_t sbytes = SkewSmem<S, QH, QF>::bytes;
+        static bool sattr_set = false;
+        if (!sattr_set) {
+          cudaFuncSetAttribute(step_skew_kernel<S, QH, QF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sbytes);
+          cudaFuncSetAttribute(step_skew_kernel<S, QH, QF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sbytes);
+          sattr_set = true;
+        }
+        if (P.alpha_ratio || P.tw_waves)
+          step_skew_kernel<S, QH, QF, true><<<bgrid, SkewSmem<S, QH, QF>::G::NTHR, sbytes, st>>>(
+              P, A, maps.h, maps.g, maps.f, sched, mode);
+        else
+          step_skew_kernel<S, QH, QF, false><<<bgrid, SkewSmem<S, QH, QF>::G::NTHR, sbytes, st>>>(
+              P, A, maps.h, maps.g, maps.f, sched, mode);
+        return;
+      }
+    }
     if (use_bulk) {
       static bool attr_set = false;
       if (!attr_set) {
@@ -23,7 +46,6 @@ void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                              (int)bytes);
         attr_set = true;
       }
-      const dim3 bgrid((unsigned)bulk_sched_blocks(sched));
       if (P.alpha_ratio || P.tw_waves || P.rho_ratio)
         step_bulk_kernel<S, QH, QF, true><<<bgrid, BulkSmem<S, QH, QF>::G::NTHR, bytes, st>>>(
             P, A, maps.h, maps.g, maps.f, sched, mode);

@@ -17,8 +17,10 @@ struct TMaps {
   CUtensorMap h, g, f;
 };
 
+// use_bulk: 0 generic kernel, 1 bulk kernel, 2 skewed kernel where its layout
+// fits (lbm_skew.cuh; the bulk kernel otherwise and with a density ratio).
 // grid / zchunk: the generic kernel's launch (TX x TY tiles, z-chunks);
-// sched: the bulk kernel's work assignment (one-dimensional grid).
+// sched: the bulk kernels' work assignment (one-dimensional grid).
 template <class S, int QH, int QF>
 void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A, const TMaps& maps,
                  dim3 grid, int zchunk, const BulkSched& sched, int mode, int use_bulk, cudaStream_t st);
@@ -30,6 +32,7 @@ void launch_ghost_fill(const DevParams& P, void* buf, int nq, cudaStream_t st);
 // Dynamic shared memory of the bulk kernel for (precision, q_phase, q_f),
 // and the largest a CTA may use; also its tile height.
 size_t bulk_smem_bytes(int prec, int qh, int qf);
+size_t skew_smem_bytes(int prec, int qh, int qf);   // 0: the skewed layout does not fit
 int bulk_tile_rows(int prec, int qh, int qf);
 int bulk_tile_cols(int prec);
 int bulk_box_cols(int prec);   // staged row length W of the bulk kernel

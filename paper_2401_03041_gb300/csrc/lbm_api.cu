@@ -58,7 +58,7 @@ struct Geometry {
   dim3 grid;       // generic kernel: (tiles x, tiles y, chunks); bulk: the same counts (reported only)
   int zchunk;
   int nblocks;     // blocks of one launch (diagnostics partials)
-  int bulk;        // 1: bulk kernel (tensor-TMA staging), 0: generic kernel
+  int bulk;        // 2: skewed kernel, 1: bulk kernel (tensor-TMA staging), 0: generic kernel
   BulkSched sched;
 };
 
@@ -123,6 +123,11 @@ Geometry geometry(int nx, int ny, int nz, lbm_precision prec, int qh, int qf, in
   const char* env = std::getenv("LBM_ZCHUNK");
   const int forced = env ? std::atoi(env) : 0;
   if (g.bulk) {
+    // the skewed kernel where its layout fits (LBM_KERNEL=bulk keeps the bulk one)
+    const char* kenv = std::getenv("LBM_KERNEL");
+    const bool no_skew = kenv && std::strcmp(kenv, "bulk") == 0;
+    if (!no_skew && skew_smem_bytes((int)prec, qh, qf) > 0 && skew_smem_bytes((int)prec, qh, qf) <= kMaxDynSmem)
+      g.bulk = 2;
     g.sched = bulk_schedule(bx, by, nz, sms > 0 ? sms : 1, forced);
     g.zchunk = g.sched.zchunk;
     g.grid = dim3(bx, by, g.sched.nchunk);
@@ -1058,7 +1063,9 @@ lbm_status lbm_kernel_info(lbm_domain* d, int32_t* info) {
   info[2] = (int32_t)d->geo.grid.y;
   info[3] = (int32_t)d->geo.grid.z;
   info[4] = d->geo.zchunk;
-  info[5] = d->geo.bulk ? (int32_t)bulk_smem_bytes((int)d->prec, d->qh, d->qf) : 0;
+  info[5] = d->geo.bulk == 2   ? (int32_t)skew_smem_bytes((int)d->prec, d->qh, d->qf)
+            : d->geo.bulk == 1 ? (int32_t)bulk_smem_bytes((int)d->prec, d->qh, d->qf)
+                               : 0;
   return LBM_OK;
 }
 

@@ -213,6 +213,92 @@ __device__ __forceinline__ void issue_stage(const DevParams& P, const CUtensorMa
   tma_load_4d(dst, map, x0 - G::GXP + P.GX, yy + P.GY, zz, q, bar);
 }
 
+// phi and T over the (TYB + 2) x (TXB + 2) halo tile of plane p, summed from
+// the staged h / f boxes of that plane (st), into the interleaved (phi, T)
+// plane pt; items k0, k0 + kstep, ... of the tile.  Ghost planes beyond a z
+// wall mirror phi and take T_g = 2 T_w - T; with an RK energy solver T comes
+// from the stored field.  Planes next to a wall take the bounce-back variant
+// (BOUNCE = true); all other planes run the select-free one.
+template <class S, int QH, int QF, bool EXT, class G, bool BOUNCE>
+__device__ __forceinline__ void stage_sum_plane_v(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
+                                                  const S* st, typename PairOf<typename Store<S>::R>::type* pt,
+                                                  int p, int pe, bool ghost, bool lo, bool hi, int x0, int y0,
+                                                  int k0, int kstep) {
+  using R = typename Store<S>::R;
+  using P2 = typename PairOf<R>::type;
+  const auto& rp = RP<R>(P);
+  const R shh = (R)rp.shift_h, shf = (R)rp.shift_f;
+  for (int k = k0; k < G::HPB; k += kstep) {
+    const int hr = k / G::HXB, hc = k % G::HXB;
+    const int col = hc + G::GXP - 1;
+    const S* rowb = st + (size_t)hr * G::W + col;
+    R phi = 0;
+    static_for<0, QH>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const bool b = BOUNCE && ((cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi));
+      const S* rowp = rowb + (size_t)i * G::HFB;
+      phi += Store<S>::ld_s(b ? rowp : rowp - cx<QH>(i));
+    });
+    phi += shh;  // sum_i w_i * shift_h
+    R T;
+    // wall temperature below this halo column (its x wrapped into the lattice)
+    auto bottom_T = [&]() {
+      int gx = x0 + hc - 1;
+      gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
+      return wall_T<R>(P, gx, true);
+    };
+    if constexpr (QF > 0) {
+      // stored values (shifted by w_i s, s = shift_f; sum_i w_i = 1);
+      // anti-bounce-back in stored form: -v_s + 2 w_i (T_w - s)
+      T = shf;
+      R Tb = 0, Tt = 0;
+      if constexpr (BOUNCE) {
+        if constexpr (EXT) Tb = bottom_T() - shf;
+        else Tb = (R)rp.T_bottom - shf;
+        Tt = (R)rp.T_top - shf;
+      }
+      static_for<0, QF>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
+        const S* rowp = rowb + (size_t)(QH + i) * G::HFB;
+        const R v = Store<S>::ld_s(b ? rowp : rowp - cx<QF>(i));
+        T += b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? Tb : Tt)) : v;
+      });
+    } else {
+      int gx = x0 + hc - 1, gy = y0 + hr - 1;
+      gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
+      gy = gy < 0 ? gy + P.ny : (gy >= P.ny ? gy - P.ny : gy);
+      T = A.T[cell_index(P, gx, gy, pe)];
+    }
+    if constexpr (EXT) {
+      if (ghost) T = (R)2 * (p < 0 ? bottom_T() : (R)rp.T_top) - T;
+    } else {
+      if (ghost) T = (R)2 * (p < 0 ? rp.T_bottom : rp.T_top) - T;
+    }
+    P2 v;
+    v.x = phi;
+    v.y = T;
+    pt[k] = v;
+  }
+}
+
+template <class S, int QH, int QF, bool EXT, class G>
+__device__ __forceinline__ void stage_sum_plane(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
+                                                const S* st, typename PairOf<typename Store<S>::R>::type* pt,
+                                                int p, int x0, int y0, int k0, int kstep) {
+  int pe = p;
+  bool ghost = false;
+  if (P.walls) {
+    if (p < 0) { pe = 0; ghost = true; }
+    else if (p >= P.nz) { pe = P.nz - 1; ghost = true; }
+  } else {
+    pe = p < 0 ? p + P.nz : (p >= P.nz ? p - P.nz : p);  // periodic z
+  }
+  const bool lo = P.walls && pe == 0, hi = P.walls && pe == P.nz - 1;
+  if (lo || hi) stage_sum_plane_v<S, QH, QF, EXT, G, true>(P, A, st, pt, p, pe, ghost, lo, hi, x0, y0, k0, kstep);
+  else stage_sum_plane_v<S, QH, QF, EXT, G, false>(P, A, st, pt, p, pe, ghost, false, false, x0, y0, k0, kstep);
+}
+
 // EXT: the extensions of the uniform-property model (conductivity ratio,
 // modulated bottom wall) are compiled in; lattices without them run the
 // EXT = false instantiation, which carries none of their code.
@@ -272,78 +358,9 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
   auto hf_ptr = [&](int p) { return hf + (size_t)hf_slot(p) * L::hf_stage; };
   auto g_ptr = [&](int p) { return gb + (size_t)g_slot(p) * L::g_stage; };
 
-  // phi / T of the halo tile of plane p from HF(p) -> phi/T slot (p - z0 + 1) % 3.
-  // Planes next to a wall take the bounce-back branch (BOUNCE = true); all
-  // other planes run the select-free variant.
-  auto sum_plane_impl = [&](auto btag, int p, int pe, bool ghost, bool lo, bool hi) {
-    constexpr bool BOUNCE = decltype(btag)::value;
-    const S* st = hf_ptr(p);
-    P2* pt = s_pt + hf_slot(p) * G::HPB;
-    for (int k = tid; k < G::HPB; k += NT) {
-      const int hr = k / G::HXB, hc = k % G::HXB;
-      const int col = hc + G::GXP - 1;
-      const S* rowb = st + (size_t)hr * G::W + col;
-      R phi = 0;
-      static_for<0, QH>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        const bool b = BOUNCE && ((cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi));
-        const S* rowp = rowb + (size_t)i * G::HFB;
-        phi += Store<S>::ld_s(b ? rowp : rowp - cx<QH>(i));
-      });
-      phi += shh;  // sum_i w_i * shift_h
-      R T;
-      // wall temperature below this halo column (its x wrapped into the lattice)
-      auto bottom_T = [&]() {
-        int gx = x0 + hc - 1;
-        gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
-        return wall_T<R>(P, gx, true);
-      };
-      if constexpr (QF > 0) {
-        // stored values (shifted by w_i s, s = shift_f; sum_i w_i = 1);
-        // anti-bounce-back in stored form: -v_s + 2 w_i (T_w - s)
-        T = shf;
-        R Tb = 0, Tt = 0;
-        if constexpr (BOUNCE) {
-          if constexpr (EXT) Tb = bottom_T() - shf;
-          else Tb = (R)rp.T_bottom - shf;
-          Tt = (R)rp.T_top - shf;
-        }
-        static_for<0, QF>([&](auto I) {
-          constexpr int i = decltype(I)::value;
-          const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
-          const S* rowp = rowb + (size_t)(QH + i) * G::HFB;
-          const R v = Store<S>::ld_s(b ? rowp : rowp - cx<QF>(i));
-          T += b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? Tb : Tt)) : v;
-        });
-      } else {
-        int gx = x0 + hc - 1, gy = y0 + hr - 1;
-        gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
-        gy = gy < 0 ? gy + P.ny : (gy >= P.ny ? gy - P.ny : gy);
-        T = A.T[cell_index(P, gx, gy, pe)];
-      }
-      if constexpr (EXT) {
-        if (ghost) T = (R)2 * (p < 0 ? bottom_T() : (R)rp.T_top) - T;
-      } else {
-        if (ghost) T = (R)2 * (p < 0 ? rp.T_bottom : rp.T_top) - T;
-      }
-      P2 v;
-      v.x = phi;
-      v.y = T;
-      pt[k] = v;
-    }
-  };
+  // phi / T of the halo tile of plane p from HF(p) -> phi/T slot (p - z0 + 1) % 3
   auto sum_plane = [&](int p) {
-    int pe = p;
-    bool ghost = false;
-    if (P.walls) {
-      if (p < 0) { pe = 0; ghost = true; }
-      else if (p >= P.nz) { pe = P.nz - 1; ghost = true; }
-    } else {
-      pe = p < 0 ? p + P.nz : (p >= P.nz ? p - P.nz : p);  // periodic z
-    }
-    const bool lo = P.walls && pe == 0, hi = P.walls && pe == P.nz - 1;
-    if (lo || hi) sum_plane_impl(std::true_type{}, p, pe, ghost, lo, hi);
-    else sum_plane_impl(std::false_type{}, p, pe, ghost, false, false);
+    stage_sum_plane<S, QH, QF, EXT, G>(P, A, hf_ptr(p), s_pt + hf_slot(p) * G::HPB, p, x0, y0, tid, NT);
   };
 
   double dsum[kDiagVals];

@@ -1,0 +1,363 @@
+// lbm_skew.cuh - the fused time-step kernel with the two roles of a cell
+// skewed by one plane, so that they never wait for each other inside a plane.
+//
+// Same staging as the bulk kernel (lbm_bulk.cuh: tensor-TMA boxes of the
+// pulled PDFs, a ring of three h/f stages, a g ring, interleaved (phi, T)
+// planes) and the same per-cell arithmetic (lbm_cell.cuh).  What differs is
+// the schedule of the two threads of a cell.  In the bulk kernel the g role
+// needs the acceleration a(z) of the stencil role and the stencil role needs
+// the first moment j(z) of the g role within the same plane, so both meet at
+// a barrier between their two halves and each waits for the other's slower
+// half.  Here, while the CTA marches over plane z,
+//   g role (A):       collides g of plane z      (m(z), and phi(z), a(z) that
+//                                                  B left in the exchange),
+//                     then takes the moments m(z + 2) of the staged G(z + 2);
+//   stencil role (B): sums phi / T of plane z + 2 from the staged h/f boxes,
+//                     computes the stencils and the force of plane z + 1,
+//                     leaves phi(z + 1), a(z + 1) for A, and collides h and f
+//                     of plane z + 1 with j(z + 1), p*(z + 1) that A left
+//                     there one plane earlier.
+// Every value a role reads from the other was written in an earlier plane,
+// so the roles meet only at the one block barrier that ends each plane (the
+// exchange is double-buffered by plane parity).  The g role carries the
+// moments of two planes in registers; the h/f ring still needs only three
+// stages (h/f boxes of z + 1 for the collisions, z + 2 just summed, z + 3 in
+// flight).
+//
+// The density-ratio forces need the moments of g and the stencil of the same
+// plane in one place, so a lattice with rho_L != rho_H runs the bulk kernel.
+// Every wait is bounded (about 2 s); on a timeout the CTA raises the domain's
+// error flag, drains its outstanding copies (bounded too) and returns.
+#pragma once
+
+#include "lbm_bulk.cuh"
+
+namespace lbm {
+
+template <class S, int QH, int QF, int TYB_>
+struct SkewSmemT {
+  using R = typename Store<S>::R;
+  using G = BulkGeom<S, TYB_>;
+  static constexpr int NHF = QH + QF;
+  static constexpr size_t hf_stage = (size_t)NHF * G::HFB;   // elements
+  static constexpr size_t g_stage = (size_t)27 * G::GB;
+  // exchange slots per cell and plane parity: phi, a (3) from B; j (3), p* from A
+  static constexpr int NX = 8;
+  static constexpr size_t fixed_bytes = 3 * hf_stage * sizeof(S) + 3 * G::HPB * 2 * sizeof(R) +
+                                        2 * NX * G::NT * sizeof(R) + 5 * sizeof(uint64_t) + 128 + 64;
+  // g ring: G(z + 2) consumed while G(z + 3) is in flight where two stages
+  // fit, else one stage refilled right after the moments are taken
+  static constexpr int GR = fixed_bytes + 2 * g_stage * sizeof(S) <= 232448 ? 2 : 1;
+  static constexpr size_t off_hf = 0;
+  static constexpr size_t off_g = off_hf + 3 * hf_stage * sizeof(S);
+  static constexpr size_t off_pt = (off_g + GR * g_stage * sizeof(S) + 15) & ~size_t(15);
+  static constexpr size_t off_x = (off_pt + 3 * G::HPB * 2 * sizeof(R) + 15) & ~size_t(15);
+  static constexpr size_t off_bar = (off_x + 2 * (size_t)NX * G::NT * sizeof(R) + 15) & ~size_t(15);
+  // + 128: the start of the dynamic shared memory is aligned at run time
+  static constexpr size_t bytes = off_bar + 5 * sizeof(uint64_t) + 128;
+  static constexpr uint32_t hf_tx = (uint32_t)((size_t)NHF * G::W * (G::TYB + 2) * sizeof(S));
+  static constexpr uint32_t g_tx = (uint32_t)((size_t)27 * G::W * G::TYB * sizeof(S));
+};
+
+// The skewed kernel uses the bulk kernel's tile (one launch geometry for
+// both, so that a lattice can switch between them); it is available where its
+// layout fits at that tile height.
+template <class S, int QH, int QF>
+using SkewSmem = SkewSmemT<S, QH, QF, BulkSmem<S, QH, QF>::G::TYB>;
+
+template <class S, int QH, int QF>
+constexpr bool skew_fits() {
+  return SkewSmem<S, QH, QF>::bytes <= 232448;
+}
+
+template <class S, int QH, int QF, bool EXT>
+__global__ void __launch_bounds__(SkewSmem<S, QH, QF>::G::NTHR, 1)
+step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
+                 const __grid_constant__ CUtensorMap mh, const __grid_constant__ CUtensorMap mg,
+                 const __grid_constant__ CUtensorMap mf, const BulkSched sched, int mode) {
+  using R = typename Store<S>::R;
+  using L = SkewSmem<S, QH, QF>;
+  using G = typename L::G;
+  using P2 = typename PairOf<R>::type;
+  constexpr int NC = G::NT;       // cells per CTA
+  constexpr int NT = G::NTHR;     // threads per CTA
+  constexpr int NX = L::NX;
+  constexpr int GR = L::GR;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+  S* hf = (S*)(smem + L::off_hf);
+  S* gb = (S*)(smem + L::off_g);
+  P2* s_pt = (P2*)(smem + L::off_pt);             // [3][HPB] (phi, T)
+  R* xch = (R*)(smem + L::off_x);                 // [2][NX][NC]
+  uint64_t* bar = (uint64_t*)(smem + L::off_bar);  // [0..2] HF ring, [3..4] G ring
+
+  const int tid = threadIdx.x;
+  const bool role_g = tid < NC;
+  const int cidx = role_g ? tid : tid - NC;
+  const int tx = cidx % G::TXB, ty = cidx / G::TXB;
+  int tcol, trow, z0, z1;
+  bulk_unit(sched, P.nz, (int)blockIdx.x, tcol, trow, z0, z1);
+  const int x0 = tcol * G::TXB, y0 = trow * G::TYB;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool active = (x < P.nx) && (y < P.ny);
+  const int col = tx + G::GXP;
+
+  if (tid == 0) {
+    for (int k = 0; k < 5; ++k) mbar_init(&bar[k], 1);
+    mbar_fence_init();
+  } else if (tid == 32) {
+    tma_prefetch_desc(&mh);
+    tma_prefetch_desc(&mg);
+    tma_prefetch_desc(&mf);
+  }
+  __syncthreads();
+
+  // ring bookkeeping, relative to the chunk: HF plane p -> slot (p - z0 + 1) % 3
+  // (fill (p - z0 + 1) / 3), G plane p -> slot (p - z0) % GR (fill (p - z0) / GR)
+  auto hf_slot = [&](int p) { return (p - z0 + 1) % 3; };
+  auto hf_par = [&](int p) { return (uint32_t)(((p - z0 + 1) / 3) & 1); };
+  auto g_slot = [&](int p) { return (p - z0) % GR; };
+  auto g_par = [&](int p) { return (uint32_t)(((p - z0) / GR) & 1); };
+  auto hf_ptr = [&](int p) { return hf + (size_t)hf_slot(p) * L::hf_stage; };
+  auto g_ptr = [&](int p) { return gb + (size_t)g_slot(p) * L::g_stage; };
+  auto pt_ptr = [&](int p) { return s_pt + hf_slot(p) * G::HPB; };
+  auto xb = [&](int p, int slot) { return xch + ((size_t)(p & 1) * NX + slot) * NC + cidx; };
+
+  bool ok = true;
+  uint32_t pending = 0, pend_par = 0;
+  auto mark = [&](int k, uint32_t par) { pending |= 1u << k; pend_par = (pend_par & ~(1u << k)) | (par << k); };
+  auto wait_slot = [&](int k, uint32_t par) {
+    const bool r = mbar_wait(&bar[k], par);
+    if (r) pending &= ~(1u << k);
+    return r;
+  };
+  // HF(p) into its slot, boxes spread over all warps
+  auto issue_hf = [&](int p, uint32_t extra) {
+    if (tid == 0) mbar_expect_tx(&bar[hf_slot(p)], L::hf_tx + extra);
+    issue_stage<S, G, QH, QF, 0>(P, &mh, &mg, &mf, hf_ptr(p), &bar[hf_slot(p)], p, x0, y0, tid);
+    mark(hf_slot(p), hf_par(p));
+  };
+  // G(p) into its slot, boxes spread over the g role's warps (g role only)
+  auto issue_g = [&](int p) {
+    if (tid == 0) mbar_expect_tx(&bar[3 + g_slot(p)], L::g_tx);
+    issue_stage<S, G, QH, QF, 1>(P, &mh, &mg, &mf, g_ptr(p), &bar[3 + g_slot(p)], p, x0, y0, tid, NC / 32);
+    mark(3 + g_slot(p), g_par(p));
+  };
+  auto a_barrier = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(NC) : "memory"); };
+  auto b_barrier = [&]() { asm volatile("bar.sync 2, %0;" ::"r"(NC) : "memory"); };
+  auto sum_plane = [&](int p, int k0, int kstep) {
+    stage_sum_plane<S, QH, QF, EXT, G>(P, A, hf_ptr(p), pt_ptr(p), p, x0, y0, k0, kstep);
+  };
+
+  // moments of the pulled g of plane p (g role), as GMoments
+  auto moments = [&](int p) {
+    const bool lo = P.walls && p == 0, hi = P.walls && p == P.nz - 1;
+    const S* grow = g_ptr(p) + (size_t)ty * G::W + col;
+    auto run = [&](auto btag) {
+      constexpr bool BOUNCE = decltype(btag)::value;
+      auto getg = [&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const bool b = BOUNCE && ((cz<27>(i) > 0 && lo) || (cz<27>(i) < 0 && hi));
+        const S* p_ = grow + (size_t)i * G::GB;
+        return Store<S>::ld_s(b ? p_ : p_ - cx<27>(i));
+      };
+      return g_moments<R>(getg);
+    };
+    return (lo || hi) ? run(std::true_type{}) : run(std::false_type{});
+  };
+  auto publish_moments = [&](int p, const GMoments<R>& m) {
+    if (mode & MODE_SAVE) save_moments<S>(P, A, cell_index(P, x, y, p), m);
+    *xb(p, 4) = m.jx;
+    *xb(p, 5) = m.jy;
+    *xb(p, 6) = m.jz;
+    *xb(p, 7) = m.pst;
+  };
+  // g collision of plane p from its moments and B's phi(p), a(p)
+  auto g_collide = [&](int p, const GMoments<R>& m) {
+    const R phi = *xb(p, 0);
+    const CellFlow<R> f = cell_velocity<R>(*xb(p, 1), *xb(p, 2), *xb(p, 3), (R)1, m.jx, m.jy, m.jz);
+    collide_g<S>(P, A, pdf_index(P, x, y, p), phi, m, f);
+  };
+
+  double dsum[kDiagVals];
+#pragma unroll
+  for (int k = 0; k < kDiagVals; ++k) dsum[k] = 0.0;
+
+  // stencil role, plane p: stencils and force; phi(p), a(p) to the exchange;
+  // then (after the plane's j and p* are in the exchange) the h and f
+  // collisions and the outputs.  The h/f half runs in a second call when
+  // `collide_now` is false (prologue).
+  Stencil27<R> fd;
+  R rgx = 0, rgy = 0, rgz = 0, rlap = 0, pgx = 0, pgy = 0, pgz = 0;
+  CellForce<R> F;
+  P2 cen;
+  auto b_stencil = [&](int p) {
+    const P2* pm = pt_ptr(p - 1);
+    const P2* pc = pt_ptr(p);
+    const P2* pp = pt_ptr(p + 1);
+    const int c0 = (ty + 1) * G::HXB + (tx + 1);
+    cen = pc[c0];
+    eval_pairs<G::HXB>(fd, pm, pc, pp, c0);
+    if constexpr (QF == 0) {
+      rk_std_pairs<P2, R, G::HXB>(pm, pc, pp, c0, rgx, rgy, rgz, rlap);
+      if constexpr (EXT)
+        if (P.alpha_ratio && !P.rk_iso) central_phi_pairs<P2, R, G::HXB>(pm, pc, pp, c0, pgx, pgy, pgz);
+    }
+    const size_t cell = cell_index(P, x, y, p);
+    if (mode & MODE_SAVE) save_stencil<S>(P, A, cell, cen.x, cen.y, fd);
+    F = cell_force<R>(P, x, y, p, cen.x, cen.y, fd.gpx, fd.gpy, fd.gpz, fd.lp, fd.gtx, fd.gty, fd.gtz);
+    *xb(p, 0) = cen.x;
+    *xb(p, 1) = F.ax;
+    *xb(p, 2) = F.ay;
+    *xb(p, 3) = F.az;
+  };
+  auto b_collide = [&](int p) {
+    const R phi = cen.x, Tc = cen.y;
+    const size_t cell = cell_index(P, x, y, p);
+    const CellFlow<R> f = cell_velocity<R>(F.ax, F.ay, F.az, F.rho, *xb(p, 4), *xb(p, 5), *xb(p, 6));
+    cell_outputs<S>(P, A, x, y, p, cell, mode, phi, Tc, *xb(p, 7), f, dsum);
+    if (!(mode & MODE_COLLIDE)) return;
+    const bool lo = P.walls && p == 0, hi = P.walls && p == P.nz - 1;
+    const size_t pcell = pdf_index(P, x, y, p);
+    const S* hrow = hf_ptr(p) + (size_t)(ty + 1) * G::W + col;   // direction 0, this cell
+    const R shf = (R)RP<R>(P).shift_f;
+    auto run = [&](auto btag) {
+      constexpr bool BOUNCE = decltype(btag)::value;
+      auto geth = [&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const bool b = BOUNCE && ((cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi));
+        const S* p_ = hrow + (size_t)i * G::HFB;
+        return Store<S>::ld_s(b ? p_ : p_ - cx<QH>(i));
+      };
+      R Tb = 0, Tt = 0;
+      if constexpr (BOUNCE && QF > 0) {
+        if constexpr (EXT) Tb = wall_T<R>(P, x, true) - shf;
+        else Tb = (R)RP<R>(P).T_bottom - shf;
+        Tt = (R)RP<R>(P).T_top - shf;
+      }
+      auto getf = [&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if constexpr (QF > 0) {
+          const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
+          const S* p_ = hrow + (size_t)(QH + i) * G::HFB;
+          const R v = Store<S>::ld_s(b ? p_ : p_ - cx<QF>(i));
+          // anti-bounce-back in stored form: -v_s + 2 w_i (T_w - s)
+          return b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? Tb : Tt)) : v;
+        } else {
+          return (R)0;
+        }
+      };
+      collide_h<S, QH>(P, A, pcell, phi, fd.gpx, fd.gpy, fd.gpz, f, geth);
+      if (EXT && P.alpha_ratio)
+        collide_f<S, QF, EXT>(P, A, x, y, p, cell, pcell, phi, Tc, fd, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf);
+      else
+        collide_f<S, QF, false>(P, A, x, y, p, cell, pcell, phi, Tc, fd, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf);
+    };
+    if (lo || hi) run(std::true_type{});
+    else run(std::false_type{});
+  };
+
+  GMoments<R> mA0, mA1;   // g role: moments of planes z and z + 1 at the start of iteration z
+  if (z0 < z1) {
+    // ---------------- prologue: phi/T of z0 - 1 .. z0 + 1, m(z0), m(z0 + 1),
+    // stencils and force of z0, h/f collisions of z0
+    // (test of the timeout path: 16 bytes more than the copies deliver, so
+    // the first stage never completes and its bounded wait runs out)
+    issue_hf(z0 - 1, P.test_stall ? 16u : 0u);
+    issue_hf(z0, 0);
+    issue_hf(z0 + 1, 0);
+    if (role_g) {
+      issue_g(z0);
+      if (GR == 2 && z0 + 1 < z1) issue_g(z0 + 1);
+    }
+    for (int p = z0 - 1; p <= z0 + 1; ++p) {
+      ok = ok && wait_slot(hf_slot(p), hf_par(p));
+      if (ok) sum_plane(p, tid, NT);
+    }
+    // every thread has summed HF(z0 - 1), whose slot HF(z0 + 2) reuses
+    if (__syncthreads_or(!ok)) ok = false;
+    if (ok) {
+      if (z0 + 2 <= z1) issue_hf(z0 + 2, 0);
+      if (role_g) {
+        ok = wait_slot(3 + g_slot(z0), g_par(z0));
+        if (ok && active) {
+          mA0 = moments(z0);
+          publish_moments(z0, mA0);
+        }
+        // after consuming G(p) its slot takes G(p + GR)
+        if (z0 + GR < z1) {
+          a_barrier();   // every g-role thread has read G(z0)
+          if (ok) issue_g(z0 + GR);
+        }
+      } else if (active) {
+        b_stencil(z0);
+      }
+    }
+    // j(z0), p*(z0) and phi(z0), a(z0) are in the exchange
+    if (__syncthreads_or(!ok)) ok = false;
+    if (ok) {
+      if (role_g) {
+        if (z0 + 1 < z1) {
+          ok = wait_slot(3 + g_slot(z0 + 1), g_par(z0 + 1));
+          if (ok && active) {
+            mA1 = moments(z0 + 1);
+            publish_moments(z0 + 1, mA1);
+          }
+          const int next = z0 + 1 + GR;   // the slot just read takes G(z0 + 1 + GR)
+          if (next < z1) {
+            a_barrier();
+            if (ok) issue_g(next);
+          }
+        }
+      } else if (active) {
+        b_collide(z0);
+      }
+    }
+    if (__syncthreads_or(!ok)) ok = false;
+  }
+
+  for (int z = z0; z < z1 && ok; ++z) {
+    // h/f boxes of plane z + 3 into the slot of plane z (its collisions were
+    // done in the previous iteration)
+    if (z + 3 <= z1) issue_hf(z + 3, 0);
+    if (role_g) {
+      if (active && (mode & MODE_COLLIDE)) g_collide(z, mA0);
+      mA0 = mA1;
+      if (z + 2 < z1) {
+        ok = ok && wait_slot(3 + g_slot(z + 2), g_par(z + 2));
+        if (ok && active) {
+          mA1 = moments(z + 2);
+          publish_moments(z + 2, mA1);
+        }
+        const int next = z + 2 + GR;
+        if (next < z1) {
+          a_barrier();   // every g-role thread has read G(z + 2)
+          if (ok) issue_g(next);
+        }
+      }
+    } else {
+      if (z + 2 <= z1) {
+        ok = ok && wait_slot(hf_slot(z + 2), hf_par(z + 2));
+        if (ok) sum_plane(z + 2, cidx, NC);
+      }
+      b_barrier();   // phi / T of plane z + 2 complete
+      if (ok && z + 1 < z1 && active) {
+        b_stencil(z + 1);
+        b_collide(z + 1);
+      }
+    }
+    if (__syncthreads_or(!ok)) { ok = false; break; }
+  }
+
+  if (!ok) {
+    // raise the error flag, drain outstanding copies (bounded), leave
+    if (tid == 0 && A.error_flag) atomicExch(A.error_flag, 1);
+    for (int k = 0; k < 5; ++k)
+      if (pending & (1u << k)) mbar_wait(&bar[k], (pend_par >> k) & 1u);
+    return;
+  }
+  // the reduction's scratch reuses the h/f ring (no copies in flight)
+  if (mode & MODE_DIAG) diag_block_reduce_in<NT>(dsum, A.diag_partials, reinterpret_cast<double*>(smem + L::off_hf));
+}
+
+}  // namespace lbm

