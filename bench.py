@@ -485,11 +485,17 @@ def main():
         J5, g5 = dd.adjoint_run(c5.steps, 100, c5.target, normal_cap=30.0)
         t_adj = time.perf_counter() - t0
         dd.close()
+        dd = c5_domain()
+        t0 = time.perf_counter()
+        _, g5x = dd.adjoint_run(c5.steps, 100, c5.target, normal_cap=0.0)
+        t_adj_x = time.perf_counter() - t0
+        dd.close()
         adj = {"workload": c5.name, "steps": c5.steps, "ckpt_every": 100, "normal_cap": 30.0,
                "forward_s": t_fwd, "adjoint_run_s": t_adj, "cost_ratio": t_adj / t_fwd,
+               "exact_adjoint_run_s": t_adj_x, "exact_cost_ratio": t_adj_x / t_fwd,
                "what": "lbm_adjoint_run (forward with checkpoints + replay + adjoint steps) wall time "
-                       "over the plain forward run of the same steps; FP64",
-               "J": J5, "grad_inf": float(np.abs(g5).max())}
+                       "over the plain forward run of the same steps; FP64; normal cap 30 and exact (cap 0)",
+               "J": J5, "grad_inf": float(np.abs(g5).max()), "exact_grad_inf": float(np.abs(g5x).max())}
 
     # ---------------- stated error: FP32 and FP16 storage vs FP64 on a bulk-kernel
     # lattice of the same workload (128^3, 8 droplets, 200 steps); the FP64

@@ -308,19 +308,42 @@ class OracleLBM:
     def _pull(self, pdf, S, rule=None, Tb=0.0, Tt=0.0):
         """Pull streaming p*_i(x) = p_i(x - c_i) (periodic by np.roll); at z
         walls the half-way bounce-back p*_i = p_opp(i) (rule None) or the
-        anti-bounce-back p*_i = -p_opp(i) + 2 w_i T_w (rule 'abb')."""
+        anti-bounce-back p*_i = -p_opp(i) + 2 w_i T_w (rule 'abb').
+
+        Moving walls (tangential velocity u_w, Sec. 3.3 sheared channel): the
+        populations coming off a wall take the wall's momentum, by the
+        equilibrium's linear term: g*_i = g_opp(i) + 2 w_i (c_i . u_w) / c_s^2
+        (rule 'g', velocity-based equilibrium) and h*_i = h_opp(i) + 2 w_i
+        phi_0 (c_i . u_w) / c_s^2 (rule 'h'), phi_0 the zeroth moment of the
+        pulled h without the correction (the corrections of a tangential wall
+        cancel in it); the thermal anti-bounce-back takes the even part of
+        the equilibrium, 2 w_i T_w [1 + (c_i . u_w)^2 / (2 c_s^4) - u_w^2 / (2 c_s^2)]."""
+        p = self.p
+        ub = tuple(getattr(p, "wall_u_bottom", (0.0, 0.0)))
+        ut = tuple(getattr(p, "wall_u_top", (0.0, 0.0)))
+        moving = any(v != 0.0 for v in ub + ut)
         out = np.empty_like(pdf)
+        fixes = []
         for i in range(S.Q):
             cx, cy, cz = (int(v) for v in S.c[i])
             out[i] = np.roll(pdf[i], shift=(cz, cy, cx), axis=(0, 1, 2))
             if self.walls and cz != 0:
                 zl = 0 if cz == 1 else -1
                 Tw = Tb if cz == 1 else Tt
+                uw = ub if cz == 1 else ut
+                cu = cx * uw[0] + cy * uw[1]
                 back = pdf[S.opp[i]][zl]
                 if rule == "abb":
-                    out[i][zl] = -back + 2.0 * S.w[i] * Tw
+                    e = 1.0 + cu * cu / (2 * CS2 * CS2) - (uw[0] ** 2 + uw[1] ** 2) / (2 * CS2)
+                    out[i][zl] = -back + 2.0 * S.w[i] * Tw * e
                 else:
                     out[i][zl] = back
+                    if moving and rule in ("g", "h") and cu != 0.0:
+                        fixes.append((i, zl, 2.0 * S.w[i] * cu / CS2))
+        if fixes:
+            phi0 = out.sum(axis=0) if rule == "h" else None
+            for i, zl, c in fixes:
+                out[i][zl] = out[i][zl] + (c * phi0[zl] if rule == "h" else c)
         return out
 
     # ------------------------------------------------------------ a3 stencils
@@ -330,12 +353,30 @@ class OracleLBM:
         q = np.pad(psi, 1, mode="wrap")
         if self.walls:
             if kind == "mirror":
-                q[0] = q[1]
-                q[-1] = q[-2]
+                # contact angle theta (through phi = 1): the ghost value g
+                # beyond the wall makes the one-sided normal derivative of
+                # the equilibrium profile, (a - g) = -k w (1 - w), k =
+                # (4 / xi) cos theta, w = (a + g) / 2 the wall value, a the
+                # first fluid cell (the wetting condition of the conservative
+                # phase field); theta = 90 degrees gives the mirror g = a
+                q[0] = self._wet_ghost(q[1], getattr(self.p, "theta_bottom", 90.0))
+                q[-1] = self._wet_ghost(q[-2], getattr(self.p, "theta_top", 90.0))
             else:
                 q[0] = 2.0 * np.pad(self.T_wall_bottom(), 1, mode="wrap") - q[1]
                 q[-1] = 2.0 * self.p.T_top - q[-2]
         return q
+
+    def _wet_ghost(self, a, theta_deg):
+        """Ghost phi beyond a wall with contact angle theta: the root of
+        g - a = k ((a + g)/2) (1 - (a + g)/2), k = (4 / xi) cos theta, that
+        tends to g = a as k -> 0, in the form s = a + g = 4 a / ((1 - k/2) +
+        sqrt((1 - k/2)^2 + 2 k a)) (no cancellation)."""
+        if theta_deg == 90.0:
+            return a.copy()
+        k = 4.0 / self.p.xi * math.cos(math.radians(theta_deg))
+        b = 1.0 - 0.5 * k
+        s = 4.0 * a / (b + np.sqrt(np.maximum(b * b + 2.0 * k * a, 0.0)))
+        return s - a
 
     def _at(self, q, c):
         """Value of a padded field at x + c for every interior x."""
@@ -480,8 +521,8 @@ class OracleLBM:
     def macro(self):
         """Macroscopic fields of the current time level (what the next step
         computes from its pulled PDFs), without advancing."""
-        hs = self._pull(self.h, self.Sh)
-        gs = self._pull(self.g, self.S27)
+        hs = self._pull(self.h, self.Sh, "h")
+        gs = self._pull(self.g, self.S27, "g")
         fs = (self._pull(self.f, self.Sf, "abb", self.T_wall_bottom(), self.p.T_top)
               if self.lb_thermal else None)
         return self._macro_from_pulled(hs, gs, fs)
@@ -492,8 +533,8 @@ class OracleLBM:
 
     def _step1(self):
         p = self.p
-        hs = self._pull(self.h, self.Sh)
-        gs = self._pull(self.g, self.S27)
+        hs = self._pull(self.h, self.Sh, "h")
+        gs = self._pull(self.g, self.S27, "g")
         fs = (self._pull(self.f, self.Sf, "abb", self.T_wall_bottom(), p.T_top)
               if self.lb_thermal else None)
         m = self._macro_from_pulled(hs, gs, fs)

@@ -88,6 +88,28 @@ __device__ __forceinline__ R cond_cross(const DevParams& P, R gpx, R gpy, R gpz,
   return dalpha_of<R>(P) * (gpx * (gtx + (R)rp.grad[0]) + gpy * (gty + (R)rp.grad[1]) + gpz * (gtz + (R)rp.grad[2]));
 }
 
+// c . v for a lattice velocity c with components in {-1, 0, 1} known at
+// compile time: only the non-zero components are summed (x * 0 cannot be
+// folded away under IEEE rules, so the plain product form costs a multiply
+// per zero component); the sum order is x, y, z as in the full product.
+template <int EX, int EY, int EZ, class R>
+__device__ __forceinline__ R cdot(R vx, R vy, R vz) {
+  if constexpr (EX != 0) {
+    R s = EX > 0 ? vx : -vx;
+    if constexpr (EY != 0) s = EY > 0 ? s + vy : s - vy;
+    if constexpr (EZ != 0) s = EZ > 0 ? s + vz : s - vz;
+    return s;
+  } else if constexpr (EY != 0) {
+    R s = EY > 0 ? vy : -vy;
+    if constexpr (EZ != 0) s = EZ > 0 ? s + vz : s - vz;
+    return s;
+  } else if constexpr (EZ != 0) {
+    return EZ > 0 ? vz : -vz;
+  } else {
+    return (R)0;
+  }
+}
+
 // Is direction i the first of its opposite pair (first non-zero component > 0)?
 template <int Q>
 __host__ __device__ constexpr bool pair_first(int i) {
@@ -141,8 +163,10 @@ template <> struct PairOf<double> { using type = double2; };
 template <int HXv>
 __device__ __forceinline__ void eval_pairs(Stencil27<float>& fd, const float2* pm, const float2* pc,
                                            const float2* pp, int c0) {
+  // Laplacian as sum_k w_k (v(c) + v(-c)) - (sum_k 2 w_k) v(0): one packed
+  // add per pair instead of three (uniform fields then give zeros to
+  // rounding rather than exactly)
   const float2 c = pc[c0];
-  const float2 nc = make_float2(-c.x, -c.y);
   const float2 m1 = make_float2(-1.f, -1.f);
   float2 L = make_float2(0.f, 0.f), Gx = L, Gy = L, Gz = L;
   static_for<1, 27>([&](auto K) {
@@ -154,13 +178,16 @@ __device__ __forceinline__ void eval_pairs(Stencil27<float>& fd, const float2* p
       constexpr int o = ey * HXv + ex;
       const float2 vp = P_[c0 + o], vm = Pm[c0 - o];
       constexpr float w = (float)weight<27>(k);
-      L = __ffma2_rn(make_float2(w, w), __fadd2_rn(__fadd2_rn(vp, nc), __fadd2_rn(vm, nc)), L);
+      L = __ffma2_rn(make_float2(w, w), __fadd2_rn(vp, vm), L);
       const float2 d = __ffma2_rn(vm, m1, vp);  // vp - vm
       if constexpr (ex != 0) Gx = __ffma2_rn(make_float2((float)ex * w, (float)ex * w), d, Gx);
       if constexpr (ey != 0) Gy = __ffma2_rn(make_float2((float)ey * w, (float)ey * w), d, Gy);
       if constexpr (ez != 0) Gz = __ffma2_rn(make_float2((float)ez * w, (float)ez * w), d, Gz);
     }
   });
+  // sum over the 13 pairs of 2 w_k = 1 - w_0 = 1 - 8/27 = 19/27
+  constexpr float w2 = (float)(1.0 - weight<27>(0));
+  L = __ffma2_rn(make_float2(-w2, -w2), c, L);
   fd.gpx = 3.f * Gx.x; fd.gpy = 3.f * Gy.x; fd.gpz = 3.f * Gz.x; fd.lp = 6.f * L.x;
   fd.gtx = 3.f * Gx.y; fd.gty = 3.f * Gy.y; fd.gtz = 3.f * Gz.y; fd.lt = 6.f * L.y;
 }
@@ -420,6 +447,8 @@ __device__ __forceinline__ void collide_g(const DevParams& P, const StepPtrs<S, 
   }
   const R ua = ux * ax + uy * ay + uz * az;
   const R base = m.pst - (R)1.5 * (uu + ua);
+  const R u3x = (R)3 * ux, u3y = (R)3 * uy, u3z = (R)3 * uz;
+  const R a15x = (R)1.5 * ax, a15y = (R)1.5 * ay, a15z = (R)1.5 * az;
   auto neq_of = [&](int ex, int ey, int ez) -> R {
     const int c = ez == 0 ? 0 : (ez > 0 ? 1 : 2);
     const R q0 = basis_pick(ey, Y0z, Y0p, Y0m);
@@ -439,13 +468,14 @@ __device__ __forceinline__ void collide_g(const DevParams& P, const StepPtrs<S, 
     if constexpr (pair_first<27>(i)) {
       constexpr int ex = cx<27>(i), ey = cy<27>(i), ez = cz<27>(i);
       constexpr R w = (R)weight<27>(i);
-      const R cu = (R)ex * ux + (R)ey * uy + (R)ez * uz;
-      const R ca = (R)ex * ax + (R)ey * ay + (R)ez * az;
       // g^eq + S/2 = w [p* + 3cu + 9/2 cu^2 - 3/2 uu + 3/2 (ca - ua) + 9/2 cu ca]
-      const R even = w * (base + (R)4.5 * cu * (cu + ca));
-      const R odd = w * ((R)3 * cu + (R)1.5 * ca);
-      Store<S>::st(A.gd[i] + pcell, even + odd + neq_of(ex, ey, ez));
-      Store<S>::st(A.gd[opp<27>(i)] + pcell, even - odd + neq_of(-ex, -ey, -ez));
+      //            = w [(base + (3cu / 2)(3cu + 3ca)) +- (3cu + 3ca / 2)]
+      const R cu3 = cdot<ex, ey, ez>(u3x, u3y, u3z);
+      const R ca15 = cdot<ex, ey, ez>(a15x, a15y, a15z);
+      const R odd = cu3 + ca15;
+      const R even = (R)0.5 * cu3 * (odd + ca15) + base;
+      Store<S>::st(A.gd[i] + pcell, w * (even + odd) + neq_of(ex, ey, ez));
+      Store<S>::st(A.gd[opp<27>(i)] + pcell, w * (even - odd) + neq_of(-ex, -ey, -ez));
     }
   });
 }
@@ -483,8 +513,8 @@ __device__ __forceinline__ void collide_h(const DevParams& P, const StepPtrs<S, 
     if constexpr (pair_first<QH>(i)) {
       constexpr int j = opp<QH>(i);
       constexpr R w = (R)weight<QH>(i);
-      const R cu = (R)cx<QH>(i) * ux + (R)cy<QH>(i) * uy + (R)cz<QH>(i) * uz;
-      const R cf = (R)cx<QH>(i) * fpx + (R)cy<QH>(i) * fpy + (R)cz<QH>(i) * fpz;
+      const R cu = cdot<cx<QH>(i), cy<QH>(i), cz<QH>(i)>(ux, uy, uz);
+      const R cf = cdot<cx<QH>(i), cy<QH>(i), cz<QH>(i)>(fpx, fpy, fpz);
       const R even = w * (base + p45 * cu * cu);
       const R odd = w * (p3 * cu);
       const R src = sc * w * cf;
@@ -543,7 +573,7 @@ __device__ __forceinline__ void collide_f(const DevParams& P, const StepPtrs<S, 
       if constexpr (pair_first<QF>(i)) {
         constexpr int j = opp<QF>(i);
         constexpr R w = (R)weight<QF>(i);
-        const R cu = (R)cx<QF>(i) * ux + (R)cy<QF>(i) * uy + (R)cz<QF>(i) * uz;
+        const R cu = cdot<cx<QF>(i), cy<QF>(i), cz<QF>(i)>(ux, uy, uz);
         const R even = w * (base + t45 * cu * cu);
         const R odd = w * (t3 * cu);
         const R wq = w * qs;

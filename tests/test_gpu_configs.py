@@ -81,3 +81,38 @@ def test_config3_fp32_tracks_fp64():
     assert np.abs(c64 - c32).max() <= 1e-3, np.abs(c64 - c32).max()
     assert abs(d64.diagnostics()["mass"] - m64) <= 1e-12 * m64
     assert abs(d32.diagnostics()["mass"] - m32) <= 1e-4 * m32
+
+
+def test_migration_speed_extrapolates_to_young_goldstein_block():
+    """Thermocapillary migration (the 64 x 64 x 128 channel of the
+    migration workload, walls at T = -0.5 / +0.5, R = 12) at three lateral
+    box sizes L = 64, 96, 128 (periodic images L apart), FP32 storage,
+    16000 steps; speed from the centroid between steps 12000 and 16000.  The
+    speed grows with L (monotone), and its linear extrapolation in R / L to
+    R / L = 0 (a Hasimoto-type image correction U(L) = U_inf (1 - c R / L))
+    lies within 25 % of the Young-Goldstein-Block speed of an unbounded
+    domain, U = 2 |sigma_T| G R / (15 mu) (viscosity and conductivity ratios
+    1), G = 1 / 128."""
+    base = W.config2("D3Q7", "fp32")
+    p = base.params
+    R = base.droplets[0].R
+    G = (p.T_top - p.T_bottom) / base.nz
+    mu = p.nu_L * 1.0
+    ygb = 2 * abs(p.sigma_T) * G * R / (15 * mu)
+    speeds = []
+    Ls = (64, 96, 128)
+    for L in Ls:
+        w = base.replace(nx=L, ny=L, droplets=[W.Droplet(L / 2, L / 2, 64.0, R)])
+        d = gpu_domain(w)
+        d.step(12000)
+        za, _ = _centroid_z(d)
+        d.step(4000)
+        zb, _ = _centroid_z(d)
+        d.close()
+        speeds.append((zb - za) / 4000)
+    x = np.array([R / L for L in Ls])
+    slope, U_inf = np.polyfit(x, np.array(speeds), 1)
+    print("migration speeds", dict(zip(Ls, speeds)), "extrapolated", U_inf, "YGB", ygb,
+          "ratio", U_inf / ygb)
+    assert speeds[0] < speeds[1] < speeds[2], speeds
+    assert abs(U_inf / ygb - 1) <= 0.25, (U_inf, ygb)

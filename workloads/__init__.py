@@ -54,6 +54,10 @@ class Params:
     rk_isotropic_fd: bool = False  # RK path: isotropic D3Q27 operators instead of 7-point
     T_bottom_amp: float = 0.0    # bottom wall T_bottom + T_bottom_amp cos(2 pi k x / nx)
     T_bottom_waves: int = 0      # k (0: uniform bottom wall)
+    wall_u_bottom: tuple = (0.0, 0.0)   # tangential (x, y) velocity of the bottom wall
+    wall_u_top: tuple = (0.0, 0.0)      # tangential (x, y) velocity of the top wall
+    theta_bottom: float = 90.0   # contact angle at the bottom wall, degrees, through phi = 1
+    theta_top: float = 90.0      # contact angle at the top wall
 
 
 @dataclass
