@@ -102,6 +102,15 @@ typedef struct {
   double T_bottom_amp;     /* bottom wall temperature T_bottom + T_bottom_amp cos(omega x), */
   int32_t T_bottom_waves;  /* omega = 2 pi T_bottom_waves / nx, x the cell centre (Sec. 3.1
                               planar heated channel); 0 = uniform T_bottom */
+  double wall_u_bottom[2]; /* tangential (x, y) velocity of the bottom / top wall (walls_z == 1;  */
+  double wall_u_top[2];    /* the sheared channel of Sec. 3.3): bounce-back adds the wall's
+                              momentum 2 w_i (c_i . u_w) / c_s^2 to g (times phi to h), and
+                              the thermal anti-bounce-back takes the even part of the
+                              equilibrium at u_w; |u_w| < 0.3 */
+  double theta_bottom;     /* contact angle (degrees, measured through phi = 1) at the bottom /   */
+  double theta_top;        /* top wall, 0 < theta < 180 (Sec. 3.3 wetting condition): the ghost
+                              phi beyond the wall solves (a - g) = -(4 / xi) cos(theta) w (1 - w),
+                              w = (a + g) / 2, a the first fluid cell; 90 = neutral (mirror) */
 } lbm_params;
 
 /* Gaussian laser heat source, Eq. HeatSource: q = Q exp(-2 r^2 / w^2) where

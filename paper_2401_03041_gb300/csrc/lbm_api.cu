@@ -457,6 +457,21 @@ void refresh_devparams(lbm_domain* d) {
   q.test_stall = d->test_stall;
   fill_real(q.pd, p, d->prec);
   fill_real(q.pf, p, d->prec);
+  q.moving_walls = (p.walls_z && (p.wall_u_bottom[0] != 0.0 || p.wall_u_bottom[1] != 0.0 ||
+                                  p.wall_u_top[0] != 0.0 || p.wall_u_top[1] != 0.0)) ? 1 : 0;
+  q.wetting = (p.walls_z && (p.theta_bottom != 90.0 || p.theta_top != 90.0)) ? 1 : 0;
+  q.wall_ext = (q.moving_walls || q.wetting) ? 1 : 0;
+  for (int c = 0; c < 2; ++c) {
+    q.uw_d[0][c] = p.wall_u_bottom[c];
+    q.uw_d[1][c] = p.wall_u_top[c];
+    q.uw_f[0][c] = (float)p.wall_u_bottom[c];
+    q.uw_f[1][c] = (float)p.wall_u_top[c];
+  }
+  const double pi = 3.14159265358979323846;
+  q.kw_d[0] = p.theta_bottom == 90.0 ? 0.0 : 4.0 / p.xi * std::cos(p.theta_bottom * pi / 180.0);
+  q.kw_d[1] = p.theta_top == 90.0 ? 0.0 : 4.0 / p.xi * std::cos(p.theta_top * pi / 180.0);
+  q.kw_f[0] = (float)q.kw_d[0];
+  q.kw_f[1] = (float)q.kw_d[1];
   q.uniform_rho = p.rho_L == p.rho_H ? 1 : 0;
   q.rho_ratio = q.uniform_rho ? 0 : 1;
   q.uniform_tau = p.nu_L == p.nu_H ? 1 : 0;
@@ -544,6 +559,7 @@ void lbm_default_params(lbm_params* p) {
   p->T_ref = 0.0;
   p->alpha_L = p->alpha_H = 0.05;
   p->eps_n = 1e-12;
+  p->theta_bottom = p->theta_top = 90.0;
   p->omega_high = 1.0;
 }
 
@@ -649,6 +665,15 @@ lbm_status lbm_set_params(lbm_domain* d, const lbm_params* p) {
   if (p->rho_L <= 0 || p->rho_H <= 0) return fail(LBM_ERR_ARG, "density must be > 0");
   if (p->eps_n < 0) return fail(LBM_ERR_ARG, "eps_n must be >= 0");
   if (p->T_bottom_waves < 0) return fail(LBM_ERR_ARG, "T_bottom_waves must be >= 0");
+  {
+    const double w[6] = {p->wall_u_bottom[0], p->wall_u_bottom[1], p->wall_u_top[0], p->wall_u_top[1],
+                         p->theta_bottom, p->theta_top};
+    if (!finite_all(w, 6)) return fail(LBM_ERR_ARG, "non-finite wall velocity or contact angle");
+    if (std::hypot(w[0], w[1]) >= 0.3 || std::hypot(w[2], w[3]) >= 0.3)
+      return fail(LBM_ERR_ARG, "wall speed must be < 0.3 (lattice units)");
+    if (!(w[4] > 0 && w[4] < 180) || !(w[5] > 0 && w[5] < 180))
+      return fail(LBM_ERR_ARG, "contact angle must lie in (0, 180) degrees");
+  }
   if (p->omega_high != 1.0)
     return fail(LBM_ERR_UNSUPPORTED, "higher-order central-moment rate != 1 not built");
   d->params = *p;
@@ -1152,6 +1177,8 @@ lbm_status adj_check(lbm_domain* d) {
     return fail(LBM_ERR_UNSUPPORTED, "the adjoint is built for equal diffusivities (alpha_L == alpha_H)");
   if (d->dp.rho_ratio)
     return fail(LBM_ERR_UNSUPPORTED, "the adjoint is built for equal densities (rho_L == rho_H)");
+  if (d->dp.wall_ext)
+    return fail(LBM_ERR_UNSUPPORTED, "the adjoint is built for walls at rest with neutral wetting");
   if ((long long)d->nx * d->ny >= (1LL << 31))
     return fail(LBM_ERR_UNSUPPORTED, "the adjoint needs nx * ny < 2^31");
   return LBM_OK;

@@ -213,6 +213,28 @@ __device__ __forceinline__ void issue_stage(const DevParams& P, const CUtensorMa
   tma_load_4d(dst, map, x0 - G::GXP + P.GX, yy + P.GY, zz, q, bar);
 }
 
+// Anti-bounce-back wall value of direction I of the thermal LB in stored form,
+// T_w E_I - s: the wall temperature (the bottom wall's modulation in EXT
+// builds), times the even part of the equilibrium at the wall's velocity for
+// a moving wall (E_I = 1 at rest), minus the storage shift s.
+template <class S, int QF, int I, bool EXT, bool BOUNCE>
+__device__ __forceinline__ typename Store<S>::R abb_wall_value(const DevParams& P, int x,
+                                                              typename Store<S>::R shf) {
+  using R = typename Store<S>::R;
+  const auto& rp = RP<R>(P);
+  constexpr bool bottom = cz<QF>(I) > 0;
+  R Tw;
+  if constexpr (bottom) {
+    if constexpr (EXT) Tw = wall_T<R>(P, x, true);
+    else Tw = (R)rp.T_bottom;
+  } else {
+    Tw = (R)rp.T_top;
+  }
+  if constexpr (EXT && BOUNCE && cz<QF>(I) != 0)
+    if (P.moving_walls) Tw *= wall_even<QF, I, R>(P, bottom ? 0 : 1);
+  return Tw - shf;
+}
+
 // phi and T over the (TYB + 2) x (TXB + 2) halo tile of plane p, summed from
 // the staged h / f boxes of that plane (st), into the interleaved (phi, T)
 // plane pt; items k0, k0 + kstep, ... of the tile.  Ghost planes beyond a z
@@ -251,18 +273,26 @@ __device__ __forceinline__ void stage_sum_plane_v(const DevParams& P, const Step
       // stored values (shifted by w_i s, s = shift_f; sum_i w_i = 1);
       // anti-bounce-back in stored form: -v_s + 2 w_i (T_w - s)
       T = shf;
-      R Tb = 0, Tt = 0;
+      R Tb = 0, Tt = 0, Tbr = 0, Ttr = 0;
       if constexpr (BOUNCE) {
-        if constexpr (EXT) Tb = bottom_T() - shf;
-        else Tb = (R)rp.T_bottom - shf;
-        Tt = (R)rp.T_top - shf;
+        if constexpr (EXT) Tb = bottom_T();
+        else Tb = (R)rp.T_bottom;
+        Tt = (R)rp.T_top;
+        Tbr = Tb - shf;
+        Ttr = Tt - shf;
       }
       static_for<0, QF>([&](auto I) {
         constexpr int i = decltype(I)::value;
         const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
         const S* rowp = rowb + (size_t)(QH + i) * G::HFB;
         const R v = Store<S>::ld_s(b ? rowp : rowp - cx<QF>(i));
-        T += b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? Tb : Tt)) : v;
+        R tw = cz<QF>(i) > 0 ? Tbr : Ttr;
+        if constexpr (EXT && BOUNCE) {
+          // moving wall: the even part of the equilibrium at u_w
+          if (P.moving_walls)
+            tw = (cz<QF>(i) > 0 ? Tb : Tt) * wall_even<QF, i, R>(P, cz<QF>(i) > 0 ? 0 : 1) - shf;
+        }
+        T += b ? (-v + (R)(2.0 * weight<QF>(i)) * tw) : v;
       });
     } else {
       int gx = x0 + hc - 1, gy = y0 + hr - 1;
@@ -272,6 +302,8 @@ __device__ __forceinline__ void stage_sum_plane_v(const DevParams& P, const Step
     }
     if constexpr (EXT) {
       if (ghost) T = (R)2 * (p < 0 ? bottom_T() : (R)rp.T_top) - T;
+      // phi beyond a wall: the mirror, or the contact-angle ghost
+      if (ghost && P.wetting) phi = wet_ghost<R>(phi, wall_k<R>(P, p < 0 ? 0 : 1));
     } else {
       if (ghost) T = (R)2 * (p < 0 ? rp.T_bottom : rp.T_top) - T;
     }
@@ -445,7 +477,10 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
             constexpr int i = decltype(I)::value;
             const bool b = BOUNCE && ((cz<27>(i) > 0 && lo) || (cz<27>(i) < 0 && hi));
             const S* p_ = grow + (size_t)i * G::GB;
-            return Store<S>::ld_s(b ? p_ : p_ - cx<27>(i));
+            R v = Store<S>::ld_s(b ? p_ : p_ - cx<27>(i));
+            if constexpr (EXT && BOUNCE && cz<27>(i) != 0)
+              if (b && P.moving_walls) v += wall_momentum<27, i, R>(P, cz<27>(i) > 0 ? 0 : 1);
+            return v;
           };
           // density ratio (EXT only): the g role adds F_p and F_mu, which need
           // the moments of g, and hands u and p* back after a second pair
@@ -571,22 +606,19 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
                 constexpr int i = decltype(I)::value;
                 const bool b = BOUNCE && ((cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi));
                 const S* p_ = hrow + (size_t)i * G::HFB;
-                return Store<S>::ld_s(b ? p_ : p_ - cx<QH>(i));
+                R v = Store<S>::ld_s(b ? p_ : p_ - cx<QH>(i));
+                if constexpr (EXT && BOUNCE && cz<QH>(i) != 0)
+                  if (b && P.moving_walls) v += phi * wall_momentum<QH, i, R>(P, cz<QH>(i) > 0 ? 0 : 1);
+                return v;
               };
-              R Tb = 0, Tt = 0;
-              if constexpr (BOUNCE && QF > 0) {
-                if constexpr (EXT) Tb = wall_T<R>(P, x, true) - shf;
-                else Tb = (R)rp.T_bottom - shf;
-                Tt = (R)rp.T_top - shf;
-              }
               auto getf = [&](auto I) {
                 constexpr int i = decltype(I)::value;
                 if constexpr (QF > 0) {
                   const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
                   const S* p_ = hrow + (size_t)(QH + i) * G::HFB;
                   const R v = Store<S>::ld_s(b ? p_ : p_ - cx<QF>(i));
-                  // anti-bounce-back in stored form: -v_s + 2 w_i (T_w - s)
-                  return b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? Tb : Tt)) : v;
+                  // anti-bounce-back in stored form: -v_s + 2 w_i (T_w E_i - s), E_i = 1 at rest
+                  return b ? (-v + (R)(2.0 * weight<QF>(i)) * abb_wall_value<S, QF, i, EXT, BOUNCE>(P, x, shf)) : v;
                 } else {
                   return (R)0;
                 }

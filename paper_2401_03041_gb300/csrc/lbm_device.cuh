@@ -152,6 +152,12 @@ struct DevParams {
   int rho_ratio;   // rho_H != rho_L: the pressure and viscous correction forces F_p, F_mu
   double four_over_xi_d, twelve_over_xi_d, inv_rho_d, omega_g_d;
   float four_over_xi_f, twelve_over_xi_f, inv_rho_f, omega_g_f;
+  // Walls with a tangential velocity or a contact angle other than 90
+  // degrees ([0] bottom, [1] top); kw = (4 / xi) cos(theta).  wall_ext
+  // selects the extension kernels.
+  int wall_ext, moving_walls, wetting;
+  double uw_d[2][2], kw_d[2];
+  float uw_f[2][2], kw_f[2];
 };
 
 template <class R> __host__ __device__ __forceinline__ const RealParams<R>& RP(const DevParams& P);
@@ -232,6 +238,48 @@ __host__ __device__ __forceinline__ void bulk_unit(const BulkSched& s, int nz, i
   }
   z0 = lo;
   z1 = hi;
+}
+
+template <class R> __device__ __forceinline__ R wall_u(const DevParams& P, int top, int c);
+template <> __device__ __forceinline__ double wall_u<double>(const DevParams& P, int top, int c) { return P.uw_d[top][c]; }
+template <> __device__ __forceinline__ float wall_u<float>(const DevParams& P, int top, int c) { return P.uw_f[top][c]; }
+template <class R> __device__ __forceinline__ R wall_k(const DevParams& P, int top);
+template <> __device__ __forceinline__ double wall_k<double>(const DevParams& P, int top) { return P.kw_d[top]; }
+template <> __device__ __forceinline__ float wall_k<float>(const DevParams& P, int top) { return P.kw_f[top]; }
+
+// Ghost phi beyond a wall with contact angle theta (k = (4 / xi) cos theta,
+// a the first fluid cell): the root of g - a = k w (1 - w), w = (a + g) / 2,
+// that tends to the mirror g = a as k -> 0, written s = a + g = 4 a / ((1 -
+// k/2) + sqrt((1 - k/2)^2 + 2 k a)) so that it has no cancellation.
+template <class R>
+__device__ __forceinline__ R wet_ghost(R a, R k) {
+  const R b = (R)1 - (R)0.5 * k;
+  const R d = b * b + (R)2 * k * a;
+  const R sum = (R)4 * a / (b + sqrt(d > (R)0 ? d : (R)0));
+  return sum - a;
+}
+
+// Moving wall: the momentum a population coming off the wall takes, by the
+// equilibrium's linear term, 2 w_I (c_I . u_w) / c_s^2 (times phi for h);
+// top = 1 for the wall above.
+template <int Q, int I, class R>
+__device__ __forceinline__ R wall_momentum(const DevParams& P, int top) {
+  constexpr R w6 = (R)(6.0 * weight<Q>(I));
+  R cu = (R)0;
+  if constexpr (cx<Q>(I) != 0) cu = cx<Q>(I) > 0 ? wall_u<R>(P, top, 0) : -wall_u<R>(P, top, 0);
+  if constexpr (cy<Q>(I) != 0) cu = cy<Q>(I) > 0 ? cu + wall_u<R>(P, top, 1) : cu - wall_u<R>(P, top, 1);
+  return w6 * cu;
+}
+
+// Moving wall, thermal anti-bounce-back: the even part of the equilibrium at
+// u_w, 1 + (c_I . u_w)^2 / (2 c_s^4) - u_w^2 / (2 c_s^2).
+template <int Q, int I, class R>
+__device__ __forceinline__ R wall_even(const DevParams& P, int top) {
+  const R ux = wall_u<R>(P, top, 0), uy = wall_u<R>(P, top, 1);
+  R cu = (R)0;
+  if constexpr (cx<Q>(I) != 0) cu = cx<Q>(I) > 0 ? ux : -ux;
+  if constexpr (cy<Q>(I) != 0) cu = cy<Q>(I) > 0 ? cu + uy : cu - uy;
+  return (R)1 + (R)4.5 * cu * cu - (R)1.5 * (ux * ux + uy * uy);
 }
 
 // Kernel modes (bit set).

@@ -159,7 +159,10 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
         constexpr int i = decltype(I)::value;
         const bool b = BOUNCE && ((cz<27>(i) > 0 && lo) || (cz<27>(i) < 0 && hi));
         const S* p_ = grow + (size_t)i * G::GB;
-        return Store<S>::ld_s(b ? p_ : p_ - cx<27>(i));
+        R v = Store<S>::ld_s(b ? p_ : p_ - cx<27>(i));
+        if constexpr (EXT && BOUNCE && cz<27>(i) != 0)
+          if (b && P.moving_walls) v += wall_momentum<27, i, R>(P, cz<27>(i) > 0 ? 0 : 1);
+        return v;
       };
       return g_moments<R>(getg);
     };
@@ -227,22 +230,19 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
         constexpr int i = decltype(I)::value;
         const bool b = BOUNCE && ((cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi));
         const S* p_ = hrow + (size_t)i * G::HFB;
-        return Store<S>::ld_s(b ? p_ : p_ - cx<QH>(i));
+        R v = Store<S>::ld_s(b ? p_ : p_ - cx<QH>(i));
+        if constexpr (EXT && BOUNCE && cz<QH>(i) != 0)
+          if (b && P.moving_walls) v += phi * wall_momentum<QH, i, R>(P, cz<QH>(i) > 0 ? 0 : 1);
+        return v;
       };
-      R Tb = 0, Tt = 0;
-      if constexpr (BOUNCE && QF > 0) {
-        if constexpr (EXT) Tb = wall_T<R>(P, x, true) - shf;
-        else Tb = (R)RP<R>(P).T_bottom - shf;
-        Tt = (R)RP<R>(P).T_top - shf;
-      }
       auto getf = [&](auto I) {
         constexpr int i = decltype(I)::value;
         if constexpr (QF > 0) {
           const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
           const S* p_ = hrow + (size_t)(QH + i) * G::HFB;
           const R v = Store<S>::ld_s(b ? p_ : p_ - cx<QF>(i));
-          // anti-bounce-back in stored form: -v_s + 2 w_i (T_w - s)
-          return b ? (-v + (R)(2.0 * weight<QF>(i)) * (cz<QF>(i) > 0 ? Tb : Tt)) : v;
+          // anti-bounce-back in stored form: -v_s + 2 w_i (T_w E_i - s), E_i = 1 at rest
+          return b ? (-v + (R)(2.0 * weight<QF>(i)) * abb_wall_value<S, QF, i, EXT, BOUNCE>(P, x, shf)) : v;
         } else {
           return (R)0;
         }

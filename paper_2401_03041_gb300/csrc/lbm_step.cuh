@@ -44,7 +44,8 @@ __device__ __forceinline__ typename Store<S>::R pull(const DevParams& P, const S
   if (P.walls && (zs < 0 || zs >= P.nz)) {
     const R v = Store<S>::ld(base + (size_t)opp<Q>(I) * P.Np + pdf_index(P, x, y, z));
     if constexpr (ABB) {
-      const R Tw = wall_T<R>(P, x, zs < 0);
+      R Tw = wall_T<R>(P, x, zs < 0);
+      if (P.moving_walls) Tw *= wall_even<Q, I, R>(P, zs >= P.nz ? 1 : 0);
       return -v + (R)2 * w * (Tw - shift);
     }
     return v;
@@ -53,6 +54,16 @@ __device__ __forceinline__ typename Store<S>::R pull(const DevParams& P, const S
   const int ys = wrap(y - cy<Q>(I), P.ny);
   const int zz = P.walls ? zs : wrap(zs, P.nz);
   return Store<S>::ld(base + (size_t)I * P.Np + pdf_index(P, xs, ys, zz));
+}
+
+// Moving-wall momentum of direction I pulled into plane z (zero unless its
+// source lies beyond a moving wall); h takes it times phi.
+template <int Q, int I, class R>
+__device__ __forceinline__ R pull_wall_term(const DevParams& P, int z) {
+  if (!P.moving_walls) return (R)0;
+  const int zs = z - cz<Q>(I);
+  if (zs >= 0 && zs < P.nz) return (R)0;
+  return wall_momentum<Q, I, R>(P, zs >= P.nz ? 1 : 0);
 }
 
 // Zeroth moment of the pulled populations (un-shifted: the stored values plus
@@ -129,8 +140,10 @@ step_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, int zc
       R T;
       if constexpr (QF > 0) T = pulled_sum<QF, true>(P, A.f_src, gx, gy, zz, shf);
       else T = A.T[cell_index(P, gx, gy, zz)];
-      if (ghost) T = (R)2 * wall_T<R>(P, gx, zp < 0) - T;  // phi: mirror
-      s_phi[slot][k] = phi;
+      if (ghost) T = (R)2 * wall_T<R>(P, gx, zp < 0) - T;
+      // phi beyond a wall: the mirror, or the contact-angle ghost
+      const R phig = (ghost && P.wetting) ? wet_ghost<R>(phi, wall_k<R>(P, zp < 0 ? 0 : 1)) : phi;
+      s_phi[slot][k] = phig;
       s_T[slot][k] = T;
     }
   };
@@ -158,8 +171,15 @@ step_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A, int zc
         if (P.alpha_ratio && !P.rk_iso) rk_std<R, HX>(s_phi[sm], s_phi[sc], s_phi[sp], c0, pgx, pgy, pgz, plap);
       }
       const size_t cell = cell_index(P, x, y, z);
-      auto geth = [&](auto I) { return pull<QH, false, decltype(I)::value>(P, A.h_src, x, y, z, shh); };
-      auto getg = [&](auto I) { return pull<27, false, decltype(I)::value>(P, A.g_src, x, y, z, (R)0); };
+      const R phic = s_phi[sc][(ty + 1) * HX + (tx + 1)];
+      auto geth = [&](auto I) {
+        constexpr int i = decltype(I)::value;
+        return pull<QH, false, i>(P, A.h_src, x, y, z, shh) + phic * pull_wall_term<QH, i, R>(P, z);
+      };
+      auto getg = [&](auto I) {
+        constexpr int i = decltype(I)::value;
+        return pull<27, false, i>(P, A.g_src, x, y, z, (R)0) + pull_wall_term<27, i, R>(P, z);
+      };
       auto getf = [&](auto I) {
         if constexpr (QF > 0) return pull<QF, true, decltype(I)::value>(P, A.f_src, x, y, z, shf);
         else return (R)0;

@@ -44,7 +44,9 @@ class Params(ctypes.Structure):
                 ("T_top", ctypes.c_double), ("grad_T", ctypes.c_double * 3),
                 ("grad_T_origin", ctypes.c_double * 3), ("eps_n", ctypes.c_double),
                 ("omega_high", ctypes.c_double), ("rk_isotropic_fd", ctypes.c_int32),
-                ("T_bottom_amp", ctypes.c_double), ("T_bottom_waves", ctypes.c_int32)]
+                ("T_bottom_amp", ctypes.c_double), ("T_bottom_waves", ctypes.c_int32),
+                ("wall_u_bottom", ctypes.c_double * 2), ("wall_u_top", ctypes.c_double * 2),
+                ("theta_bottom", ctypes.c_double), ("theta_top", ctypes.c_double)]
 
 
 class HeatSource(ctypes.Structure):
@@ -158,7 +160,7 @@ def make_params(src=None, **kw) -> Params:
                 items[name] = getattr(src, name)
     items.update(kw)
     for name, val in items.items():
-        if name in ("gravity", "grad_T", "grad_T_origin"):
+        if name in ("gravity", "grad_T", "grad_T_origin", "wall_u_bottom", "wall_u_top"):
             getattr(p, name)[:] = [float(v) for v in val]
         elif name in ("walls_z", "rk_isotropic_fd"):
             setattr(p, name, int(bool(val)))
