@@ -70,6 +70,17 @@ typedef enum {
   LBM_TH_RK2 = 4, LBM_TH_RK4 = 5
 } lbm_thermal;
 
+/* Storage of the PDF sets.  LBM_LAYOUT_TWO_GRID: two sets, each step reads
+ * one and writes the other (the pull scheme of Sec. 4.1, "one step, two
+ * grids").  LBM_LAYOUT_AA: one set updated in place with the AA pattern
+ * (alternating a step that gathers from the neighbours and scatters to them
+ * with a step that gathers and scatters within the cell; Sec. 4.1 discusses
+ * such single-grid schemes), about half the memory; each step first writes
+ * a (phi, T) field of the level for the finite differences.  Same results
+ * (in FP64 bit for bit those of the generic two-grid kernel); the adjoint
+ * needs LBM_LAYOUT_TWO_GRID. */
+typedef enum { LBM_LAYOUT_TWO_GRID = 0, LBM_LAYOUT_AA = 1 } lbm_layout;
+
 /* Model parameters (Sec. 2.1-2.3).  lbm_default_params() fills defaults. */
 typedef struct {
   double nu_L, nu_H;       /* kinematic viscosity of the light (phi=0) / heavy (phi=1) phase;
@@ -161,6 +172,21 @@ lbm_status lbm_create_domain(int nx, int ny, int nz, lbm_precision prec,
                              lbm_thermal thermal, int q_phase, void* stream,
                              void* workspace, size_t workspace_bytes,
                              lbm_domain** out);
+
+/* lbm_workspace_bytes / lbm_create_domain with a choice of PDF layout
+ * (lbm_layout; the functions above use LBM_LAYOUT_TWO_GRID).  The in-place
+ * layout holds one PDF set plus a (phi, T) field: about half the bytes of
+ * the two-grid layout.  Every other call works on either layout;
+ * lbm_get_pdfs / lbm_set_pdfs exchange the same post-collision populations
+ * p_i(x) whatever the layout, and saved states record it (a state loads only
+ * into a domain of the same layout).  Errors as lbm_create_domain, and
+ * LBM_ERR_ARG for an unknown layout (lbm_workspace_bytes_layout: 0). */
+size_t lbm_workspace_bytes_layout(int nx, int ny, int nz, lbm_precision prec,
+                                  lbm_thermal thermal, int q_phase, lbm_layout pdf_layout);
+lbm_status lbm_create_domain_layout(int nx, int ny, int nz, lbm_precision prec,
+                                    lbm_thermal thermal, int q_phase, lbm_layout pdf_layout,
+                                    void* stream, void* workspace, size_t workspace_bytes,
+                                    lbm_domain** out);
 
 /* Synchronise the domain's stream and release everything the library owns. */
 lbm_status lbm_destroy_domain(lbm_domain* dom);

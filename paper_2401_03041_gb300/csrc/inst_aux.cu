@@ -2,6 +2,7 @@
 // conversion, diagnostics reduction).
 #include "launchers.h"
 #include "lbm_aux.cuh"
+#include "lbm_aa.cuh"
 #include "lbm_skew.cuh"
 
 namespace lbm {
@@ -31,6 +32,43 @@ void launch_pdf_convert(const DevParams& P, int Q, bool to_f64, void* pdf, doubl
     case 15: convert_q<S, 15>(P, to_f64, pdf, f64, shift, st); break;
     case 19: convert_q<S, 19>(P, to_f64, pdf, f64, shift, st); break;
     default: convert_q<S, 27>(P, to_f64, pdf, f64, shift, st); break;
+  }
+}
+
+template <class S, int Q>
+static void aa_swap_q(const DevParams& P, S* base, cudaStream_t st) {
+  const long long blocks = (P.N + 255) / 256;
+  const int grid = (int)(blocks < 152 * 64 ? blocks : 152 * 64);
+  aa_swap_kernel<S, Q><<<grid, 256, 0, st>>>(P, base);
+}
+
+template <class S>
+void launch_aa_swap(const DevParams& P, int Q, S* base, cudaStream_t st) {
+  switch (Q) {
+    case 7: aa_swap_q<S, 7>(P, base, st); break;
+    case 15: aa_swap_q<S, 15>(P, base, st); break;
+    case 19: aa_swap_q<S, 19>(P, base, st); break;
+    default: aa_swap_q<S, 27>(P, base, st); break;
+  }
+}
+
+template <class S, int Q>
+static void aa_convert_q(const DevParams& P, bool to_f64, void* pdf, double* f64, double shift, int odd,
+                         cudaStream_t st) {
+  const long long blocks = (P.N + 255) / 256;
+  const int grid = (int)(blocks < 152 * 64 ? blocks : 152 * 64);
+  if (to_f64) aa_to_f64_kernel<S, Q><<<grid, 256, 0, st>>>(P, (const S*)pdf, f64, shift, odd);
+  else f64_to_aa_kernel<S, Q><<<grid, 256, 0, st>>>(P, f64, (S*)pdf, shift, odd);
+}
+
+template <class S>
+void launch_aa_convert(const DevParams& P, int Q, bool to_f64, void* pdf, double* f64, double shift,
+                       int odd_level, cudaStream_t st) {
+  switch (Q) {
+    case 7: aa_convert_q<S, 7>(P, to_f64, pdf, f64, shift, odd_level, st); break;
+    case 15: aa_convert_q<S, 15>(P, to_f64, pdf, f64, shift, odd_level, st); break;
+    case 19: aa_convert_q<S, 19>(P, to_f64, pdf, f64, shift, odd_level, st); break;
+    default: aa_convert_q<S, 27>(P, to_f64, pdf, f64, shift, odd_level, st); break;
   }
 }
 
@@ -130,6 +168,12 @@ template void launch_rk_stage<__half>(const DevParams&, const float*, float*, co
 template void launch_pdf_convert<double>(const DevParams&, int, bool, void*, double*, double, cudaStream_t);
 template void launch_pdf_convert<float>(const DevParams&, int, bool, void*, double*, double, cudaStream_t);
 template void launch_pdf_convert<__half>(const DevParams&, int, bool, void*, double*, double, cudaStream_t);
+template void launch_aa_swap<double>(const DevParams&, int, double*, cudaStream_t);
+template void launch_aa_swap<float>(const DevParams&, int, float*, cudaStream_t);
+template void launch_aa_swap<__half>(const DevParams&, int, __half*, cudaStream_t);
+template void launch_aa_convert<double>(const DevParams&, int, bool, void*, double*, double, int, cudaStream_t);
+template void launch_aa_convert<float>(const DevParams&, int, bool, void*, double*, double, int, cudaStream_t);
+template void launch_aa_convert<__half>(const DevParams&, int, bool, void*, double*, double, int, cudaStream_t);
 template void launch_ghost_fill<double>(const DevParams&, void*, int, cudaStream_t);
 template void launch_ghost_fill<float>(const DevParams&, void*, int, cudaStream_t);
 template void launch_ghost_fill<__half>(const DevParams&, void*, int, cudaStream_t);

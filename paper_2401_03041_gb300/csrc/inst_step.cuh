@@ -5,6 +5,7 @@
 
 #include "launchers.h"
 #include "lbm_aux.cuh"
+#include "lbm_aa.cuh"
 #include "lbm_skew.cuh"
 
 namespace lbm {
@@ -59,6 +60,17 @@ void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
 }
 
 template <class S, int QH, int QF>
+void launch_aa_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A, void* phiT, int nb,
+                    dim3 grid, int zchunk, int mode, cudaStream_t st) {
+  using R = typename Store<S>::R;
+  using P2 = typename PairOf<R>::type;
+  const long long blocks = (P.N + 255) / 256;
+  const int mgrid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
+  aa_moments_kernel<S, QH, QF><<<mgrid, 256, 0, st>>>(P, A.h_src, A.f_src, A.T, nb, (P2*)phiT);
+  aa_step_kernel<S, QH, QF><<<grid, dim3(TX, TY), 0, st>>>(P, A, (const P2*)phiT, nb, zchunk, mode);
+}
+
+template <class S, int QH, int QF>
 void launch_init(const DevParams& P, const double* drops, int nd, S* h, S* g, S* f,
                  typename Store<S>::R* T, cudaStream_t st) {
   const dim3 grid((P.nx + kInitTX - 1) / kInitTX, (P.ny + kInitTY - 1) / kInitTY,
@@ -71,6 +83,9 @@ void launch_init(const DevParams& P, const double* drops, int nd, S* h, S* g, S*
                                                const StepPtrs<LBM_S, Store<LBM_S>::R>&,       \
                                                const TMaps&, dim3, int, const BulkSched&, int, int, \
                                                cudaStream_t);                                 \
+  template void launch_aa_step<LBM_S, LBM_QH, QF>(const DevParams&,                           \
+                                                  const StepPtrs<LBM_S, Store<LBM_S>::R>&,    \
+                                                  void*, int, dim3, int, int, cudaStream_t);  \
   template void launch_init<LBM_S, LBM_QH, QF>(const DevParams&, const double*, int, LBM_S*,  \
                                                LBM_S*, LBM_S*, Store<LBM_S>::R*, cudaStream_t);
 LBM_INST(0)

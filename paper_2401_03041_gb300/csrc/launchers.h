@@ -38,6 +38,17 @@ int bulk_tile_cols(int prec);
 int bulk_box_cols(int prec);   // staged row length W of the bulk kernel
 constexpr size_t kMaxDynSmem = 232448;
 
+// In-place (AA) layout: (phi, T) pass then the step, on the generic tiles;
+// nb = 1 for a step from an even level.
+template <class S, int QH, int QF>
+void launch_aa_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A, void* phiT, int nb,
+                    dim3 grid, int zchunk, int mode, cudaStream_t st);
+template <class S>
+void launch_aa_swap(const DevParams& P, int Q, S* base, cudaStream_t st);
+template <class S>
+void launch_aa_convert(const DevParams& P, int Q, bool to_f64, void* pdf, double* f64, double shift,
+                       int odd_level, cudaStream_t st);
+
 template <class S, int QH, int QF>
 void launch_init(const DevParams& P, const double* drops, int nd, S* h, S* g, S* f,
                  typename Store<S>::R* T, cudaStream_t st);

@@ -5,7 +5,9 @@
 //   T[N], u[3][N], S_a[N], S_b[N], acc[N]           RK thermal fields (compute type)
 //   diagnostics partials [grid][7], result [8]      FP64 reduction scratch
 //   droplet table [LBM_MAX_DROPLETS][7]             FP64 init input
-// Each step reads buffer `cur` and writes `cur ^ 1`, then flips `cur`.
+// Each step reads buffer `cur` and writes `cur ^ 1`, then flips `cur`.  With
+// the in-place (AA) layout there is one PDF set, stepped in place, plus a
+// (phi, T) field [N] of the compute type that each step refreshes first.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,7 +51,7 @@ size_t store_bytes(lbm_precision p) { return p == LBM_FP64 ? 8 : (p == LBM_FP32 
 size_t field_bytes(lbm_precision p) { return p == LBM_FP64 ? 8 : 4; }
 
 struct Layout {
-  size_t h[2], g[2], f[2], T, u, sa, sb, acc, phi, partials, diag, drops, errflag, total;
+  size_t h[2], g[2], f[2], T, u, sa, sb, acc, phi, phiT, partials, diag, drops, errflag, total;
 };
 
 // Launch geometry of the step kernel: TX x rows columns, z split into chunks;
@@ -170,7 +172,7 @@ Pad padding(int nx, int ny, int nz, lbm_precision prec) {
   return p;
 }
 
-bool layout(int nx, int ny, int nz, lbm_precision prec, lbm_thermal th, int qh, Layout* L) {
+bool layout(int nx, int ny, int nz, lbm_precision prec, lbm_thermal th, int qh, Layout* L, bool aa = false) {
   // launch grids put nz (one plane per z block) and ny / 4 on the 16-bit grid axes
   if (nx < 1 || ny < 1 || nz < 1 || nz > 65535 || ny > 262140) return false;
   if (qh != 15 && qh != 27) return false;
@@ -185,6 +187,13 @@ bool layout(int nx, int ny, int nz, lbm_precision prec, lbm_thermal th, int qh, 
   // one PDF set = [h (qh) | g (27) | f (qf)] directions of Np elements each,
   // contiguous, so that one ghost-fill launch covers the whole set
   for (int k = 0; k < 2; ++k) {
+    if (aa && k == 1) {
+      // in-place layout: one set, both indices name it
+      L->h[1] = L->h[0];
+      L->g[1] = L->g[0];
+      L->f[1] = L->f[0];
+      break;
+    }
     L->h[k] = off;
     L->g[k] = off + (size_t)qh * pd.Np * sb;
     L->f[k] = L->g[k] + (size_t)27 * pd.Np * sb;
@@ -198,6 +207,7 @@ bool layout(int nx, int ny, int nz, lbm_precision prec, lbm_thermal th, int qh, 
   L->sb = off; off = align256(off + (rk4 ? N * fb : 0));
   L->acc = off; off = align256(off + (rk4 ? N * fb : 0));
   L->phi = off; off = align256(off + (rk ? N * fb : 0));   // phi of the step (conductivity ratio)
+  L->phiT = off; off = align256(off + (aa ? 2 * N * fb : 0));   // (phi, T) of the level (in-place layout)
   // room for the largest grid any kernel / z-chunk choice can produce
   const size_t max_blocks = (size_t)((nx + TX - 1) / TX) * ((ny + 3) / 4) * nz;
   L->partials = off; off = align256(off + max_blocks * kDiagVals * 8);
@@ -222,6 +232,7 @@ struct lbm_domain {
   bool owns_ws;
   Layout L;
   Geometry geo;
+  bool aa = false;  // in-place (AA) layout
   int sms;  // multiprocessors of the device (launch geometry)
   int cur;
   bool params_set, inited;
@@ -315,6 +326,28 @@ void step_launch(lbm_domain* d, const StepPtrs<S, typename Store<S>::R>& A, int 
   else step_qf<S, 27>(d, A, mode);
 }
 
+// In-place layout: (phi, T) of the level, then the step (gathers from the
+// neighbours when the level is even, locally when it is odd).
+template <class S>
+void aa_launch(lbm_domain* d, const StepPtrs<S, typename Store<S>::R>& A, int mode) {
+  using R = typename Store<S>::R;
+  const int nb = (d->level & 1) == 0 ? 1 : 0;
+  void* phiT = at(d, d->L.phiT);
+  auto qf = [&](auto qh_tag) {
+    constexpr int QH = decltype(qh_tag)::value;
+    switch (d->qf) {
+      case 0: launch_aa_step<S, QH, 0>(d->dp, A, phiT, nb, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
+      case 7: launch_aa_step<S, QH, 7>(d->dp, A, phiT, nb, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
+      case 15: launch_aa_step<S, QH, 15>(d->dp, A, phiT, nb, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
+      case 19: launch_aa_step<S, QH, 19>(d->dp, A, phiT, nb, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
+      default: launch_aa_step<S, QH, 27>(d->dp, A, phiT, nb, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
+    }
+  };
+  (void)sizeof(R);
+  if (d->qh == 15) qf(std::integral_constant<int, 15>{});
+  else qf(std::integral_constant<int, 27>{});
+}
+
 template <class S>
 void rk_tail(lbm_domain* d) {
   using R = typename Store<S>::R;
@@ -354,7 +387,8 @@ lbm_status run_pass(lbm_domain* d, int mode, void* macro_out = nullptr, int macr
     A.macro_mask = mask;
     const bool timed = d->prof_on && (size_t)(2 * d->prof_n + 1) < d->prof_ev.size();
     if (timed) cudaEventRecord(d->prof_ev[2 * d->prof_n], d->stream);
-    step_launch<S>(d, A, mode);
+    if (d->aa) aa_launch<S>(d, A, mode);
+    else step_launch<S>(d, A, mode);
     if (timed) cudaEventRecord(d->prof_ev[2 * d->prof_n++ + 1], d->stream);
     if (mode & MODE_COLLIDE) ghost_fill(d, d->cur ^ 1);
     if ((mode & MODE_COLLIDE) && d->qf == 0) rk_tail<S>(d);
@@ -365,7 +399,7 @@ lbm_status run_pass(lbm_domain* d, int mode, void* macro_out = nullptr, int macr
   lbm_status s = check_launch(d, "step kernel launch");
   if (s != LBM_OK) return s;
   if (mode & MODE_COLLIDE) {
-    d->cur ^= 1;
+    if (!d->aa) d->cur ^= 1;
     d->level += 1;
   }
   return LBM_OK;
@@ -563,21 +597,37 @@ void lbm_default_params(lbm_params* p) {
   p->omega_high = 1.0;
 }
 
+size_t lbm_workspace_bytes_layout(int nx, int ny, int nz, lbm_precision prec, lbm_thermal thermal,
+                                  int q_phase, lbm_layout pdf_layout) {
+  Layout L;
+  if (pdf_layout != LBM_LAYOUT_TWO_GRID && pdf_layout != LBM_LAYOUT_AA) return 0;
+  if (!layout(nx, ny, nz, prec, thermal, q_phase, &L, pdf_layout == LBM_LAYOUT_AA)) return 0;
+  return L.total;
+}
+
 size_t lbm_workspace_bytes(int nx, int ny, int nz, lbm_precision prec, lbm_thermal thermal,
                            int q_phase) {
-  Layout L;
-  if (!layout(nx, ny, nz, prec, thermal, q_phase, &L)) return 0;
-  return L.total;
+  return lbm_workspace_bytes_layout(nx, ny, nz, prec, thermal, q_phase, LBM_LAYOUT_TWO_GRID);
 }
 
 lbm_status lbm_create_domain(int nx, int ny, int nz, lbm_precision prec, lbm_thermal thermal,
                              int q_phase, void* stream, void* workspace, size_t workspace_bytes,
                              lbm_domain** out) {
+  return lbm_create_domain_layout(nx, ny, nz, prec, thermal, q_phase, LBM_LAYOUT_TWO_GRID, stream, workspace,
+                                  workspace_bytes, out);
+}
+
+lbm_status lbm_create_domain_layout(int nx, int ny, int nz, lbm_precision prec, lbm_thermal thermal,
+                                    int q_phase, lbm_layout pdf_layout, void* stream, void* workspace,
+                                    size_t workspace_bytes, lbm_domain** out) {
   g_last_error.clear();
   if (!out) return fail(LBM_ERR_ARG, "out is null");
   *out = nullptr;
+  if (pdf_layout != LBM_LAYOUT_TWO_GRID && pdf_layout != LBM_LAYOUT_AA)
+    return fail(LBM_ERR_ARG, "unknown PDF layout");
+  const bool aa = pdf_layout == LBM_LAYOUT_AA;
   Layout L;
-  if (!layout(nx, ny, nz, prec, thermal, q_phase, &L))
+  if (!layout(nx, ny, nz, prec, thermal, q_phase, &L, aa))
     return fail(LBM_ERR_ARG, "invalid lattice size, precision, thermal scheme or q_phase");
   if (workspace && workspace_bytes < L.total)
     return fail(LBM_ERR_OOM, "workspace smaller than lbm_workspace_bytes()");
@@ -590,6 +640,7 @@ lbm_status lbm_create_domain(int nx, int ny, int nz, lbm_precision prec, lbm_the
   d->prec = prec; d->th = thermal; d->qh = q_phase; d->qf = thermal_q(thermal);
   d->stream = (cudaStream_t)stream;
   d->L = L;
+  d->aa = aa;
   {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -599,7 +650,8 @@ lbm_status lbm_create_domain(int nx, int ny, int nz, lbm_precision prec, lbm_the
     }
     d->sms = sms;
   }
-  d->geo = geometry(nx, ny, nz, prec, q_phase, thermal_q(thermal), d->sms);
+  // the in-place layout runs its own kernels on the generic kernel's tiles
+  d->geo = geometry(nx, ny, nz, prec, q_phase, thermal_q(thermal), d->sms, !aa);
   d->sticky = LBM_OK;
   if (const char* env = std::getenv("LBM_TEST_STALL")) d->test_stall = std::atoi(env) != 0;
   lbm_default_params(&d->params);
@@ -796,6 +848,18 @@ lbm_status lbm_init_droplets(lbm_domain* d, int n, const lbm_droplet* drops) {
   else if (d->prec == LBM_FP32) go(float{});
   else go(__half{});
   ghost_fill(d, 0);
+  if (d->aa) {
+    // level 0 of the in-place layout: p_i(x) in slot opp(i)
+    auto sw = [&](auto tag) {
+      using S = decltype(tag);
+      launch_aa_swap<S>(d->dp, d->qh, (S*)at(d, d->L.h[0]), d->stream);
+      launch_aa_swap<S>(d->dp, 27, (S*)at(d, d->L.g[0]), d->stream);
+      if (d->qf > 0) launch_aa_swap<S>(d->dp, d->qf, (S*)at(d, d->L.f[0]), d->stream);
+    };
+    if (d->prec == LBM_FP64) sw(double{});
+    else if (d->prec == LBM_FP32) sw(float{});
+    else sw(__half{});
+  }
   s = check_launch(d, "init kernel launch");
   if (s != LBM_OK) return s;
   if (n > 0) {
@@ -916,7 +980,8 @@ static lbm_status pdf_io(lbm_domain* d, int which, double* host, bool to_host) {
   if (s != LBM_OK) return s;
   auto conv = [&](auto tag, bool dir) {
     using S = decltype(tag);
-    launch_pdf_convert<S>(d->dp, Q, dir, buf, tmp, shift, d->stream);
+    if (d->aa) launch_aa_convert<S>(d->dp, Q, dir, buf, tmp, shift, (int)(d->level & 1), d->stream);
+    else launch_pdf_convert<S>(d->dp, Q, dir, buf, tmp, shift, d->stream);
   };
   if (!to_host) s = check_cuda(d, cudaMemcpyAsync(tmp, host, bytes, cudaMemcpyHostToDevice, d->stream), "upload");
   if (s == LBM_OK) {
@@ -952,7 +1017,7 @@ namespace {
 // Header of a saved state: the domain description it belongs to.
 struct StateHeader {
   char magic[8];
-  int32_t version, nx, ny, nz, prec, thermal, q_phase, pad_;
+  int32_t version, nx, ny, nz, prec, thermal, q_phase, pad_;   // pad_: PDF layout (1 = in place)
   int64_t level;
   uint64_t pdf_bytes, field_bytes;
 };
@@ -986,6 +1051,7 @@ lbm_status lbm_save_state(lbm_domain* d, void* host_buf, size_t bytes) {
   h.version = 1;
   h.nx = d->nx; h.ny = d->ny; h.nz = d->nz;
   h.prec = (int32_t)d->prec; h.thermal = (int32_t)d->th; h.q_phase = d->qh;
+  h.pad_ = d->aa ? 1 : 0;   // PDF layout
   h.level = d->level;
   h.pdf_bytes = state_pdf_bytes(d);
   h.field_bytes = state_field_bytes(d);
@@ -1010,8 +1076,8 @@ lbm_status lbm_load_state(lbm_domain* d, const void* host_buf, size_t bytes) {
   if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 1)
     return fail(LBM_ERR_ARG, "not a saved state (bad magic or version)");
   if (h.nx != d->nx || h.ny != d->ny || h.nz != d->nz || h.prec != (int32_t)d->prec ||
-      h.thermal != (int32_t)d->th || h.q_phase != d->qh)
-    return fail(LBM_ERR_ARG, "saved state belongs to a domain of another size, precision or stencil");
+      h.thermal != (int32_t)d->th || h.q_phase != d->qh || h.pad_ != (d->aa ? 1 : 0))
+    return fail(LBM_ERR_ARG, "saved state belongs to a domain of another size, precision, stencil or layout");
   if (h.pdf_bytes != state_pdf_bytes(d) || h.field_bytes != state_field_bytes(d) ||
       bytes < lbm_state_bytes(d))
     return fail(LBM_ERR_ARG, "saved state has an unexpected size");
@@ -1083,7 +1149,7 @@ lbm_status lbm_stencil(int Q, int32_t* c_out, double* w_out) {
 
 lbm_status lbm_kernel_info(lbm_domain* d, int32_t* info) {
   if (!d || !info) return fail(LBM_ERR_ARG, "null argument");
-  info[0] = d->geo.bulk;
+  info[0] = d->aa ? 3 : d->geo.bulk;
   info[1] = (int32_t)d->geo.grid.x;
   info[2] = (int32_t)d->geo.grid.y;
   info[3] = (int32_t)d->geo.grid.z;
@@ -1179,6 +1245,7 @@ lbm_status adj_check(lbm_domain* d) {
     return fail(LBM_ERR_UNSUPPORTED, "the adjoint is built for equal densities (rho_L == rho_H)");
   if (d->dp.wall_ext)
     return fail(LBM_ERR_UNSUPPORTED, "the adjoint is built for walls at rest with neutral wetting");
+  if (d->aa) return fail(LBM_ERR_UNSUPPORTED, "the adjoint is built for the two-grid layout");
   if ((long long)d->nx * d->ny >= (1LL << 31))
     return fail(LBM_ERR_UNSUPPORTED, "the adjoint needs nx * ny < 2^31");
   return LBM_OK;

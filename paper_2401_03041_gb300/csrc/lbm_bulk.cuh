@@ -245,12 +245,12 @@ template <class S, int QH, int QF, bool EXT, class G, bool BOUNCE>
 __device__ __forceinline__ void stage_sum_plane_v(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                                                   const S* st, typename PairOf<typename Store<S>::R>::type* pt,
                                                   int p, int pe, bool ghost, bool lo, bool hi, int x0, int y0,
-                                                  int k0, int kstep) {
+                                                  int k0, int kstep, int kend) {
   using R = typename Store<S>::R;
   using P2 = typename PairOf<R>::type;
   const auto& rp = RP<R>(P);
   const R shh = (R)rp.shift_h, shf = (R)rp.shift_f;
-  for (int k = k0; k < G::HPB; k += kstep) {
+  for (int k = k0; k < kend; k += kstep) {
     const int hr = k / G::HXB, hc = k % G::HXB;
     const int col = hc + G::GXP - 1;
     const S* rowb = st + (size_t)hr * G::W + col;
@@ -317,7 +317,8 @@ __device__ __forceinline__ void stage_sum_plane_v(const DevParams& P, const Step
 template <class S, int QH, int QF, bool EXT, class G>
 __device__ __forceinline__ void stage_sum_plane(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                                                 const S* st, typename PairOf<typename Store<S>::R>::type* pt,
-                                                int p, int x0, int y0, int k0, int kstep) {
+                                                int p, int x0, int y0, int k0, int kstep,
+                                                int kend = G::HPB) {
   int pe = p;
   bool ghost = false;
   if (P.walls) {
@@ -327,8 +328,10 @@ __device__ __forceinline__ void stage_sum_plane(const DevParams& P, const StepPt
     pe = p < 0 ? p + P.nz : (p >= P.nz ? p - P.nz : p);  // periodic z
   }
   const bool lo = P.walls && pe == 0, hi = P.walls && pe == P.nz - 1;
-  if (lo || hi) stage_sum_plane_v<S, QH, QF, EXT, G, true>(P, A, st, pt, p, pe, ghost, lo, hi, x0, y0, k0, kstep);
-  else stage_sum_plane_v<S, QH, QF, EXT, G, false>(P, A, st, pt, p, pe, ghost, false, false, x0, y0, k0, kstep);
+  if (lo || hi)
+    stage_sum_plane_v<S, QH, QF, EXT, G, true>(P, A, st, pt, p, pe, ghost, lo, hi, x0, y0, k0, kstep, kend);
+  else
+    stage_sum_plane_v<S, QH, QF, EXT, G, false>(P, A, st, pt, p, pe, ghost, false, false, x0, y0, k0, kstep, kend);
 }
 
 // EXT: the extensions of the uniform-property model (conductivity ratio,

@@ -110,6 +110,12 @@ __device__ __forceinline__ R cdot(R vx, R vy, R vz) {
   }
 }
 
+// Where a collision writes its post-collision populations: StdPut stores
+// direction i of the cell at dst[i] + pcell (the two-grid layout); another
+// policy is a callable put(std::integral_constant<int, i>, value) (the
+// in-place AA layout, whose destinations depend on the step's phase).
+struct StdPut {};
+
 // Is direction i the first of its opposite pair (first non-zero component > 0)?
 template <int Q>
 __host__ __device__ constexpr bool pair_first(int i) {
@@ -411,11 +417,11 @@ __device__ __forceinline__ void cell_outputs(const DevParams& P, const StepPtrs<
 }
 
 // a8: g collision (central moments, closed form)
-template <class S>
+template <class S, class PUT = StdPut>
 __device__ __forceinline__ void collide_g(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                                           size_t pcell, typename Store<S>::R phi,
                                           const GMoments<typename Store<S>::R>& m,
-                                          const CellFlow<typename Store<S>::R>& f) {
+                                          const CellFlow<typename Store<S>::R>& f, PUT put = PUT{}) {
   using R = typename Store<S>::R;
   const auto& rp = RP<R>(P);
   const R ux = f.ux, uy = f.uy, uz = f.uz, ax = f.ax, ay = f.ay, az = f.az, uu = f.uu;
@@ -462,7 +468,11 @@ __device__ __forceinline__ void collide_g(const DevParams& P, const StepPtrs<S, 
     const R r2 = ex == 0 ? (R)-1 : (R)0.5;
     return r0 * B0 + r1 * B1 + r2 * B2;
   };
-  Store<S>::st(A.gd[0] + pcell, (R)weight<27>(0) * base + neq_of(0, 0, 0));
+  auto out = [&](auto I, R v) {
+    if constexpr (std::is_same<PUT, StdPut>::value) Store<S>::st(A.gd[decltype(I)::value] + pcell, v);
+    else put(I, v);
+  };
+  out(std::integral_constant<int, 0>{}, (R)weight<27>(0) * base + neq_of(0, 0, 0));
   static_for<1, 27>([&](auto I) {
     constexpr int i = decltype(I)::value;
     if constexpr (pair_first<27>(i)) {
@@ -474,8 +484,8 @@ __device__ __forceinline__ void collide_g(const DevParams& P, const StepPtrs<S, 
       const R ca15 = cdot<ex, ey, ez>(a15x, a15y, a15z);
       const R odd = cu3 + ca15;
       const R even = (R)0.5 * cu3 * (odd + ca15) + base;
-      Store<S>::st(A.gd[i] + pcell, w * (even + odd) + neq_of(ex, ey, ez));
-      Store<S>::st(A.gd[opp<27>(i)] + pcell, w * (even - odd) + neq_of(-ex, -ey, -ez));
+      out(I, w * (even + odd) + neq_of(ex, ey, ez));
+      out(std::integral_constant<int, opp<27>(i)>{}, w * (even - odd) + neq_of(-ex, -ey, -ez));
     }
   });
 }
@@ -486,11 +496,11 @@ __device__ __forceinline__ void collide_g(const DevParams& P, const StepPtrs<S, 
 //   h'_i - w_i s = hs_i - omega (hs_i - w_i (phi E_i - s)) + S_i
 // works on stored values throughout, so the shift costs nothing per
 // direction.
-template <class S, int QH, class GH>
+template <class S, int QH, class GH, class PUT = StdPut>
 __device__ __forceinline__ void collide_h(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                                           size_t pcell, typename Store<S>::R phi, typename Store<S>::R gpx,
                                           typename Store<S>::R gpy, typename Store<S>::R gpz,
-                                          const CellFlow<typename Store<S>::R>& f, GH geth) {
+                                          const CellFlow<typename Store<S>::R>& f, GH geth, PUT put = PUT{}) {
   using R = typename Store<S>::R;
   const auto& rp = RP<R>(P);
   const R ux = f.ux, uy = f.uy, uz = f.uz, uu = f.uu;
@@ -503,10 +513,14 @@ __device__ __forceinline__ void collide_h(const DevParams& P, const StepPtrs<S, 
   const R sh = (R)rp.shift_h;
   const R base = phi * ((R)1 - (R)1.5 * uu) - sh;   // phi e0 - s
   const R p45 = (R)4.5 * phi, p3 = (R)3 * phi;
+  auto out = [&](auto I, R v) {
+    if constexpr (std::is_same<PUT, StdPut>::value) Store<S>::st(A.hd[decltype(I)::value] + pcell, v);
+    else put(I, v);
+  };
   {
     constexpr R w = (R)weight<QH>(0);
     const R hs = geth(std::integral_constant<int, 0>{});
-    Store<S>::st(A.hd[0] + pcell, hs - om * (hs - w * base));
+    out(std::integral_constant<int, 0>{}, hs - om * (hs - w * base));
   }
   static_for<1, QH>([&](auto I) {
     constexpr int i = decltype(I)::value;
@@ -519,8 +533,8 @@ __device__ __forceinline__ void collide_h(const DevParams& P, const StepPtrs<S, 
       const R odd = w * (p3 * cu);
       const R src = sc * w * cf;
       const R hi = geth(I), hj = geth(std::integral_constant<int, j>{});
-      Store<S>::st(A.hd[i] + pcell, hi - om * (hi - (even + odd)) + src);
-      Store<S>::st(A.hd[j] + pcell, hj - om * (hj - (even - odd)) - src);
+      out(I, hi - om * (hi - (even + odd)) + src);
+      out(std::integral_constant<int, j>{}, hj - om * (hj - (even - odd)) - src);
     }
   });
 }
@@ -532,7 +546,7 @@ __device__ __forceinline__ void collide_h(const DevParams& P, const StepPtrs<S, 
 // term, with grad phi from its own operator (pgx.. central differences for the
 // 7-point set, the isotropic gradient otherwise).  RATIO = P.alpha_ratio,
 // resolved by the caller so that the equal-diffusivity path carries none of it.
-template <class S, int QF, bool RATIO, class GF>
+template <class S, int QF, bool RATIO, class GF, class PUT = StdPut>
 __device__ __forceinline__ void collide_f(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                                           int x, int y, int z, size_t cell, size_t pcell,
                                           typename Store<S>::R phi, typename Store<S>::R Tc,
@@ -541,11 +555,15 @@ __device__ __forceinline__ void collide_f(const DevParams& P, const StepPtrs<S, 
                                           typename Store<S>::R rgz, typename Store<S>::R rlap,
                                           typename Store<S>::R pgx, typename Store<S>::R pgy,
                                           typename Store<S>::R pgz,
-                                          const CellFlow<typename Store<S>::R>& f, GF getf) {
+                                          const CellFlow<typename Store<S>::R>& f, GF getf, PUT put = PUT{}) {
   using R = typename Store<S>::R;
   const auto& rp = RP<R>(P);
   const R ux = f.ux, uy = f.uy, uz = f.uz, uu = f.uu;
   const R Gx = (R)rp.grad[0], Gy = (R)rp.grad[1], Gz = (R)rp.grad[2];
+  auto out = [&](auto I, R v) {
+    if constexpr (std::is_same<PUT, StdPut>::value) Store<S>::st(A.fd[decltype(I)::value] + pcell, v);
+    else put(I, v);
+  };
   const R q = heat_source<R>(P, x, y, z);
   const R uG = ux * Gx + uy * Gy + uz * Gz;
   if constexpr (QF > 0) {
@@ -562,11 +580,11 @@ __device__ __forceinline__ void collide_f(const DevParams& P, const StepPtrs<S, 
     if constexpr (weight<QF>(0) != 0.0) {
       constexpr R w = (R)weight<QF>(0);
       const R fs = getf(std::integral_constant<int, 0>{});
-      Store<S>::st(A.fd[0] + pcell, fs - om * (fs - w * base) + w * qs);
+      out(std::integral_constant<int, 0>{}, fs - om * (fs - w * base) + w * qs);
     } else {
       // D3Q7 (w_0 = 0): the rest population relaxes to 0
       const R fs = getf(std::integral_constant<int, 0>{});
-      Store<S>::st(A.fd[0] + pcell, fs - om * fs);
+      out(std::integral_constant<int, 0>{}, fs - om * fs);
     }
     static_for<1, QF>([&](auto I) {
       constexpr int i = decltype(I)::value;
@@ -578,8 +596,8 @@ __device__ __forceinline__ void collide_f(const DevParams& P, const StepPtrs<S, 
         const R odd = w * (t3 * cu);
         const R wq = w * qs;
         const R fi = getf(I), fj = getf(std::integral_constant<int, j>{});
-        Store<S>::st(A.fd[i] + pcell, fi - om * (fi - (even + odd)) + wq);
-        Store<S>::st(A.fd[j] + pcell, fj - om * (fj - (even - odd)) + wq);
+        out(I, fi - om * (fi - (even + odd)) + wq);
+        out(std::integral_constant<int, j>{}, fj - om * (fj - (even - odd)) + wq);
       }
     });
   } else {

@@ -57,6 +57,11 @@ struct SkewSmemT {
   static constexpr size_t bytes = off_bar + 5 * sizeof(uint64_t) + 128;
   static constexpr uint32_t hf_tx = (uint32_t)((size_t)NHF * G::W * (G::TYB + 2) * sizeof(S));
   static constexpr uint32_t g_tx = (uint32_t)((size_t)27 * G::W * G::TYB * sizeof(S));
+  // halo items of a plane's phi / T sum taken by the g role: the first SUM_A
+  // of the tile's HPB items, as many as leave one item per stencil-role
+  // thread (at most one per g-role thread); the stencil role sums the rest
+  // and waits for both shares
+  static constexpr int SUM_A = G::HPB - G::NT < 0 ? 0 : (G::HPB - G::NT > G::NT ? G::NT : G::HPB - G::NT);
 };
 
 // The skewed kernel uses the bulk kernel's tile (one launch geometry for
@@ -144,10 +149,13 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     mark(3 + g_slot(p), g_par(p));
   };
   auto a_barrier = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(NC) : "memory"); };
-  auto b_barrier = [&]() { asm volatile("bar.sync 2, %0;" ::"r"(NC) : "memory"); };
-  auto sum_plane = [&](int p, int k0, int kstep) {
-    stage_sum_plane<S, QH, QF, EXT, G>(P, A, hf_ptr(p), pt_ptr(p), p, x0, y0, k0, kstep);
+  auto sum_plane = [&](int p, int k0, int kstep, int kend = G::HPB) {
+    stage_sum_plane<S, QH, QF, EXT, G>(P, A, hf_ptr(p), pt_ptr(p), p, x0, y0, k0, kstep, kend);
   };
+  // producer / consumer barrier of a plane's phi / T sum: the g role arrives
+  // once its share is written, the stencil role waits for every share
+  auto sum_arrive = [&]() { asm volatile("bar.arrive 3, %0;" ::"r"(NT) : "memory"); };
+  auto sum_wait = [&]() { asm volatile("bar.sync 3, %0;" ::"r"(NT) : "memory"); };
 
   // moments of the pulled g of plane p (g role), as GMoments
   auto moments = [&](int p) {
@@ -321,6 +329,12 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     // done in the previous iteration)
     if (z + 3 <= z1) issue_hf(z + 3, 0);
     if (role_g) {
+      // the g role's share of phi / T of plane z + 2, first
+      if (z + 2 <= z1) {
+        ok = ok && wait_slot(hf_slot(z + 2), hf_par(z + 2));
+        if (ok) sum_plane(z + 2, cidx, NC, L::SUM_A);
+      }
+      sum_arrive();
       if (active && (mode & MODE_COLLIDE)) g_collide(z, mA0);
       mA0 = mA1;
       if (z + 2 < z1) {
@@ -338,9 +352,9 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     } else {
       if (z + 2 <= z1) {
         ok = ok && wait_slot(hf_slot(z + 2), hf_par(z + 2));
-        if (ok) sum_plane(z + 2, cidx, NC);
+        if (ok) sum_plane(z + 2, L::SUM_A + cidx, NC);
       }
-      b_barrier();   // phi / T of plane z + 2 complete
+      sum_wait();   // phi / T of plane z + 2 complete (both shares)
       if (ok && z + 1 < z1 && active) {
         b_stencil(z + 1);
         b_collide(z + 1);

@@ -20,9 +20,11 @@ STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_OOM",
 PRECISION = {"fp64": 0, "fp32": 1, "fp16": 2}
 THERMAL = {"D3Q7": 0, "D3Q15": 1, "D3Q19": 2, "D3Q27": 3, "RK2": 4, "RK4": 5}
 FIELD_PHI, FIELD_U, FIELD_P, FIELD_T = 1, 2, 4, 8
+LAYOUT = {"two_grid": 0, "aa": 1}
 
 # Every symbol include/lbm.h declares.
 SYMBOLS = ("lbm_default_params", "lbm_workspace_bytes", "lbm_create_domain",
+           "lbm_workspace_bytes_layout", "lbm_create_domain_layout",
            "lbm_destroy_domain", "lbm_set_params", "lbm_set_heat_sources",
            "lbm_set_heater_patches", "lbm_set_heater_field", "lbm_init_droplets", "lbm_step",
            "lbm_step_diagnostics", "lbm_get_diagnostics", "lbm_get_fields",
@@ -102,6 +104,9 @@ def lib():
         "lbm_default_params": (None, [P(Params)]),
         "lbm_workspace_bytes": (sz, [c_int, c_int, c_int, c_int, c_int, c_int]),
         "lbm_create_domain": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int, vp, vp, sz, P(vp)]),
+        "lbm_workspace_bytes_layout": (sz, [c_int, c_int, c_int, c_int, c_int, c_int, c_int]),
+        "lbm_create_domain_layout": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int, c_int, vp, vp, sz,
+                                             P(vp)]),
         "lbm_destroy_domain": (c_int, [vp]),
         "lbm_set_params": (c_int, [vp, P(Params)]),
         "lbm_set_heat_sources": (c_int, [vp, c_int, P(HeatSource)]),
@@ -211,26 +216,28 @@ class Domain:
     (default: torch's current stream)."""
 
     def __init__(self, nx, ny, nz, precision="fp64", thermal="D3Q7", q_phase=15,
-                 stream=None, device=None):
+                 stream=None, device=None, layout="two_grid"):
         import torch
         L = lib()
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.N = self.nx * self.ny * self.nz
         self.precision, self.thermal, self.q_phase = precision, thermal, int(q_phase)
+        self.layout = layout
+        lay = LAYOUT[layout]
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-        nbytes = L.lbm_workspace_bytes(self.nx, self.ny, self.nz, PRECISION[precision],
-                                       THERMAL[thermal], self.q_phase)
+        nbytes = L.lbm_workspace_bytes_layout(self.nx, self.ny, self.nz, PRECISION[precision],
+                                              THERMAL[thermal], self.q_phase, lay)
         if nbytes == 0:
             raise LBMError("lbm_workspace_bytes", -1, "invalid domain description")
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         h = ctypes.c_void_p()
-        _check("lbm_create_domain",
-               L.lbm_create_domain(self.nx, self.ny, self.nz, PRECISION[precision],
-                                   THERMAL[thermal], self.q_phase,
-                                   ctypes.c_void_p(self.stream.cuda_stream),
-                                   ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
-                                   ctypes.byref(h)))
+        _check("lbm_create_domain_layout",
+               L.lbm_create_domain_layout(self.nx, self.ny, self.nz, PRECISION[precision],
+                                          THERMAL[thermal], self.q_phase, lay,
+                                          ctypes.c_void_p(self.stream.cuda_stream),
+                                          ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                          ctypes.byref(h)))
         self._h = h
         self._npatch = 0
 
@@ -321,7 +328,7 @@ class Domain:
     def kernel_info(self) -> dict:
         v = (ctypes.c_int32 * 6)()
         _check("lbm_kernel_info", lib().lbm_kernel_info(self._h, v))
-        return {"kernel": {0: "generic", 1: "bulk", 2: "skew"}.get(v[0], str(v[0])),
+        return {"kernel": {0: "generic", 1: "bulk", 2: "skew", 3: "aa"}.get(v[0], str(v[0])),
                 "grid": (v[1], v[2], v[3]), "zchunk": v[4], "smem_bytes": v[5]}
 
     def adjoint_run(self, steps: int, ckpt_every: int, target, normal_cap: float = 0.0):
