@@ -309,11 +309,14 @@ def main():
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the thermal option x storage sweep (kernel-only timing of each)")
     ap.add_argument("--sweep-steps", type=int, default=8)
+    ap.add_argument("--no-aa", action="store_true", help="skip the in-place (AA) layout leg")
+    ap.add_argument("--aa-large-n", type=int, default=1024,
+                    help="edge of the large lattice run in the in-place layout (0: skip)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time the step kernel only (no CPU, e2e, FP64, sweep or error legs; for profiling)")
     args = ap.parse_args()
     if args.kernel_only:
-        args.no_cpu = args.no_fp64 = args.no_adjoint = args.no_sweep = True
+        args.no_cpu = args.no_fp64 = args.no_adjoint = args.no_sweep = args.no_aa = True
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
@@ -559,6 +562,45 @@ def main():
                 del ds
                 torch.cuda.empty_cache()
 
+    # ---------------- in-place (AA) layout: the headline workload, then a
+    # lattice the two-grid layout cannot hold on this GPU
+    aa = None
+    if not args.no_aa:
+        aa = []
+        peak_a, _ = peaks()
+        free_b, total_b = torch.cuda.mem_get_info(dev)
+        for n_aa, nst in ((args.n, args.sweep_steps), (args.aa_large_n, 3)):
+            if n_aa <= 0:
+                continue
+            wa = W.config4(args.thermal, args.precision, n=n_aa)
+            two = lbm.lib().lbm_workspace_bytes_layout(n_aa, n_aa, n_aa, lbm.PRECISION[args.precision],
+                                                       lbm.THERMAL[wa.thermal], wa.q_phase, 0)
+            one = lbm.lib().lbm_workspace_bytes_layout(n_aa, n_aa, n_aa, lbm.PRECISION[args.precision],
+                                                       lbm.THERMAL[wa.thermal], wa.q_phase, 1)
+            rec = {"n": n_aa, "workspace_gb": one / 1e9, "two_grid_workspace_gb": two / 1e9,
+                   "gpu_memory_gb": total_b / 1e9, "two_grid_fits": two < free_b}
+            if one >= free_b:
+                rec["skipped"] = "does not fit"
+                aa.append(rec)
+                continue
+            da = lbm.Domain(wa.nx, wa.ny, wa.nz, args.precision, wa.thermal, wa.q_phase, device=dev, layout="aa")
+            da.set_params(wa.params)
+            da.init_droplets(wa.droplets)
+            asecs, _, aker = timed_steps(da, nst, 3)
+            asecs = reduce_max(asecs)
+            aker = reduce_max(aker) if aker else None
+            bpa = step_kernel_bytes_per_cell(args.precision, wa.thermal, wa.q_phase)
+            rec.update({"kernel": da.kernel_info()["kernel"], "steps": nst,
+                        "mlups": job_mlups(wa.cells, nst, world, asecs), "step_ms": asecs / nst * 1e3,
+                        "kernels_ms": aker * 1e3 if aker else None,
+                        "frac": bpa * wa.cells / aker / 1e9 / peak_a if aker else None,
+                        "what": "(phi, T) pass + in-place step (two launches per step); frac from the "
+                                "algorithmic bytes of the two-grid step"})
+            da.close()
+            del da
+            torch.cuda.empty_cache()
+            aa.append(rec)
+
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -614,6 +656,7 @@ def main():
         "fp32_vs_fp64": fp64 and {"speedup": mlups / fp64["mlups"]},
         "error_vs_fp64": err,
         "sweep": sweep,
+        "aa_layout": aa,
         "final_diag": {"mass": diag_final["mass"], "level": diag_final["level"]},
         "clocks": clocks,
     }

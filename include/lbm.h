@@ -350,6 +350,41 @@ lbm_status lbm_adjoint_step(lbm_domain* dom, const double* lam_in_host, double* 
 lbm_status lbm_profile_steps(lbm_domain* dom, int enable);
 lbm_status lbm_profile_read(lbm_domain* dom, double* ms_total, int32_t* launches);
 
+/* Halo exchange of a decomposition into x slabs (Sec. 4.3: each slab holds
+ * its own columns plus halo columns that the neighbouring slabs refresh
+ * after every step).  A slab is a domain of its own (periodic in x, so its
+ * halo columns hold garbage after a step until they are refreshed); a step
+ * produces correct values wherever the step's dependencies (2 cells for the
+ * LB energy solvers, 5 for RK4) stay inside the slab.
+ *   lbm_halo_bytes:    bytes of the buffer for `width` columns: the stored
+ *                      populations of every PDF set direction (storage
+ *                      type), [direction (h, then g, then f)][z][y][width],
+ *                      then, 16-byte aligned, the RK temperature [z][y][width]
+ *                      (compute type); 0 for width outside [1, nx].
+ *   lbm_pack_halo_x:   copy columns [x0, x0 + width) of the current state
+ *                      into dst_dev (device memory, lbm_halo_bytes bytes).
+ *   lbm_unpack_halo_x: copy src_dev into columns [x0, x0 + width) of the
+ *                      current state (and refresh the tiled kernels'
+ *                      periodic ghost copies).
+ * Both are enqueued on the domain's stream (no synchronisation); moving the
+ * buffer between slabs (NCCL, peer copies, host staging) is the caller's.
+ * Errors: LBM_ERR_ARG (columns outside the lattice, null or non-device
+ * buffer), LBM_ERR_STATE (not initialised), LBM_ERR_UNSUPPORTED (in-place
+ * layout). */
+/* Declare the domain an x slab of a larger lattice: local column x is global
+ * column (x + x_offset) mod nx_global for every position-dependent term
+ * (heat sources, heater patches, the background gradient, the modulated
+ * bottom wall, droplets of lbm_init_droplets, the first moments of
+ * lbm_diag), so that a slab with halo columns computes exactly what the
+ * whole lattice computes in its own columns.  (0, nx) restores a whole
+ * lattice.  LBM_ERR_ARG for nx_global < nx; LBM_ERR_UNSUPPORTED for the
+ * in-place layout; the adjoint rejects sub-domains. */
+lbm_status lbm_set_subdomain(lbm_domain* dom, int x_offset, int nx_global);
+
+size_t lbm_halo_bytes(lbm_domain* dom, int width);
+lbm_status lbm_pack_halo_x(lbm_domain* dom, int x0, int width, void* dst_dev);
+lbm_status lbm_unpack_halo_x(lbm_domain* dom, int x0, int width, const void* src_dev);
+
 /* FP64 mass and first moments of a caller-owned device field, computed
  * without allocating any memory.  The paper has no counterpart: this is a
  * utility of the library (the phi mass and centroid moments of lbm_diag, for

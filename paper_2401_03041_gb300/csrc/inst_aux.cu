@@ -73,6 +73,15 @@ void launch_aa_convert(const DevParams& P, int Q, bool to_f64, void* pdf, double
 }
 
 template <class S>
+void launch_halo_x(const DevParams& P, S* set, int nq, typename Store<S>::R* T, int x0, int w, void* buf,
+                   size_t t_off, bool to_buf, cudaStream_t st) {
+  const long long total = (long long)(nq + (T ? 1 : 0)) * P.nz * P.ny * w;
+  const long long blocks = (total + 255) / 256;
+  const int grid = (int)(blocks < 152 * 64 ? blocks : 152 * 64);
+  halo_x_kernel<S><<<grid, 256, 0, st>>>(P, set, nq, T, x0, w, (unsigned char*)buf, t_off, to_buf ? 1 : 0);
+}
+
+template <class S>
 void launch_ghost_fill(const DevParams& P, void* buf, int nq, cudaStream_t st) {
   constexpr int V = 16 / (int)sizeof(S);
   const int per_plane = P.NYP + 2 * P.GY * ((P.nx + V - 1) / V);
@@ -174,6 +183,12 @@ template void launch_aa_swap<__half>(const DevParams&, int, __half*, cudaStream_
 template void launch_aa_convert<double>(const DevParams&, int, bool, void*, double*, double, int, cudaStream_t);
 template void launch_aa_convert<float>(const DevParams&, int, bool, void*, double*, double, int, cudaStream_t);
 template void launch_aa_convert<__half>(const DevParams&, int, bool, void*, double*, double, int, cudaStream_t);
+template void launch_halo_x<double>(const DevParams&, double*, int, double*, int, int, void*, size_t, bool,
+                                    cudaStream_t);
+template void launch_halo_x<float>(const DevParams&, float*, int, float*, int, int, void*, size_t, bool,
+                                   cudaStream_t);
+template void launch_halo_x<__half>(const DevParams&, __half*, int, float*, int, int, void*, size_t, bool,
+                                    cudaStream_t);
 template void launch_ghost_fill<double>(const DevParams&, void*, int, cudaStream_t);
 template void launch_ghost_fill<float>(const DevParams&, void*, int, cudaStream_t);
 template void launch_ghost_fill<__half>(const DevParams&, void*, int, cudaStream_t);

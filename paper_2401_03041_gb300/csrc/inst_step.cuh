@@ -29,7 +29,7 @@ void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                                (int)sbytes);
           sattr_set = true;
         }
-        if (P.alpha_ratio || P.tw_waves || P.wall_ext)
+        if (P.alpha_ratio || P.tw_waves || P.wall_ext || P.sub)
           step_skew_kernel<S, QH, QF, true><<<bgrid, SkewSmem<S, QH, QF>::G::NTHR, sbytes, st>>>(
               P, A, maps.h, maps.g, maps.f, sched, mode);
         else
@@ -47,7 +47,7 @@ void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                              (int)bytes);
         attr_set = true;
       }
-      if (P.alpha_ratio || P.tw_waves || P.rho_ratio || P.wall_ext)
+      if (P.alpha_ratio || P.tw_waves || P.rho_ratio || P.wall_ext || P.sub)
         step_bulk_kernel<S, QH, QF, true><<<bgrid, BulkSmem<S, QH, QF>::G::NTHR, bytes, st>>>(
             P, A, maps.h, maps.g, maps.f, sched, mode);
       else

@@ -49,6 +49,11 @@ template <class S>
 void launch_aa_convert(const DevParams& P, int Q, bool to_f64, void* pdf, double* f64, double shift,
                        int odd_level, cudaStream_t st);
 
+// Slab halo columns <-> contiguous buffer (see halo_x_kernel).
+template <class S>
+void launch_halo_x(const DevParams& P, S* set, int nq, typename Store<S>::R* T, int x0, int w, void* buf,
+                   size_t t_off, bool to_buf, cudaStream_t st);
+
 template <class S, int QH, int QF>
 void launch_init(const DevParams& P, const double* drops, int nd, S* h, S* g, S* f,
                  typename Store<S>::R* T, cudaStream_t st);

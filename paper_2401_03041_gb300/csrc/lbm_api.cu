@@ -1147,6 +1147,71 @@ lbm_status lbm_stencil(int Q, int32_t* c_out, double* w_out) {
   return LBM_OK;
 }
 
+// ---------------------------------------------------------------- slab halos
+
+lbm_status lbm_set_subdomain(lbm_domain* d, int x_offset, int nx_global) {
+  lbm_status s = usable(d);
+  if (s != LBM_OK) return s;
+  if (nx_global < d->nx) return fail(LBM_ERR_ARG, "nx_global must be >= nx");
+  if (d->aa) return fail(LBM_ERR_UNSUPPORTED, "sub-domains are built for the two-grid layout");
+  const bool plain = x_offset == 0 && nx_global == d->nx;
+  d->dp.sub = plain ? 0 : 1;
+  d->dp.sub_x0 = x_offset;
+  d->dp.gnx = nx_global;
+  return LBM_OK;
+}
+
+static size_t halo_pdf_bytes(const lbm_domain* d, int width) {
+  return (size_t)(d->qh + 27 + d->qf) * d->nz * d->ny * (size_t)width * store_bytes(d->prec);
+}
+
+size_t lbm_halo_bytes(lbm_domain* d, int width) {
+  if (!d || width < 1 || width > d->nx) return 0;
+  const size_t pdf = (halo_pdf_bytes(d, width) + 15) & ~size_t(15);
+  return pdf + (d->qf == 0 ? (size_t)d->nz * d->ny * width * field_bytes(d->prec) : 0);
+}
+
+static lbm_status halo_io(lbm_domain* d, int x0, int width, void* buf, bool to_buf) {
+  lbm_status s = usable(d);
+  if (s != LBM_OK) return s;
+  if (!buf) return fail(LBM_ERR_ARG, "buffer is null");
+  if (width < 1 || x0 < 0 || x0 + width > d->nx) return fail(LBM_ERR_ARG, "columns outside the lattice");
+  if (d->aa) return fail(LBM_ERR_UNSUPPORTED, "halo exchange is built for the two-grid layout");
+  if (!d->inited) return fail(LBM_ERR_STATE, "domain not initialised");
+  cudaPointerAttributes pa{};
+  if (cudaPointerGetAttributes(&pa, buf) != cudaSuccess ||
+      (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)) {
+    cudaGetLastError();
+    return fail(LBM_ERR_ARG, "halo buffer must be device memory");
+  }
+  const size_t t_off = (halo_pdf_bytes(d, width) + 15) & ~size_t(15);
+  const int nq = d->qh + 27 + d->qf;
+  auto go = [&](auto tag) {
+    using S = decltype(tag);
+    using R = typename Store<S>::R;
+    launch_halo_x<S>(d->dp, (S*)cur_set_ptr(d), nq, d->qf == 0 ? (R*)at(d, d->L.T) : nullptr, x0, width, buf,
+                     t_off, to_buf, d->stream);
+  };
+  if (d->prec == LBM_FP64) go(double{});
+  else if (d->prec == LBM_FP32) go(float{});
+  else go(__half{});
+  s = check_launch(d, "halo kernel");
+  // the tiled kernels read periodic ghost copies of the edge columns
+  if (s == LBM_OK && !to_buf) {
+    ghost_fill(d, d->cur);
+    s = check_launch(d, "ghost fill");
+  }
+  return s;
+}
+
+lbm_status lbm_pack_halo_x(lbm_domain* d, int x0, int width, void* dst_dev) {
+  return halo_io(d, x0, width, dst_dev, true);
+}
+
+lbm_status lbm_unpack_halo_x(lbm_domain* d, int x0, int width, const void* src_dev) {
+  return halo_io(d, x0, width, const_cast<void*>(src_dev), false);
+}
+
 lbm_status lbm_kernel_info(lbm_domain* d, int32_t* info) {
   if (!d || !info) return fail(LBM_ERR_ARG, "null argument");
   info[0] = d->aa ? 3 : d->geo.bulk;
@@ -1246,6 +1311,7 @@ lbm_status adj_check(lbm_domain* d) {
   if (d->dp.wall_ext)
     return fail(LBM_ERR_UNSUPPORTED, "the adjoint is built for walls at rest with neutral wetting");
   if (d->aa) return fail(LBM_ERR_UNSUPPORTED, "the adjoint is built for the two-grid layout");
+  if (d->dp.sub) return fail(LBM_ERR_UNSUPPORTED, "the adjoint is built for whole lattices");
   if ((long long)d->nx * d->ny >= (1LL << 31))
     return fail(LBM_ERR_UNSUPPORTED, "the adjoint needs nx * ny < 2^31");
   return LBM_OK;

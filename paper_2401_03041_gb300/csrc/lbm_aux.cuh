@@ -24,14 +24,21 @@ __device__ __forceinline__ RF stage_at(const DevParams& P, const RF* __restrict_
 }
 
 // phi at (x+dx, y+dy, z+dz): periodic in x, y (and z without walls); beyond a
-// wall the mirror ghost phi(first cell).
+// wall the mirror ghost phi(first cell), or the contact-angle ghost.
 template <class RF>
 __device__ __forceinline__ RF phi_at(const DevParams& P, const RF* __restrict__ phi, int x, int y, int z,
                                      int dx, int dy, int dz) {
   const int xx = wrap(x + dx, P.nx), yy = wrap(y + dy, P.ny);
   int zz = z + dz;
-  if (P.walls) zz = zz < 0 ? 0 : (zz >= P.nz ? P.nz - 1 : zz);
-  else zz = wrap(zz, P.nz);
+  if (P.walls) {
+    if (zz < 0 || zz >= P.nz) {
+      const int top = zz >= P.nz ? 1 : 0;
+      const RF a = phi[cell_index(P, xx, yy, top ? P.nz - 1 : 0)];
+      return P.wetting ? wet_ghost<RF>(a, wall_k<RF>(P, top)) : a;
+    }
+  } else {
+    zz = wrap(zz, P.nz);
+  }
   return phi[cell_index(P, xx, yy, zz)];
 }
 
@@ -186,7 +193,9 @@ init_kernel(const DevParams P, const double* __restrict__ drops, int nd, S* h, S
     for (int j = tid; j < 1024; j += NT) {   // every warp takes whole 32-droplet words
       const int k = k0 + j;
       bool near = false;
-      if (k < nd) {
+      if (k < nd && P.sub) {
+        near = true;   // sub-domain: no culling (the tile box is in local columns)
+      } else if (k < nd) {
         const double* d = drops + 7 * k;
         double dx = bcx - d[0], dy = bcy - d[1], dz = bcz - d[2];
         dx = min_image(dx, P.nx);
@@ -207,8 +216,8 @@ init_kernel(const DevParams P, const double* __restrict__ drops, int nd, S* h, S
         for (uint32_t m = mask[wd]; m; m &= m - 1) {
           const int k = k0 + wd * 32 + __ffs(m) - 1;
           const double* d = drops + 7 * k;
-          double dx = x + 0.5 - d[0], dy = y + 0.5 - d[1], dz = z + 0.5 - d[2];
-          dx = min_image(dx, P.nx);
+          double dx = global_x(P, x) + 0.5 - d[0], dy = y + 0.5 - d[1], dz = z + 0.5 - d[2];
+          dx = min_image(dx, P.sub ? P.gnx : P.nx);
           dy = min_image(dy, P.ny);
           if (!P.walls) dz = min_image(dz, P.nz);
           const double r = sqrt(dx * dx + dy * dy + dz * dz);
@@ -370,6 +379,37 @@ static __global__ void diag_finalize_kernel(const double* __restrict__ partials,
     }
     if (threadIdx.x == 0) out[k] = s[0];
     __syncthreads();
+  }
+}
+
+// Halo exchange of an x-slab decomposition: columns [x0, x0 + w) of every
+// row, for the nq directions of one padded PDF set (stride Np, stored
+// values) and, if T is given, of the dense RK temperature field, to / from
+// a contiguous buffer [direction][z][y][w] followed (16-byte aligned) by
+// T [z][y][w].
+template <class S>
+__global__ void halo_x_kernel(const DevParams P, S* __restrict__ set, int nq, typename Store<S>::R* __restrict__ T,
+                              int x0, int w, unsigned char* __restrict__ buf, size_t t_off, int to_buf) {
+  using R = typename Store<S>::R;
+  const size_t plane = (size_t)P.nz * P.ny * w;
+  const size_t npdf = (size_t)nq * plane;
+  const size_t total = npdf + (T ? plane : 0);
+  S* pb = reinterpret_cast<S*>(buf);
+  R* tb = reinterpret_cast<R*>(buf + t_off);
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = k < npdf ? k % plane : k - npdf;
+    const int xx = (int)(r % w), y = (int)((r / w) % P.ny), z = (int)(r / ((size_t)w * P.ny));
+    const int x = x0 + xx;
+    if (k < npdf) {
+      const int i = (int)(k / plane);
+      S* at = set + (size_t)i * P.Np + pdf_index(P, x, y, z);
+      if (to_buf) pb[k] = *at;
+      else *at = pb[k];
+    } else {
+      R* at = T + ((size_t)z * P.ny + y) * P.nx + x;
+      if (to_buf) tb[r] = *at;
+      else *at = tb[r];
+    }
   }
 }
 

@@ -564,7 +564,7 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
           if (mode & MODE_SAVE) save_stencil<S>(P, A, cell, cen.x, cen.y, fd);
           // a4-a5 need nothing from the g role: the force is computed here,
           // once, and only phi and a go across
-          F = cell_force<R>(P, x, y, z, cen.x, cen.y, fd.gpx, fd.gpy, fd.gpz, fd.lp, fd.gtx, fd.gty, fd.gtz);
+          F = cell_force<R, EXT>(P, x, y, z, cen.x, cen.y, fd.gpx, fd.gpy, fd.gpz, fd.lp, fd.gtx, fd.gty, fd.gtz);
           xch[cidx] = cen.x;
           xch[NC + cidx] = F.ax;
           xch[2 * NC + cidx] = F.ay;

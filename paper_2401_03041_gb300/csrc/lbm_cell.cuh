@@ -45,8 +45,9 @@ template <class R>
 __device__ __forceinline__ R heat_source(const DevParams& P, int x, int y, int z) {
   const auto& rp = RP<R>(P);
   R q = 0;
+  const int xg = global_x(P, x);
   for (int k = 0; k < P.nsrc; ++k) {
-    const R dx = (R)x + (R)0.5 - (R)rp.src[k][0];
+    const R dx = (R)xg + (R)0.5 - (R)rp.src[k][0];
     const R dy = (R)y + (R)0.5 - (R)rp.src[k][1];
     const R dz = (R)z + (R)0.5 - (R)rp.src[k][2];
     const R r2 = dx * dx + dy * dy + dz * dz;
@@ -55,7 +56,7 @@ __device__ __forceinline__ R heat_source(const DevParams& P, int x, int y, int z
   }
   if (P.npatch > 0 && z == P.patch_z) {
     for (int k = 0; k < P.npatch; ++k) {
-      if (x >= P.px0[k] && x < P.px0[k] + P.patch_sx && y >= P.py0[k] && y < P.py0[k] + P.patch_sy)
+      if (xg >= P.px0[k] && xg < P.px0[k] + P.patch_sx && y >= P.py0[k] && y < P.py0[k] + P.patch_sy)
         q += (R)rp.pI[k];
     }
   }
@@ -297,12 +298,15 @@ struct CellForce {
   R ax, ay, az, rho;
 };
 
-template <class R>
+// GX: positions may be those of a sub-domain (global_x); the tiled kernels'
+// builds without the extensions pass false.
+template <class R, bool GX = true>
 __device__ __forceinline__ CellForce<R> cell_force(const DevParams& P, int x, int y, int z, R phi, R Tc,
                                                    R gpx, R gpy, R gpz, R lp, R gtx, R gty, R gtz) {
   const auto& rp = RP<R>(P);
   const Derived<R> dv = derived<R>(P);
   const R Gx = (R)rp.grad[0], Gy = (R)rp.grad[1], Gz = (R)rp.grad[2];
+  if constexpr (GX) x = global_x(P, x);
   const R Ttot = Tc + Gx * ((R)x + (R)0.5 - (R)rp.origin[0]) + Gy * ((R)y + (R)0.5 - (R)rp.origin[1]) +
                  Gz * ((R)z + (R)0.5 - (R)rp.origin[2]);
   const R gTx = gtx + Gx, gTy = gty + Gy, gTz = gtz + Gz;
@@ -393,7 +397,7 @@ __device__ __forceinline__ void cell_outputs(const DevParams& P, const StepPtrs<
     dsum[0] += dphi;
     dsum[1] += (double)Tc;
     dsum[2] += 0.5 * (double)f.rho * (double)f.uu;
-    dsum[3] += dphi * (x + 0.5);
+    dsum[3] += dphi * (global_x(P, x) + 0.5);
     dsum[4] += dphi * (y + 0.5);
     dsum[5] += dphi * (z + 0.5);
     if (!isfinite(dphi) || !isfinite((double)Tc) || !isfinite((double)f.uu)) dsum[6] += 1.0;

@@ -158,7 +158,18 @@ struct DevParams {
   int wall_ext, moving_walls, wetting;
   double uw_d[2][2], kw_d[2];
   float uw_f[2][2], kw_f[2];
+  // Sub-domain (a slab of a larger lattice): local column x is global column
+  // (x + sub_x0) mod gnx for every position-dependent term.
+  int sub, sub_x0, gnx;
 };
+
+// Global column of local column x (positions of sources, patches, the
+// background gradient, the modulated wall, droplets, first moments).
+__host__ __device__ __forceinline__ int global_x(const DevParams& P, int x) {
+  if (!P.sub) return x;
+  int g = (x + P.sub_x0) % P.gnx;
+  return g < 0 ? g + P.gnx : g;
+}
 
 template <class R> __host__ __device__ __forceinline__ const RealParams<R>& RP(const DevParams& P);
 template <> __host__ __device__ __forceinline__ const RealParams<double>& RP<double>(const DevParams& P) { return P.pd; }
@@ -191,7 +202,8 @@ __device__ __forceinline__ R wall_T(const DevParams& P, int x, bool bottom) {
   const auto& rp = RP<R>(P);
   if (!bottom) return (R)rp.T_top;
   R t = (R)rp.T_bottom;
-  if (P.tw_waves) t += t_amp_of<R>(P) * cos_pi((R)(2 * P.tw_waves) * ((R)x + (R)0.5) / (R)P.nx);
+  if (P.tw_waves)
+    t += t_amp_of<R>(P) * cos_pi((R)(2 * P.tw_waves) * ((R)global_x(P, x) + (R)0.5) / (R)(P.sub ? P.gnx : P.nx));
   return t;
 }
 

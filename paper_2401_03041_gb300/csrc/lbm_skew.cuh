@@ -216,7 +216,7 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     }
     const size_t cell = cell_index(P, x, y, p);
     if (mode & MODE_SAVE) save_stencil<S>(P, A, cell, cen.x, cen.y, fd);
-    F = cell_force<R>(P, x, y, p, cen.x, cen.y, fd.gpx, fd.gpy, fd.gpz, fd.lp, fd.gtx, fd.gty, fd.gtz);
+    F = cell_force<R, EXT>(P, x, y, p, cen.x, cen.y, fd.gpx, fd.gpy, fd.gpz, fd.lp, fd.gtx, fd.gty, fd.gtz);
     *xb(p, 0) = cen.x;
     *xb(p, 1) = F.ax;
     *xb(p, 2) = F.ay;

@@ -25,6 +25,7 @@ LAYOUT = {"two_grid": 0, "aa": 1}
 # Every symbol include/lbm.h declares.
 SYMBOLS = ("lbm_default_params", "lbm_workspace_bytes", "lbm_create_domain",
            "lbm_workspace_bytes_layout", "lbm_create_domain_layout",
+           "lbm_halo_bytes", "lbm_pack_halo_x", "lbm_unpack_halo_x", "lbm_set_subdomain",
            "lbm_destroy_domain", "lbm_set_params", "lbm_set_heat_sources",
            "lbm_set_heater_patches", "lbm_set_heater_field", "lbm_init_droplets", "lbm_step",
            "lbm_step_diagnostics", "lbm_get_diagnostics", "lbm_get_fields",
@@ -105,6 +106,10 @@ def lib():
         "lbm_workspace_bytes": (sz, [c_int, c_int, c_int, c_int, c_int, c_int]),
         "lbm_create_domain": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int, vp, vp, sz, P(vp)]),
         "lbm_workspace_bytes_layout": (sz, [c_int, c_int, c_int, c_int, c_int, c_int, c_int]),
+        "lbm_halo_bytes": (sz, [vp, c_int]),
+        "lbm_set_subdomain": (c_int, [vp, c_int, c_int]),
+        "lbm_pack_halo_x": (c_int, [vp, c_int, c_int, vp]),
+        "lbm_unpack_halo_x": (c_int, [vp, c_int, c_int, vp]),
         "lbm_create_domain_layout": (c_int, [c_int, c_int, c_int, c_int, c_int, c_int, c_int, vp, vp, sz,
                                              P(vp)]),
         "lbm_destroy_domain": (c_int, [vp]),
@@ -356,6 +361,29 @@ class Domain:
                                                           ctypes.c_void_p(out.ctypes.data),
                                                           float(normal_cap)))
         return out
+
+    def set_subdomain(self, x_offset: int, nx_global: int):
+        """Local column x is global column (x + x_offset) mod nx_global."""
+        _check("lbm_set_subdomain", lib().lbm_set_subdomain(self._h, int(x_offset), int(nx_global)))
+
+    def halo_bytes(self, width: int) -> int:
+        """Bytes of the halo buffer of `width` columns (lbm_halo_bytes)."""
+        return int(lib().lbm_halo_bytes(self._h, int(width)))
+
+    def pack_halo_x(self, x0: int, width: int, buf):
+        """Columns [x0, x0 + width) of the current state into `buf` (a CUDA
+        uint8 tensor of halo_bytes(width) bytes), on the domain's stream."""
+        if not buf.is_cuda or buf.numel() * buf.element_size() < self.halo_bytes(width):
+            raise ValueError("halo buffer must be a CUDA tensor of halo_bytes(width) bytes")
+        _check("lbm_pack_halo_x", lib().lbm_pack_halo_x(self._h, int(x0), int(width),
+                                                        ctypes.c_void_p(buf.data_ptr())))
+
+    def unpack_halo_x(self, x0: int, width: int, buf):
+        """`buf` (as written by pack_halo_x) into columns [x0, x0 + width)."""
+        if not buf.is_cuda or buf.numel() * buf.element_size() < self.halo_bytes(width):
+            raise ValueError("halo buffer must be a CUDA tensor of halo_bytes(width) bytes")
+        _check("lbm_unpack_halo_x", lib().lbm_unpack_halo_x(self._h, int(x0), int(width),
+                                                            ctypes.c_void_p(buf.data_ptr())))
 
     def save_state(self) -> bytes:
         """The current state (PDFs, RK temperature, time level) as bytes."""

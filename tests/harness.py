@@ -21,14 +21,16 @@ def relerr(a, b, floor=1e-6):
 
 def gpu_domain(w: W.Workload, precision=None, kernel=None):
     """kernel: None (library's choice), 'generic' or 'bulk' (forced through
-    LBM_KERNEL) or 'skew' (asserted to be the library's choice)."""
+    LBM_KERNEL), 'skew' (asserted to be the library's choice) or 'aa' (the
+    in-place PDF layout)."""
     import os
     from paper_2401_03041_gb300 import lbm
     old = os.environ.pop("LBM_KERNEL", None)
     if kernel in ("generic", "bulk"):
         os.environ["LBM_KERNEL"] = kernel
     try:
-        d = lbm.Domain(w.nx, w.ny, w.nz, precision or w.precision, w.thermal, w.q_phase)
+        d = lbm.Domain(w.nx, w.ny, w.nz, precision or w.precision, w.thermal, w.q_phase,
+                       layout="aa" if kernel == "aa" else "two_grid")
     finally:
         os.environ.pop("LBM_KERNEL", None)
         if old is not None:

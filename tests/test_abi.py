@@ -106,3 +106,17 @@ def test_header_is_plain_c_and_usable_from_c(L, tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
+
+
+def test_in_place_layout_workspace_about_half():
+    """lbm_workspace_bytes_layout: the in-place (AA) layout holds one PDF set
+    plus a (phi, T) field, about half the two-grid workspace; the plain call
+    is the two-grid layout; an unknown layout gives 0."""
+    from paper_2401_03041_gb300 import lbm
+    L = lbm.lib()
+    for prec in (0, 1, 2):
+        two = L.lbm_workspace_bytes_layout(256, 256, 256, prec, 0, 15, 0)
+        aa = L.lbm_workspace_bytes_layout(256, 256, 256, prec, 0, 15, 1)
+        assert two == L.lbm_workspace_bytes(256, 256, 256, prec, 0, 15)
+        assert 0.45 * two < aa < 0.6 * two, (prec, aa / two)
+    assert L.lbm_workspace_bytes_layout(8, 8, 8, 1, 0, 15, 7) == 0

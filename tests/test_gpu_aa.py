@@ -1,0 +1,123 @@
+"""The in-place (AA-pattern) PDF layout: one PDF set per field, updated in
+place by alternating a gather-from-neighbours step and a local step, with a
+(phi, T) field of each level for the finite differences.
+
+FP64: equal to the generic two-grid kernel bit for bit (fields and the
+populations p_i(x) returned by lbm_get_pdfs, after an odd and an even number
+of steps) on workloads that exercise every wall rule and extension, and
+within 1e-11 of the oracle after 200 steps.  FP32 / FP16 storage: within the
+reduced-precision bounds of the tiled kernels.  Checkpoints resume bit for
+bit, the layout is recorded in the state, and the workspace is about half.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from harness import gpu_domain, gpu_fields, gpu_state_in_oracle_order, oracle_for, ragged_workload, relerr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_03041_gb300 import build
+    build.build()
+
+
+def _variant(name):
+    if name == "walls_moving_wetting":
+        w = ragged_workload("D3Q7", 15, walls=True)
+        return w.replace(params=W.Params(**dict(w.params.__dict__, wall_u_top=(0.02, -0.01),
+                                                wall_u_bottom=(-0.005, 0.01), theta_bottom=60.0,
+                                                theta_top=130.0)))
+    if name == "periodic_d3q19_q27":
+        return ragged_workload("D3Q19", 27, walls=False)
+    if name == "rk4_conductivity_ratio":
+        w = ragged_workload("RK4", 15, walls=True)
+        return w.replace(params=W.Params(**dict(w.params.__dict__, alpha_L=0.1, alpha_H=0.02)))
+    if name == "density_ratio_d3q15":
+        w = ragged_workload("D3Q15", 15, walls=True)
+        return w.replace(params=W.Params(**dict(w.params.__dict__, rho_L=1.0, rho_H=10.0)))
+    if name == "rk2_periodic_heaters":
+        return ragged_workload("RK2", 15, walls=False)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["walls_moving_wetting", "periodic_d3q19_q27", "rk4_conductivity_ratio",
+                                  "density_ratio_d3q15", "rk2_periodic_heaters"])
+def test_aa_equals_two_grid_bitwise_fp64(name):
+    w = _variant(name)
+    a = gpu_domain(w, kernel="aa")
+    b = gpu_domain(w, kernel="generic")
+    assert a.kernel_info()["kernel"] == "aa"
+    for steps in (7, 6):          # odd level 7, then even level 13
+        a.step(steps)
+        b.step(steps)
+        fa, fb = gpu_fields(a), gpu_fields(b)
+        for k in fa:
+            assert np.array_equal(fa[k], fb[k]), (name, k, a.level())
+        sa, sb = gpu_state_in_oracle_order(a, w), gpu_state_in_oracle_order(b, w)
+        for k in sa:
+            assert np.array_equal(sa[k], sb[k]), (name, k, a.level())
+    da, db = a.diagnostics(), b.diagnostics()
+    assert da["mass"] == db["mass"] and da["kinetic"] == db["kinetic"]
+
+
+def test_aa_fp64_200_steps_vs_oracle():
+    w = ragged_workload("D3Q7", 15, walls=True, shape=(40, 24, 16))
+    o = oracle_for(w)
+    o.step(200)
+    d = gpu_domain(w, kernel="aa")
+    d.step(200)
+    gf, om_ = gpu_fields(d), o.macro()
+    errs = {k: relerr(gf[k], om_[k]) for k in ("phi", "p", "T", "u")}
+    st, ost = gpu_state_in_oracle_order(d, w), o.state()
+    for k in st:
+        errs["pdf_" + k] = relerr(st[k], ost[k])
+    print("aa fp64 200 steps", {k: f"{v:.2e}" for k, v in errs.items()})
+    for k, v in errs.items():
+        assert v < 1e-11, (k, v)
+
+
+@pytest.mark.parametrize("precision,tol_phi", [("fp32", 1.1e-4), ("fp16", 5e-2)])
+def test_aa_reduced_precision_matches_two_grid(precision, tol_phi):
+    """Reduced-precision storage in the in-place layout: the same rounding of
+    the same stored values, so it equals the generic two-grid kernel in FP32
+    / FP16 storage to the last bit as well, and stays within the FP64
+    oracle's phi bound after 60 steps."""
+    w = ragged_workload("D3Q7", 15, walls=True, precision=precision, shape=(40, 20, 13))
+    a = gpu_domain(w, kernel="aa")
+    b = gpu_domain(w, kernel="generic")
+    a.step(60)
+    b.step(60)
+    fa, fb = gpu_fields(a), gpu_fields(b)
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), (precision, k)
+    o = oracle_for(w.replace(precision="fp64"))
+    o.step(60)
+    assert np.abs(fa["phi"] - o.macro()["phi"]).max() < tol_phi
+
+
+def test_aa_checkpoint_resume_and_layout_check():
+    from paper_2401_03041_gb300 import lbm
+    w = ragged_workload("D3Q15", 15, walls=True)
+    a = gpu_domain(w, kernel="aa")
+    a.step(5)                          # odd level
+    blob = a.save_state()
+    a.step(4)
+    ref = gpu_fields(a)
+    b = gpu_domain(w, kernel="aa")
+    b.load_state(blob)
+    assert b.level() == 5
+    b.step(4)
+    got = gpu_fields(b)
+    for k in ref:
+        assert np.array_equal(ref[k], got[k]), k
+    c = gpu_domain(w, kernel="generic")
+    with pytest.raises(lbm.LBMError):
+        c.load_state(blob)            # a state of the in-place layout
+    with pytest.raises(lbm.LBMError):
+        a.adjoint_run(2, 1, (0.0, 0.0, 0.0))
