@@ -31,6 +31,11 @@ def case_workload(name):
     raise KeyError(name)
 
 
+# FP64 slabs against the whole lattice: rounding only (observed <= 5e-16 of
+# the field's magnitude after the test's steps)
+TOL = 1e-12
+
+
 def state_names(w):
     return ["h", "g", "f"] if w.thermal.startswith("D3Q") else ["h", "g", "T"]
 
@@ -39,7 +44,7 @@ def run(rank, world, port, name, steps, out_path):
     import numpy as np
     import torch
     import torch.distributed as dist
-    from harness import gpu_domain, gpu_fields
+    from harness import gpu_domain, gpu_fields, relerr
     from paper_2401_03041_gb300 import lbm
 
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
@@ -93,11 +98,15 @@ def run(rank, world, port, name, steps, out_path):
         rf = gpu_fields(ref)
         for k in state_names(w):
             rf["pdf_" + k] = ref.get_pdfs(k)
+        # the slabs run the position-aware kernel variant and the whole
+        # lattice the default one: the compiler contracts their products into
+        # FMAs differently, so they agree to rounding, not bit for bit
         bad = []
         for key, v in rf.items():
             got = np.concatenate([g[key] for g in gathered], axis=-1)
-            if not np.array_equal(got, v):
-                bad.append((key, float(np.abs(got - v).max())))
+            e = relerr(got, v)
+            if not e <= TOL:
+                bad.append((key, e))
         with open(out_path, "w") as fh:
             fh.write("ok\n" if not bad else f"mismatch {bad}\n")
     dist.barrier()

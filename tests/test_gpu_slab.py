@@ -1,10 +1,11 @@
 """x-slab decomposition on the GPU (Sec. 4.3 ghost-layer exchange): two
 processes share cuda:0, each stepping one slab with halo columns that the
 library's pack / unpack kernels exchange after every step (carried through
-gloo on the host); the gathered slabs equal the whole-lattice run bit for
-bit (FP64; walls with a moving top wall and a contact angle, periodic RK4
-with its 5-column halo, and a wide lattice on the tiled kernel).  The
-kernels never wait on one another: every exchange is host-synchronised."""
+gloo on the host); the gathered slabs equal the whole-lattice run to
+rounding, within 1e-12 of each field's magnitude (FP64; walls with a moving
+top wall and a contact angle, periodic RK4 with its 5-column halo, and a wide
+lattice on the tiled kernel).  The kernels never wait on one another: every
+exchange is host-synchronised."""
 import os
 import socket
 import subprocess
