@@ -488,20 +488,42 @@ class OracleLBM:
         return Fp + Fmu
 
     # ------------------------------------------------------------ RK (a9')
-    def alpha(self, phi):
-        """Thermal diffusivity kappa / (rho c_p) interpolated linearly in phi
-        like kappa and c_p (Sec. 2.3), with rho c_p = 1: alpha_L at phi = 0,
-        alpha_H at phi = 1."""
+    def kappa(self, phi):
+        """Thermal conductivity, linear in phi (Sec. 2.3; the printed
+        kappa_H + phi (kappa_H - kappa_L) read as kappa_L at phi = 0 and
+        kappa_H at phi = 1)."""
         p = self.p
         return p.alpha_L + phi * (p.alpha_H - p.alpha_L)
 
+    def heat_capacity(self, phi):
+        """Volumetric heat capacity rho c_p of Eq. temperature, with rho and
+        c_p each linear in phi (Eq. rho(phi); Sec. 2.3 for c_p, read like
+        kappa)."""
+        p = self.p
+        return (p.rho_L + phi * (p.rho_H - p.rho_L)) * (p.cp_L + phi * (p.cp_H - p.cp_L))
+
+    def heat_capacity_slope(self, phi):
+        """d(rho c_p)/d phi."""
+        p = self.p
+        rho = p.rho_L + phi * (p.rho_H - p.rho_L)
+        cp = p.cp_L + phi * (p.cp_H - p.cp_L)
+        return (p.rho_H - p.rho_L) * cp + rho * (p.cp_H - p.cp_L)
+
+    def varying_heat_capacity(self):
+        p = self.p
+        return p.cp_H != p.cp_L or p.rho_H != p.rho_L
+
+    def alpha(self, phi):
+        """Thermal diffusivity kappa / (rho c_p) of a cell."""
+        return self.kappa(phi) / self.heat_capacity(phi)
+
     def rk_rhs(self, psi, u, phi):
         """R(T) = -u.(grad T + G) + alpha(phi) lap T
-                  + (alpha_H - alpha_L) grad phi . (grad T + G) + q_T
-        (Eq. temperature with rho c_p = 1: grad kappa . grad T_total plus
-        kappa lap T, where T_total = T + G.(x - x0) and lap of the linear
-        background is zero); standard 7-point / central operators, or the
-        isotropic D3Q27 ones, for T and phi alike (phi mirrored at walls)."""
+                  + (kappa_H - kappa_L) / (rho c_p) grad phi . (grad T + G) + q_T
+        (Eq. temperature: (grad kappa . grad T_total + kappa lap T) / (rho c_p),
+        where T_total = T + G.(x - x0) and lap of the linear background is
+        zero); standard 7-point / central operators, or the isotropic D3Q27
+        ones, for T and phi alike (phi mirrored at walls)."""
         p = self.p
         q = self._pad(psi, "dirichlet")
         qp = self._pad(phi, "mirror")
@@ -512,9 +534,10 @@ class OracleLBM:
         G = p.grad_T
         gt = [gr[k] + G[k] for k in range(3)]
         adv = u[0] * gt[0] + u[1] * gt[1] + u[2] * gt[2]
-        cond = self.alpha(phi) * lp
+        C = self.heat_capacity(phi)
+        cond = self.kappa(phi) / C * lp
         if p.alpha_H != p.alpha_L:
-            cond = cond + (p.alpha_H - p.alpha_L) * (gp[0] * gt[0] + gp[1] * gt[1] + gp[2] * gt[2])
+            cond = cond + (p.alpha_H - p.alpha_L) / C * (gp[0] * gt[0] + gp[1] * gt[1] + gp[2] * gt[2])
         return -adv + cond + self.q
 
     # ------------------------------------------------------------ step
@@ -563,13 +586,23 @@ class OracleLBM:
         G = p.grad_T
         uG = u[0] * G[0] + u[1] * G[1] + u[2] * G[2]
         if self.lb_thermal:
-            # per-cell rate from alpha(phi); the LB recovers div(alpha grad T),
-            # and the background part of T_total adds grad alpha . G
-            w_T = 1.0 / (0.5 + self.alpha(phi) / CS2)
+            # per-cell rate from alpha(phi) = kappa / (rho c_p); the LB
+            # recovers div(alpha grad T) = alpha lap T + grad alpha . grad T.
+            # Eq. temperature wants alpha lap T + grad kappa . (grad T + G) / C
+            # (C = rho c_p), and grad kappa / C - grad alpha = alpha grad C / C,
+            # so the source adds grad kappa . G / C and alpha (C' / C)
+            # grad phi . grad T (grad T without the background)
+            alpha = self.alpha(phi)
+            w_T = 1.0 / (0.5 + alpha / CS2)
             src = self.q - uG
+            gphi = m["gphi"]
             if p.alpha_H != p.alpha_L:
-                gphi = m["gphi"]
-                src = src + (p.alpha_H - p.alpha_L) * (gphi[0] * G[0] + gphi[1] * G[1] + gphi[2] * G[2])
+                src = src + (p.alpha_H - p.alpha_L) / self.heat_capacity(phi) * (
+                    gphi[0] * G[0] + gphi[1] * G[1] + gphi[2] * G[2])
+            if self.varying_heat_capacity():
+                gT = [m["gT"][k] - G[k] for k in range(3)]
+                src = src + alpha * self.heat_capacity_slope(phi) / self.heat_capacity(phi) * (
+                    gphi[0] * gT[0] + gphi[1] * gT[1] + gphi[2] * gT[2])
             feq = eq_scalar(m["T"], u, self.Sf)
             f_new = np.empty(fs.shape, dtype=np.result_type(fs, feq, src, w_T))
             for i in range(self.Sf.Q):

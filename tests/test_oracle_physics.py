@@ -425,6 +425,108 @@ def test_modulated_wall_conduction_closed_form(thermal, tol):
     assert np.abs(o.macro()["T"] - exact).max() < tol
 
 
+@pytest.mark.parametrize("thermal", ["D3Q7", "D3Q19", "RK4"])
+def test_heat_capacity_sets_diffusivity(thermal):
+    """Uniform rho = 2, c_p = 1.5 and kappa = 0.15 (Eq. temperature): the
+    diffusivity is kappa / (rho c_p) = 0.05, so a sine mode decays at
+    0.05 k^2 per step (LB, to 1 %) or by the exact RK4 amplification factor
+    of the 7-point Laplacian at that diffusivity; taking kappa itself as the
+    diffusivity would triple the rate."""
+    kap, rho, cp = 0.15, 2.0, 1.5
+    alpha = kap / (rho * cp)
+    o = make(32, 1, 1, thermal=thermal, alpha_L=kap, alpha_H=kap, rho_L=rho, rho_H=rho, cp_L=cp, cp_H=cp)
+    k = 2 * math.pi / 32
+    x = o.X
+    T0 = 1e-2 * np.sin(k * x)
+    set_fields(o, 0.0, T=T0)
+    if thermal == "RK4":
+        z = alpha * (2 * math.cos(k) - 2)
+        P = 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+        o.step(5)
+        assert np.abs(o.T - P ** 5 * T0).max() < 1e-15
+        return
+    o.step(10)
+    a0 = _amp(o.macro()["T"], x, k)
+    o.step(200)
+    a1 = _amp(o.macro()["T"], x, k)
+    rate = -math.log(a1 / a0) / 200
+    assert abs(rate / (alpha * k * k) - 1) < 0.01
+
+
+def _heat_capacity_steady_profile(nz, zc, xi, kL, kH, CL_of, q):
+    """Steady state of C dT/dt = d/dz (kappa dT/dz) + C q between walls at
+    T = 0 (faces z = 0 and z = nz), kappa and C functions of the tanh profile
+    phi(z): kappa T' = A - q F(z), F = int_0^z C, and T(nz) = 0 fixes A.
+    Also returns the profile of the model that drops the heat-capacity
+    gradient term, (alpha T')' = -q with alpha = kappa / C."""
+    from scipy.integrate import quad
+
+    def phi(z):
+        return 0.5 * (1 + math.tanh(2 * (z - zc) / xi))
+
+    def kap(z):
+        return kL + phi(z) * (kH - kL)
+
+    def C(z):
+        return CL_of(phi(z))
+
+    def F(z):
+        return quad(C, 0, z, points=[zc] if z > zc else None)[0]
+
+    def integ(fun, z):
+        return quad(fun, 0, z, points=[zc] if z > zc else None, limit=200)[0]
+
+    A = q * integ(lambda s: F(s) / kap(s), nz) / integ(lambda s: 1 / kap(s), nz)
+    B = q * integ(lambda s: s * C(s) / kap(s), nz) / integ(lambda s: C(s) / kap(s), nz)
+    zs = np.arange(nz) + 0.5
+    exact = np.array([integ(lambda s: (A - q * F(s)) / kap(s), z) for z in zs])
+    wrong = np.array([integ(lambda s: (B - q * s) * C(s) / kap(s), z) for z in zs])
+    return exact, wrong
+
+
+def _steady_heating_error(thermal, kw, scale=1):
+    nz, xi, zc, q = 16 * scale, 3.0 * scale, 8.0 * scale, 1e-3 / scale ** 2
+    kL, kH = 0.5, 0.25
+    o = make(1, 1, nz, thermal=thermal, alpha_L=kL, alpha_H=kH, xi=xi, sigma_ref=1e-4,
+             sigma_T=0.0, walls_z=True, T_bottom=0.0, T_top=0.0, **kw)
+    exact, wrong = _heat_capacity_steady_profile(nz, zc, xi, kL, kH, lambda ph: 1.0 + 2.0 * ph, q)
+    phi = 0.5 * (1 + np.tanh(2 * (o.Z - zc) / xi))
+    set_fields(o, phi, T=exact.reshape(nz, 1, 1))
+    o.add_heat_field(np.full(nz, q))
+    o.step(1500 * scale * scale)
+    T = o.macro()["T"][:, 0, 0]
+    peak = np.abs(exact).max()
+    assert np.abs(o.macro()["u"]).max() < 1e-6
+    return np.abs(T - exact).max() / peak, np.abs(wrong - exact).max() / peak
+
+
+@pytest.mark.parametrize("thermal,tol", [("D3Q7", 4e-2), ("D3Q27", 4e-2), ("RK4", 2e-2)])
+@pytest.mark.parametrize("ratio", ["cp", "rho"])
+def test_heat_capacity_ratio_steady_heating(thermal, tol, ratio):
+    """A planar diffuse interface (xi = 3) between walls at T = 0 sixteen
+    cells apart, uniform heating q of dT/dt, conductivity ratio 1/2 and a
+    heat-capacity ratio 3 carried by c_p (or by the density, Eq. rho(phi),
+    with c_p = 1): the steady state of Eq. temperature solves
+    (kappa T')' = -q rho c_p (closed form by quadrature).  The solvers reach
+    it to their discretisation error (measured 2.7 % of the peak for the
+    LB, 1.4 % for RK4, second order: see the next test); the model without
+    the grad(rho c_p) term of the LB source is off by 27 %."""
+    err, gap = _steady_heating_error(thermal, dict(cp_L=1.0, cp_H=3.0) if ratio == "cp"
+                                     else dict(rho_L=1.0, rho_H=3.0))
+    print(thermal, ratio, "steady error", err, "wrong model", gap)
+    assert gap > 0.25
+    assert err < tol
+
+
+def test_heat_capacity_steady_heating_second_order():
+    """The same problem at twice the resolution (interface width, distance
+    and heating scaled): the LB error falls by about 4."""
+    e1, _ = _steady_heating_error("D3Q7", dict(cp_L=1.0, cp_H=3.0))
+    e2, _ = _steady_heating_error("D3Q7", dict(cp_L=1.0, cp_H=3.0), scale=2)
+    print("steady heating error", e1, e2, e1 / e2)
+    assert 3.3 < e1 / e2 < 4.8
+
+
 def test_conductivity_ratio_lb_conserves_heat():
     """Periodic box at rest, alpha_H = alpha_L / 5 with a droplet-shaped phi:
     the per-cell relaxation rate leaves sum T unchanged (no sources)."""

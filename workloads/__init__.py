@@ -41,8 +41,8 @@ class Params:
     sigma_ref: float = 5e-3      # surface tension at T_ref
     sigma_T: float = -5e-4       # d sigma / d T
     T_ref: float = 0.0
-    alpha_L: float = 0.05        # thermal diffusivity kappa/(rho c_p), light phase
-    alpha_H: float = 0.05        # thermal diffusivity, heavy phase
+    alpha_L: float = 0.05        # thermal conductivity kappa, light phase (the diffusivity when rho c_p = 1)
+    alpha_H: float = 0.05        # thermal conductivity kappa, heavy phase
     gravity: tuple = (0.0, 0.0, 0.0)
     walls_z: bool = False        # no-slip walls at both z faces (x, y periodic)
     T_bottom: float = 0.0        # wall temperature at z = 0
@@ -58,6 +58,8 @@ class Params:
     wall_u_top: tuple = (0.0, 0.0)      # tangential (x, y) velocity of the top wall
     theta_bottom: float = 90.0   # contact angle at the bottom wall, degrees, through phi = 1
     theta_top: float = 90.0      # contact angle at the top wall
+    cp_L: float = 1.0            # specific heat capacity c_p, light phase
+    cp_H: float = 1.0            # specific heat capacity c_p, heavy phase
 
 
 @dataclass
