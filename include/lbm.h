@@ -89,18 +89,21 @@ typedef struct {
                               + phi (rho_H - rho_L).  With rho_L != rho_H the pressure and
                               viscous correction forces F_p = -p* c_s^2 (rho_H - rho_L) grad phi
                               and F_mu = nu (rho_H - rho_L) [grad u + grad u^T] . grad phi act
-                              (Sec. 2.2; strain from the non-equilibrium moments of g).  The
-                              energy equation keeps rho c_p = 1 (alpha_* are diffusivities).
-                              The adjoint needs rho_L == rho_H. */
+                              (Sec. 2.2; strain from the non-equilibrium moments of g).  rho
+                              also enters the heat capacity rho c_p of the energy equation
+                              (see cp_L, cp_H).  The adjoint needs rho_L == rho_H. */
   double mobility;         /* Allen-Cahn mobility M; omega_phi = 1 / (1/2 + M / c_s^2) */
   double xi;               /* interface width */
   double sigma_ref, sigma_T, T_ref;  /* sigma(T) = sigma_ref + sigma_T (T - T_ref) */
-  double alpha_L, alpha_H; /* thermal diffusivity kappa / (rho c_p) of the light / heavy phase,
-                              with rho c_p = 1: alpha(phi) = alpha_L + phi (alpha_H - alpha_L)
-                              (Sec. 2.3, kappa linear in phi).  LB: per-cell rate
-                              omega_T = 1 / (1/2 + alpha(phi) / c_s^2); RK: alpha(phi) lap T
-                              + (alpha_H - alpha_L) grad phi . grad T_total.  The adjoint
-                              needs alpha_L == alpha_H. */
+  double alpha_L, alpha_H; /* thermal conductivity kappa of the light / heavy phase,
+                              kappa(phi) = alpha_L + phi (alpha_H - alpha_L) (Sec. 2.3); the
+                              diffusivity is alpha = kappa / C with C = rho(phi) c_p(phi) (equal
+                              to kappa at the default rho = c_p = 1).  Eq. temperature:
+                              dT/dt = -u.grad T_total + alpha lap T + (grad kappa / C)
+                              . grad T_total + q_T.  LB: per-cell rate omega_T = 1 / (1/2 +
+                              alpha / c_s^2), source (grad kappa / C) . G + alpha (C' / C)
+                              grad phi . grad T; RK: the right-hand side as written.  The
+                              adjoint needs a constant alpha (kappa and C uniform). */
   double gravity[3];       /* body-force acceleration g (F_b = rho g) */
   int32_t walls_z;         /* 1: no-slip walls at both z faces, else periodic in z */
   double T_bottom, T_top;  /* wall temperatures (walls_z == 1) */
@@ -122,6 +125,8 @@ typedef struct {
   double theta_top;        /* top wall, 0 < theta < 180 (Sec. 3.3 wetting condition): the ghost
                               phi beyond the wall solves (a - g) = -(4 / xi) cos(theta) w (1 - w),
                               w = (a + g) / 2, a the first fluid cell; 90 = neutral (mirror) */
+  double cp_L, cp_H;       /* specific heat capacity of the light / heavy phase, c_p(phi) =
+                              cp_L + phi (cp_H - cp_L) (Sec. 2.3); > 0, default 1 */
 } lbm_params;
 
 /* Gaussian laser heat source, Eq. HeatSource: q = Q exp(-2 r^2 / w^2) where

@@ -452,15 +452,21 @@ bool finite_all(const double* v, int n) {
   return true;
 }
 
+// rho c_p of the light phase; the constant heat capacity when neither rho nor
+// c_p differs between the phases (1 at the defaults, so alpha = kappa).
+double heat_capacity_L(const lbm_params& p) { return p.rho_L * p.cp_L; }
+bool varying_heat_capacity(const lbm_params& p) { return p.rho_L != p.rho_H || p.cp_L != p.cp_H; }
+
 template <class R>
 void fill_real(RealParams<R>& r, const lbm_params& p, lbm_precision prec) {
   const double cs2 = 1.0 / 3.0;
+  const double alpha_L = p.alpha_L / heat_capacity_L(p);
   r.omega_phi = (R)(1.0 / (0.5 + p.mobility / cs2));
-  r.omega_T = (R)(1.0 / (0.5 + p.alpha_L / cs2));
+  r.omega_T = (R)(1.0 / (0.5 + alpha_L / cs2));
   r.tau_L = (R)(p.nu_L / cs2 + 0.5);
   r.tau_H = (R)(p.nu_H / cs2 + 0.5);
   r.rho_L = (R)p.rho_L; r.rho_H = (R)p.rho_H; r.xi = (R)p.xi;
-  r.sigma_ref = (R)p.sigma_ref; r.sigma_T = (R)p.sigma_T; r.T_ref = (R)p.T_ref; r.alpha = (R)p.alpha_L;
+  r.sigma_ref = (R)p.sigma_ref; r.sigma_T = (R)p.sigma_T; r.T_ref = (R)p.T_ref; r.alpha = (R)alpha_L;
 
   for (int k = 0; k < 3; ++k) {
     r.gravity[k] = (R)p.gravity[k];
@@ -482,10 +488,18 @@ void refresh_devparams(lbm_domain* d) {
   q.GX = pd.GX; q.GY = pd.GY; q.NXP = pd.NXP; q.NYP = pd.NYP; q.Np = (long long)pd.Np;
   q.walls = p.walls_z ? 1 : 0;
   q.rk_iso = p.rk_isotropic_fd ? 1 : 0;
-  q.alpha_ratio = p.alpha_H != p.alpha_L ? 1 : 0;
+  q.heat_cap = varying_heat_capacity(p) ? 1 : 0;
+  q.alpha_ratio = (p.alpha_H != p.alpha_L || q.heat_cap) ? 1 : 0;
   q.tw_waves = p.T_bottom_amp != 0.0 ? p.T_bottom_waves : 0;
-  q.dalpha_d = p.alpha_H - p.alpha_L;
-  q.dalpha_f = (float)(p.alpha_H - p.alpha_L);
+  q.dalpha_d = (p.alpha_H - p.alpha_L) / heat_capacity_L(p);
+  q.dalpha_f = (float)q.dalpha_d;
+  {
+    const double hc[6] = {p.alpha_L, p.alpha_H - p.alpha_L, p.rho_L, p.rho_H - p.rho_L, p.cp_L, p.cp_H - p.cp_L};
+    for (int k = 0; k < 6; ++k) {
+      q.hc_d[k] = hc[k];
+      q.hc_f[k] = (float)hc[k];
+    }
+  }
   q.T_bottom_amp_d = p.T_bottom_amp;
   q.T_bottom_amp_f = (float)p.T_bottom_amp;
   q.test_stall = d->test_stall;
@@ -595,6 +609,7 @@ void lbm_default_params(lbm_params* p) {
   p->eps_n = 1e-12;
   p->theta_bottom = p->theta_top = 90.0;
   p->omega_high = 1.0;
+  p->cp_L = p->cp_H = 1.0;
 }
 
 size_t lbm_workspace_bytes_layout(int nx, int ny, int nz, lbm_precision prec, lbm_thermal thermal,
@@ -707,13 +722,14 @@ lbm_status lbm_set_params(lbm_domain* d, const lbm_params* p) {
                          p->sigma_T, p->T_ref, p->alpha_L, p->alpha_H, p->gravity[0], p->gravity[1],
                          p->gravity[2], p->T_bottom, p->T_top, p->grad_T[0], p->grad_T[1],
                          p->grad_T[2], p->grad_T_origin[0], p->grad_T_origin[1],
-                         p->grad_T_origin[2], p->eps_n, p->omega_high, p->T_bottom_amp};
+                         p->grad_T_origin[2], p->eps_n, p->omega_high, p->T_bottom_amp, p->cp_L, p->cp_H};
   if (!finite_all(vals, (int)(sizeof(vals) / sizeof(vals[0]))))
     return fail(LBM_ERR_ARG, "non-finite parameter");
   if (p->nu_L <= 0 || p->nu_H <= 0) return fail(LBM_ERR_ARG, "viscosity must be > 0");
   if (p->mobility <= 0) return fail(LBM_ERR_ARG, "mobility must be > 0");
   if (p->xi <= 0) return fail(LBM_ERR_ARG, "interface width must be > 0");
-  if (p->alpha_L <= 0 || p->alpha_H <= 0) return fail(LBM_ERR_ARG, "diffusivity must be > 0");
+  if (p->alpha_L <= 0 || p->alpha_H <= 0) return fail(LBM_ERR_ARG, "conductivity must be > 0");
+  if (p->cp_L <= 0 || p->cp_H <= 0) return fail(LBM_ERR_ARG, "heat capacity must be > 0");
   if (p->rho_L <= 0 || p->rho_H <= 0) return fail(LBM_ERR_ARG, "density must be > 0");
   if (p->eps_n < 0) return fail(LBM_ERR_ARG, "eps_n must be >= 0");
   if (p->T_bottom_waves < 0) return fail(LBM_ERR_ARG, "T_bottom_waves must be >= 0");
@@ -1303,9 +1319,9 @@ lbm_status adj_check(lbm_domain* d) {
   if (s != LBM_OK) return s;
   if (!d->inited) return fail(LBM_ERR_STATE, "domain not initialised");
   if (d->prec != LBM_FP64 || !adj_supported(d->qh, d->qf))
-    return fail(LBM_ERR_UNSUPPORTED, "the adjoint needs FP64 storage and the D3Q7 thermal LB");
+    return fail(LBM_ERR_UNSUPPORTED, "the adjoint needs FP64 storage and a thermal LB (D3Q7/15/19/27)");
   if (d->dp.alpha_ratio)
-    return fail(LBM_ERR_UNSUPPORTED, "the adjoint is built for equal diffusivities (alpha_L == alpha_H)");
+    return fail(LBM_ERR_UNSUPPORTED, "the adjoint is built for a uniform diffusivity (kappa and rho c_p equal in both phases)");
   if (d->dp.rho_ratio)
     return fail(LBM_ERR_UNSUPPORTED, "the adjoint is built for equal densities (rho_L == rho_H)");
   if (d->dp.wall_ext)

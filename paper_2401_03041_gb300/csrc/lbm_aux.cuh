@@ -71,8 +71,8 @@ __device__ __forceinline__ void rk_phi_grad(const DevParams& P, const RF* __rest
 
 // R(psi) = -u.(grad psi + G) + alpha lap psi + q_T  (Eq. temperature, uniform
 // kappa and rho c_p); 7-point / central operators or the isotropic D3Q27 ones.
-// With a conductivity ratio (phi != null): alpha(phi) lap psi plus
-// (alpha_H - alpha_L) grad phi . (grad psi + G), phi of this step.
+// With a conductivity or heat-capacity ratio (phi != null): alpha(phi) lap psi
+// plus (kappa_H - kappa_L) / C(phi) grad phi . (grad psi + G), phi of this step.
 template <class RF>
 __device__ __forceinline__ RF rk_rhs(const DevParams& P, const RF* __restrict__ psi, const RF* u,
                                      const RF* __restrict__ phi, int x, int y, int z, size_t cell) {
@@ -109,9 +109,10 @@ __device__ __forceinline__ RF rk_rhs(const DevParams& P, const RF* __restrict__ 
   if (phi) {
     RF pgx, pgy, pgz;
     rk_phi_grad(P, phi, x, y, z, pgx, pgy, pgz);
-    return -(ux * (gx + (RF)rp.grad[0]) + uy * (gy + (RF)rp.grad[1]) + uz * (gz + (RF)rp.grad[2])) +
-           alpha_of<RF>(P, phi[cell]) * lap + heat_source<RF>(P, x, y, z) +
-           cond_cross<RF>(P, pgx, pgy, pgz, gx, gy, gz);
+    const ThermCoef<RF> tc = therm_coef<RF>(P, phi[cell]);
+    const RF Gx = (RF)rp.grad[0], Gy = (RF)rp.grad[1], Gz = (RF)rp.grad[2];
+    return -(ux * (gx + Gx) + uy * (gy + Gy) + uz * (gz + Gz)) + tc.alpha * lap + heat_source<RF>(P, x, y, z) +
+           tc.dk_C * (pgx * (gx + Gx) + pgy * (gy + Gy) + pgz * (gz + Gz));
   }
   return -(ux * (gx + (RF)rp.grad[0]) + uy * (gy + (RF)rp.grad[1]) + uz * (gz + (RF)rp.grad[2])) +
          (RF)rp.alpha * lap + heat_source<RF>(P, x, y, z);

@@ -71,22 +71,28 @@ __device__ __forceinline__ R heat_source(const DevParams& P, int x, int y, int z
 template <class R>
 __device__ __forceinline__ R basis_pick(int c, R z, R p, R m) { return c == 0 ? z : (c > 0 ? p : m); }
 
-// Conductivity ratio (Sec. 2.3, kappa and c_p linear in phi; rho c_p = 1 here):
-// alpha(phi) = alpha_L + phi (alpha_H - alpha_L).
+// Thermal coefficients of a cell (Eq. temperature; Sec. 2.3: kappa and c_p
+// linear in phi, rho linear in phi, C = rho c_p): the diffusivity
+// alpha = kappa / C, the conduction cross coefficient (kappa_H - kappa_L) / C
+// of grad phi . (grad T + G), and C' / C (d C / d phi over C).  With a
+// constant C the host has folded 1 / C into alpha and dalpha, and C' = 0.
 template <class R>
-__device__ __forceinline__ R alpha_of(const DevParams& P, R phi) {
-  const auto& rp = RP<R>(P);
-  return (R)rp.alpha + phi * dalpha_of<R>(P);
-}
+struct ThermCoef {
+  R alpha, dk_C, dC_C;
+};
 
-// The grad alpha term of the energy equation, (alpha_H - alpha_L) grad phi .
-// (grad T + G), from the solver's own gradient operators.  The LB recovers
-// div(alpha grad T) by itself and takes only the background part
-// (gT = 0 there).
 template <class R>
-__device__ __forceinline__ R cond_cross(const DevParams& P, R gpx, R gpy, R gpz, R gtx, R gty, R gtz) {
-  const auto& rp = RP<R>(P);
-  return dalpha_of<R>(P) * (gpx * (gtx + (R)rp.grad[0]) + gpy * (gty + (R)rp.grad[1]) + gpz * (gtz + (R)rp.grad[2]));
+__device__ __forceinline__ ThermCoef<R> therm_coef(const DevParams& P, R phi) {
+  if (!P.heat_cap) {
+    const auto& rp = RP<R>(P);
+    return {(R)rp.alpha + phi * dalpha_of<R>(P), dalpha_of<R>(P), (R)0};
+  }
+  const R* hc = hc_of<R>(P);
+  const R kap = hc[0] + phi * hc[1];
+  const R rho = hc[2] + phi * hc[3];
+  const R cp = hc[4] + phi * hc[5];
+  const R iC = (R)1 / (rho * cp);
+  return {kap * iC, hc[1] * iC, (hc[3] * cp + rho * hc[5]) * iC};
 }
 
 // c . v for a lattice velocity c with components in {-1, 0, 1} known at
@@ -544,12 +550,15 @@ __device__ __forceinline__ void collide_h(const DevParams& P, const StepPtrs<S, 
 }
 
 // a9 / a9': thermal LB collision, or RK stage 1 (QF = 0).  With a
-// conductivity ratio the LB relaxes at the cell's own rate
-// 1 / (1/2 + alpha(phi) / c_s^2) and adds the background part of the grad alpha
-// term as a source; RK stage 1 takes alpha(phi) lap T plus the whole grad alpha
-// term, with grad phi from its own operator (pgx.. central differences for the
-// 7-point set, the isotropic gradient otherwise).  RATIO = P.alpha_ratio,
-// resolved by the caller so that the equal-diffusivity path carries none of it.
+// conductivity or heat-capacity ratio the LB relaxes at the cell's own rate
+// 1 / (1/2 + alpha(phi) / c_s^2), which recovers div(alpha grad T); Eq.
+// temperature asks for alpha lap T + (grad kappa / C) . (grad T + G), so the
+// source adds (grad kappa / C) . G and (grad kappa / C - grad alpha) . grad T
+// = alpha (C' / C) grad phi . grad T (isotropic grad T).  RK stage 1 takes
+// alpha(phi) lap T plus the whole (grad kappa / C) . (grad T + G), with
+// grad phi from its own operator (pgx.. central differences for the 7-point
+// set, the isotropic gradient otherwise).  RATIO = P.alpha_ratio, resolved by
+// the caller so that the uniform-property path carries none of it.
 template <class S, int QF, bool RATIO, class GF, class PUT = StdPut>
 __device__ __forceinline__ void collide_f(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                                           int x, int y, int z, size_t cell, size_t pcell,
@@ -574,8 +583,10 @@ __device__ __forceinline__ void collide_f(const DevParams& P, const StepPtrs<S, 
     R om = (R)rp.omega_T;
     R qs = q - uG;
     if constexpr (RATIO) {
-      om = (R)1 / ((R)0.5 + (R)3 * alpha_of<R>(P, phi));
-      qs += cond_cross<R>(P, fdv.gpx, fdv.gpy, fdv.gpz, (R)0, (R)0, (R)0);
+      const ThermCoef<R> tc = therm_coef<R>(P, phi);
+      om = (R)1 / ((R)0.5 + (R)3 * tc.alpha);
+      qs += tc.dk_C * (fdv.gpx * Gx + fdv.gpy * Gy + fdv.gpz * Gz);
+      if (P.heat_cap) qs += tc.alpha * tc.dC_C * (fdv.gpx * fdv.gtx + fdv.gpy * fdv.gty + fdv.gpz * fdv.gtz);
     }
     // stored values throughout, as in collide_h (s = shift_f)
     const R sf = (R)rp.shift_f;
@@ -614,9 +625,10 @@ __device__ __forceinline__ void collide_f(const DevParams& P, const StepPtrs<S, 
     }
     R K1 = -(ux * (gx_ + Gx) + uy * (gy_ + Gy) + uz * (gz_ + Gz)) + (R)rp.alpha * lap + q;
     if constexpr (RATIO) {
-      K1 = -(ux * (gx_ + Gx) + uy * (gy_ + Gy) + uz * (gz_ + Gz)) + alpha_of<R>(P, phi) * lap + q;
-      K1 += P.rk_iso ? cond_cross<R>(P, fdv.gpx, fdv.gpy, fdv.gpz, gx_, gy_, gz_)
-                     : cond_cross<R>(P, pgx, pgy, pgz, gx_, gy_, gz_);
+      const ThermCoef<R> tc = therm_coef<R>(P, phi);
+      K1 = -(ux * (gx_ + Gx) + uy * (gy_ + Gy) + uz * (gz_ + Gz)) + tc.alpha * lap + q;
+      K1 += P.rk_iso ? tc.dk_C * (fdv.gpx * (gx_ + Gx) + fdv.gpy * (gy_ + Gy) + fdv.gpz * (gz_ + Gz))
+                     : tc.dk_C * (pgx * (gx_ + Gx) + pgy * (gy_ + Gy) + pgz * (gz_ + Gz));
       A.phi_out[cell] = phi;
     }
     A.u_out[cell] = ux;

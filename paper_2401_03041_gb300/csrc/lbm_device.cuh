@@ -161,6 +161,13 @@ struct DevParams {
   // Sub-domain (a slab of a larger lattice): local column x is global column
   // (x + sub_x0) mod gnx for every position-dependent term.
   int sub, sub_x0, gnx;
+  // Volumetric heat capacity C = rho c_p that varies with phi (rho or c_p
+  // unequal in the two phases): kappa_L, kappa_H - kappa_L, rho_L,
+  // rho_H - rho_L, c_p,L, c_p,H - c_p,L.  With a constant C the host folds
+  // 1 / C into alpha and its slope instead and leaves heat_cap 0.
+  int heat_cap;
+  double hc_d[6];
+  float hc_f[6];
 };
 
 // Global column of local column x (positions of sources, patches, the
@@ -178,6 +185,9 @@ template <> __host__ __device__ __forceinline__ const RealParams<float>& RP<floa
 template <class R> __device__ __forceinline__ R dalpha_of(const DevParams& P);
 template <> __device__ __forceinline__ double dalpha_of<double>(const DevParams& P) { return P.dalpha_d; }
 template <> __device__ __forceinline__ float dalpha_of<float>(const DevParams& P) { return P.dalpha_f; }
+template <class R> __device__ __forceinline__ const R* hc_of(const DevParams& P);
+template <> __device__ __forceinline__ const double* hc_of<double>(const DevParams& P) { return P.hc_d; }
+template <> __device__ __forceinline__ const float* hc_of<float>(const DevParams& P) { return P.hc_f; }
 template <class R> struct Derived { R four_over_xi, twelve_over_xi, inv_rho, omega_g; };
 template <class R> __device__ __forceinline__ Derived<R> derived(const DevParams& P);
 template <> __device__ __forceinline__ Derived<double> derived<double>(const DevParams& P) {

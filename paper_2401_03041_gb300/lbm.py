@@ -49,7 +49,8 @@ class Params(ctypes.Structure):
                 ("omega_high", ctypes.c_double), ("rk_isotropic_fd", ctypes.c_int32),
                 ("T_bottom_amp", ctypes.c_double), ("T_bottom_waves", ctypes.c_int32),
                 ("wall_u_bottom", ctypes.c_double * 2), ("wall_u_top", ctypes.c_double * 2),
-                ("theta_bottom", ctypes.c_double), ("theta_top", ctypes.c_double)]
+                ("theta_bottom", ctypes.c_double), ("theta_top", ctypes.c_double),
+                ("cp_L", ctypes.c_double), ("cp_H", ctypes.c_double)]
 
 
 class HeatSource(ctypes.Structure):

@@ -43,12 +43,17 @@ def _variant(name):
     if name == "density_ratio_d3q15":
         w = ragged_workload("D3Q15", 15, walls=True)
         return w.replace(params=W.Params(**dict(w.params.__dict__, rho_L=1.0, rho_H=10.0)))
+    if name == "d3q7_heat_capacity_ratio":
+        w = ragged_workload("D3Q7", 15, walls=True)
+        return w.replace(params=W.Params(**dict(w.params.__dict__, alpha_L=0.1, alpha_H=0.02, cp_L=1.0,
+                                                cp_H=3.0)))
     if name == "rk2_periodic_heaters":
         return ragged_workload("RK2", 15, walls=False)
     raise KeyError(name)
 
 
 @pytest.mark.parametrize("name", ["walls_moving_wetting", "periodic_d3q19_q27", "rk4_conductivity_ratio",
+                                  "d3q7_heat_capacity_ratio",
                                   "density_ratio_d3q15", "rk2_periodic_heaters"])
 def test_aa_equals_two_grid_fp64(name):
     w = _variant(name)

@@ -229,6 +229,36 @@ def test_conductivity_ratio_fp64(thermal, walls, iso):
         compare_all(d, o, w, TOL64, f"conductivity ratio {thermal} walls={walls} iso={iso} {kern}")
 
 
+@pytest.mark.parametrize("thermal,walls,iso,case",
+                         [("D3Q7", True, False, "cp"), ("D3Q19", False, False, "cp"),
+                          ("D3Q27", True, False, "cp_rho"), ("RK4", True, False, "cp"),
+                          ("RK2", False, True, "cp_rho"), ("D3Q15", True, False, "uniform"),
+                          ("RK4", False, False, "uniform")])
+def test_heat_capacity_ratio_fp64(thermal, walls, iso, case):
+    """Heat capacity rho c_p of Eq. temperature with c_p linear in phi
+    (Sec. 2.3): c_p,H / c_p,L = 3 with a conductivity ratio 1/5 ("cp"), also
+    with rho_H / rho_L = 4 entering rho c_p ("cp_rho"), or a uniform
+    rho c_p = 3 that only rescales the diffusivity ("uniform"): per-cell LB
+    rate with the background and grad(rho c_p) sources, or the RK right-hand
+    side divided by rho c_p; generic and tiled kernels match the oracle
+    within 1e-11 after 12 steps."""
+    w = ragged_workload(thermal, 15, walls=walls)
+    kw = dict(w.params.__dict__, rk_isotropic_fd=iso)
+    if case == "uniform":
+        kw.update(cp_L=3.0, cp_H=3.0, alpha_L=0.15, alpha_H=0.15)
+    else:
+        kw.update(cp_L=1.0, cp_H=3.0, alpha_L=0.1, alpha_H=0.02)
+        if case == "cp_rho":
+            kw.update(rho_L=1.0, rho_H=4.0)
+    w = w.replace(params=W.Params(**kw))
+    o = oracle_for(w)
+    o.step(12)
+    for kern in _kernels("fp64", 15, thermal):
+        d = gpu_domain(w, kernel=kern)
+        d.step(12)
+        compare_all(d, o, w, TOL64, f"heat capacity {case} {thermal} walls={walls} iso={iso} {kern}")
+
+
 @pytest.mark.parametrize("thermal,ratio", [("D3Q7", False), ("D3Q19", True), ("RK4", True), ("RK2", False)])
 def test_modulated_bottom_wall_fp64(thermal, ratio):
     """Bottom wall at T_bottom + 0.3 cos(2 pi 2 (x + 1/2) / nx) (the heated
