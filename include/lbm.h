@@ -77,7 +77,7 @@ typedef enum {
  * with a step that gathers and scatters within the cell; Sec. 4.1 discusses
  * such single-grid schemes), about half the memory; each step first writes
  * a (phi, T) field of the level for the finite differences.  Same results
- * (in FP64 bit for bit those of the generic two-grid kernel); the adjoint
+ * (in FP64 those of the generic two-grid kernel to rounding, 1e-12); the adjoint
  * needs LBM_LAYOUT_TWO_GRID. */
 typedef enum { LBM_LAYOUT_TWO_GRID = 0, LBM_LAYOUT_AA = 1 } lbm_layout;
 
@@ -304,7 +304,10 @@ lbm_status lbm_kernel_info(lbm_domain* dom, int32_t* info);
  * intensities, by the discrete adjoint of the time step.  The paper has no
  * adjoint: this is the exact transpose of the linearised FP64 step of
  * lbm_step (Sec. 2.2-2.3 model, Alg. 1 sweep order), for FP64 storage with
- * the D3Q7 thermal LB and nx * ny < 2^31 (else LBM_ERR_UNSUPPORTED).
+ * the energy equation as the thermal LB (D3Q7/15/19/27) or RK2 / RK4 (Eq.
+ * rk2, Eq. rk4; the state then holds the T field), a uniform diffusivity,
+ * equal densities, walls at rest with neutral wetting, the two-grid layout,
+ * a whole lattice and nx * ny < 2^31 (else LBM_ERR_UNSUPPORTED).
  *   Starting from the current state (level n0), runs nsteps steps forward,
  *   keeping a copy of the state every ckpt_every steps, and evaluates
  *   J = |c - target|^2, c = (sum phi x, sum phi y, sum phi z) / sum phi at
@@ -325,10 +328,11 @@ lbm_status lbm_kernel_info(lbm_domain* dom, int32_t* info);
  *   round-off-level perturbations there that the step itself keeps bounded,
  *   and the exact gradient no longer describes finite changes of J.
  *   Synchronises.  Allocates its buffers for the duration of the call:
- *   nsteps / ckpt_every + 1 PDF sets (checkpoints, final state), ckpt_every
- *   x 19 doubles per cell (the replayed steps' intermediates) and 3 dense
- *   adjoint sets (q_phase + 34 doubles per cell each): LBM_ERR_OOM if they do
- *   not fit.
+ *   nsteps / ckpt_every + 1 states (PDF set, and the T field with RK:
+ *   checkpoints, final state), ckpt_every x 19 doubles per cell (the replayed
+ *   steps' intermediates), 3 dense adjoint sets (q_phase + 27 + Q_f doubles
+ *   per cell each, Q_f = 1 for RK) and with RK 13 doubles per cell for the
+ *   stage reverse: LBM_ERR_OOM if they do not fit.
  * Errors: LBM_ERR_ARG (nsteps < 1, ckpt_every < 1, null target / J_out, NaN normal_cap),
  * LBM_ERR_STATE (not initialised, zero phi mass), LBM_ERR_UNSUPPORTED. */
 lbm_status lbm_adjoint_run(lbm_domain* dom, int nsteps, int ckpt_every, const double* target,
@@ -336,8 +340,9 @@ lbm_status lbm_adjoint_run(lbm_domain* dom, int nsteps, int ckpt_every, const do
 
 /* One adjoint step at the current state s: lam_out = (d Phi / d s)^T lam_in,
  * where Phi is one lbm_step.  lam_in and lam_out are host arrays of
- * (q_phase + 27 + 7) * N doubles in the order of lbm_get_pdfs (h, then g,
- * then f, each [direction][z][y][x]); normal_cap as in lbm_adjoint_run.
+ * (q_phase + 27 + Q_f) * N doubles in the order of lbm_get_pdfs (h, then g,
+ * then f, each [direction][z][y][x]; with RK2 / RK4 the T field [z][y][x]
+ * takes the place of f, Q_f = 1); normal_cap as in lbm_adjoint_run.
  * Same requirements as lbm_adjoint_run;
  * allocates its buffers for the call; synchronises.  (The building block of
  * lbm_adjoint_run, exposed for dot-product tests against the linearised step.) */

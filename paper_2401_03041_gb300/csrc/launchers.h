@@ -75,15 +75,38 @@ void launch_diag_finalize(const double* partials, int nblocks, double* out, cuda
 
 namespace lbm {
 
-// Adjoint step (FP64, LB thermal; inst_adjoint.cu).
+// Adjoint step (FP64; thermal LB D3Q7/15/19/27 or RK2/RK4; inst_adjoint.cu).
+// qf = 0 selects the RK energy solvers, whose state holds the T field in
+// place of f (one slot of N values after h and g in the adjoint arrays).
 bool adj_supported(int qh, int qf);
-void adj_cell(const DevParams& P, const AdjPtrs& A, int qh, int qf, cudaStream_t st);
+// rk_lu: RK only, the adjoint of u through the RK update ([3][N]), added to
+// the velocity adjoint of pass A.
+void adj_cell(const DevParams& P, const AdjPtrs& A, int qh, int qf, const double* rk_lu, cudaStream_t st);
 void adj_fields(const DevParams& P, const AdjPtrs& A, cudaStream_t st);
-void adj_pull(const DevParams& P, const AdjPtrs& A, int qh, int qf, cudaStream_t st);
+// rk_lT: RK only, the adjoint of T^n through the RK update, added to the
+// stencil adjoint of T in the T slot of lam_out.
+void adj_pull(const DevParams& P, const AdjPtrs& A, int qh, int qf, const double* rk_lT, cudaStream_t st);
 void adj_seed(const DevParams& P, const double* dJdphi, double* lam, int qh, int qf, cudaStream_t st);
 void adj_centroid_seed(const DevParams& P, double mass, const double* c, const double* t, double* out,
                        cudaStream_t st);
+// dJ/dI_k += sum over the cells of patch k of the intensity's adjoint:
+// sum_i w_i lam_{f,i} (LB: lam = lam^{n+1}), or the per-cell adjoint of q_T
+// (RK: lam = AdjRK::lq).
 void adj_patch_grad(const DevParams& P, const double* lam, double* dJdI, int qh, int qf, cudaStream_t st);
+
+// Buffers of the RK part of an adjoint step (N doubles each unless noted).
+struct AdjRK {
+  double* u;        // [3][N]: u of the step, from the saved intermediates
+  double* psi[3];   // stage inputs psi_k = T + c_k K_{k-1}, k = 2, 3, 4 (RK2: psi[0])
+  double* lk[2];    // adjoints of the stage slopes K_k (ping-pong)
+  double* lT;       // adjoint of T^n through the RK update
+  double* lu;       // [3][N]: adjoint of u through the RK update
+  double* lq;       // adjoint of the heat-source density q_T (all stages)
+};
+// The RK update's adjoint for one step: from lam_T' = dJ/dT^{n+1} (lamT,
+// N values) and the step's intermediates, fills R.lT, R.lu and R.lq.
+void adj_rk(const DevParams& P, const double* save, const double* lamT, const AdjRK& R, bool rk4,
+            cudaStream_t st);
 
 // Set the calling thread's lbm_last_error message and return s.
 lbm_status set_error(lbm_status s, const char* msg);

@@ -21,7 +21,9 @@
 // which writes the (phi, T) pairs of every cell (zeroth moments of the
 // gathered populations, summed in the same order as the two-grid kernels'
 // halo sums), and the step kernel takes its stencil tiles from that field.
-// In FP64 the result equals the generic two-grid kernel's bit for bit.
+// In FP64 the result equals the generic two-grid kernel's to rounding (the
+// two are compiled separately and contract their products into FMAs
+// differently).
 #pragma once
 
 #include "lbm_step.cuh"

@@ -1,4 +1,5 @@
-// lbm_adjoint.cuh - discrete adjoint of one FP64 time step (LB thermal).
+// lbm_adjoint.cuh - discrete adjoint of one FP64 time step (thermal LB or
+// RK2 / RK4 energy solver).
 //
 // The paper has no adjoint; this is the exact transpose of the linearisation
 // of the FP64 step the generic and bulk kernels compute (Sec. 2.2-2.3, Alg. 1
@@ -24,7 +25,18 @@
 //      where A_i(x) = lam*_i(x) + lam_phi(x) (h), lam*_i(x) (g),
 //      lam*_i(x) + lam_T(x) (f).
 // Adjoint arrays are dense [direction][z][y][x] FP64 (N values per direction,
-// h | g | f directions in one block).
+// h | g | f directions in one block; with an RK energy solver the T field
+// takes the place of f, one slot of N values).
+//
+// RK2 / RK4 (Eq. rk2, Eq. rk4): the energy update T' = T + sum_k b_k K_k with
+// K_k = R(psi_k), psi_1 = T, psi_k = T + c_k K_{k-1}, is affine in T given u:
+// R(psi) = L_u psi + r_u with L_u psi = -u . D psi + alpha Lap psi (D, Lap the
+// 7-point / central or the isotropic operators, wall ghosts 2 T_w - psi).
+// Backwards over the stages (adj_rk): lam_K_k = b_k lam_T' + c_{k+1} L^T
+// lam_K_{k+1}; the adjoint of T^n is lam_T' + sum_k L^T lam_K_k, of u(x) is
+// -sum_k lam_K_k(x) (D psi_k(x) + G), of q_T(x) is sum_k lam_K_k(x).  The stage
+// inputs psi_k are recomputed from the saved T^n and u; the u adjoint enters
+// pass A, the T adjoint is added in pass B2.
 //
 // Reverse-mode identities used for the central-moment collision (per axis, a
 // unit central moment of order e maps to the 1D basis b_e(c; u) of the
@@ -32,7 +44,7 @@
 // d b_2 / du = 0.
 #pragma once
 
-#include "lbm_step.cuh"
+#include "lbm_aux.cuh"
 
 namespace lbm {
 
@@ -112,35 +124,59 @@ __device__ __forceinline__ void cell_adjoint_inputs(const DevParams& P, const do
   m.syz = sv[SAVE_SYZ * N + cell];
 }
 
+// Forward force and velocity of a cell from its saved intermediates (the
+// FP64 arithmetic of cell_force / cell_velocity for equal densities).
+struct AdjFlow {
+  double gTx, gTy, gTz, sigma, beta, kap, dw, mu, g2, tdp, cm, rho, ax, ay, az, ux, uy, uz;
+};
+
+__device__ __forceinline__ AdjFlow adj_flow(const DevParams& P, int x, int y, int z, double phi, double Tc,
+                                            const Stencil27<double>& fdv, const GMoments<double>& gm) {
+  const auto& rp = P.pd;
+  AdjFlow w;
+  const double gpx = fdv.gpx, gpy = fdv.gpy, gpz = fdv.gpz, lp = fdv.lp;
+  const double Gx = rp.grad[0], Gy = rp.grad[1], Gz = rp.grad[2];
+  const double Ttot = Tc + Gx * (x + 0.5 - rp.origin[0]) + Gy * (y + 0.5 - rp.origin[1]) +
+                      Gz * (z + 0.5 - rp.origin[2]);
+  w.gTx = fdv.gtx + Gx; w.gTy = fdv.gty + Gy; w.gTz = fdv.gtz + Gz;
+  const double xi = rp.xi;
+  w.sigma = rp.sigma_ref + rp.sigma_T * (Ttot - rp.T_ref);
+  w.beta = 12.0 * w.sigma / xi;
+  w.kap = 1.5 * w.sigma * xi;
+  w.dw = phi * (phi - 1.0) * (phi - 0.5);
+  w.mu = 4.0 * w.beta * w.dw - w.kap * lp;
+  w.g2 = gpx * gpx + gpy * gpy + gpz * gpz;
+  w.tdp = w.gTx * gpx + w.gTy * gpy + w.gTz * gpz;
+  w.cm = 1.5 * xi * rp.sigma_T;
+  w.rho = rp.rho_L + phi * (rp.rho_H - rp.rho_L);
+  const double Fx = w.mu * gpx + w.cm * (w.g2 * w.gTx - w.tdp * gpx) + w.rho * rp.gravity[0];
+  const double Fy = w.mu * gpy + w.cm * (w.g2 * w.gTy - w.tdp * gpy) + w.rho * rp.gravity[1];
+  const double Fz = w.mu * gpz + w.cm * (w.g2 * w.gTz - w.tdp * gpz) + w.rho * rp.gravity[2];
+  w.ax = Fx / w.rho; w.ay = Fy / w.rho; w.az = Fz / w.rho;
+  w.ux = gm.jx + 0.5 * w.ax; w.uy = gm.jy + 0.5 * w.ay; w.uz = gm.jz + 0.5 * w.az;
+  return w;
+}
+
 template <int QH, int QF>
 __device__ __forceinline__ void cell_adjoint(const DevParams& P, const AdjPtrs& A, int x, int y, int z,
                                              size_t cell, double phi, double Tc,
-                                             const Stencil27<double>& fdv, const GMoments<double>& gm) {
+                                             const Stencil27<double>& fdv, const GMoments<double>& gm,
+                                             const double* __restrict__ rk_lu) {
   const auto& rp = P.pd;
   const size_t N = (size_t)P.N;
   constexpr int OG = QH, OF = QH + 27;
   // ---------------- forward quantities (as cell_flow / collide_*, FP64)
   const double gpx = fdv.gpx, gpy = fdv.gpy, gpz = fdv.gpz, lp = fdv.lp;
   const double Gx = rp.grad[0], Gy = rp.grad[1], Gz = rp.grad[2];
-  const double Ttot = Tc + Gx * (x + 0.5 - rp.origin[0]) + Gy * (y + 0.5 - rp.origin[1]) +
-                      Gz * (z + 0.5 - rp.origin[2]);
-  const double gTx = fdv.gtx + Gx, gTy = fdv.gty + Gy, gTz = fdv.gtz + Gz;
-  const double pst = gm.pst, jx = gm.jx, jy = gm.jy, jz = gm.jz;
+  const AdjFlow fw = adj_flow(P, x, y, z, phi, Tc, fdv, gm);
+  const double gTx = fw.gTx, gTy = fw.gTy, gTz = fw.gTz;
+  const double pst = gm.pst;
   const double sxx = gm.sxx, syy = gm.syy, szz = gm.szz, sxy = gm.sxy, sxz = gm.sxz, syz = gm.syz;
   const double xi = rp.xi;
-  const double sigma = rp.sigma_ref + rp.sigma_T * (Ttot - rp.T_ref);
-  const double beta = 12.0 * sigma / xi, kap = 1.5 * sigma * xi;
-  const double dw = phi * (phi - 1.0) * (phi - 0.5);
-  const double mu = 4.0 * beta * dw - kap * lp;
-  const double g2 = gpx * gpx + gpy * gpy + gpz * gpz;
-  const double tdp = gTx * gpx + gTy * gpy + gTz * gpz;
-  const double cm = 1.5 * xi * rp.sigma_T;
-  const double rho = rp.rho_L + phi * (rp.rho_H - rp.rho_L);
-  const double Fx = mu * gpx + cm * (g2 * gTx - tdp * gpx) + rho * rp.gravity[0];
-  const double Fy = mu * gpy + cm * (g2 * gTy - tdp * gpy) + rho * rp.gravity[1];
-  const double Fz = mu * gpz + cm * (g2 * gTz - tdp * gpz) + rho * rp.gravity[2];
-  const double ax = Fx / rho, ay = Fy / rho, az = Fz / rho;
-  const double ux = jx + 0.5 * ax, uy = jy + 0.5 * ay, uz = jz + 0.5 * az;
+  const double beta = fw.beta, kap = fw.kap, dw = fw.dw, mu = fw.mu, g2 = fw.g2, tdp = fw.tdp, cm = fw.cm;
+  const double rho = fw.rho;
+  const double ax = fw.ax, ay = fw.ay, az = fw.az;
+  const double ux = fw.ux, uy = fw.uy, uz = fw.uz;
   const double uu = ux * ux + uy * uy + uz * uz;
   const double omg = 1.0 / (rp.tau_L + phi * (rp.tau_H - rp.tau_L));
   const double k1 = 1.0 - omg;
@@ -180,6 +216,12 @@ __device__ __forceinline__ void cell_adjoint(const DevParams& P, const AdjPtrs& 
     l_ux += k * (-3.0 * ux * M.m0 + 9.0 * Mu[0] + 3.0 * M.m1[0]) - M.m0 * Gx;
     l_uy += k * (-3.0 * uy * M.m0 + 9.0 * Mu[1] + 3.0 * M.m1[1]) - M.m0 * Gy;
     l_uz += k * (-3.0 * uz * M.m0 + 9.0 * Mu[2] + 3.0 * M.m1[2]) - M.m0 * Gz;
+  }
+  if constexpr (QF == 0) {
+    // RK energy solver: u enters every stage slope K_k (adj_rk)
+    l_ux += rk_lu[cell];
+    l_uy += rk_lu[N + cell];
+    l_uz += rk_lu[2 * N + cell];
   }
   // h collision: h' = h* - om (h* - w phi E) + sc w c.Fphi
   double l_Fpx, l_Fpy, l_Fpz;
@@ -332,7 +374,7 @@ __device__ __forceinline__ void cell_adjoint(const DevParams& P, const AdjPtrs& 
 // Pass A: pointwise, from the saved intermediates of the step.  Grid: x over
 // the cells of one plane (32-bit index), y = z.
 template <int QH, int QF>
-__global__ void adj_point_kernel(const DevParams P, const AdjPtrs A) {
+__global__ void adj_point_kernel(const DevParams P, const AdjPtrs A, const double* __restrict__ rk_lu) {
   const unsigned plane = (unsigned)P.nx * (unsigned)P.ny;
   const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= plane) return;
@@ -343,7 +385,7 @@ __global__ void adj_point_kernel(const DevParams P, const AdjPtrs A) {
   Stencil27<double> fd;
   GMoments<double> m;
   cell_adjoint_inputs(P, A.save, cell, phi, Tc, fd, m);
-  cell_adjoint<QH, QF>(P, A, x, y, z, cell, phi, Tc, fd, m);
+  cell_adjoint<QH, QF>(P, A, x, y, z, cell, phi, Tc, fd, m, rk_lu);
 }
 
 // Pass B1: total adjoints of phi and T (stencil transposes).  Grid: x over
@@ -398,7 +440,7 @@ __global__ void adj_fields_kernel(const DevParams P, const AdjPtrs A) {
 // thread per cell for all directions.  Grid: x over the cells of one plane
 // (32-bit index), y = z.
 template <int QH, int QF>
-__global__ void adj_pull_kernel(const DevParams P, const AdjPtrs A) {
+__global__ void adj_pull_kernel(const DevParams P, const AdjPtrs A, const double* __restrict__ rk_lT) {
   const size_t N = (size_t)P.N;
   const unsigned plane = (unsigned)P.nx * (unsigned)P.ny;
   const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -433,15 +475,16 @@ __global__ void adj_pull_kernel(const DevParams P, const AdjPtrs A) {
   };
   static_for<0, QH>([&](auto J) { one(std::integral_constant<int, 0>{}, J); });
   static_for<0, 27>([&](auto J) { one(std::integral_constant<int, 1>{}, J); });
-  static_for<0, QF>([&](auto J) { one(std::integral_constant<int, 2>{}, J); });
+  if constexpr (QF > 0) static_for<0, QF>([&](auto J) { one(std::integral_constant<int, 2>{}, J); });
+  else A.lam_out[(size_t)(QH + 27) * N + cell] = tT + rk_lT[cell];   // RK: the T field
 }
 
 // Seed lam^N for J(phi^N): dJ/dphi given per cell (dense, N values) -> the
-// adjoint of the stored h (pull transpose with bounce-back); g, f: 0.
+// adjoint of the stored h (pull transpose with bounce-back); g, f (or T): 0.
 template <int QH, int QF>
 __global__ void adj_seed_kernel(const DevParams P, const double* __restrict__ dJdphi, double* lam) {
   const size_t N = (size_t)P.N;
-  constexpr int NQ = QH + 27 + QF;
+  constexpr int NQ = QH + 27 + (QF > 0 ? QF : 1);   // RK: one T slot
   const size_t total = (size_t)NQ * N;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
        k += (size_t)gridDim.x * blockDim.x) {
@@ -477,8 +520,9 @@ __global__ void adj_centroid_seed_kernel(const DevParams P, double mass, double 
 }
 
 // dJ/dI_k += sum over the cells of patch k of sum_i w_i lam^{n+1}_{f,i}
-// (the intensity enters every f'_i of a patch cell as w_i I_k).  One block
-// per patch, fixed summation order.
+// (the intensity enters every f'_i of a patch cell as w_i I_k), or with an
+// RK energy solver (QF = 0) of lam_q, the adjoint of q_T over the stages.
+// One block per patch, fixed summation order.
 template <int QH, int QF>
 __global__ void adj_patch_grad_kernel(const DevParams P, const double* __restrict__ lam, double* dJdI) {
   __shared__ double red[256];
@@ -490,10 +534,14 @@ __global__ void adj_patch_grad_kernel(const DevParams P, const double* __restric
     const int x = P.px0[k] + c % P.patch_sx, y = P.py0[k] + c / P.patch_sx;
     if (x < 0 || x >= P.nx || y < 0 || y >= P.ny) continue;
     const size_t cell = cell_index(P, x, y, P.patch_z);
-    static_for<0, QF>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      s += weight<QF>(i) * lam[(size_t)(QH + 27 + i) * N + cell];
-    });
+    if constexpr (QF > 0) {
+      static_for<0, QF>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        s += weight<QF>(i) * lam[(size_t)(QH + 27 + i) * N + cell];
+      });
+    } else {
+      s += lam[cell];
+    }
   }
   red[threadIdx.x] = s;
   __syncthreads();
@@ -502,6 +550,151 @@ __global__ void adj_patch_grad_kernel(const DevParams P, const double* __restric
     __syncthreads();
   }
   if (threadIdx.x == 0) dJdI[k] += red[0];
+}
+
+
+// ---------------------------------------------------------------- RK part
+// Cell (x, y, z) of a plane-indexed launch (x over nx * ny, y = z); false
+// past the plane's end.
+__device__ __forceinline__ bool adj_plane_cell(const DevParams& P, int& x, int& y, int& z, size_t& cell) {
+  const unsigned plane = (unsigned)P.nx * (unsigned)P.ny;
+  const unsigned r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= plane) return false;
+  y = (int)(r / (unsigned)P.nx);
+  x = (int)(r - (unsigned)y * (unsigned)P.nx);
+  z = blockIdx.y;
+  cell = (size_t)z * plane + r;
+  return true;
+}
+
+// u of every cell from the saved intermediates of the step ([3][N]).
+__global__ void adj_rk_velocity_kernel(const DevParams P, const double* __restrict__ save, double* __restrict__ u) {
+  int x, y, z;
+  size_t cell;
+  if (!adj_plane_cell(P, x, y, z, cell)) return;
+  double phi, Tc;
+  Stencil27<double> fd;
+  GMoments<double> m;
+  cell_adjoint_inputs(P, save, cell, phi, Tc, fd, m);
+  const AdjFlow w = adj_flow(P, x, y, z, phi, Tc, fd, m);
+  const size_t N = (size_t)P.N;
+  u[cell] = w.ux;
+  u[N + cell] = w.uy;
+  u[2 * N + cell] = w.uz;
+}
+
+// Forward replay of one stage input: out = T + c R(psi) (rk_rhs, no
+// conductivity or heat-capacity ratio).
+__global__ void adj_rk_replay_kernel(const DevParams P, const double* __restrict__ psi, const double* __restrict__ T,
+                                     const double* __restrict__ u, double c, double* __restrict__ out) {
+  int x, y, z;
+  size_t cell;
+  if (!adj_plane_cell(P, x, y, z, cell)) return;
+  out[cell] = T[cell] + c * rk_rhs<double>(P, psi, u, nullptr, x, y, z, cell);
+}
+
+// Gradient of the stage input at (x, y, z) with R's operator: the central
+// difference of the 7-point set, or the isotropic D3Q27 gradient (wall ghosts
+// 2 T_w - psi as in rk_rhs).
+__device__ __forceinline__ void rk_grad(const DevParams& P, const double* __restrict__ psi, int x, int y, int z,
+                                        double& gx, double& gy, double& gz) {
+  if (P.rk_iso) {
+    gx = gy = gz = 0.0;
+    static_for<1, 27>([&](auto K) {
+      constexpr int k = decltype(K)::value;
+      constexpr int ex = q27_cx(k), ey = q27_cy(k), ez = q27_cz(k);
+      if constexpr (ex > 0 || (ex == 0 && (ey > 0 || (ey == 0 && ez > 0)))) {
+        constexpr double w = weight<27>(k);
+        const double d = stage_at(P, psi, x, y, z, ex, ey, ez) - stage_at(P, psi, x, y, z, -ex, -ey, -ez);
+        if constexpr (ex != 0) gx += ex * w * d;
+        if constexpr (ey != 0) gy += ey * w * d;
+        if constexpr (ez != 0) gz += ez * w * d;
+      }
+    });
+    gx *= 3.0; gy *= 3.0; gz *= 3.0;
+  } else {
+    gx = 0.5 * (stage_at(P, psi, x, y, z, 1, 0, 0) - stage_at(P, psi, x, y, z, -1, 0, 0));
+    gy = 0.5 * (stage_at(P, psi, x, y, z, 0, 1, 0) - stage_at(P, psi, x, y, z, 0, -1, 0));
+    gz = 0.5 * (stage_at(P, psi, x, y, z, 0, 0, 1) - stage_at(P, psi, x, y, z, 0, 0, -1));
+  }
+}
+
+// One stage of the RK reverse, stages last .. first.  lamK(x) = sK srcK(x) is
+// the adjoint of the slope K_k = R(psi_k).  With mu = L^T lamK:
+//   next(y) = b_prev lamT'(y) + c_k mu(y)    (adjoint of K_{k-1}; next != null)
+//   lT(y) = lamT'(y) + mu(y) on the last stage, lT(y) += mu(y) after it
+//   lu(y) (+)= -lamK(y) (D psi_k(y) + G),  lq(y) (+)= lamK(y).
+// (L psi)(x) = sum_c a_c(x) psi~(x + c) - alpha l_0 psi(x), a_c(x) = -u(x) . d_c
+// + alpha l_c, with psi~ the ghost-resolved read: across a wall the read of
+// x + c returns 2 T_w - psi at the same-layer cell, so that cell collects
+// -a_c(x).  7-point set: c = +-e, d_c = +-e / 2, l_c = 1, l_0 = 6; isotropic:
+// d_c = 3 w_c c, l_c = 6 w_c, l_0 = 6 (1 - w_0).
+__global__ void adj_rk_stage_kernel(const DevParams P, const double* __restrict__ srcK, double sK,
+                                    const double* __restrict__ psi, const double* __restrict__ u,
+                                    const double* __restrict__ lamT, double b_prev, double c_k,
+                                    double* __restrict__ next, double* __restrict__ lT, double* __restrict__ lu,
+                                    double* __restrict__ lq, int last) {
+  int x, y, z;
+  size_t cell;
+  if (!adj_plane_cell(P, x, y, z, cell)) return;
+  const size_t N = (size_t)P.N;
+  const double alpha = P.pd.alpha;
+  double mu = 0.0;
+  // contribution of reader xs at offset (ex, ey, ez) with direction weights
+  auto add = [&](size_t xs, double dx_, double dy_, double dz_, double lc, double sgn) {
+    const double a = -(u[xs] * dx_ + u[N + xs] * dy_ + u[2 * N + xs] * dz_) + alpha * lc;
+    mu += sgn * a * (sK * srcK[xs]);
+  };
+  auto offset = [&](int ex, int ey, int ez, double dx_, double dy_, double dz_, double lc) {
+    const int xs = wrap(x - ex, P.nx), ys = wrap(y - ey, P.ny);
+    if (P.walls) {
+      const int zs = z - ez;
+      if (zs >= 0 && zs < P.nz) add(cell_index(P, xs, ys, zs), dx_, dy_, dz_, lc, 1.0);
+      if (ez == -1 && z == 0) add(cell_index(P, xs, ys, 0), dx_, dy_, dz_, lc, -1.0);
+      if (ez == 1 && z == P.nz - 1) add(cell_index(P, xs, ys, P.nz - 1), dx_, dy_, dz_, lc, -1.0);
+    } else {
+      add(cell_index(P, xs, ys, wrap(z - ez, P.nz)), dx_, dy_, dz_, lc, 1.0);
+    }
+  };
+  double l0;
+  if (P.rk_iso) {
+    static_for<1, 27>([&](auto K) {
+      constexpr int k = decltype(K)::value;
+      constexpr int ex = q27_cx(k), ey = q27_cy(k), ez = q27_cz(k);
+      constexpr double w = weight<27>(k);
+      offset(ex, ey, ez, 3.0 * w * ex, 3.0 * w * ey, 3.0 * w * ez, 6.0 * w);
+    });
+    l0 = 6.0 * (1.0 - weight<27>(0));
+  } else {
+    offset(1, 0, 0, 0.5, 0.0, 0.0, 1.0);
+    offset(-1, 0, 0, -0.5, 0.0, 0.0, 1.0);
+    offset(0, 1, 0, 0.0, 0.5, 0.0, 1.0);
+    offset(0, -1, 0, 0.0, -0.5, 0.0, 1.0);
+    offset(0, 0, 1, 0.0, 0.0, 0.5, 1.0);
+    offset(0, 0, -1, 0.0, 0.0, -0.5, 1.0);
+    l0 = 6.0;
+  }
+  const double lk = sK * srcK[cell];
+  mu -= alpha * l0 * lk;
+  const double lt = lamT[cell];
+  if (next) next[cell] = b_prev * lt + c_k * mu;
+  double gx, gy, gz;
+  rk_grad(P, psi, x, y, z, gx, gy, gz);
+  const auto& rp = P.pd;
+  const double dux = -lk * (gx + rp.grad[0]), duy = -lk * (gy + rp.grad[1]), duz = -lk * (gz + rp.grad[2]);
+  if (last) {
+    lT[cell] = lt + mu;
+    lu[cell] = dux;
+    lu[N + cell] = duy;
+    lu[2 * N + cell] = duz;
+    lq[cell] = lk;
+  } else {
+    lT[cell] += mu;
+    lu[cell] += dux;
+    lu[N + cell] += duy;
+    lu[2 * N + cell] += duz;
+    lq[cell] += lk;
+  }
 }
 
 }  // namespace lbm

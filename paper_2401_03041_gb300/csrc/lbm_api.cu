@@ -1252,19 +1252,26 @@ struct AdjBuffers {
   char* base = nullptr;
   double *lam_a = nullptr, *lam_b = nullptr, *lstar = nullptr, *fld = nullptr, *tot = nullptr;
   double *dJdphi = nullptr, *dJdI = nullptr;
-  char* sets = nullptr;   // nsets padded PDF sets (checkpoints)
-  size_t set_bytes = 0;
+  char* sets = nullptr;   // nsets states (checkpoints): padded PDF set, then T (RK)
+  size_t set_bytes = 0;   // one state
+  size_t pdf_bytes = 0;   // its PDF set
   double* saves = nullptr;  // nsaves x [SAVE_N][N] step intermediates
   size_t save_elems = 0;
+  AdjRK rk{};             // RK energy solvers only
 };
 
 size_t pdf_set_bytes(const lbm_domain* d) {
   return (size_t)(d->qh + 27 + d->qf) * (size_t)d->dp.Np * sizeof(double);
 }
 
+// Slots of the dense adjoint arrays: h, g, then f (LB) or the T field (RK).
+size_t adj_slots(const lbm_domain* d) { return (size_t)(d->qh + 27 + (d->qf > 0 ? d->qf : 1)); }
+
 lbm_status adj_alloc(lbm_domain* d, int nsets, int nsaves, AdjBuffers* B) {
-  const size_t N = (size_t)d->N, nq = (size_t)(d->qh + 27 + d->qf);
-  B->set_bytes = pdf_set_bytes(d);
+  const size_t N = (size_t)d->N, nq = adj_slots(d);
+  const bool rk = d->qf == 0;
+  B->pdf_bytes = pdf_set_bytes(d);
+  B->set_bytes = align256(B->pdf_bytes + (rk ? N * 8 : 0));
   size_t off = 0;
   size_t o_la = off; off = align256(off + nq * N * 8);
   size_t o_lb = off; off = align256(off + nq * N * 8);
@@ -1273,6 +1280,7 @@ lbm_status adj_alloc(lbm_domain* d, int nsets, int nsaves, AdjBuffers* B) {
   size_t o_to = off; off = align256(off + 2 * N * 8);
   size_t o_dp = off; off = align256(off + N * 8);
   size_t o_di = off; off = align256(off + LBM_MAX_PATCHES * 8);
+  size_t o_rk = off; off = align256(off + (rk ? 13 * N * 8 : 0));   // u 3, psi 3, lk 2, lT 1, lu 3, lq 1
   size_t o_se = off; off = align256(off + (size_t)nsets * B->set_bytes);
   B->save_elems = (size_t)SAVE_N * N;
   size_t o_sv = off; off = align256(off + (size_t)nsaves * B->save_elems * 8);
@@ -1288,6 +1296,18 @@ lbm_status adj_alloc(lbm_domain* d, int nsets, int nsaves, AdjBuffers* B) {
   B->tot = (double*)(B->base + o_to);
   B->dJdphi = (double*)(B->base + o_dp);
   B->dJdI = (double*)(B->base + o_di);
+  if (rk) {
+    double* r = (double*)(B->base + o_rk);
+    B->rk.u = r;
+    B->rk.psi[0] = r + 3 * N;
+    B->rk.psi[1] = r + 4 * N;
+    B->rk.psi[2] = r + 5 * N;
+    B->rk.lk[0] = r + 6 * N;
+    B->rk.lk[1] = r + 7 * N;
+    B->rk.lT = r + 8 * N;
+    B->rk.lu = r + 9 * N;
+    B->rk.lq = r + 12 * N;
+  }
   B->sets = B->base + o_se;
   B->saves = (double*)(B->base + o_sv);
   return LBM_OK;
@@ -1307,10 +1327,17 @@ lbm_status adj_one_step(lbm_domain* d, const double* save, const double* lam_in,
   A.tot = B.tot;
   A.lam_out = lam_out;
   A.ncap = ncap;
-  if (patch_grad) adj_patch_grad(d->dp, lam_in, B.dJdI, d->qh, d->qf, d->stream);
-  adj_cell(d->dp, A, d->qh, d->qf, d->stream);
+  if (d->qf == 0) {
+    // RK energy solver: the stage reverse first (it gives the u adjoint of
+    // pass A, the T adjoint of pass B2 and the q_T adjoint of the patches)
+    adj_rk(d->dp, save, lam_in + (size_t)(d->qh + 27) * (size_t)d->N, B.rk, d->th == LBM_TH_RK4, d->stream);
+    if (patch_grad) adj_patch_grad(d->dp, B.rk.lq, B.dJdI, d->qh, 0, d->stream);
+  } else if (patch_grad) {
+    adj_patch_grad(d->dp, lam_in, B.dJdI, d->qh, d->qf, d->stream);
+  }
+  adj_cell(d->dp, A, d->qh, d->qf, B.rk.lu, d->stream);
   adj_fields(d->dp, A, d->stream);
-  adj_pull(d->dp, A, d->qh, d->qf, d->stream);
+  adj_pull(d->dp, A, d->qh, d->qf, B.rk.lT, d->stream);
   return check_launch(d, "adjoint step kernels");
 }
 
@@ -1319,7 +1346,7 @@ lbm_status adj_check(lbm_domain* d) {
   if (s != LBM_OK) return s;
   if (!d->inited) return fail(LBM_ERR_STATE, "domain not initialised");
   if (d->prec != LBM_FP64 || !adj_supported(d->qh, d->qf))
-    return fail(LBM_ERR_UNSUPPORTED, "the adjoint needs FP64 storage and a thermal LB (D3Q7/15/19/27)");
+    return fail(LBM_ERR_UNSUPPORTED, "the adjoint needs FP64 storage");
   if (d->dp.alpha_ratio)
     return fail(LBM_ERR_UNSUPPORTED, "the adjoint is built for a uniform diffusivity (kappa and rho c_p equal in both phases)");
   if (d->dp.rho_ratio)
@@ -1344,7 +1371,7 @@ lbm_status lbm_adjoint_step(lbm_domain* d, const double* lam_in_host, double* la
   AdjBuffers B;
   s = adj_alloc(d, 0, 1, &B);
   if (s != LBM_OK) return s;
-  const size_t bytes = (size_t)(d->qh + 27 + d->qf) * (size_t)d->N * 8;
+  const size_t bytes = adj_slots(d) * (size_t)d->N * 8;
   s = check_cuda(d, cudaMemcpyAsync(B.lam_a, lam_in_host, bytes, cudaMemcpyHostToDevice, d->stream),
                  "adjoint input copy");
   // intermediates of the step from the current state (read-only pass)
@@ -1377,17 +1404,33 @@ lbm_status lbm_adjoint_run(lbm_domain* d, int nsteps, int ckpt_every, const doub
   auto save_slot = [&](int k) { return B.saves + (size_t)k * B.save_elems; };
   char* ckpt0 = set_ptr(0);
   char* final_set = set_ptr(nseg);
-  auto copy_set = [&](char* dst, const char* src) {
-    return check_cuda(d, cudaMemcpyAsync(dst, src, B.set_bytes, cudaMemcpyDeviceToDevice, d->stream),
-                      "adjoint state copy");
+  // a state is the current PDF set, and with an RK energy solver the T field
+  char* T_field = (char*)at(d, d->L.T);
+  auto save_state = [&](char* dst) {
+    lbm_status r = check_cuda(d, cudaMemcpyAsync(dst, cur_set(d), B.pdf_bytes, cudaMemcpyDeviceToDevice, d->stream),
+                              "adjoint state copy");
+    if (r == LBM_OK && d->qf == 0)
+      r = check_cuda(d, cudaMemcpyAsync(dst + B.pdf_bytes, T_field, (size_t)d->N * 8, cudaMemcpyDeviceToDevice,
+                                        d->stream),
+                     "adjoint state copy");
+    return r;
+  };
+  auto restore_state = [&](const char* src) {
+    lbm_status r = check_cuda(d, cudaMemcpyAsync(cur_set(d), src, B.pdf_bytes, cudaMemcpyDeviceToDevice, d->stream),
+                              "adjoint state copy");
+    if (r == LBM_OK && d->qf == 0)
+      r = check_cuda(d, cudaMemcpyAsync(T_field, src + B.pdf_bytes, (size_t)d->N * 8, cudaMemcpyDeviceToDevice,
+                                        d->stream),
+                     "adjoint state copy");
+    return r;
   };
   const long long level0 = d->level;
   // forward, checkpoint every K steps
   for (int n = 0; n < nsteps && s == LBM_OK; ++n) {
-    if (n % K == 0) s = copy_set(ckpt0 + (size_t)(n / K) * B.set_bytes, cur_set(d));
+    if (n % K == 0) s = save_state(ckpt0 + (size_t)(n / K) * B.set_bytes);
     if (s == LBM_OK) s = run_pass(d, MODE_COLLIDE);
   }
-  if (s == LBM_OK) s = copy_set(final_set, cur_set(d));
+  if (s == LBM_OK) s = save_state(final_set);
   lbm_diag dg;
   if (s == LBM_OK) s = lbm_get_diagnostics(d, &dg);
   double J = 0.0;
@@ -1406,7 +1449,7 @@ lbm_status lbm_adjoint_run(lbm_domain* d, int nsteps, int ckpt_every, const doub
   // replayed steps save the intermediates the adjoint steps read
   for (int seg = nseg - 1; seg >= 0 && s == LBM_OK; --seg) {
     const int n0 = seg * K, n1 = std::min(n0 + K, nsteps);
-    s = copy_set(cur_set(d), ckpt0 + (size_t)seg * B.set_bytes);
+    s = restore_state(ckpt0 + (size_t)seg * B.set_bytes);
     for (int n = n0; n < n1 && s == LBM_OK; ++n) {
       d->save_ptr = save_slot(n - n0);
       // the last step of a segment only needs its intermediates
@@ -1420,7 +1463,7 @@ lbm_status lbm_adjoint_run(lbm_domain* d, int nsteps, int ckpt_every, const doub
   }
   d->save_ptr = nullptr;
   // leave the domain at the forward result
-  if (s == LBM_OK) s = copy_set(cur_set(d), final_set);
+  if (s == LBM_OK) s = restore_state(final_set);
   if (s == LBM_OK && d->dp.npatch > 0 && dJdI_host)
     s = check_cuda(d, cudaMemcpyAsync(dJdI_host, B.dJdI, (size_t)d->dp.npatch * 8, cudaMemcpyDeviceToHost,
                                       d->stream),

@@ -354,9 +354,14 @@ class Domain:
 
     def adjoint_step(self, lam, normal_cap: float = 0.0):
         """(d step / d state)^T lam for the current state; lam is a float64
-        array of (q_phase + 34) * N values in get_pdfs order (h, g, f)."""
+        array of (q_phase + 27 + Q_f) * N values in get_pdfs order (h, g,
+        then f for the thermal LB, or the T field, Q_f = 1, for RK2 / RK4)."""
         import numpy as np
-        lam_in = np.ascontiguousarray(lam, dtype=np.float64)
+        lam_in = np.ascontiguousarray(lam, dtype=np.float64).ravel()
+        qf = 1 if self.thermal.startswith("RK") else int(self.thermal[3:])
+        want = (self.q_phase + 27 + qf) * self.nx * self.ny * self.nz
+        if lam_in.size != want:
+            raise ValueError(f"adjoint_step: lam has {lam_in.size} values, the state has {want}")
         out = np.empty_like(lam_in)
         _check("lbm_adjoint_step", lib().lbm_adjoint_step(self._h, ctypes.c_void_p(lam_in.ctypes.data),
                                                           ctypes.c_void_p(out.ctypes.data),
@@ -457,7 +462,7 @@ def capture_objective(intensities, setup, steps: int, ckpt_every: int, target,
     """J(I) = |droplet centroid after ``steps`` steps - target|^2 as a
     differentiable function of the heater-patch intensities I (a 1-D tensor).
 
-    ``setup(I)`` must return an initialised FP64 D3Q7 :class:`Domain` whose
+    ``setup(I)`` must return an initialised FP64 :class:`Domain` whose
     heater patches carry the intensities ``I`` (a list of floats).  The
     forward pass runs the steps through ``Domain.adjoint_run``, which also
     computes dJ/dI with the adjoint kernels; backward returns it scaled by the

@@ -4,11 +4,11 @@ Checks, all in FP64:
   * per step, exact adjoint: <lam, (Phi(s + e d) - Phi(s - e d)) / 2e> =
     <(dPhi/ds)^T lam, d> for random lam and d (walls and periodic, D3Q15 and
     D3Q27 phase field, unequal viscosities, gravity, background gradient,
-    heat sources);
+    heat sources; every energy solver: thermal LB D3Q7/15/19/27, RK2, RK4);
   * the exact gradient dJ/dI of the droplet-capture objective against central
     finite differences of the FP64 *oracle* (independent of the CUDA path) on
-    the 16^3 adjoint workload (40 steps), and against the oracle's exact
-    complex-step derivatives (stored golden values);
+    the 16^3 adjoint workload (40 steps; D3Q7, D3Q19, RK4, RK2), and against
+    the oracle's exact complex-step derivatives (stored golden values);
   * on the full 64^3, 2000-step workload the exact linearisation diverges
     (the interface normal's derivative in far-field tails); the adjoint that
     holds the normal fixed where |4 phi (1 - phi) / xi| > 30 |grad phi| is
@@ -40,45 +40,71 @@ def _with_intensity(w, intensity):
     return w.replace(patches=dataclasses.replace(w.patches, intensity=list(intensity)))
 
 
+def _third(d):
+    """The energy solver's state: f (thermal LB) or the T field (RK)."""
+    return "T" if d.thermal.startswith("RK") else "f"
+
+
 def _state(d):
-    return np.concatenate([d.get_pdfs("h").ravel(), d.get_pdfs("g").ravel(), d.get_pdfs("f").ravel()])
+    return np.concatenate([d.get_pdfs("h").ravel(), d.get_pdfs("g").ravel(), d.get_pdfs(_third(d)).ravel()])
 
 
 def _set_state(d, s, qh, N):
     nh, ng = qh * N, 27 * N
     d.set_pdfs("h", s[:nh].reshape(qh, -1))
     d.set_pdfs("g", s[nh:nh + ng].reshape(27, -1))
-    d.set_pdfs("f", s[nh + ng:].reshape(7, -1))
+    third = _third(d)
+    d.set_pdfs(third, s[nh + ng:].reshape(-1, N) if third == "f" else s[nh + ng:])
 
 
-def _periodic_case(q_phase):
-    w = ragged_workload("D3Q7", q_phase, walls=False, precision="fp64", shape=(12, 10, 8))
+def _periodic_case(q_phase, thermal="D3Q7"):
+    w = ragged_workload(thermal, q_phase, walls=False, precision="fp64", shape=(12, 10, 8))
     return w
 
 
-@pytest.mark.parametrize("case", ["walls_patches_q15", "periodic_q15", "periodic_q27"])
+@pytest.mark.parametrize("case", ["walls_patches_q15", "periodic_q15", "periodic_q27", "walls_patches_q15_f19",
+                                  "periodic_q27_f15", "periodic_q15_f27", "walls_patches_q15_rk4",
+                                  "walls_patches_q27_rk2", "periodic_q15_rk4", "periodic_q15_rk2iso",
+                                  "walls_patches_q15_rk4iso"])
 def test_adjoint_step_dot_product(case):
-    if case == "walls_patches_q15":
+    """Per step: <lam, central difference of the step along d> (Richardson-
+    extrapolated; measured 1e-12 .. 4e-9) equals <adjoint(lam), d> to 1e-8,
+    h on D3Q15 / D3Q27 and
+    the energy equation as the thermal LB on D3Q7 / 15 / 19 / 27 or RK2 / RK4
+    (7-point or isotropic operators; the state then holds the T field)."""
+    tag = case.split("_")[-1]
+    thermal = {"f19": "D3Q19", "f15": "D3Q15", "f27": "D3Q27", "rk4": "RK4", "rk2": "RK2", "rk2iso": "RK2",
+               "rk4iso": "RK4"}.get(tag, "D3Q7")
+    q_phase = 27 if "_q27" in case else 15
+    if case.startswith("walls_patches"):
         w = W.config5(n=16)
+        w = w.replace(thermal=thermal, q_phase=q_phase)
     else:
-        w = _periodic_case(15 if case.endswith("q15") else 27)
+        w = _periodic_case(q_phase, thermal)
+    if tag.endswith("iso"):
+        w = w.replace(params=W.Params(**dict(w.params.__dict__, rk_isotropic_fd=True)))
     d = gpu_domain(w)
     d.step(5)                                   # a state with flow and interface forces
     s = _state(d)
     rng = np.random.default_rng(11)
     lam = rng.standard_normal(s.size)
     dlt = rng.standard_normal(s.size) * (1e-2 * np.abs(s).max())
-    eps = 1e-5
-    out = []
-    for sg in (1.0, -1.0):
-        _set_state(d, s + sg * eps * dlt, w.q_phase, w.cells)
-        d.step(1)
-        out.append(_state(d))
-    lhs = lam @ ((out[0] - out[1]) / (2 * eps))
+    def central(eps):
+        out = []
+        for sg in (1.0, -1.0):
+            _set_state(d, s + sg * eps * dlt, w.q_phase, w.cells)
+            d.step(1)
+            out.append(_state(d))
+        return lam @ ((out[0] - out[1]) / (2 * eps))
+
+    # Richardson extrapolation of the central difference removes its
+    # O(eps^2) truncation error (the step is nonlinear in the state)
+    d1, d2 = central(2e-5), central(1e-5)
+    lhs = (4.0 * d2 - d1) / 3.0
     _set_state(d, s, w.q_phase, w.cells)
     rhs = d.adjoint_step(lam) @ dlt
-    print(case, lhs, rhs, abs(lhs - rhs) / abs(rhs))
-    assert abs(lhs - rhs) <= 1e-7 * abs(rhs), (lhs, rhs)
+    print(case, lhs, rhs, abs(lhs - rhs) / abs(rhs), "plain central difference", abs(d2 - rhs) / abs(rhs))
+    assert abs(lhs - rhs) <= 1e-8 * abs(rhs), (lhs, rhs)
 
 
 def _oracle_J(w, steps):
@@ -92,11 +118,15 @@ def _oracle_J(w, steps):
     return float(((c - np.array(w.target)) ** 2).sum())
 
 
-def test_adjoint_gradient_matches_oracle_finite_differences():
-    """16^3 adjoint workload (4 x 4 patches of 4 x 4 cells, walls), 40 steps:
-    GPU adjoint dJ/dI against central differences (h = 1e-4) of the FP64
-    oracle, every patch."""
+@pytest.mark.parametrize("thermal", ["D3Q7", "D3Q19", "RK4", "RK2"])
+def test_adjoint_gradient_matches_oracle_finite_differences(thermal):
+    """16^3 adjoint workload (4 x 4 patches of 4 x 4 cells, walls), 40 steps,
+    energy equation as the thermal LB on D3Q7 (the workload's) or D3Q19, or
+    RK4 / RK2: GPU adjoint dJ/dI against central differences (h = 1e-4) of
+    the FP64 oracle, every patch."""
     w = W.config5(n=16)
+    if thermal != "D3Q7":
+        w = w.replace(thermal=thermal)
     steps = 40
     d = gpu_domain(w)
     J, g = d.adjoint_run(steps, 10, w.target)
@@ -133,8 +163,11 @@ def test_adjoint_gradient_matches_complex_step_oracle():
     assert err <= 1e-7
 
 
-def test_adjoint_checkpoint_spacing_is_exact():
-    w = W.config5(n=16)
+@pytest.mark.parametrize("thermal", ["D3Q7", "RK4"])
+def test_adjoint_checkpoint_spacing_is_exact(thermal):
+    """Checkpoints every 1, 7 or 40 steps give the same J and gradient bit
+    for bit (with RK the checkpoints carry the T field)."""
+    w = W.config5(n=16).replace(thermal=thermal)
     res = []
     for K in (1, 7, 40):
         d = gpu_domain(w)
