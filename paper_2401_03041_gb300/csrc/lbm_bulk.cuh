@@ -239,13 +239,16 @@ __device__ __forceinline__ typename Store<S>::R abb_wall_value(const DevParams& 
 // the staged h / f boxes of that plane (st), into the interleaved (phi, T)
 // plane pt; items k0, k0 + kstep, ... of the tile.  Ghost planes beyond a z
 // wall mirror phi and take T_g = 2 T_w - T; with an RK energy solver T comes
-// from the stored field.  Planes next to a wall take the bounce-back variant
-// (BOUNCE = true); all other planes run the select-free one.
+// from the stored field (or, for the first item, from *tpre: the caller's
+// value of that field cell, loaded ahead).  Planes next to a wall take the
+// bounce-back variant (BOUNCE = true); all other planes run the select-free
+// one.
 template <class S, int QH, int QF, bool EXT, class G, bool BOUNCE>
 __device__ __forceinline__ void stage_sum_plane_v(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                                                   const S* st, typename PairOf<typename Store<S>::R>::type* pt,
                                                   int p, int pe, bool ghost, bool lo, bool hi, int x0, int y0,
-                                                  int k0, int kstep, int kend) {
+                                                  int k0, int kstep, int kend,
+                                                  const typename Store<S>::R* tpre) {
   using R = typename Store<S>::R;
   using P2 = typename PairOf<R>::type;
   const auto& rp = RP<R>(P);
@@ -295,10 +298,14 @@ __device__ __forceinline__ void stage_sum_plane_v(const DevParams& P, const Step
         T += b ? (-v + (R)(2.0 * weight<QF>(i)) * tw) : v;
       });
     } else {
-      int gx = x0 + hc - 1, gy = y0 + hr - 1;
-      gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
-      gy = gy < 0 ? gy + P.ny : (gy >= P.ny ? gy - P.ny : gy);
-      T = A.T[cell_index(P, gx, gy, pe)];
+      if (tpre && k == k0) {
+        T = *tpre;
+      } else {
+        int gx = x0 + hc - 1, gy = y0 + hr - 1;
+        gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
+        gy = gy < 0 ? gy + P.ny : (gy >= P.ny ? gy - P.ny : gy);
+        T = A.T[cell_index(P, gx, gy, pe)];
+      }
     }
     if constexpr (EXT) {
       if (ghost) T = (R)2 * (p < 0 ? bottom_T() : (R)rp.T_top) - T;
@@ -318,7 +325,7 @@ template <class S, int QH, int QF, bool EXT, class G>
 __device__ __forceinline__ void stage_sum_plane(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                                                 const S* st, typename PairOf<typename Store<S>::R>::type* pt,
                                                 int p, int x0, int y0, int k0, int kstep,
-                                                int kend = G::HPB) {
+                                                int kend = G::HPB, const typename Store<S>::R* tpre = nullptr) {
   int pe = p;
   bool ghost = false;
   if (P.walls) {
@@ -329,9 +336,10 @@ __device__ __forceinline__ void stage_sum_plane(const DevParams& P, const StepPt
   }
   const bool lo = P.walls && pe == 0, hi = P.walls && pe == P.nz - 1;
   if (lo || hi)
-    stage_sum_plane_v<S, QH, QF, EXT, G, true>(P, A, st, pt, p, pe, ghost, lo, hi, x0, y0, k0, kstep, kend);
+    stage_sum_plane_v<S, QH, QF, EXT, G, true>(P, A, st, pt, p, pe, ghost, lo, hi, x0, y0, k0, kstep, kend, tpre);
   else
-    stage_sum_plane_v<S, QH, QF, EXT, G, false>(P, A, st, pt, p, pe, ghost, false, false, x0, y0, k0, kstep, kend);
+    stage_sum_plane_v<S, QH, QF, EXT, G, false>(P, A, st, pt, p, pe, ghost, false, false, x0, y0, k0, kstep, kend,
+                                                tpre);
 }
 
 // EXT: the extensions of the uniform-property model (conductivity ratio,

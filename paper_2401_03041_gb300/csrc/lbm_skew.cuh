@@ -149,9 +149,28 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     mark(3 + g_slot(p), g_par(p));
   };
   auto a_barrier = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(NC) : "memory"); };
-  auto sum_plane = [&](int p, int k0, int kstep, int kend = G::HPB) {
-    stage_sum_plane<S, QH, QF, EXT, G>(P, A, hf_ptr(p), pt_ptr(p), p, x0, y0, k0, kstep, kend);
+  auto sum_plane = [&](int p, int k0, int kstep, int kend = G::HPB, const R* tpre = nullptr) {
+    stage_sum_plane<S, QH, QF, EXT, G>(P, A, hf_ptr(p), pt_ptr(p), p, x0, y0, k0, kstep, kend, tpre);
   };
+  // RK energy solvers: the stored T of the one plane-sum item this thread
+  // takes in the main loop (g role: item cidx < SUM_A; stencil role: item
+  // SUM_A + cidx), read one plane ahead so that the load's latency is
+  // covered by a plane's work.  p stays within z0 - 1 .. z1, like the sums.
+  const int k_me = role_g ? cidx : L::SUM_A + cidx;
+  const bool t_item_valid = role_g ? cidx < L::SUM_A : L::SUM_A + cidx < G::HPB;
+  auto t_item = [&](int p) -> R {
+    if (!t_item_valid) return (R)0;
+    int pe;
+    if (P.walls) pe = p < 0 ? 0 : (p >= P.nz ? P.nz - 1 : p);
+    else pe = p < 0 ? p + P.nz : (p >= P.nz ? p - P.nz : p);
+    int gx = x0 + k_me % G::HXB - 1, gy = y0 + k_me / G::HXB - 1;
+    gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
+    gy = gy < 0 ? gy + P.ny : (gy >= P.ny ? gy - P.ny : gy);
+    return A.T[cell_index(P, gx, gy, pe)];
+  };
+  R t_cur = 0, t_next = 0;
+  if constexpr (QF == 0)
+    if (z0 + 2 <= z1) t_cur = t_item(z0 + 2);
   // producer / consumer barrier of a plane's phi / T sum: the g role arrives
   // once its share is written, the stencil role waits for every share
   auto sum_arrive = [&]() { asm volatile("bar.arrive 3, %0;" ::"r"(NT) : "memory"); };
@@ -328,11 +347,13 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     // h/f boxes of plane z + 3 into the slot of plane z (its collisions were
     // done in the previous iteration)
     if (z + 3 <= z1) issue_hf(z + 3, 0);
+    if constexpr (QF == 0)
+      if (z + 3 <= z1) t_next = t_item(z + 3);
     if (role_g) {
       // the g role's share of phi / T of plane z + 2, first
       if (z + 2 <= z1) {
         ok = ok && wait_slot(hf_slot(z + 2), hf_par(z + 2));
-        if (ok) sum_plane(z + 2, cidx, NC, L::SUM_A);
+        if (ok) sum_plane(z + 2, cidx, NC, L::SUM_A, QF == 0 ? &t_cur : nullptr);
       }
       sum_arrive();
       if (active && (mode & MODE_COLLIDE)) g_collide(z, mA0);
@@ -352,7 +373,7 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     } else {
       if (z + 2 <= z1) {
         ok = ok && wait_slot(hf_slot(z + 2), hf_par(z + 2));
-        if (ok) sum_plane(z + 2, L::SUM_A + cidx, NC);
+        if (ok) sum_plane(z + 2, L::SUM_A + cidx, NC, G::HPB, QF == 0 ? &t_cur : nullptr);
       }
       sum_wait();   // phi / T of plane z + 2 complete (both shares)
       if (ok && z + 1 < z1 && active) {
@@ -360,6 +381,7 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
         b_collide(z + 1);
       }
     }
+    if constexpr (QF == 0) t_cur = t_next;
     if (__syncthreads_or(!ok)) { ok = false; break; }
   }
 
