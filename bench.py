@@ -602,7 +602,8 @@ def main():
                         "mlups": job_mlups(wa.cells, nst, world, asecs), "step_ms": asecs / nst * 1e3,
                         "kernels_ms": aker * 1e3 if aker else None,
                         "frac": bpa * wa.cells / aker / 1e9 / peak_a if aker else None,
-                        "what": "(phi, T) pass + in-place step (two launches per step); frac from the "
+                        "what": "(phi, T) pass + in-place step (+ ghost refresh before and fold after "
+                                "the steps from even levels), kernels_ms per step; frac from the "
                                 "algorithmic bytes of the two-grid step"})
             da.close()
             del da

@@ -287,12 +287,17 @@ lbm_status lbm_get_level(lbm_domain* dom, int64_t* level);
  * LBM_ERR_TIMEOUT if the work has not finished after timeout_ms. */
 lbm_status lbm_synchronize(lbm_domain* dom, int timeout_ms);
 
-/* Launch configuration of the domain's step kernel: info[0] = 1 for the
- * bulk kernel (PDF boxes staged in shared memory by tensor-TMA copies), 0 for
- * the generic kernel; info[1..3] = grid x, y, z; info[4] = planes per CTA;
- * info[5] = dynamic shared memory bytes.  info holds 6 int32 values.  The
- * environment variable LBM_KERNEL=generic, read at creation, forces the
- * generic kernel; LBM_ZCHUNK=<planes> sets the planes per CTA.
+/* Launch configuration of the domain's step kernel: info[0] = 0 for the
+ * generic kernel, 1 for the bulk kernel (PDF boxes staged in shared memory by
+ * tensor-TMA copies), 2 for the skewed kernel (the same staging, the two
+ * threads of a cell one plane apart), 3 for the in-place layout on the
+ * generic tiles, 4 for the in-place layout on the skewed kernel's tiles (the
+ * uniform-property model; other parameters run it on the generic tiles);
+ * info[1..3] = grid x, y, z (tile counts and z-chunks); info[4] = planes per
+ * CTA; info[5] = dynamic shared memory bytes.  info holds 6 int32 values.
+ * The environment variable LBM_KERNEL=generic, read at creation, forces the
+ * generic kernels (two-grid and in-place), LBM_KERNEL=bulk the bulk kernel;
+ * LBM_ZCHUNK=<planes> sets the planes per CTA.
  * LBM_TEST_STALL=1, read at creation, tests failure detection: the bulk
  * kernel's first copy wait of every CTA then runs out (after about 2 s per
  * wait, no fault), the kernel raises the domain's error flag and returns, and

@@ -122,6 +122,28 @@ static size_t skew_bytes_qf(int qf) {
   }
 }
 
+template <class S, int QH, int QF>
+static constexpr size_t aa_skew_bytes_one() {
+  return skew_fits<S, QH, QF, 1>() ? SkewSmem<S, QH, QF, 1>::bytes : 0;
+}
+
+template <class S, int QH>
+static size_t aa_skew_bytes_qf(int qf) {
+  switch (qf) {
+    case 0: return aa_skew_bytes_one<S, QH, 0>();
+    case 7: return aa_skew_bytes_one<S, QH, 7>();
+    case 15: return aa_skew_bytes_one<S, QH, 15>();
+    case 19: return aa_skew_bytes_one<S, QH, 19>();
+    default: return aa_skew_bytes_one<S, QH, 27>();
+  }
+}
+
+size_t aa_skew_smem_bytes(int prec, int qh, int qf) {
+  if (prec == 0) return qh == 15 ? aa_skew_bytes_qf<double, 15>(qf) : aa_skew_bytes_qf<double, 27>(qf);
+  if (prec == 1) return qh == 15 ? aa_skew_bytes_qf<float, 15>(qf) : aa_skew_bytes_qf<float, 27>(qf);
+  return qh == 15 ? aa_skew_bytes_qf<__half, 15>(qf) : aa_skew_bytes_qf<__half, 27>(qf);
+}
+
 size_t skew_smem_bytes(int prec, int qh, int qf) {
   if (prec == 0) return qh == 15 ? skew_bytes_qf<double, 15>(qf) : skew_bytes_qf<double, 27>(qf);
   if (prec == 1) return qh == 15 ? skew_bytes_qf<float, 15>(qf) : skew_bytes_qf<float, 27>(qf);

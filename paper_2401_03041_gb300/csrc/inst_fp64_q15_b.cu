@@ -1,0 +1,6 @@
+// Step/init kernel instantiations: storage double, phase-field D3Q15;
+// energy solvers D3Q19, D3Q27.
+#define LBM_S double
+#define LBM_QH 15
+#define LBM_QF_PART 1
+#include "inst_step.cuh"

@@ -1,6 +1,7 @@
 // inst_step.cuh - explicit instantiations of the step-kernel launchers for one
 // storage type LBM_S and one phase-field stencil LBM_QH (set by the including
-// translation unit), for every energy solver (QF = 0: RK; 7/15/19/27: LB).
+// translation unit), for the energy solvers of part LBM_QF_PART (QF = 0: RK;
+// 7/15/19/27: LB).
 #pragma once
 
 #include "launchers.h"
@@ -31,10 +32,10 @@ void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
         }
         if (P.alpha_ratio || P.tw_waves || P.wall_ext || P.sub)
           step_skew_kernel<S, QH, QF, true><<<bgrid, SkewSmem<S, QH, QF>::G::NTHR, sbytes, st>>>(
-              P, A, maps.h, maps.g, maps.f, sched, mode);
+              P, A, maps.h, maps.g, maps.f, sched, mode, nullptr);
         else
           step_skew_kernel<S, QH, QF, false><<<bgrid, SkewSmem<S, QH, QF>::G::NTHR, sbytes, st>>>(
-              P, A, maps.h, maps.g, maps.f, sched, mode);
+              P, A, maps.h, maps.g, maps.f, sched, mode, nullptr);
         return;
       }
     }
@@ -71,6 +72,39 @@ void launch_aa_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>&
 }
 
 template <class S, int QH, int QF>
+void launch_aa_tiled(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A, const TMaps& maps,
+                     void* phiT, int nb, const BulkSched& sched, int mode, cudaStream_t st) {
+  using R = typename Store<S>::R;
+  using P2 = typename PairOf<R>::type;
+  if constexpr (skew_fits<S, QH, QF, 1>()) {
+    constexpr size_t sbytes = SkewSmem<S, QH, QF, 1>::bytes;
+    constexpr int nthr = SkewSmem<S, QH, QF, 1>::G::NTHR;
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(step_skew_kernel<S, QH, QF, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sbytes);
+      cudaFuncSetAttribute(step_skew_kernel<S, QH, QF, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sbytes);
+      attr_set = true;
+    }
+    const long long blocks = (P.N + 255) / 256;
+    const int mgrid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
+    aa_moments_kernel<S, QH, QF><<<mgrid, 256, 0, st>>>(P, A.h_src, A.f_src, A.T, nb, (P2*)phiT);
+    S* set = const_cast<S*>(A.h_src);
+    const dim3 bgrid((unsigned)bulk_sched_blocks(sched));
+    if (nb) {
+      launch_ghost_fill<S>(P, set, QH + 27 + QF, st);
+      step_skew_kernel<S, QH, QF, false, 2><<<bgrid, nthr, sbytes, st>>>(P, A, maps.h, maps.g, maps.f, sched, mode,
+                                                                          (const P2*)phiT);
+      aa_fold_kernel<S, QH, QF><<<dim3((P.nx + P.ny + 127) / 128, P.nz, QH + 27 + QF), 128, 0, st>>>(P, set);
+    } else {
+      step_skew_kernel<S, QH, QF, false, 1><<<bgrid, nthr, sbytes, st>>>(P, A, maps.h, maps.g, maps.f, sched, mode,
+                                                                          (const P2*)phiT);
+    }
+  }
+}
+
+template <class S, int QH, int QF>
 void launch_init(const DevParams& P, const double* drops, int nd, S* h, S* g, S* f,
                  typename Store<S>::R* T, cudaStream_t st) {
   const dim3 grid((P.nx + kInitTX - 1) / kInitTX, (P.ny + kInitTY - 1) / kInitTY,
@@ -86,13 +120,23 @@ void launch_init(const DevParams& P, const double* drops, int nd, S* h, S* g, S*
   template void launch_aa_step<LBM_S, LBM_QH, QF>(const DevParams&,                           \
                                                   const StepPtrs<LBM_S, Store<LBM_S>::R>&,    \
                                                   void*, int, dim3, int, int, cudaStream_t);  \
+  template void launch_aa_tiled<LBM_S, LBM_QH, QF>(const DevParams&,                          \
+                                                   const StepPtrs<LBM_S, Store<LBM_S>::R>&,   \
+                                                   const TMaps&, void*, int, const BulkSched&, \
+                                                   int, cudaStream_t);                        \
   template void launch_init<LBM_S, LBM_QH, QF>(const DevParams&, const double*, int, LBM_S*,  \
                                                LBM_S*, LBM_S*, Store<LBM_S>::R*, cudaStream_t);
+// LBM_QF_PART (set by the including unit) splits the energy solvers over two
+// translation units so that they compile in parallel: 0 = RK, D3Q7, D3Q15;
+// 1 = D3Q19, D3Q27.
+#if LBM_QF_PART == 0
 LBM_INST(0)
 LBM_INST(7)
 LBM_INST(15)
+#else
 LBM_INST(19)
 LBM_INST(27)
+#endif
 #undef LBM_INST
 
 }  // namespace lbm

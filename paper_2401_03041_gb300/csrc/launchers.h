@@ -33,6 +33,7 @@ void launch_ghost_fill(const DevParams& P, void* buf, int nq, cudaStream_t st);
 // and the largest a CTA may use; also its tile height.
 size_t bulk_smem_bytes(int prec, int qh, int qf);
 size_t skew_smem_bytes(int prec, int qh, int qf);   // 0: the skewed layout does not fit
+size_t aa_skew_smem_bytes(int prec, int qh, int qf);   // the same for its in-place variant
 int bulk_tile_rows(int prec, int qh, int qf);
 int bulk_tile_cols(int prec);
 int bulk_box_cols(int prec);   // staged row length W of the bulk kernel
@@ -43,6 +44,12 @@ constexpr size_t kMaxDynSmem = 232448;
 template <class S, int QH, int QF>
 void launch_aa_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A, void* phiT, int nb,
                     dim3 grid, int zchunk, int mode, cudaStream_t st);
+// The same on the skewed kernel's tensor-TMA tiles (maps: TYB-row boxes over
+// the one set): (phi, T) pass; from an even level the periodic ghosts are
+// refreshed first and folded back after the step.
+template <class S, int QH, int QF>
+void launch_aa_tiled(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A, const TMaps& maps,
+                     void* phiT, int nb, const BulkSched& sched, int mode, cudaStream_t st);
 template <class S>
 void launch_aa_swap(const DevParams& P, int Q, S* base, cudaStream_t st);
 template <class S>

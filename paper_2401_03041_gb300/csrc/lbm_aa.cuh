@@ -272,4 +272,5 @@ __global__ void f64_to_aa_kernel(const DevParams P, const double* __restrict__ s
   }
 }
 
+
 }  // namespace lbm

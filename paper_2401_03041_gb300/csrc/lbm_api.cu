@@ -232,6 +232,8 @@ struct lbm_domain {
   bool owns_ws;
   Layout L;
   Geometry geo;
+  Geometry geo_aa{};     // in-place layout: the tiled kernels' geometry (bulk == 2 when they apply)
+  int diag_nblocks = 0;  // CTAs of the last step launch (diagnostics partials)
   bool aa = false;  // in-place (AA) layout
   int sms;  // multiprocessors of the device (launch geometry)
   int cur;
@@ -322,25 +324,42 @@ void step_qf(lbm_domain* d, const StepPtrs<S, typename Store<S>::R>& A, int mode
 
 template <class S>
 void step_launch(lbm_domain* d, const StepPtrs<S, typename Store<S>::R>& A, int mode) {
+  d->diag_nblocks = d->geo.nblocks;
   if (d->qh == 15) step_qf<S, 15>(d, A, mode);
   else step_qf<S, 27>(d, A, mode);
 }
 
 // In-place layout: (phi, T) of the level, then the step (gathers from the
-// neighbours when the level is even, locally when it is odd).
+// neighbours when the level is even, locally when it is odd), on the tiled
+// kernel where it applies (the uniform-property model) and on the generic
+// tiles otherwise.
+bool aa_tiled(const lbm_domain* d) {
+  const DevParams& q = d->dp;
+  return d->aa && d->geo_aa.bulk == 2 && !(q.alpha_ratio || q.tw_waves || q.wall_ext || q.sub || q.rho_ratio);
+}
+
 template <class S>
 void aa_launch(lbm_domain* d, const StepPtrs<S, typename Store<S>::R>& A, int mode) {
   using R = typename Store<S>::R;
   const int nb = (d->level & 1) == 0 ? 1 : 0;
   void* phiT = at(d, d->L.phiT);
+  const bool tiled = aa_tiled(d);
+  d->diag_nblocks = tiled ? d->geo_aa.nblocks : d->geo.nblocks;
   auto qf = [&](auto qh_tag) {
     constexpr int QH = decltype(qh_tag)::value;
+    auto go = [&](auto qf_tag) {
+      constexpr int QF = decltype(qf_tag)::value;
+      if (tiled)
+        launch_aa_tiled<S, QH, QF>(d->dp, A, d->maps[0], phiT, nb, d->geo_aa.sched, mode, d->stream);
+      else
+        launch_aa_step<S, QH, QF>(d->dp, A, phiT, nb, d->geo.grid, d->geo.zchunk, mode, d->stream);
+    };
     switch (d->qf) {
-      case 0: launch_aa_step<S, QH, 0>(d->dp, A, phiT, nb, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
-      case 7: launch_aa_step<S, QH, 7>(d->dp, A, phiT, nb, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
-      case 15: launch_aa_step<S, QH, 15>(d->dp, A, phiT, nb, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
-      case 19: launch_aa_step<S, QH, 19>(d->dp, A, phiT, nb, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
-      default: launch_aa_step<S, QH, 27>(d->dp, A, phiT, nb, d->geo.grid, d->geo.zchunk, mode, d->stream); break;
+      case 0: go(std::integral_constant<int, 0>{}); break;
+      case 7: go(std::integral_constant<int, 7>{}); break;
+      case 15: go(std::integral_constant<int, 15>{}); break;
+      case 19: go(std::integral_constant<int, 19>{}); break;
+      default: go(std::integral_constant<int, 27>{}); break;
     }
   };
   (void)sizeof(R);
@@ -421,7 +440,7 @@ lbm_status check_error_flag(lbm_domain* d) {
 }
 
 lbm_status finish_diag(lbm_domain* d, long long level, lbm_diag* out) {
-  launch_diag_finalize((const double*)at(d, d->L.partials), d->geo.nblocks,
+  launch_diag_finalize((const double*)at(d, d->L.partials), d->diag_nblocks,
                        (double*)at(d, d->L.diag), d->stream);
   lbm_status s = check_launch(d, "diagnostics reduction");
   if (s != LBM_OK) return s;
@@ -575,6 +594,17 @@ bool make_map(CUtensorMap* m, void* base, lbm_precision prec, const DevParams& P
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// In-place layout: maps over the one set, every box the tile's own rows.
+bool make_maps_aa(lbm_domain* d) {
+  const int w = bulk_box_cols((int)d->prec), rows = bulk_tile_rows((int)d->prec, d->qh, d->qf);
+  TMaps& t = d->maps[0];
+  if (!make_map(&t.h, at(d, d->L.h[0]), d->prec, d->dp, d->qh, w, rows)) return false;
+  if (!make_map(&t.g, at(d, d->L.g[0]), d->prec, d->dp, 27, w, rows)) return false;
+  if (d->qf > 0) return make_map(&t.f, at(d, d->L.f[0]), d->prec, d->dp, d->qf, w, rows);
+  t.f = t.h;  // unused with an RK energy solver
+  return true;
+}
+
 bool make_maps(lbm_domain* d) {
   const int w = bulk_box_cols((int)d->prec), rows = bulk_tile_rows((int)d->prec, d->qh, d->qf);
   for (int k = 0; k < 2; ++k) {
@@ -665,8 +695,17 @@ lbm_status lbm_create_domain_layout(int nx, int ny, int nz, lbm_precision prec, 
     }
     d->sms = sms;
   }
-  // the in-place layout runs its own kernels on the generic kernel's tiles
+  // the in-place layout runs its own kernels: on the skewed kernel's tiles
+  // where they fit (geo_aa), else on the generic kernel's (geo)
   d->geo = geometry(nx, ny, nz, prec, q_phase, thermal_q(thermal), d->sms, !aa);
+  d->diag_nblocks = d->geo.nblocks;
+  if (aa) {
+    const size_t ab = aa_skew_smem_bytes((int)prec, q_phase, thermal_q(thermal));
+    if (bulk_ok(nx, ny, prec, q_phase, thermal_q(thermal)) && ab > 0 && ab <= kMaxDynSmem) {
+      d->geo_aa = geometry(nx, ny, nz, prec, q_phase, thermal_q(thermal), d->sms, true);
+      d->geo_aa.bulk = 2;
+    }
+  }
   d->sticky = LBM_OK;
   if (const char* env = std::getenv("LBM_TEST_STALL")) d->test_stall = std::atoi(env) != 0;
   lbm_default_params(&d->params);
@@ -690,7 +729,9 @@ lbm_status lbm_create_domain_layout(int nx, int ny, int nz, lbm_precision prec, 
   if (d->geo.bulk && !make_maps(d)) {
     // no tensor-map support: run the generic kernel
     d->geo = geometry(nx, ny, nz, prec, q_phase, thermal_q(thermal), d->sms, false);
+    d->diag_nblocks = d->geo.nblocks;
   }
+  if (d->geo_aa.bulk && !make_maps_aa(d)) d->geo_aa.bulk = 0;
   {
     const cudaError_t e = cudaMemsetAsync(at(d, L.errflag), 0, sizeof(int), d->stream);
     if (e != cudaSuccess) {
@@ -1230,14 +1271,18 @@ lbm_status lbm_unpack_halo_x(lbm_domain* d, int x0, int width, const void* src_d
 
 lbm_status lbm_kernel_info(lbm_domain* d, int32_t* info) {
   if (!d || !info) return fail(LBM_ERR_ARG, "null argument");
-  info[0] = d->aa ? 3 : d->geo.bulk;
-  info[1] = (int32_t)d->geo.grid.x;
-  info[2] = (int32_t)d->geo.grid.y;
-  info[3] = (int32_t)d->geo.grid.z;
-  info[4] = d->geo.zchunk;
-  info[5] = d->geo.bulk == 2   ? (int32_t)skew_smem_bytes((int)d->prec, d->qh, d->qf)
-            : d->geo.bulk == 1 ? (int32_t)bulk_smem_bytes((int)d->prec, d->qh, d->qf)
-                               : 0;
+  const bool tiled_aa = aa_tiled(d);
+  const Geometry& g = tiled_aa ? d->geo_aa : d->geo;
+  info[0] = d->aa ? (tiled_aa ? 4 : 3) : d->geo.bulk;
+  info[1] = (int32_t)g.grid.x;
+  info[2] = (int32_t)g.grid.y;
+  info[3] = (int32_t)g.grid.z;
+  info[4] = g.zchunk;
+  info[5] = tiled_aa             ? (int32_t)aa_skew_smem_bytes((int)d->prec, d->qh, d->qf)
+            : d->aa              ? 0
+            : d->geo.bulk == 2   ? (int32_t)skew_smem_bytes((int)d->prec, d->qh, d->qf)
+            : d->geo.bulk == 1   ? (int32_t)bulk_smem_bytes((int)d->prec, d->qh, d->qf)
+                                 : 0;
   return LBM_OK;
 }
 

@@ -168,7 +168,10 @@ using BulkSmem = BulkSmemT<S, QH, QF, (BulkSmemT<S, QH, QF, 4>::bytes <= 232448 
 //                h (map mh), QH..QH+QF-1 from f (map mf).
 //   KIND 1 (G):  rows y0 .. y0 + TYB - 1 of plane p; g directions (map mg).
 // Tensor coordinates are those of the padded arrays: (x + GX, y + GY, z, q).
-template <class S, class G, int QH, int QF, int KIND>
+// AAM selects the in-place layout's gathers (0: two grids; 1: odd level, all
+// local; 2: even level, F[opp(i)] from x - c_i); its h/f boxes hold rows
+// y0 .. y0 + TYB - 1 only (maps with TYB-row boxes).
+template <class S, class G, int QH, int QF, int KIND, int AAM = 0>
 __device__ __forceinline__ void issue_stage(const DevParams& P, const CUtensorMap* mh,
                                             const CUtensorMap* mg, const CUtensorMap* mf,
                                             S* dst_stage, uint64_t* bar, int p, int x0, int y0,
@@ -195,21 +198,35 @@ __device__ __forceinline__ void issue_stage(const DevParams& P, const CUtensorMa
     q = d - QH;
     k27 = QF == 15 ? rt_to27<15>(q) : q;   // Q7/Q19/Q27 are prefixes of the D3Q27 order
   }
-  const int ylo = y0 - (KIND == 0 ? 1 : 0);
-  int zz = pe - kDir27.c[k27][2], yy;
-  if (P.walls && (zz < 0 || zz >= P.nz)) {
-    // bounce-back: opposite direction, same cells
+  // the array of the opposite direction
+  auto opp_q = [&]() {
     const int o27 = kDir27.opp[k27];
-    if (KIND == 1) q = o27;
-    else if (d < QH) q = rt_from27<QH>(o27);
-    else q = QF == 15 ? rt_from27<15>(o27) : o27;
+    if (KIND == 1) return o27;
+    if (d < QH) return rt_from27<QH>(o27);
+    return QF == 15 ? rt_from27<15>(o27) : o27;
+  };
+  // in place (AAM != 0) the boxes hold the tile's own rows only; the two-grid
+  // h/f boxes add one halo row on each side
+  const int ylo = y0 - ((KIND == 0 && AAM == 0) ? 1 : 0);
+  int zz = pe - kDir27.c[k27][2], yy;
+  if (AAM == 1) {
+    // in place, odd level: every population is gathered from its own cell
+    zz = pe;
+    yy = ylo;
+  } else if (P.walls && (zz < 0 || zz >= P.nz)) {
+    // source beyond a wall.  Two grids: the opposite direction of the same
+    // cells (bounce-back).  In place, even level: the direction's own array
+    // at the same cells, where the previous step left the reflected value.
+    if (AAM == 0) q = opp_q();
     zz = pe;
     yy = ylo;
   } else {
     zz = zz < 0 ? zz + P.nz : (zz >= P.nz ? zz - P.nz : zz);
     yy = ylo - kDir27.c[k27][1];
+    // in place, even level: f*_i(x) = F[opp(i)](x - c_i)
+    if (AAM == 2) q = opp_q();
   }
-  S* dst = dst_stage + (size_t)d * (KIND == 0 ? G::HFB : G::GB);
+  S* dst = dst_stage + (size_t)d * ((KIND == 0 && AAM == 0) ? G::HFB : G::GB);
   tma_load_4d(dst, map, x0 - G::GXP + P.GX, yy + P.GY, zz, q, bar);
 }
 

@@ -26,6 +26,16 @@
 //
 // The density-ratio forces need the moments of g and the stencil of the same
 // plane in one place, so a lattice with rho_L != rho_H runs the bulk kernel.
+//
+// In-place layout (AAM != 0; lbm_aa.cuh has the AA pattern): one PDF set is
+// gathered and overwritten.  The boxes then hold the tile's own rows only
+// (each slot is read and written by exactly one cell within a step, and a
+// halo row of another tile may already hold that tile's new values), and phi
+// / T of the halo tile come from the level's (phi, T) field instead of the
+// staged boxes.  AAM = 1, odd level: f*_i(x) = F[i](x), new values to
+// F[opp(i)](x).  AAM = 2, even level: f*_i(x) = F[opp(i)](x - c_i), new values
+// to F[i](x + c_i); x + c_i may be a periodic ghost column or row, which the
+// host folds back into the interior after the step (aa_fold_kernel).
 // Every wait is bounded (about 2 s); on a timeout the CTA raises the domain's
 // error flag, drains its outstanding copies (bounded too) and returns.
 #pragma once
@@ -34,12 +44,14 @@
 
 namespace lbm {
 
-template <class S, int QH, int QF, int TYB_>
+template <class S, int QH, int QF, int TYB_, int AAM = 0>
 struct SkewSmemT {
   using R = typename Store<S>::R;
   using G = BulkGeom<S, TYB_>;
   static constexpr int NHF = QH + QF;
-  static constexpr size_t hf_stage = (size_t)NHF * G::HFB;   // elements
+  // h/f box pitch: halo rows included (two grids) or the tile's rows (in place)
+  static constexpr int HFP = AAM ? G::GB : G::HFB;
+  static constexpr size_t hf_stage = (size_t)NHF * HFP;   // elements
   static constexpr size_t g_stage = (size_t)27 * G::GB;
   // exchange slots per cell and plane parity: phi, a (3) from B; j (3), p* from A
   static constexpr int NX = 8;
@@ -55,7 +67,7 @@ struct SkewSmemT {
   static constexpr size_t off_bar = (off_x + 2 * (size_t)NX * G::NT * sizeof(R) + 15) & ~size_t(15);
   // + 128: the start of the dynamic shared memory is aligned at run time
   static constexpr size_t bytes = off_bar + 5 * sizeof(uint64_t) + 128;
-  static constexpr uint32_t hf_tx = (uint32_t)((size_t)NHF * G::W * (G::TYB + 2) * sizeof(S));
+  static constexpr uint32_t hf_tx = (uint32_t)((size_t)NHF * G::W * (AAM ? G::TYB : G::TYB + 2) * sizeof(S));
   static constexpr uint32_t g_tx = (uint32_t)((size_t)27 * G::W * G::TYB * sizeof(S));
   // halo items of a plane's phi / T sum taken by the g role: the first SUM_A
   // of the tile's HPB items, as many as leave one item per stencil-role
@@ -67,21 +79,47 @@ struct SkewSmemT {
 // The skewed kernel uses the bulk kernel's tile (one launch geometry for
 // both, so that a lattice can switch between them); it is available where its
 // layout fits at that tile height.
-template <class S, int QH, int QF>
-using SkewSmem = SkewSmemT<S, QH, QF, BulkSmem<S, QH, QF>::G::TYB>;
+template <class S, int QH, int QF, int AAM = 0>
+using SkewSmem = SkewSmemT<S, QH, QF, BulkSmem<S, QH, QF>::G::TYB, AAM>;
 
-template <class S, int QH, int QF>
+template <class S, int QH, int QF, int AAM = 0>
 constexpr bool skew_fits() {
-  return SkewSmem<S, QH, QF>::bytes <= 232448;
+  return SkewSmem<S, QH, QF, AAM>::bytes <= 232448;
 }
 
-template <class S, int QH, int QF, bool EXT>
-__global__ void __launch_bounds__(SkewSmem<S, QH, QF>::G::NTHR, 1)
+// In-place store of the new population of direction I (stencil Q) of the cell
+// at pcell: odd level F[opp(I)](x); even level F[I](x + c_I), or F[opp(I)](x)
+// where x + c_I lies beyond a z wall (lo: the cell is on plane 0, hi: on
+// plane nz - 1).  off_m / off_p: element offsets to the planes below / above
+// (periodic wrap included); x + c_I and y + c_I may be ghost positions.
+template <class S, int Q, int I, int AAM, bool BOUNCE>
+__device__ __forceinline__ void aa_store(const DevParams& P, S* base, size_t pcell, long long off_m,
+                                         long long off_p, bool lo, bool hi, typename Store<S>::R v) {
+  constexpr int o = opp<Q>(I);
+  if constexpr (AAM == 1) {
+    Store<S>::st(base + (size_t)o * P.Np + pcell, v);
+  } else {
+    constexpr int ex = cx<Q>(I), ey = cy<Q>(I), ez = cz<Q>(I);
+    if constexpr (BOUNCE && ez != 0) {
+      if ((ez < 0 && lo) || (ez > 0 && hi)) {
+        Store<S>::st(base + (size_t)o * P.Np + pcell, v);
+        return;
+      }
+    }
+    const long long off = (ez < 0 ? off_m : (ez > 0 ? off_p : 0LL)) + (long long)ey * P.NXP + ex;
+    Store<S>::st(base + (size_t)I * P.Np + (size_t)((long long)pcell + off), v);
+  }
+}
+
+template <class S, int QH, int QF, bool EXT, int AAM = 0>
+__global__ void __launch_bounds__(SkewSmem<S, QH, QF, AAM>::G::NTHR, 1)
 step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
                  const __grid_constant__ CUtensorMap mh, const __grid_constant__ CUtensorMap mg,
-                 const __grid_constant__ CUtensorMap mf, const BulkSched sched, int mode) {
+                 const __grid_constant__ CUtensorMap mf, const BulkSched sched, int mode,
+                 const typename PairOf<typename Store<S>::R>::type* __restrict__ aa_phiT) {
+  static_assert(AAM == 0 || !EXT, "the in-place kernels cover the uniform-property model");
   using R = typename Store<S>::R;
-  using L = SkewSmem<S, QH, QF>;
+  using L = SkewSmem<S, QH, QF, AAM>;
   using G = typename L::G;
   using P2 = typename PairOf<R>::type;
   constexpr int NC = G::NT;       // cells per CTA
@@ -139,18 +177,41 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
   // HF(p) into its slot, boxes spread over all warps
   auto issue_hf = [&](int p, uint32_t extra) {
     if (tid == 0) mbar_expect_tx(&bar[hf_slot(p)], L::hf_tx + extra);
-    issue_stage<S, G, QH, QF, 0>(P, &mh, &mg, &mf, hf_ptr(p), &bar[hf_slot(p)], p, x0, y0, tid);
+    issue_stage<S, G, QH, QF, 0, AAM>(P, &mh, &mg, &mf, hf_ptr(p), &bar[hf_slot(p)], p, x0, y0, tid);
     mark(hf_slot(p), hf_par(p));
   };
   // G(p) into its slot, boxes spread over the g role's warps (g role only)
   auto issue_g = [&](int p) {
     if (tid == 0) mbar_expect_tx(&bar[3 + g_slot(p)], L::g_tx);
-    issue_stage<S, G, QH, QF, 1>(P, &mh, &mg, &mf, g_ptr(p), &bar[3 + g_slot(p)], p, x0, y0, tid, NC / 32);
+    issue_stage<S, G, QH, QF, 1, AAM>(P, &mh, &mg, &mf, g_ptr(p), &bar[3 + g_slot(p)], p, x0, y0, cidx, NC / 32);
     mark(3 + g_slot(p), g_par(p));
   };
   auto a_barrier = [&]() { asm volatile("bar.sync 1, %0;" ::"r"(NC) : "memory"); };
-  auto sum_plane = [&](int p, int k0, int kstep, int kend = G::HPB, const R* tpre = nullptr) {
-    stage_sum_plane<S, QH, QF, EXT, G>(P, A, hf_ptr(p), pt_ptr(p), p, x0, y0, k0, kstep, kend, tpre);
+  // in place: (phi, T) of halo-tile item k of plane p as stored in the
+  // level's field (raw), and the value the plane takes (ghost planes beyond a
+  // wall: phi mirrored, T_g = 2 T_w - T)
+  auto field_raw = [&](int p, int k) -> P2 {
+    int pe;
+    if (P.walls) pe = p < 0 ? 0 : (p >= P.nz ? P.nz - 1 : p);
+    else pe = p < 0 ? p + P.nz : (p >= P.nz ? p - P.nz : p);
+    int gx = x0 + k % G::HXB - 1, gy = y0 + k / G::HXB - 1;
+    gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
+    gy = gy < 0 ? gy + P.ny : (gy >= P.ny ? gy - P.ny : gy);
+    return aa_phiT[cell_index(P, gx, gy, pe)];
+  };
+  auto field_put = [&](int p, int k, P2 v) {
+    if (P.walls && (p < 0 || p >= P.nz)) v.y = (R)2 * (R)(p < 0 ? RP<R>(P).T_bottom : RP<R>(P).T_top) - v.y;
+    pt_ptr(p)[k] = v;
+  };
+  // the plane's (phi, T) pairs, items k0, k0 + kstep, .. < kend (tpre: the
+  // value of the first item, loaded ahead)
+  auto sum_plane = [&](int p, int k0, int kstep, int kend = G::HPB, const R* tpre = nullptr,
+                       const P2* fpre = nullptr) {
+    if constexpr (AAM != 0) {
+      for (int k = k0; k < kend; k += kstep) field_put(p, k, (fpre && k == k0) ? *fpre : field_raw(p, k));
+    } else {
+      stage_sum_plane<S, QH, QF, EXT, G>(P, A, hf_ptr(p), pt_ptr(p), p, x0, y0, k0, kstep, kend, tpre);
+    }
   };
   // RK energy solvers: the stored T of the one plane-sum item this thread
   // takes in the main loop (g role: item cidx < SUM_A; stencil role: item
@@ -169,8 +230,12 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     return A.T[cell_index(P, gx, gy, pe)];
   };
   R t_cur = 0, t_next = 0;
-  if constexpr (QF == 0)
+  P2 f_cur{}, f_next{};   // in place: the item's (phi, T), one plane ahead
+  if constexpr (AAM != 0) {
+    if (z0 + 2 <= z1 && t_item_valid) f_cur = field_raw(z0 + 2, k_me);
+  } else if constexpr (QF == 0) {
     if (z0 + 2 <= z1) t_cur = t_item(z0 + 2);
+  }
   // producer / consumer barrier of a plane's phi / T sum: the g role arrives
   // once its share is written, the stencil role waits for every share
   auto sum_arrive = [&]() { asm volatile("bar.arrive 3, %0;" ::"r"(NT) : "memory"); };
@@ -184,7 +249,7 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
       constexpr bool BOUNCE = decltype(btag)::value;
       auto getg = [&](auto I) {
         constexpr int i = decltype(I)::value;
-        const bool b = BOUNCE && ((cz<27>(i) > 0 && lo) || (cz<27>(i) < 0 && hi));
+        const bool b = AAM == 1 || (BOUNCE && ((cz<27>(i) > 0 && lo) || (cz<27>(i) < 0 && hi)));
         const S* p_ = grow + (size_t)i * G::GB;
         R v = Store<S>::ld_s(b ? p_ : p_ - cx<27>(i));
         if constexpr (EXT && BOUNCE && cz<27>(i) != 0)
@@ -203,10 +268,29 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     *xb(p, 7) = m.pst;
   };
   // g collision of plane p from its moments and B's phi(p), a(p)
+  // element offsets to the planes below / above plane p (periodic wrap)
+  const long long plane_el = (long long)P.NYP * P.NXP;
+  auto off_below = [&](int p) { return p == 0 ? (long long)(P.nz - 1) * plane_el : -plane_el; };
+  auto off_above = [&](int p) { return p == P.nz - 1 ? -(long long)(P.nz - 1) * plane_el : plane_el; };
   auto g_collide = [&](int p, const GMoments<R>& m) {
     const R phi = *xb(p, 0);
     const CellFlow<R> f = cell_velocity<R>(*xb(p, 1), *xb(p, 2), *xb(p, 3), (R)1, m.jx, m.jy, m.jz);
-    collide_g<S>(P, A, pdf_index(P, x, y, p), phi, m, f);
+    const size_t pcell = pdf_index(P, x, y, p);
+    if constexpr (AAM != 0) {
+      const bool lo = P.walls && p == 0, hi = P.walls && p == P.nz - 1;
+      const long long om = off_below(p), op = off_above(p);
+      S* gbase = const_cast<S*>(A.g_src);
+      auto run = [&](auto btag) {
+        constexpr bool BOUNCE = decltype(btag)::value;
+        collide_g<S>(P, A, pcell, phi, m, f, [&](auto I, R v) {
+          aa_store<S, 27, decltype(I)::value, AAM, BOUNCE>(P, gbase, pcell, om, op, lo, hi, v);
+        });
+      };
+      if (lo || hi) run(std::true_type{});
+      else run(std::false_type{});
+    } else {
+      collide_g<S>(P, A, pcell, phi, m, f);
+    }
   };
 
   double dsum[kDiagVals];
@@ -249,14 +333,14 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     if (!(mode & MODE_COLLIDE)) return;
     const bool lo = P.walls && p == 0, hi = P.walls && p == P.nz - 1;
     const size_t pcell = pdf_index(P, x, y, p);
-    const S* hrow = hf_ptr(p) + (size_t)(ty + 1) * G::W + col;   // direction 0, this cell
+    const S* hrow = hf_ptr(p) + (size_t)(ty + (AAM ? 0 : 1)) * G::W + col;   // direction 0, this cell
     const R shf = (R)RP<R>(P).shift_f;
     auto run = [&](auto btag) {
       constexpr bool BOUNCE = decltype(btag)::value;
       auto geth = [&](auto I) {
         constexpr int i = decltype(I)::value;
-        const bool b = BOUNCE && ((cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi));
-        const S* p_ = hrow + (size_t)i * G::HFB;
+        const bool b = AAM == 1 || (BOUNCE && ((cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi)));
+        const S* p_ = hrow + (size_t)i * L::HFP;
         R v = Store<S>::ld_s(b ? p_ : p_ - cx<QH>(i));
         if constexpr (EXT && BOUNCE && cz<QH>(i) != 0)
           if (b && P.moving_walls) v += phi * wall_momentum<QH, i, R>(P, cz<QH>(i) > 0 ? 0 : 1);
@@ -266,19 +350,33 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
         constexpr int i = decltype(I)::value;
         if constexpr (QF > 0) {
           const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
-          const S* p_ = hrow + (size_t)(QH + i) * G::HFB;
-          const R v = Store<S>::ld_s(b ? p_ : p_ - cx<QF>(i));
+          const S* p_ = hrow + (size_t)(QH + i) * L::HFP;
+          const R v = Store<S>::ld_s((AAM == 1 || b) ? p_ : p_ - cx<QF>(i));
           // anti-bounce-back in stored form: -v_s + 2 w_i (T_w E_i - s), E_i = 1 at rest
           return b ? (-v + (R)(2.0 * weight<QF>(i)) * abb_wall_value<S, QF, i, EXT, BOUNCE>(P, x, shf)) : v;
         } else {
           return (R)0;
         }
       };
-      collide_h<S, QH>(P, A, pcell, phi, fd.gpx, fd.gpy, fd.gpz, f, geth);
-      if (EXT && P.alpha_ratio)
-        collide_f<S, QF, EXT>(P, A, x, y, p, cell, pcell, phi, Tc, fd, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf);
-      else
-        collide_f<S, QF, false>(P, A, x, y, p, cell, pcell, phi, Tc, fd, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf);
+      if constexpr (AAM != 0) {
+        const long long om = off_below(p), op = off_above(p);
+        S* hbase = const_cast<S*>(A.h_src);
+        S* fbase = const_cast<S*>(A.f_src);
+        collide_h<S, QH>(P, A, pcell, phi, fd.gpx, fd.gpy, fd.gpz, f, geth, [&](auto I, R v) {
+          aa_store<S, QH, decltype(I)::value, AAM, BOUNCE>(P, hbase, pcell, om, op, lo, hi, v);
+        });
+        collide_f<S, QF, false>(P, A, x, y, p, cell, pcell, phi, Tc, fd, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf,
+                                [&](auto I, R v) {
+                                  if constexpr (QF > 0)
+                                    aa_store<S, QF, decltype(I)::value, AAM, BOUNCE>(P, fbase, pcell, om, op, lo, hi, v);
+                                });
+      } else {
+        collide_h<S, QH>(P, A, pcell, phi, fd.gpx, fd.gpy, fd.gpz, f, geth);
+        if (EXT && P.alpha_ratio)
+          collide_f<S, QF, EXT>(P, A, x, y, p, cell, pcell, phi, Tc, fd, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf);
+        else
+          collide_f<S, QF, false>(P, A, x, y, p, cell, pcell, phi, Tc, fd, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf);
+      }
     };
     if (lo || hi) run(std::true_type{});
     else run(std::false_type{});
@@ -347,13 +445,16 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     // h/f boxes of plane z + 3 into the slot of plane z (its collisions were
     // done in the previous iteration)
     if (z + 3 <= z1) issue_hf(z + 3, 0);
-    if constexpr (QF == 0)
+    if constexpr (AAM != 0) {
+      if (z + 3 <= z1 && t_item_valid) f_next = field_raw(z + 3, k_me);
+    } else if constexpr (QF == 0) {
       if (z + 3 <= z1) t_next = t_item(z + 3);
+    }
     if (role_g) {
       // the g role's share of phi / T of plane z + 2, first
       if (z + 2 <= z1) {
         ok = ok && wait_slot(hf_slot(z + 2), hf_par(z + 2));
-        if (ok) sum_plane(z + 2, cidx, NC, L::SUM_A, QF == 0 ? &t_cur : nullptr);
+        if (ok) sum_plane(z + 2, cidx, NC, L::SUM_A, QF == 0 ? &t_cur : nullptr, &f_cur);
       }
       sum_arrive();
       if (active && (mode & MODE_COLLIDE)) g_collide(z, mA0);
@@ -373,7 +474,7 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     } else {
       if (z + 2 <= z1) {
         ok = ok && wait_slot(hf_slot(z + 2), hf_par(z + 2));
-        if (ok) sum_plane(z + 2, L::SUM_A + cidx, NC, G::HPB, QF == 0 ? &t_cur : nullptr);
+        if (ok) sum_plane(z + 2, L::SUM_A + cidx, NC, G::HPB, QF == 0 ? &t_cur : nullptr, &f_cur);
       }
       sum_wait();   // phi / T of plane z + 2 complete (both shares)
       if (ok && z + 1 < z1 && active) {
@@ -381,7 +482,8 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
         b_collide(z + 1);
       }
     }
-    if constexpr (QF == 0) t_cur = t_next;
+    if constexpr (AAM != 0) f_cur = f_next;
+    else if constexpr (QF == 0) t_cur = t_next;
     if (__syncthreads_or(!ok)) { ok = false; break; }
   }
 
@@ -395,5 +497,45 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
   // the reduction's scratch reuses the h/f ring (no copies in flight)
   if (mode & MODE_DIAG) diag_block_reduce_in<NT>(dsum, A.diag_partials, reinterpret_cast<double*>(smem + L::off_hf));
 }
+
+// After a tiled in-place step from an even level (the skewed kernel with
+// AAM = 2): the cells on the lattice's x / y edges scattered their new values
+// of direction i to x + c_i, which may be a periodic ghost column or row of
+// the padded arrays; copy each such ghost value to the interior cell it
+// stands for.  One thread per (written ghost position, plane zd, array q):
+// positions written by the columns x = 0 / nx - 1 (c_x != 0; ny of them) and
+// by the rows y = 0 / ny - 1 (c_y != 0; nx, the corners counted with the
+// columns).  The writers sit on plane zd - c_z; beyond a z wall they stored
+// locally instead.
+template <class S, int QH, int QF>
+__global__ void __launch_bounds__(128) aa_fold_kernel(const DevParams P, S* __restrict__ set) {
+  const int q = blockIdx.z, zd = blockIdx.y;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int k27;
+  if (q < QH) k27 = rt_to27<QH>(q);
+  else if (q < QH + 27) k27 = q - QH;
+  else k27 = QF == 15 ? rt_to27<15>(q - QH - 27) : q - QH - 27;
+  const int ex = kDir27.c[k27][0], ey = kDir27.c[k27][1], ez = kDir27.c[k27][2];
+  if (P.walls && (zd - ez < 0 || zd - ez >= P.nz)) return;
+  int xs, ys;
+  if (r < P.ny) {
+    if (ex == 0) return;
+    xs = ex > 0 ? P.nx - 1 : 0;
+    ys = r;
+  } else {
+    const int j = r - P.ny;
+    if (j >= P.nx || ey == 0) return;
+    xs = j;
+    ys = ey > 0 ? P.ny - 1 : 0;
+    if (ex != 0 && (xs + ex < 0 || xs + ex >= P.nx)) return;   // a corner: done by the column
+  }
+  const int xg = xs + ex, yg = ys + ey;
+  if (xg >= 0 && xg < P.nx && yg >= 0 && yg < P.ny) return;
+  const int xi = xg < 0 ? xg + P.nx : (xg >= P.nx ? xg - P.nx : xg);
+  const int yi = yg < 0 ? yg + P.ny : (yg >= P.ny ? yg - P.ny : yg);
+  S* a = set + (size_t)q * P.Np;
+  a[pdf_index(P, xi, yi, zd)] = a[pdf_index(P, xg, yg, zd)];
+}
+
 
 }  // namespace lbm

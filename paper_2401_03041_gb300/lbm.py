@@ -334,7 +334,7 @@ class Domain:
     def kernel_info(self) -> dict:
         v = (ctypes.c_int32 * 6)()
         _check("lbm_kernel_info", lib().lbm_kernel_info(self._h, v))
-        return {"kernel": {0: "generic", 1: "bulk", 2: "skew", 3: "aa"}.get(v[0], str(v[0])),
+        return {"kernel": {0: "generic", 1: "bulk", 2: "skew", 3: "aa", 4: "aa_tiled"}.get(v[0], str(v[0])),
                 "grid": (v[1], v[2], v[3]), "zchunk": v[4], "smem_bytes": v[5]}
 
     def adjoint_run(self, steps: int, ckpt_every: int, target, normal_cap: float = 0.0):

@@ -21,23 +21,24 @@ def relerr(a, b, floor=1e-6):
 
 def gpu_domain(w: W.Workload, precision=None, kernel=None):
     """kernel: None (library's choice), 'generic' or 'bulk' (forced through
-    LBM_KERNEL), 'skew' (asserted to be the library's choice) or 'aa' (the
-    in-place PDF layout)."""
+    LBM_KERNEL), 'skew' (asserted to be the library's choice), 'aa' (the
+    in-place PDF layout on the generic tiles, forced) or 'aa_tiled' (the
+    in-place layout on the skewed kernel's tiles, asserted)."""
     import os
     from paper_2401_03041_gb300 import lbm
     old = os.environ.pop("LBM_KERNEL", None)
-    if kernel in ("generic", "bulk"):
-        os.environ["LBM_KERNEL"] = kernel
+    if kernel in ("generic", "bulk", "aa"):
+        os.environ["LBM_KERNEL"] = "generic" if kernel == "aa" else kernel
     try:
         d = lbm.Domain(w.nx, w.ny, w.nz, precision or w.precision, w.thermal, w.q_phase,
-                       layout="aa" if kernel == "aa" else "two_grid")
+                       layout="aa" if kernel in ("aa", "aa_tiled") else "two_grid")
     finally:
         os.environ.pop("LBM_KERNEL", None)
         if old is not None:
             os.environ["LBM_KERNEL"] = old
+    d.set_params(w.params)
     if kernel is not None:
         assert d.kernel_info()["kernel"] == kernel, d.kernel_info()
-    d.set_params(w.params)
     if w.sources:
         d.set_heat_sources(w.sources)
     if w.patches is not None:
