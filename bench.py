@@ -320,6 +320,8 @@ def main():
     ap.add_argument("--no-aa", action="store_true", help="skip the in-place (AA) layout leg")
     ap.add_argument("--aa-large-n", type=int, default=1024,
                     help="edge of the large lattice run in the in-place layout (0: skip)")
+    ap.add_argument("--layout", default="two_grid", choices=["two_grid", "aa"],
+                    help="PDF layout of the main leg (aa: the in-place layout; for profiling it)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time the step kernel only (no CPU, e2e, FP64, sweep or error legs; for profiling)")
     args = ap.parse_args()
@@ -367,7 +369,7 @@ def main():
     w = W.config4(args.thermal, args.precision, n=args.n)
 
     def make_domain(prec):
-        d = lbm.Domain(w.nx, w.ny, w.nz, prec, w.thermal, w.q_phase, device=dev)
+        d = lbm.Domain(w.nx, w.ny, w.nz, prec, w.thermal, w.q_phase, device=dev, layout=args.layout)
         d.set_params(w.params)
         d.init_droplets(w.droplets)
         return d
@@ -630,7 +632,7 @@ def main():
         "dtype": "f32" if args.precision == "fp32" else ("f64" if args.precision == "fp64" else "f16-store/f32"),
         "data": "synthetic (seeded droplets, workloads.config4)",
         "config": {"workload": w.name, "lattice": [w.nx, w.ny, w.nz], "precision": args.precision,
-                   "kernel": kinfo,
+                   "layout": args.layout, "kernel": kinfo,
                    "thermal": w.thermal, "q_phase": w.q_phase, "hydro": "D3Q27 central moment",
                    "l2": "state 52.6 GB >> 129 MB L2: no flush needed",
                    "parallelism": f"replicas x{world} (independent lattices, no collective)"},

@@ -65,9 +65,8 @@ void launch_aa_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>&
                     dim3 grid, int zchunk, int mode, cudaStream_t st) {
   using R = typename Store<S>::R;
   using P2 = typename PairOf<R>::type;
-  const long long blocks = (P.N + 255) / 256;
-  const int mgrid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
-  aa_moments_kernel<S, QH, QF><<<mgrid, 256, 0, st>>>(P, A.h_src, A.f_src, A.T, nb, (P2*)phiT);
+  const dim3 mgrid((unsigned)(((P.nx + kAaRowBlock - 1) / kAaRowBlock) * P.ny), (unsigned)P.nz);
+  aa_moments_kernel<S, QH, QF><<<mgrid, kAaRowBlock, 0, st>>>(P, A.h_src, A.f_src, A.T, nb, (P2*)phiT);
   aa_step_kernel<S, QH, QF><<<grid, dim3(TX, TY), 0, st>>>(P, A, (const P2*)phiT, nb, zchunk, mode);
 }
 
@@ -87,18 +86,32 @@ void launch_aa_tiled(const DevParams& P, const StepPtrs<S, typename Store<S>::R>
                            (int)sbytes);
       attr_set = true;
     }
-    const long long blocks = (P.N + 255) / 256;
-    const int mgrid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
-    aa_moments_kernel<S, QH, QF><<<mgrid, 256, 0, st>>>(P, A.h_src, A.f_src, A.T, nb, (P2*)phiT);
+    const dim3 mgrid((unsigned)(((P.nx + kAaRowBlock - 1) / kAaRowBlock) * P.ny), (unsigned)P.nz);
     S* set = const_cast<S*>(A.h_src);
+    // destination pointers of the level: F[i] shifted by c_i's x and y
+    // (even) or F[opp(i)] (odd); the kernel adds the cell and, for even
+    // levels, the z offset of the destination plane
+    StepPtrs<S, R> B = A;
+    const long long np = P.Np, nxp = P.NXP;
+    auto point = [&](auto qtag, const S* base, S** out) {
+      constexpr int Q = decltype(qtag)::value;
+      S* b = const_cast<S*>(base);
+      for (int i = 0; i < Q; ++i)
+        out[i] = nb ? b + (long long)i * np + cx<Q>(i) + (long long)cy<Q>(i) * nxp : b + (long long)opp<Q>(i) * np;
+    };
+    point(std::integral_constant<int, QH>{}, A.h_src, B.hd);
+    point(std::integral_constant<int, 27>{}, A.g_src, B.gd);
+    if constexpr (QF > 0) point(std::integral_constant<int, QF>{}, A.f_src, B.fd);
     const dim3 bgrid((unsigned)bulk_sched_blocks(sched));
     if (nb) {
       launch_ghost_fill<S>(P, set, QH + 27 + QF, st);
-      step_skew_kernel<S, QH, QF, false, 2><<<bgrid, nthr, sbytes, st>>>(P, A, maps.h, maps.g, maps.f, sched, mode,
+      aa_moments_kernel<S, QH, QF><<<mgrid, kAaRowBlock, 0, st>>>(P, A.h_src, A.f_src, A.T, nb, (P2*)phiT);
+      step_skew_kernel<S, QH, QF, false, 2><<<bgrid, nthr, sbytes, st>>>(P, B, maps.h, maps.g, maps.f, sched, mode,
                                                                           (const P2*)phiT);
       aa_fold_kernel<S, QH, QF><<<dim3((P.nx + P.ny + 127) / 128, P.nz, QH + 27 + QF), 128, 0, st>>>(P, set);
     } else {
-      step_skew_kernel<S, QH, QF, false, 1><<<bgrid, nthr, sbytes, st>>>(P, A, maps.h, maps.g, maps.f, sched, mode,
+      aa_moments_kernel<S, QH, QF><<<mgrid, kAaRowBlock, 0, st>>>(P, A.h_src, A.f_src, A.T, nb, (P2*)phiT);
+      step_skew_kernel<S, QH, QF, false, 1><<<bgrid, nthr, sbytes, st>>>(P, B, maps.h, maps.g, maps.f, sched, mode,
                                                                           (const P2*)phiT);
     }
   }

@@ -640,8 +640,8 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
                 return v;
               };
               auto getf = [&](auto I) {
-                constexpr int i = decltype(I)::value;
                 if constexpr (QF > 0) {
+                  constexpr int i = decltype(I)::value;
                   const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
                   const S* p_ = hrow + (size_t)(QH + i) * G::HFB;
                   const R v = Store<S>::ld_s(b ? p_ : p_ - cx<QF>(i));

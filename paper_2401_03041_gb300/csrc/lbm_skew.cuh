@@ -35,7 +35,9 @@
 // staged boxes.  AAM = 1, odd level: f*_i(x) = F[i](x), new values to
 // F[opp(i)](x).  AAM = 2, even level: f*_i(x) = F[opp(i)](x - c_i), new values
 // to F[i](x + c_i); x + c_i may be a periodic ghost column or row, which the
-// host folds back into the interior after the step (aa_fold_kernel).
+// host folds back into the interior after the step (aa_fold_kernel).  The
+// host sets the per-direction destination pointers (StepPtrs hd, gd, fd) for
+// the level: F[opp(i)] (odd) or F[i] shifted by c_i's x and y (even).
 // Every wait is bounded (about 2 s); on a timeout the CTA raises the domain's
 // error flag, drains its outstanding copies (bounded too) and returns.
 #pragma once
@@ -87,28 +89,25 @@ constexpr bool skew_fits() {
   return SkewSmem<S, QH, QF, AAM>::bytes <= 232448;
 }
 
-// In-place store of the new population of direction I (stencil Q) of the cell
-// at pcell: odd level F[opp(I)](x); even level F[I](x + c_I), or F[opp(I)](x)
-// where x + c_I lies beyond a z wall (lo: the cell is on plane 0, hi: on
-// plane nz - 1).  off_m / off_p: element offsets to the planes below / above
-// (periodic wrap included); x + c_I and y + c_I may be ghost positions.
-template <class S, int Q, int I, int AAM, bool BOUNCE>
-__device__ __forceinline__ void aa_store(const DevParams& P, S* base, size_t pcell, long long off_m,
-                                         long long off_p, bool lo, bool hi, typename Store<S>::R v) {
-  constexpr int o = opp<Q>(I);
-  if constexpr (AAM == 1) {
-    Store<S>::st(base + (size_t)o * P.Np + pcell, v);
-  } else {
-    constexpr int ex = cx<Q>(I), ey = cy<Q>(I), ez = cz<Q>(I);
-    if constexpr (BOUNCE && ez != 0) {
-      if ((ez < 0 && lo) || (ez > 0 && hi)) {
-        Store<S>::st(base + (size_t)o * P.Np + pcell, v);
-        return;
-      }
+// In-place store, even level, of the new population of direction I (stencil
+// Q) of the cell at pcell: F[I](x + c_I), or F[opp(I)](x) where x + c_I lies
+// beyond a z wall (lo: the cell is on plane 0, hi: on plane nz - 1).  The
+// host points dst[I] at F[I] shifted by c_I's x and y components (the
+// destination may be a ghost column or row); pc_m / pc_p are pcell moved to
+// the plane below / above (periodic wrap included).  At an odd level the
+// host points dst[I] at F[opp(I)] and the plain store dst[I] + pcell applies.
+template <class S, int Q, int I, bool BOUNCE>
+__device__ __forceinline__ void aa_store_even(const DevParams& P, S* const* dst, const S* base, size_t pcell,
+                                              size_t pc_m, size_t pc_p, bool lo, bool hi,
+                                              typename Store<S>::R v) {
+  constexpr int ez = cz<Q>(I);
+  if constexpr (BOUNCE && ez != 0) {
+    if ((ez < 0 && lo) || (ez > 0 && hi)) {
+      Store<S>::st(const_cast<S*>(base) + (size_t)opp<Q>(I) * P.Np + pcell, v);
+      return;
     }
-    const long long off = (ez < 0 ? off_m : (ez > 0 ? off_p : 0LL)) + (long long)ey * P.NXP + ex;
-    Store<S>::st(base + (size_t)I * P.Np + (size_t)((long long)pcell + off), v);
   }
+  Store<S>::st(dst[I] + (ez < 0 ? pc_m : (ez > 0 ? pc_p : pcell)), v);
 }
 
 template <class S, int QH, int QF, bool EXT, int AAM = 0>
@@ -276,19 +275,19 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     const R phi = *xb(p, 0);
     const CellFlow<R> f = cell_velocity<R>(*xb(p, 1), *xb(p, 2), *xb(p, 3), (R)1, m.jx, m.jy, m.jz);
     const size_t pcell = pdf_index(P, x, y, p);
-    if constexpr (AAM != 0) {
+    if constexpr (AAM == 2) {
       const bool lo = P.walls && p == 0, hi = P.walls && p == P.nz - 1;
-      const long long om = off_below(p), op = off_above(p);
-      S* gbase = const_cast<S*>(A.g_src);
+      const size_t pc_m = pcell + (size_t)off_below(p), pc_p = pcell + (size_t)off_above(p);
       auto run = [&](auto btag) {
         constexpr bool BOUNCE = decltype(btag)::value;
         collide_g<S>(P, A, pcell, phi, m, f, [&](auto I, R v) {
-          aa_store<S, 27, decltype(I)::value, AAM, BOUNCE>(P, gbase, pcell, om, op, lo, hi, v);
+          aa_store_even<S, 27, decltype(I)::value, BOUNCE>(P, A.gd, A.g_src, pcell, pc_m, pc_p, lo, hi, v);
         });
       };
       if (lo || hi) run(std::true_type{});
       else run(std::false_type{});
     } else {
+      // two grids, or in place at an odd level (dst pointers at F[opp(i)])
       collide_g<S>(P, A, pcell, phi, m, f);
     }
   };
@@ -347,8 +346,8 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
         return v;
       };
       auto getf = [&](auto I) {
-        constexpr int i = decltype(I)::value;
         if constexpr (QF > 0) {
+          constexpr int i = decltype(I)::value;
           const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
           const S* p_ = hrow + (size_t)(QH + i) * L::HFP;
           const R v = Store<S>::ld_s((AAM == 1 || b) ? p_ : p_ - cx<QF>(i));
@@ -358,18 +357,20 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
           return (R)0;
         }
       };
-      if constexpr (AAM != 0) {
-        const long long om = off_below(p), op = off_above(p);
-        S* hbase = const_cast<S*>(A.h_src);
-        S* fbase = const_cast<S*>(A.f_src);
+      if constexpr (AAM == 2) {
+        const size_t pc_m = pcell + (size_t)off_below(p), pc_p = pcell + (size_t)off_above(p);
         collide_h<S, QH>(P, A, pcell, phi, fd.gpx, fd.gpy, fd.gpz, f, geth, [&](auto I, R v) {
-          aa_store<S, QH, decltype(I)::value, AAM, BOUNCE>(P, hbase, pcell, om, op, lo, hi, v);
+          aa_store_even<S, QH, decltype(I)::value, BOUNCE>(P, A.hd, A.h_src, pcell, pc_m, pc_p, lo, hi, v);
         });
         collide_f<S, QF, false>(P, A, x, y, p, cell, pcell, phi, Tc, fd, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf,
                                 [&](auto I, R v) {
                                   if constexpr (QF > 0)
-                                    aa_store<S, QF, decltype(I)::value, AAM, BOUNCE>(P, fbase, pcell, om, op, lo, hi, v);
+                                    aa_store_even<S, QF, decltype(I)::value, BOUNCE>(P, A.fd, A.f_src, pcell, pc_m,
+                                                                                     pc_p, lo, hi, v);
                                 });
+      } else if constexpr (AAM == 1) {
+        collide_h<S, QH>(P, A, pcell, phi, fd.gpx, fd.gpy, fd.gpz, f, geth);
+        collide_f<S, QF, false>(P, A, x, y, p, cell, pcell, phi, Tc, fd, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf);
       } else {
         collide_h<S, QH>(P, A, pcell, phi, fd.gpx, fd.gpy, fd.gpz, f, geth);
         if (EXT && P.alpha_ratio)
