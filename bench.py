@@ -90,6 +90,17 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
+# What each step-kernel choice of lbm_kernel_info is, for the roofline record.
+KERNEL_NAMES = {
+    "skew": "lbm::step_skew_kernel (fused h/g/f stream-collide, tensor-TMA staging, two threads per cell "
+            "one plane apart)",
+    "bulk": "lbm::step_bulk_kernel (fused h/g/f stream-collide, tensor-TMA staging, two threads per cell)",
+    "generic": "lbm::step_kernel (fused, generic tiles)",
+    "aa_tiled": "lbm::aa_moments_kernel + lbm::step_skew_kernel in place (tensor-TMA tiles) per step",
+    "aa": "lbm::aa_moments_kernel + lbm::aa_step_kernel (in place, generic tiles) per step",
+}
+
+
 # FP64 peak of the GB300 (nominal): 152 SMs x 2 FP64 FMA lanes per cycle x 2 FLOP
 # per FMA x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -623,7 +634,7 @@ def main():
     # the dominant kernel's own average launch time (CUDA events around each
     # step-kernel launch on the domain's stream, inside the timed region)
     achieved = bpc * cells / kernel_secs / 1e9 if (bpc and kernel_secs) else None
-    tr = traffic_per_cell(args.precision, w.thermal)
+    tr = traffic_per_cell(args.precision, w.thermal) if args.layout == "two_grid" else None
     tpc, tr_n = tr if tr else (None, None)
     line = {
         "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world,
@@ -647,9 +658,7 @@ def main():
                                         f"launch at {tr_n}^3 (profiles/step_kernel_counters.json): "
                                         f"{tpc:.1f} B/cell, scaled by the cell count"
                                         if tpc else "no ncu record for the current kernel sources"),
-                     "kernel": "lbm::step_bulk_kernel (fused h/g/f stream-collide, tensor-TMA staging, "
-                               "two threads per cell)"
-                               if kinfo["kernel"] == "bulk" else "lbm::step_kernel (fused, generic)"},
+                     "kernel": KERNEL_NAMES.get(kinfo["kernel"], kinfo["kernel"])},
         "cpu_baseline": ({"value": cpu["mlups"], "unit": "MLUPS", "cores": 1, "kind": "oracle",
                           "sample": f"{cpu['name']}: {cpu['steps']} FP64 numpy oracle steps in "
                                     f"{cpu['seconds']:.1f} s, single thread",
