@@ -158,9 +158,7 @@ aa_step_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     }
   };
 
-  double dsum[kDiagVals];
-#pragma unroll
-  for (int k = 0; k < kDiagVals; ++k) dsum[k] = 0.0;
+  DiagAcc<R> dsum;   // per-thread FP64 diagnostics
 
   int sm = 0, sc = 1, sp = 2;
   if (z0 < z1) {
@@ -228,7 +226,11 @@ aa_step_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     sp = t;
   }
 
-  if (mode & MODE_DIAG) diag_block_reduce<NTHREADS>(dsum, A.diag_partials);
+  if (mode & MODE_DIAG) {
+    double ds[kDiagVals];
+    dsum.flush(ds);
+    diag_block_reduce<NTHREADS>(ds, A.diag_partials);
+  }
 }
 
 // In-place swap of the opposite slots of every cell: turns populations stored

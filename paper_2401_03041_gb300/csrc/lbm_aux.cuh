@@ -153,8 +153,9 @@ __global__ void rk_stage_kernel(const DevParams P, const RF* __restrict__ psi, R
 }
 
 // Initial state: tanh droplets (periodic minimum image), u = sum phi_k v_k,
-// conduction profile between walls, all in FP64; the equilibria of Sec. 2.2
-// are then evaluated in the compute type of the storage (FP64 in FP64 mode).
+// conduction profile between walls; profiles and equilibria of Sec. 2.2 in
+// the compute type of the storage (FP64 in FP64 mode; FP32 otherwise, with
+// the offsets to the droplet centres formed in FP64).
 //
 // A block covers a 32 x 4 x 2 tile of cells.  Before the per-cell loop it
 // culls the droplet table against the tile's bounding box: droplet k matters
@@ -166,6 +167,7 @@ __global__ void rk_stage_kernel(const DevParams P, const RF* __restrict__ psi, R
 constexpr int kInitTX = 32, kInitTY = 4, kInitTZ = 2;
 
 __device__ __forceinline__ double min_image(double d, int n) { return d - n * rint(d / n); }
+__device__ __forceinline__ float min_image(float d, int n) { return d - (float)n * rintf(d / (float)n); }
 
 template <class S, int QH, int QF>
 __global__ void __launch_bounds__(kInitTX * kInitTY * kInitTZ)
@@ -189,7 +191,12 @@ init_kernel(const DevParams P, const double* __restrict__ drops, int nd, S* h, S
   const double bcz = 0.5 * (bz0 + bz1), bhz = 0.5 * (bz1 - bz0 - 1);
   const double reach = 20.0 * rp.xi + 1.0;
 
-  double phi = 0.0, ux = 0.0, uy = 0.0, uz = 0.0;
+  // droplet profiles in the compute type of the storage: FP64 in FP64 mode;
+  // with FP32 / FP16 storage the offsets to the centre are formed in FP64
+  // and the profile evaluated in FP32 (the FP64 pipe is a small fraction of
+  // the FP32 rate on this GPU and would dominate the initialisation)
+  using PR = R;
+  PR phi = 0, ux = 0, uy = 0, uz = 0;
   for (int k0 = 0; k0 < nd; k0 += 1024) {
     for (int j = tid; j < 1024; j += NT) {   // every warp takes whole 32-droplet words
       const int k = k0 + j;
@@ -217,18 +224,18 @@ init_kernel(const DevParams P, const double* __restrict__ drops, int nd, S* h, S
         for (uint32_t m = mask[wd]; m; m &= m - 1) {
           const int k = k0 + wd * 32 + __ffs(m) - 1;
           const double* d = drops + 7 * k;
-          double dx = global_x(P, x) + 0.5 - d[0], dy = y + 0.5 - d[1], dz = z + 0.5 - d[2];
+          PR dx = (PR)(global_x(P, x) + 0.5 - d[0]), dy = (PR)(y + 0.5 - d[1]), dz = (PR)(z + 0.5 - d[2]);
           dx = min_image(dx, P.sub ? P.gnx : P.nx);
           dy = min_image(dy, P.ny);
           if (!P.walls) dz = min_image(dz, P.nz);
-          const double r = sqrt(dx * dx + dy * dy + dz * dz);
-          const double a = 2.0 * (d[3] - r) / rp.xi;
-          if (a < -40.0) continue;
-          const double pk = 0.5 * (1.0 + tanh(a));
+          const PR r = sqrt(dx * dx + dy * dy + dz * dz);
+          const PR a = (PR)2 * ((PR)d[3] - r) / (PR)rp.xi;
+          if (a < (PR)-40) continue;
+          const PR pk = (PR)0.5 * ((PR)1 + tanh(a));
           phi = fmax(phi, pk);
-          ux += pk * d[4];
-          uy += pk * d[5];
-          uz += pk * d[6];
+          ux += pk * (PR)d[4];
+          uy += pk * (PR)d[5];
+          uz += pk * (PR)d[6];
         }
       }
     }

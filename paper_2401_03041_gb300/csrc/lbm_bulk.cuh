@@ -423,9 +423,7 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     stage_sum_plane<S, QH, QF, EXT, G>(P, A, hf_ptr(p), s_pt + hf_slot(p) * G::HPB, p, x0, y0, tid, NT);
   };
 
-  double dsum[kDiagVals];
-#pragma unroll
-  for (int k = 0; k < kDiagVals; ++k) dsum[k] = 0.0;
+  DiagAcc<R> dsum;   // per-thread FP64 diagnostics
 
   bool ok = true;
   // pending[k]: slot k has copies in flight with parity pend_par[k]
@@ -677,7 +675,11 @@ step_bulk_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
   // the reduction's scratch reuses the h/f ring (no copies are in flight and
   // every thread has passed the last plane's barrier), so the kernel needs
   // no static shared memory beyond its dynamic layout
-  if (mode & MODE_DIAG) diag_block_reduce_in<NT>(dsum, A.diag_partials, reinterpret_cast<double*>(smem + L::off_hf));
+  if (mode & MODE_DIAG) {
+    double ds[kDiagVals];
+    dsum.flush(ds);
+    diag_block_reduce_in<NT>(ds, A.diag_partials, reinterpret_cast<double*>(smem + L::off_hf));
+  }
 }
 
 }  // namespace lbm

@@ -391,22 +391,81 @@ __device__ __forceinline__ CellFlow<R> cell_flow(const DevParams& P, int x, int 
   return cell_velocity<R>(F.ax, F.ay, F.az, F.rho, jx, jy, jz);
 }
 
+// Per-thread accumulators of the FP64 diagnostics (a10).  With an FP64
+// compute type they are doubles.  With FP32 they are unevaluated sums hi + lo
+// of two floats (Knuth's TwoSum for every addition; a product enters with its
+// exact rounding error from an FMA), about 48 significant bits, so that the
+// FP64 pipe, a small fraction of the FP32 rate on this GPU, is used once per
+// thread (flush) instead of for every cell.
+template <class R>
+struct DiagAcc {
+  double s[kDiagVals];
+  __device__ __forceinline__ DiagAcc() {
+#pragma unroll
+    for (int k = 0; k < kDiagVals; ++k) s[k] = 0.0;
+  }
+  __device__ __forceinline__ void add(int k, double v) { s[k] += v; }
+  __device__ __forceinline__ void flush(double* out) const {
+#pragma unroll
+    for (int k = 0; k < kDiagVals; ++k) out[k] = s[k];
+  }
+};
+
+template <>
+struct DiagAcc<float> {
+  float hi[kDiagVals], lo[kDiagVals];
+  __device__ __forceinline__ DiagAcc() {
+#pragma unroll
+    for (int k = 0; k < kDiagVals; ++k) hi[k] = lo[k] = 0.f;
+  }
+  // the _rn intrinsics keep the compiler from contracting these into FMAs
+  __device__ __forceinline__ void add(int k, float v) {
+    const float t = __fadd_rn(hi[k], v);
+    const float bv = __fsub_rn(t, hi[k]);
+    lo[k] = __fadd_rn(lo[k], __fadd_rn(__fsub_rn(hi[k], __fsub_rn(t, bv)), __fsub_rn(v, bv)));
+    hi[k] = t;
+  }
+  __device__ __forceinline__ void add_prod(int k, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    lo[k] = __fadd_rn(lo[k], fmaf(a, b, -p));
+    add(k, p);
+  }
+  __device__ __forceinline__ void flush(double* out) const {
+#pragma unroll
+    for (int k = 0; k < kDiagVals; ++k) out[k] = (double)hi[k] + (double)lo[k];
+  }
+};
+
+
 // a10 diagnostics (FP64 partial sums) and the macroscopic output pass.
 template <class S>
 __device__ __forceinline__ void cell_outputs(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A,
                                              int x, int y, int z, size_t cell, int mode,
                                              typename Store<S>::R phi, typename Store<S>::R Tc,
                                              typename Store<S>::R pst,
-                                             const CellFlow<typename Store<S>::R>& f, double* dsum) {
+                                             const CellFlow<typename Store<S>::R>& f,
+                                             DiagAcc<typename Store<S>::R>& dsum) {
+  using R = typename Store<S>::R;
   if (mode & MODE_DIAG) {
-    const double dphi = (double)phi;
-    dsum[0] += dphi;
-    dsum[1] += (double)Tc;
-    dsum[2] += 0.5 * (double)f.rho * (double)f.uu;
-    dsum[3] += dphi * (global_x(P, x) + 0.5);
-    dsum[4] += dphi * (y + 0.5);
-    dsum[5] += dphi * (z + 0.5);
-    if (!isfinite(dphi) || !isfinite((double)Tc) || !isfinite((double)f.uu)) dsum[6] += 1.0;
+    if constexpr (std::is_same<R, double>::value) {
+      const double dphi = (double)phi;
+      dsum.s[0] += dphi;
+      dsum.s[1] += (double)Tc;
+      dsum.s[2] += 0.5 * (double)f.rho * (double)f.uu;
+      dsum.s[3] += dphi * (global_x(P, x) + 0.5);
+      dsum.s[4] += dphi * (y + 0.5);
+      dsum.s[5] += dphi * (z + 0.5);
+      if (!isfinite(dphi) || !isfinite((double)Tc) || !isfinite((double)f.uu)) dsum.s[6] += 1.0;
+    } else {
+      // cell centres are exact in FP32 below 2^23; 0.5 rho is exact
+      dsum.add(0, phi);
+      dsum.add(1, Tc);
+      dsum.add_prod(2, (R)0.5 * f.rho, f.uu);
+      dsum.add_prod(3, phi, (R)global_x(P, x) + (R)0.5);
+      dsum.add_prod(4, phi, (R)y + (R)0.5);
+      dsum.add_prod(5, phi, (R)z + (R)0.5);
+      if (!isfinite(phi) || !isfinite(Tc) || !isfinite(f.uu)) dsum.hi[6] += 1.f;
+    }
   }
   if (mode & MODE_MACRO) {
     const double vals[6] = {(double)phi, (double)f.ux, (double)f.uy, (double)f.uz, (double)pst, (double)Tc};
@@ -683,7 +742,8 @@ __device__ __forceinline__ void cell_update(const DevParams& P, const StepPtrs<S
                                             typename Store<S>::R rgx, typename Store<S>::R rgy,
                                             typename Store<S>::R rgz, typename Store<S>::R rlap,
                                             typename Store<S>::R pgx, typename Store<S>::R pgy,
-                                            typename Store<S>::R pgz, GH geth, GG getg, GF getf, double* dsum) {
+                                            typename Store<S>::R pgz, GH geth, GG getg, GF getf,
+                                            DiagAcc<typename Store<S>::R>& dsum) {
   using R = typename Store<S>::R;
   const GMoments<R> m = g_moments<R>(getg);
   if (mode & MODE_SAVE) {

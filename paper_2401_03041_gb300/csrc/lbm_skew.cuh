@@ -292,9 +292,7 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     }
   };
 
-  double dsum[kDiagVals];
-#pragma unroll
-  for (int k = 0; k < kDiagVals; ++k) dsum[k] = 0.0;
+  DiagAcc<R> dsum;   // per-thread FP64 diagnostics
 
   // stencil role, plane p: stencils and force; phi(p), a(p) to the exchange;
   // then (after the plane's j and p* are in the exchange) the h and f
@@ -496,7 +494,11 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     return;
   }
   // the reduction's scratch reuses the h/f ring (no copies in flight)
-  if (mode & MODE_DIAG) diag_block_reduce_in<NT>(dsum, A.diag_partials, reinterpret_cast<double*>(smem + L::off_hf));
+  if (mode & MODE_DIAG) {
+    double ds[kDiagVals];
+    dsum.flush(ds);
+    diag_block_reduce_in<NT>(ds, A.diag_partials, reinterpret_cast<double*>(smem + L::off_hf));
+  }
 }
 
 // After a tiled in-place step from an even level (the skewed kernel with
