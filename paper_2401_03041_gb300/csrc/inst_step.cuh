@@ -86,7 +86,6 @@ void launch_aa_tiled(const DevParams& P, const StepPtrs<S, typename Store<S>::R>
                            (int)sbytes);
       attr_set = true;
     }
-    const dim3 mgrid((unsigned)(((P.nx + kAaRowBlock - 1) / kAaRowBlock) * P.ny), (unsigned)P.nz);
     S* set = const_cast<S*>(A.h_src);
     // destination pointers of the level: F[i] shifted by c_i's x and y
     // (even) or F[opp(i)] (odd); the kernel adds the cell and, for even
@@ -103,14 +102,28 @@ void launch_aa_tiled(const DevParams& P, const StepPtrs<S, typename Store<S>::R>
     point(std::integral_constant<int, 27>{}, A.g_src, B.gd);
     if constexpr (QF > 0) point(std::integral_constant<int, QF>{}, A.f_src, B.fd);
     const dim3 bgrid((unsigned)bulk_sched_blocks(sched));
+    // (phi, T) of the level from TMA-staged boxes (as plain loads the gathers
+    // of an even level, shifted rows of three planes, ran at half the copy rate)
+    constexpr size_t mbytes = AaMomSmem<S, QH, QF>::bytes;
+    constexpr int mthr = AaMomSmem<S, QH, QF>::G::NT;
+    static bool mattr_set = false;
+    if (!mattr_set) {
+      cudaFuncSetAttribute(aa_moments_tiled_kernel<S, QH, QF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)mbytes);
+      cudaFuncSetAttribute(aa_moments_tiled_kernel<S, QH, QF, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)mbytes);
+      mattr_set = true;
+    }
     if (nb) {
       launch_ghost_fill<S>(P, set, QH + 27 + QF, st);
-      aa_moments_kernel<S, QH, QF><<<mgrid, kAaRowBlock, 0, st>>>(P, A.h_src, A.f_src, A.T, nb, (P2*)phiT);
+      aa_moments_tiled_kernel<S, QH, QF, 2><<<bgrid, mthr, mbytes, st>>>(P, maps.h, maps.f, sched, A.T, (P2*)phiT,
+                                                                         A.error_flag);
       step_skew_kernel<S, QH, QF, false, 2><<<bgrid, nthr, sbytes, st>>>(P, B, maps.h, maps.g, maps.f, sched, mode,
                                                                           (const P2*)phiT);
       aa_fold_kernel<S, QH, QF><<<dim3((P.nx + P.ny + 127) / 128, P.nz, QH + 27 + QF), 128, 0, st>>>(P, set);
     } else {
-      aa_moments_kernel<S, QH, QF><<<mgrid, kAaRowBlock, 0, st>>>(P, A.h_src, A.f_src, A.T, nb, (P2*)phiT);
+      aa_moments_tiled_kernel<S, QH, QF, 1><<<bgrid, mthr, mbytes, st>>>(P, maps.h, maps.f, sched, A.T, (P2*)phiT,
+                                                                         A.error_flag);
       step_skew_kernel<S, QH, QF, false, 1><<<bgrid, nthr, sbytes, st>>>(P, B, maps.h, maps.g, maps.f, sched, mode,
                                                                           (const P2*)phiT);
     }

@@ -17,10 +17,11 @@
 // to F[i](x), the slot the previous phase left the reflected population in.
 //
 // The finite differences need phi and T of level n at the neighbours, which
-// an in-place update overwrites; so each step first runs aa_moments_kernel,
-// which writes the (phi, T) pairs of every cell (zeroth moments of the
-// gathered populations, summed in the same order as the two-grid kernels'
-// halo sums), and the step kernel takes its stencil tiles from that field.
+// an in-place update overwrites; so each step first writes the (phi, T) pairs
+// of every cell (zeroth moments of the gathered populations, summed in the
+// same order as the two-grid kernels' halo sums: aa_moments_kernel here, or
+// aa_moments_tiled_kernel in lbm_skew.cuh on the tiled path), and the step
+// kernel takes its stencil values from that field.
 // In FP64 the result equals the generic two-grid kernel's to rounding (the
 // two are compiled separately and contract their products into FMAs
 // differently).

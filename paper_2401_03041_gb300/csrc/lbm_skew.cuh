@@ -541,4 +541,133 @@ __global__ void __launch_bounds__(128) aa_fold_kernel(const DevParams P, S* __re
 }
 
 
+
+// (phi, T) of a level of the in-place layout on the tiled kernels' geometry:
+// the h / f boxes of each plane are staged by tensor-TMA exactly as the
+// in-place step of that level stages them (AAM = 1, odd: array i at the
+// cell; AAM = 2, even: array opp(i) shifted by -c_i, or the direction's own
+// array where the source lies beyond a z wall, with the periodic ghosts
+// refreshed first), and each thread sums its cell's gathered populations in
+// the two-grid kernels' order: phi = s_h + sum_i h*_i, T = s_f + sum_i f*_i
+// with the anti-bounce-back at walls (LB), or the stored T (RK).  A ring of
+// two stages; one thread per cell of the TXB x TYB tile.
+template <class S, int QH, int QF>
+struct AaMomSmem {
+  using G = typename BulkSmem<S, QH, QF>::G;
+  static constexpr int NHF = QH + QF;
+  static constexpr size_t stage = (size_t)NHF * G::GB;   // elements
+  static constexpr uint32_t tx = (uint32_t)((size_t)NHF * G::W * G::TYB * sizeof(S));
+  static constexpr size_t off_bar = (2 * stage * sizeof(S) + 15) & ~size_t(15);
+  static constexpr size_t bytes = off_bar + 2 * sizeof(uint64_t) + 128;
+};
+
+template <class S, int QH, int QF, int AAM>
+__global__ void __launch_bounds__(AaMomSmem<S, QH, QF>::G::NT)
+aa_moments_tiled_kernel(const DevParams P, const __grid_constant__ CUtensorMap mh,
+                        const __grid_constant__ CUtensorMap mf, const BulkSched sched,
+                        const typename Store<S>::R* __restrict__ Tfield,
+                        typename PairOf<typename Store<S>::R>::type* __restrict__ phiT, int* error_flag) {
+  using R = typename Store<S>::R;
+  using L = AaMomSmem<S, QH, QF>;
+  using G = typename L::G;
+  constexpr int NT = G::NT;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+  S* st = (S*)smem;
+  uint64_t* bar = (uint64_t*)(smem + L::off_bar);
+  const int tid = threadIdx.x;
+  const int tx = tid % G::TXB, ty = tid / G::TXB;
+  int tcol, trow, z0, z1;
+  bulk_unit(sched, P.nz, (int)blockIdx.x, tcol, trow, z0, z1);
+  const int x0 = tcol * G::TXB, y0 = trow * G::TYB;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool active = x < P.nx && y < P.ny;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  } else if (tid == 32) {
+    tma_prefetch_desc(&mh);
+    tma_prefetch_desc(&mf);
+  }
+  __syncthreads();
+  auto issue = [&](int p) {
+    const int k = (p - z0) & 1;
+    if (tid == 0) mbar_expect_tx(&bar[k], L::tx);
+    issue_stage<S, G, QH, QF, 0, AAM>(P, &mh, &mh, &mf, st + (size_t)k * L::stage, &bar[k], p, x0, y0, tid,
+                                      NT / 32);
+  };
+  const auto& rp = RP<R>(P);
+  const R shh = (R)rp.shift_h, shf = (R)rp.shift_f;
+  // slots with a copy in flight, and the phase parity each will complete
+  uint32_t pending = 0, pend_par = 0;
+  auto mark = [&](int p) {
+    const int k = (p - z0) & 1;
+    pending |= 1u << k;
+    pend_par = (pend_par & ~(1u << k)) | ((uint32_t)(((p - z0) >> 1) & 1) << k);
+  };
+  bool ok = true;
+  if (z0 < z1) {
+    issue(z0);
+    mark(z0);
+    if (z0 + 1 < z1) {
+      issue(z0 + 1);
+      mark(z0 + 1);
+    }
+  }
+  for (int p = z0; p < z1; ++p) {
+    const int k = (p - z0) & 1;
+    if (ok) {
+      ok = mbar_wait(&bar[k], (uint32_t)(((p - z0) >> 1) & 1));
+      if (ok) pending &= ~(1u << k);
+    }
+    if (ok && active) {
+      const bool lo = P.walls && p == 0, hi = P.walls && p == P.nz - 1;
+      const S* row = st + (size_t)k * L::stage + (size_t)ty * G::W + tx + G::GXP;
+      auto run = [&](auto btag) {
+        constexpr bool BOUNCE = decltype(btag)::value;
+        R phi = 0;
+        static_for<0, QH>([&](auto I) {
+          constexpr int i = decltype(I)::value;
+          const bool b = BOUNCE && ((cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi));
+          const S* q = row + (size_t)i * G::GB;
+          phi += Store<S>::ld_s((AAM == 1 || b) ? q : q - cx<QH>(i));
+        });
+        phi += shh;
+        R T;
+        if constexpr (QF > 0) {
+          T = shf;
+          static_for<0, QF>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
+            const S* q = row + (size_t)(QH + i) * G::GB;
+            const R v = Store<S>::ld_s((AAM == 1 || b) ? q : q - cx<QF>(i));
+            T += b ? (-v + (R)(2.0 * weight<QF>(i)) * abb_wall_value<S, QF, i, false, BOUNCE>(P, x, shf)) : v;
+          });
+        } else {
+          T = Tfield[cell_index(P, x, y, p)];
+        }
+        typename PairOf<R>::type v;
+        v.x = phi;
+        v.y = T;
+        phiT[cell_index(P, x, y, p)] = v;
+      };
+      if (lo || hi) run(std::true_type{});
+      else run(std::false_type{});
+    }
+    // every thread has read the stage before it takes plane p + 2
+    if (__syncthreads_or(!ok)) ok = false;
+    if (ok && p + 2 < z1) {
+      issue(p + 2);
+      mark(p + 2);
+    }
+  }
+  if (!ok) {
+    // raise the error flag, drain outstanding copies (bounded), leave
+    if (tid == 0 && error_flag) atomicExch(error_flag, 1);
+    for (int k = 0; k < 2; ++k)
+      if (pending & (1u << k)) mbar_wait(&bar[k], (pend_par >> k) & 1u);
+  }
+}
+
 }  // namespace lbm
