@@ -291,8 +291,8 @@ lbm_status lbm_synchronize(lbm_domain* dom, int timeout_ms);
  * generic kernel, 1 for the bulk kernel (PDF boxes staged in shared memory by
  * tensor-TMA copies), 2 for the skewed kernel (the same staging, the two
  * threads of a cell one plane apart), 3 for the in-place layout on the
- * generic tiles, 4 for the in-place layout on the skewed kernel's tiles (the
- * uniform-property model; other parameters run it on the generic tiles);
+ * generic tiles, 4 for the in-place layout on the skewed kernel's tiles (all
+ * parameters but a density ratio, which runs it on the generic tiles);
  * info[1..3] = grid x, y, z (tile counts and z-chunks); info[4] = planes per
  * CTA; info[5] = dynamic shared memory bytes.  info holds 6 int32 values.
  * The environment variable LBM_KERNEL=generic, read at creation, forces the

@@ -84,6 +84,10 @@ void launch_aa_tiled(const DevParams& P, const StepPtrs<S, typename Store<S>::R>
                            (int)sbytes);
       cudaFuncSetAttribute(step_skew_kernel<S, QH, QF, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sbytes);
+      cudaFuncSetAttribute(step_skew_kernel<S, QH, QF, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sbytes);
+      cudaFuncSetAttribute(step_skew_kernel<S, QH, QF, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sbytes);
       attr_set = true;
     }
     S* set = const_cast<S*>(A.h_src);
@@ -108,25 +112,36 @@ void launch_aa_tiled(const DevParams& P, const StepPtrs<S, typename Store<S>::R>
     constexpr int mthr = AaMomSmem<S, QH, QF>::G::NT;
     static bool mattr_set = false;
     if (!mattr_set) {
-      cudaFuncSetAttribute(aa_moments_tiled_kernel<S, QH, QF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(aa_moments_tiled_kernel<S, QH, QF, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)mbytes);
-      cudaFuncSetAttribute(aa_moments_tiled_kernel<S, QH, QF, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(aa_moments_tiled_kernel<S, QH, QF, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)mbytes);
+      cudaFuncSetAttribute(aa_moments_tiled_kernel<S, QH, QF, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)mbytes);
+      cudaFuncSetAttribute(aa_moments_tiled_kernel<S, QH, QF, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)mbytes);
       mattr_set = true;
     }
-    if (nb) {
-      launch_ghost_fill<S>(P, set, QH + 27 + QF, st);
-      aa_moments_tiled_kernel<S, QH, QF, 2><<<bgrid, mthr, mbytes, st>>>(P, maps.h, maps.f, sched, A.T, (P2*)phiT,
-                                                                         A.error_flag);
-      step_skew_kernel<S, QH, QF, false, 2><<<bgrid, nthr, sbytes, st>>>(P, B, maps.h, maps.g, maps.f, sched, mode,
+    // model extensions (conductivity / heat-capacity ratio, modulated wall,
+    // moving walls, wetting) in their own instantiation, as on two grids
+    auto go = [&](auto ext_tag) {
+      constexpr bool EXT = decltype(ext_tag)::value;
+      if (nb) {
+        launch_ghost_fill<S>(P, set, QH + 27 + QF, st);
+        aa_moments_tiled_kernel<S, QH, QF, 2, EXT><<<bgrid, mthr, mbytes, st>>>(P, maps.h, maps.f, sched, A.T,
+                                                                                (P2*)phiT, A.error_flag);
+        step_skew_kernel<S, QH, QF, EXT, 2><<<bgrid, nthr, sbytes, st>>>(P, B, maps.h, maps.g, maps.f, sched, mode,
                                                                           (const P2*)phiT);
-      aa_fold_kernel<S, QH, QF><<<dim3((P.nx + P.ny + 127) / 128, P.nz, QH + 27 + QF), 128, 0, st>>>(P, set);
-    } else {
-      aa_moments_tiled_kernel<S, QH, QF, 1><<<bgrid, mthr, mbytes, st>>>(P, maps.h, maps.f, sched, A.T, (P2*)phiT,
-                                                                         A.error_flag);
-      step_skew_kernel<S, QH, QF, false, 1><<<bgrid, nthr, sbytes, st>>>(P, B, maps.h, maps.g, maps.f, sched, mode,
+        aa_fold_kernel<S, QH, QF><<<dim3((P.nx + P.ny + 127) / 128, P.nz, QH + 27 + QF), 128, 0, st>>>(P, set);
+      } else {
+        aa_moments_tiled_kernel<S, QH, QF, 1, EXT><<<bgrid, mthr, mbytes, st>>>(P, maps.h, maps.f, sched, A.T,
+                                                                                (P2*)phiT, A.error_flag);
+        step_skew_kernel<S, QH, QF, EXT, 1><<<bgrid, nthr, sbytes, st>>>(P, B, maps.h, maps.g, maps.f, sched, mode,
                                                                           (const P2*)phiT);
-    }
+      }
+    };
+    if (P.alpha_ratio || P.tw_waves || P.wall_ext) go(std::true_type{});
+    else go(std::false_type{});
   }
 }
 

@@ -331,11 +331,12 @@ void step_launch(lbm_domain* d, const StepPtrs<S, typename Store<S>::R>& A, int 
 
 // In-place layout: (phi, T) of the level, then the step (gathers from the
 // neighbours when the level is even, locally when it is odd), on the tiled
-// kernel where it applies (the uniform-property model) and on the generic
-// tiles otherwise.
+// kernels where they apply (all but the density ratio, whose forces need
+// the moments and stencils of one plane together, and sub-domains) and on
+// the generic tiles otherwise.
 bool aa_tiled(const lbm_domain* d) {
   const DevParams& q = d->dp;
-  return d->aa && d->geo_aa.bulk == 2 && !(q.alpha_ratio || q.tw_waves || q.wall_ext || q.sub || q.rho_ratio);
+  return d->aa && d->geo_aa.bulk == 2 && !(q.sub || q.rho_ratio);
 }
 
 template <class S>

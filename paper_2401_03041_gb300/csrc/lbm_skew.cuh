@@ -116,7 +116,6 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
                  const __grid_constant__ CUtensorMap mh, const __grid_constant__ CUtensorMap mg,
                  const __grid_constant__ CUtensorMap mf, const BulkSched sched, int mode,
                  const typename PairOf<typename Store<S>::R>::type* __restrict__ aa_phiT) {
-  static_assert(AAM == 0 || !EXT, "the in-place kernels cover the uniform-property model");
   using R = typename Store<S>::R;
   using L = SkewSmem<S, QH, QF, AAM>;
   using G = typename L::G;
@@ -199,7 +198,18 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
     return aa_phiT[cell_index(P, gx, gy, pe)];
   };
   auto field_put = [&](int p, int k, P2 v) {
-    if (P.walls && (p < 0 || p >= P.nz)) v.y = (R)2 * (R)(p < 0 ? RP<R>(P).T_bottom : RP<R>(P).T_top) - v.y;
+    if (P.walls && (p < 0 || p >= P.nz)) {
+      if constexpr (EXT) {
+        // the modulated bottom wall's value above this column; the
+        // contact-angle ghost of phi
+        int gx = x0 + k % G::HXB - 1;
+        gx = gx < 0 ? gx + P.nx : (gx >= P.nx ? gx - P.nx : gx);
+        v.y = (R)2 * (p < 0 ? wall_T<R>(P, gx, true) : (R)RP<R>(P).T_top) - v.y;
+        if (P.wetting) v.x = wet_ghost<R>(v.x, wall_k<R>(P, p < 0 ? 0 : 1));
+      } else {
+        v.y = (R)2 * (R)(p < 0 ? RP<R>(P).T_bottom : RP<R>(P).T_top) - v.y;
+      }
+    }
     pt_ptr(p)[k] = v;
   };
   // the plane's (phi, T) pairs, items k0, k0 + kstep, .. < kend (tpre: the
@@ -248,9 +258,11 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
       constexpr bool BOUNCE = decltype(btag)::value;
       auto getg = [&](auto I) {
         constexpr int i = decltype(I)::value;
-        const bool b = AAM == 1 || (BOUNCE && ((cz<27>(i) > 0 && lo) || (cz<27>(i) < 0 && hi)));
+        // b: the source lies beyond a wall; the read is local then, and
+        // always at an odd in-place level
+        const bool b = BOUNCE && ((cz<27>(i) > 0 && lo) || (cz<27>(i) < 0 && hi));
         const S* p_ = grow + (size_t)i * G::GB;
-        R v = Store<S>::ld_s(b ? p_ : p_ - cx<27>(i));
+        R v = Store<S>::ld_s((AAM == 1 || b) ? p_ : p_ - cx<27>(i));
         if constexpr (EXT && BOUNCE && cz<27>(i) != 0)
           if (b && P.moving_walls) v += wall_momentum<27, i, R>(P, cz<27>(i) > 0 ? 0 : 1);
         return v;
@@ -336,9 +348,9 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
       constexpr bool BOUNCE = decltype(btag)::value;
       auto geth = [&](auto I) {
         constexpr int i = decltype(I)::value;
-        const bool b = AAM == 1 || (BOUNCE && ((cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi)));
+        const bool b = BOUNCE && ((cz<QH>(i) > 0 && lo) || (cz<QH>(i) < 0 && hi));
         const S* p_ = hrow + (size_t)i * L::HFP;
-        R v = Store<S>::ld_s(b ? p_ : p_ - cx<QH>(i));
+        R v = Store<S>::ld_s((AAM == 1 || b) ? p_ : p_ - cx<QH>(i));
         if constexpr (EXT && BOUNCE && cz<QH>(i) != 0)
           if (b && P.moving_walls) v += phi * wall_momentum<QH, i, R>(P, cz<QH>(i) > 0 ? 0 : 1);
         return v;
@@ -360,15 +372,22 @@ step_skew_kernel(const DevParams P, const StepPtrs<S, typename Store<S>::R> A,
         collide_h<S, QH>(P, A, pcell, phi, fd.gpx, fd.gpy, fd.gpz, f, geth, [&](auto I, R v) {
           aa_store_even<S, QH, decltype(I)::value, BOUNCE>(P, A.hd, A.h_src, pcell, pc_m, pc_p, lo, hi, v);
         });
-        collide_f<S, QF, false>(P, A, x, y, p, cell, pcell, phi, Tc, fd, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf,
-                                [&](auto I, R v) {
-                                  if constexpr (QF > 0)
-                                    aa_store_even<S, QF, decltype(I)::value, BOUNCE>(P, A.fd, A.f_src, pcell, pc_m,
-                                                                                     pc_p, lo, hi, v);
-                                });
+        auto putf = [&](auto I, R v) {
+          if constexpr (QF > 0)
+            aa_store_even<S, QF, decltype(I)::value, BOUNCE>(P, A.fd, A.f_src, pcell, pc_m, pc_p, lo, hi, v);
+        };
+        if (EXT && P.alpha_ratio)
+          collide_f<S, QF, EXT>(P, A, x, y, p, cell, pcell, phi, Tc, fd, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf,
+                                putf);
+        else
+          collide_f<S, QF, false>(P, A, x, y, p, cell, pcell, phi, Tc, fd, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f,
+                                  getf, putf);
       } else if constexpr (AAM == 1) {
         collide_h<S, QH>(P, A, pcell, phi, fd.gpx, fd.gpy, fd.gpz, f, geth);
-        collide_f<S, QF, false>(P, A, x, y, p, cell, pcell, phi, Tc, fd, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf);
+        if (EXT && P.alpha_ratio)
+          collide_f<S, QF, EXT>(P, A, x, y, p, cell, pcell, phi, Tc, fd, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf);
+        else
+          collide_f<S, QF, false>(P, A, x, y, p, cell, pcell, phi, Tc, fd, rgx, rgy, rgz, rlap, pgx, pgy, pgz, f, getf);
       } else {
         collide_h<S, QH>(P, A, pcell, phi, fd.gpx, fd.gpy, fd.gpz, f, geth);
         if (EXT && P.alpha_ratio)
@@ -549,8 +568,9 @@ __global__ void __launch_bounds__(128) aa_fold_kernel(const DevParams P, S* __re
 // array where the source lies beyond a z wall, with the periodic ghosts
 // refreshed first), and each thread sums its cell's gathered populations in
 // the two-grid kernels' order: phi = s_h + sum_i h*_i, T = s_f + sum_i f*_i
-// with the anti-bounce-back at walls (LB), or the stored T (RK).  A ring of
-// two stages; one thread per cell of the TXB x TYB tile.
+// with the anti-bounce-back at walls (LB; EXT: the modulated bottom wall and
+// moving walls), or the stored T (RK).  A ring of two stages; one thread per
+// cell of the TXB x TYB tile.
 template <class S, int QH, int QF>
 struct AaMomSmem {
   using G = typename BulkSmem<S, QH, QF>::G;
@@ -561,7 +581,7 @@ struct AaMomSmem {
   static constexpr size_t bytes = off_bar + 2 * sizeof(uint64_t) + 128;
 };
 
-template <class S, int QH, int QF, int AAM>
+template <class S, int QH, int QF, int AAM, bool EXT>
 __global__ void __launch_bounds__(AaMomSmem<S, QH, QF>::G::NT)
 aa_moments_tiled_kernel(const DevParams P, const __grid_constant__ CUtensorMap mh,
                         const __grid_constant__ CUtensorMap mf, const BulkSched sched,
@@ -642,7 +662,7 @@ aa_moments_tiled_kernel(const DevParams P, const __grid_constant__ CUtensorMap m
             const bool b = BOUNCE && ((cz<QF>(i) > 0 && lo) || (cz<QF>(i) < 0 && hi));
             const S* q = row + (size_t)(QH + i) * G::GB;
             const R v = Store<S>::ld_s((AAM == 1 || b) ? q : q - cx<QF>(i));
-            T += b ? (-v + (R)(2.0 * weight<QF>(i)) * abb_wall_value<S, QF, i, false, BOUNCE>(P, x, shf)) : v;
+            T += b ? (-v + (R)(2.0 * weight<QF>(i)) * abb_wall_value<S, QF, i, EXT, BOUNCE>(P, x, shf)) : v;
           });
         } else {
           T = Tfield[cell_index(P, x, y, p)];

@@ -3,9 +3,9 @@ place by alternating a gather-from-neighbours step and a local step, with a
 (phi, T) field of each level for the finite differences.
 
 Two implementations: the generic tiles ('aa', every model extension) and the
-skewed kernel's tensor-TMA tiles ('aa_tiled', the uniform-property model,
-with the periodic ghosts refreshed before and folded back after each step
-from an even level).
+skewed kernel's tensor-TMA tiles ('aa_tiled', every extension but the
+density ratio, with the periodic ghosts refreshed before and folded back
+after each step from an even level).
 
 FP64: equal to the generic two-grid kernel to rounding (fields and the
 populations p_i(x) returned by lbm_get_pdfs, after an odd and an even number
@@ -58,6 +58,10 @@ def _variant(name):
 
 
 def _uniform_variant(name):
+    if name == "modulated_wall_d3q19":
+        w = ragged_workload("D3Q19", 15, walls=True)
+        return w.replace(params=W.Params(**dict(w.params.__dict__, T_bottom_amp=0.3, T_bottom_waves=2,
+                                                wall_u_bottom=(0.01, 0.005))))
     if name == "walls_d3q7":
         return ragged_workload("D3Q7", 15, walls=True)
     if name == "periodic_d3q15_q27":
@@ -73,7 +77,9 @@ def _uniform_variant(name):
                                                              "rk4_conductivity_ratio", "d3q7_heat_capacity_ratio",
                                                              "density_ratio_d3q15", "rk2_periodic_heaters")]
                          + [("aa_tiled", n) for n in ("walls_d3q7", "periodic_d3q19_q27", "periodic_d3q15_q27",
-                                                      "walls_rk4", "rk2_periodic_heaters", "periodic_d3q27")])
+                                                      "walls_rk4", "rk2_periodic_heaters", "periodic_d3q27",
+                                                      "walls_moving_wetting", "rk4_conductivity_ratio",
+                                                      "d3q7_heat_capacity_ratio", "modulated_wall_d3q19")])
 def test_aa_equals_two_grid_fp64(kernel, name):
     """40 x 20 x 13 (ragged against the tiles in x and y): both in-place
     implementations against the generic two-grid kernel after an odd (7) and
@@ -136,13 +142,15 @@ def test_aa_reduced_precision_matches_two_grid(kernel, precision, tol_phi):
     assert ea < tol_phi and eb < tol_phi
 
 
-def test_aa_tiled_falls_back_for_model_extensions():
-    """The tiled in-place kernel covers the uniform-property model; a moving
-    wall (or any other extension) runs the in-place step on the generic tiles."""
+def test_aa_tiled_falls_back_for_density_ratio():
+    """The tiled in-place kernels cover every model extension but the density
+    ratio (its forces need the moments and the stencils of one plane
+    together), which runs the in-place step on the generic tiles."""
     w = ragged_workload("D3Q7", 15, walls=True)
     d = gpu_domain(w, kernel="aa_tiled")
-    p = W.Params(**dict(w.params.__dict__, wall_u_top=(0.01, 0.0)))
-    d.set_params(p)
+    d.set_params(W.Params(**dict(w.params.__dict__, wall_u_top=(0.01, 0.0), theta_top=60.0, alpha_H=0.02)))
+    assert d.kernel_info()["kernel"] == "aa_tiled"
+    d.set_params(W.Params(**dict(w.params.__dict__, rho_H=4.0)))
     assert d.kernel_info()["kernel"] == "aa"
     d.set_params(w.params)
     assert d.kernel_info()["kernel"] == "aa_tiled"
