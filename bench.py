@@ -421,10 +421,22 @@ def main():
     cells = w.cells
     mlups = job_mlups(cells, args.steps, world, secs)
     per_step = secs / args.steps
-    # one step-kernel launch, + one ghost-fill launch with the bulk kernel,
-    # + the RK stages of the finite-difference energy solvers
-    launches_per_step = (1 + (1 if kinfo["kernel"] == "bulk" else 0)
-                         + (0 if w.thermal.startswith("D3Q") else (1 if w.thermal == "RK2" else 3)))
+    # launches of the timed steps: the step kernel, + the ghost fill after it
+    # with the tiled kernels (the generic one wraps its reads); in place, the
+    # (phi, T) pass + the step, + a ghost refresh and a fold around the tiled
+    # steps from even levels; + the RK stages of the finite-difference solvers
+    rk_stages = 0 if w.thermal.startswith("D3Q") else (1 if w.thermal == "RK2" else 3)
+    kname = kinfo["kernel"]
+    if kname in ("skew", "bulk"):
+        timed_launches = args.steps * (2 + rk_stages)
+    elif kname == "aa_tiled":
+        # levels warmup .. warmup + steps - 1 (the initial state is level 0)
+        n_even = (args.warmup + args.steps + 1) // 2 - (args.warmup + 1) // 2
+        timed_launches = args.steps * (2 + rk_stages) + 2 * n_even
+    elif kname == "aa":
+        timed_launches = args.steps * (2 + rk_stages)
+    else:
+        timed_launches = args.steps * (1 + rk_stages)
 
     # ---------------- e2e: a job through the C ABI with host buffers
     # init from the host droplet table, K steps each returning FP64
@@ -670,7 +682,7 @@ def main():
                                         if cpu_all and "mlups" in cpu_all else cpu_all)}
                          if cpu and "mlups" in cpu else cpu),
         "e2e": e2e,
-        "gpu_launches": args.steps * launches_per_step,
+        "gpu_launches": timed_launches,
         "adjoint": adj,
         "fp64": fp64,
         "fp32_vs_fp64": fp64 and {"speedup": mlups / fp64["mlups"]},

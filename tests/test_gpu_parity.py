@@ -119,25 +119,27 @@ def test_bulk_multi_tile_chunked_fp64(walls, thermal, kernel, monkeypatch):
 
 
 @pytest.mark.parametrize("kernel", ["bulk", "skew"])
-@pytest.mark.parametrize("nx", [74, 75])
-def test_bulk_ghost_fill_paths_fp64(nx, kernel):
+@pytest.mark.parametrize("nx,ny", [(74, 16), (75, 16), (75, 18)])
+def test_bulk_ghost_fill_paths_fp64(nx, ny, kernel):
     """Periodic in x and y with nx a multiple of the 16-byte vector width but
     not of two vectors (74) or not of one (75): the two slower ghost-fill
-    paths, against the oracle."""
-    w = ragged_workload("D3Q7", 15, walls=False, shape=(nx, 16, 8))
+    paths; with ny a multiple of the tile rows or not (18, a last tile row
+    half outside the lattice); against the oracle."""
+    w = ragged_workload("D3Q7", 15, walls=False, shape=(nx, ny, 8))
     o = oracle_for(w)
     o.step(8)
     d = gpu_domain(w, kernel=kernel)
     d.step(8)
-    compare_all(d, o, w, TOL64, f"{kernel} ghost paths nx={nx}")
+    compare_all(d, o, w, TOL64, f"{kernel} ghost paths nx={nx} ny={ny}")
 
 
 @pytest.mark.parametrize("kernel", ["bulk", "skew"])
-@pytest.mark.parametrize("precision,nx", [("fp32", 76), ("fp32", 78), ("fp16", 88), ("fp16", 84)])
-def test_bulk_ghost_fill_paths_reduced_precision(precision, nx, kernel):
+@pytest.mark.parametrize("precision,nx,ny", [("fp32", 76, 16), ("fp32", 78, 16), ("fp32", 78, 18),
+                                             ("fp16", 88, 16), ("fp16", 84, 16), ("fp16", 84, 18)])
+def test_bulk_ghost_fill_paths_reduced_precision(precision, nx, ny, kernel):
     """The same ghost-fill paths in FP32 / FP16 storage: the tiled kernels
     equal the generic one to the storage rounding after 12 periodic steps."""
-    w = ragged_workload("D3Q7", 15, walls=False, precision=precision, shape=(nx, 16, 8))
+    w = ragged_workload("D3Q7", 15, walls=False, precision=precision, shape=(nx, ny, 8))
     a = gpu_domain(w, kernel="generic")
     b = gpu_domain(w, kernel=kernel)
     a.step(12)
