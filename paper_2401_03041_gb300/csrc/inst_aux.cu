@@ -82,12 +82,14 @@ void launch_halo_x(const DevParams& P, S* set, int nq, typename Store<S>::R* T, 
 }
 
 template <class S>
-void launch_ghost_fill(const DevParams& P, void* buf, int nq, cudaStream_t st) {
+void launch_ghost_fill(const DevParams& P, void* buf, int nq, cudaStream_t st, const unsigned char* sides) {
   constexpr int V = 16 / (int)sizeof(S);
   const int per_plane = P.NYP + 2 * P.GY * ((P.nx + V - 1) / V);
   const int bx = (per_plane + 127) / 128;
+  GhostSides g;
+  for (int q = 0; q < kMaxSetArrays; ++q) g.m[q] = (sides && q < nq) ? sides[q] : (unsigned char)15;
   // grid y = z and grid z = direction; nz is bounded by 65535 in the API
-  ghost_fill_kernel<S><<<dim3(bx, P.nz, nq), 128, 0, st>>>(P, (S*)buf);
+  ghost_fill_kernel<S><<<dim3(bx, P.nz, nq), 128, 0, st>>>(P, (S*)buf, g);
 }
 
 template <class S, int QH>
@@ -211,8 +213,11 @@ template void launch_halo_x<float>(const DevParams&, float*, int, float*, int, i
                                    cudaStream_t);
 template void launch_halo_x<__half>(const DevParams&, __half*, int, float*, int, int, void*, size_t, bool,
                                     cudaStream_t);
-template void launch_ghost_fill<double>(const DevParams&, void*, int, cudaStream_t);
-template void launch_ghost_fill<float>(const DevParams&, void*, int, cudaStream_t);
-template void launch_ghost_fill<__half>(const DevParams&, void*, int, cudaStream_t);
+template void launch_ghost_fill<double>(const DevParams&, void*, int, cudaStream_t,
+                                          const unsigned char*);
+template void launch_ghost_fill<float>(const DevParams&, void*, int, cudaStream_t,
+                                          const unsigned char*);
+template void launch_ghost_fill<__half>(const DevParams&, void*, int, cudaStream_t,
+                                          const unsigned char*);
 
 }  // namespace lbm

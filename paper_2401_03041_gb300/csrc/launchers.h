@@ -25,9 +25,12 @@ template <class S, int QH, int QF>
 void launch_step(const DevParams& P, const StepPtrs<S, typename Store<S>::R>& A, const TMaps& maps,
                  dim3 grid, int zchunk, const BulkSched& sched, int mode, int use_bulk, cudaStream_t st);
 
-// Refresh the periodic ghost cells of nq consecutive padded directions at buf.
+// Refresh the periodic ghost cells of nq consecutive padded directions at buf:
+// the sides that sides[q] selects for array q (bits of GhostSides in
+// lbm_aux.cuh; null: every side, the whole periodic extension).
 template <class S>
-void launch_ghost_fill(const DevParams& P, void* buf, int nq, cudaStream_t st);
+void launch_ghost_fill(const DevParams& P, void* buf, int nq, cudaStream_t st,
+                       const unsigned char* sides = nullptr);
 
 // Dynamic shared memory of the bulk kernel for (precision, q_phase, q_f),
 // and the largest a CTA may use; also its tile height.

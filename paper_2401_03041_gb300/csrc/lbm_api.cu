@@ -386,14 +386,54 @@ void rk_tail(lbm_domain* d) {
   }
 }
 
-// Refresh the periodic ghost cells of PDF set k (bulk kernel only).
+// Direction i of stencil Q (7, 15, 19, 27): its velocity components.
+static void stencil_c(int Q, int i, int c[3]) {
+  const int k = (Q == 15 && i >= 7) ? i + 12 : i;   // D3Q15 indexes into D3Q27 past the faces
+  c[0] = q27_cx(k);
+  c[1] = q27_cy(k);
+  c[2] = q27_cz(k);
+}
+
+// The ghost sides the tiled two-grid kernels read, per array of a PDF set
+// (the bits of GhostSides).  g is only pulled into the tile's own cells, so
+// direction c reads the ghosts at depth 1 on the side -c points to: x < 0
+// for c_x = 1, x >= nx for c_x = -1, none for c_x = 0 (y alike).  h and f are
+// also summed into phi and T over the tile's one-cell halo ring, whose pulls
+// reach x = -1 - c_x and x = nx - c_x: the columns x < 0 unless c_x = -1, the
+// columns x >= nx unless c_x = 1.  Beyond a z wall the bounce-back source of
+// a halo cell is the opposite direction at that cell itself, so on plane 0
+// the arrays with c_z = -1 (the opposites of c_z = 1) are read on every side
+// at depth 1, and on plane nz - 1 those with c_z = 1.
+static void ghost_sides(const lbm_domain* d, unsigned char* m) {
+  int q = 0, c[3];
+  auto halo = [&](int Q, int n) {
+    for (int i = 0; i < n; ++i) {
+      stencil_c(Q, i, c);
+      unsigned v = (c[0] >= 0 ? 1u : 0u) | (c[0] <= 0 ? 2u : 0u) | (c[1] >= 0 ? 4u : 0u) | (c[1] <= 0 ? 8u : 0u);
+      if (d->dp.walls) v |= (c[2] < 0 ? 16u : 0u) | (c[2] > 0 ? 32u : 0u);
+      m[q++] = (unsigned char)v;
+    }
+  };
+  halo(d->qh, d->qh);
+  for (int i = 0; i < 27; ++i) {
+    stencil_c(27, i, c);
+    m[q++] = (unsigned char)((c[0] > 0 ? 1u : 0u) | (c[0] < 0 ? 2u : 0u) | (c[1] > 0 ? 4u : 0u) |
+                             (c[1] < 0 ? 8u : 0u));
+  }
+  if (d->qf > 0) halo(d->qf, d->qf);
+}
+
+// Refresh the periodic ghost cells of PDF set k that the tiled kernels read
+// (bulk and skewed kernels only).
 void ghost_fill(lbm_domain* d, int k) {
   if (!d->geo.bulk) return;
   void* base = at(d, d->L.h[k]);
   const int nq = d->qh + 27 + d->qf;
-  if (d->prec == LBM_FP64) launch_ghost_fill<double>(d->dp, base, nq, d->stream);
-  else if (d->prec == LBM_FP32) launch_ghost_fill<float>(d->dp, base, nq, d->stream);
-  else launch_ghost_fill<__half>(d->dp, base, nq, d->stream);
+  unsigned char sides[27 + 27 + 27];
+  ghost_sides(d, sides);
+  if (d->prec == LBM_FP64) launch_ghost_fill<double>(d->dp, base, nq, d->stream, sides);
+  else if (d->prec == LBM_FP32) launch_ghost_fill<float>(d->dp, base, nq, d->stream, sides);
+  else launch_ghost_fill<__half>(d->dp, base, nq, d->stream, sides);
 }
 
 // One step (mode: MODE_COLLIDE [| MODE_DIAG]), or a read-only pass.

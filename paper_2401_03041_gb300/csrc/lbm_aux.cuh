@@ -313,54 +313,75 @@ __global__ void f64_to_pdf_kernel(const DevParams P, const double* __restrict__ 
   }
 }
 
+// Which ghost sides of each array of a PDF set a ghost fill writes (bits:
+// 1 the columns x < 0, 2 the columns x >= nx, 4 the rows y < 0, 8 the rows y
+// >= ny; a corner where its column and row sides both apply; 16 / 32 every
+// side on plane 0 / nz - 1 when the lattice has z walls).  All bits: the
+// whole periodic extension.
+constexpr int kMaxSetArrays = 27 + 27 + 27;
+struct GhostSides {
+  unsigned char m[kMaxSetArrays];
+};
+
 // Periodic ghost cells of one padded PDF buffer of nq directions: every
-// ghost position (x, y) outside [0, nx) x [0, ny) receives the value of cell
-// (x mod nx, y mod ny) of the same plane and direction (the single-GPU form
-// of a ghost-layer exchange).  Grid: x over the items of one plane, y = z,
-// z = direction.  Items [0, NYP): the ghost columns of padded row y (ghost
-// rows included, sources taken from row y mod ny); items [NYP, NYP + 2 GY
-// nvec): one 16-byte vector of interior columns of a ghost row.  With nx a
-// multiple of V = 16 / sizeof(S) (GX = V) a row's two ghost blocks are 16-byte
-// vectors; with nx a multiple of 2V each is written together with the
-// interior half of its 32-byte sector (the same values that half holds), so
-// that no sector is written partially.
+// ghost position (x, y) outside [0, nx) x [0, ny) on a side that sides.m[q]
+// selects receives the value of cell (x mod nx, y mod ny) of the same plane
+// and direction (the single-GPU form of a ghost-layer exchange).  Grid: x
+// over the items of one plane, y = z, z = direction.  Items [0, NYP): the
+// ghost columns of padded row y (ghost rows included, sources taken from row
+// y mod ny); items [NYP, NYP + 2 GY nvec): one 16-byte vector of interior
+// columns of a ghost row.  With nx a multiple of V = 16 / sizeof(S) (GX = V) a
+// row's two ghost blocks are 16-byte vectors; with nx a multiple of 2V each is
+// written together with the interior half of its 32-byte sector (the same
+// values that half holds), so that no sector is written partially.
 template <class S>
-__global__ void __launch_bounds__(128) ghost_fill_kernel(const DevParams P, S* __restrict__ buf) {
+__global__ void __launch_bounds__(128) ghost_fill_kernel(const DevParams P, S* __restrict__ buf,
+                                                         const __grid_constant__ GhostSides sides) {
   constexpr int V = 16 / (int)sizeof(S);
   const int GX = P.GX, GY = P.GY, nx = P.nx, ny = P.ny;
   const int z = blockIdx.y, q = blockIdx.z;
+  unsigned m = sides.m[q];
+  if (P.walls && (((m & 16) && z == 0) || ((m & 32) && z == P.nz - 1))) m |= 15;
+  if ((m & 15) == 0) return;
+  const bool left = m & 1, right = m & 2, low = m & 4, high = m & 8;
   S* plane = buf + (size_t)q * P.Np + (size_t)z * P.NYP * P.NXP;
   const int nvec = (nx + V - 1) / V;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   auto wrap_y = [&](int y) { int ys = y % ny; return ys < 0 ? ys + ny : ys; };
   if (r < P.NYP) {
     const int y = r - GY;
+    if ((y < 0 && !low) || (y >= ny && !high)) return;
     S* row = plane + (size_t)r * P.NXP;                        // element x at row[x + GX]
     const S* src = plane + (size_t)(wrap_y(y) + GY) * P.NXP;
     if (nx % V == 0) {
-      const uint4 a = *reinterpret_cast<const uint4*>(src + GX);           // x = 0 .. V-1
-      const uint4 b = *reinterpret_cast<const uint4*>(src + GX + nx - V);  // x = nx-V .. nx-1
       if (nx % (2 * V) == 0) {
         // sectors [x -V .. V-1] and [x nx-V .. nx+V-1] both become (b, a)
-        uint4* s0 = reinterpret_cast<uint4*>(row);
-        uint4* s1 = reinterpret_cast<uint4*>(row + GX + nx - V);
-        s0[0] = b; s0[1] = a;
-        s1[0] = b; s1[1] = a;
+        const uint4 a = *reinterpret_cast<const uint4*>(src + GX);           // x = 0 .. V-1
+        const uint4 b = *reinterpret_cast<const uint4*>(src + GX + nx - V);  // x = nx-V .. nx-1
+        if (left) {
+          uint4* s0 = reinterpret_cast<uint4*>(row);
+          s0[0] = b; s0[1] = a;
+        }
+        if (right) {
+          uint4* s1 = reinterpret_cast<uint4*>(row + GX + nx - V);
+          s1[0] = b; s1[1] = a;
+        }
       } else {
-        *reinterpret_cast<uint4*>(row) = b;
-        *reinterpret_cast<uint4*>(row + GX + nx) = a;
+        if (left) *reinterpret_cast<uint4*>(row) = *reinterpret_cast<const uint4*>(src + GX + nx - V);
+        if (right) *reinterpret_cast<uint4*>(row + GX + nx) = *reinterpret_cast<const uint4*>(src + GX);
       }
     } else {
       for (int j = 0; j < GX; ++j) {
         int xl = (j - GX) % nx; if (xl < 0) xl += nx;               // ghost x = j - GX
-        row[j] = src[GX + xl];
-        row[GX + nx + j] = src[GX + (j % nx)];                      // ghost x = nx + j
+        if (left) row[j] = src[GX + xl];
+        if (right) row[GX + nx + j] = src[GX + (j % nx)];            // ghost x = nx + j
       }
     }
   } else {
     const int k = r - P.NYP;
     if (k >= 2 * GY * nvec) return;
     const int which = k / nvec, j = k - which * nvec;
+    if ((which < GY && !low) || (which >= GY && !high)) return;
     const int y = which < GY ? which - GY : ny + (which - GY);      // ghost row
     S* dst = plane + (size_t)(y + GY) * P.NXP + GX + j * V;
     const S* src = plane + (size_t)(wrap_y(y) + GY) * P.NXP + GX + j * V;
