@@ -88,15 +88,18 @@ def test_ragged_walls_fp64(thermal, q_phase):
         compare_all(d, o, w, TOL64, f"ragged walls {thermal} q{q_phase} {kern}")
 
 
-@pytest.mark.parametrize("thermal", ["D3Q7", "D3Q15", "D3Q19", "RK2", "RK4"])
-def test_ragged_periodic_fp64(thermal):
-    w = ragged_workload(thermal, 15, walls=False)
+@pytest.mark.parametrize("thermal,q_phase", [("D3Q7", 15), ("D3Q15", 15), ("D3Q19", 15), ("RK2", 15), ("RK4", 15),
+                                             ("D3Q27", 15), ("D3Q7", 27), ("D3Q27", 27)])
+def test_ragged_periodic_fp64(thermal, q_phase):
+    """Periodic in x, y and z: every ghost side the tiled kernels read, for
+    each stencil of h, g and f (the ghost fill refreshes only those)."""
+    w = ragged_workload(thermal, q_phase, walls=False)
     o = oracle_for(w)
     o.step(12)
-    for kern in _kernels("fp64", 15, thermal):
+    for kern in _kernels("fp64", q_phase, thermal):
         d = gpu_domain(w, kernel=kern)
         d.step(12)
-        compare_all(d, o, w, TOL64, f"ragged periodic {thermal} {kern}")
+        compare_all(d, o, w, TOL64, f"ragged periodic {thermal} q{q_phase} {kern}")
 
 
 @pytest.mark.parametrize("kernel", ["bulk", "skew"])
@@ -149,6 +152,25 @@ def test_bulk_ghost_fill_paths_reduced_precision(precision, nx, ny, kernel):
     for k in ("phi", "u", "p", "T"):
         e = relerr(fb[k], fa[k])
         assert e < tol, (precision, nx, k, e)
+
+
+@pytest.mark.parametrize("thermal,q_phase", [("D3Q19", 15), ("D3Q27", 15), ("D3Q7", 27)])
+def test_tiled_equals_generic_periodic_fp32(thermal, q_phase):
+    """Periodic FP32 lattices with the larger stencils: the library's tiled
+    kernel (skewed, or bulk where the skewed layout does not fit) equals the
+    generic one to the storage rounding after 20 steps, so every ghost side it
+    reads is refreshed."""
+    w = ragged_workload(thermal, q_phase, walls=False, precision="fp32", shape=(80, 24, 12))
+    a = gpu_domain(w, kernel="generic")
+    b = gpu_domain(w)
+    assert b.kernel_info()["kernel"] in ("bulk", "skew"), b.kernel_info()
+    a.step(20)
+    b.step(20)
+    fa, fb = gpu_fields(a), gpu_fields(b)
+    for k in ("phi", "u", "p", "T"):
+        e = relerr(fb[k], fa[k])
+        print(thermal, q_phase, b.kernel_info()["kernel"], k, f"{e:.2e}")
+        assert e < 1e-5, (k, e)
 
 
 @pytest.mark.parametrize("kernel", ["bulk", "skew"])
