@@ -90,6 +90,21 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
+def timed_launch_count(kernel: str, thermal: str, steps: int, warmup: int) -> int:
+    """Kernel launches of `steps` timed steps after `warmup` steps from the
+    initial state (level 0): the step kernel, + the ghost fill after it with
+    the tiled kernels (the generic one wraps its reads); in place, the (phi, T)
+    pass + the step, + a ghost refresh and a fold around the tiled steps from
+    even levels; + the RK stages of the finite-difference energy solvers."""
+    rk_stages = 0 if thermal.startswith("D3Q") else (1 if thermal == "RK2" else 3)
+    if kernel in ("skew", "bulk", "aa"):
+        return steps * (2 + rk_stages)
+    if kernel == "aa_tiled":
+        n_even = (warmup + steps + 1) // 2 - (warmup + 1) // 2   # levels warmup .. warmup + steps - 1
+        return steps * (2 + rk_stages) + 2 * n_even
+    return steps * (1 + rk_stages)
+
+
 # What each step-kernel choice of lbm_kernel_info is, for the roofline record.
 KERNEL_NAMES = {
     "skew": "lbm::step_skew_kernel (fused h/g/f stream-collide, tensor-TMA staging, two threads per cell "
@@ -421,22 +436,7 @@ def main():
     cells = w.cells
     mlups = job_mlups(cells, args.steps, world, secs)
     per_step = secs / args.steps
-    # launches of the timed steps: the step kernel, + the ghost fill after it
-    # with the tiled kernels (the generic one wraps its reads); in place, the
-    # (phi, T) pass + the step, + a ghost refresh and a fold around the tiled
-    # steps from even levels; + the RK stages of the finite-difference solvers
-    rk_stages = 0 if w.thermal.startswith("D3Q") else (1 if w.thermal == "RK2" else 3)
-    kname = kinfo["kernel"]
-    if kname in ("skew", "bulk"):
-        timed_launches = args.steps * (2 + rk_stages)
-    elif kname == "aa_tiled":
-        # levels warmup .. warmup + steps - 1 (the initial state is level 0)
-        n_even = (args.warmup + args.steps + 1) // 2 - (args.warmup + 1) // 2
-        timed_launches = args.steps * (2 + rk_stages) + 2 * n_even
-    elif kname == "aa":
-        timed_launches = args.steps * (2 + rk_stages)
-    else:
-        timed_launches = args.steps * (1 + rk_stages)
+    timed_launches = timed_launch_count(kinfo["kernel"], w.thermal, args.steps, args.warmup)
 
     # ---------------- e2e: a job through the C ABI with host buffers
     # init from the host droplet table, K steps each returning FP64
